@@ -1,0 +1,16 @@
+"""B300-native cross-correlation sub-pixel tracking (arXiv 2310.08770).
+
+The compute path lives in the CUDA library ``libccst.so`` (built from
+``csrc/``); :mod:`.ccst` is a thin ctypes binding to its C ABI. Importing the
+package does not load the library: the first call that needs it does, and it
+raises if the library is missing.
+"""
+_BINDING = ("CC_SN", "CC_U", "Tracker", "ccst_create", "ccst_destroy", "ccst_track",
+            "ccst_version", "library_path", "CcstError")
+
+
+def __getattr__(name):
+    if name in _BINDING:
+        from . import ccst
+        return getattr(ccst, name)
+    raise AttributeError(name)

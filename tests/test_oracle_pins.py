@@ -1,0 +1,340 @@
+"""Pins of the FP64 oracle to facts fixed by the paper and by mathematics.
+
+None of these re-types the oracle's formulas: each compares it with an
+independent route (direct sum vs FFT, Dirichlet-kernel brute force), an exact
+answer (integer rolls, noise-free band-limited spots, the sign flip of Eq. (4)
+under swapping the images), a value the paper prints (the u = 256 grid), or a
+statistical bound (the Poisson Cramer-Rao limit of Sec. IV).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import CC_SN, CC_U
+from paper_2310_08770_b300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def paper_constants():
+    out = {}
+    with open(os.path.join(GOLDEN, "paper_constants.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            key, val = line.split()[:2]
+            out[key] = float(val)
+    return out
+
+
+# ---------------------------------------------------------------- grid (Sec. III)
+def test_grid_matches_paper_example():
+    c = paper_constants()
+    assert oracle.grid_size(256) == int(c["grid_points_u256"])
+    # the grid spans the 1.5-pixel square: M/u ~ 1.5 and offsets straddle 0
+    for u in (1, 2, 3, 7, 100, 128, 256, 1024):
+        M = oracle.grid_size(u)
+        assert M == math.ceil(c["grid_span_px"] * u)
+        offs = (np.arange(M) - M // 2) / u
+        assert 0.0 in offs
+        # M points at spacing 1/u, floor(M/2) of them below the centre
+        assert offs[0] >= -0.75 - 0.5 / u and offs[-1] <= 0.75
+        assert (M - 1) / u <= 1.5
+
+
+def test_signed_frequency_convention():
+    assert list(oracle.signed_freq(8)) == [0, 1, 2, 3, -4, -3, -2, -1]
+    assert list(oracle.signed_freq(5)) == [0, 1, 2, -2, -1]
+    assert np.array_equal(oracle.signed_freq(12), np.fft.fftfreq(12, 1 / 12).astype(int))
+
+
+# ---------------------------------------------------------------- Eq. (4) identity
+@pytest.mark.parametrize("shape", [(8, 8), (12, 8), (6, 10), (16, 16)])
+@pytest.mark.parametrize("method", [CC_U, CC_SN])
+def test_direct_sum_equals_fft_route(shape, method):
+    rng = np.random.default_rng(7)
+    I = rng.poisson(100.0, size=shape).astype(float)
+    E = rng.uniform(5.0, 500.0, size=shape)
+    a, b, _ = oracle.surface_operands(I, E, method, 200.0)
+    cd = oracle.cc_surface_direct(a, b)
+    cf = oracle.cc_surface_fft(a, b)
+    scale = np.sum(np.abs(a)) * np.sum(np.abs(b))
+    assert np.max(np.abs(cd - cf)) <= 1e-13 * scale
+    # a shift moves the surface by the same shift (translation covariance)
+    cs = oracle.cc_surface_direct(np.roll(a, (2, 3), axis=(0, 1)), b)
+    assert np.allclose(cs, np.roll(cd, (2, 3), axis=(0, 1)), rtol=0, atol=1e-12 * scale)
+
+
+@pytest.mark.parametrize("method", [CC_U, CC_SN])
+def test_surface_is_chi_square_up_to_constants(method):
+    # Eq. (1) with sigma = const (CC-U, Eqs. (2)-(3)) or sigma^2 = E (CC-SN, Eqs. (5)-(6)):
+    # chi^2(s) = sum_r (I'(r+s) - E(r))^2 / sigma^2(r) must equal the surface up to an
+    # affine map that does not depend on s, and its minimum is the surface's extremum.
+    rng = np.random.default_rng(9)
+    H, W = 10, 12
+    I = rng.poisson(200.0, size=(H, W)).astype(float)
+    E = rng.uniform(20.0, 400.0, size=(H, W))
+    eps = 200.0
+    a, b, sense = oracle.surface_operands(I, E, method, eps)
+    c = oracle.cc_surface_direct(a, b)
+    Ip = I + eps if method == CC_SN else I
+    Ew = E + eps if method == CC_SN else E
+    var = Ew if method == CC_SN else np.ones_like(E)
+    chi2 = np.empty((H, W))
+    for sy in range(H):
+        for sx in range(W):
+            shifted = np.roll(Ip, (-sy, -sx), axis=(0, 1))      # shifted[r] = I'(r + s)
+            chi2[sy, sx] = np.sum((shifted - Ew) ** 2 / var)
+    if method == CC_SN:
+        expect = c - 2 * np.sum(Ip) + np.sum(Ew)                 # Eq. (6)
+    else:
+        expect = np.sum(I * I) + np.sum(E * E) - 2 * c          # Eq. (2)-(3)
+    assert np.allclose(chi2, expect, rtol=1e-12, atol=0)
+    assert oracle.extremum_index(c, sense) == int(np.argmin(chi2))
+
+
+def test_direct_sum_small_case_by_hand():
+    # 1-D-like 2x2 case worked by hand: a = [[1,2],[3,4]], b = [[1,0],[0,0]]
+    # c(s) = a(s) * b(0) -> c == a
+    a = np.array([[1.0, 2.0], [3.0, 4.0]])
+    b = np.array([[1.0, 0.0], [0.0, 0.0]])
+    assert np.array_equal(oracle.cc_surface_direct(a, b), a)
+    # b = delta at (0,1): c(s) = a(s + (0,1)) -> columns rolled left by one
+    b2 = np.array([[0.0, 1.0], [0.0, 0.0]])
+    assert np.array_equal(oracle.cc_surface_direct(a, b2), np.array([[2.0, 1.0], [4.0, 3.0]]))
+
+
+# ---------------------------------------------------------------- P1 exact integer shifts
+def _refs():
+    rng = np.random.default_rng(3)
+    return [
+        ("gauss64", synth.gaussian_spot(64, 64, 32.0, 32.0, 3.0, 1000.0, 10.0)),
+        ("texture48x40", synth.random_texture(rng, 48, 40)),
+        ("gauss16x24", synth.gaussian_spot(16, 24, 7.3, 12.1, 1.7, 500.0, 3.0)),
+    ]
+
+
+@pytest.mark.parametrize("name,E", _refs())
+@pytest.mark.parametrize("u", [1, 2, 7, 100])
+def test_integer_roll_recovered_exactly_ccu(name, E, u):
+    H, W = E.shape
+    for dy, dx in [(0, 0), (1, -2), (-5, 7), (H // 2, -(W // 2) + 1), (-(H // 2) + 1, W // 2), (3, 0)]:
+        I = np.roll(E, (dy, dx), axis=(0, 1))        # I(r) = E(r - d)
+        r = oracle.track_one(I, E, u=u, method=CC_U)
+        assert (r["ipy"], r["ipx"]) == (dy, dx)
+        assert r["dy"] == dy and r["dx"] == dx
+        # the peak value is the direct sum sum_r I(r + d) E(r) = sum E^2
+        assert r["peak"] == pytest.approx(np.sum(E * E), rel=1e-12)
+
+
+@pytest.mark.parametrize("name,E", _refs())
+def test_integer_roll_recovered_ccsn(name, E):
+    H, W = E.shape
+    for dy, dx in [(0, 0), (2, -3), (-(H // 2) + 1, W // 2)]:
+        I = np.roll(E, (dy, dx), axis=(0, 1))
+        r = oracle.track_one(I, E, u=50, method=CC_SN, eps=200.0)
+        # Cauchy-Schwarz: sum a(r+s)^2 / a(r) >= sum a with equality only when aligned
+        assert (r["ipy"], r["ipx"]) == (dy, dx)
+
+
+# ---------------------------------------------------------------- P2 sign flip
+def test_swap_flips_sign_exactly():
+    rng = np.random.default_rng(11)
+    E = synth.gaussian_spot(64, 64, 32.0, 32.0, 3.0, 1000.0, 10.0)
+    checked = 0
+    for _ in range(12):
+        d = rng.uniform(-6, 6, size=2)
+        I = synth.poisson_frame(rng, synth.gaussian_spot(64, 64, 32 + d[1], 32 + d[0], 3.0, 1000.0, 10.0))
+        a = oracle.track_one(I, E, u=100)
+        b = oracle.track_one(E, I, u=100)
+        M = oracle.grid_size(100)
+        if a["jx"] == 0 or a["jy"] == 0 or a["sub_margin"] < 1e-9:
+            continue                                  # asymmetric grid edge / genuine tie
+        assert b["dx"] == -a["dx"] and b["dy"] == -a["dy"]
+        assert b["peak"] == pytest.approx(a["peak"], rel=1e-12)
+        assert M == 150
+        checked += 1
+    assert checked >= 8
+
+
+# ---------------------------------------------------------------- P3 noise-free sub-pixel spots
+@pytest.mark.parametrize("u,d", [
+    (100, (0.37, -1.21)),
+    (256, (0.37, -1.21)),
+    (100, (2.123, 0.456)),
+    (10, (-3.31, 4.77)),
+    (37, (0.9, -0.25)),
+])
+@pytest.mark.parametrize("sigma,N", [(3.0, 64), (2.5, 128)])
+def test_noise_free_subpixel_is_nearest_grid_point(u, d, sigma, N):
+    # keep the test shift at least 0.1 bin from a half-bin, as the nearest point must be unique
+    for v in d:
+        frac = (u * v) % 1.0
+        assert abs(frac - 0.5) > 0.1
+    c = N / 2.0
+    E = synth.gaussian_spot(N, N, c, c, sigma, 1000.0, 10.0)
+    I = synth.gaussian_spot(N, N, c + d[1], c + d[0], sigma, 1000.0, 10.0)
+    r = oracle.track_one(I, E, u=u)
+    assert r["dx"] == round(u * d[0]) / u
+    assert r["dy"] == round(u * d[1]) / u
+
+
+def test_paper_u256_example_values():
+    # u = 256, shift (0.37, -1.21): round(256 d)/256 = (0.37109375, -1.2109375)
+    E = synth.gaussian_spot(64, 64, 32.0, 32.0, 3.0, 1000.0, 10.0)
+    I = synth.gaussian_spot(64, 64, 32.0 - 1.21, 32.37, 3.0, 1000.0, 10.0)
+    r = oracle.track_one(I, E, u=256)
+    assert (r["dx"], r["dy"]) == (0.37109375, -1.2109375)
+
+
+# ---------------------------------------------------------------- P5 interpolation identity
+@pytest.mark.parametrize("method", [CC_U, CC_SN])
+def test_grid_centre_equals_direct_sum(method):
+    p = synth.single_pair()
+    a, b, sense = oracle.surface_operands(p.frame, p.ref, method, 200.0)
+    c = oracle.cc_surface_direct(a, b)
+    X = oracle.product_spectrum(a, b)
+    H, W = a.shape
+    idx = oracle.extremum_index(c, sense)
+    py, px = oracle.wrap_shift(idx // W, H), oracle.wrap_shift(idx % W, W)
+    cu = oracle.upsampled_cc(X, py, px, 100)
+    M = oracle.grid_size(100)
+    assert cu[M // 2, M // 2] == pytest.approx(c[py % H, px % W], rel=1e-12)
+    # and every integer offset inside the square reproduces the integer surface
+    u = 4
+    cu4 = oracle.upsampled_cc(X, py, px, u)
+    M4 = oracle.grid_size(u)
+    for jy in range(M4):
+        for jx in range(M4):
+            oy, ox = jy - M4 // 2, jx - M4 // 2
+            if oy % u == 0 and ox % u == 0:
+                sy, sx = (py + oy // u) % H, (px + ox // u) % W
+                assert cu4[jy, jx] == pytest.approx(c[sy, sx], rel=1e-12)
+
+
+# ---------------------------------------------------------------- P6 Dirichlet-kernel brute force
+def _dirichlet(N, x):
+    k = np.fft.fftfreq(N, 1.0 / N)          # numpy's own signed-frequency set
+    return np.exp(2j * np.pi * np.multiply.outer(x, k) / N).sum(-1) / N
+
+
+@pytest.mark.parametrize("shape,u", [((8, 8), 6), ((6, 10), 5), ((5, 7), 4)])
+@pytest.mark.parametrize("method", [CC_U, CC_SN])
+def test_upsampled_grid_equals_dirichlet_brute_force(shape, u, method):
+    rng = np.random.default_rng(5)
+    H, W = shape
+    I = rng.poisson(50.0, size=shape).astype(float) + 5
+    E = rng.uniform(10.0, 100.0, size=shape)
+    a, b, sense = oracle.surface_operands(I, E, method, 200.0)
+    X = oracle.product_spectrum(a, b)
+    c = oracle.cc_surface_fft(a, b)
+    idx = oracle.extremum_index(c, sense)
+    py, px = oracle.wrap_shift(idx // W, H), oracle.wrap_shift(idx % W, W)
+    cu = oracle.upsampled_cc(X, py, px, u)
+    M = oracle.grid_size(u)
+    oy = py + (np.arange(M) - M // 2) / u
+    ox = px + (np.arange(M) - M // 2) / u
+    ry = np.arange(H)
+    rx = np.arange(W)
+    # Dy[j, r, r'] = D_H(r' - r + s_j)
+    Dy = _dirichlet(H, ry[None, None, :] - ry[None, :, None] + oy[:, None, None])
+    Dx = _dirichlet(W, rx[None, None, :] - rx[None, :, None] + ox[:, None, None])
+    brute = np.real(np.einsum("yx,zw,jyz,kxw->jk", a, b, Dy, Dx))
+    scale = np.sum(np.abs(a)) * np.sum(np.abs(b))
+    assert np.max(np.abs(brute - cu)) <= 1e-12 * scale
+    r = oracle.track_one(I, E, u=u, method=method)
+    j = oracle.extremum_index(brute, sense)
+    assert (r["jy"], r["jx"]) == divmod(j, M)
+
+
+# ---------------------------------------------------------------- config 1 and degenerate cases
+def test_config1_single_pair():
+    p = synth.single_pair()
+    r = oracle.track_one(p.frame, p.ref, u=100)
+    assert abs(r["dx"] - 0.37) < 0.05 and abs(r["dy"] + 1.21) < 0.05
+    r2 = oracle.track_one(p.frame, p.ref, u=100, integer_route="direct")
+    assert (r2["dx"], r2["dy"], r2["ipx"], r2["ipy"]) == (r["dx"], r["dy"], r["ipx"], r["ipy"])
+
+
+def test_constant_frame_ties_go_to_lowest_index():
+    E = synth.gaussian_spot(16, 16, 8.0, 8.0, 2.0, 100.0, 5.0)
+    I = np.full((16, 16), 7.0)
+    r = oracle.track_one(I, E, u=10)
+    M = oracle.grid_size(10)
+    assert (r["ipy"], r["ipx"], r["jy"], r["jx"]) == (0, 0, 0, 0)
+    assert r["dx"] == r["dy"] == -(M // 2) / 10
+
+
+def test_ccsn_approaches_ccu_for_large_offset():
+    # Sec. IV: for large eps the CC-SN results approach those of CC-U
+    rng = np.random.default_rng(2)
+    E = synth.gaussian_spot(64, 64, 32.0, 32.0, 3.0, 1000.0, 10.0)
+    for _ in range(4):
+        d = rng.uniform(-3, 3, size=2)
+        I = synth.poisson_frame(rng, synth.gaussian_spot(64, 64, 32 + d[1], 32 + d[0], 3.0, 1000.0, 10.0))
+        ru = oracle.track_one(I, E, u=100, method=CC_U)
+        # eps = 1e5: the O(E/eps) correction is far below one bin, and the
+        # informative part of the surface is still far above float64 rounding
+        rs = oracle.track_one(I, E, u=100, method=CC_SN, eps=1e5)
+        assert (rs["dx"], rs["dy"]) == (ru["dx"], ru["dy"])
+        r200 = oracle.track_one(I, E, u=100, method=CC_SN, eps=200.0)
+        assert abs(r200["dx"] - d[0]) < 0.08 and abs(r200["dy"] - d[1]) < 0.08
+
+
+# ---------------------------------------------------------------- P4 Cramer-Rao bound (Sec. IV)
+def _crlb_x(H, W, y0, x0, sigma, A, bg):
+    """sqrt of the (x, x) element of the inverse pixelated Poisson Fisher information."""
+    def g_and_dg(n, c):
+        i = np.arange(n, dtype=float)
+        s = math.sqrt(2.0) * sigma
+        from scipy.special import erf
+        g = sigma * math.sqrt(math.pi / 2) * (erf((i + 0.5 - c) / s) - erf((i - 0.5 - c) / s))
+        dg = -(np.exp(-((i + 0.5 - c) ** 2) / (2 * sigma ** 2)) - np.exp(-((i - 0.5 - c) ** 2) / (2 * sigma ** 2)))
+        return g, dg
+    gy, dgy = g_and_dg(H, y0)
+    gx, dgx = g_and_dg(W, x0)
+    mu = bg + A * np.outer(gy, gx)
+    dmx = A * np.outer(gy, dgx)
+    dmy = A * np.outer(dgy, gx)
+    J = np.array([[np.sum(dmx * dmx / mu), np.sum(dmx * dmy / mu)],
+                  [np.sum(dmy * dmx / mu), np.sum(dmy * dmy / mu)]])
+    return math.sqrt(np.linalg.inv(J)[0, 0])
+
+
+def test_fisher_bound_reduces_to_paper_limit_without_background():
+    # Sec. IV: shot-noise limit w0 / (2 sqrt(N_gamma)), w0 = 2 sigma, N_gamma = 2 pi sigma^2 A
+    sigma, A = 6.0, 1000.0
+    crlb = _crlb_x(128, 128, 64.0, 64.0, sigma, A, 1e-9)
+    limit = (2 * sigma) / (2 * math.sqrt(2 * math.pi * sigma ** 2 * A))
+    # pixelation adds a small excess (~1/(12 sigma^2) in variance); it is below 2 % here
+    assert limit <= crlb <= 1.02 * limit
+
+
+def test_oracle_error_respects_cramer_rao_bound():
+    K, u = 300, 100
+    d = (0.37, -1.21)
+    E = synth.gaussian_spot(64, 64, 32.0, 32.0, 3.0, 1000.0, 10.0).astype(np.float32)
+    mu = synth.gaussian_spot(64, 64, 32.0 + d[1], 32.0 + d[0], 3.0, 1000.0, 10.0)
+    rng = np.random.default_rng(0)
+    err = np.array([oracle.track_one(rng.poisson(mu).astype(np.float32), E, u=u)["dx"] - d[0]
+                    for _ in range(K)])
+    crlb = _crlb_x(64, 64, 32.0 + d[1], 32.0 + d[0], 3.0, 1000.0, 10.0)
+    std = err.std(ddof=1)
+    assert std >= crlb * (1 - 3 / math.sqrt(2 * K))
+    assert std <= 2.5 * math.sqrt(crlb ** 2 + 1 / (12 * u ** 2))
+    assert abs(err.mean()) < 4 * std / math.sqrt(K) + 1e-3
+
+
+def test_single_pair_matches_stored_oracle_values():
+    import json
+    with open(os.path.join(GOLDEN, "single_pair_oracle.json")) as f:
+        g = json.load(f)
+    p = synth.single_pair(seed=0)
+    for name, method in (("ccu", CC_U), ("ccsn", CC_SN)):
+        r = oracle.track_one(p.frame, p.ref, u=100, method=method, eps=200.0)
+        for k in ("dx", "dy", "ipy", "ipx", "jy", "jx"):
+            assert r[k] == g[name][k]
+        assert r["peak"] == pytest.approx(g[name]["peak"], rel=1e-12)
