@@ -1,0 +1,415 @@
+#!/usr/bin/env python3
+"""Throughput / latency benchmark of the cross-correlation tracking hot path.
+
+Workload (frame stream): 10,000 uint16 128x128 frames of a Gaussian spot
+(sigma 2.5 px, peak 2000 photons, background 20, Poisson noise) on a reflected
+2-D Brownian trajectory (step 0.3 px), tracked against one noise-free reference
+with u = 100, CC-U, in 256-frame batches (the last batch has 16 frames), one
+CUDA-graph launch per batch. One step = one batch. The stream (328 MB) is larger
+than L2 and is staged in HBM before timing; consecutive steps read different
+slices of it.
+
+Prints one JSON line (see the repository's design notes for every key).
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H = W = 128
+U = 100
+N_FRAMES = 10_000
+BATCH = 256
+SM_COUNT = 148
+FP32_LANES_PER_SM = 128          # FFMA lanes per SM (4 SMSPs x 32)
+MAX_SM_MHZ = 2032.0
+PROFILE_FILE = os.path.join(ROOT, "profiles", "track_kernel_128x128_u100.txt")
+KERNEL_SOURCES = ["paper_2310_08770_b300/csrc/ccst_kernels.cuh", "paper_2310_08770_b300/csrc/ccst_device.cuh"]
+
+
+def grid_size(u):
+    return (3 * u + 1) // 2
+
+
+def flop_per_frame(h=H, w=W, u=U):
+    """Algorithmic FP32 flops of one frame in the folded formulation the kernel computes."""
+    m = grid_size(u)
+    h0 = m // 2
+    wc = w // 2 + 1
+    fft = 2 * 2.5 * h * w * math.log2(h * w)           # R2C forward + C2R inverse
+    product = 6 * h * wc                                 # X = F[a] conj F[b]
+    stage_a = h0 * wc * (h // 2) * 8                     # U', V: 4 FMA per (t, kx, m)
+    stage_b = m * m * wc * 2                             # one FMA per (grid point, kx)
+    g_row = (h0 + 1) * wc * 4
+    return fft + product + stage_a + stage_b + g_row
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel."""
+    try:
+        with open(PROFILE_FILE) as f:
+            kv = dict(line.split(":", 1) for line in f if ":" in line and not line.startswith("#"))
+        kv = {k.strip(): v.strip() for k, v in kv.items()}
+        if kv.get("kernel_source_hash") != kernel_source_hash():
+            return None
+        return float(kv["dram_bytes_per_launch_full_batch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for r in csv.reader(f):
+                if len(r) >= 9:
+                    rows.append([x.strip() for x in r])
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = np.array([num(r[1]) for r in rows])
+        mx = np.array([num(r[2]) for r in rows])
+        pw = np.array([num(r[3]) for r in rows])
+        load = pw >= np.nanmax(pw) * 0.6 if np.isfinite(pw).any() else np.ones_like(sm, bool)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.nanmedian(sm[load])), "sm_max_mhz": float(np.nanmax(mx)),
+                "power_w_max": float(np.nanmax(pw)), "samples": int(len(rows)), "reasons": reasons}
+
+
+# ---------------------------------------------------------------- distributed plumbing
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def shard_seed(rank: int) -> int:
+    """Each rank tracks its own independent stream (weak scaling); rank 0 is the seed-0 workload."""
+    return rank
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weighted_percentile(values, weights, q):
+    order = np.argsort(values)
+    v = np.asarray(values, float)[order]
+    w = np.asarray(weights, float)[order]
+    c = np.cumsum(w)
+    return float(v[np.searchsorted(c, q / 100.0 * c[-1])])
+
+
+# ---------------------------------------------------------------- CPU baseline (oracle)
+def _oracle_chunk(args):
+    import oracle
+    frames, ref = args
+    return oracle.track_batch(frames, ref, u=U)
+
+
+def cpu_baseline(frames, ref, budget_s=15.0):
+    """The FP64 oracle, as it stands, over all host cores on a bounded sample of the stream."""
+    import multiprocessing as mp
+    import oracle
+    t0 = time.perf_counter()
+    oracle.track_one(frames[0], ref, u=U)
+    t1 = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    n = int(min(len(frames), max(cores, budget_s * cores / max(t1, 1e-3))))
+    n = max(1, min(n, 4096))
+    ctx = mp.get_context("spawn")
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_chunk, [(frames[:1], ref)] * cores)          # start-up outside the timing
+        chunks = [(c, ref) for c in np.array_split(frames[:n], cores) if len(c)]
+        t0 = time.perf_counter()
+        parts = pool.map(_oracle_chunk, chunks)
+        dt = time.perf_counter() - t0
+    res = [r for p in parts for r in p]
+    return res, {"value": n / dt, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                 "sample": f"first {n} frames of the 128x128 stream, FP64 numpy oracle, "
+                           f"{cores} spawn workers with one BLAS thread each"}
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    from paper_2310_08770_b300 import ccst as C
+    from paper_2310_08770_b300 import synth
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    s = synth.frame_stream(seed=shard_seed(rank), n=N_FRAMES)
+    frames_dev = torch.from_numpy(s.frames.view(np.int16)).cuda().view(torch.uint16)
+    nb = (N_FRAMES + BATCH - 1) // BATCH
+    outs = torch.empty((N_FRAMES, 24), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    t = C.Tracker(s.ref, upsample=U, method="ccu", in_dtype="u16", max_batch=BATCH, stream=stream,
+                  graphs=True, profile=True)
+
+    def step(i):
+        b = i % nb
+        lo, hi = b * BATCH, min(N_FRAMES, (b + 1) * BATCH)
+        C.ccst_track(t.ctx, frames_dev[lo:hi], hi - lo, 0, outs[lo:hi])
+        return hi - lo
+
+    with torch.cuda.stream(stream):
+        for i in range(max(args.warmup, nb)):          # warm-up also captures every batch's graph
+            step(i)
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        sizes = []
+        clocks = ClockSampler(local)
+        clocks.start()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        C.ccst_profile_reset(t.ctx)
+        for i in range(args.steps):
+            starts[i].record(stream)
+            sizes.append(step(i))
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        clk = clocks.stop()
+    lat_ms = np.array([starts[i].elapsed_time(ends[i]) for i in range(args.steps)])
+    total_ms = starts[0].elapsed_time(ends[-1])
+    kern_ms, kern_launches = C.ccst_profile_kernel_ms(t.ctx)
+    total_ms_max = max_over_ranks(total_ms, world, device="cuda")
+    frames_all = sum(sizes) * world
+    value = frames_all / (total_ms_max / 1e3)
+
+    # roofline of the dominant kernel (FP32 ALU bound): the graphs' last replays cover
+    # every batch of the stream once
+    kframes = N_FRAMES if kern_launches == nb else kern_launches * BATCH
+    fpf = flop_per_frame()
+    achieved = fpf * kframes / (kern_ms / 1e3) / 1e12
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    res_all = C.decode(outs)
+    flags = res_all["flags"]
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    e2e_steps = min(args.steps, 2 * nb)
+    pinned_t = torch.from_numpy(s.frames.view(np.int16)).pin_memory()
+    pinned = pinned_t.numpy().view(np.uint16)
+    host_out_t = torch.empty((BATCH * 24,), dtype=torch.uint8).pin_memory()
+    host_out = host_out_t.numpy().view(C.RESULT_DTYPE)
+    for i in range(3):
+        C.ccst_track_host(t.ctx, pinned[:BATCH], BATCH, 0, host_out)
+    t0 = time.perf_counter()
+    e2e_frames = 0
+    for i in range(e2e_steps):
+        b = i % nb
+        lo, hi = b * BATCH, min(N_FRAMES, (b + 1) * BATCH)
+        C.ccst_track_host(t.ctx, pinned[lo:hi], hi - lo, 0, host_out[:hi - lo])
+        e2e_frames += hi - lo
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, device="cuda")
+    e2e = {"value": e2e_frames * world / e2e_s, "unit": "frames/s",
+           "h2d_bytes_per_step": BATCH * H * W * 2, "d2h_bytes_per_step": BATCH * 24,
+           "api": "ccst_track_host (pinned host frames in, host results out, synchronous per batch)"}
+
+    line = {
+        "metric": "frames/s and p50/p99 per-frame latency (us) at 128x128, <=1e-3 px vs FP64 oracle",
+        "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "p50_us": weighted_percentile(lat_ms * 1e3, sizes, 50), "p99_us": weighted_percentile(lat_ms * 1e3, sizes, 99),
+        "config": {"workload": "frame stream: 10000 uint16 128x128 Gaussian-spot frames (sigma 2.5, peak 2000, "
+                               "bg 20, Poisson), Brownian trajectory step 0.3 px, u=100, CC-U, "
+                               "256-frame CUDA-graph batches",
+                   "global_batch": BATCH * world, "frames_per_rank": N_FRAMES, "upsample": U,
+                   "parallelism": f"replicas x{world} (independent streams)",
+                   "l2": "inputs larger than L2 (328 MB stream per rank, each step reads a new 8.4 MB slice)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": profiled_traffic(),
+                     "kernel": "track_kernel", "flop_per_frame": fpf,
+                     "kernel_ms_per_full_batch": kern_ms / max(kern_launches, 1),
+                     "peak_basis": "148 SMs x 128 FP32 FMA lanes x 2 x 2032 MHz (nominal max clock)"},
+        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+        "guard": {"frames": int(len(flags)), "int": int(np.sum((flags & C.R_INT_GUARD) != 0)),
+                  "sub": int(np.sum((flags & C.R_SUB_GUARD) != 0)), "fp64": int(np.sum((flags & C.R_FP64) != 0)),
+                  "overflow": int(np.sum((flags & C.R_OVERFLOW) != 0))},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        orc, cb = cpu_baseline(s.frames, s.ref)
+        n = len(orc)
+        g = res_all[:n]
+        mism = sum(1 for a, o in zip(g, orc)
+                   if (int(a["ipy"]), int(a["ipx"])) != (o["ipy"], o["ipx"])
+                   or abs(float(a["dx"]) - o["dx32"]) > 1e-3 or abs(float(a["dy"]) - o["dy32"]) > 1e-3)
+        line["cpu_baseline"] = cb
+        line["parity"] = {"frames": n, "mismatches": mism, "tolerance_px": 1e-3}
+    t.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- reference arm (the oracle)
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import multiprocessing as mp
+    import oracle
+    from paper_2310_08770_b300 import synth
+    s = synth.frame_stream(seed=0, n=N_FRAMES)
+    t0 = time.perf_counter()
+    oracle.track_one(s.frames[0], s.ref, u=U)
+    t1 = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    budget = 150.0
+    per_step = int(max(1, budget * cores / ((args.steps + args.warmup) * max(t1, 1e-3))))
+    per_step = min(per_step, BATCH)
+    use_pool = per_step >= cores
+    pool = None
+    if use_pool:
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[k] = "1"
+        pool = mp.get_context("spawn").Pool(cores)
+        pool.map(_oracle_chunk, [(s.frames[:1], s.ref)] * cores)
+    nb = (N_FRAMES + BATCH - 1) // BATCH
+
+    def step(i):
+        b = i % nb
+        fr = s.frames[b * BATCH: b * BATCH + per_step]
+        if pool:
+            pool.map(_oracle_chunk, [(c, s.ref) for c in np.array_split(fr, cores) if len(c)])
+        else:
+            oracle.track_batch(fr, s.ref, u=U)
+        return len(fr)
+
+    for i in range(args.warmup):
+        step(i)
+    lat = []
+    sizes = []
+    t_all = time.perf_counter()
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        sizes.append(step(i))
+        lat.append(time.perf_counter() - t0)
+    dt = time.perf_counter() - t_all
+    if pool:
+        pool.close()
+    value = sum(sizes) / dt
+    sample = (f"{per_step} frame(s) of each 256-frame batch per step, FP64 numpy oracle, "
+              f"{cores if use_pool else 1} process(es)")
+    print(json.dumps({
+        "impl": "reference",
+        "metric": "frames/s and p50/p99 per-frame latency (us) at 128x128, <=1e-3 px vs FP64 oracle",
+        "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "p50_us": float(np.median(lat)) * 1e6, "p99_us": float(np.percentile(lat, 99)) * 1e6,
+        "config": {"workload": "frame stream: 10000 uint16 128x128 Gaussian-spot frames, u=100, CC-U "
+                               "(bounded per-step sample on the host)", "global_batch": per_step,
+                   "upsample": U, "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores if use_pool else 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=40)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        from paper_2310_08770_b300 import build
+        build.build()
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * ccst.h -- C ABI of libccst: cross-correlation sub-pixel tracking on one GPU.
+ *
+ * Method (arXiv 2310.08770):
+ *   - Sec. II, Eqs. (1)-(4): uniform-weight cross-correlation (CC-U). The
+ *     displacement maximises c(s) = sum_r I(r+s) E(r) = F^-1[F[I] conj F[E]](s)
+ *     between a frame I and the reference image E (periodic boundaries).
+ *   - Sec. II, Eqs. (5)-(7): shot-noise-weighted cross-correlation (CC-SN).
+ *     The frame is offset by eps, I' = I + eps, the reference becomes
+ *     E_SN = E + eps, and the surface is c(s) = sum_r I'(r+s)^2 / E_SN(r).
+ *     The chi^2 of Eq. (6) is smallest where this surface is smallest, so CC-SN
+ *     takes the minimum.
+ *   - Sec. III: the integer extremum of c is refined on a grid of
+ *     M = ceil(1.5 u) x M points, spaced 1/u pixel, centred on it. The product
+ *     spectrum of Eq. (4) / (7) is inverse-DFT'd onto that grid (the
+ *     matrix-multiply DFT of the paper's ref. [27]), and the extremum of that
+ *     upsampled surface is the sub-pixel displacement.
+ *
+ * Conventions:
+ *   - Images are H rows x W columns, row-major; x is the column (contiguous) index.
+ *   - The reported displacement d = (dx, dy) is the motion of the frame content
+ *     relative to the reference: frame(r) ~ ref(r - d).
+ *   - Integer peaks are wrapped to (-ceil(N/2), floor(N/2)] per axis.
+ *   - Grid offsets are (j - floor(M/2))/u, j = 0..M-1.
+ *   - Ties go to the lowest row-major index, as in the FP64 oracle.
+ *   - `peak` is the surface value at the reported point, in the units of the
+ *     direct sum above. It equals c(p) at offset 0.
+ *
+ * Errors: every call returns an int. 0 is CCST_OK; negative values are errors.
+ *   - No exception or abort crosses the ABI.
+ *   - A CUDA error inside a call marks the context unusable (sticky). Later calls
+ *     return CCST_E_CUDA, and ccst_last_error() gives the message.
+ *
+ * Threading: one context must not be used from two host threads at once.
+ * Separate contexts are independent.
+ */
+#ifndef CCST_H
+#define CCST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CCST_VERSION 10000 /* 1.0.0 */
+
+/* return codes */
+#define CCST_OK             0
+#define CCST_E_INVALID     -1  /* null pointer, bad enum, n < 0, ... */
+#define CCST_E_SHAPE       -2  /* H, W outside the supported set, or frames larger than create() allowed */
+#define CCST_E_UNSUPPORTED -3  /* a valid request this build does not implement */
+#define CCST_E_NOMEM       -4  /* device or pinned host allocation failed */
+#define CCST_E_CUDA        -5  /* a CUDA runtime error; the context is now unusable */
+#define CCST_E_TIMEOUT     -6  /* ccst_poll: not finished within the timeout */
+#define CCST_E_BUSY        -7  /* ccst_submit: all in-flight slots are taken */
+
+/* methods (Sec. II) */
+#define CCST_CC_U  0  /* uniform weight, Eq. (4): maximum of sum I E        */
+#define CCST_CC_SN 1  /* shot-noise weight, Eq. (7): minimum of sum I'^2/E_SN */
+
+/* frame element types */
+#define CCST_U16 0
+#define CCST_F32 1
+
+/* ccst_params.flags */
+#define CCST_FLAG_TIE_GUARD 0x1u  /* resolve near-ties of the FP32 surfaces in higher precision (default on) */
+#define CCST_FLAG_GRAPHS    0x2u  /* ccst_track replays one captured CUDA graph per (frames, n, pitch, out) */
+#define CCST_FLAG_PROFILE   0x4u  /* record CUDA events around each launch of the tracking kernel */
+
+/* ccst_result.flags (per frame) */
+#define CCST_R_INT_GUARD   0x01u /* integer peak re-decided by FP64 direct sums */
+#define CCST_R_SUB_GUARD   0x02u /* sub-pixel peak re-decided by exact FP32 grid differences */
+#define CCST_R_FP64        0x04u /* sub-pixel peak decided by the FP64 re-evaluation */
+#define CCST_R_OVERFLOW    0x08u /* too many near-tied points to certify: the FP32 choice is reported */
+#define CCST_R_NONFINITE   0x10u /* the surface held no finite value (non-finite input) */
+
+typedef struct ccst_params {
+    int32_t  upsample;   /* u >= 1, default 100 (Sec. III)                          */
+    int32_t  method;     /* CCST_CC_U or CCST_CC_SN                                 */
+    float    eps;        /* CC-SN offset, default 200 = 200 x noise gain 1 (Sec. IV) */
+    int32_t  in_dtype;   /* CCST_U16 or CCST_F32                                    */
+    int32_t  max_batch;  /* largest n one ccst_track call may pass; > 0            */
+    int32_t  max_H;      /* reserved: 0                                             */
+    int32_t  max_W;      /* reserved: 0                                             */
+    void*    stream;     /* cudaStream_t the context works on; NULL = legacy default */
+    uint32_t flags;      /* CCST_FLAG_*                                             */
+} ccst_params;
+
+/* Per-frame result: 24 bytes, naturally aligned. */
+typedef struct ccst_result {
+    float    dx, dy;     /* sub-pixel displacement (px), frame(r) ~ ref(r - d)      */
+    float    peak;       /* surface value at d, direct-sum units                    */
+    int32_t  ipy, ipx;   /* wrapped integer peak                                    */
+    uint32_t flags;      /* CCST_R_*                                                */
+} ccst_result;
+
+typedef struct ccst_ctx ccst_ctx;
+
+/* Library version, CCST_VERSION. */
+int ccst_version(void);
+
+/* Fill *p with the defaults: u = 100, CC-U, eps = 200, uint16 frames,
+ * max_batch = 256, stream NULL, flags = CCST_FLAG_TIE_GUARD. */
+int ccst_default_params(ccst_params* p);
+
+/* Create a tracking context for H x W frames against the reference image `ref`.
+ *
+ * Arguments:
+ *   ref   H*W float32, row-major, host or device memory (detected). It is copied;
+ *         the caller keeps ownership.
+ *   H, W  powers of two, 8 <= H, W <= 128 in this build. Other sizes return
+ *         CCST_E_SHAPE.
+ *   p     parameters; NULL means the defaults.
+ *   out   receives the context.
+ *
+ * The context owns the reference spectrum (FP32 and FP64, Eq. (4)/(7) right-hand
+ * side), the upsampling tables and all device workspace. Synchronous.
+ * Errors: CCST_E_INVALID, CCST_E_SHAPE, CCST_E_NOMEM, CCST_E_CUDA. */
+int ccst_create(const float* ref, int H, int W, const ccst_params* p, ccst_ctx** out);
+
+/* Track n frames (Sec. II-III) on the context's stream. Stream-ordered and
+ * asynchronous.
+ *
+ * Arguments:
+ *   frames_dev   caller-owned device memory holding n frames of H rows, each row
+ *                `pitch_elems` elements apart (0 means W), frames H*pitch
+ *                apart, element type params.in_dtype.
+ *   out_dev      caller-owned device memory for n ccst_result records.
+ *
+ * The results are valid once the stream reaches this point (synchronise the
+ * stream or call ccst_sync). 0 <= n <= max_batch; n = 0 is a no-op.
+ * Errors: CCST_E_INVALID (null pointers, n out of range, pitch < W),
+ *         CCST_E_CUDA. */
+int ccst_track(ccst_ctx* ctx, const void* frames_dev, int64_t n, int64_t pitch_elems,
+               ccst_result* out_dev);
+
+/* Same computation for host memory. Copies the n frames host -> device, tracks
+ * them, copies the results back, and returns after the results are in out_host.
+ * Pageable or pinned host memory are both accepted; pinned is faster.
+ * Errors: as ccst_track. */
+int ccst_track_host(ccst_ctx* ctx, const void* frames_host, int64_t n, int64_t pitch_elems,
+                    ccst_result* out_host);
+
+/* Work on `stream` (a cudaStream_t) from now on. The caller orders this
+ * against earlier work. */
+int ccst_set_stream(ccst_ctx* ctx, void* stream);
+
+/* Block until all work issued on the context's stream has finished. */
+int ccst_sync(ccst_ctx* ctx);
+
+/* Asynchronous serving form of ccst_track: enqueue and return a ticket.
+ * At most 64 submissions may be in flight per context; more return CCST_E_BUSY. */
+int ccst_submit(ccst_ctx* ctx, const void* frames_dev, int64_t n, ccst_result* out_dev,
+                uint64_t* ticket);
+
+/* Ask whether a ticket has finished. Waits at most timeout_us microseconds.
+ *   CCST_OK          *done = 1 and the slot is released.
+ *   CCST_E_TIMEOUT   *done = 0; poll again later.
+ *   CCST_E_INVALID   unknown ticket. */
+int ccst_poll(ccst_ctx* ctx, uint64_t ticket, int timeout_us, int* done);
+
+/* Vector-Jacobian product of the displacement with respect to the frame pixels
+ * and the reference. Not implemented in this build: returns CCST_E_UNSUPPORTED. */
+int ccst_backward(ccst_ctx* ctx, const void* frames_dev, int64_t n, const float* g_dxdy_dev,
+                  float* g_frames_dev, float* g_ref_dev);
+
+/* Free everything the context owns. NULL is a no-op. Synchronises its stream first. */
+void ccst_destroy(ccst_ctx* ctx);
+
+/* Last error message of this context (or of the last failed create when ctx is NULL).
+ * Valid until the next call on the same context. Never NULL. */
+const char* ccst_last_error(ccst_ctx* ctx);
+
+/* Profiling (CCST_FLAG_PROFILE): total device time of the FP32 tracking kernel
+ * and the number of launches it covers. Each captured graph owns one event pair
+ * and contributes its latest replay. Direct launches use a ring of 1024 pairs
+ * and contribute every launch since the last reset. Synchronises the stream.
+ * Errors: CCST_E_INVALID (profiling off, NULL pointers), CCST_E_CUDA. */
+int ccst_profile_kernel_ms(ccst_ctx* ctx, double* sum_ms, int64_t* launches);
+int ccst_profile_reset(ccst_ctx* ctx);
+
+/* Number of grid points per axis of the refinement square, M = ceil(1.5 u)
+ * (Sec. III); CCST_E_INVALID for a NULL context. */
+int ccst_grid_size(ccst_ctx* ctx);
+
+/* Diagnostic form of ccst_track, for tests.
+ * It runs without graphs and, when the pointers are non-NULL, also writes:
+ *   int_surf_dev  n x H x W floats: the FP32 integer surface H*W*c(s)
+ *                 (unnormalised), s in 0..H-1 x 0..W-1 (Eq. (4)/(7));
+ *   sub_surf_dev  n x M x M floats: the FP32 upsampled surface relative to the
+ *                 integer peak, H*W*(cu(j) - cu(centre)), row = y offset (Sec. III).
+ * Both buffers are caller-owned device memory.
+ * Errors: as ccst_track. */
+int ccst_debug_surfaces(ccst_ctx* ctx, const void* frames_dev, int64_t n, int64_t pitch_elems,
+                        ccst_result* out_dev, float* int_surf_dev, float* sub_surf_dev);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCST_H */

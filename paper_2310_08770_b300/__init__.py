@@ -5,8 +5,11 @@ The compute path lives in the CUDA library ``libccst.so`` (built from
 package does not load the library: the first call that needs it does, and it
 raises if the library is missing.
 """
-_BINDING = ("CC_SN", "CC_U", "Tracker", "ccst_create", "ccst_destroy", "ccst_track",
-            "ccst_version", "library_path", "CcstError")
+_BINDING = ("CC_SN", "CC_U", "Tracker", "CcstError", "RESULT_DTYPE", "decode", "library_path",
+            "ccst_version", "ccst_default_params", "ccst_create", "ccst_track", "ccst_track_host",
+            "ccst_set_stream", "ccst_sync", "ccst_submit", "ccst_poll", "ccst_backward",
+            "ccst_destroy", "ccst_grid_size", "ccst_debug_surfaces", "ccst_profile_kernel_ms",
+            "ccst_profile_reset")
 
 
 def __getattr__(name):

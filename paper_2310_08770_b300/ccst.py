@@ -1,0 +1,278 @@
+"""Thin ctypes binding of libccst (include/ccst.h).
+
+Argument marshalling only: every step of the tracking path runs in the CUDA
+library. torch is used for device memory and streams. The functions keep the C
+names; :class:`Tracker` is a small convenience wrapper over them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+CC_U = 0
+CC_SN = 1
+U16 = 0
+F32 = 1
+FLAG_TIE_GUARD = 0x1
+FLAG_GRAPHS = 0x2
+FLAG_PROFILE = 0x4
+
+R_INT_GUARD = 0x01
+R_SUB_GUARD = 0x02
+R_FP64 = 0x04
+R_OVERFLOW = 0x08
+R_NONFINITE = 0x10
+
+OK, E_INVALID, E_SHAPE, E_UNSUPPORTED, E_NOMEM, E_CUDA, E_TIMEOUT, E_BUSY = 0, -1, -2, -3, -4, -5, -6, -7
+_CODES = {0: "OK", -1: "E_INVALID", -2: "E_SHAPE", -3: "E_UNSUPPORTED", -4: "E_NOMEM",
+          -5: "E_CUDA", -6: "E_TIMEOUT", -7: "E_BUSY"}
+
+RESULT_DTYPE = np.dtype([("dx", "<f4"), ("dy", "<f4"), ("peak", "<f4"),
+                         ("ipy", "<i4"), ("ipx", "<i4"), ("flags", "<u4")])
+
+
+class ccst_params(ctypes.Structure):
+    _fields_ = [("upsample", ctypes.c_int32), ("method", ctypes.c_int32), ("eps", ctypes.c_float),
+                ("in_dtype", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("max_H", ctypes.c_int32),
+                ("max_W", ctypes.c_int32), ("stream", ctypes.c_void_p), ("flags", ctypes.c_uint32)]
+
+
+class CcstError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_CODES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "libccst.so")
+
+
+# (name, restype, argtypes) of every declared entry point
+_SIGS = [
+    ("ccst_version", ctypes.c_int, []),
+    ("ccst_default_params", ctypes.c_int, [ctypes.POINTER(ccst_params)]),
+    ("ccst_create", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ccst_params),
+                                   ctypes.POINTER(ctypes.c_void_p)]),
+    ("ccst_track", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                  ctypes.c_void_p]),
+    ("ccst_track_host", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                       ctypes.c_void_p]),
+    ("ccst_set_stream", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("ccst_sync", ctypes.c_int, [ctypes.c_void_p]),
+    ("ccst_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                   ctypes.POINTER(ctypes.c_uint64)]),
+    ("ccst_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("ccst_backward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p]),
+    ("ccst_destroy", None, [ctypes.c_void_p]),
+    ("ccst_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("ccst_grid_size", ctypes.c_int, [ctypes.c_void_p]),
+    ("ccst_profile_kernel_ms", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_int64)]),
+    ("ccst_profile_reset", ctypes.c_int, [ctypes.c_void_p]),
+    ("ccst_debug_surfaces", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+]
+
+
+def lib() -> ctypes.CDLL:
+    """Load libccst.so (once). Raises if the library has not been built."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise ImportError(f"libccst.so not found at {path}; build it with "
+                              "`python -m paper_2310_08770_b300.build`")
+        L = ctypes.CDLL(path)
+        for name, res, args in _SIGS:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(code, ctx=None):
+    if code != OK:
+        msg = lib().ccst_last_error(ctx)
+        raise CcstError(code, msg.decode() if msg else "")
+    return code
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor or numpy array."""
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if x is None:
+        return None
+    return int(x)
+
+
+# ---------------------------------------------------------------- C-named wrappers
+def ccst_version() -> int:
+    return lib().ccst_version()
+
+
+def ccst_default_params() -> ccst_params:
+    p = ccst_params()
+    _check(lib().ccst_default_params(ctypes.byref(p)))
+    return p
+
+
+def ccst_create(ref, H: int, W: int, params: ccst_params | None = None) -> ctypes.c_void_p:
+    """ref: float32 H x W (host numpy or CUDA tensor), copied by the library."""
+    ctx = ctypes.c_void_p()
+    p = ctypes.byref(params) if params is not None else None
+    _check(lib().ccst_create(_ptr(ref), int(H), int(W), p, ctypes.byref(ctx)))
+    return ctx
+
+
+def ccst_track(ctx, frames_dev, n: int, pitch_elems: int, out_dev) -> None:
+    _check(lib().ccst_track(ctx, _ptr(frames_dev), int(n), int(pitch_elems), _ptr(out_dev)), ctx)
+
+
+def ccst_track_host(ctx, frames_host, n: int, pitch_elems: int, out_host) -> None:
+    _check(lib().ccst_track_host(ctx, _ptr(frames_host), int(n), int(pitch_elems), _ptr(out_host)), ctx)
+
+
+def ccst_set_stream(ctx, stream) -> None:
+    _check(lib().ccst_set_stream(ctx, stream), ctx)
+
+
+def ccst_sync(ctx) -> None:
+    _check(lib().ccst_sync(ctx), ctx)
+
+
+def ccst_submit(ctx, frames_dev, n: int, out_dev) -> int:
+    t = ctypes.c_uint64()
+    _check(lib().ccst_submit(ctx, _ptr(frames_dev), int(n), _ptr(out_dev), ctypes.byref(t)), ctx)
+    return t.value
+
+
+def ccst_poll(ctx, ticket: int, timeout_us: int) -> bool:
+    done = ctypes.c_int()
+    rc = lib().ccst_poll(ctx, ctypes.c_uint64(ticket), int(timeout_us), ctypes.byref(done))
+    if rc == E_TIMEOUT:
+        return False
+    _check(rc, ctx)
+    return bool(done.value)
+
+
+def ccst_backward(ctx, frames_dev, n, g_dxdy_dev, g_frames_dev, g_ref_dev) -> None:
+    _check(lib().ccst_backward(ctx, _ptr(frames_dev), int(n), _ptr(g_dxdy_dev), _ptr(g_frames_dev),
+                               _ptr(g_ref_dev)), ctx)
+
+
+def ccst_destroy(ctx) -> None:
+    lib().ccst_destroy(ctx)
+
+
+def ccst_grid_size(ctx) -> int:
+    return _check_nonneg(lib().ccst_grid_size(ctx), ctx)
+
+
+def ccst_profile_kernel_ms(ctx):
+    """(total ms, launches) of the FP32 tracking kernel since the last reset."""
+    ms = ctypes.c_double()
+    cnt = ctypes.c_int64()
+    _check(lib().ccst_profile_kernel_ms(ctx, ctypes.byref(ms), ctypes.byref(cnt)), ctx)
+    return ms.value, cnt.value
+
+
+def ccst_profile_reset(ctx) -> None:
+    _check(lib().ccst_profile_reset(ctx), ctx)
+
+
+def _check_nonneg(v, ctx):
+    if v < 0:
+        _check(v, ctx)
+    return v
+
+
+def ccst_debug_surfaces(ctx, frames_dev, n, pitch_elems, out_dev, int_surf_dev, sub_surf_dev) -> None:
+    _check(lib().ccst_debug_surfaces(ctx, _ptr(frames_dev), int(n), int(pitch_elems), _ptr(out_dev),
+                                     _ptr(int_surf_dev), _ptr(sub_surf_dev)), ctx)
+
+
+# ---------------------------------------------------------------- convenience wrapper
+class Tracker:
+    """One reference image, many frames.
+
+    >>> t = Tracker(ref, upsample=100, method="ccu", in_dtype="u16")
+    >>> res = t.track(frames)          # frames: CUDA tensor (n, H, W)
+    >>> res["dx"], res["dy"]           # numpy structured array (RESULT_DTYPE)
+    """
+
+    def __init__(self, ref, upsample: int = 100, method: str | int = "ccu", eps: float = 200.0,
+                 in_dtype: str | int = "u16", max_batch: int = 256, stream=None, graphs: bool = False,
+                 tie_guard: bool = True, profile: bool = False):
+        import torch
+        ref_np = ref.detach().cpu().numpy() if hasattr(ref, "detach") else np.asarray(ref)
+        ref_np = np.ascontiguousarray(ref_np, dtype=np.float32)
+        self.H, self.W = ref_np.shape
+        p = ccst_default_params()
+        p.upsample = int(upsample)
+        p.method = {"ccu": CC_U, "ccsn": CC_SN}.get(method, method)
+        p.eps = float(eps)
+        p.in_dtype = {"u16": U16, "f32": F32}.get(in_dtype, in_dtype)
+        p.max_batch = int(max_batch)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        p.stream = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        p.flags = (FLAG_TIE_GUARD if tie_guard else 0) | (FLAG_GRAPHS if graphs else 0) | \
+            (FLAG_PROFILE if profile else 0)
+        self.params = p
+        self.max_batch = int(max_batch)
+        self.ctx = ccst_create(ref_np, self.H, self.W, p)
+        self.M = ccst_grid_size(self.ctx)
+        self._torch = torch
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            ccst_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def empty_results(self, n: int):
+        return self._torch.empty((n, 24), dtype=self._torch.uint8, device="cuda")
+
+    def track_into(self, frames, out, pitch_elems: int = 0) -> None:
+        """Asynchronous: frames (n, H, W) CUDA tensor, out (n, 24) uint8 CUDA tensor."""
+        ccst_track(self.ctx, frames, frames.shape[0], pitch_elems, out)
+
+    def track(self, frames) -> np.ndarray:
+        """Synchronous convenience: all frames, in chunks of max_batch; returns RESULT_DTYPE records."""
+        n = frames.shape[0]
+        out = self.empty_results(n)
+        for s in range(0, n, self.max_batch):
+            e = min(n, s + self.max_batch)
+            ccst_track(self.ctx, frames[s:e], e - s, 0, out[s:e])
+        ccst_sync(self.ctx)
+        return decode(out)
+
+    def track_host(self, frames_np: np.ndarray) -> np.ndarray:
+        n = frames_np.shape[0]
+        frames_np = np.ascontiguousarray(frames_np)
+        res = np.empty(n, dtype=RESULT_DTYPE)
+        for s in range(0, n, self.max_batch):
+            e = min(n, s + self.max_batch)
+            ccst_track_host(self.ctx, frames_np[s:e], e - s, 0, res[s:e])
+        return res
+
+
+def decode(out) -> np.ndarray:
+    """(n, 24) uint8 tensor/array of records -> numpy structured array."""
+    a = out.cpu().numpy() if hasattr(out, "cpu") else np.asarray(out)
+    return np.ascontiguousarray(a).view(RESULT_DTYPE).reshape(-1)

@@ -1,0 +1,562 @@
+// ccst.cu -- the C ABI of libccst (declared in include/ccst.h): context set-up,
+// launches, CUDA-graph replay of batches and the serving tickets.
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "ccst.h"
+#include "ccst_kernels.cuh"
+
+using namespace ccst;
+
+static_assert(sizeof(ccst_result) == sizeof(Result), "result record layout");
+static_assert(sizeof(ccst_result) == 24, "result record is 24 bytes");
+
+namespace {
+
+constexpr int kL2Slots = 32;      // CTAs (and workspace slots) of the FP64 re-evaluation
+constexpr int kTickets = 64;      // in-flight submissions per context
+constexpr size_t kMaxGraphs = 512;
+
+// Guard thresholds, in units of the FP32 unit roundoff times sum w|X| (see DESIGN notes
+// in the repository: calibrated against the FP64 oracle with a wide margin).
+constexpr float kEps32 = 1.1920929e-07f;
+constexpr float kTauInt = 16.0f * kEps32;
+constexpr float kTau0 = 1.0f * kEps32;
+constexpr float kTau1 = 0.05f * kEps32;
+
+std::mutex g_create_err_mu;
+std::string g_create_err = "no error";
+
+// ------------------------------------------------------------ init kernels
+__global__ void init_twiddles(int Ntw, double2* tw64, float2* tw32) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < Ntw / 2; k += gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(-2.0 * (double)k / (double)Ntw, &s, &c);
+        tw64[k] = make_double2(c, s);
+        tw32[k] = make_float2((float)c, (float)s);
+    }
+}
+
+__global__ void init_tables(Geom g, float* cm1, float* sA, float* wc, float* ws, float* gc) {
+    const long long Dy = (long long)g.u * g.H, Dx = (long long)g.u * g.W;
+    const int nA = g.Hh * g.T1p, nB = g.Wc * g.T1p;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nA + nB; i += gridDim.x * blockDim.x) {
+        if (i < nA) {
+            const int m = i / g.T1p + 1, t = i % g.T1p;
+            float c1 = 0.f, s1 = 0.f;
+            if (t <= g.h0) {
+                const long long r = ((long long)m * t) % Dy;     // angle 2 pi r / (uH)
+                const double h = sinpi((double)r / (double)Dy);
+                c1 = (float)(-2.0 * h * h);                       // cos - 1 without cancellation
+                s1 = (float)sinpi(2.0 * (double)r / (double)Dy);
+            }
+            cm1[i] = c1;
+            sA[i] = s1;
+        } else {
+            const int k = i - nA;
+            const int kx = k / g.T1p, t = k % g.T1p;
+            const int kxs = (kx < g.W / 2) ? kx : kx - g.W;      // W/2 -> -W/2
+            const double w = (kx == 0 || 2 * kx == g.W) ? 1.0 : 2.0;
+            float a = 0.f, b = 0.f, c = 0.f;
+            if (t <= g.h0) {
+                long long r = ((long long)kxs * t) % Dx;
+                if (r < 0) r += Dx;
+                double s, co;
+                sincospi(2.0 * (double)r / (double)Dx, &s, &co);
+                const double h = sinpi((double)r / (double)Dx);
+                a = (float)(w * co);
+                b = (float)(w * s);
+                c = (float)(w * (-2.0 * h * h));
+            }
+            wc[k] = a;
+            ws[k] = b;
+            gc[k] = c;
+        }
+    }
+}
+
+__global__ void init_ref_operand(Geom g, const float* ref, double* b64) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.H * g.W; i += gridDim.x * blockDim.x) {
+        const double e = (double)ref[i];
+        b64[i] = (g.method == 0) ? e : 1.0 / (e + (double)g.eps);
+    }
+}
+
+__global__ void __launch_bounds__(256) init_ref_spectrum(Geom g, double2* work, double2* FE64, float2* FE32) {
+    __shared__ double red[32];
+    double2* Z = work;
+    double2* Xh = work + (size_t)(g.H / 2) * g.W;
+    fft_r2c_f64_global(g, g.b64, nullptr, 0, Z, Xh, red);
+    for (int idx = threadIdx.x; idx < g.H * g.Wc; idx += blockDim.x) {
+        const int ky = idx / g.Wc, kx = idx - ky * g.Wc;
+        const double2 v = Xh[ky * g.Wcp + kx];
+        FE64[idx] = v;
+        FE32[idx] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+int ilog2(int x) { int l = 0; while ((1 << l) < x) ++l; return l; }
+
+}  // namespace
+
+// ---------------------------------------------------------------- context
+struct ccst_ctx {
+    Geom g{};
+    ccst_params p{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int grid_main = 1;
+    size_t smem = 0;
+    bool dead = false;
+    std::string err = "no error";
+    // device allocations
+    void* d_ref32 = nullptr;
+    double* d_b64 = nullptr;
+    double2* d_FE64 = nullptr;
+    float2* d_FE32 = nullptr;
+    double2* d_tw64 = nullptr;
+    float2* d_tw32 = nullptr;
+    float* d_tab = nullptr;       // all stage tables in one block
+    GuardRec* d_guard = nullptr;  // max_batch
+    double2* d_l2work = nullptr;  // kL2Slots workspaces
+    void* d_frames = nullptr;     // host-path staging
+    Result* d_out = nullptr;      // host-path staging
+    // graphs keyed by (frames, n, pitch, out), each with its own profiling event pair
+    struct GraphEntry {
+        cudaGraphExec_t exec = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+    };
+    std::map<std::tuple<const void*, long long, long long, void*>, GraphEntry> graphs;
+    // profiling ring for direct launches
+    std::vector<cudaEvent_t> prof0, prof1;
+    int prof_next = 0, prof_used = 0;
+    bool capturing = false;
+    cudaEvent_t cap_e0 = nullptr, cap_e1 = nullptr;   // event pair of the graph being captured
+    // serving tickets
+    cudaEvent_t ev[kTickets] = {};
+    bool busy[kTickets] = {};
+    uint64_t ticket_of[kTickets] = {};
+    uint64_t next_ticket = 1;
+};
+
+static int fail(ccst_ctx* c, int code, const std::string& msg) {
+    if (c) {
+        c->err = msg;
+        if (code == CCST_E_CUDA) c->dead = true;
+    } else {
+        std::lock_guard<std::mutex> lk(g_create_err_mu);
+        g_create_err = msg;
+    }
+    return code;
+}
+
+#define CK(ctx, call)                                                                              \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation ? CCST_E_NOMEM : CCST_E_CUDA,       \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                      \
+    } while (0)
+
+static void drop_graphs(ccst_ctx* c) {
+    for (auto& kv : c->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.e0) cudaEventDestroy(kv.second.e0);
+        if (kv.second.e1) cudaEventDestroy(kv.second.e1);
+    }
+    c->graphs.clear();
+}
+
+static void free_all(ccst_ctx* c) {
+    drop_graphs(c);
+    for (size_t i = 0; i < c->prof0.size(); ++i) {
+        cudaEventDestroy(c->prof0[i]);
+        cudaEventDestroy(c->prof1[i]);
+    }
+    c->prof0.clear();
+    c->prof1.clear();
+    for (int i = 0; i < kTickets; ++i)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    void* ptrs[] = {c->d_ref32, c->d_b64, c->d_FE64, c->d_FE32, c->d_tw64, c->d_tw32,
+                    c->d_tab,   c->d_guard, c->d_l2work, c->d_frames, c->d_out};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+extern "C" int ccst_version(void) { return CCST_VERSION; }
+
+extern "C" int ccst_default_params(ccst_params* p) {
+    if (!p) return CCST_E_INVALID;
+    std::memset(p, 0, sizeof(*p));
+    p->upsample = 100;
+    p->method = CCST_CC_U;
+    p->eps = 200.0f;
+    p->in_dtype = CCST_U16;
+    p->max_batch = 256;
+    p->stream = nullptr;
+    p->flags = CCST_FLAG_TIE_GUARD;
+    return CCST_OK;
+}
+
+extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pin, ccst_ctx** out) {
+    if (!ref || !out) return fail(nullptr, CCST_E_INVALID, "ccst_create: null ref or out");
+    *out = nullptr;
+    ccst_params p;
+    if (pin) p = *pin; else ccst_default_params(&p);
+    if (!is_pow2(H) || !is_pow2(W) || H < 8 || W < 8 || H > 128 || W > 128)
+        return fail(nullptr, CCST_E_SHAPE, "ccst_create: H and W must be powers of two in [8, 128]");
+    if (p.upsample < 1 || p.upsample > 16384)
+        return fail(nullptr, CCST_E_INVALID, "ccst_create: upsample must be in [1, 16384]");
+    if (p.method != CCST_CC_U && p.method != CCST_CC_SN)
+        return fail(nullptr, CCST_E_INVALID, "ccst_create: unknown method");
+    if (p.in_dtype != CCST_U16 && p.in_dtype != CCST_F32)
+        return fail(nullptr, CCST_E_INVALID, "ccst_create: unknown in_dtype");
+    if (p.max_batch < 1) return fail(nullptr, CCST_E_INVALID, "ccst_create: max_batch must be > 0");
+    if (p.method == CCST_CC_SN && !(p.eps == p.eps))
+        return fail(nullptr, CCST_E_INVALID, "ccst_create: eps is NaN");
+
+    ccst_ctx* c = new (std::nothrow) ccst_ctx();
+    if (!c) return fail(nullptr, CCST_E_NOMEM, "ccst_create: host allocation failed");
+    c->p = p;
+    c->stream = (cudaStream_t)p.stream;
+    Geom& g = c->g;
+    g.H = H; g.W = W; g.logH = ilog2(H); g.logW = ilog2(W); g.Hh = H / 2;
+    g.Wc = W / 2 + 1; g.Wcp = (g.Wc + 1) & ~1;
+    g.u = p.upsample; g.M = (3 * p.upsample + 1) / 2; g.h0 = g.M / 2; g.pmax = g.M - 1 - g.h0;
+    g.T1p = (g.h0 + 1 + 3) & ~3;
+    g.Ntw = H > W ? H : W; g.logNtw = ilog2(g.Ntw);
+    g.method = p.method; g.in_dtype = p.in_dtype; g.eps = p.eps;
+    g.sense = p.method == CCST_CC_U ? 1.f : -1.f;
+    g.tau_int = kTauInt; g.tau0 = kTau0; g.tau1 = kTau1;
+    g.guard = (p.flags & CCST_FLAG_TIE_GUARD) ? 1 : 0;
+
+    auto bail = [&](int code) { free_all(c); delete c; return code; };
+    cudaError_t e;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) {
+        fail(nullptr, CCST_E_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+        return bail(CCST_E_CUDA);
+    }
+    c->device = dev;
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, dev)) != cudaSuccess) {
+        fail(nullptr, CCST_E_CUDA, std::string("cudaGetDeviceProperties: ") + cudaGetErrorString(e));
+        return bail(CCST_E_CUDA);
+    }
+    // stage-A chunk: as many t rows as fit next to the FFT buffers
+    const size_t limit = prop.sharedMemPerBlockOptin;
+    g.TC = g.T1p;
+    for (;;) {
+        g.nchunk = (g.h0 + 1 + g.TC - 1) / g.TC;
+        if (smem_bytes(g) <= limit || g.TC <= 4) break;
+        g.TC -= 4;
+    }
+    c->smem = smem_bytes(g);
+    if (c->smem > limit) {
+        fail(nullptr, CCST_E_SHAPE, "ccst_create: frame too large for shared memory");
+        return bail(CCST_E_SHAPE);
+    }
+
+    const size_t HW = (size_t)H * W, HWc = (size_t)H * g.Wc;
+    const size_t tabA = (size_t)g.Hh * g.T1p, tabB = (size_t)g.Wc * g.T1p;
+    const size_t l2per = (size_t)(H / 2) * W + (size_t)H * g.Wcp;
+    const size_t elem = p.in_dtype == CCST_U16 ? 2 : 4;
+    struct { void** ptr; size_t bytes; } allocs[] = {
+        {(void**)&c->d_ref32, HW * sizeof(float)},
+        {(void**)&c->d_b64, HW * sizeof(double)},
+        {(void**)&c->d_FE64, HWc * sizeof(double2)},
+        {(void**)&c->d_FE32, HWc * sizeof(float2)},
+        {(void**)&c->d_tw64, (size_t)(g.Ntw / 2) * sizeof(double2)},
+        {(void**)&c->d_tw32, (size_t)(g.Ntw / 2) * sizeof(float2)},
+        {(void**)&c->d_tab, (2 * tabA + 3 * tabB) * sizeof(float)},
+        {(void**)&c->d_guard, (size_t)p.max_batch * sizeof(GuardRec)},
+        {(void**)&c->d_l2work, (size_t)kL2Slots * l2per * sizeof(double2)},
+        {(void**)&c->d_frames, (size_t)p.max_batch * HW * elem},
+        {(void**)&c->d_out, (size_t)p.max_batch * sizeof(Result)},
+    };
+    for (auto& a : allocs) {
+        if ((e = cudaMalloc(a.ptr, a.bytes)) != cudaSuccess) {
+            fail(nullptr, e == cudaErrorMemoryAllocation ? CCST_E_NOMEM : CCST_E_CUDA,
+                 std::string("cudaMalloc: ") + cudaGetErrorString(e));
+            return bail(e == cudaErrorMemoryAllocation ? CCST_E_NOMEM : CCST_E_CUDA);
+        }
+    }
+    g.FE32 = c->d_FE32; g.FE64 = c->d_FE64; g.b64 = c->d_b64; g.tw32 = c->d_tw32; g.tw64 = c->d_tw64;
+    g.tA_cm1 = c->d_tab; g.tA_s = c->d_tab + tabA;
+    g.tB_wc = c->d_tab + 2 * tabA; g.tB_ws = g.tB_wc + tabB; g.tB_gc = g.tB_ws + tabB;
+
+    auto step = [&](cudaError_t e2, const char* what) {
+        if (e2 != cudaSuccess) fail(nullptr, CCST_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e2));
+        return e2 == cudaSuccess;
+    };
+    if (!step(cudaMemcpyAsync(c->d_ref32, ref, HW * sizeof(float), cudaMemcpyDefault, c->stream), "copy ref") ||
+        !step(cudaMemsetAsync(c->d_guard, 0, (size_t)p.max_batch * sizeof(GuardRec), c->stream), "memset guard"))
+        return bail(CCST_E_CUDA);
+    init_twiddles<<<1, 256, 0, c->stream>>>(g.Ntw, c->d_tw64, c->d_tw32);
+    init_tables<<<64, 256, 0, c->stream>>>(g, (float*)g.tA_cm1, (float*)g.tA_s, (float*)g.tB_wc,
+                                           (float*)g.tB_ws, (float*)g.tB_gc);
+    init_ref_operand<<<32, 256, 0, c->stream>>>(g, (const float*)c->d_ref32, c->d_b64);
+    init_ref_spectrum<<<1, 256, 0, c->stream>>>(g, c->d_l2work, c->d_FE64, c->d_FE32);
+    if (!step(cudaGetLastError(), "init kernels") || !step(cudaStreamSynchronize(c->stream), "init sync"))
+        return bail(CCST_E_CUDA);
+    // the attribute is per function: set it to the device limit so contexts of any size coexist
+    if (!step(cudaFuncSetAttribute(track_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit),
+              "smem attribute"))
+        return bail(CCST_E_CUDA);
+    int occ = 0;
+    if (!step(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, track_kernel, kThreads, c->smem), "occupancy"))
+        return bail(CCST_E_CUDA);
+    if (occ < 1) {
+        fail(nullptr, CCST_E_SHAPE, "ccst_create: tracking kernel does not fit on an SM");
+        return bail(CCST_E_SHAPE);
+    }
+    c->grid_main = prop.multiProcessorCount * occ;
+    for (int i = 0; i < kTickets; ++i)
+        if (!step(cudaEventCreateWithFlags(&c->ev[i], cudaEventDisableTiming), "event"))
+            return bail(CCST_E_CUDA);
+    if (p.flags & CCST_FLAG_PROFILE) {
+        c->prof0.resize(1024);
+        c->prof1.resize(1024);
+        for (int i = 0; i < 1024; ++i)
+            if (!step(cudaEventCreate(&c->prof0[i]), "event") || !step(cudaEventCreate(&c->prof1[i]), "event"))
+                return bail(CCST_E_CUDA);
+    }
+    *out = c;
+    return CCST_OK;
+}
+
+static int launch(ccst_ctx* c, const Batch& b) {
+    if (b.n == 0) return CCST_OK;
+    const int grid = (int)(b.n < c->grid_main ? b.n : c->grid_main);
+    const bool prof = (c->p.flags & CCST_FLAG_PROFILE) != 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (prof) {
+        if (c->capturing) {
+            e0 = c->cap_e0;
+            e1 = c->cap_e1;
+        } else {
+            e0 = c->prof0[c->prof_next];
+            e1 = c->prof1[c->prof_next];
+            c->prof_next = (c->prof_next + 1) % (int)c->prof0.size();
+            if (c->prof_used < (int)c->prof0.size()) ++c->prof_used;
+        }
+        CK(c, cudaEventRecordWithFlags(e0, c->stream, c->capturing ? cudaEventRecordExternal : 0));
+    }
+    track_kernel<<<grid, kThreads, c->smem, c->stream>>>(c->g, b);
+    if (prof) CK(c, cudaEventRecordWithFlags(e1, c->stream, c->capturing ? cudaEventRecordExternal : 0));
+    if (c->g.guard) {
+        const int g2 = (int)(b.n < kL2Slots ? b.n : kL2Slots);
+        fp64_guard_kernel<<<g2, 256, 0, c->stream>>>(c->g, b, c->d_l2work);
+    }
+    CK(c, cudaGetLastError());
+    return CCST_OK;
+}
+
+static int check_ctx(ccst_ctx* c) {
+    if (!c) return CCST_E_INVALID;
+    if (c->dead) return CCST_E_CUDA;
+    return CCST_OK;
+}
+
+static int make_batch(ccst_ctx* c, const void* frames, int64_t n, int64_t pitch, ccst_result* out, Batch* b) {
+    if (n < 0 || n > c->p.max_batch) return fail(c, CCST_E_INVALID, "n outside [0, max_batch]");
+    if (n > 0 && (!frames || !out)) return fail(c, CCST_E_INVALID, "null frames or out");
+    if (pitch == 0) pitch = c->g.W;
+    if (pitch < c->g.W) return fail(c, CCST_E_INVALID, "pitch_elems < W");
+    b->frames = frames;
+    b->n = n;
+    b->pitch = pitch;
+    b->out = (Result*)out;
+    b->guard = c->d_guard;
+    b->dbg_int = nullptr;
+    b->dbg_sub = nullptr;
+    return CCST_OK;
+}
+
+extern "C" int ccst_track(ccst_ctx* c, const void* frames_dev, int64_t n, int64_t pitch_elems,
+                          ccst_result* out_dev) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    Batch b;
+    if ((rc = make_batch(c, frames_dev, n, pitch_elems, out_dev, &b))) return rc;
+    if (n == 0) return CCST_OK;
+    const bool graphs = (c->p.flags & CCST_FLAG_GRAPHS) && c->stream != nullptr;
+    if (!graphs) return launch(c, b);
+    auto key = std::make_tuple(frames_dev, (long long)n, (long long)b.pitch, (void*)out_dev);
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+        if (c->graphs.size() >= kMaxGraphs) drop_graphs(c);
+        ccst_ctx::GraphEntry ent;
+        if (c->p.flags & CCST_FLAG_PROFILE) {
+            CK(c, cudaEventCreate(&ent.e0));
+            CK(c, cudaEventCreate(&ent.e1));
+        }
+        cudaGraph_t graph;
+        CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        c->capturing = true;
+        c->cap_e0 = ent.e0;
+        c->cap_e1 = ent.e1;
+        const int lrc = launch(c, b);
+        c->capturing = false;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        if (lrc) return lrc;
+        CK(c, e);
+        e = cudaGraphInstantiate(&ent.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(c, e);
+        it = c->graphs.emplace(key, ent).first;
+    }
+    CK(c, cudaGraphLaunch(it->second.exec, c->stream));
+    return CCST_OK;
+}
+
+extern "C" int ccst_track_host(ccst_ctx* c, const void* frames_host, int64_t n, int64_t pitch_elems,
+                               ccst_result* out_host) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (n < 0 || n > c->p.max_batch) return fail(c, CCST_E_INVALID, "n outside [0, max_batch]");
+    if (n == 0) return CCST_OK;
+    if (!frames_host || !out_host) return fail(c, CCST_E_INVALID, "null frames or out");
+    if (pitch_elems == 0) pitch_elems = c->g.W;
+    if (pitch_elems < c->g.W) return fail(c, CCST_E_INVALID, "pitch_elems < W");
+    const size_t elem = c->p.in_dtype == CCST_U16 ? 2 : 4;
+    const size_t row = (size_t)c->g.W * elem;
+    CK(c, cudaMemcpy2DAsync(c->d_frames, row, frames_host, (size_t)pitch_elems * elem, row,
+                            (size_t)n * c->g.H, cudaMemcpyHostToDevice, c->stream));
+    if ((rc = ccst_track(c, c->d_frames, n, 0, (ccst_result*)c->d_out))) return rc;
+    CK(c, cudaMemcpyAsync(out_host, c->d_out, (size_t)n * sizeof(Result), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return CCST_OK;
+}
+
+extern "C" int ccst_set_stream(ccst_ctx* c, void* stream) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if ((cudaStream_t)stream != c->stream) drop_graphs(c);
+    c->stream = (cudaStream_t)stream;
+    return CCST_OK;
+}
+
+extern "C" int ccst_sync(ccst_ctx* c) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    CK(c, cudaStreamSynchronize(c->stream));
+    return CCST_OK;
+}
+
+extern "C" int ccst_submit(ccst_ctx* c, const void* frames_dev, int64_t n, ccst_result* out_dev,
+                           uint64_t* ticket) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!ticket) return fail(c, CCST_E_INVALID, "null ticket");
+    const uint64_t t = c->next_ticket;
+    const int slot = (int)(t % kTickets);
+    if (c->busy[slot]) return fail(c, CCST_E_BUSY, "all submission slots in flight");
+    if ((rc = ccst_track(c, frames_dev, n, 0, out_dev))) return rc;
+    CK(c, cudaEventRecord(c->ev[slot], c->stream));
+    c->busy[slot] = true;
+    c->ticket_of[slot] = t;
+    c->next_ticket = t + 1;
+    *ticket = t;
+    return CCST_OK;
+}
+
+extern "C" int ccst_poll(ccst_ctx* c, uint64_t ticket, int timeout_us, int* done) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!done) return fail(c, CCST_E_INVALID, "null done");
+    *done = 0;
+    const int slot = (int)(ticket % kTickets);
+    if (!c->busy[slot] || c->ticket_of[slot] != ticket) return fail(c, CCST_E_INVALID, "unknown ticket");
+    const auto t_end = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us < 0 ? 0 : timeout_us);
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(c->ev[slot]);
+        if (e == cudaSuccess) {
+            c->busy[slot] = false;
+            *done = 1;
+            return CCST_OK;
+        }
+        if (e != cudaErrorNotReady) CK(c, e);
+        if (std::chrono::steady_clock::now() >= t_end) return CCST_E_TIMEOUT;
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+extern "C" int ccst_backward(ccst_ctx* c, const void*, int64_t, const float*, float*, float*) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    return fail(c, CCST_E_UNSUPPORTED, "ccst_backward is not implemented in this build");
+}
+
+extern "C" void ccst_destroy(ccst_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+extern "C" const char* ccst_last_error(ccst_ctx* c) {
+    if (c) return c->err.c_str();
+    std::lock_guard<std::mutex> lk(g_create_err_mu);
+    return g_create_err.c_str();
+}
+
+// Diagnostic entry (tests only): runs ccst_track without graphs and also writes the
+// FP32 integer surfaces (n x H x W, unnormalised) and the FP32 delta surfaces
+// (n x M x M, unnormalised, relative to the integer peak) when the pointers are non-null.
+extern "C" int ccst_debug_surfaces(ccst_ctx* c, const void* frames_dev, int64_t n, int64_t pitch_elems,
+                                   ccst_result* out_dev, float* int_surf_dev, float* sub_surf_dev) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    Batch b;
+    if ((rc = make_batch(c, frames_dev, n, pitch_elems, out_dev, &b))) return rc;
+    b.dbg_int = int_surf_dev;
+    b.dbg_sub = sub_surf_dev;
+    return launch(c, b);
+}
+
+extern "C" int ccst_profile_kernel_ms(ccst_ctx* c, double* sum_ms, int64_t* launches) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!(c->p.flags & CCST_FLAG_PROFILE) || !sum_ms || !launches)
+        return fail(c, CCST_E_INVALID, "profiling is off or null output");
+    CK(c, cudaStreamSynchronize(c->stream));
+    double total = 0.0;
+    int64_t cnt = 0;
+    float ms = 0.f;
+    for (auto& kv : c->graphs) {
+        if (cudaEventElapsedTime(&ms, kv.second.e0, kv.second.e1) == cudaSuccess) { total += ms; ++cnt; }
+    }
+    cudaGetLastError();   // a graph that never replayed leaves its events unrecorded
+    for (int i = 0; i < c->prof_used; ++i) {
+        CK(c, cudaEventElapsedTime(&ms, c->prof0[i], c->prof1[i]));
+        total += ms;
+        ++cnt;
+    }
+    *sum_ms = total;
+    *launches = cnt;
+    return CCST_OK;
+}
+
+extern "C" int ccst_profile_reset(ccst_ctx* c) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    c->prof_used = 0;
+    c->prof_next = 0;
+    return CCST_OK;
+}
+
+// Grid size M of the refinement square for this context (tests and bindings).
+extern "C" int ccst_grid_size(ccst_ctx* c) { return c ? c->g.M : CCST_E_INVALID; }

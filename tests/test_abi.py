@@ -1,0 +1,80 @@
+"""The C-ABI library loads on a CPU-only machine and exports every entry point the header declares."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2310_08770_b300 import ccst as C
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    with open(os.path.join(ROOT, "include", "ccst.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ccst_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2310_08770_b300 import build
+    build.build()
+    return C.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    # and the binding wraps each one under the same name
+    wrapped = {n for n, _, _ in C._SIGS}
+    assert set(names) <= wrapped
+
+
+def test_version_and_defaults(lib):
+    assert C.ccst_version() == 10000
+    p = C.ccst_default_params()
+    assert (p.upsample, p.method, p.eps, p.in_dtype, p.max_batch, p.flags) == (100, 0, 200.0, 0, 256, 1)
+
+
+def test_result_record_layout():
+    assert C.RESULT_DTYPE.itemsize == 24
+    assert C.ccst_params.stream.offset == 32 and ctypes.sizeof(C.ccst_params) == 48
+
+
+def test_invalid_arguments_return_codes_without_gpu(lib):
+    ctx = ctypes.c_void_p()
+    ref = np.zeros((64, 64), np.float32)
+    # null ref / null out
+    assert lib.ccst_create(None, 64, 64, None, ctypes.byref(ctx)) == C.E_INVALID
+    assert lib.ccst_create(ref.ctypes.data, 64, 64, None, None) == C.E_INVALID
+    # shapes outside the supported set are rejected before touching the device
+    for H, W in [(0, 64), (48, 64), (64, 256), (4, 4), (64, 100)]:
+        assert lib.ccst_create(ref.ctypes.data, H, W, None, ctypes.byref(ctx)) == C.E_SHAPE
+    p = C.ccst_default_params()
+    p.upsample = 0
+    assert lib.ccst_create(ref.ctypes.data, 64, 64, ctypes.byref(p), ctypes.byref(ctx)) == C.E_INVALID
+    p = C.ccst_default_params()
+    p.method = 7
+    assert lib.ccst_create(ref.ctypes.data, 64, 64, ctypes.byref(p), ctypes.byref(ctx)) == C.E_INVALID
+    assert b"method" in lib.ccst_last_error(None)
+    # calls on a NULL context
+    assert lib.ccst_track(None, None, 0, 0, None) == C.E_INVALID
+    assert lib.ccst_sync(None) == C.E_INVALID
+    assert lib.ccst_grid_size(None) == C.E_INVALID
+    lib.ccst_destroy(None)           # NULL-safe
+
+
+def test_python_binding_raises_cleanly_without_device(lib):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    with pytest.raises(C.CcstError):
+        C.ccst_create(np.zeros((64, 64), np.float32), 64, 64)

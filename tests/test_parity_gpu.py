@@ -1,0 +1,324 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bar: integer peaks identical; |dx|, |dy| within 1e-3 px of the oracle's float32
+result (with u = 100 the grid step is 0.01 px, so this means the same grid
+point). The only exception allowed is a genuine tie: a frame whose oracle top-2
+margin (relative to sum|X|/HW) is below 1e-12, where both choices are maxima
+to float64 precision. ``peak`` agrees to 2e-5 relative.
+"""
+import ctypes
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_08770_b300 import ccst as C
+from paper_2310_08770_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_PX = 1e-3
+TIE = 1e-12
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    if not _t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_08770_b300 import build
+    build.build()
+    return _t
+
+
+def run_gpu(torch, ref, frames, u=100, method=0, eps=200.0, graphs=False, debug=False, pitch_pad=0,
+            max_batch=256):
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream() if graphs else None
+    frames = np.asarray(frames)
+    in_dtype = "u16" if frames.dtype == np.uint16 else "f32"
+    if in_dtype == "f32":
+        frames = frames.astype(np.float32)
+    n, H, W = frames.shape
+    t = C.Tracker(ref.astype(np.float32), upsample=u, method=method, eps=eps, in_dtype=in_dtype,
+                  max_batch=max_batch, graphs=graphs, stream=stream)
+    tdt = torch.uint16 if in_dtype == "u16" else torch.float32
+    if pitch_pad:
+        host = np.zeros((n, H, W + pitch_pad), dtype=frames.dtype)
+        host[:, :, :W] = frames
+        dev = torch.from_numpy(host.view(np.int16) if in_dtype == "u16" else host).cuda()
+        pitch = W + pitch_pad
+    else:
+        dev = torch.from_numpy(frames.view(np.int16) if in_dtype == "u16" else frames).cuda()
+        pitch = 0
+    dev = dev.view(tdt) if in_dtype == "u16" else dev
+    out = torch.empty((n, 24), dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    surf_i = surf_s = None
+    if debug:
+        surf_i = torch.empty((n, H, W), dtype=torch.float32, device="cuda")
+        surf_s = torch.empty((n, t.M, t.M), dtype=torch.float32, device="cuda")
+        C.ccst_debug_surfaces(t.ctx, dev, n, pitch, out, surf_i, surf_s)
+    else:
+        for s in range(0, n, max_batch):
+            e = min(n, s + max_batch)
+            C.ccst_track(t.ctx, dev[s:e], e - s, pitch, out[s:e])
+    C.ccst_sync(t.ctx)
+    res = C.decode(out)
+    t.close()
+    if debug:
+        return res, surf_i.cpu().numpy(), surf_s.cpu().numpy()
+    return res
+
+
+def compare(res, orc, label=""):
+    bad = []
+    for i, (g, o) in enumerate(zip(res, orc)):
+        int_ok = (g["ipy"], g["ipx"]) == (o["ipy"], o["ipx"]) or o["int_margin"] < TIE
+        sub_ok = (abs(float(g["dx"]) - o["dx32"]) <= TOL_PX and abs(float(g["dy"]) - o["dy32"]) <= TOL_PX) \
+            or o["sub_margin"] < TIE or o["int_margin"] < TIE
+        peak_ok = abs(float(g["peak"]) - o["peak"]) <= 2e-5 * max(abs(o["peak"]), o["scale"] * 1e-3)
+        if not (int_ok and sub_ok and peak_ok):
+            bad.append((i, (float(g["dx"]), float(g["dy"]), int(g["ipy"]), int(g["ipx"]), float(g["peak"]),
+                            int(g["flags"])),
+                        (o["dx"], o["dy"], o["ipy"], o["ipx"], o["peak"], o["sub_margin"])))
+    assert not bad, f"{label}: {len(bad)} of {len(orc)} frames differ; first: {bad[:5]}"
+
+
+def flag_counts(res):
+    f = res["flags"]
+    return {name: int(np.sum((f & bit) != 0)) for name, bit in
+            (("int", C.R_INT_GUARD), ("sub", C.R_SUB_GUARD), ("fp64", C.R_FP64), ("overflow", C.R_OVERFLOW))}
+
+
+# ------------------------------------------------------------------ single pair
+@pytest.mark.parametrize("method", [oracle.CC_U, oracle.CC_SN])
+def test_single_pair(torch, method):
+    p = synth.single_pair(seed=0)
+    res = run_gpu(torch, p.ref, p.frame[None], u=100, method=method)
+    orc = [oracle.track_one(p.frame, p.ref, u=100, method=method)]
+    compare(res, orc, "single pair")
+    with open(os.path.join(GOLDEN, "single_pair_oracle.json")) as f:
+        gold = json.load(f)["ccu" if method == 0 else "ccsn"]
+    assert float(res["dx"][0]) == np.float32(gold["dx"]) and float(res["dy"][0]) == np.float32(gold["dy"])
+
+
+# ------------------------------------------------------------------ exact cases
+@pytest.mark.parametrize("N,sigma,u", [(64, 3.0, 100), (128, 2.5, 100), (64, 3.0, 256), (32, 2.0, 37)])
+def test_noise_free_subpixel_exact(torch, N, sigma, u):
+    rng = np.random.default_rng(1)
+    c = N / 2.0
+    ref = synth.gaussian_spot(N, N, c, c, sigma, 1000.0, 10.0)
+    frames, expect = [], []
+    while len(frames) < 24:
+        d = rng.uniform(-4, 4, size=2)
+        if min(abs((u * d[0]) % 1 - 0.5), abs((u * d[1]) % 1 - 0.5)) < 0.1:
+            continue
+        frames.append(synth.gaussian_spot(N, N, c + d[1], c + d[0], sigma, 1000.0, 10.0))
+        expect.append((round(u * d[0]) / u, round(u * d[1]) / u))
+    res = run_gpu(torch, ref, np.array(frames, np.float32), u=u)
+    for r, (ex, ey) in zip(res, expect):
+        assert float(r["dx"]) == np.float32(ex) and float(r["dy"]) == np.float32(ey)
+
+
+@pytest.mark.parametrize("shape", [(64, 64), (128, 128), (32, 64), (128, 16), (8, 8)])
+def test_integer_rolls_exact(torch, shape):
+    rng = np.random.default_rng(4)
+    H, W = shape
+    ref = synth.random_texture(rng, H, W)
+    shifts = [(0, 0), (1, -2), (H // 2, -(W // 2) + 1), (-(H // 2) + 1, W // 2), (H // 4, W // 3)]
+    frames = np.array([np.roll(ref, s, axis=(0, 1)) for s in shifts], np.float32)
+    for method in (oracle.CC_U, oracle.CC_SN):
+        res = run_gpu(torch, ref, frames, u=100, method=method)
+        for r, (dy, dx) in zip(res, shifts):
+            assert (int(r["ipy"]), int(r["ipx"])) == (dy, dx)
+            if method == oracle.CC_U:
+                assert float(r["dx"]) == dx and float(r["dy"]) == dy
+
+
+# ------------------------------------------------------------------ frame stream
+def test_frame_stream_first_batch(torch):
+    s = synth.frame_stream(seed=0, n=10_000, count=256)
+    res = run_gpu(torch, s.ref, s.frames, u=100)
+    orc = oracle.track_batch_parallel(s.frames, s.ref, u=100)
+    compare(res, orc, "stream batch 0")
+    # the estimates track the known trajectory
+    err = np.hypot(res["dx"] - s.d_true[:, 0], res["dy"] - s.d_true[:, 1])
+    assert np.median(err) < 0.05
+    print("flags", flag_counts(res))
+
+
+def test_frame_stream_full_size_sampled(torch):
+    """The full 10,000-frame stream in 256-frame graph batches; a sample checked frame by frame."""
+    s = synth.frame_stream(seed=0, n=10_000)
+    res = run_gpu(torch, s.ref, s.frames, u=100, graphs=True)
+    assert res.shape == (10_000,)
+    # properties that hold at every frame: inside the refinement square, near the truth
+    assert np.all(np.abs(res["dx"] - res["ipx"]) <= 0.76) and np.all(np.abs(res["dy"] - res["ipy"]) <= 0.76)
+    err = np.hypot(res["dx"] - s.d_true[:, 0], res["dy"] - s.d_true[:, 1])
+    assert np.max(err) < 0.5 and np.median(err) < 0.05
+    assert not np.any(res["flags"] & (C.R_OVERFLOW | C.R_NONFINITE))
+    rng = np.random.default_rng(123)
+    idx = np.sort(rng.choice(10_000, size=160, replace=False))
+    idx = np.unique(np.concatenate([idx, [0, 255, 256, 9_983, 9_984, 9_999]]))
+    orc = oracle.track_batch_parallel(s.frames[idx], s.ref, u=100)
+    compare(res[idx], orc, "stream sample")
+    # every frame the guard had to re-decide is checked too
+    gidx = np.nonzero(res["flags"] & (C.R_SUB_GUARD | C.R_FP64 | C.R_INT_GUARD))[0][:200]
+    if len(gidx):
+        compare(res[gidx], oracle.track_batch_parallel(s.frames[gidx], s.ref, u=100), "guarded frames")
+    print("flags over 10000 frames", flag_counts(res))
+
+
+# ------------------------------------------------------------------ shapes, u, methods
+@pytest.mark.parametrize("H,W,u", [(8, 8, 7), (16, 16, 1), (16, 32, 2), (32, 32, 37), (64, 32, 100),
+                                   (32, 128, 100), (128, 64, 50), (64, 64, 256), (128, 128, 11)])
+@pytest.mark.parametrize("method", [oracle.CC_U, oracle.CC_SN])
+def test_shapes_and_upsampling(torch, H, W, u, method):
+    rng = np.random.default_rng(H * 1000 + W + u)
+    ref = synth.gaussian_spot(H, W, H / 2, W / 2, max(1.2, min(H, W) / 16), 800.0, 12.0)
+    frames = []
+    for _ in range(12):
+        d = rng.uniform(-min(H, W) / 6, min(H, W) / 6, size=2)
+        frames.append(rng.poisson(synth.gaussian_spot(H, W, H / 2 + d[1], W / 2 + d[0],
+                                                      max(1.2, min(H, W) / 16), 800.0, 12.0)))
+    frames = np.array(frames, np.float32)
+    res = run_gpu(torch, ref, frames, u=u, method=method)
+    orc = oracle.track_batch(frames, ref, u=u, method=method)
+    compare(res, orc, f"{H}x{W} u={u} m={method}")
+
+
+def test_ccsn_stream_batch(torch):
+    s = synth.frame_stream(seed=3, n=128, H=64, W=64, sigma=3.0, amplitude=1000.0, background=10.0, step=0.5,
+                           bound=10.0)
+    res = run_gpu(torch, s.ref, s.frames, u=100, method=oracle.CC_SN, eps=200.0)
+    orc = oracle.track_batch_parallel(s.frames, s.ref, u=100, method=oracle.CC_SN, eps=200.0)
+    compare(res, orc, "cc-sn stream")
+
+
+def test_textures_ragged_batch(torch):
+    rng = np.random.default_rng(8)
+    ref = synth.random_texture(rng, 64, 64)
+    frames = []
+    for _ in range(37):                         # ragged: not a multiple of anything
+        d = rng.uniform(-8, 8, size=2)
+        mu = np.real(np.fft.ifft2(np.fft.fft2(ref) * np.exp(
+            -2j * np.pi * (np.fft.fftfreq(64)[:, None] * d[1] + np.fft.fftfreq(64)[None, :] * d[0]))))
+        frames.append(rng.poisson(np.maximum(mu, 0)))
+    frames = np.array(frames, np.float32)
+    res = run_gpu(torch, ref, frames, u=100, max_batch=16)
+    compare(res, oracle.track_batch(frames, ref, u=100), "textures")
+
+
+# ------------------------------------------------------------------ guard levels
+@pytest.mark.parametrize("delta", [1e-4, 1e-5, 3e-6, 1e-6, 1e-7])
+def test_near_half_bin_shifts_exercise_guard(torch, delta):
+    """Noise-free spots placed delta px past a half-bin: top-2 margins shrink with delta
+    (about 1e-3 * delta relative), walking the decision through every guard level."""
+    N, sigma, u = 64, 3.0, 100
+    rng = np.random.default_rng(int(1 / delta))
+    ref = synth.gaussian_spot(N, N, 32.0, 32.0, sigma, 1000.0, 10.0)
+    frames = []
+    for _ in range(16):
+        k = rng.integers(-150, 150, size=2)
+        d = (k + 0.5) / u + delta * rng.choice([-1, 1], size=2)
+        frames.append(synth.gaussian_spot(N, N, 32.0 + d[1], 32.0 + d[0], sigma, 1000.0, 10.0))
+    frames = np.array(frames, np.float32)
+    res = run_gpu(torch, ref, frames, u=u)
+    orc = oracle.track_batch(frames, ref, u=u)
+    compare(res, orc, f"half-bin delta={delta}")
+    print("delta", delta, flag_counts(res))
+
+
+# ------------------------------------------------------------------ FP32 error vs thresholds
+def test_fp32_surface_error_is_far_below_guard_thresholds(torch):
+    """The guard is only sound if its thresholds bound the FP32 surface error. Measure the
+    error of the FP32 delta surface near its maximum against the FP64 oracle."""
+    s = synth.frame_stream(seed=5, n=64)
+    res, si, ss = run_gpu(torch, s.ref, s.frames, u=100, debug=True)
+    eps32 = 2.0 ** -23
+    worst_sub, worst_int = 0.0, 0.0
+    for f in range(len(s.frames)):
+        a, b, sense = oracle.surface_operands(s.frames[f], s.ref)
+        X = oracle.product_spectrum(a, b)
+        H, W = a.shape
+        scale = float(np.sum(np.abs(X.real) + np.abs(X.imag)))     # sum w|X| over the full plane
+        c64 = np.real(np.fft.ifft2(X)) * H * W
+        worst_int = max(worst_int, np.max(np.abs(si[f] - c64)) / scale)
+        py, px = int(res["ipy"][f]), int(res["ipx"][f])
+        cu = oracle.upsampled_cc(X, py, px, 100) * H * W
+        M = cu.shape[0]
+        d64 = cu - cu[M // 2, M // 2]
+        near = d64 >= d64.max() - 1e-5 * scale
+        worst_sub = max(worst_sub, np.max(np.abs(ss[f] - d64)[near]) / scale)
+    print(f"worst FP32 errors / (eps32 * sum|X|): integer {worst_int / eps32:.3g}, sub-pixel {worst_sub / eps32:.3g}")
+    assert worst_sub < 0.125 * 1.0 * eps32      # tau0 = 1 eps32: keep an 8x margin
+    assert worst_int < 0.125 * 16.0 * eps32     # tau_int = 16 eps32
+
+
+# ------------------------------------------------------------------ paths and edges
+def test_host_path_graphs_and_submit_match_device_path(torch):
+    s = synth.frame_stream(seed=2, n=300, count=300)
+    base = run_gpu(torch, s.ref, s.frames[:256], u=100)
+    stream = torch.cuda.Stream()
+    t = C.Tracker(s.ref, upsample=100, graphs=True, stream=stream, profile=True)
+    host = t.track_host(s.frames[:256])
+    assert np.array_equal(host, base)
+    dev = torch.from_numpy(s.frames.view(np.int16)).cuda().view(torch.uint16)
+    out = torch.empty((256, 24), dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    for _ in range(3):                       # capture once, replay twice
+        C.ccst_track(t.ctx, dev[:256], 256, 0, out)
+    C.ccst_sync(t.ctx)
+    assert np.array_equal(C.decode(out), base)
+    ms, launches = C.ccst_profile_kernel_ms(t.ctx)
+    assert launches >= 1 and ms > 0
+    out2 = torch.empty((256, 24), dtype=torch.uint8, device="cuda")
+    tk = C.ccst_submit(t.ctx, dev[:256], 256, out2)
+    done = False
+    for _ in range(10000):
+        if C.ccst_poll(t.ctx, tk, 1000):
+            done = True
+            break
+    assert done and np.array_equal(C.decode(out2), base)
+    with pytest.raises(C.CcstError):
+        C.ccst_poll(t.ctx, tk, 0)            # released ticket is unknown now
+    t.close()
+
+
+def test_edge_cases(torch):
+    H = W = 32
+    ref = synth.gaussian_spot(H, W, 16.0, 16.0, 2.0, 500.0, 5.0).astype(np.float32)
+    t = C.Tracker(ref, upsample=10, in_dtype="f32", max_batch=8)
+    out = torch.empty((8, 24), dtype=torch.uint8, device="cuda")
+    frames = torch.zeros((9, H, W), dtype=torch.float32, device="cuda")
+    C.ccst_track(t.ctx, frames, 0, 0, out)                       # n = 0: no-op
+    with pytest.raises(C.CcstError) as e:
+        C.ccst_track(t.ctx, frames, 9, 0, out)                   # n > max_batch
+    assert e.value.code == C.E_INVALID
+    with pytest.raises(C.CcstError):
+        C.ccst_track(t.ctx, frames, 1, W - 1, out)               # pitch < W
+    with pytest.raises(C.CcstError) as e:
+        C.ccst_backward(t.ctx, frames, 1, None, None, None)
+    assert e.value.code == C.E_UNSUPPORTED
+    # constant frame: every point ties; lowest index everywhere, as in the oracle
+    frames[0] = 7.0
+    C.ccst_track(t.ctx, frames, 1, 0, out)
+    C.ccst_sync(t.ctx)
+    r = C.decode(out)[0]
+    o = oracle.track_one(np.full((H, W), 7.0), ref, u=10)
+    assert (int(r["ipy"]), int(r["ipx"]), float(r["dx"]), float(r["dy"])) == (o["ipy"], o["ipx"], o["dx"], o["dy"])
+    t.close()
+    # row pitch larger than W
+    s = synth.frame_stream(seed=4, n=20, H=64, W=64, sigma=3.0, amplitude=1000.0, background=10.0)
+    a = run_gpu(torch, s.ref, s.frames, u=100, pitch_pad=24)
+    b = run_gpu(torch, s.ref, s.frames, u=100)
+    assert np.array_equal(a, b)
+    # a frame with zero pixels under CC-SN
+    f = s.frames[:2].copy()
+    f[:, :10, :] = 0
+    compare(run_gpu(torch, s.ref, f, method=oracle.CC_SN), oracle.track_batch(f, s.ref, method=oracle.CC_SN),
+            "zeros cc-sn")
