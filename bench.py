@@ -217,17 +217,18 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    s = synth.frame_stream(seed=shard_seed(rank), n=N_FRAMES)
+    n_frames = args.frames
+    s = synth.frame_stream(seed=shard_seed(rank), n=N_FRAMES, count=n_frames)
     frames_dev = torch.from_numpy(s.frames.view(np.int16)).cuda().view(torch.uint16)
-    nb = (N_FRAMES + BATCH - 1) // BATCH
-    outs = torch.empty((N_FRAMES, 24), dtype=torch.uint8, device="cuda")
+    nb = (n_frames + BATCH - 1) // BATCH
+    outs = torch.empty((n_frames, 24), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.Stream()
     t = C.Tracker(s.ref, upsample=U, method="ccu", in_dtype="u16", max_batch=BATCH, stream=stream,
                   graphs=True, profile=True)
 
     def step(i):
         b = i % nb
-        lo, hi = b * BATCH, min(N_FRAMES, (b + 1) * BATCH)
+        lo, hi = b * BATCH, min(n_frames, (b + 1) * BATCH)
         C.ccst_track(t.ctx, frames_dev[lo:hi], hi - lo, 0, outs[lo:hi])
         return hi - lo
 
@@ -261,7 +262,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel (FP32 ALU bound): the graphs' last replays cover
     # every batch of the stream once
-    kframes = N_FRAMES if kern_launches == nb else kern_launches * BATCH
+    kframes = n_frames if kern_launches == nb else kern_launches * BATCH
     fpf = flop_per_frame()
     achieved = fpf * kframes / (kern_ms / 1e3) / 1e12
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
@@ -269,22 +270,22 @@ def run_ours(args):
     flags = res_all["flags"]
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
-    e2e_steps = min(args.steps, 2 * nb)
+    e2e_steps = 0 if args.no_e2e else min(args.steps, 2 * nb)
     pinned_t = torch.from_numpy(s.frames.view(np.int16)).pin_memory()
     pinned = pinned_t.numpy().view(np.uint16)
     host_out_t = torch.empty((BATCH * 24,), dtype=torch.uint8).pin_memory()
     host_out = host_out_t.numpy().view(C.RESULT_DTYPE)
-    for i in range(3):
+    for i in range(3 if e2e_steps else 0):
         C.ccst_track_host(t.ctx, pinned[:BATCH], BATCH, 0, host_out)
     t0 = time.perf_counter()
     e2e_frames = 0
     for i in range(e2e_steps):
         b = i % nb
-        lo, hi = b * BATCH, min(N_FRAMES, (b + 1) * BATCH)
+        lo, hi = b * BATCH, min(n_frames, (b + 1) * BATCH)
         C.ccst_track_host(t.ctx, pinned[lo:hi], hi - lo, 0, host_out[:hi - lo])
         e2e_frames += hi - lo
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, device="cuda")
-    e2e = {"value": e2e_frames * world / e2e_s, "unit": "frames/s",
+    e2e = {"value": e2e_frames * world / e2e_s if e2e_frames else None, "unit": "frames/s",
            "h2d_bytes_per_step": BATCH * H * W * 2, "d2h_bytes_per_step": BATCH * 24,
            "api": "ccst_track_host (pinned host frames in, host results out, synchronous per batch)"}
 
@@ -297,7 +298,7 @@ def run_ours(args):
         "config": {"workload": "frame stream: 10000 uint16 128x128 Gaussian-spot frames (sigma 2.5, peak 2000, "
                                "bg 20, Poisson), Brownian trajectory step 0.3 px, u=100, CC-U, "
                                "256-frame CUDA-graph batches",
-                   "global_batch": BATCH * world, "frames_per_rank": N_FRAMES, "upsample": U,
+                   "global_batch": BATCH * world, "frames_per_rank": n_frames, "upsample": U,
                    "parallelism": f"replicas x{world} (independent streams)",
                    "l2": "inputs larger than L2 (328 MB stream per rank, each step reads a new 8.4 MB slice)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -400,6 +401,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=40)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--frames", type=int, default=N_FRAMES,
+                    help="frames of the stream to stage (the workload is 10000; smaller only for profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -31,7 +31,7 @@ constexpr size_t kMaxGraphs = 512;
 // Guard thresholds, in units of the FP32 unit roundoff times sum w|X| (see DESIGN notes
 // in the repository: calibrated against the FP64 oracle with a wide margin).
 constexpr float kEps32 = 1.1920929e-07f;
-constexpr float kTauInt = 16.0f * kEps32;
+constexpr float kTauInt = 32.0f * kEps32;
 constexpr float kTau0 = 1.0f * kEps32;
 constexpr float kTau1 = 0.05f * kEps32;
 

@@ -97,8 +97,9 @@ __device__ T block_sum(T v, T* scratch) {
     if (lane == 0) scratch[wid] = v;
     __syncthreads();
     T r = 0;
+    const int nwarps = (blockDim.x + 31) >> 5;
     if (wid == 0) {
-        r = lane < kWarps ? scratch[lane] : T(0);
+        r = lane < nwarps ? scratch[lane] : T(0);
         r = warp_sum(r);
         if (lane == 0) scratch[0] = r;
     }
@@ -160,9 +161,10 @@ __device__ void block_topk(TopK<K>& t, float* sv, int* sj) {
         for (int k = 0; k < K; ++k) { sv[wid * K + k] = t.v[k]; sj[wid * K + k] = t.j[k]; }
     }
     __syncthreads();
+    const int nwarps = (blockDim.x + 31) >> 5;
     if (wid == 0) {
         t.init();
-        if (lane < kWarps) {
+        if (lane < nwarps) {
 #pragma unroll
             for (int k = 0; k < K; ++k) t.push(sv[lane * K + k], sj[lane * K + k]);
         }

@@ -22,6 +22,11 @@
 // real-input spectrum). The pairs +-ky and +-t are folded too:
 //   T'(+-t) = U'(t) +- i V(t),  U'(t) = sum_m (cos th_mt - 1) P(m),  V(t) = sum_m sin th_mt Q(m),
 //   P(m) = X'(m) + X'(-m),  Q(m) = X'(m) - X'(-m),  th_mt = 2 pi m t / (uH).
+// The interpolant is the real part of the full signed-frequency sum (Nyquist bin
+// at -N/2). For the y-Nyquist row (ky = H/2) in the columns 0 < kx < W/2 that
+// real part pairs each term with its Hermitian partner so that the row's y-phase
+// enters only through its real part cos(pi s_y); the folded sums reproduce this by
+// keeping only the cosine part of that row (Q(H/2, kx) = 0 for kx < W/2).
 // The same algebra is exact in real arithmetic; in FP32 it keeps the rounding
 // error proportional to the surface's variation over the grid rather than to
 // its value, which is what decides the sub-pixel argmax.
@@ -150,7 +155,7 @@ __host__ __device__ inline size_t smem_bytes(const Geom& g) {
     off += sizeof(float2) * (size_t)g.H * g.Wcp;            // B
     size_t cbytes = sizeof(float4) * (size_t)g.TC * g.Wcp;
     const size_t packed = sizeof(float2) * (size_t)(g.H / 2) * g.W;
-    const size_t l1 = sizeof(float2) * (size_t)(3 * g.H + 2 * g.Wcp);
+    const size_t l1 = sizeof(float2) * (size_t)(3 * g.H + 2 * g.Wcp + 2);
     if (cbytes < packed) cbytes = packed;
     if (cbytes < l1) cbytes = l1;
     off += align_up(cbytes, 16);                            // C
@@ -171,7 +176,7 @@ __device__ inline Smem carve(const Geom& g, unsigned char* base) {
     s.B = (float2*)(base + off); off += sizeof(float2) * (size_t)g.H * g.Wcp;
     size_t cbytes = sizeof(float4) * (size_t)g.TC * g.Wcp;
     const size_t packed = sizeof(float2) * (size_t)(g.H / 2) * g.W;
-    const size_t l1 = sizeof(float2) * (size_t)(3 * g.H + 2 * g.Wcp);
+    const size_t l1 = sizeof(float2) * (size_t)(3 * g.H + 2 * g.Wcp + 2);
     if (cbytes < packed) cbytes = packed;
     if (cbytes < l1) cbytes = l1;
     s.C = (float4*)(base + off); off += align_up(cbytes, 16);
@@ -378,14 +383,20 @@ __device__ void stage_a(const Geom& g, const Smem& S, int t0) {
 #pragma unroll
             for (int k = 0; k < 2; ++k) acc[i][k] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (tb < g.T1p) {
-            // Nyquist row first (signed -H/2): P = X'(Hh), Q = -X'(Hh)
+            // Nyquist row first (signed -H/2): P = X'(Hh); Q = -X'(Hh) in the x-Nyquist
+            // column only (elsewhere the row contributes through cos(pi t/u) alone)
             for (int m = Hh; m >= 1; --m) {
                 const float4 cm = __ldg((const float4*)&g.tA_cm1[(m - 1) * g.T1p + tb]);
                 const float4 sn = __ldg((const float4*)&g.tA_s[(m - 1) * g.T1p + tb]);
                 const float4 p = *(const float4*)&S.A[m * Wcp + kb];
                 float4 q;
-                if (m == Hh) q = make_float4(-p.x, -p.y, -p.z, -p.w);
-                else q = *(const float4*)&S.A[(H - m) * Wcp + kb];
+                if (m == Hh) {
+                    const int kn = g.W >> 1;
+                    q = make_float4(kb == kn ? -p.x : 0.f, kb == kn ? -p.y : 0.f,
+                                    kb + 1 == kn ? -p.z : 0.f, kb + 1 == kn ? -p.w : 0.f);
+                } else {
+                    q = *(const float4*)&S.A[(H - m) * Wcp + kb];
+                }
                 const float cmv[4] = {cm.x, cm.y, cm.z, cm.w};
                 const float snv[4] = {sn.x, sn.y, sn.z, sn.w};
 #pragma unroll
@@ -551,17 +562,22 @@ __device__ int pair_difference_guard(const Geom& g, const Smem& S, int nc, float
     float2* dEx = dEy + H;             // Wcp    w (E(kx, tx_c) - E(kx, rx))
     const int j1 = S.cj[0];
     const int ry = j1 / g.M - g.h0, rx = j1 % g.M - g.h0;
-    // G(ky), using the table twiddles w E(kx, rx) = wc -+ i ws
+    // G(ky), using the table twiddles w E(kx, rx) = wc -+ i ws. For the Nyquist row the
+    // x-Nyquist column is kept apart in slot H + 3H + Wcp (it takes the full y-phase).
+    float2* GN = dEx + Wcp;
+    const int kn = g.W >> 1;
     for (int ky = threadIdx.x; ky < H; ky += blockDim.x) {
-        float2 acc = make_float2(0.f, 0.f);
+        float2 acc = make_float2(0.f, 0.f), accn = make_float2(0.f, 0.f);
         const int arx = rx < 0 ? -rx : rx;
         for (int kx = Wc - 1; kx >= 0; --kx) {
             const float c = __ldg(&g.tB_wc[kx * g.T1p + arx]);
             float s = __ldg(&g.tB_ws[kx * g.T1p + arx]);
             if (rx < 0) s = -s;
-            acc = cadd(acc, cmul(xprime(g, S, ky, kx), make_float2(c, s)));
+            const float2 t = cmul(xprime(g, S, ky, kx), make_float2(c, s));
+            if (ky == g.Hh && kx == kn) accn = t; else acc = cadd(acc, t);
         }
         G[ky] = acc;
+        if (ky == g.Hh) GN[0] = accn;
     }
     __syncthreads();
     if (threadIdx.x == 0) S.cv[0] = 0.f;
@@ -586,11 +602,18 @@ __device__ int pair_difference_guard(const Geom& g, const Smem& S, int nc, float
         __syncthreads();
         float part = 0.f;
         for (int ky = threadIdx.x; ky < H; ky += blockDim.x) {
-            float2 F = make_float2(0.f, 0.f);
-            for (int kx = Wc - 1; kx >= 0; --kx) F = cadd(F, cmul(xprime(g, S, ky, kx), dEx[kx]));
-            const float2 t1 = cmul(Eyc[ky], F);
-            const float2 t2 = cmul(dEy[ky], G[ky]);
-            part += t1.x + t2.x;
+            float2 F = make_float2(0.f, 0.f), FN = make_float2(0.f, 0.f);
+            for (int kx = Wc - 1; kx >= 0; --kx) {
+                const float2 t = cmul(xprime(g, S, ky, kx), dEx[kx]);
+                if (ky == g.Hh && kx == kn) FN = t; else F = cadd(F, t);
+            }
+            if (ky == g.Hh) {
+                // real part of the row's y-phase, except in the x-Nyquist column
+                part += Eyc[ky].x * F.x + dEy[ky].x * G[ky].x;
+                part += cmul(Eyc[ky], FN).x + cmul(dEy[ky], GN[0]).x;
+            } else {
+                part += cmul(Eyc[ky], F).x + cmul(dEy[ky], G[ky]).x;
+            }
         }
         const float D = block_sum(part, S.rv);
         if (threadIdx.x == 0) S.cv[c] = g.sense * D;
@@ -804,7 +827,10 @@ __global__ void __launch_bounds__(256) fp64_guard_kernel(Geom g, Batch b, double
             double acc = 0.0;
             for (int idx = threadIdx.x; idx < g.H * g.Wc; idx += blockDim.x) {
                 const int ky = idx / g.Wc, kx = idx - ky * g.Wc;
-                const double2 e = cmul(ey[ky], ex[kx]);
+                // the Nyquist row enters through the real part of its y-phase, except in
+                // the x-Nyquist column (real part of the full signed-frequency sum)
+                const double2 eyk = (ky == g.Hh && 2 * kx != g.W) ? make_double2(ey[ky].x, 0.0) : ey[ky];
+                const double2 e = cmul(eyk, ex[kx]);
                 const double2 x = Xh[ky * g.Wcp + kx];
                 acc = fma(x.x, e.x, fma(-x.y, e.y, acc));
             }
