@@ -39,7 +39,8 @@ SM_COUNT = 148
 FP32_LANES_PER_SM = 128          # FFMA lanes per SM (4 SMSPs x 32)
 MAX_SM_MHZ = 2032.0
 PROFILE_FILE = os.path.join(ROOT, "profiles", "track_kernel_128x128_u100.txt")
-KERNEL_SOURCES = ["paper_2310_08770_b300/csrc/ccst_kernels.cuh", "paper_2310_08770_b300/csrc/ccst_device.cuh"]
+KERNEL_SOURCES = ["paper_2310_08770_b300/csrc/ccst_kernels.cuh", "paper_2310_08770_b300/csrc/ccst_device.cuh",
+                  "paper_2310_08770_b300/csrc/ccst_dfloat.cuh"]
 
 
 def grid_size(u):
@@ -308,9 +309,9 @@ def run_ours(args):
                      "peak_basis": "148 SMs x 128 FP32 FMA lanes x 2 x 2032 MHz (nominal max clock)"},
         "clocks": clk,
         "e2e": e2e,
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": args.steps,                     # one tracking kernel per batch
         "guard": {"frames": int(len(flags)), "int": int(np.sum((flags & C.R_INT_GUARD) != 0)),
-                  "sub": int(np.sum((flags & C.R_SUB_GUARD) != 0)), "fp64": int(np.sum((flags & C.R_FP64) != 0)),
+                  "sub": int(np.sum((flags & C.R_SUB_GUARD) != 0)), "df64": int(np.sum((flags & C.R_DF64) != 0)),
                   "overflow": int(np.sum((flags & C.R_OVERFLOW) != 0))},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

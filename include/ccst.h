@@ -71,7 +71,7 @@ extern "C" {
 /* ccst_result.flags (per frame) */
 #define CCST_R_INT_GUARD   0x01u /* integer peak re-decided by FP64 direct sums */
 #define CCST_R_SUB_GUARD   0x02u /* sub-pixel peak re-decided by exact FP32 grid differences */
-#define CCST_R_FP64        0x04u /* sub-pixel peak decided by the FP64 re-evaluation */
+#define CCST_R_DF64        0x04u /* sub-pixel peak decided from a double-float (~48-bit) product spectrum */
 #define CCST_R_OVERFLOW    0x08u /* too many near-tied points to certify: the FP32 choice is reported */
 #define CCST_R_NONFINITE   0x10u /* the surface held no finite value (non-finite input) */
 
@@ -194,6 +194,17 @@ int ccst_grid_size(ccst_ctx* ctx);
  * Errors: as ccst_track. */
 int ccst_debug_surfaces(ccst_ctx* ctx, const void* frames_dev, int64_t n, int64_t pitch_elems,
                         ccst_result* out_dev, float* int_surf_dev, float* sub_surf_dev);
+
+/* Diagnostic entry, for tests that calibrate the tie guard.
+ * For frame f it computes v(jb) - v(ja) of the upsampled surface (Sec. III),
+ * unnormalised and relative to the frame's integer peak, for the flat grid
+ * indices ja = pairs_dev[2f] and jb = pairs_dev[2f+1], two ways:
+ *   d32_dev[f]  by the FP32 pair-difference guard;
+ *   d64_dev[f]  accumulated in FP64 from the same FP32 product spectrum.
+ * No tracking results are written. All buffers are caller-owned device memory.
+ * Errors: as ccst_track, plus CCST_E_INVALID for NULL buffers. */
+int ccst_debug_pairs(ccst_ctx* ctx, const void* frames_dev, int64_t n, int64_t pitch_elems,
+                     const int32_t* pairs_dev, float* d32_dev, double* d64_dev);
 
 #ifdef __cplusplus
 }

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libccst.so")
 SOURCES = ["ccst.cu"]
-DEPS = SOURCES + ["ccst_kernels.cuh", "ccst_device.cuh"]
+DEPS = SOURCES + ["ccst_kernels.cuh", "ccst_device.cuh", "ccst_dfloat.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

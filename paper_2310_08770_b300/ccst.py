@@ -21,7 +21,7 @@ FLAG_PROFILE = 0x4
 
 R_INT_GUARD = 0x01
 R_SUB_GUARD = 0x02
-R_FP64 = 0x04
+R_DF64 = 0x04
 R_OVERFLOW = 0x08
 R_NONFINITE = 0x10
 
@@ -77,6 +77,8 @@ _SIGS = [
     ("ccst_profile_reset", ctypes.c_int, [ctypes.c_void_p]),
     ("ccst_debug_surfaces", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("ccst_debug_pairs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 ]
 
 
@@ -199,6 +201,11 @@ def _check_nonneg(v, ctx):
 def ccst_debug_surfaces(ctx, frames_dev, n, pitch_elems, out_dev, int_surf_dev, sub_surf_dev) -> None:
     _check(lib().ccst_debug_surfaces(ctx, _ptr(frames_dev), int(n), int(pitch_elems), _ptr(out_dev),
                                      _ptr(int_surf_dev), _ptr(sub_surf_dev)), ctx)
+
+
+def ccst_debug_pairs(ctx, frames_dev, n, pitch_elems, pairs_dev, d32_dev, d64_dev) -> None:
+    _check(lib().ccst_debug_pairs(ctx, _ptr(frames_dev), int(n), int(pitch_elems), _ptr(pairs_dev),
+                                  _ptr(d32_dev), _ptr(d64_dev)), ctx)
 
 
 # ---------------------------------------------------------------- convenience wrapper

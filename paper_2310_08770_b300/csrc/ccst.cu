@@ -24,7 +24,6 @@ static_assert(sizeof(ccst_result) == 24, "result record is 24 bytes");
 
 namespace {
 
-constexpr int kL2Slots = 32;      // CTAs (and workspace slots) of the FP64 re-evaluation
 constexpr int kTickets = 64;      // in-flight submissions per context
 constexpr size_t kMaxGraphs = 512;
 
@@ -33,7 +32,7 @@ constexpr size_t kMaxGraphs = 512;
 constexpr float kEps32 = 1.1920929e-07f;
 constexpr float kTauInt = 32.0f * kEps32;
 constexpr float kTau0 = 1.0f * kEps32;
-constexpr float kTau1 = 0.05f * kEps32;
+constexpr float kTau1 = 0.02f * kEps32;
 
 std::mutex g_create_err_mu;
 std::string g_create_err = "no error";
@@ -86,6 +85,38 @@ __global__ void init_tables(Geom g, float* cm1, float* sA, float* wc, float* ws,
     }
 }
 
+// Double-float copies: FFT twiddles, the reference spectrum, and the two-level tables of
+// exp(2 pi i n / D) for D = uH and uW (coarse steps of B, fine steps of 1).
+__global__ void init_dfloat(Geom g, const double2* tw64, const double2* FE64, dfc* twdf, dfc* FEdf,
+                            dfc* eyc, dfc* eyf, dfc* exc, dfc* exf, int ncy, int ncx) {
+    const long long Dy = (long long)g.u * g.H, Dx = (long long)g.u * g.W;
+    const int nFE = g.H * g.Wc, ntw = g.Ntw / 2;
+    const int total = ntw + nFE + ncy + g.By + ncx + g.Bx;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        int k = i;
+        if (k < ntw) {
+            twdf[k] = {df_from_double(tw64[k].x), df_from_double(tw64[k].y)};
+            continue;
+        }
+        k -= ntw;
+        if (k < nFE) {
+            FEdf[k] = {df_from_double(FE64[k].x), df_from_double(FE64[k].y)};
+            continue;
+        }
+        k -= nFE;
+        long long n;
+        long long D;
+        dfc* dst;
+        if (k < ncy) { n = (long long)k * g.By; D = Dy; dst = eyc + k; }
+        else if ((k -= ncy) < g.By) { n = k; D = Dy; dst = eyf + k; }
+        else if ((k -= g.By) < ncx) { n = (long long)k * g.Bx; D = Dx; dst = exc + k; }
+        else { k -= ncx; n = k; D = Dx; dst = exf + k; }
+        double s, c;
+        sincospi(2.0 * (double)(n % D) / (double)D, &s, &c);
+        *dst = {df_from_double(c), df_from_double(s)};
+    }
+}
+
 __global__ void init_ref_operand(Geom g, const float* ref, double* b64) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.H * g.W; i += gridDim.x * blockDim.x) {
         const double e = (double)ref[i];
@@ -129,8 +160,7 @@ struct ccst_ctx {
     double2* d_tw64 = nullptr;
     float2* d_tw32 = nullptr;
     float* d_tab = nullptr;       // all stage tables in one block
-    GuardRec* d_guard = nullptr;  // max_batch
-    double2* d_l2work = nullptr;  // kL2Slots workspaces
+    dfc* d_df = nullptr;          // double-float tables in one block
     void* d_frames = nullptr;     // host-path staging
     Result* d_out = nullptr;      // host-path staging
     // graphs keyed by (frames, n, pitch, out), each with its own profiling event pair
@@ -190,7 +220,7 @@ static void free_all(ccst_ctx* c) {
     for (int i = 0; i < kTickets; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     void* ptrs[] = {c->d_ref32, c->d_b64, c->d_FE64, c->d_FE32, c->d_tw64, c->d_tw32,
-                    c->d_tab,   c->d_guard, c->d_l2work, c->d_frames, c->d_out};
+                    c->d_tab,   c->d_df,  c->d_frames, c->d_out};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -271,8 +301,14 @@ extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pi
 
     const size_t HW = (size_t)H * W, HWc = (size_t)H * g.Wc;
     const size_t tabA = (size_t)g.Hh * g.T1p, tabB = (size_t)g.Wc * g.T1p;
-    const size_t l2per = (size_t)(H / 2) * W + (size_t)H * g.Wcp;
+    const size_t l2per = (size_t)(H / 2) * W + (size_t)H * g.Wcp;   // FP64 FFT workspace at create
     const size_t elem = p.in_dtype == CCST_U16 ? 2 : 4;
+    const long long Dy = (long long)g.u * H, Dx = (long long)g.u * W;
+    g.By = 1; while ((long long)g.By * g.By < Dy) ++g.By;
+    g.Bx = 1; while ((long long)g.Bx * g.Bx < Dx) ++g.Bx;
+    const int ncy = (int)((Dy + g.By - 1) / g.By), ncx = (int)((Dx + g.Bx - 1) / g.Bx);
+    const size_t ndf = (size_t)(g.Ntw / 2) + HWc + ncy + g.By + ncx + g.Bx;
+    double2* d_work = nullptr;
     struct { void** ptr; size_t bytes; } allocs[] = {
         {(void**)&c->d_ref32, HW * sizeof(float)},
         {(void**)&c->d_b64, HW * sizeof(double)},
@@ -281,8 +317,8 @@ extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pi
         {(void**)&c->d_tw64, (size_t)(g.Ntw / 2) * sizeof(double2)},
         {(void**)&c->d_tw32, (size_t)(g.Ntw / 2) * sizeof(float2)},
         {(void**)&c->d_tab, (2 * tabA + 3 * tabB) * sizeof(float)},
-        {(void**)&c->d_guard, (size_t)p.max_batch * sizeof(GuardRec)},
-        {(void**)&c->d_l2work, (size_t)kL2Slots * l2per * sizeof(double2)},
+        {(void**)&c->d_df, ndf * sizeof(dfc)},
+        {(void**)&d_work, l2per * sizeof(double2)},
         {(void**)&c->d_frames, (size_t)p.max_batch * HW * elem},
         {(void**)&c->d_out, (size_t)p.max_batch * sizeof(Result)},
     };
@@ -296,21 +332,31 @@ extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pi
     g.FE32 = c->d_FE32; g.FE64 = c->d_FE64; g.b64 = c->d_b64; g.tw32 = c->d_tw32; g.tw64 = c->d_tw64;
     g.tA_cm1 = c->d_tab; g.tA_s = c->d_tab + tabA;
     g.tB_wc = c->d_tab + 2 * tabA; g.tB_ws = g.tB_wc + tabB; g.tB_gc = g.tB_ws + tabB;
+    dfc* twdf = c->d_df;
+    dfc* FEdf = twdf + g.Ntw / 2;
+    dfc* eyc = FEdf + HWc;
+    dfc* eyf = eyc + ncy;
+    dfc* exc = eyf + g.By;
+    dfc* exf = exc + ncx;
+    g.twdf = twdf; g.FEdf = FEdf; g.eyc = eyc; g.eyf = eyf; g.exc = exc; g.exf = exf;
 
     auto step = [&](cudaError_t e2, const char* what) {
         if (e2 != cudaSuccess) fail(nullptr, CCST_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e2));
         return e2 == cudaSuccess;
     };
-    if (!step(cudaMemcpyAsync(c->d_ref32, ref, HW * sizeof(float), cudaMemcpyDefault, c->stream), "copy ref") ||
-        !step(cudaMemsetAsync(c->d_guard, 0, (size_t)p.max_batch * sizeof(GuardRec), c->stream), "memset guard"))
-        return bail(CCST_E_CUDA);
+    auto bail_work = [&](int code) { cudaFree(d_work); return bail(code); };
+    if (!step(cudaMemcpyAsync(c->d_ref32, ref, HW * sizeof(float), cudaMemcpyDefault, c->stream), "copy ref"))
+        return bail_work(CCST_E_CUDA);
     init_twiddles<<<1, 256, 0, c->stream>>>(g.Ntw, c->d_tw64, c->d_tw32);
     init_tables<<<64, 256, 0, c->stream>>>(g, (float*)g.tA_cm1, (float*)g.tA_s, (float*)g.tB_wc,
                                            (float*)g.tB_ws, (float*)g.tB_gc);
     init_ref_operand<<<32, 256, 0, c->stream>>>(g, (const float*)c->d_ref32, c->d_b64);
-    init_ref_spectrum<<<1, 256, 0, c->stream>>>(g, c->d_l2work, c->d_FE64, c->d_FE32);
+    init_ref_spectrum<<<1, 256, 0, c->stream>>>(g, d_work, c->d_FE64, c->d_FE32);
+    init_dfloat<<<32, 256, 0, c->stream>>>(g, c->d_tw64, c->d_FE64, twdf, FEdf, eyc, eyf, exc, exf, ncy, ncx);
     if (!step(cudaGetLastError(), "init kernels") || !step(cudaStreamSynchronize(c->stream), "init sync"))
-        return bail(CCST_E_CUDA);
+        return bail_work(CCST_E_CUDA);
+    cudaFree(d_work);
+    d_work = nullptr;
     // the attribute is per function: set it to the device limit so contexts of any size coexist
     if (!step(cudaFuncSetAttribute(track_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit),
               "smem attribute"))
@@ -356,10 +402,6 @@ static int launch(ccst_ctx* c, const Batch& b) {
     }
     track_kernel<<<grid, kThreads, c->smem, c->stream>>>(c->g, b);
     if (prof) CK(c, cudaEventRecordWithFlags(e1, c->stream, c->capturing ? cudaEventRecordExternal : 0));
-    if (c->g.guard) {
-        const int g2 = (int)(b.n < kL2Slots ? b.n : kL2Slots);
-        fp64_guard_kernel<<<g2, 256, 0, c->stream>>>(c->g, b, c->d_l2work);
-    }
     CK(c, cudaGetLastError());
     return CCST_OK;
 }
@@ -379,9 +421,11 @@ static int make_batch(ccst_ctx* c, const void* frames, int64_t n, int64_t pitch,
     b->n = n;
     b->pitch = pitch;
     b->out = (Result*)out;
-    b->guard = c->d_guard;
     b->dbg_int = nullptr;
     b->dbg_sub = nullptr;
+    b->dbg_pairs = nullptr;
+    b->dbg_d32 = nullptr;
+    b->dbg_d64 = nullptr;
     return CCST_OK;
 }
 
@@ -555,6 +599,26 @@ extern "C" int ccst_profile_reset(ccst_ctx* c) {
     if (rc) return rc;
     c->prof_used = 0;
     c->prof_next = 0;
+    return CCST_OK;
+}
+
+// Diagnostic entry (tests only): for frame f, v(jb) - v(ja) of the upsampled surface for the
+// grid pair pairs_dev[2f], pairs_dev[2f+1], by the FP32 pair-difference guard (d32) and by
+// FP64 accumulation over the FP32 spectrum (d64). Unnormalised units. Results only: no tracking.
+extern "C" int ccst_debug_pairs(ccst_ctx* c, const void* frames_dev, int64_t n, int64_t pitch_elems,
+                                const int32_t* pairs_dev, float* d32_dev, double* d64_dev) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!pairs_dev || !d32_dev || !d64_dev) return fail(c, CCST_E_INVALID, "null pair buffers");
+    Batch b;
+    if ((rc = make_batch(c, frames_dev, n, pitch_elems, (ccst_result*)c->d_out, &b))) return rc;
+    b.dbg_pairs = pairs_dev;
+    b.dbg_d32 = d32_dev;
+    b.dbg_d64 = d64_dev;
+    if (n == 0) return CCST_OK;
+    const int grid = (int)(n < c->grid_main ? n : c->grid_main);
+    track_kernel<<<grid, kThreads, c->smem, c->stream>>>(c->g, b);
+    CK(c, cudaGetLastError());
     return CCST_OK;
 }
 

@@ -10,6 +10,8 @@
 #include <math.h>
 #include <limits.h>
 
+#include "ccst_dfloat.cuh"
+
 namespace ccst {
 
 constexpr int kThreads = 512;            // threads per CTA of the tracking kernels
@@ -64,7 +66,7 @@ __device__ void fft_r2_passes(C* buf, int logN, int nseq, int seq_stride, int el
             const int i0 = ((k >> s) << (s + 1)) + pos;
             const int i1 = i0 + half;
             C w = tw[pos << twshift];
-            if (inverse) w.y = -w.y;
+            if (inverse) w = cconj(w);
             C* base = buf + (size_t)seq * seq_stride;
             const C a = base[(size_t)i0 * elem_stride];
             const C c = base[(size_t)i1 * elem_stride];

@@ -34,7 +34,8 @@
 // Near-ties of the FP32 sub-pixel surface are re-decided from exact pair
 // differences v(j) - v(j1) = Re sum_k w X'(k) [E(ty)E(tx) - E(ry)E(rx)], split
 // into terms with small factors (E(tx) - E(rx) = 2i sin(.) exp(i .)), and, if
-// still tied, by an FP64 re-evaluation in a second kernel.
+// still tied, by re-evaluating the tied candidates from a double-float product
+// spectrum (about 48 significant bits) computed in the same CTA.
 #pragma once
 
 #include "ccst_device.cuh"
@@ -62,6 +63,12 @@ struct Geom {
     const float* tB_wc;                 // [Wc][T1p]  w cos(2 pi kx' t/(uW))
     const float* tB_ws;                 // [Wc][T1p]  w sin(2 pi kx' t/(uW))
     const float* tB_gc;                 // [Wc][T1p]  w (cos(2 pi kx' t/(uW)) - 1)
+    // double-float data for the last guard level
+    const dfc* FEdf;                    // H x Wc   F[b]
+    const dfc* twdf;                    // Ntw/2    exp(-2 pi i k/Ntw)
+    const dfc* eyc; const dfc* eyf;     // exp(2 pi i n/(uH)) = eyc[n / By] * eyf[n % By]
+    const dfc* exc; const dfc* exf;     // exp(2 pi i n/(uW)) = exc[n / Bx] * exf[n % Bx]
+    int By, Bx;
 };
 
 struct Result {  // mirrors ccst_result
@@ -70,20 +77,16 @@ struct Result {  // mirrors ccst_result
     unsigned flags;
 };
 
-struct GuardRec {  // handed from the FP32 kernel to the FP64 re-evaluation
-    int n;               // number of candidates (0 = nothing to do)
-    int py, px;          // integer peak (wrapped)
-    int j[kMaxCandL2];   // candidate flat grid indices
-};
-
 struct Batch {
     const void* frames;
     long long n;
     long long pitch;     // row pitch in elements
     Result* out;
-    GuardRec* guard;     // n records
     float* dbg_int;      // optional: n x H x W integer surfaces (unnormalised), or null
     float* dbg_sub;      // optional: n x M x M delta surfaces (unnormalised), or null
+    const int* dbg_pairs;  // optional: n x 2 grid indices (ja, jb); then only the pair difference runs
+    float* dbg_d32;        // n: v(jb) - v(ja) by the FP32 pair-difference guard
+    double* dbg_d64;       // n: the same difference accumulated in FP64 from the FP32 spectrum
 };
 
 // --------------------------------------------------------------------- helpers
@@ -650,6 +653,166 @@ __device__ int pair_difference_guard(const Geom& g, const Smem& S, int nc, float
     return bj;
 }
 
+// v(jb) - v(ja) from the FP32 X' in shared memory, with FP64 twiddles and FP64
+// accumulation (the Nyquist-row rule included). Scratch: S.C.
+__device__ double pair_difference_f64(const Geom& g, const Smem& S, int ja, int jb, double* red) {
+    const int H = g.H, Wc = g.Wc;
+    double2* eyA = (double2*)S.C;
+    double2* eyB = eyA + H;
+    double2* exA = eyB + H;
+    double2* exB = exA + Wc;
+    const int tya = ja / g.M - g.h0, txa = ja % g.M - g.h0;
+    const int tyb = jb / g.M - g.h0, txb = jb % g.M - g.h0;
+    const long long Dy = (long long)g.u * H, Dx = (long long)g.u * g.W;
+    for (int k = threadIdx.x; k < H + Wc; k += blockDim.x) {
+        const bool isy = k < H;
+        const int kk = isy ? k : k - H;
+        const long long ks = isy ? signed_k(kk, H) : signed_k(kk, g.W);
+        const long long D = isy ? Dy : Dx;
+        long long na = (ks * (isy ? tya : txa)) % D, nb = (ks * (isy ? tyb : txb)) % D;
+        if (na < 0) na += D;
+        if (nb < 0) nb += D;
+        double sa, ca, sb, cb;
+        sincospi(2.0 * (double)na / (double)D, &sa, &ca);
+        sincospi(2.0 * (double)nb / (double)D, &sb, &cb);
+        if (isy) { eyA[kk] = make_double2(ca, sa); eyB[kk] = make_double2(cb, sb); }
+        else {
+            const double w = (kk == 0 || 2 * kk == g.W) ? 1.0 : 2.0;
+            exA[kk] = make_double2(w * ca, w * sa); exB[kk] = make_double2(w * cb, w * sb);
+        }
+    }
+    __syncthreads();
+    double acc = 0.0;
+    for (int idx = threadIdx.x; idx < H * Wc; idx += blockDim.x) {
+        const int ky = idx / Wc, kx = idx - ky * Wc;
+        const float2 xf = xprime(g, S, ky, kx);
+        const double2 x = make_double2(xf.x, xf.y);
+        double2 ea = eyA[ky], eb = eyB[ky];
+        if (ky == g.Hh && 2 * kx != g.W) { ea.y = 0.0; eb.y = 0.0; }
+        const double2 pa = cmul(ea, exA[kx]), pb = cmul(eb, exB[kx]);
+        acc += x.x * (pb.x - pa.x) - x.y * (pb.y - pa.y);
+    }
+    return block_sum(acc, red);
+}
+
+// ------------------------------------------- last guard level: double-float
+__device__ __forceinline__ dfc df_twiddle(const dfc* coarse, const dfc* fine, int B, long long n) {
+    return cmul(coarse[n / B], fine[n % B]);
+}
+
+__device__ df block_sum_df(df v, double* red) {
+    // double-float sum across the block; the 16 warp partials are combined in FP64 (few ops)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        df w = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = df_add(v, w);
+    }
+    const double d = df_to_double(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = d;
+    __syncthreads();
+    double r = 0.0;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int k = 0; k < nw; ++k) r += red[k];
+    __syncthreads();
+    return df_from_double(r);
+}
+
+// Re-evaluate the candidates S.cj[0..nc) from a double-float product spectrum
+// X = F[a] conj(F[b]): R2C FFT of the operand in double-float (S.A..S.B hold the
+// H x Wcp half spectrum, S.C the packed row chunks), then
+//   cu(j) = Re sum_{ky,kx} w X(ky,kx) E_y(ky, py u + ty) E_x(kx, px u + tx)
+// with exactly reduced angles. Returns the winner (sense-adjusted maximum,
+// lowest index on ties) and its unnormalised value in *val.
+__device__ int df_reevaluate(const Geom& g, const Smem& S, const void* frame, long long pitch,
+                             int py, int px, int nc, double* val) {
+    const int H = g.H, W = g.W, Wc = g.Wc, Wcp = g.Wcp, Hh = g.Hh;
+    dfc* Xd = (dfc*)S.A;                        // spans S.A and S.B
+    dfc* Zc = (dfc*)S.C;
+    const int cbytes = (int)((char*)S.tw - (char*)S.C);
+    int R = 1;
+    while (2 * R <= Hh && 2 * R * W * (int)sizeof(dfc) <= cbytes) R *= 2;
+    for (int r0 = 0; r0 < Hh; r0 += R) {
+        for (int idx = threadIdx.x; idx < 2 * R * W; idx += blockDim.x) {
+            const int yl = idx / W, x = idx - yl * W;
+            const int y = 2 * r0 + yl;
+            const float I = pixel_f32(frame, g.in_dtype, (long long)y * pitch + x);
+            df a = df_make(I);
+            if (g.method != 0) {
+                float s, e;
+                two_sum(I, g.eps, s, e);
+                const df ip = {s, e};
+                a = df_mul(ip, ip);
+            }
+            dfc* z = &Zc[(yl >> 1) * W + brev(x, g.logW)];
+            if (y & 1) z->im = a; else z->re = a;
+        }
+        __syncthreads();
+        fft_r2_passes(Zc, g.logW, R, W, 1, g.twdf, g.logNtw, false);
+        for (int idx = threadIdx.x; idx < R * Wcp; idx += blockDim.x) {
+            const int rl = idx / Wcp, kx = idx - rl * Wcp;
+            dfc fe = {{0.f, 0.f}, {0.f, 0.f}}, fo = fe;
+            if (kx < Wc) {
+                const dfc z = Zc[rl * W + kx];
+                const dfc zc = cconj(Zc[rl * W + ((W - kx) & (W - 1))]);
+                const dfc sp = cadd(z, zc), dm = csub(z, zc);
+                fe = {df_scale(sp.re, 0.5f), df_scale(sp.im, 0.5f)};
+                fo = {df_scale(dm.im, 0.5f), df_scale(df_neg(dm.re), 0.5f)};   // (z - zc) / (2i)
+            }
+            const int r = r0 + rl;
+            Xd[brev(2 * r, g.logH) * Wcp + kx] = fe;
+            Xd[brev(2 * r + 1, g.logH) * Wcp + kx] = fo;
+        }
+        __syncthreads();
+    }
+    fft_r2_passes(Xd, g.logH, Wc, 1, Wcp, g.twdf, g.logNtw, false);
+    for (int idx = threadIdx.x; idx < H * Wc; idx += blockDim.x) {
+        const int ky = idx / Wc, kx = idx - ky * Wc;
+        Xd[ky * Wcp + kx] = cmul(Xd[ky * Wcp + kx], cconj(g.FEdf[idx]));
+    }
+    __syncthreads();
+    dfc* Ey = Zc;            // H
+    dfc* Ex = Zc + H;        // Wc
+    const long long Dy = (long long)g.u * H, Dx = (long long)g.u * W;
+    double bestv = -INFINITY, bestraw = 0.0;
+    int bestj = INT_MAX;
+    for (int c = 0; c < nc; ++c) {
+        const int j = S.cj[c];
+        const int ty = j / g.M - g.h0, tx = j % g.M - g.h0;
+        for (int k = threadIdx.x; k < H + Wc; k += blockDim.x) {
+            if (k < H) {
+                long long n = ((long long)signed_k(k, H) * ((long long)py * g.u + ty)) % Dy;
+                if (n < 0) n += Dy;
+                Ey[k] = df_twiddle(g.eyc, g.eyf, g.By, n);
+            } else {
+                const int kx = k - H;
+                long long n = ((long long)signed_k(kx, W) * ((long long)px * g.u + tx)) % Dx;
+                if (n < 0) n += Dx;
+                dfc e = df_twiddle(g.exc, g.exf, g.Bx, n);
+                if (kx != 0 && 2 * kx != W) e = {df_scale(e.re, 2.f), df_scale(e.im, 2.f)};
+                Ex[kx] = e;
+            }
+        }
+        __syncthreads();
+        df acc = {0.f, 0.f};
+        for (int idx = threadIdx.x; idx < H * Wc; idx += blockDim.x) {
+            const int ky = idx / Wc, kx = idx - ky * Wc;
+            dfc ey = Ey[ky];
+            if (ky == Hh && 2 * kx != W) ey.im = {0.f, 0.f};   // real part of the Nyquist row's phase
+            const dfc e = cmul(ey, Ex[kx]);
+            const dfc x = Xd[ky * Wcp + kx];
+            acc = df_add(acc, df_sub(df_mul(x.re, e.re), df_mul(x.im, e.im)));
+        }
+        const double v = df_to_double(block_sum_df(acc, S.rd));
+        const double sv = (double)g.sense * v;
+        if (sv > bestv || (sv == bestv && j < bestj)) { bestv = sv; bestj = j; bestraw = v; }
+        __syncthreads();
+    }
+    *val = bestraw;
+    return bestj;
+}
+
 // ---------------------------------------------------------- the FP32 kernel
 __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -667,6 +830,21 @@ __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
         const int py = wrap_shift(ip >> g.logW, g.H), px = wrap_shift(ip & (g.W - 1), g.W);
         __syncthreads();
         build_pq_and_g(g, S, py, px);
+        if (b.dbg_pairs) {
+            const int ja = b.dbg_pairs[2 * f], jb = b.dbg_pairs[2 * f + 1];
+            const double d64 = pair_difference_f64(g, S, ja, jb, S.rd);
+            if (threadIdx.x == 0) { S.cj[0] = ja; S.cj[1] = jb; }
+            __syncthreads();
+            int nl2dummy = 0;
+            float dw = 0.f;
+            pair_difference_guard(g, S, 2, 0.f, &nl2dummy, &dw);
+            if (threadIdx.x == 0) {
+                b.dbg_d32[f] = g.sense * S.cv[1];
+                b.dbg_d64[f] = d64;
+            }
+            __syncthreads();
+            continue;
+        }
         TopK<kTopK> top;
         top.init();
         float* dbg = b.dbg_sub ? b.dbg_sub + (size_t)f * g.M * g.M : nullptr;
@@ -712,25 +890,25 @@ __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
             }
         }
         __syncthreads();
+        // raw value at the winner: c(p) + sense * (v(j1) + D(winner))
+        float peak = (c0 + ((flags & 0x10u) ? 0.f : g.sense * (vw + dwin))) / (float)(g.H * g.W);
+        if (nl2 > 0) {
+            double raw = 0.0;
+            jw = df_reevaluate(g, S, frame, b.pitch, py, px, nl2, &raw);
+            peak = (float)(raw / ((double)g.H * g.W));
+            flags |= 0x04u;
+        }
         if (threadIdx.x == 0) {
             const int jy = jw / g.M, jx = jw % g.M;
             const int ty = jy - g.h0, tx = jx - g.h0;
             Result r;
             r.dy = (float)(((double)py * g.u + ty) / g.u);
             r.dx = (float)(((double)px * g.u + tx) / g.u);
-            // raw delta value at the winner: sense * (v(j1) + D(winner))
-            const float vrel = (flags & 0x10u) ? 0.f : g.sense * (vw + dwin);
-            r.peak = (c0 + vrel) / (float)(g.H * g.W);
+            r.peak = peak;
             r.ipy = py;
             r.ipx = px;
-            if (nl2 > 0) flags |= 0x04u;
             r.flags = flags;
             b.out[f] = r;
-            GuardRec* gr = b.guard + f;
-            gr->n = nl2;
-            gr->py = py;
-            gr->px = px;
-            for (int k = 0; k < nl2; ++k) gr->j[k] = S.cj[k];
         }
         __syncthreads();
     }
@@ -776,79 +954,6 @@ __device__ void fft_r2c_f64_global(const Geom& g, const double* a_or_null, const
     __syncthreads();
     fft_r2_passes(Xh, g.logH, Wc, 1, Wcp, g.tw64, g.logNtw, false);
     (void)red;
-}
-
-constexpr int kMaxSide = 128;
-
-__global__ void __launch_bounds__(256) fp64_guard_kernel(Geom g, Batch b, double2* work) {
-    __shared__ double red[32];
-    __shared__ double2 ey[kMaxSide];
-    __shared__ double2 ex[kMaxSide / 2 + 2];
-    const size_t per = (size_t)(g.H / 2) * g.W + (size_t)g.H * g.Wcp;
-    double2* Z = work + per * blockIdx.x;
-    double2* Xh = Z + (size_t)(g.H / 2) * g.W;
-    const size_t elem = g.in_dtype == 0 ? 2 : 4;
-    const long long Dy = (long long)g.u * g.H, Dx = (long long)g.u * g.W;
-    for (long long f = blockIdx.x; f < b.n; f += gridDim.x) {
-        const GuardRec* gr = b.guard + f;
-        const int nc = gr->n;
-        if (nc <= 0) continue;
-        const char* frame = (const char*)b.frames + (size_t)f * g.H * b.pitch * elem;
-        fft_r2c_f64_global(g, nullptr, frame, b.pitch, Z, Xh, red);
-        // X = F[a] conj(F[b]) in place
-        for (int idx = threadIdx.x; idx < g.H * g.Wc; idx += blockDim.x) {
-            const int ky = idx / g.Wc, kx = idx - ky * g.Wc;
-            Xh[ky * g.Wcp + kx] = cmul(Xh[ky * g.Wcp + kx], cconj(g.FE64[idx]));
-        }
-        __syncthreads();
-        const int py = gr->py, px = gr->px;
-        double bestv = -INFINITY, bestraw = 0.0;
-        int bestj = INT_MAX;
-        for (int c = 0; c < nc; ++c) {
-            const int j = gr->j[c];
-            const int ty = j / g.M - g.h0, tx = j % g.M - g.h0;
-            // separable twiddles, angles reduced exactly in integers
-            for (int ky = threadIdx.x; ky < g.H; ky += blockDim.x) {
-                long long n = ((long long)signed_k(ky, g.H) * ((long long)py * g.u + ty)) % Dy;
-                if (n < 0) n += Dy;
-                double s, co;
-                sincospi(2.0 * (double)n / (double)Dy, &s, &co);
-                ey[ky] = make_double2(co, s);
-            }
-            for (int kx = threadIdx.x; kx < g.Wc; kx += blockDim.x) {
-                long long n = ((long long)signed_k(kx, g.W) * ((long long)px * g.u + tx)) % Dx;
-                if (n < 0) n += Dx;
-                double s, co;
-                sincospi(2.0 * (double)n / (double)Dx, &s, &co);
-                const double w = (kx == 0 || 2 * kx == g.W) ? 1.0 : 2.0;
-                ex[kx] = make_double2(w * co, w * s);
-            }
-            __syncthreads();
-            double acc = 0.0;
-            for (int idx = threadIdx.x; idx < g.H * g.Wc; idx += blockDim.x) {
-                const int ky = idx / g.Wc, kx = idx - ky * g.Wc;
-                // the Nyquist row enters through the real part of its y-phase, except in
-                // the x-Nyquist column (real part of the full signed-frequency sum)
-                const double2 eyk = (ky == g.Hh && 2 * kx != g.W) ? make_double2(ey[ky].x, 0.0) : ey[ky];
-                const double2 e = cmul(eyk, ex[kx]);
-                const double2 x = Xh[ky * g.Wcp + kx];
-                acc = fma(x.x, e.x, fma(-x.y, e.y, acc));
-            }
-            const double v = block_sum(acc, red);
-            const double sv = (double)g.sense * v;
-            if (sv > bestv || (sv == bestv && j < bestj)) { bestv = sv; bestj = j; bestraw = v; }
-        }
-        if (threadIdx.x == 0) {
-            const int ty = bestj / g.M - g.h0, tx = bestj % g.M - g.h0;
-            Result r = b.out[f];
-            r.dy = (float)(((double)py * g.u + ty) / g.u);
-            r.dx = (float)(((double)px * g.u + tx) / g.u);
-            r.peak = (float)(bestraw / ((double)g.H * g.W));
-            r.flags |= 0x04u;
-            b.out[f] = r;
-        }
-        __syncthreads();
-    }
 }
 
 }  // namespace ccst

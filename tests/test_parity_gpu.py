@@ -91,7 +91,7 @@ def compare(res, orc, label=""):
 def flag_counts(res):
     f = res["flags"]
     return {name: int(np.sum((f & bit) != 0)) for name, bit in
-            (("int", C.R_INT_GUARD), ("sub", C.R_SUB_GUARD), ("fp64", C.R_FP64), ("overflow", C.R_OVERFLOW))}
+            (("int", C.R_INT_GUARD), ("sub", C.R_SUB_GUARD), ("df64", C.R_DF64), ("overflow", C.R_OVERFLOW))}
 
 
 # ------------------------------------------------------------------ single pair
@@ -167,7 +167,7 @@ def test_frame_stream_full_size_sampled(torch):
     orc = oracle.track_batch_parallel(s.frames[idx], s.ref, u=100)
     compare(res[idx], orc, "stream sample")
     # every frame the guard had to re-decide is checked too
-    gidx = np.nonzero(res["flags"] & (C.R_SUB_GUARD | C.R_FP64 | C.R_INT_GUARD))[0][:200]
+    gidx = np.nonzero(res["flags"] & (C.R_SUB_GUARD | C.R_DF64 | C.R_INT_GUARD))[0][:200]
     if len(gidx):
         compare(res[gidx], oracle.track_batch_parallel(s.frames[gidx], s.ref, u=100), "guarded frames")
     print("flags over 10000 frames", flag_counts(res))
@@ -322,3 +322,47 @@ def test_edge_cases(torch):
     f[:, :10, :] = 0
     compare(run_gpu(torch, s.ref, f, method=oracle.CC_SN), oracle.track_batch(f, s.ref, method=oracle.CC_SN),
             "zeros cc-sn")
+
+
+def test_pair_difference_error_is_far_below_tau1(torch):
+    """Calibrates the middle guard level: the FP32 pair difference v(jb) - v(ja) between the
+    winner and its neighbours, against the oracle's exact FP64 difference. Also reports the
+    error left by the FP32 product spectrum alone (FP64 accumulation over it)."""
+    s = synth.frame_stream(seed=7, n=64)
+    frames = s.frames
+    res = run_gpu(torch, s.ref, frames, u=100)
+    M, h0, u = 150, 75, 100
+    n = len(frames)
+    eps32 = 2.0 ** -23
+    worst32 = worst64 = 0.0
+    dev = torch.from_numpy(frames.view(np.int16)).cuda().view(torch.uint16)
+    t = C.Tracker(s.ref, upsample=u, max_batch=n)
+    cus, scales = [], []
+    for f in range(n):
+        a, b, _ = oracle.surface_operands(frames[f], s.ref)
+        X = oracle.product_spectrum(a, b)
+        cus.append(oracle.upsampled_cc(X, int(res["ipy"][f]), int(res["ipx"][f]), u) * 128 * 128)
+        scales.append(float(np.sum(np.abs(X.real) + np.abs(X.imag))))
+    for dy, dx in [(0, 1), (1, 0), (1, 1), (0, -1), (-1, 0), (-1, 1), (2, 0), (0, 3)]:
+        pairs = np.zeros((n, 2), np.int32)
+        for f in range(n):
+            jy = int(round(float(res["dy"][f]) * u)) - int(res["ipy"][f]) * u + h0
+            jx = int(round(float(res["dx"][f]) * u)) - int(res["ipx"][f]) * u + h0
+            jby, jbx = min(max(jy + dy, 0), M - 1), min(max(jx + dx, 0), M - 1)
+            pairs[f] = (jy * M + jx, jby * M + jbx)
+        pd = torch.from_numpy(pairs).cuda()
+        d32 = torch.empty(n, dtype=torch.float32, device="cuda")
+        d64 = torch.empty(n, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        C.ccst_debug_pairs(t.ctx, dev, n, 0, pd, d32, d64)
+        C.ccst_sync(t.ctx)
+        d32, d64 = d32.cpu().numpy(), d64.cpu().numpy()
+        for f in range(n):
+            cu = cus[f].ravel()
+            exact = cu[pairs[f, 1]] - cu[pairs[f, 0]]
+            worst32 = max(worst32, abs(d32[f] - exact) / scales[f])
+            worst64 = max(worst64, abs(d64[f] - exact) / scales[f])
+    t.close()
+    print(f"pair-difference error / (eps32 sum|X|): FP32 guard {worst32 / eps32:.3g}, "
+          f"FP64 over the FP32 spectrum {worst64 / eps32:.3g}")
+    assert worst32 < 0.05 * eps32 / 8          # tau1 = 0.05 eps32 with an 8x margin
