@@ -195,6 +195,52 @@ int ccst_grid_size(ccst_ctx* ctx);
 int ccst_debug_surfaces(ccst_ctx* ctx, const void* frames_dev, int64_t n, int64_t pitch_elems,
                         ccst_result* out_dev, float* int_surf_dev, float* sub_surf_dev);
 
+/* Allocation-free tracking, for callers that must not allocate device memory
+ * while they run.
+ *
+ * No counterpart in the paper: this is a deployment form of ccst_create +
+ * ccst_track. Typical callers are a real-time camera or feedback loop that
+ * reserves all GPU memory when it starts and cannot afford a cudaMalloc later
+ * (it may synchronise the device and has no time bound), or a plug-in inside a
+ * host program that owns the device's memory pool.
+ *
+ * It computes the same results as ccst_create(ref, H, W, p) followed by
+ * ccst_track(frames, n, pitch, out). Everything the context would own
+ * (reference spectra, upsampling tables, twiddles, the FP64 FFT workspace) is
+ * rebuilt on each call inside one file-scope device array of 2 MiB per device.
+ *
+ * Arguments:
+ *   ref_dev     H*W float32 reference, device memory.
+ *   p           parameters; p->max_batch and CCST_FLAG_GRAPHS / CCST_FLAG_PROFILE
+ *               are ignored. NULL means the defaults.
+ *   frames_dev  device memory, laid out as for ccst_track.
+ *   out_dev     n ccst_result records, device memory.
+ *   n           any count >= 0.
+ * The work is enqueued on p->stream and the call returns without waiting.
+ *
+ * Limits: H, W powers of two in [8, 128]. The scratch of the requested H, W and
+ * upsample must fit in the 2 MiB array (128 x 128 fits up to upsample ~1000);
+ * larger requests return CCST_E_SHAPE.
+ *
+ * Rules:
+ *   - The first call on each device resolves the array's device address and sets
+ *     the kernel's shared-memory limit. Make that first call before any stream
+ *     capture.
+ *   - Every call on a device shares the one array, which keeps the last call's
+ *     contents; each call rewrites all of it before use. Calls whose GPU work
+ *     overlaps (different streams, or different host threads) race on it and
+ *     must be serialised by the caller.
+ *   - No cudaMalloc, cudaFree or other allocating call is made, on the device or
+ *     the host.
+ * Errors: CCST_E_INVALID, CCST_E_SHAPE, CCST_E_UNSUPPORTED, CCST_E_CUDA; the message
+ * is in ccst_static_last_error(). */
+int ccst_track_static(const float* ref_dev, int H, int W, const ccst_params* p,
+                      const void* frames_dev, int64_t n, int64_t pitch_elems,
+                      ccst_result* out_dev);
+
+/* Message of the last failed ccst_track_static call in this process. Never NULL. */
+const char* ccst_static_last_error(void);
+
 /* Diagnostic entry, for tests that calibrate the tie guard.
  * For frame f it computes v(jb) - v(ja) of the upsampled surface (Sec. III),
  * unnormalised and relative to the frame's integer peak, for the flat grid

@@ -9,7 +9,8 @@ _BINDING = ("CC_SN", "CC_U", "Tracker", "CcstError", "RESULT_DTYPE", "decode", "
             "ccst_version", "ccst_default_params", "ccst_create", "ccst_track", "ccst_track_host",
             "ccst_set_stream", "ccst_sync", "ccst_submit", "ccst_poll", "ccst_backward",
             "ccst_destroy", "ccst_grid_size", "ccst_debug_surfaces", "ccst_profile_kernel_ms",
-            "ccst_profile_reset", "ccst_debug_pairs")
+            "ccst_profile_reset", "ccst_debug_pairs",
+            "ccst_track_static")
 
 
 def __getattr__(name):

@@ -79,6 +79,9 @@ _SIGS = [
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("ccst_debug_pairs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("ccst_track_static", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ccst_params),
+                                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]),
+    ("ccst_static_last_error", ctypes.c_char_p, []),
 ]
 
 
@@ -206,6 +209,16 @@ def ccst_debug_surfaces(ctx, frames_dev, n, pitch_elems, out_dev, int_surf_dev, 
 def ccst_debug_pairs(ctx, frames_dev, n, pitch_elems, pairs_dev, d32_dev, d64_dev) -> None:
     _check(lib().ccst_debug_pairs(ctx, _ptr(frames_dev), int(n), int(pitch_elems), _ptr(pairs_dev),
                                   _ptr(d32_dev), _ptr(d64_dev)), ctx)
+
+
+def ccst_track_static(ref_dev, H: int, W: int, params: ccst_params | None, frames_dev, n: int,
+                      pitch_elems: int, out_dev) -> None:
+    """Allocation-free tracking: no context, all workspace in the library's fixed device array."""
+    p = ctypes.byref(params) if params is not None else None
+    rc = lib().ccst_track_static(_ptr(ref_dev), int(H), int(W), p, _ptr(frames_dev), int(n), int(pitch_elems),
+                                 _ptr(out_dev))
+    if rc != OK:
+        raise CcstError(rc, lib().ccst_static_last_error().decode())
 
 
 # ---------------------------------------------------------------- convenience wrapper

@@ -624,3 +624,174 @@ extern "C" int ccst_debug_pairs(ccst_ctx* c, const void* frames_dev, int64_t n, 
 
 // Grid size M of the refinement square for this context (tests and bindings).
 extern "C" int ccst_grid_size(ccst_ctx* c) { return c ? c->g.M : CCST_E_INVALID; }
+
+// ------------------------------------------------------------------------------------
+// Allocation-free tracking (ccst_track_static).
+//
+// For callers that are not allowed to allocate device memory at run time: for
+// instance a camera/feedback loop that reserves all GPU memory when it starts and
+// must never stall on cudaMalloc (which can synchronise the device), or a plug-in
+// inside a host program that owns the device memory pool. Everything ccst_create
+// would allocate (reference spectra, upsampling tables, FFT twiddles and the FP64
+// FFT workspace used to build the reference spectrum) lives instead in one
+// file-scope device array of fixed size, shared by every call in the process.
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)2 << 20;   // 2 MiB per device
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+struct StaticDevice {
+    bool ready = false;
+    unsigned char* scratch = nullptr;   // device address of g_static_scratch on this device
+    size_t smem_limit = 0;
+    int sms = 0;
+};
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+StaticDevice g_static_dev[kStaticMaxDevices];
+char g_static_err[256] = "no error";
+
+int static_fail(int code, const char* msg, const char* detail = "") {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    snprintf(g_static_err, sizeof(g_static_err), "%s%s", msg, detail);
+    return code;
+}
+
+// Once per device, with that device current: resolve the array's device address
+// (the host-side symbol is only a stand-in) and raise the kernel's shared-memory limit.
+int static_setup(int dev, StaticDevice* out) {
+    if (dev < 0 || dev >= kStaticMaxDevices) return static_fail(CCST_E_UNSUPPORTED, "ccst_track_static: device ordinal >= 64");
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    StaticDevice& d = g_static_dev[dev];
+    if (!d.ready) {
+        cudaError_t e = cudaGetSymbolAddress((void**)&d.scratch, g_static_scratch);
+        if (e != cudaSuccess) {
+            snprintf(g_static_err, sizeof(g_static_err), "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+            return CCST_E_CUDA;
+        }
+        cudaDeviceProp prop;
+        if ((e = cudaGetDeviceProperties(&prop, dev)) != cudaSuccess) {
+            snprintf(g_static_err, sizeof(g_static_err), "cudaGetDeviceProperties: %s", cudaGetErrorString(e));
+            return CCST_E_CUDA;
+        }
+        d.smem_limit = prop.sharedMemPerBlockOptin;
+        d.sms = prop.multiProcessorCount;
+        if ((e = cudaFuncSetAttribute(track_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)d.smem_limit)) != cudaSuccess) {
+            snprintf(g_static_err, sizeof(g_static_err), "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+            return CCST_E_CUDA;
+        }
+        d.ready = true;
+    }
+    *out = d;
+    return CCST_OK;
+}
+
+}  // namespace
+
+extern "C" int ccst_track_static(const float* ref_dev, int H, int W, const ccst_params* pin,
+                                 const void* frames_dev, int64_t n, int64_t pitch_elems,
+                                 ccst_result* out_dev) {
+    ccst_params p;
+    if (pin) p = *pin; else ccst_default_params(&p);
+    if (!ref_dev) return static_fail(CCST_E_INVALID, "ccst_track_static: null reference");
+    if (n < 0) return static_fail(CCST_E_INVALID, "ccst_track_static: n < 0");
+    if (n > 0 && (!frames_dev || !out_dev)) return static_fail(CCST_E_INVALID, "ccst_track_static: null frames or out");
+    if (!is_pow2(H) || !is_pow2(W) || H < 8 || W < 8 || H > 128 || W > 128)
+        return static_fail(CCST_E_SHAPE, "ccst_track_static: H and W must be powers of two in [8, 128]");
+    if (p.upsample < 1 || p.upsample > 16384)
+        return static_fail(CCST_E_INVALID, "ccst_track_static: upsample must be in [1, 16384]");
+    if (p.method != CCST_CC_U && p.method != CCST_CC_SN)
+        return static_fail(CCST_E_INVALID, "ccst_track_static: unknown method");
+    if (p.in_dtype != CCST_U16 && p.in_dtype != CCST_F32)
+        return static_fail(CCST_E_INVALID, "ccst_track_static: unknown in_dtype");
+    if (pitch_elems == 0) pitch_elems = W;
+    if (pitch_elems < W) return static_fail(CCST_E_INVALID, "ccst_track_static: pitch_elems < W");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return static_fail(CCST_E_CUDA, "cudaGetDevice: ", cudaGetErrorString(e));
+    StaticDevice sd;
+    int rc = static_setup(dev, &sd);
+    if (rc) return rc;
+    cudaStream_t stream = (cudaStream_t)p.stream;
+
+    // geometry: the same choices ccst_create makes
+    Geom g{};
+    g.H = H; g.W = W; g.logH = ilog2(H); g.logW = ilog2(W); g.Hh = H / 2;
+    g.Wc = W / 2 + 1; g.Wcp = (g.Wc + 1) & ~1;
+    g.u = p.upsample; g.M = (3 * p.upsample + 1) / 2; g.h0 = g.M / 2; g.pmax = g.M - 1 - g.h0;
+    g.T1p = (g.h0 + 1 + 3) & ~3;
+    g.Ntw = H > W ? H : W; g.logNtw = ilog2(g.Ntw);
+    g.method = p.method; g.in_dtype = p.in_dtype; g.eps = p.eps;
+    g.sense = p.method == CCST_CC_U ? 1.f : -1.f;
+    g.tau_int = kTauInt; g.tau0 = kTau0; g.tau1 = kTau1;
+    g.guard = (p.flags & CCST_FLAG_TIE_GUARD) ? 1 : 0;
+    const long long Dy = (long long)g.u * H, Dx = (long long)g.u * W;
+    g.By = 1; while ((long long)g.By * g.By < Dy) ++g.By;
+    g.Bx = 1; while ((long long)g.Bx * g.Bx < Dx) ++g.Bx;
+    const int ncy = (int)((Dy + g.By - 1) / g.By), ncx = (int)((Dx + g.Bx - 1) / g.Bx);
+
+    // carve the static array (256-byte aligned regions)
+    const size_t HW = (size_t)H * W, HWc = (size_t)H * g.Wc;
+    const size_t tabA = (size_t)g.Hh * g.T1p, tabB = (size_t)g.Wc * g.T1p;
+    const size_t ndf = (size_t)(g.Ntw / 2) + HWc + ncy + g.By + ncx + g.Bx;
+    const size_t work = (size_t)(H / 2) * W + (size_t)H * g.Wcp;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return sd.scratch + o; };
+    double* b64 = (double*)take(HW * sizeof(double));
+    double2* FE64 = (double2*)take(HWc * sizeof(double2));
+    float2* FE32 = (float2*)take(HWc * sizeof(float2));
+    double2* tw64 = (double2*)take((size_t)(g.Ntw / 2) * sizeof(double2));
+    float2* tw32 = (float2*)take((size_t)(g.Ntw / 2) * sizeof(float2));
+    float* tab = (float*)take((2 * tabA + 3 * tabB) * sizeof(float));
+    dfc* dfb = (dfc*)take(ndf * sizeof(dfc));
+    double2* wk = (double2*)take(work * sizeof(double2));
+    if (off > kStaticScratchBytes)
+        return static_fail(CCST_E_SHAPE, "ccst_track_static: this H, W and upsample need more scratch than "
+                                         "the 2 MiB static array holds (lower upsample)");
+    g.TC = g.T1p;
+    for (;;) {
+        g.nchunk = (g.h0 + 1 + g.TC - 1) / g.TC;
+        if (smem_bytes(g) <= sd.smem_limit || g.TC <= 4) break;
+        g.TC -= 4;
+    }
+    const size_t smem = smem_bytes(g);
+    if (smem > sd.smem_limit) return static_fail(CCST_E_SHAPE, "ccst_track_static: frame too large for shared memory");
+    g.FE32 = FE32; g.FE64 = FE64; g.b64 = b64; g.tw32 = tw32; g.tw64 = tw64;
+    g.tA_cm1 = tab; g.tA_s = tab + tabA; g.tB_wc = tab + 2 * tabA; g.tB_ws = g.tB_wc + tabB; g.tB_gc = g.tB_ws + tabB;
+    dfc* twdf = dfb;
+    dfc* FEdf = twdf + g.Ntw / 2;
+    dfc* eyc = FEdf + HWc;
+    dfc* eyf = eyc + ncy;
+    dfc* exc = eyf + g.By;
+    dfc* exf = exc + ncx;
+    g.twdf = twdf; g.FEdf = FEdf; g.eyc = eyc; g.eyf = eyf; g.exc = exc; g.exf = exf;
+
+    // every region is rewritten in full below before anything reads it
+    init_twiddles<<<1, 256, 0, stream>>>(g.Ntw, tw64, tw32);
+    init_tables<<<64, 256, 0, stream>>>(g, tab, tab + tabA, tab + 2 * tabA, tab + 2 * tabA + tabB,
+                                        tab + 2 * tabA + 2 * tabB);
+    init_ref_operand<<<32, 256, 0, stream>>>(g, ref_dev, b64);
+    init_ref_spectrum<<<1, 256, 0, stream>>>(g, wk, FE64, FE32);
+    init_dfloat<<<32, 256, 0, stream>>>(g, tw64, FE64, twdf, FEdf, eyc, eyf, exc, exf, ncy, ncx);
+    if (n > 0) {
+        Batch b{};
+        b.frames = frames_dev;
+        b.n = n;
+        b.pitch = pitch_elems;
+        b.out = (Result*)out_dev;
+        int occ = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, track_kernel, kThreads, smem);
+        const long long cap = (long long)sd.sms * (occ > 0 ? occ : 1);
+        const int grid = (int)(n < cap ? n : cap);
+        track_kernel<<<grid, kThreads, smem, stream>>>(g, b);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return static_fail(CCST_E_CUDA, "ccst_track_static launch: ", cudaGetErrorString(e));
+    return CCST_OK;
+}
+
+extern "C" const char* ccst_static_last_error(void) {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    return g_static_err;
+}
