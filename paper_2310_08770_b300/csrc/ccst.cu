@@ -47,22 +47,24 @@ __global__ void init_twiddles(int Ntw, double2* tw64, float2* tw32) {
     }
 }
 
-__global__ void init_tables(Geom g, float* cm1, float* sA, float* wc, float* ws, float* gc) {
+__global__ void init_tables(Geom g, float* cm1, float* sA, float* wc, float* ws, float* gc, float4* tA2) {
     const long long Dy = (long long)g.u * g.H, Dx = (long long)g.u * g.W;
-    const int nA = g.Hh * g.T1p, nB = g.Wc * g.T1p;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nA + nB; i += gridDim.x * blockDim.x) {
+    const int nA = g.Hh * g.T1p, nB = g.Wc * g.T1p, nA2 = g.TAB * (g.Hh / 2);
+    auto cm1_s = [&](int m, int t, float* c1, float* s1) {
+        *c1 = 0.f;
+        *s1 = 0.f;
+        if (t >= 0 && t <= g.h0) {
+            const long long r = ((long long)m * t) % Dy;     // angle 2 pi r / (uH)
+            const double h = sinpi((double)r / (double)Dy);
+            *c1 = (float)(-2.0 * h * h);                     // cos - 1 without cancellation
+            *s1 = (float)sinpi(2.0 * (double)r / (double)Dy);
+        }
+    };
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nA + nB + nA2; i += gridDim.x * blockDim.x) {
         if (i < nA) {
             const int m = i / g.T1p + 1, t = i % g.T1p;
-            float c1 = 0.f, s1 = 0.f;
-            if (t <= g.h0) {
-                const long long r = ((long long)m * t) % Dy;     // angle 2 pi r / (uH)
-                const double h = sinpi((double)r / (double)Dy);
-                c1 = (float)(-2.0 * h * h);                       // cos - 1 without cancellation
-                s1 = (float)sinpi(2.0 * (double)r / (double)Dy);
-            }
-            cm1[i] = c1;
-            sA[i] = s1;
-        } else {
+            cm1_s(m, t, &cm1[i], &sA[i]);
+        } else if (i < nA + nB) {
             const int k = i - nA;
             const int kx = k / g.T1p, t = k % g.T1p;
             const int kxs = (kx < g.W / 2) ? kx : kx - g.W;      // W/2 -> -W/2
@@ -81,6 +83,14 @@ __global__ void init_tables(Geom g, float* cm1, float* sA, float* wc, float* ws,
             wc[k] = a;
             ws[k] = b;
             gc[k] = c;
+        } else {
+            // [t - 1][q]: (cm1, s) of m = 2q+1 and m = 2q+2 at t = 1..TAB (zero beyond h0)
+            const int k = i - nA - nB;
+            const int t = k / (g.Hh / 2) + 1, q = k % (g.Hh / 2);
+            float a, b, c, d;
+            cm1_s(2 * q + 1, t, &a, &b);
+            cm1_s(2 * q + 2, t, &c, &d);
+            tA2[k] = make_float4(a, b, c, d);
         }
     }
 }
@@ -140,6 +150,37 @@ __global__ void __launch_bounds__(256) init_ref_spectrum(Geom g, double2* work, 
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 int ilog2(int x) { int l = 0; while ((1 << l) < x) ++l; return l; }
 
+// Sizes, layout choices and the shared-memory plan for H x W frames and params p.
+// Returns false if no plan fits in smem_limit bytes.
+bool plan_geometry(int H, int W, const ccst_params& p, size_t smem_limit, Geom* out) {
+    Geom g{};
+    g.H = H; g.W = W; g.logH = ilog2(H); g.logW = ilog2(W); g.Hh = H / 2;
+    g.Wc = W / 2 + 1; g.Wcp = (g.Wc + 1) & ~1;
+    g.SA = W / 2;
+    const int pg = split_n2(W) > 1 ? split_n2(W) : W;   // padding group of the packed rows
+    const int len = W + W / pg;
+    g.SZ = ((len + 7) / 16) * 16 + 8;                    // >= len and = 8 (mod 16): conflict-free passes
+    if (g.SZ < len) g.SZ += 16;
+    g.u = p.upsample; g.M = (3 * p.upsample + 1) / 2; g.h0 = g.M / 2; g.pmax = g.M - 1 - g.h0;
+    g.T1p = (g.h0 + 1 + 3) & ~3;
+    g.Ntw = H > W ? H : W; g.logNtw = ilog2(g.Ntw);
+    g.method = p.method; g.in_dtype = p.in_dtype; g.eps = p.eps;
+    g.sense = p.method == CCST_CC_U ? 1.f : -1.f;
+    g.tau_int = kTauInt; g.tau0 = kTau0; g.tau1 = kTau1;
+    g.guard = (p.flags & CCST_FLAG_TIE_GUARD) ? 1 : 0;
+    const int h15 = ((g.h0 + 14) / 15) * 15;
+    for (int smem_tables = 1; smem_tables >= 0; --smem_tables) {
+        for (int tc = h15; tc >= 15; tc -= 15) {
+            g.TC = tc;
+            g.nchunk = (g.h0 + tc - 1) / tc;
+            g.TAB = g.nchunk * tc;
+            g.tables_smem = smem_tables;
+            if (smem_plan(g).total <= smem_limit) { *out = g; return true; }
+        }
+    }
+    return false;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- context
@@ -150,6 +191,7 @@ struct ccst_ctx {
     int device = 0;
     int grid_main = 1;
     size_t smem = 0;
+    const void* kernel = nullptr;      // track_kernel<H, W>
     bool dead = false;
     std::string err = "no error";
     // device allocations
@@ -262,16 +304,6 @@ extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pi
     c->p = p;
     c->stream = (cudaStream_t)p.stream;
     Geom& g = c->g;
-    g.H = H; g.W = W; g.logH = ilog2(H); g.logW = ilog2(W); g.Hh = H / 2;
-    g.Wc = W / 2 + 1; g.Wcp = (g.Wc + 1) & ~1;
-    g.u = p.upsample; g.M = (3 * p.upsample + 1) / 2; g.h0 = g.M / 2; g.pmax = g.M - 1 - g.h0;
-    g.T1p = (g.h0 + 1 + 3) & ~3;
-    g.Ntw = H > W ? H : W; g.logNtw = ilog2(g.Ntw);
-    g.method = p.method; g.in_dtype = p.in_dtype; g.eps = p.eps;
-    g.sense = p.method == CCST_CC_U ? 1.f : -1.f;
-    g.tau_int = kTauInt; g.tau0 = kTau0; g.tau1 = kTau1;
-    g.guard = (p.flags & CCST_FLAG_TIE_GUARD) ? 1 : 0;
-
     auto bail = [&](int code) { free_all(c); delete c; return code; };
     cudaError_t e;
     int dev = 0;
@@ -285,22 +317,16 @@ extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pi
         fail(nullptr, CCST_E_CUDA, std::string("cudaGetDeviceProperties: ") + cudaGetErrorString(e));
         return bail(CCST_E_CUDA);
     }
-    // stage-A chunk: as many t rows as fit next to the FFT buffers
     const size_t limit = prop.sharedMemPerBlockOptin;
-    g.TC = g.T1p;
-    for (;;) {
-        g.nchunk = (g.h0 + 1 + g.TC - 1) / g.TC;
-        if (smem_bytes(g) <= limit || g.TC <= 4) break;
-        g.TC -= 4;
-    }
-    c->smem = smem_bytes(g);
-    if (c->smem > limit) {
+    if (!plan_geometry(H, W, p, limit, &g)) {
         fail(nullptr, CCST_E_SHAPE, "ccst_create: frame too large for shared memory");
         return bail(CCST_E_SHAPE);
     }
+    c->smem = smem_plan(g).total;
 
     const size_t HW = (size_t)H * W, HWc = (size_t)H * g.Wc;
     const size_t tabA = (size_t)g.Hh * g.T1p, tabB = (size_t)g.Wc * g.T1p;
+    const size_t tabA2 = (size_t)g.TAB * (g.Hh / 2);                  // float4
     const size_t l2per = (size_t)(H / 2) * W + (size_t)H * g.Wcp;   // FP64 FFT workspace at create
     const size_t elem = p.in_dtype == CCST_U16 ? 2 : 4;
     const long long Dy = (long long)g.u * H, Dx = (long long)g.u * W;
@@ -316,7 +342,7 @@ extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pi
         {(void**)&c->d_FE32, HWc * sizeof(float2)},
         {(void**)&c->d_tw64, (size_t)(g.Ntw / 2) * sizeof(double2)},
         {(void**)&c->d_tw32, (size_t)(g.Ntw / 2) * sizeof(float2)},
-        {(void**)&c->d_tab, (2 * tabA + 3 * tabB) * sizeof(float)},
+        {(void**)&c->d_tab, (2 * tabA + 3 * tabB + 4 * tabA2) * sizeof(float)},
         {(void**)&c->d_df, ndf * sizeof(dfc)},
         {(void**)&d_work, l2per * sizeof(double2)},
         {(void**)&c->d_frames, (size_t)p.max_batch * HW * elem},
@@ -332,6 +358,7 @@ extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pi
     g.FE32 = c->d_FE32; g.FE64 = c->d_FE64; g.b64 = c->d_b64; g.tw32 = c->d_tw32; g.tw64 = c->d_tw64;
     g.tA_cm1 = c->d_tab; g.tA_s = c->d_tab + tabA;
     g.tB_wc = c->d_tab + 2 * tabA; g.tB_ws = g.tB_wc + tabB; g.tB_gc = g.tB_ws + tabB;
+    g.tA2 = (const float4*)(g.tB_gc + tabB);          // 16-byte aligned: the block sizes above are multiples of 4
     dfc* twdf = c->d_df;
     dfc* FEdf = twdf + g.Ntw / 2;
     dfc* eyc = FEdf + HWc;
@@ -349,7 +376,7 @@ extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pi
         return bail_work(CCST_E_CUDA);
     init_twiddles<<<1, 256, 0, c->stream>>>(g.Ntw, c->d_tw64, c->d_tw32);
     init_tables<<<64, 256, 0, c->stream>>>(g, (float*)g.tA_cm1, (float*)g.tA_s, (float*)g.tB_wc,
-                                           (float*)g.tB_ws, (float*)g.tB_gc);
+                                           (float*)g.tB_ws, (float*)g.tB_gc, (float4*)g.tA2);
     init_ref_operand<<<32, 256, 0, c->stream>>>(g, (const float*)c->d_ref32, c->d_b64);
     init_ref_spectrum<<<1, 256, 0, c->stream>>>(g, d_work, c->d_FE64, c->d_FE32);
     init_dfloat<<<32, 256, 0, c->stream>>>(g, c->d_tw64, c->d_FE64, twdf, FEdf, eyc, eyf, exc, exf, ncy, ncx);
@@ -357,12 +384,13 @@ extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pi
         return bail_work(CCST_E_CUDA);
     cudaFree(d_work);
     d_work = nullptr;
+    c->kernel = track_kernel_for(H, W);
     // the attribute is per function: set it to the device limit so contexts of any size coexist
-    if (!step(cudaFuncSetAttribute(track_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit),
+    if (!step(cudaFuncSetAttribute(c->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit),
               "smem attribute"))
         return bail(CCST_E_CUDA);
     int occ = 0;
-    if (!step(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, track_kernel, kThreads, c->smem), "occupancy"))
+    if (!step(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->kernel, kThreads, c->smem), "occupancy"))
         return bail(CCST_E_CUDA);
     if (occ < 1) {
         fail(nullptr, CCST_E_SHAPE, "ccst_create: tracking kernel does not fit on an SM");
@@ -400,7 +428,12 @@ static int launch(ccst_ctx* c, const Batch& b) {
         }
         CK(c, cudaEventRecordWithFlags(e0, c->stream, c->capturing ? cudaEventRecordExternal : 0));
     }
-    track_kernel<<<grid, kThreads, c->smem, c->stream>>>(c->g, b);
+    {
+        Geom gk = c->g;
+        Batch bk = b;
+        void* args[] = {&gk, &bk};
+        CK(c, cudaLaunchKernel(c->kernel, dim3(grid), dim3(kThreads), args, c->smem, c->stream));
+    }
     if (prof) CK(c, cudaEventRecordWithFlags(e1, c->stream, c->capturing ? cudaEventRecordExternal : 0));
     CK(c, cudaGetLastError());
     return CCST_OK;
@@ -421,6 +454,8 @@ static int make_batch(ccst_ctx* c, const void* frames, int64_t n, int64_t pitch,
     b->n = n;
     b->pitch = pitch;
     b->out = (Result*)out;
+    const size_t el = c->p.in_dtype == CCST_U16 ? 2 : 4;
+    b->vec_ok = ((uintptr_t)frames % 16 == 0) && ((size_t)pitch * el % 16 == 0) ? 1 : 0;
     b->dbg_int = nullptr;
     b->dbg_sub = nullptr;
     b->dbg_pairs = nullptr;
@@ -617,8 +652,9 @@ extern "C" int ccst_debug_pairs(ccst_ctx* c, const void* frames_dev, int64_t n, 
     b.dbg_d64 = d64_dev;
     if (n == 0) return CCST_OK;
     const int grid = (int)(n < c->grid_main ? n : c->grid_main);
-    track_kernel<<<grid, kThreads, c->smem, c->stream>>>(c->g, b);
-    CK(c, cudaGetLastError());
+    Geom gk = c->g;
+    void* args[] = {&gk, &b};
+    CK(c, cudaLaunchKernel(c->kernel, dim3(grid), dim3(kThreads), args, c->smem, c->stream));
     return CCST_OK;
 }
 
@@ -658,7 +694,7 @@ int static_fail(int code, const char* msg, const char* detail = "") {
 }
 
 // Once per device, with that device current: resolve the array's device address
-// (the host-side symbol is only a stand-in) and raise the kernel's shared-memory limit.
+// (the host-side symbol is only a stand-in) and raise the kernels' shared-memory limit.
 int static_setup(int dev, StaticDevice* out) {
     if (dev < 0 || dev >= kStaticMaxDevices) return static_fail(CCST_E_UNSUPPORTED, "ccst_track_static: device ordinal >= 64");
     std::lock_guard<std::mutex> lk(g_static_mu);
@@ -676,11 +712,14 @@ int static_setup(int dev, StaticDevice* out) {
         }
         d.smem_limit = prop.sharedMemPerBlockOptin;
         d.sms = prop.multiProcessorCount;
-        if ((e = cudaFuncSetAttribute(track_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)d.smem_limit)) != cudaSuccess) {
-            snprintf(g_static_err, sizeof(g_static_err), "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-            return CCST_E_CUDA;
-        }
+        for (int h = 8; h <= 128; h *= 2)
+            for (int w = 8; w <= 128; w *= 2) {
+                if ((e = cudaFuncSetAttribute(track_kernel_for(h, w), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)d.smem_limit)) != cudaSuccess) {
+                    snprintf(g_static_err, sizeof(g_static_err), "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+                    return CCST_E_CUDA;
+                }
+            }
         d.ready = true;
     }
     *out = d;
@@ -717,15 +756,9 @@ extern "C" int ccst_track_static(const float* ref_dev, int H, int W, const ccst_
 
     // geometry: the same choices ccst_create makes
     Geom g{};
-    g.H = H; g.W = W; g.logH = ilog2(H); g.logW = ilog2(W); g.Hh = H / 2;
-    g.Wc = W / 2 + 1; g.Wcp = (g.Wc + 1) & ~1;
-    g.u = p.upsample; g.M = (3 * p.upsample + 1) / 2; g.h0 = g.M / 2; g.pmax = g.M - 1 - g.h0;
-    g.T1p = (g.h0 + 1 + 3) & ~3;
-    g.Ntw = H > W ? H : W; g.logNtw = ilog2(g.Ntw);
-    g.method = p.method; g.in_dtype = p.in_dtype; g.eps = p.eps;
-    g.sense = p.method == CCST_CC_U ? 1.f : -1.f;
-    g.tau_int = kTauInt; g.tau0 = kTau0; g.tau1 = kTau1;
-    g.guard = (p.flags & CCST_FLAG_TIE_GUARD) ? 1 : 0;
+    if (!plan_geometry(H, W, p, sd.smem_limit, &g))
+        return static_fail(CCST_E_SHAPE, "ccst_track_static: frame too large for shared memory");
+    const size_t smem = smem_plan(g).total;
     const long long Dy = (long long)g.u * H, Dx = (long long)g.u * W;
     g.By = 1; while ((long long)g.By * g.By < Dy) ++g.By;
     g.Bx = 1; while ((long long)g.Bx * g.Bx < Dx) ++g.Bx;
@@ -734,6 +767,7 @@ extern "C" int ccst_track_static(const float* ref_dev, int H, int W, const ccst_
     // carve the static array (256-byte aligned regions)
     const size_t HW = (size_t)H * W, HWc = (size_t)H * g.Wc;
     const size_t tabA = (size_t)g.Hh * g.T1p, tabB = (size_t)g.Wc * g.T1p;
+    const size_t tabA2 = (size_t)g.TAB * (g.Hh / 2);
     const size_t ndf = (size_t)(g.Ntw / 2) + HWc + ncy + g.By + ncx + g.Bx;
     const size_t work = (size_t)(H / 2) * W + (size_t)H * g.Wcp;
     size_t off = 0;
@@ -743,22 +777,15 @@ extern "C" int ccst_track_static(const float* ref_dev, int H, int W, const ccst_
     float2* FE32 = (float2*)take(HWc * sizeof(float2));
     double2* tw64 = (double2*)take((size_t)(g.Ntw / 2) * sizeof(double2));
     float2* tw32 = (float2*)take((size_t)(g.Ntw / 2) * sizeof(float2));
-    float* tab = (float*)take((2 * tabA + 3 * tabB) * sizeof(float));
+    float* tab = (float*)take((2 * tabA + 3 * tabB + 4 * tabA2) * sizeof(float));
     dfc* dfb = (dfc*)take(ndf * sizeof(dfc));
     double2* wk = (double2*)take(work * sizeof(double2));
     if (off > kStaticScratchBytes)
         return static_fail(CCST_E_SHAPE, "ccst_track_static: this H, W and upsample need more scratch than "
                                          "the 2 MiB static array holds (lower upsample)");
-    g.TC = g.T1p;
-    for (;;) {
-        g.nchunk = (g.h0 + 1 + g.TC - 1) / g.TC;
-        if (smem_bytes(g) <= sd.smem_limit || g.TC <= 4) break;
-        g.TC -= 4;
-    }
-    const size_t smem = smem_bytes(g);
-    if (smem > sd.smem_limit) return static_fail(CCST_E_SHAPE, "ccst_track_static: frame too large for shared memory");
     g.FE32 = FE32; g.FE64 = FE64; g.b64 = b64; g.tw32 = tw32; g.tw64 = tw64;
     g.tA_cm1 = tab; g.tA_s = tab + tabA; g.tB_wc = tab + 2 * tabA; g.tB_ws = g.tB_wc + tabB; g.tB_gc = g.tB_ws + tabB;
+    g.tA2 = (const float4*)(g.tB_gc + tabB);
     dfc* twdf = dfb;
     dfc* FEdf = twdf + g.Ntw / 2;
     dfc* eyc = FEdf + HWc;
@@ -770,7 +797,7 @@ extern "C" int ccst_track_static(const float* ref_dev, int H, int W, const ccst_
     // every region is rewritten in full below before anything reads it
     init_twiddles<<<1, 256, 0, stream>>>(g.Ntw, tw64, tw32);
     init_tables<<<64, 256, 0, stream>>>(g, tab, tab + tabA, tab + 2 * tabA, tab + 2 * tabA + tabB,
-                                        tab + 2 * tabA + 2 * tabB);
+                                        tab + 2 * tabA + 2 * tabB, (float4*)g.tA2);
     init_ref_operand<<<32, 256, 0, stream>>>(g, ref_dev, b64);
     init_ref_spectrum<<<1, 256, 0, stream>>>(g, wk, FE64, FE32);
     init_dfloat<<<32, 256, 0, stream>>>(g, tw64, FE64, twdf, FEdf, eyc, eyf, exc, exf, ncy, ncx);
@@ -780,11 +807,16 @@ extern "C" int ccst_track_static(const float* ref_dev, int H, int W, const ccst_
         b.n = n;
         b.pitch = pitch_elems;
         b.out = (Result*)out_dev;
+        const size_t el = p.in_dtype == CCST_U16 ? 2 : 4;
+        b.vec_ok = ((uintptr_t)frames_dev % 16 == 0) && ((size_t)pitch_elems * el % 16 == 0) ? 1 : 0;
+        const void* kern = track_kernel_for(H, W);
         int occ = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, track_kernel, kThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
         const long long cap = (long long)sd.sms * (occ > 0 ? occ : 1);
         const int grid = (int)(n < cap ? n : cap);
-        track_kernel<<<grid, kThreads, smem, stream>>>(g, b);
+        void* args[] = {&g, &b};
+        if ((e = cudaLaunchKernel(kern, dim3(grid), dim3(kThreads), args, smem, stream)) != cudaSuccess)
+            return static_fail(CCST_E_CUDA, "ccst_track_static launch: ", cudaGetErrorString(e));
     }
     if ((e = cudaGetLastError()) != cudaSuccess)
         return static_fail(CCST_E_CUDA, "ccst_track_static launch: ", cudaGetErrorString(e));

@@ -52,7 +52,7 @@ __device__ __forceinline__ int brev(int x, int logN) { return (int)(__brev((unsi
 // tw[k] = exp(-2 pi i k / Ntw), k < Ntw/2, Ntw = 2^logNtw >= N. inverse=true uses
 // exp(+2 pi i ...) and does not scale. Ends with __syncthreads().
 template <typename C>
-__device__ void fft_r2_passes(C* buf, int logN, int nseq, int seq_stride, int elem_stride,
+static __device__ void fft_r2_passes(C* buf, int logN, int nseq, int seq_stride, int elem_stride,
                               const C* tw, int logNtw, bool inverse) {
     const int halfN = 1 << (logN - 1);
     const int total = halfN * nseq;
@@ -152,9 +152,30 @@ struct TopK {
     }
 };
 
+// Block-wide (value, index) maximum under better(); every thread gets it.
+// sv/sj: >= 32 entries of scratch.
+__device__ __forceinline__ void block_argmax(float& v, int& j, float* sv, int* sj) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, j, o);
+        if (better(ov, oj, v, j)) { v = ov; j = oj; }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) { sv[wid] = v; sj[wid] = j; }
+    __syncthreads();
+    const int nwarps = (blockDim.x + 31) >> 5;
+    v = -INFINITY;
+    j = INT_MAX;
+    for (int w = 0; w < nwarps; ++w)
+        if (better(sv[w], sj[w], v, j)) { v = sv[w]; j = sj[w]; }
+    __syncthreads();
+}
+
 // Block-wide top-K; all threads return the merged list. sv/sj: >= kWarps*K entries.
 template <int K>
-__device__ void block_topk(TopK<K>& t, float* sv, int* sj) {
+__device__ __forceinline__ void block_topk(TopK<K>& t, float* sv, int* sj) {
     t.warp_merge();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __syncthreads();

@@ -1,16 +1,20 @@
-// ccst_kernels.cuh -- the tracking kernels for sm_103a.
+// ccst_kernels.cuh -- the tracking kernel for sm_103a.
 //
 // One CTA tracks one frame at a time (grid-stride over the batch). Every step
 // stays in shared memory:
-//   a1  ingest the frame (uint16 or float32) and form the surface operand: the
-//       frame itself for CC-U, (I + eps)^2 for CC-SN (Sec. II, Eqs. (4), (7));
-//   a2  2-D R2C FFT (two real rows packed per complex row, radix-2);
-//   a3  product with the resident reference spectrum, X = F[a] conj(F[b]);
+//   a1  ingest the frame (uint16 or float32, 16-byte vector loads) and form the
+//       surface operand: the frame itself for CC-U, (I + eps)^2 for CC-SN
+//       (Sec. II, Eqs. (4), (7));
+//   a2  2-D R2C FFT: two real rows per complex row, four-step passes with the
+//       small DFTs in registers; the real/complex split is fused into the column
+//       pass loads, and the DC and Nyquist columns travel as one complex column;
+//   a3  product with the resident reference spectrum, X = F[a] conj(F[b]), fused
+//       into the last column pass;
 //   a4  inverse 2-D FFT -> integer surface c(s) (right-hand side of Eq. (4)/(7));
 //   a5  integer extremum, lowest row-major index on ties, wrapped shift;
 //       near-ties re-decided by FP64 direct sums sum_r a(r+s) b(r);
 //   a6  upsampled DFT on the M x M grid around it (Sec. III), as two dense
-//       contractions with frame-independent tables;
+//       contractions with frame-independent tables staged in shared memory;
 //   a7  sub-pixel extremum and the output record.
 //
 // a6 is evaluated relative to the integer peak (the "delta" form): with
@@ -39,14 +43,19 @@
 #pragma once
 
 #include "ccst_device.cuh"
+#include "ccst_fft.cuh"
 
 namespace ccst {
 
 struct Geom {
     int H, W, logH, logW, Hh, Wc, Wcp;  // Wc = W/2+1 (half spectrum), Wcp = Wc rounded up to even
+    int SA;                             // column slots of the spectrum buffer: W/2 (slot 0 = DC, + Nyquist array)
+    int SZ;                             // padded row stride (float2) of the packed-row buffer
     int u, M, h0, pmax;                 // grid: M points, offsets t = j - h0 in [-h0, pmax]
-    int T1p;                            // table row length for t, tx in [0, h0] (padded to 4)
-    int TC, nchunk;                     // stage-A chunk rows (multiple of 4) and number of chunks
+    int T1p;                            // table row length for tx in [0, h0] (padded to 4)
+    int TAB;                            // t rows 1..TAB of the stage tables (h0 rounded up to 15)
+    int TC, nchunk;                     // t rows per stage chunk (multiple of 15) and number of chunks
+    int tables_smem;                    // stage tables staged in shared memory (else read from global)
     int Ntw, logNtw;                    // twiddle table length = max(H, W)
     int method, in_dtype;
     float eps, sense;                   // sense = +1 (CC-U maximum) or -1 (CC-SN minimum)
@@ -60,6 +69,7 @@ struct Geom {
     const double2* tw64;
     const float* tA_cm1;                // [Hh][T1p]  cos(2 pi m t/(uH)) - 1, m = 1..Hh
     const float* tA_s;                  // [Hh][T1p]  sin(2 pi m t/(uH))
+    const float4* tA2;                  // [TAB][Hh/2] (cm1, s) for m = 2q+1, 2q+2 at t = 1..TAB
     const float* tB_wc;                 // [Wc][T1p]  w cos(2 pi kx' t/(uW))
     const float* tB_ws;                 // [Wc][T1p]  w sin(2 pi kx' t/(uW))
     const float* tB_gc;                 // [Wc][T1p]  w (cos(2 pi kx' t/(uW)) - 1)
@@ -81,6 +91,7 @@ struct Batch {
     const void* frames;
     long long n;
     long long pitch;     // row pitch in elements
+    int vec_ok;          // frames and pitch allow 16-byte vector loads
     Result* out;
     float* dbg_int;      // optional: n x H x W integer surfaces (unnormalised), or null
     float* dbg_sub;      // optional: n x M x M delta surfaces (unnormalised), or null
@@ -134,144 +145,266 @@ __device__ __forceinline__ double operand_f64(double I, const Geom& g) {
 }
 
 // ------------------------------------------------------------- shared layout
+// R1: A (H x SA float2: the spectrum, later X' with P/Q rows) and XN (H float2: the
+//     x-Nyquist column kx = W/2 of the same).
+// R2, FFT phase: B (H x SA float2, inverse-FFT workspace) and ZC (H/2 x SZ float2,
+//     packed rows: the frame, then the integer surface).
+// R2, contraction phase: TA (stage-A table), TB (stage-B tables), UV (TC x SA float4),
+//     UVN (TC float4, x-Nyquist column). After the contraction R2 holds the guard
+//     scratch. The last guard level uses R1 + R2 as one block.
 struct Smem {
-    float2* A;     // H x Wcp   X, then X' with P/Q rows
-    float2* B;     // H x Wcp   inverse-FFT workspace
-    float4* C;     // TC x Wcp  U'/V chunk; also packed rows (H/2 x W complex) and L1 arrays
-    float2* tw;    // Ntw/2
-    float* gP;     // T1p: g(+tx)
-    float* gM;     // T1p: g(-tx)
-    float* rv;     // reduction scratch (floats)
-    int* rj;       // reduction scratch (ints)
-    double* rd;    // reduction scratch (doubles)
-    int* cj;       // candidate list
-    float* cv;     // candidate values
-    int* misc;     // small broadcast ints
-    float* miscf;  // small broadcast floats
+    float2* A;
+    float2* XN;
+    float2* B;
+    float2* ZC;
+    float4* TA;
+    float* TBc;
+    float* TBs;
+    float4* UV;
+    float4* UVN;
+    unsigned char* r1;     // start of R1
+    size_t r12_bytes;      // bytes of R1 + R2
+    float2* tw;            // Ntw/2
+    int4* rowq;            // Hh/2: row offsets (x SA) of P(m1), P(m2), Q(m1), Q(m2)
+    float* gP;             // T1p: g(+tx)
+    float* gM;             // T1p: g(-tx)
+    float* rv;             // reduction scratch (floats)
+    int* rj;               // reduction scratch (ints)
+    double* rd;            // reduction scratch (doubles)
+    int* cj;               // candidate list
+    float* cv;             // candidate values
+    int* misc;             // small broadcast ints
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline size_t smem_bytes(const Geom& g) {
-    size_t off = 0;
-    off += sizeof(float2) * (size_t)g.H * g.Wcp;            // A
-    off += sizeof(float2) * (size_t)g.H * g.Wcp;            // B
-    size_t cbytes = sizeof(float4) * (size_t)g.TC * g.Wcp;
-    const size_t packed = sizeof(float2) * (size_t)(g.H / 2) * g.W;
-    const size_t l1 = sizeof(float2) * (size_t)(3 * g.H + 2 * g.Wcp + 2);
-    if (cbytes < packed) cbytes = packed;
-    if (cbytes < l1) cbytes = l1;
-    off += align_up(cbytes, 16);                            // C
-    off += sizeof(float2) * (size_t)(g.Ntw / 2);            // tw
-    off += sizeof(float) * 2 * (size_t)g.T1p;               // gP, gM
-    off += sizeof(float) * 128 + sizeof(int) * 128;         // rv, rj
-    off = align_up(off, 8);
-    off += sizeof(double) * 32;                             // rd
-    off += (sizeof(int) + sizeof(float)) * kMaxCand;        // cj, cv
-    off += sizeof(int) * 16 + sizeof(float) * 16;           // misc
-    return align_up(off, 16);
+struct SmemPlan {
+    size_t a, xn, r1, b, zc, ta, tbc, tbs, uv, uvn, r2, misc, total;
+};
+
+__host__ __device__ inline size_t table_bytes(const Geom& g) {
+    return sizeof(float4) * (size_t)g.TAB * (g.Hh / 2) + 2 * sizeof(float) * (size_t)g.Wc * g.T1p;
 }
 
-__device__ inline Smem carve(const Geom& g, unsigned char* base) {
+__host__ __device__ inline SmemPlan smem_plan(const Geom& g) {
+    SmemPlan p;
+    p.a = align_up(sizeof(float2) * (size_t)g.H * g.SA, 16);
+    p.xn = align_up(sizeof(float2) * (size_t)g.H, 16);
+    p.r1 = p.a + p.xn;
+    p.b = align_up(sizeof(float2) * (size_t)g.H * g.SA, 16);
+    p.zc = align_up(sizeof(float2) * (size_t)(g.H / 2) * g.SZ, 16);
+    const size_t fft = p.b + p.zc;
+    p.ta = g.tables_smem ? align_up(sizeof(float4) * (size_t)g.TAB * (g.Hh / 2), 16) : 0;
+    p.tbc = g.tables_smem ? align_up(sizeof(float) * (size_t)g.Wc * g.T1p, 16) : 0;
+    p.tbs = p.tbc;
+    p.uv = align_up(sizeof(float4) * (size_t)g.TC * g.SA, 16);
+    // the P/Q build keeps R(kx), its 8 partial sums and the g partial sums here first
+    const size_t rscr = sizeof(float2) * ((size_t)g.Wcp + 8 * (size_t)(g.SA + 1)) + sizeof(float) * 8 * (size_t)g.T1p;
+    if (p.uv < rscr) p.uv = align_up(rscr, 16);
+    p.uvn = align_up(sizeof(float4) * (size_t)g.TC, 16);
+    const size_t k6 = p.ta + p.tbc + p.tbs + p.uv + p.uvn;
+    const size_t l1 = sizeof(float2) * (size_t)(3 * g.H + 2 * g.Wcp + 2) + sizeof(double2) * (size_t)(2 * g.H + 2 * g.Wc);
+    p.r2 = fft > k6 ? fft : k6;
+    if (p.r2 < l1) p.r2 = align_up(l1, 16);
+    // the double-float level needs H x Wcp dfc plus one packed-row chunk (2 rows of W dfc),
+    // which later holds the H + Wc candidate twiddles
+    const size_t chunk = 2 * (size_t)g.W > (size_t)(g.H + g.Wc) ? 2 * (size_t)g.W : (size_t)(g.H + g.Wc);
+    const size_t dfl = sizeof(dfc) * ((size_t)g.H * g.Wcp + chunk);
+    if (p.r1 + p.r2 < dfl) p.r2 = align_up(dfl - p.r1, 16);
+    p.misc = sizeof(double) * 32 + sizeof(float2) * (size_t)(g.Ntw / 2) + sizeof(int4) * (size_t)(g.Hh / 2) +
+             sizeof(float) * 2 * (size_t)g.T1p + sizeof(float) * 64 + sizeof(int) * 64 +
+             (sizeof(int) + sizeof(float)) * kMaxCand + sizeof(int) * 16 + 64;
+    p.total = align_up(p.r1 + p.r2 + p.misc, 16);
+    return p;
+}
+
+static __device__ inline Smem carve(const Geom& g, unsigned char* base) {
+    const SmemPlan p = smem_plan(g);
     Smem s;
-    size_t off = 0;
-    s.A = (float2*)(base + off); off += sizeof(float2) * (size_t)g.H * g.Wcp;
-    s.B = (float2*)(base + off); off += sizeof(float2) * (size_t)g.H * g.Wcp;
-    size_t cbytes = sizeof(float4) * (size_t)g.TC * g.Wcp;
-    const size_t packed = sizeof(float2) * (size_t)(g.H / 2) * g.W;
-    const size_t l1 = sizeof(float2) * (size_t)(3 * g.H + 2 * g.Wcp + 2);
-    if (cbytes < packed) cbytes = packed;
-    if (cbytes < l1) cbytes = l1;
-    s.C = (float4*)(base + off); off += align_up(cbytes, 16);
-    s.tw = (float2*)(base + off); off += sizeof(float2) * (size_t)(g.Ntw / 2);
-    s.gP = (float*)(base + off); off += sizeof(float) * g.T1p;
-    s.gM = (float*)(base + off); off += sizeof(float) * g.T1p;
-    s.rv = (float*)(base + off); off += sizeof(float) * 128;
-    s.rj = (int*)(base + off); off += sizeof(int) * 128;
-    off = align_up(off, 8);
-    s.rd = (double*)(base + off); off += sizeof(double) * 32;
-    s.cj = (int*)(base + off); off += sizeof(int) * kMaxCand;
-    s.cv = (float*)(base + off); off += sizeof(float) * kMaxCand;
-    s.misc = (int*)(base + off); off += sizeof(int) * 16;
-    s.miscf = (float*)(base + off);
+    s.r1 = base;
+    s.A = (float2*)base;
+    s.XN = (float2*)(base + p.a);
+    unsigned char* r2 = base + p.r1;
+    s.B = (float2*)r2;
+    s.ZC = (float2*)(r2 + p.b);
+    s.TA = (float4*)r2;
+    s.TBc = (float*)(r2 + p.ta);
+    s.TBs = (float*)(r2 + p.ta + p.tbc);
+    s.UV = (float4*)(r2 + p.ta + p.tbc + p.tbs);
+    s.UVN = (float4*)(r2 + p.ta + p.tbc + p.tbs + p.uv);
+    s.r12_bytes = p.r1 + p.r2;
+    unsigned char* m = r2 + p.r2;
+    s.rd = (double*)m; m += sizeof(double) * 32;
+    s.tw = (float2*)m; m += sizeof(float2) * (g.Ntw / 2);
+    s.rowq = (int4*)m; m += sizeof(int4) * (g.Hh / 2);
+    s.gP = (float*)m; m += sizeof(float) * g.T1p;
+    s.gM = (float*)m; m += sizeof(float) * g.T1p;
+    s.rv = (float*)m; m += sizeof(float) * 64;
+    s.rj = (int*)m; m += sizeof(int) * 64;
+    s.cj = (int*)m; m += sizeof(int) * kMaxCand;
+    s.cv = (float*)m; m += sizeof(float) * kMaxCand;
+    s.misc = (int*)m;
     return s;
 }
 
-// ------------------------------------------------------- a1-a4: FFT correlation
-// Leaves X = F[a] conj(F[b]) (H x Wc, natural order) in S.A and the unnormalised
-// integer surface HW*c(s) packed in S.C as (row 2r, row 2r+1) pairs. Returns
-// sum w|X| (for the guard thresholds), identical in every thread.
-__device__ float fft_correlate(const Geom& g, const Smem& S, const void* frame, long long pitch) {
-    const int H = g.H, W = g.W, Wc = g.Wc, Wcp = g.Wcp, Hh = g.Hh;
-    float2* Z = (float2*)S.C;  // packed rows: H/2 x W
-
-    // a1: ingest, operand, pack rows (2r, 2r+1) -> one complex row, x bit-reversed
-    for (int idx = threadIdx.x; idx < H * W; idx += blockDim.x) {
-        const int y = idx >> g.logW, x = idx & (W - 1);
-        const float a = operand_f32(pixel_f32(frame, g.in_dtype, (long long)y * pitch + x), g);
-        float* dst = (float*)&Z[(y >> 1) * W + brev(x, g.logW)];
-        dst[y & 1] = a;
-    }
-    __syncthreads();
-    // a2: row FFTs
-    fft_r2_passes(Z, g.logW, Hh, W, 1, S.tw, g.logNtw, false);
-    // split the packed spectra into rows 2r, 2r+1 of the half spectrum (rows bit-reversed)
-    for (int idx = threadIdx.x; idx < Hh * Wcp; idx += blockDim.x) {
-        const int r = idx / Wcp, kx = idx - r * Wcp;
-        float2 fe = make_float2(0.f, 0.f), fo = make_float2(0.f, 0.f);
-        if (kx < Wc) {
-            const float2 z = Z[r * W + kx];
-            const float2 zc = cconj(Z[r * W + ((W - kx) & (W - 1))]);
-            fe = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y + zc.y));
-            const float2 d = csub(z, zc);
-            fo = make_float2(0.5f * d.y, -0.5f * d.x);   // (z - zc) / (2i)
-        }
-        S.A[brev(2 * r, g.logH) * Wcp + kx] = fe;
-        S.A[brev(2 * r + 1, g.logH) * Wcp + kx] = fo;
-    }
-    __syncthreads();
-    // column FFTs
-    fft_r2_passes(S.A, g.logH, Wc, 1, Wcp, S.tw, g.logNtw, false);
-    // a3: product with conj(F[b]); bit-reversed copy for the inverse column pass
-    float sabs = 0.f;
-    for (int idx = threadIdx.x; idx < H * Wc; idx += blockDim.x) {
-        const int ky = idx / Wc, kx = idx - ky * Wc;
-        const float2 fe = __ldg(&g.FE32[idx]);
-        const float2 x = cmul(S.A[ky * Wcp + kx], cconj(fe));
-        S.A[ky * Wcp + kx] = x;
-        S.B[brev(ky, g.logH) * Wcp + kx] = x;
-        const float w = (kx == 0 || 2 * kx == W) ? 1.f : 2.f;
-        sabs += w * (fabsf(x.x) + fabsf(x.y));
-    }
-    __syncthreads();
-    const float scale = block_sum(sabs, S.rv);
-    // a4: inverse column FFTs, then C2R rows packed two per complex row
-    fft_r2_passes(S.B, g.logH, Wc, 1, Wcp, S.tw, g.logNtw, true);
-    for (int idx = threadIdx.x; idx < Hh * W; idx += blockDim.x) {
-        const int r = idx >> g.logW, kx = idx & (W - 1);
-        float2 ye, yo;
-        if (kx < Wc) {
-            ye = S.B[(2 * r) * Wcp + kx];
-            yo = S.B[(2 * r + 1) * Wcp + kx];
-        } else {
-            ye = cconj(S.B[(2 * r) * Wcp + (W - kx)]);
-            yo = cconj(S.B[(2 * r + 1) * Wcp + (W - kx)]);
-        }
-        Z[r * W + brev(kx, g.logW)] = make_float2(ye.x - yo.y, ye.y + yo.x);  // ye + i yo
-    }
-    __syncthreads();
-    fft_r2_passes(Z, g.logW, Hh, W, 1, S.tw, g.logNtw, true);
-    return scale;
+// Positions: spectrum rows after the column passes, packed-row elements after the row passes.
+__device__ __forceinline__ int posH(const Geom& g, int ky) { return fft_pos(ky, split_n1(g.H), split_n2(g.H)); }
+__device__ __forceinline__ int physZ(const Geom& g, int q) {
+    const int n2 = split_n2(g.W);
+    return q + q / (n2 > 1 ? n2 : g.W);
 }
 
+// ------------------------------------------------------- a1-a4: FFT correlation
+template <int H, int W>
+static __device__ void fft_correlate_t(const Geom& g, const Smem& S, const void* frame, long long pitch, int vec_ok,
+                                float* scale_out) {
+    constexpr int N1w = Split<W>::N1, N2w = Split<W>::N2, N1h = Split<H>::N1, N2h = Split<H>::N2;
+    constexpr int Hh = H / 2, SA = W / 2;
+    constexpr int PG = N2w > 1 ? N2w : W;          // padding group of the packed rows
+    const int SZ = g.SZ;
+    float2* Z = S.ZC;
+    float2* A = S.A;
+    float2* B = S.B;
+    float2* XN = S.XN;
+    auto zphys = [&](int q) { return q + q / PG; };
+
+    // a1: ingest: packed rows Z[r][x] = (a(2r, x), a(2r+1, x)), natural x order
+    if (vec_ok && g.in_dtype == 0) {
+        for (int idx = threadIdx.x; idx < H * W / 8; idx += blockDim.x) {
+            const int y = idx / (W / 8), x0 = (idx - y * (W / 8)) * 8;
+            const uint4 v = __ldg((const uint4*)((const unsigned short*)frame + (long long)y * pitch + x0));
+            const unsigned int w[4] = {v.x, v.y, v.z, v.w};
+            float* zr = (float*)&Z[(y >> 1) * SZ] + (y & 1);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                zr[2 * zphys(x0 + 2 * k)] = operand_f32((float)(w[k] & 0xffffu), g);
+                zr[2 * zphys(x0 + 2 * k + 1)] = operand_f32((float)(w[k] >> 16), g);
+            }
+        }
+    } else if (vec_ok) {
+        for (int idx = threadIdx.x; idx < H * W / 4; idx += blockDim.x) {
+            const int y = idx / (W / 4), x0 = (idx - y * (W / 4)) * 4;
+            const float4 v = __ldg((const float4*)((const float*)frame + (long long)y * pitch + x0));
+            float* zr = (float*)&Z[(y >> 1) * SZ] + (y & 1);
+            zr[2 * zphys(x0)] = operand_f32(v.x, g);
+            zr[2 * zphys(x0 + 1)] = operand_f32(v.y, g);
+            zr[2 * zphys(x0 + 2)] = operand_f32(v.z, g);
+            zr[2 * zphys(x0 + 3)] = operand_f32(v.w, g);
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < H * W; idx += blockDim.x) {
+            const int y = idx / W, x = idx - y * W;
+            float* zr = (float*)&Z[(y >> 1) * SZ] + (y & 1);
+            zr[2 * zphys(x)] = operand_f32(pixel_f32(frame, g.in_dtype, (long long)y * pitch + x), g);
+        }
+    }
+    __syncthreads();
+    // a2: row FFTs (forward), in place
+    fft_pass1<N1w, N2w, false, false>(
+        Hh, S.tw, g.logNtw, [&](int s, int q) { return Z[s * SZ + zphys(q)]; },
+        [&](int s, int q, float2 v) { Z[s * SZ + zphys(q)] = v; });
+    __syncthreads();
+    if (N2w > 1) {
+        fft_pass2<N1w, N2w, false, false>(
+            Hh, [&](int s, int q) { return Z[s * SZ + zphys(q)]; },
+            [&](int s, int k, int q, float2 v) { Z[s * SZ + zphys(q)] = v; });
+        __syncthreads();
+    }
+    // column pass 1 (forward) with the real/complex split fused into the loads.
+    // Slot 0 carries the DC and Nyquist columns as one complex column (both are real
+    // sequences along y for real rows).
+    auto zrow = [&](int r, int k) { return Z[r * SZ + zphys(fft_pos(k, N1w, N2w))]; };
+    fft_pass1<N1h, N2h, false, true>(
+        SA, S.tw, g.logNtw,
+        [&](int s, int y) {
+            const int r = y >> 1;
+            if (s == 0) {
+                const float2 z0 = zrow(r, 0), zn = zrow(r, W / 2);
+                return (y & 1) ? make_float2(z0.y, zn.y) : make_float2(z0.x, zn.x);
+            }
+            const float2 z = zrow(r, s), zc = zrow(r, W - s);   // zc not yet conjugated
+            if (y & 1) return make_float2(0.5f * (z.y + zc.y), -0.5f * (z.x - zc.x));   // (z - conj zc)/(2i)
+            return make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y));               // (z + conj zc)/2
+        },
+        [&](int s, int q, float2 v) { A[q * SA + s] = v; });
+    __syncthreads();
+    // column pass 2 + a3: product with conj(F[b]) (slot 0 is unpacked afterwards)
+    float sabs = 0.f;
+    fft_pass2<N1h, N2h, false, true>(
+        SA, [&](int s, int q) { return A[q * SA + s]; },
+        [&](int s, int ky, int q, float2 v) {
+            if (s != 0) {
+                const float2 x = cmul(v, cconj(__ldg(&g.FE32[ky * (W / 2 + 1) + s])));
+                sabs += 2.f * (fabsf(x.x) + fabsf(x.y));
+                v = x;
+            }
+            A[q * SA + s] = v;
+        });
+    __syncthreads();
+    // unpack slot 0 into X(ky, 0) (kept in slot 0) and X(ky, W/2) (in XN)
+    for (int ky = threadIdx.x; ky < H; ky += blockDim.x) {
+        const int q = fft_pos(ky, N1h, N2h), qm = fft_pos((H - ky) & (H - 1), N1h, N2h);
+        const float2 zp = A[q * SA], zm = cconj(A[qm * SA]);
+        const float2 f0 = make_float2(0.5f * (zp.x + zm.x), 0.5f * (zp.y + zm.y));
+        const float2 d = csub(zp, zm);
+        const float2 fn = make_float2(0.5f * d.y, -0.5f * d.x);
+        const float2 x0 = cmul(f0, cconj(__ldg(&g.FE32[ky * (W / 2 + 1)])));
+        const float2 xn = cmul(fn, cconj(__ldg(&g.FE32[ky * (W / 2 + 1) + W / 2])));
+        sabs += fabsf(x0.x) + fabsf(x0.y) + fabsf(xn.x) + fabsf(xn.y);
+        XN[q] = xn;
+        B[q] = x0;                       // staged: other threads still read slot 0
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < H; q += blockDim.x) A[q * SA] = B[q];
+    __syncthreads();
+    *scale_out = block_sum(sabs, S.rv);
+    // a4: inverse column pass 1 (slot 0 packs X(.,0) + i X(.,W/2), whose transforms are real)
+    fft_pass1<N1h, N2h, true, true>(
+        SA, S.tw, g.logNtw,
+        [&](int s, int ky) {
+            const int q = fft_pos(ky, N1h, N2h);
+            if (s == 0) {
+                const float2 a = A[q * SA], n = XN[q];
+                return make_float2(a.x - n.y, a.y + n.x);
+            }
+            return A[q * SA + s];
+        },
+        [&](int s, int q, float2 v) { B[q * SA + s] = v; });
+    __syncthreads();
+    fft_pass2<N1h, N2h, true, true>(
+        SA, [&](int s, int q) { return B[q * SA + s]; }, [&](int s, int y, int q, float2 v) { B[q * SA + s] = v; });
+    __syncthreads();
+    // C2R rows: packed row r = Y(2r,.) + i Y(2r+1,.), Hermitian extension for kx > W/2
+    fft_pass1<N1w, N2w, true, false>(
+        Hh, S.tw, g.logNtw,
+        [&](int r, int kx) {
+            const int qe = fft_pos(2 * r, N1h, N2h), qo = fft_pos(2 * r + 1, N1h, N2h);
+            float2 ye, yo;
+            if (kx == 0) { ye = make_float2(B[qe * SA].x, 0.f); yo = make_float2(B[qo * SA].x, 0.f); }
+            else if (2 * kx == W) { ye = make_float2(B[qe * SA].y, 0.f); yo = make_float2(B[qo * SA].y, 0.f); }
+            else if (2 * kx < W) { ye = B[qe * SA + kx]; yo = B[qo * SA + kx]; }
+            else { ye = cconj(B[qe * SA + (W - kx)]); yo = cconj(B[qo * SA + (W - kx)]); }
+            return make_float2(ye.x - yo.y, ye.y + yo.x);
+        },
+        [&](int r, int q, float2 v) { Z[r * SZ + zphys(q)] = v; });
+    __syncthreads();
+    if (N2w > 1) {
+        fft_pass2<N1w, N2w, true, false>(
+            Hh, [&](int s, int q) { return Z[s * SZ + zphys(q)]; },
+            [&](int s, int k, int q, float2 v) { Z[s * SZ + zphys(q)] = v; });
+        __syncthreads();
+    }
+}
+
+// Integer surface HW*c(y, x) from the packed-row buffer.
 __device__ __forceinline__ float int_surface(const Geom& g, const Smem& S, int flat) {
     const int y = flat >> g.logW, x = flat & (g.W - 1);
-    const float2 z = ((const float2*)S.C)[(y >> 1) * g.W + x];
+    const float2 z = S.ZC[(y >> 1) * g.SZ + physZ(g, fft_pos(x, split_n1(g.W), split_n2(g.W)))];
     return (y & 1) ? z.y : z.x;
 }
 
 // FP64 direct sum c(s) = sum_r a((r + s) mod N) b(r) (left-hand side of Eq. (4)/(7)).
-__device__ double direct_sum_f64(const Geom& g, const Smem& S, const void* frame, long long pitch,
+static __device__ double direct_sum_f64(const Geom& g, const Smem& S, const void* frame, long long pitch,
                                  int sy, int sx) {
     double acc = 0.0;
     for (int idx = threadIdx.x; idx < g.H * g.W; idx += blockDim.x) {
@@ -286,25 +419,36 @@ __device__ double direct_sum_f64(const Geom& g, const Smem& S, const void* frame
 }
 
 // ------------------------------------------------------ a5: integer extremum
-// Returns the flat index of the integer peak (0..HW-1) and sets *flags.
-__device__ int integer_peak(const Geom& g, const Smem& S, const void* frame, long long pitch,
-                            float scale, unsigned* flags, float* dbg) {
+// Scans the packed-row buffer in its storage order (row pairs, padded positions),
+// recovering each element's natural flat index for the tie rule.
+__device__ __forceinline__ int integer_peak(const Geom& g, const Smem& S, const void* frame, long long pitch,
+                                            float scale, unsigned* flags, float* dbg) {
     TopK<2> t2;
     t2.init();
-    for (int idx = threadIdx.x; idx < g.H * g.W; idx += blockDim.x) {
-        const float c = int_surface(g, S, idx);
-        if (dbg) dbg[idx] = c;
-        t2.push(g.sense * c, idx);
+    const int W = g.W, n1 = split_n1(W), n2 = split_n2(W);
+    for (int idx = threadIdx.x; idx < (g.H / 2) * W; idx += blockDim.x) {
+        const int r = idx >> g.logW, q = idx & (W - 1);
+        const float2 z = S.ZC[r * g.SZ + physZ(g, q)];
+        const int x = fft_unpos(q, n1, n2);
+        const int fe = (2 * r) * W + x, fo = fe + W;
+        if (dbg) { dbg[fe] = z.x; dbg[fo] = z.y; }
+        t2.push(g.sense * z.x, fe);
+        t2.push(g.sense * z.y, fo);
     }
-    block_topk(t2, S.rv, S.rj);
+    float v1 = t2.v[0];
     int best = t2.j[0];
-    if (!(t2.v[0] > -INFINITY)) { *flags |= 0x10u; return 0; }
+    block_argmax(v1, best, S.rv, S.rj);
+    if (!(v1 > -INFINITY)) { *flags |= 0x10u; return 0; }
     const float tau = g.tau_int * scale;
-    if (!g.guard || !(t2.v[0] - t2.v[1] <= tau)) return best;
+    if (!g.guard) return best;
+    // unique unless some other shift lies within tau of the best
+    const int near = __syncthreads_count(t2.v[0] >= v1 - tau && t2.j[0] != best) +
+                     __syncthreads_count(t2.v[1] >= v1 - tau && t2.j[1] != best);
+    if (near == 0) return best;
     // collect every integer shift within tau of the best
     if (threadIdx.x == 0) S.misc[0] = 0;
     __syncthreads();
-    const float thr = t2.v[0] - tau;
+    const float thr = v1 - tau;
     for (int idx = threadIdx.x; idx < g.H * g.W; idx += blockDim.x) {
         if (g.sense * int_surface(g, S, idx) >= thr) {
             const int k = atomicAdd(&S.misc[0], 1);
@@ -326,45 +470,100 @@ __device__ int integer_peak(const Geom& g, const Smem& S, const void* frame, lon
     return bestj;
 }
 
+// Copy the stage tables into shared memory (asynchronous 16-byte copies).
+__device__ __forceinline__ void stage_tables_async(const Geom& g, const Smem& S) {
+    if (!g.tables_smem) return;
+    const int na = g.TAB * (g.Hh / 2);                 // float4
+    const int nb = g.Wc * g.T1p / 4;                   // float4 per table
+    for (int i = threadIdx.x; i < na + 2 * nb; i += blockDim.x) {
+        const void* src;
+        void* dst;
+        if (i < na) { src = g.tA2 + i; dst = S.TA + i; }
+        else if (i < na + nb) { src = (const float4*)g.tB_wc + (i - na); dst = (float4*)S.TBc + (i - na); }
+        else { src = (const float4*)g.tB_ws + (i - na - nb); dst = (float4*)S.TBs + (i - na - nb); }
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void stage_tables_wait(const Geom& g) {
+    if (!g.tables_smem) return;
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 // --------------------------------------------- a6 prologue: X' and P/Q, R, g
-// In place in S.A: row 0 = X'(0), row Hh = X'(Hh), row m = P(m), row H-m = Q(m).
-// Writes g(+tx), g(-tx) to S.gP / S.gM.
-__device__ void build_pq_and_g(const Geom& g, const Smem& S, int py, int px) {
-    const int H = g.H, W = g.W, Wc = g.Wc, Wcp = g.Wcp, Hh = g.Hh;
+// In place over S.A / S.XN (rows at their positions posH): row 0 = X'(0),
+// row Hh = X'(Hh), row m = P(m), row H-m = Q(m). Writes g(+tx), g(-tx).
+static __device__ void build_pq_and_g(const Geom& g, const Smem& S, int py, int px) {
+    const int H = g.H, W = g.W, SA = g.SA, Hh = g.Hh;
     const int pyy = py & (H - 1), pxx = px & (W - 1);
-    for (int idx = threadIdx.x; idx < (Hh + 1) * Wc; idx += blockDim.x) {
-        const int m = idx / Wc, kx = idx - m * Wc;
+    const int ncol = SA + 1;          // slots 0..SA-1 and the Nyquist column
+    for (int idx = threadIdx.x; idx < (Hh + 1) * ncol; idx += blockDim.x) {
+        const int m = idx / ncol, c = idx - m * ncol;
+        const bool nyq = (c == SA);
+        const int kx = nyq ? W / 2 : c;
         const int kxs = signed_k(kx, W);
         const float2 ex = twiddle_pos(S.tw, (kxs * pxx) & (W - 1), g.logW, g.logNtw);
+        float2* colbase = nyq ? S.XN : S.A + c;
+        const int cstride = nyq ? 1 : SA;
         if (m == 0 || m == Hh) {
             const int kys = signed_k(m, H);
             const float2 ey = twiddle_pos(S.tw, (kys * pyy) & (H - 1), g.logH, g.logNtw);
-            S.A[m * Wcp + kx] = cmul(S.A[m * Wcp + kx], cmul(ey, ex));
+            float2* r = colbase + posH(g, m) * cstride;
+            *r = cmul(*r, cmul(ey, ex));
         } else {
             const float2 eyp = twiddle_pos(S.tw, (m * pyy) & (H - 1), g.logH, g.logNtw);
             const float2 eym = twiddle_pos(S.tw, (-m * pyy) & (H - 1), g.logH, g.logNtw);
-            const float2 xp = cmul(S.A[m * Wcp + kx], cmul(eyp, ex));
-            const float2 xm = cmul(S.A[(H - m) * Wcp + kx], cmul(eym, ex));
-            S.A[m * Wcp + kx] = cadd(xp, xm);
-            S.A[(H - m) * Wcp + kx] = csub(xp, xm);
+            float2* rp = colbase + posH(g, m) * cstride;
+            float2* rm = colbase + posH(g, H - m) * cstride;
+            const float2 xp = cmul(*rp, cmul(eyp, ex));
+            const float2 xm = cmul(*rm, cmul(eym, ex));
+            *rp = cadd(xp, xm);
+            *rm = csub(xp, xm);
         }
     }
     __syncthreads();
-    // R(kx) = X'(0) + sum_{m=1}^{Hh-1} P(m) + X'(Hh), kept in S.B row 0
-    for (int kx = threadIdx.x; kx < Wc; kx += blockDim.x) {
-        float2 r = S.A[Hh * Wcp + kx];
-        for (int m = Hh - 1; m >= 1; --m) r = cadd(r, S.A[m * Wcp + kx]);
-        r = cadd(r, S.A[kx]);
-        S.B[kx] = r;
+    // R(kx) = X'(0) + sum_{m=1}^{Hh-1} P(m) + X'(Hh), in the (not yet used) UV area:
+    // 8 partial column sums per column, then the column totals
+    float2* R = (float2*)S.UV;
+    float2* Rp = R + g.Wcp;                         // [8][ncol] partials
+    for (int task = threadIdx.x; task < 8 * ncol; task += blockDim.x) {
+        const int part = task / ncol, c = task - part * ncol;
+        const bool nyq = (c == SA);
+        const float2* colbase = nyq ? S.XN : S.A + c;
+        const int cstride = nyq ? 1 : SA;
+        float2 r = make_float2(0.f, 0.f);
+        for (int m = Hh - part; m >= 0; m -= 8)          // rows X'(Hh), P(Hh-1) .. P(1), X'(0)
+            r = cadd(r, colbase[posH(g, m) * cstride]);
+        Rp[part * ncol + c] = r;
     }
     __syncthreads();
-    // g(+-tx) = sum_kx gc Rr -+ ws Ri
-    for (int tx = threadIdx.x; tx < g.T1p; tx += blockDim.x) {
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+        float2 r = make_float2(0.f, 0.f);
+        for (int part = 7; part >= 0; --part) r = cadd(r, Rp[part * ncol + c]);
+        R[c == SA ? W / 2 : c] = r;
+    }
+    __syncthreads();
+    // g(+-tx) = sum_kx gc Rr -+ ws Ri: 4 partial sums per tx, then totals
+    float* gpart = (float*)(Rp + 8 * ncol);          // [4][T1p][2]
+    const int nk = g.Wc;
+    for (int task = threadIdx.x; task < 4 * g.T1p; task += blockDim.x) {
+        const int part = task / g.T1p, tx = task - part * g.T1p;
         float a = 0.f, b = 0.f;
-        for (int kx = Wc - 1; kx >= 0; --kx) {
-            const float2 r = S.B[kx];
+        for (int kx = nk - 1 - part; kx >= 0; kx -= 4) {
+            const float2 r = R[kx];
             a = fmaf(__ldg(&g.tB_gc[kx * g.T1p + tx]), r.x, a);
             b = fmaf(__ldg(&g.tB_ws[kx * g.T1p + tx]), r.y, b);
+        }
+        gpart[2 * task] = a;
+        gpart[2 * task + 1] = b;
+    }
+    __syncthreads();
+    for (int tx = threadIdx.x; tx < g.T1p; tx += blockDim.x) {
+        float a = 0.f, b = 0.f;
+        for (int part = 3; part >= 0; --part) {
+            a += gpart[2 * (part * g.T1p + tx)];
+            b += gpart[2 * (part * g.T1p + tx) + 1];
         }
         S.gP[tx] = a - b;
         S.gM[tx] = a + b;
@@ -373,52 +572,72 @@ __device__ void build_pq_and_g(const Geom& g, const Smem& S, int py, int px) {
 }
 
 // --------------------------------------------------- a6: stage A (one chunk)
-// UV[t - t0][kx] = (U'r, U'i, Vr, Vi)(t, kx) for t in [t0, t0 + TC).
-__device__ void stage_a(const Geom& g, const Smem& S, int t0) {
-    const int Wcp = g.Wcp, Hh = g.Hh, H = g.H;
-    const int ntile_t = g.TC / 4, ntile_k = Wcp / 2;
-    for (int tile = threadIdx.x; tile < ntile_t * ntile_k; tile += blockDim.x) {
-        const int tt = tile / ntile_k, kk = tile - tt * ntile_k;
-        const int tb = t0 + 4 * tt, kb = 2 * kk;
-        float4 acc[4][2];
+// UV[lt][slot] = (U'r, U'i, Vr, Vi)(t, kx) for t = t0 + lt, lt in [0, TC); UVN the
+// x-Nyquist column. Tiles: 5 t x 2 slots; the Nyquist column uses spare threads.
+__device__ __forceinline__ void stage_a(const Geom& g, const Smem& S, int t0, const float4* tA2) {
+    const int SA = g.SA, Hq = g.Hh / 2, H = g.H, Hh = g.Hh;
+    const int ntt = g.TC / 5, nkk = SA / 2;
+    const int nmain = ntt * nkk;
+    const int ntask = nmain + ntt;                         // + x-Nyquist column in 5-row strips
+    for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
+        if (task < nmain) {
+            const int tt = task / nkk, kk = task - tt * nkk;
+            const int lt0 = 5 * tt, kb = 2 * kk;
+            float4 acc[5][2];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 5; ++i) { acc[i][0] = make_float4(0.f, 0.f, 0.f, 0.f); acc[i][1] = acc[i][0]; }
+            const float4* tab = tA2 + (size_t)(t0 - 1 + lt0) * Hq;
+            for (int mp = Hq - 1; mp >= 0; --mp) {
+                const int4 ro = S.rowq[mp];
+                const float4 p1 = *(const float4*)&S.A[ro.x + kb];
+                const float4 p2 = *(const float4*)&S.A[ro.y + kb];
+                const float4 q1 = *(const float4*)&S.A[ro.z + kb];
+                // m2 = 2 mp + 2 = Hh (Nyquist row): no sine part outside the x-Nyquist column
+                const float4 q2 = (2 * mp + 2 == Hh) ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                                     : *(const float4*)&S.A[ro.w + kb];
 #pragma unroll
-            for (int k = 0; k < 2; ++k) acc[i][k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (tb < g.T1p) {
-            // Nyquist row first (signed -H/2): P = X'(Hh); Q = -X'(Hh) in the x-Nyquist
-            // column only (elsewhere the row contributes through cos(pi t/u) alone)
-            for (int m = Hh; m >= 1; --m) {
-                const float4 cm = __ldg((const float4*)&g.tA_cm1[(m - 1) * g.T1p + tb]);
-                const float4 sn = __ldg((const float4*)&g.tA_s[(m - 1) * g.T1p + tb]);
-                const float4 p = *(const float4*)&S.A[m * Wcp + kb];
-                float4 q;
-                if (m == Hh) {
-                    const int kn = g.W >> 1;
-                    q = make_float4(kb == kn ? -p.x : 0.f, kb == kn ? -p.y : 0.f,
-                                    kb + 1 == kn ? -p.z : 0.f, kb + 1 == kn ? -p.w : 0.f);
-                } else {
-                    q = *(const float4*)&S.A[(H - m) * Wcp + kb];
-                }
-                const float cmv[4] = {cm.x, cm.y, cm.z, cm.w};
-                const float snv[4] = {sn.x, sn.y, sn.z, sn.w};
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    acc[i][0].x = fmaf(cmv[i], p.x, acc[i][0].x);
-                    acc[i][0].y = fmaf(cmv[i], p.y, acc[i][0].y);
-                    acc[i][0].z = fmaf(snv[i], q.x, acc[i][0].z);
-                    acc[i][0].w = fmaf(snv[i], q.y, acc[i][0].w);
-                    acc[i][1].x = fmaf(cmv[i], p.z, acc[i][1].x);
-                    acc[i][1].y = fmaf(cmv[i], p.w, acc[i][1].y);
-                    acc[i][1].z = fmaf(snv[i], q.z, acc[i][1].z);
-                    acc[i][1].w = fmaf(snv[i], q.w, acc[i][1].w);
+                for (int i = 0; i < 5; ++i) {
+                    const float4 tw = tab[i * Hq + mp];   // (cm1(m1), s(m1), cm1(m2), s(m2)) at t
+                    acc[i][0].x = fmaf(tw.x, p1.x, fmaf(tw.z, p2.x, acc[i][0].x));
+                    acc[i][0].y = fmaf(tw.x, p1.y, fmaf(tw.z, p2.y, acc[i][0].y));
+                    acc[i][0].z = fmaf(tw.y, q1.x, fmaf(tw.w, q2.x, acc[i][0].z));
+                    acc[i][0].w = fmaf(tw.y, q1.y, fmaf(tw.w, q2.y, acc[i][0].w));
+                    acc[i][1].x = fmaf(tw.x, p1.z, fmaf(tw.z, p2.z, acc[i][1].x));
+                    acc[i][1].y = fmaf(tw.x, p1.w, fmaf(tw.z, p2.w, acc[i][1].y));
+                    acc[i][1].z = fmaf(tw.y, q1.z, fmaf(tw.w, q2.z, acc[i][1].z));
+                    acc[i][1].w = fmaf(tw.y, q1.w, fmaf(tw.w, q2.w, acc[i][1].w));
                 }
             }
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                float4* dst = &S.UV[(lt0 + i) * SA + kb];
+                dst[0] = acc[i][0];
+                dst[1] = acc[i][1];
+            }
+        } else {
+            // x-Nyquist column (kx = W/2), rows 5 (task - nmain) .. +4: P/Q from S.XN; its
+            // Nyquist row keeps the full phase
+            const int lt0 = 5 * (task - nmain);
+            float4 acc[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4* tab = tA2 + (size_t)(t0 - 1 + lt0) * Hq;
+            for (int mp = Hq - 1; mp >= 0; --mp) {
+                const int4 ro = S.rowq[mp];
+                const float2 p1 = S.XN[ro.x / SA], p2 = S.XN[ro.y / SA], q1 = S.XN[ro.z / SA];
+                const float2 q2 = (2 * mp + 2 == Hh) ? make_float2(-p2.x, -p2.y) : S.XN[ro.w / SA];
+#pragma unroll
+                for (int i = 0; i < 5; ++i) {
+                    const float4 tw = tab[i * Hq + mp];
+                    acc[i].x = fmaf(tw.x, p1.x, fmaf(tw.z, p2.x, acc[i].x));
+                    acc[i].y = fmaf(tw.x, p1.y, fmaf(tw.z, p2.y, acc[i].y));
+                    acc[i].z = fmaf(tw.y, q1.x, fmaf(tw.w, q2.x, acc[i].z));
+                    acc[i].w = fmaf(tw.y, q1.y, fmaf(tw.w, q2.y, acc[i].w));
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 5; ++i) S.UVN[lt0 + i] = acc[i];
         }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int k = 0; k < 2; ++k) S.C[(4 * tt + i) * Wcp + kb + k] = acc[i][k];
     }
     __syncthreads();
 }
@@ -428,42 +647,58 @@ __device__ __forceinline__ int grid_index(const Geom& g, int ty, int tx) {
 }
 
 // --------------------------------------------------- a6: stage B (one chunk)
-// Evaluates v = sense * (S + g) at every grid point whose |ty| lies in the chunk,
-// feeding the top-K. With collect=true, also appends every point with v >= thr
-// to the candidate list instead.
+// Evaluates v = sense * (S + g) at every grid point whose |ty| lies in the chunk
+// (t = t0 .. t0 + TC - 1, t >= 1), feeding the top-K. With kCollect, appends every
+// point with v >= thr to the candidate list instead. Tiles: 3 t x 4 tx.
 template <bool kCollect>
-__device__ void stage_b(const Geom& g, const Smem& S, int t0, TopK<kTopK>& top, float thr, float* dbg) {
-    const int Wcp = g.Wcp, Wc = g.Wc;
-    const int ntile_t = g.TC / 4, ntile_x = g.T1p / 4;
-    for (int tile = threadIdx.x; tile < ntile_t * ntile_x; tile += blockDim.x) {
-        const int tt = tile / ntile_x, xx = tile - tt * ntile_x;
-        const int tb = t0 + 4 * tt, xb = 4 * xx;
-        if (tb > g.h0) continue;
-        float aU[4][4], aV[4][4], bU[4][4], bV[4][4];
+__device__ __forceinline__ void stage_b(const Geom& g, const Smem& S, int t0, const float* TBc, const float* TBs,
+                                        TopK<kTopK>& top, float thr, float* dbg) {
+    const int SA = g.SA, T1p = g.T1p;
+    const int ntt = g.TC / 3, nxx = T1p / 4;
+    auto emit = [&](float raw, int j) {
+        const float v = g.sense * raw;
+        if (kCollect) {
+            if (v >= thr) {
+                const int k = atomicAdd(&S.misc[1], 1);
+                if (k < kMaxCand) { S.cj[k] = j; S.cv[k] = v; }
+            }
+        } else {
+            if (dbg) dbg[j] = raw;
+            top.push(v, j);
+        }
+    };
+    for (int task = threadIdx.x; task < ntt * nxx; task += blockDim.x) {
+        const int tt = task / nxx, xx = task - tt * nxx;
+        const int lt0 = 3 * tt, xb = 4 * xx;
+        if (t0 + lt0 > g.h0) continue;
+        float aU[3][4], aV[3][4], bU[3][4], bV[3][4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int l = 0; l < 4; ++l) { aU[i][l] = 0.f; aV[i][l] = 0.f; bU[i][l] = 0.f; bV[i][l] = 0.f; }
-        for (int kx = Wc - 1; kx >= 0; --kx) {
-            const float4 wc = __ldg((const float4*)&g.tB_wc[kx * g.T1p + xb]);
-            const float4 ws = __ldg((const float4*)&g.tB_ws[kx * g.T1p + xb]);
+        auto step = [&](int kx, float4 u0, float4 u1, float4 u2) {
+            const float4 wc = *(const float4*)&TBc[kx * T1p + xb];
+            const float4 ws = *(const float4*)&TBs[kx * T1p + xb];
             const float wcv[4] = {wc.x, wc.y, wc.z, wc.w};
             const float wsv[4] = {ws.x, ws.y, ws.z, ws.w};
+            const float4 uv[3] = {u0, u1, u2};
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float4 uv = S.C[(4 * tt + i) * Wcp + kx];
+            for (int i = 0; i < 3; ++i)
 #pragma unroll
                 for (int l = 0; l < 4; ++l) {
-                    aU[i][l] = fmaf(wcv[l], uv.x, aU[i][l]);
-                    aV[i][l] = fmaf(wcv[l], uv.w, aV[i][l]);
-                    bU[i][l] = fmaf(wsv[l], uv.y, bU[i][l]);
-                    bV[i][l] = fmaf(wsv[l], uv.z, bV[i][l]);
+                    aU[i][l] = fmaf(wcv[l], uv[i].x, aU[i][l]);
+                    aV[i][l] = fmaf(wcv[l], uv[i].w, aV[i][l]);
+                    bU[i][l] = fmaf(wsv[l], uv[i].y, bU[i][l]);
+                    bV[i][l] = fmaf(wsv[l], uv[i].z, bV[i][l]);
                 }
-            }
-        }
+        };
+        // x-Nyquist column first (highest frequency), then slots SA-1 .. 0
+        step(SA, S.UVN[lt0], S.UVN[lt0 + 1], S.UVN[lt0 + 2]);
+        for (int kx = SA - 1; kx >= 0; --kx)
+            step(kx, S.UV[lt0 * SA + kx], S.UV[(lt0 + 1) * SA + kx], S.UV[(lt0 + 2) * SA + kx]);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int t = tb + i;
+        for (int i = 0; i < 3; ++i) {
+            const int t = t0 + lt0 + i;
             if (t > g.h0) continue;
 #pragma unroll
             for (int l = 0; l < 4; ++l) {
@@ -471,64 +706,51 @@ __device__ void stage_b(const Geom& g, const Smem& S, int t0, TopK<kTopK>& top, 
                 if (x > g.h0) continue;
                 const float gp = S.gP[x], gm = S.gM[x];
                 const float A0 = aU[i][l] - aV[i][l], A1 = aU[i][l] + aV[i][l];
-                float vals[4];
-                int js[4];
-                int nv = 0;
-                // (+t, +x)
-                if (t <= g.pmax && x <= g.pmax) {
-                    vals[nv] = A0 - bU[i][l] - bV[i][l] + gp; js[nv++] = grid_index(g, t, x);
-                }
-                // (+t, -x)
-                if (t <= g.pmax && x >= 1) {
-                    vals[nv] = A0 + bU[i][l] + bV[i][l] + gm; js[nv++] = grid_index(g, t, -x);
-                }
-                // (-t, +x)
-                if (t >= 1 && x <= g.pmax) {
-                    vals[nv] = A1 - bU[i][l] + bV[i][l] + gp; js[nv++] = grid_index(g, -t, x);
-                }
-                // (-t, -x)
-                if (t >= 1 && x >= 1) {
-                    vals[nv] = A1 + bU[i][l] - bV[i][l] + gm; js[nv++] = grid_index(g, -t, -x);
-                }
-                for (int q = 0; q < nv; ++q) {
-                    const float v = g.sense * vals[q];
-                    if (kCollect) {
-                        if (v >= thr) {
-                            const int k = atomicAdd(&S.misc[1], 1);
-                            if (k < kMaxCand) { S.cj[k] = js[q]; S.cv[k] = v; }
-                        }
-                    } else {
-                        if (dbg) dbg[js[q]] = vals[q];
-                        top.push(v, js[q]);
-                    }
-                }
+                if (t <= g.pmax && x <= g.pmax) emit(A0 - bU[i][l] - bV[i][l] + gp, grid_index(g, t, x));
+                if (t <= g.pmax && x >= 1) emit(A0 + bU[i][l] + bV[i][l] + gm, grid_index(g, t, -x));
+                if (x <= g.pmax) emit(A1 - bU[i][l] + bV[i][l] + gp, grid_index(g, -t, x));
+                if (x >= 1) emit(A1 + bU[i][l] - bV[i][l] + gm, grid_index(g, -t, -x));
             }
+        }
+    }
+    // the t = 0 row: S = 0, the surface is g(tx)
+    if (t0 == 1) {
+        for (int x = threadIdx.x; x <= g.h0; x += blockDim.x) {
+            if (x <= g.pmax) emit(S.gP[x], grid_index(g, 0, x));
+            if (x >= 1) emit(S.gM[x], grid_index(g, 0, -x));
         }
     }
 }
 
 // Full upsampled surface pass (all chunks): top-K, or candidate collection.
 template <bool kCollect>
-__device__ void upsampled_pass(const Geom& g, const Smem& S, TopK<kTopK>& top, float thr, float* dbg) {
+__device__ __forceinline__ void upsampled_pass(const Geom& g, const Smem& S, TopK<kTopK>& top, float thr,
+                                               float* dbg) {
+    const float4* tA2 = g.tables_smem ? S.TA : g.tA2;
+    const float* TBc = g.tables_smem ? S.TBc : g.tB_wc;
+    const float* TBs = g.tables_smem ? S.TBs : g.tB_ws;
     for (int c = 0; c < g.nchunk; ++c) {
-        const int t0 = c * g.TC;
-        stage_a(g, S, t0);
-        stage_b<kCollect>(g, S, t0, top, thr, dbg);
+        const int t0 = 1 + c * g.TC;
+        stage_a(g, S, t0, tA2);
+        stage_b<kCollect>(g, S, t0, TBc, TBs, top, thr, dbg);
         __syncthreads();
     }
 }
 
 // ---------------------------------- a7 guard: exact FP32 pair differences
-// X'(ky, kx) for any row, from the P/Q layout of S.A.
+// X'(ky, kx) for any row and column, from the P/Q layout.
 __device__ __forceinline__ float2 xprime(const Geom& g, const Smem& S, int ky, int kx) {
-    const int Hh = g.Hh, Wcp = g.Wcp;
-    if (ky == 0 || ky == Hh) return S.A[ky * Wcp + kx];
+    const int Hh = g.Hh;
+    const bool nyq = (2 * kx == g.W);
+    const float2* colbase = nyq ? S.XN : S.A + kx;
+    const int cstride = nyq ? 1 : g.SA;
+    if (ky == 0 || ky == Hh) return colbase[posH(g, ky) * cstride];
     if (ky < Hh) {
-        const float2 p = S.A[ky * Wcp + kx], q = S.A[(g.H - ky) * Wcp + kx];
+        const float2 p = colbase[posH(g, ky) * cstride], q = colbase[posH(g, g.H - ky) * cstride];
         return make_float2(0.5f * (p.x + q.x), 0.5f * (p.y + q.y));
     }
     const int m = g.H - ky;
-    const float2 p = S.A[m * Wcp + kx], q = S.A[ky * Wcp + kx];
+    const float2 p = colbase[posH(g, m) * cstride], q = colbase[posH(g, ky) * cstride];
     return make_float2(0.5f * (p.x - q.x), 0.5f * (p.y - q.y));
 }
 
@@ -544,7 +766,7 @@ __device__ __forceinline__ float sin_pi_frac(long long n, long long D) {
     return sinpif((float)n / (float)D);
 }
 
-// Full twiddle exp(2 pi i k' t / (uN)) of the stage tables (FP64-rounded values).
+// Full twiddle exp(2 pi i k' t / (uH)) of the stage tables (FP64-rounded values).
 __device__ __forceinline__ float2 table_twiddle_y(const Geom& g, int ks, int t) {
     const int m = ks < 0 ? -ks : ks, at = t < 0 ? -t : t;
     if (m == 0 || at == 0) return make_float2(1.f, 0.f);
@@ -554,20 +776,18 @@ __device__ __forceinline__ float2 table_twiddle_y(const Geom& g, int ks, int t) 
 }
 
 // Decide among the candidates S.cj[0..nc) (S.cj[0] is the FP32 best j1) with exact
-// pair differences D(j) = v(j) - v(j1). Returns the winner; sets *l2 when the two
+// pair differences D(j) = v(j) - v(j1). Returns the winner; sets *nl2 when the two
 // best remain within tau1, leaving the tied candidates in S.cj[0..*nl2).
-__device__ int pair_difference_guard(const Geom& g, const Smem& S, int nc, float scale, int* nl2,
+static __device__ int pair_difference_guard(const Geom& g, const Smem& S, int nc, float scale, int* nl2,
                                      float* dwin) {
     const int H = g.H, Wc = g.Wc, Wcp = g.Wcp, u = g.u;
-    float2* G = (float2*)S.C;          // H      G(ky) = sum_kx w X'(ky,kx) E(kx, rx)
+    float2* G = (float2*)S.TA;         // H      G(ky) = sum_kx w X'(ky,kx) E(kx, rx)  (R2 is free here)
     float2* Eyc = G + H;               // H      E(ky, ty_c)
     float2* dEy = Eyc + H;             // H      E(ky, ty_c) - E(ky, ry)
     float2* dEx = dEy + H;             // Wcp    w (E(kx, tx_c) - E(kx, rx))
+    float2* GN = dEx + Wcp;            // 1      the Nyquist row's x-Nyquist term of G
     const int j1 = S.cj[0];
     const int ry = j1 / g.M - g.h0, rx = j1 % g.M - g.h0;
-    // G(ky), using the table twiddles w E(kx, rx) = wc -+ i ws. For the Nyquist row the
-    // x-Nyquist column is kept apart in slot H + 3H + Wcp (it takes the full y-phase).
-    float2* GN = dEx + Wcp;
     const int kn = g.W >> 1;
     for (int ky = threadIdx.x; ky < H; ky += blockDim.x) {
         float2 acc = make_float2(0.f, 0.f), accn = make_float2(0.f, 0.f);
@@ -636,7 +856,7 @@ __device__ int pair_difference_guard(const Geom& g, const Smem& S, int nc, float
     *dwin = bv;
     const float tau1 = g.tau1 * scale;
     if (nc > 1 && bv - sv <= tau1) {
-        // keep every candidate within tau1 of the winner for the FP64 pass
+        // keep every candidate within tau1 of the winner for the last level
         __syncthreads();
         if (threadIdx.x == 0) {
             int k = 0;
@@ -654,10 +874,10 @@ __device__ int pair_difference_guard(const Geom& g, const Smem& S, int nc, float
 }
 
 // v(jb) - v(ja) from the FP32 X' in shared memory, with FP64 twiddles and FP64
-// accumulation (the Nyquist-row rule included). Scratch: S.C.
-__device__ double pair_difference_f64(const Geom& g, const Smem& S, int ja, int jb, double* red) {
+// accumulation (the Nyquist-row rule included). Scratch: the start of R2.
+static __device__ double pair_difference_f64(const Geom& g, const Smem& S, int ja, int jb, double* red) {
     const int H = g.H, Wc = g.Wc;
-    double2* eyA = (double2*)S.C;
+    double2* eyA = (double2*)(S.TA);
     double2* eyB = eyA + H;
     double2* exA = eyB + H;
     double2* exB = exA + Wc;
@@ -700,8 +920,8 @@ __device__ __forceinline__ dfc df_twiddle(const dfc* coarse, const dfc* fine, in
     return cmul(coarse[n / B], fine[n % B]);
 }
 
-__device__ df block_sum_df(df v, double* red) {
-    // double-float sum across the block; the 16 warp partials are combined in FP64 (few ops)
+static __device__ df block_sum_df(df v, double* red) {
+    // double-float sum across the block; the warp partials are combined in FP64 (few ops)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         df w = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
@@ -720,19 +940,19 @@ __device__ df block_sum_df(df v, double* red) {
 }
 
 // Re-evaluate the candidates S.cj[0..nc) from a double-float product spectrum
-// X = F[a] conj(F[b]): R2C FFT of the operand in double-float (S.A..S.B hold the
-// H x Wcp half spectrum, S.C the packed row chunks), then
+// X = F[a] conj(F[b]): R2C FFT of the operand in double-float (the first H x Wcp
+// dfc of R1 + R2 hold the half spectrum, the rest the packed row chunks), then
 //   cu(j) = Re sum_{ky,kx} w X(ky,kx) E_y(ky, py u + ty) E_x(kx, px u + tx)
 // with exactly reduced angles. Returns the winner (sense-adjusted maximum,
 // lowest index on ties) and its unnormalised value in *val.
-__device__ int df_reevaluate(const Geom& g, const Smem& S, const void* frame, long long pitch,
+static __device__ int df_reevaluate(const Geom& g, const Smem& S, const void* frame, long long pitch,
                              int py, int px, int nc, double* val) {
     const int H = g.H, W = g.W, Wc = g.Wc, Wcp = g.Wcp, Hh = g.Hh;
-    dfc* Xd = (dfc*)S.A;                        // spans S.A and S.B
-    dfc* Zc = (dfc*)S.C;
-    const int cbytes = (int)((char*)S.tw - (char*)S.C);
+    dfc* Xd = (dfc*)S.r1;
+    dfc* Zc = Xd + (size_t)H * Wcp;
+    const long long cbytes = (long long)S.r12_bytes - (long long)sizeof(dfc) * H * Wcp;
     int R = 1;
-    while (2 * R <= Hh && 2 * R * W * (int)sizeof(dfc) <= cbytes) R *= 2;
+    while (2 * R <= Hh && 2LL * R * W * (long long)sizeof(dfc) <= cbytes) R *= 2;
     for (int r0 = 0; r0 < Hh; r0 += R) {
         for (int idx = threadIdx.x; idx < 2 * R * W; idx += blockDim.x) {
             const int yl = idx / W, x = idx - yl * W;
@@ -814,22 +1034,33 @@ __device__ int df_reevaluate(const Geom& g, const Smem& S, const void* frame, lo
 }
 
 // ---------------------------------------------------------- the FP32 kernel
+// One instantiation per frame size (H, W); the host picks it through track_kernel_for().
+template <int H, int W>
 __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Smem S = carve(g, smem_raw);
     for (int k = threadIdx.x; k < g.Ntw / 2; k += blockDim.x) S.tw[k] = g.tw32[k];
+    for (int mp = threadIdx.x; mp < g.Hh / 2; mp += blockDim.x) {
+        const int m1 = 2 * mp + 1, m2 = 2 * mp + 2;
+        S.rowq[mp] = make_int4(posH(g, m1) * g.SA, posH(g, m2) * g.SA, posH(g, g.H - m1) * g.SA,
+                               posH(g, g.H - m2) * g.SA);
+    }
     __syncthreads();
     const size_t elem = g.in_dtype == 0 ? 2 : 4;
     for (long long f = blockIdx.x; f < b.n; f += gridDim.x) {
         const char* frame = (const char*)b.frames + (size_t)f * g.H * b.pitch * elem;
         unsigned flags = 0;
-        const float scale = fft_correlate(g, S, frame, b.pitch);
+        float scale = 0.f;
+        fft_correlate_t<H, W>(g, S, frame, b.pitch, b.vec_ok, &scale);
         const int ip = integer_peak(g, S, frame, b.pitch, scale, &flags,
                                     b.dbg_int ? b.dbg_int + (size_t)f * g.H * g.W : nullptr);
         const float c0 = int_surface(g, S, ip);           // HW * c(p)
         const int py = wrap_shift(ip >> g.logW, g.H), px = wrap_shift(ip & (g.W - 1), g.W);
         __syncthreads();
+        stage_tables_async(g, S);                          // overlaps the P/Q build
         build_pq_and_g(g, S, py, px);
+        stage_tables_wait(g);
+        __syncthreads();
         if (b.dbg_pairs) {
             const int ja = b.dbg_pairs[2 * f], jb = b.dbg_pairs[2 * f + 1];
             const double d64 = pair_difference_f64(g, S, ja, jb, S.rd);
@@ -849,28 +1080,42 @@ __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
         top.init();
         float* dbg = b.dbg_sub ? b.dbg_sub + (size_t)f * g.M * g.M : nullptr;
         upsampled_pass<false>(g, S, top, 0.f, dbg);
-        block_topk(top, S.rv, S.rj);
+        float vw = top.v[0];
         int jw = top.j[0];
-        const float vw = top.v[0];
+        block_argmax(vw, jw, S.rv, S.rj);
         float dwin = 0.f;
         int nl2 = 0;
         if (!(vw > -INFINITY)) {
             flags |= 0x10u;
             jw = 0;
         } else if (g.guard) {
-            const float tau0 = g.tau0 * scale;
-            const float thr = top.v[0] - tau0;
+            const float thr = vw - g.tau0 * scale;
+            // each thread kept its best kTopK points; count those within tau0 of the maximum
             int nc = 0;
+            unsigned mine = 0;
 #pragma unroll
-            for (int k = 0; k < kTopK; ++k) nc += (top.v[k] >= thr) ? 1 : 0;
+            for (int k = 0; k < kTopK; ++k) {
+                const bool q = top.v[k] >= thr;
+                mine |= (q ? 1u : 0u) << k;
+                nc += __syncthreads_count(q);
+            }
+            const bool full = __syncthreads_or(top.v[kTopK - 1] >= thr);
             if (nc > 1) {
                 flags |= 0x02u;
-                if (nc < kTopK) {
-                    if (threadIdx.x == 0)
-                        for (int k = 0; k < nc; ++k) S.cj[k] = top.j[k];
+                if (!full && nc <= kMaxCand) {
+                    // every point within tau0 is among the kept ones: gather them, j1 first
+                    if (threadIdx.x == 0) { S.misc[1] = 1; S.cj[0] = jw; S.cv[0] = vw; }
+                    __syncthreads();
+#pragma unroll
+                    for (int k = 0; k < kTopK; ++k)
+                        if (((mine >> k) & 1u) && top.j[k] != jw) {
+                            const int slot = atomicAdd(&S.misc[1], 1);
+                            S.cj[slot] = top.j[k];
+                            S.cv[slot] = top.v[k];
+                        }
                     __syncthreads();
                 } else {
-                    // more than K-1 near ties: collect them all with a second pass
+                    // a thread holds more near-ties than it kept: collect them all with a second pass
                     if (threadIdx.x == 0) S.misc[1] = 0;
                     __syncthreads();
                     upsampled_pass<true>(g, S, top, thr, nullptr);
@@ -914,13 +1159,30 @@ __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
     }
 }
 
+// Address of track_kernel<H, W> (defined in the per-height translation units).
+const void* track_kernel_h8(int W);
+const void* track_kernel_h16(int W);
+const void* track_kernel_h32(int W);
+const void* track_kernel_h64(int W);
+const void* track_kernel_h128(int W);
+inline const void* track_kernel_for(int H, int W) {
+    switch (H) {
+        case 8: return track_kernel_h8(W);
+        case 16: return track_kernel_h16(W);
+        case 32: return track_kernel_h32(W);
+        case 64: return track_kernel_h64(W);
+        case 128: return track_kernel_h128(W);
+        default: return nullptr;
+    }
+}
+
 // ------------------------------------------------------ FP64 re-evaluation
 // For frames whose FP32 pair differences stayed within tau1, recompute the product
 // spectrum in FP64 (R2C FFT of the operand, product with the FP64 reference
 // spectrum) and evaluate the upsampled surface at the candidates directly:
 //   cu(j) = Re sum_{ky,kx} w X(ky,kx) exp(2 pi i [ky'(py u + ty)/(uH) + kx'(px u + tx)/(uW)]).
 // Workspace: per CTA, H/2*W + H*Wcp double2 in global memory.
-__device__ void fft_r2c_f64_global(const Geom& g, const double* a_or_null, const void* frame,
+static __device__ void fft_r2c_f64_global(const Geom& g, const double* a_or_null, const void* frame,
                                    long long pitch, double2* Z, double2* Xh, double* red) {
     const int H = g.H, W = g.W, Hh = g.Hh, Wc = g.Wc, Wcp = g.Wcp;
     for (int idx = threadIdx.x; idx < H * W; idx += blockDim.x) {
