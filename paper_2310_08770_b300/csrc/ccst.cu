@@ -164,6 +164,8 @@ bool plan_geometry(int H, int W, const ccst_params& p, size_t smem_limit, Geom* 
     g.u = p.upsample; g.M = (3 * p.upsample + 1) / 2; g.h0 = g.M / 2; g.pmax = g.M - 1 - g.h0;
     g.T1p = (g.h0 + 1 + 3) & ~3;
     g.Ntw = H > W ? H : W; g.logNtw = ilog2(g.Ntw);
+    g.lN1h = ilog2(split_n1(H)); g.lN2h = ilog2(split_n2(H));
+    g.lN1w = ilog2(split_n1(W)); g.lN2w = ilog2(split_n2(W));
     g.method = p.method; g.in_dtype = p.in_dtype; g.eps = p.eps;
     g.sense = p.method == CCST_CC_U ? 1.f : -1.f;
     g.tau_int = kTauInt; g.tau0 = kTau0; g.tau1 = kTau1;

@@ -46,44 +46,66 @@ __device__ __forceinline__ float s16(int k) {
 // x * exp(-+ 2 pi i idx / 16) (forward: minus sign), idx a compile-time constant after unrolling.
 template <bool INV>
 __device__ __forceinline__ float2 mul_w16(float2 x, int idx) {
+    idx &= 15;
+    if (idx >= 8) { x = make_float2(-x.x, -x.y); idx -= 8; }      // W^8 = -1
     if (idx == 0) return x;
     if (idx == 4) return INV ? make_float2(-x.y, x.x) : make_float2(x.y, -x.x);
     const float c = c16(idx), s = INV ? s16(idx) : -s16(idx);
     return make_float2(fmaf(x.x, c, -x.y * s), fmaf(x.x, s, x.y * c));
 }
 
-__host__ __device__ constexpr int brev_c(int i, int bits) {
-    int r = 0;
-    for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
-    return r;
+template <bool INV>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+    const float2 t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
 }
-__host__ __device__ constexpr int log2_c(int n) { return n <= 1 ? 0 : 1 + log2_c(n / 2); }
+// 4-point DFT in place: (a, b, c, d) <- X[0..3].
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& a, float2& b, float2& c, float2& d) {
+    const float2 s0 = cadd(a, c), d0 = csub(a, c), s1 = cadd(b, d), d1 = csub(b, d);
+    const float2 r = INV ? make_float2(-d1.y, d1.x) : make_float2(d1.y, -d1.x);   // -+ i d1
+    a = cadd(s0, s1);
+    c = csub(s0, s1);
+    b = cadd(d0, r);
+    d = csub(d0, r);
+}
 
-// In-register DFT of R = 1, 2, 4, 8 or 16 points, natural order in and out.
+// In-register DFT of R = 1, 2, 4, 8 or 16 points, natural order in and out. 8 = 2 x 4 and
+// 16 = 4 x 4 use the same four-step split as the shared-memory passes: R1-point DFTs over
+// the samples R2 n1 + n2, twiddles W_R^{n2 k1}, R2-point DFTs, then X[k1 + R1 k2] is read
+// from slot R2 k1 + k2. Every loop has constant bounds so all indices and twiddles fold.
 template <int R, bool INV>
 __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
-    if (R == 1) return;
-    constexpr int bits = log2_c(R);
+    if constexpr (R == 2) {
+        dft2<INV>(v[0], v[1]);
+    } else if constexpr (R == 4) {
+        dft4<INV>(v[0], v[1], v[2], v[3]);
+    } else if constexpr (R == 8 || R == 16) {
+        constexpr int R1 = R / 4, R2 = 4;
 #pragma unroll
-    for (int i = 0; i < R; ++i) {
-        const int j = brev_c(i, bits);
-        if (j > i) { const float2 t = v[i]; v[i] = v[j]; v[j] = t; }
-    }
-#pragma unroll
-    for (int span = 2; span <= R; span <<= 1) {
-        const int half = span >> 1;
-#pragma unroll
-        for (int st = 0; st < R; st += span) {
-#pragma unroll
-            for (int j = 0; j < half; ++j) {
-                const float2 b = mul_w16<INV>(v[st + j + half], j * (16 / span));
-                const float2 a = v[st + j];
-                v[st + j] = make_float2(a.x + b.x, a.y + b.y);
-                v[st + j + half] = make_float2(a.x - b.x, a.y - b.y);
-            }
+        for (int n2 = 0; n2 < R2; ++n2) {
+            if constexpr (R1 == 2) dft2<INV>(v[n2], v[R2 + n2]);
+            else dft4<INV>(v[n2], v[R2 + n2], v[2 * R2 + n2], v[3 * R2 + n2]);
         }
+#pragma unroll
+        for (int k1 = 1; k1 < R1; ++k1)
+#pragma unroll
+            for (int n2 = 1; n2 < R2; ++n2)
+                v[R2 * k1 + n2] = mul_w16<INV>(v[R2 * k1 + n2], n2 * k1 * (16 / R));
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) dft4<INV>(v[R2 * k1], v[R2 * k1 + 1], v[R2 * k1 + 2], v[R2 * k1 + 3]);
+        float2 t[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) t[i] = v[i];
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1)
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) v[k1 + R1 * k2] = t[R2 * k1 + k2];
     }
 }
+
+__host__ __device__ constexpr int log2_c(int n) { return n <= 1 ? 0 : 1 + log2_c(n / 2); }
 
 // W_N^{e} = exp(-+ 2 pi i e / N), 0 <= e < N, from the shared table tw[k] = exp(-2 pi i k / Ntw).
 template <int N, bool INV>
@@ -97,11 +119,25 @@ __device__ __forceinline__ float2 tw_n(const float2* tw, int logNtw, int e) {
     return t;
 }
 
+// Inter-pass twiddles W_N^{n2 k1} laid out [k1][n2] (N1 x N2 entries), so that the
+// lanes of a warp, which differ in n2 or share it, read distinct banks or broadcast.
+template <int N>
+__device__ __forceinline__ void build_pass_twiddles(float2* t4, const float2* tw, int logNtw) {
+    constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int k1 = i / N2, n2 = i - k1 * N2;
+        t4[i] = tw_n<N, false>(tw, logNtw, n2 * k1);
+    }
+}
+
 // Pass 1 over nseq sequences. kSeqFast: consecutive tasks take consecutive sequences
 // (column-like data); otherwise consecutive n2 of one sequence (row-like data).
+// t4: the [k1][n2] twiddle table of this length (build_pass_twiddles).
+// ld(s, n2, n1) returns sample N2 n1 + n2 of sequence s; st(s, n2, k1, v) stores the
+// pass result k1 at index N2 k1 + n2. The index parts are passed separately so that
+// the functors' addresses are linear in the unrolled n1 / k1.
 template <int N1, int N2, bool INV, bool kSeqFast, class LD, class ST>
-__device__ __forceinline__ void fft_pass1(int nseq, const float2* tw, int logNtw, LD ld, ST st) {
-    constexpr int N = N1 * N2;
+__device__ __forceinline__ void fft_pass1(int nseq, const float2* t4, LD ld, ST st) {
     const int ntask = nseq * N2;
     for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
         int s, n2;
@@ -109,18 +145,23 @@ __device__ __forceinline__ void fft_pass1(int nseq, const float2* tw, int logNtw
         else { s = task / N2; n2 = task - s * N2; }
         float2 v[N1];
 #pragma unroll
-        for (int n1 = 0; n1 < N1; ++n1) v[n1] = ld(s, N2 * n1 + n2);
+        for (int n1 = 0; n1 < N1; ++n1) v[n1] = ld(s, n2, n1);
         dft_reg<N1, INV>(v);
         if (N2 > 1) {
 #pragma unroll
-            for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul(v[k1], tw_n<N, INV>(tw, logNtw, n2 * k1));
+            for (int k1 = 1; k1 < N1; ++k1) {
+                float2 w = t4[k1 * N2 + n2];
+                if (INV) w.y = -w.y;
+                v[k1] = cmul(v[k1], w);
+            }
         }
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) st(s, N2 * k1 + n2, v[k1]);
+        for (int k1 = 0; k1 < N1; ++k1) st(s, n2, k1, v[k1]);
     }
 }
 
-// Pass 2: st(s, k, q, value) receives X[k] (k = k1 + N1 k2) and its in-place position q.
+// Pass 2: ld(s, k1, n2) returns the pass-1 result at index N2 k1 + n2; st(s, k1, k2, v)
+// receives X[k1 + N1 k2], whose in-place position is N2 k1 + k2.
 template <int N1, int N2, bool INV, bool kSeqFast, class LD, class ST>
 __device__ __forceinline__ void fft_pass2(int nseq, LD ld, ST st) {
     const int ntask = nseq * N1;
@@ -130,10 +171,10 @@ __device__ __forceinline__ void fft_pass2(int nseq, LD ld, ST st) {
         else { s = task / N1; k1 = task - s * N1; }
         float2 w[N2];
 #pragma unroll
-        for (int n2 = 0; n2 < N2; ++n2) w[n2] = ld(s, N2 * k1 + n2);
+        for (int n2 = 0; n2 < N2; ++n2) w[n2] = ld(s, k1, n2);
         dft_reg<N2, INV>(w);
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) st(s, k1 + N1 * k2, N2 * k1 + k2, w[k2]);
+        for (int k2 = 0; k2 < N2; ++k2) st(s, k1, k2, w[k2]);
     }
 }
 

@@ -57,6 +57,7 @@ struct Geom {
     int TC, nchunk;                     // t rows per stage chunk (multiple of 15) and number of chunks
     int tables_smem;                    // stage tables staged in shared memory (else read from global)
     int Ntw, logNtw;                    // twiddle table length = max(H, W)
+    int lN1h, lN2h, lN1w, lN2w;         // log2 of the four-step splits of H and W
     int method, in_dtype;
     float eps, sense;                   // sense = +1 (CC-U maximum) or -1 (CC-SN minimum)
     float tau_int, tau0, tau1;          // guard thresholds, relative to sum w|X|
@@ -165,6 +166,8 @@ struct Smem {
     unsigned char* r1;     // start of R1
     size_t r12_bytes;      // bytes of R1 + R2
     float2* tw;            // Ntw/2
+    float2* t4h;           // H: four-step inter-pass twiddles of length H, [k1][n2]
+    float2* t4w;           // W: the same for length W
     int4* rowq;            // Hh/2: row offsets (x SA) of P(m1), P(m2), Q(m1), Q(m2)
     float* gP;             // T1p: g(+tx)
     float* gM;             // T1p: g(-tx)
@@ -199,19 +202,22 @@ __host__ __device__ inline SmemPlan smem_plan(const Geom& g) {
     p.tbs = p.tbc;
     p.uv = align_up(sizeof(float4) * (size_t)g.TC * g.SA, 16);
     // the P/Q build keeps R(kx), its 8 partial sums and the g partial sums here first
-    const size_t rscr = sizeof(float2) * ((size_t)g.Wcp + 8 * (size_t)(g.SA + 1)) + sizeof(float) * 8 * (size_t)g.T1p;
+    size_t rscr = sizeof(float2) * ((size_t)g.Wcp + 8 * (size_t)(g.SA + 1)) + sizeof(float) * 8 * (size_t)g.T1p;
+    // ... and afterwards the guard scratch (FP32 pair differences, or the FP64 diagnostic)
+    const size_t gscr = sizeof(float2) * (size_t)(7 * g.H + g.Wc + 6);
+    const size_t dscr = sizeof(double2) * (size_t)(2 * g.H + 2 * g.Wc);
+    if (rscr < gscr) rscr = gscr;
+    if (rscr < dscr) rscr = dscr;
     if (p.uv < rscr) p.uv = align_up(rscr, 16);
     p.uvn = align_up(sizeof(float4) * (size_t)g.TC, 16);
     const size_t k6 = p.ta + p.tbc + p.tbs + p.uv + p.uvn;
-    const size_t l1 = sizeof(float2) * (size_t)(3 * g.H + 2 * g.Wcp + 2) + sizeof(double2) * (size_t)(2 * g.H + 2 * g.Wc);
     p.r2 = fft > k6 ? fft : k6;
-    if (p.r2 < l1) p.r2 = align_up(l1, 16);
     // the double-float level needs H x Wcp dfc plus one packed-row chunk (2 rows of W dfc),
     // which later holds the H + Wc candidate twiddles
     const size_t chunk = 2 * (size_t)g.W > (size_t)(g.H + g.Wc) ? 2 * (size_t)g.W : (size_t)(g.H + g.Wc);
-    const size_t dfl = sizeof(dfc) * ((size_t)g.H * g.Wcp + chunk);
+    const size_t dfl = sizeof(dfc) * ((size_t)g.H * g.Wcp + (size_t)(g.Ntw / 2) + chunk);
     if (p.r1 + p.r2 < dfl) p.r2 = align_up(dfl - p.r1, 16);
-    p.misc = sizeof(double) * 32 + sizeof(float2) * (size_t)(g.Ntw / 2) + sizeof(int4) * (size_t)(g.Hh / 2) +
+    p.misc = sizeof(double) * 32 + sizeof(float2) * (size_t)(g.Ntw / 2 + g.H + g.W) + sizeof(int4) * (size_t)(g.Hh / 2) +
              sizeof(float) * 2 * (size_t)g.T1p + sizeof(float) * 64 + sizeof(int) * 64 +
              (sizeof(int) + sizeof(float)) * kMaxCand + sizeof(int) * 16 + 64;
     p.total = align_up(p.r1 + p.r2 + p.misc, 16);
@@ -236,6 +242,8 @@ static __device__ inline Smem carve(const Geom& g, unsigned char* base) {
     unsigned char* m = r2 + p.r2;
     s.rd = (double*)m; m += sizeof(double) * 32;
     s.tw = (float2*)m; m += sizeof(float2) * (g.Ntw / 2);
+    s.t4h = (float2*)m; m += sizeof(float2) * g.H;
+    s.t4w = (float2*)m; m += sizeof(float2) * g.W;
     s.rowq = (int4*)m; m += sizeof(int4) * (g.Hh / 2);
     s.gP = (float*)m; m += sizeof(float) * g.T1p;
     s.gM = (float*)m; m += sizeof(float) * g.T1p;
@@ -247,11 +255,20 @@ static __device__ inline Smem carve(const Geom& g, unsigned char* base) {
     return s;
 }
 
-// Positions: spectrum rows after the column passes, packed-row elements after the row passes.
-__device__ __forceinline__ int posH(const Geom& g, int ky) { return fft_pos(ky, split_n1(g.H), split_n2(g.H)); }
+// Positions: spectrum rows after the column passes, packed-row elements after the row passes
+// (all sizes are powers of two: shifts and masks).
+__device__ __forceinline__ int posH(const Geom& g, int ky) {
+    return ((ky & ((1 << g.lN1h) - 1)) << g.lN2h) | (ky >> g.lN1h);
+}
+__device__ __forceinline__ int posW(const Geom& g, int kx) {
+    return ((kx & ((1 << g.lN1w) - 1)) << g.lN2w) | (kx >> g.lN1w);
+}
+__device__ __forceinline__ int unposW(const Geom& g, int q) {
+    return ((q & ((1 << g.lN2w) - 1)) << g.lN1w) | (q >> g.lN2w);
+}
 __device__ __forceinline__ int physZ(const Geom& g, int q) {
-    const int n2 = split_n2(g.W);
-    return q + q / (n2 > 1 ? n2 : g.W);
+    const int lpg = g.lN2w > 0 ? g.lN2w : g.logW;      // padding group: N2, or W for one-pass rows
+    return q + (q >> lpg);
 }
 
 // ------------------------------------------------------- a1-a4: FFT correlation
@@ -299,46 +316,50 @@ static __device__ void fft_correlate_t(const Geom& g, const Smem& S, const void*
         }
     }
     __syncthreads();
+    // element n of a packed row sits at Z[r][n + n / PG]; for n = N2w a + b (b < N2w) that
+    // is (N2w + 1) a + b, linear in the unrolled index a
+    constexpr int RP = N2w > 1 ? N2w + 1 : 1;        // padded stride of a row-pass group
     // a2: row FFTs (forward), in place
     fft_pass1<N1w, N2w, false, false>(
-        Hh, S.tw, g.logNtw, [&](int s, int q) { return Z[s * SZ + zphys(q)]; },
-        [&](int s, int q, float2 v) { Z[s * SZ + zphys(q)] = v; });
+        Hh, S.t4w, [&](int s, int n2, int n1) { return Z[s * SZ + RP * n1 + n2]; },
+        [&](int s, int n2, int k1, float2 v) { Z[s * SZ + RP * k1 + n2] = v; });
     __syncthreads();
     if (N2w > 1) {
         fft_pass2<N1w, N2w, false, false>(
-            Hh, [&](int s, int q) { return Z[s * SZ + zphys(q)]; },
-            [&](int s, int k, int q, float2 v) { Z[s * SZ + zphys(q)] = v; });
+            Hh, [&](int s, int k1, int n2) { return Z[s * SZ + RP * k1 + n2]; },
+            [&](int s, int k1, int k2, float2 v) { Z[s * SZ + RP * k1 + k2] = v; });
         __syncthreads();
     }
-    // column pass 1 (forward) with the real/complex split fused into the loads.
-    // Slot 0 carries the DC and Nyquist columns as one complex column (both are real
-    // sequences along y for real rows).
-    auto zrow = [&](int r, int k) { return Z[r * SZ + zphys(fft_pos(k, N1w, N2w))]; };
+    // Z_r(k) now sits at Z[r][zphys(fft_pos(k))]. Column pass 1 (forward) with the
+    // real/complex split fused into the loads; slot 0 carries the DC and Nyquist columns
+    // as one complex column (both are real sequences along y for real rows).
     fft_pass1<N1h, N2h, false, true>(
-        SA, S.tw, g.logNtw,
-        [&](int s, int y) {
-            const int r = y >> 1;
+        SA, S.t4h,
+        [&](int s, int n2, int n1) {
+            const int y = N2h * n1 + n2;
+            const float2* zr = Z + (y >> 1) * SZ;
             if (s == 0) {
-                const float2 z0 = zrow(r, 0), zn = zrow(r, W / 2);
+                const float2 z0 = zr[0], zn = zr[zphys(fft_pos(W / 2, N1w, N2w))];
                 return (y & 1) ? make_float2(z0.y, zn.y) : make_float2(z0.x, zn.x);
             }
-            const float2 z = zrow(r, s), zc = zrow(r, W - s);   // zc not yet conjugated
+            const float2 z = zr[zphys(fft_pos(s, N1w, N2w))], zc = zr[zphys(fft_pos(W - s, N1w, N2w))];
             if (y & 1) return make_float2(0.5f * (z.y + zc.y), -0.5f * (z.x - zc.x));   // (z - conj zc)/(2i)
             return make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y));               // (z + conj zc)/2
         },
-        [&](int s, int q, float2 v) { A[q * SA + s] = v; });
+        [&](int s, int n2, int k1, float2 v) { A[(N2h * k1 + n2) * SA + s] = v; });
     __syncthreads();
     // column pass 2 + a3: product with conj(F[b]) (slot 0 is unpacked afterwards)
     float sabs = 0.f;
     fft_pass2<N1h, N2h, false, true>(
-        SA, [&](int s, int q) { return A[q * SA + s]; },
-        [&](int s, int ky, int q, float2 v) {
+        SA, [&](int s, int k1, int n2) { return A[(N2h * k1 + n2) * SA + s]; },
+        [&](int s, int k1, int k2, float2 v) {
             if (s != 0) {
+                const int ky = k1 + N1h * k2;
                 const float2 x = cmul(v, cconj(__ldg(&g.FE32[ky * (W / 2 + 1) + s])));
                 sabs += 2.f * (fabsf(x.x) + fabsf(x.y));
                 v = x;
             }
-            A[q * SA + s] = v;
+            A[(N2h * k1 + k2) * SA + s] = v;
         });
     __syncthreads();
     // unpack slot 0 into X(ky, 0) (kept in slot 0) and X(ky, W/2) (in XN)
@@ -358,40 +379,48 @@ static __device__ void fft_correlate_t(const Geom& g, const Smem& S, const void*
     for (int q = threadIdx.x; q < H; q += blockDim.x) A[q * SA] = B[q];
     __syncthreads();
     *scale_out = block_sum(sabs, S.rv);
-    // a4: inverse column pass 1 (slot 0 packs X(.,0) + i X(.,W/2), whose transforms are real)
+    // a4: inverse column pass 1 (slot 0 packs X(.,0) + i X(.,W/2), whose transforms are real).
+    // X(ky) sits at row fft_pos(ky); ky = N2h n1 + n2.
     fft_pass1<N1h, N2h, true, true>(
-        SA, S.tw, g.logNtw,
-        [&](int s, int ky) {
-            const int q = fft_pos(ky, N1h, N2h);
+        SA, S.t4h,
+        [&](int s, int n2, int n1) {
+            const int q = fft_pos(N2h * n1 + n2, N1h, N2h);
             if (s == 0) {
                 const float2 a = A[q * SA], n = XN[q];
                 return make_float2(a.x - n.y, a.y + n.x);
             }
             return A[q * SA + s];
         },
-        [&](int s, int q, float2 v) { B[q * SA + s] = v; });
+        [&](int s, int n2, int k1, float2 v) { B[(N2h * k1 + n2) * SA + s] = v; });
     __syncthreads();
     fft_pass2<N1h, N2h, true, true>(
-        SA, [&](int s, int q) { return B[q * SA + s]; }, [&](int s, int y, int q, float2 v) { B[q * SA + s] = v; });
+        SA, [&](int s, int k1, int n2) { return B[(N2h * k1 + n2) * SA + s]; },
+        [&](int s, int k1, int k2, float2 v) { B[(N2h * k1 + k2) * SA + s] = v; });
     __syncthreads();
-    // C2R rows: packed row r = Y(2r,.) + i Y(2r+1,.), Hermitian extension for kx > W/2
+    // C2R rows: packed row r = Y(2r,.) + i Y(2r+1,.), Hermitian extension for kx > W/2.
+    // kx = N2w n1 + n2 lies below W/2 exactly when n1 < N1w/2.
     fft_pass1<N1w, N2w, true, false>(
-        Hh, S.tw, g.logNtw,
-        [&](int r, int kx) {
-            const int qe = fft_pos(2 * r, N1h, N2h), qo = fft_pos(2 * r + 1, N1h, N2h);
+        Hh, S.t4w,
+        [&](int r, int n2, int n1) {
+            const float2* be = B + fft_pos(2 * r, N1h, N2h) * SA;
+            const float2* bo = B + fft_pos(2 * r + 1, N1h, N2h) * SA;
+            const int kx = N2w * n1 + n2;
             float2 ye, yo;
-            if (kx == 0) { ye = make_float2(B[qe * SA].x, 0.f); yo = make_float2(B[qo * SA].x, 0.f); }
-            else if (2 * kx == W) { ye = make_float2(B[qe * SA].y, 0.f); yo = make_float2(B[qo * SA].y, 0.f); }
-            else if (2 * kx < W) { ye = B[qe * SA + kx]; yo = B[qo * SA + kx]; }
-            else { ye = cconj(B[qe * SA + (W - kx)]); yo = cconj(B[qo * SA + (W - kx)]); }
+            if (2 * n1 < N1w) {
+                if (kx == 0) { ye = make_float2(be[0].x, 0.f); yo = make_float2(bo[0].x, 0.f); }
+                else { ye = be[kx]; yo = bo[kx]; }
+            } else {
+                if (2 * kx == W) { ye = make_float2(be[0].y, 0.f); yo = make_float2(bo[0].y, 0.f); }
+                else { ye = cconj(be[W - kx]); yo = cconj(bo[W - kx]); }
+            }
             return make_float2(ye.x - yo.y, ye.y + yo.x);
         },
-        [&](int r, int q, float2 v) { Z[r * SZ + zphys(q)] = v; });
+        [&](int r, int n2, int k1, float2 v) { Z[r * SZ + RP * k1 + n2] = v; });
     __syncthreads();
     if (N2w > 1) {
         fft_pass2<N1w, N2w, true, false>(
-            Hh, [&](int s, int q) { return Z[s * SZ + zphys(q)]; },
-            [&](int s, int k, int q, float2 v) { Z[s * SZ + zphys(q)] = v; });
+            Hh, [&](int s, int k1, int n2) { return Z[s * SZ + RP * k1 + n2]; },
+            [&](int s, int k1, int k2, float2 v) { Z[s * SZ + RP * k1 + k2] = v; });
         __syncthreads();
     }
 }
@@ -399,7 +428,7 @@ static __device__ void fft_correlate_t(const Geom& g, const Smem& S, const void*
 // Integer surface HW*c(y, x) from the packed-row buffer.
 __device__ __forceinline__ float int_surface(const Geom& g, const Smem& S, int flat) {
     const int y = flat >> g.logW, x = flat & (g.W - 1);
-    const float2 z = S.ZC[(y >> 1) * g.SZ + physZ(g, fft_pos(x, split_n1(g.W), split_n2(g.W)))];
+    const float2 z = S.ZC[(y >> 1) * g.SZ + physZ(g, posW(g, x))];
     return (y & 1) ? z.y : z.x;
 }
 
@@ -425,11 +454,11 @@ __device__ __forceinline__ int integer_peak(const Geom& g, const Smem& S, const 
                                             float scale, unsigned* flags, float* dbg) {
     TopK<2> t2;
     t2.init();
-    const int W = g.W, n1 = split_n1(W), n2 = split_n2(W);
+    const int W = g.W;
     for (int idx = threadIdx.x; idx < (g.H / 2) * W; idx += blockDim.x) {
         const int r = idx >> g.logW, q = idx & (W - 1);
         const float2 z = S.ZC[r * g.SZ + physZ(g, q)];
-        const int x = fft_unpos(q, n1, n2);
+        const int x = unposW(g, q);
         const int fe = (2 * r) * W + x, fo = fe + W;
         if (dbg) { dbg[fe] = z.x; dbg[fo] = z.y; }
         t2.push(g.sense * z.x, fe);
@@ -624,8 +653,9 @@ __device__ __forceinline__ void stage_a(const Geom& g, const Smem& S, int t0, co
             const float4* tab = tA2 + (size_t)(t0 - 1 + lt0) * Hq;
             for (int mp = Hq - 1; mp >= 0; --mp) {
                 const int4 ro = S.rowq[mp];
-                const float2 p1 = S.XN[ro.x / SA], p2 = S.XN[ro.y / SA], q1 = S.XN[ro.z / SA];
-                const float2 q2 = (2 * mp + 2 == Hh) ? make_float2(-p2.x, -p2.y) : S.XN[ro.w / SA];
+                const int lsa = g.logW - 1;                       // SA = W/2
+                const float2 p1 = S.XN[ro.x >> lsa], p2 = S.XN[ro.y >> lsa], q1 = S.XN[ro.z >> lsa];
+                const float2 q2 = (2 * mp + 2 == Hh) ? make_float2(-p2.x, -p2.y) : S.XN[ro.w >> lsa];
 #pragma unroll
                 for (int i = 0; i < 5; ++i) {
                     const float4 tw = tab[i * Hq + mp];
@@ -778,67 +808,87 @@ __device__ __forceinline__ float2 table_twiddle_y(const Geom& g, int ks, int t) 
 // Decide among the candidates S.cj[0..nc) (S.cj[0] is the FP32 best j1) with exact
 // pair differences D(j) = v(j) - v(j1). Returns the winner; sets *nl2 when the two
 // best remain within tau1, leaving the tied candidates in S.cj[0..*nl2).
+// Every row sum is split four ways over the CTA; the stage-B tables are read from
+// where the contraction left them. Scratch: the UV area (dead after stage B).
 static __device__ int pair_difference_guard(const Geom& g, const Smem& S, int nc, float scale, int* nl2,
-                                     float* dwin) {
-    const int H = g.H, Wc = g.Wc, Wcp = g.Wcp, u = g.u;
-    float2* G = (float2*)S.TA;         // H      G(ky) = sum_kx w X'(ky,kx) E(kx, rx)  (R2 is free here)
+                                            float* dwin) {
+    const int H = g.H, Wc = g.Wc, u = g.u, Hh = g.Hh, T1p = g.T1p;
+    const float* TBc = g.tables_smem ? S.TBc : g.tB_wc;
+    const float* TBs = g.tables_smem ? S.TBs : g.tB_ws;
+    float2* G = (float2*)S.UV;         // H      G(ky) = sum_kx w X'(ky,kx) E(kx, rx)
     float2* Eyc = G + H;               // H      E(ky, ty_c)
     float2* dEy = Eyc + H;             // H      E(ky, ty_c) - E(ky, ry)
-    float2* dEx = dEy + H;             // Wcp    w (E(kx, tx_c) - E(kx, rx))
-    float2* GN = dEx + Wcp;            // 1      the Nyquist row's x-Nyquist term of G
+    float2* dEx = dEy + H;             // Wc     w (E(kx, tx_c) - E(kx, rx))
+    float2* GN = dEx + Wc;             // 1      the Nyquist row's x-Nyquist term of G
+    float2* part = GN + 1;             // 4 x H  partial row sums
+    float2* partN = part + 4 * H;      // 4      partial x-Nyquist terms of the Nyquist row
     const int j1 = S.cj[0];
     const int ry = j1 / g.M - g.h0, rx = j1 % g.M - g.h0;
     const int kn = g.W >> 1;
-    for (int ky = threadIdx.x; ky < H; ky += blockDim.x) {
-        float2 acc = make_float2(0.f, 0.f), accn = make_float2(0.f, 0.f);
-        const int arx = rx < 0 ? -rx : rx;
-        for (int kx = Wc - 1; kx >= 0; --kx) {
-            const float c = __ldg(&g.tB_wc[kx * g.T1p + arx]);
-            float s = __ldg(&g.tB_ws[kx * g.T1p + arx]);
-            if (rx < 0) s = -s;
-            const float2 t = cmul(xprime(g, S, ky, kx), make_float2(c, s));
-            if (ky == g.Hh && kx == kn) accn = t; else acc = cadd(acc, t);
+    const int arx = rx < 0 ? -rx : rx;
+    // row sums over kx of X'(ky, kx) * f(kx), split into 4 interleaved parts
+    auto row_sums = [&](auto factor) {
+        for (int task = threadIdx.x; task < 4 * H; task += blockDim.x) {
+            const int q = task / H, ky = task - q * H;
+            float2 acc = make_float2(0.f, 0.f), accn = make_float2(0.f, 0.f);
+            for (int kx = Wc - 1 - q; kx >= 0; kx -= 4) {
+                const float2 t = cmul(xprime(g, S, ky, kx), factor(kx));
+                if (ky == Hh && kx == kn) accn = t; else acc = cadd(acc, t);
+            }
+            part[q * H + ky] = acc;
+            if (ky == Hh) partN[q] = accn;
         }
-        G[ky] = acc;
-        if (ky == g.Hh) GN[0] = accn;
-    }
-    __syncthreads();
+        __syncthreads();
+    };
+    auto fold = [&](float2* dst, float2* dstN) {
+        for (int ky = threadIdx.x; ky < H; ky += blockDim.x) {
+            dst[ky] = cadd(cadd(part[ky], part[H + ky]), cadd(part[2 * H + ky], part[3 * H + ky]));
+            if (ky == Hh) *dstN = cadd(cadd(partN[0], partN[1]), cadd(partN[2], partN[3]));
+        }
+        __syncthreads();
+    };
+    row_sums([&](int kx) {
+        const float c = TBc[kx * T1p + arx];
+        const float s = TBs[kx * T1p + arx];
+        return make_float2(c, rx < 0 ? -s : s);
+    });
+    fold(G, GN);
     if (threadIdx.x == 0) S.cv[0] = 0.f;
     for (int c = 1; c < nc; ++c) {
         const int jc = S.cj[c];
         const int ty = jc / g.M - g.h0, tx = jc % g.M - g.h0;
-        for (int ky = threadIdx.x; ky < H; ky += blockDim.x) {
-            const int ks = signed_k(ky, H);
-            Eyc[ky] = table_twiddle_y(g, ks, ty);
-            // E(ty) - E(ry) = 2i sin(pi k'(ty - ry)/(uH)) exp(i pi k'(ty + ry)/(uH))
-            const float s1 = sin_pi_frac((long long)ks * (ty - ry), (long long)u * H);
-            const float2 e2 = expi_pi_frac((long long)ks * (ty + ry), (long long)u * H);
-            dEy[ky] = make_float2(-2.f * s1 * e2.y, 2.f * s1 * e2.x);
-        }
-        for (int kx = threadIdx.x; kx < Wc; kx += blockDim.x) {
-            const int ks = signed_k(kx, g.W);
-            const float w = (kx == 0 || 2 * kx == g.W) ? 1.f : 2.f;
-            const float s1 = sin_pi_frac((long long)ks * (tx - rx), (long long)u * g.W);
-            const float2 e2 = expi_pi_frac((long long)ks * (tx + rx), (long long)u * g.W);
-            dEx[kx] = make_float2(-2.f * w * s1 * e2.y, 2.f * w * s1 * e2.x);
+        for (int k = threadIdx.x; k < H + Wc; k += blockDim.x) {
+            if (k < H) {
+                const int ks = signed_k(k, H);
+                Eyc[k] = table_twiddle_y(g, ks, ty);
+                // E(ty) - E(ry) = 2i sin(pi k'(ty - ry)/(uH)) exp(i pi k'(ty + ry)/(uH))
+                const float s1 = sin_pi_frac((long long)ks * (ty - ry), (long long)u * H);
+                const float2 e2 = expi_pi_frac((long long)ks * (ty + ry), (long long)u * H);
+                dEy[k] = make_float2(-2.f * s1 * e2.y, 2.f * s1 * e2.x);
+            } else {
+                const int kx = k - H;
+                const int ks = signed_k(kx, g.W);
+                const float w = (kx == 0 || 2 * kx == g.W) ? 1.f : 2.f;
+                const float s1 = sin_pi_frac((long long)ks * (tx - rx), (long long)u * g.W);
+                const float2 e2 = expi_pi_frac((long long)ks * (tx + rx), (long long)u * g.W);
+                dEx[kx] = make_float2(-2.f * w * s1 * e2.y, 2.f * w * s1 * e2.x);
+            }
         }
         __syncthreads();
-        float part = 0.f;
+        row_sums([&](int kx) { return dEx[kx]; });
+        float acc = 0.f;
         for (int ky = threadIdx.x; ky < H; ky += blockDim.x) {
-            float2 F = make_float2(0.f, 0.f), FN = make_float2(0.f, 0.f);
-            for (int kx = Wc - 1; kx >= 0; --kx) {
-                const float2 t = cmul(xprime(g, S, ky, kx), dEx[kx]);
-                if (ky == g.Hh && kx == kn) FN = t; else F = cadd(F, t);
-            }
-            if (ky == g.Hh) {
+            const float2 F = cadd(cadd(part[ky], part[H + ky]), cadd(part[2 * H + ky], part[3 * H + ky]));
+            if (ky == Hh) {
+                const float2 FN = cadd(cadd(partN[0], partN[1]), cadd(partN[2], partN[3]));
                 // real part of the row's y-phase, except in the x-Nyquist column
-                part += Eyc[ky].x * F.x + dEy[ky].x * G[ky].x;
-                part += cmul(Eyc[ky], FN).x + cmul(dEy[ky], GN[0]).x;
+                acc += Eyc[ky].x * F.x + dEy[ky].x * G[ky].x;
+                acc += cmul(Eyc[ky], FN).x + cmul(dEy[ky], GN[0]).x;
             } else {
-                part += cmul(Eyc[ky], F).x + cmul(dEy[ky], G[ky]).x;
+                acc += cmul(Eyc[ky], F).x + cmul(dEy[ky], G[ky]).x;
             }
         }
-        const float D = block_sum(part, S.rv);
+        const float D = block_sum(acc, S.rv);
         if (threadIdx.x == 0) S.cv[c] = g.sense * D;
         __syncthreads();
     }
@@ -874,10 +924,10 @@ static __device__ int pair_difference_guard(const Geom& g, const Smem& S, int nc
 }
 
 // v(jb) - v(ja) from the FP32 X' in shared memory, with FP64 twiddles and FP64
-// accumulation (the Nyquist-row rule included). Scratch: the start of R2.
+// accumulation (the Nyquist-row rule included). Scratch: the UV area.
 static __device__ double pair_difference_f64(const Geom& g, const Smem& S, int ja, int jb, double* red) {
     const int H = g.H, Wc = g.Wc;
-    double2* eyA = (double2*)(S.TA);
+    double2* eyA = (double2*)(S.UV);
     double2* eyB = eyA + H;
     double2* exA = eyB + H;
     double2* exB = exA + Wc;
@@ -949,8 +999,10 @@ static __device__ int df_reevaluate(const Geom& g, const Smem& S, const void* fr
                              int py, int px, int nc, double* val) {
     const int H = g.H, W = g.W, Wc = g.Wc, Wcp = g.Wcp, Hh = g.Hh;
     dfc* Xd = (dfc*)S.r1;
-    dfc* Zc = Xd + (size_t)H * Wcp;
-    const long long cbytes = (long long)S.r12_bytes - (long long)sizeof(dfc) * H * Wcp;
+    dfc* twd = Xd + (size_t)H * Wcp;           // Ntw/2 FFT twiddles, staged from global
+    dfc* Zc = twd + g.Ntw / 2;
+    const long long cbytes = (long long)S.r12_bytes - (long long)sizeof(dfc) * ((long long)H * Wcp + g.Ntw / 2);
+    for (int k2 = threadIdx.x; k2 < g.Ntw / 2; k2 += blockDim.x) twd[k2] = g.twdf[k2];
     int R = 1;
     while (2 * R <= Hh && 2LL * R * W * (long long)sizeof(dfc) <= cbytes) R *= 2;
     for (int r0 = 0; r0 < Hh; r0 += R) {
@@ -969,7 +1021,7 @@ static __device__ int df_reevaluate(const Geom& g, const Smem& S, const void* fr
             if (y & 1) z->im = a; else z->re = a;
         }
         __syncthreads();
-        fft_r2_passes(Zc, g.logW, R, W, 1, g.twdf, g.logNtw, false);
+        fft_r2_passes(Zc, g.logW, R, W, 1, twd, g.logNtw, false);
         for (int idx = threadIdx.x; idx < R * Wcp; idx += blockDim.x) {
             const int rl = idx / Wcp, kx = idx - rl * Wcp;
             dfc fe = {{0.f, 0.f}, {0.f, 0.f}}, fo = fe;
@@ -986,7 +1038,7 @@ static __device__ int df_reevaluate(const Geom& g, const Smem& S, const void* fr
         }
         __syncthreads();
     }
-    fft_r2_passes(Xd, g.logH, Wc, 1, Wcp, g.twdf, g.logNtw, false);
+    fft_r2_passes(Xd, g.logH, Wc, 1, Wcp, twd, g.logNtw, false);
     for (int idx = threadIdx.x; idx < H * Wc; idx += blockDim.x) {
         const int ky = idx / Wc, kx = idx - ky * Wc;
         Xd[ky * Wcp + kx] = cmul(Xd[ky * Wcp + kx], cconj(g.FEdf[idx]));
@@ -1040,6 +1092,9 @@ __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Smem S = carve(g, smem_raw);
     for (int k = threadIdx.x; k < g.Ntw / 2; k += blockDim.x) S.tw[k] = g.tw32[k];
+    __syncthreads();
+    build_pass_twiddles<H>(S.t4h, S.tw, g.logNtw);
+    build_pass_twiddles<W>(S.t4w, S.tw, g.logNtw);
     for (int mp = threadIdx.x; mp < g.Hh / 2; mp += blockDim.x) {
         const int m1 = 2 * mp + 1, m2 = 2 * mp + 2;
         S.rowq[mp] = make_int4(posH(g, m1) * g.SA, posH(g, m2) * g.SA, posH(g, g.H - m1) * g.SA,
