@@ -123,7 +123,7 @@ __device__ __forceinline__ float2 tw_n(const float2* tw, int logNtw, int e) {
 // lanes of a warp, which differ in n2 or share it, read distinct banks or broadcast.
 template <int N>
 __device__ __forceinline__ void build_pass_twiddles(float2* t4, const float2* tw, int logNtw) {
-    constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+    constexpr int N2 = Split<N>::N2;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         const int k1 = i / N2, n2 = i - k1 * N2;
         t4[i] = tw_n<N, false>(tw, logNtw, n2 * k1);

@@ -47,6 +47,10 @@
 
 namespace ccst {
 
+// g(+-tx) row sums: partial sums per tx, each of at most kGTerms table terms
+// (kGParts * kGTerms >= W/2 + 1 for W <= 128)
+constexpr int kGParts = 6, kGTerms = 11;
+
 struct Geom {
     int H, W, logH, logW, Hh, Wc, Wcp;  // Wc = W/2+1 (half spectrum), Wcp = Wc rounded up to even
     int SA;                             // column slots of the spectrum buffer: W/2 (slot 0 = DC, + Nyquist array)
@@ -202,7 +206,7 @@ __host__ __device__ inline SmemPlan smem_plan(const Geom& g) {
     p.tbs = p.tbc;
     p.uv = align_up(sizeof(float4) * (size_t)g.TC * g.SA, 16);
     // the P/Q build keeps R(kx), its 8 partial sums and the g partial sums here first
-    size_t rscr = sizeof(float2) * ((size_t)g.Wcp + 8 * (size_t)(g.SA + 1)) + sizeof(float) * 8 * (size_t)g.T1p;
+    size_t rscr = sizeof(float2) * ((size_t)g.Wcp + 8 * (size_t)(g.SA + 1)) + sizeof(float) * 2 * kGParts * (size_t)g.T1p;
     // ... and afterwards the guard scratch (FP32 pair differences, or the FP64 diagnostic)
     const size_t gscr = sizeof(float2) * (size_t)(7 * g.H + g.Wc + 6);
     const size_t dscr = sizeof(double2) * (size_t)(2 * g.H + 2 * g.Wc);
@@ -272,9 +276,11 @@ __device__ __forceinline__ int physZ(const Geom& g, int q) {
 }
 
 // ------------------------------------------------------- a1-a4: FFT correlation
+// Also scans the integer surface as the last inverse pass stores it: t2 receives each
+// thread's two best (sense * HW c(y, x), y * W + x); dbg, if set, the whole surface.
 template <int H, int W>
 static __device__ void fft_correlate_t(const Geom& g, const Smem& S, const void* frame, long long pitch, int vec_ok,
-                                float* scale_out) {
+                                float* scale_out, TopK<2>& t2, float* dbg) {
     constexpr int N1w = Split<W>::N1, N2w = Split<W>::N2, N1h = Split<H>::N1, N2h = Split<H>::N2;
     constexpr int Hh = H / 2, SA = W / 2;
     constexpr int PG = N2w > 1 ? N2w : W;          // padding group of the packed rows
@@ -397,6 +403,14 @@ static __device__ void fft_correlate_t(const Geom& g, const Smem& S, const void*
         SA, [&](int s, int k1, int n2) { return B[(N2h * k1 + n2) * SA + s]; },
         [&](int s, int k1, int k2, float2 v) { B[(N2h * k1 + k2) * SA + s] = v; });
     __syncthreads();
+    // packed row r holds HW c(2r, x) + i HW c(2r+1, x) once the row passes are done
+    t2.init();
+    auto scan = [&](int r, int x, float2 v) {
+        const int fe = (2 * r) * W + x;
+        if (dbg) { dbg[fe] = v.x; dbg[fe + W] = v.y; }
+        t2.push(g.sense * v.x, fe);
+        t2.push(g.sense * v.y, fe + W);
+    };
     // C2R rows: packed row r = Y(2r,.) + i Y(2r+1,.), Hermitian extension for kx > W/2.
     // kx = N2w n1 + n2 lies below W/2 exactly when n1 < N1w/2.
     fft_pass1<N1w, N2w, true, false>(
@@ -415,12 +429,18 @@ static __device__ void fft_correlate_t(const Geom& g, const Smem& S, const void*
             }
             return make_float2(ye.x - yo.y, ye.y + yo.x);
         },
-        [&](int r, int n2, int k1, float2 v) { Z[r * SZ + RP * k1 + n2] = v; });
+        [&](int r, int n2, int k1, float2 v) {
+            Z[r * SZ + RP * k1 + n2] = v;
+            if (N2w == 1) scan(r, k1, v);
+        });
     __syncthreads();
     if (N2w > 1) {
         fft_pass2<N1w, N2w, true, false>(
             Hh, [&](int s, int k1, int n2) { return Z[s * SZ + RP * k1 + n2]; },
-            [&](int s, int k1, int k2, float2 v) { Z[s * SZ + RP * k1 + k2] = v; });
+            [&](int s, int k1, int k2, float2 v) {
+                Z[s * SZ + RP * k1 + k2] = v;
+                scan(s, k1 + N1w * k2, v);
+            });
         __syncthreads();
     }
 }
@@ -448,22 +468,10 @@ static __device__ double direct_sum_f64(const Geom& g, const Smem& S, const void
 }
 
 // ------------------------------------------------------ a5: integer extremum
-// Scans the packed-row buffer in its storage order (row pairs, padded positions),
-// recovering each element's natural flat index for the tie rule.
+// t2: each thread's two best points of the integer surface (value, natural flat index),
+// collected while the inverse FFT stored them.
 __device__ __forceinline__ int integer_peak(const Geom& g, const Smem& S, const void* frame, long long pitch,
-                                            float scale, unsigned* flags, float* dbg) {
-    TopK<2> t2;
-    t2.init();
-    const int W = g.W;
-    for (int idx = threadIdx.x; idx < (g.H / 2) * W; idx += blockDim.x) {
-        const int r = idx >> g.logW, q = idx & (W - 1);
-        const float2 z = S.ZC[r * g.SZ + physZ(g, q)];
-        const int x = unposW(g, q);
-        const int fe = (2 * r) * W + x, fo = fe + W;
-        if (dbg) { dbg[fe] = z.x; dbg[fo] = z.y; }
-        t2.push(g.sense * z.x, fe);
-        t2.push(g.sense * z.y, fo);
-    }
+                                            float scale, unsigned* flags, const TopK<2>& t2) {
     float v1 = t2.v[0];
     int best = t2.j[0];
     block_argmax(v1, best, S.rv, S.rj);
@@ -527,6 +535,21 @@ static __device__ void build_pq_and_g(const Geom& g, const Smem& S, int py, int 
     const int H = g.H, W = g.W, SA = g.SA, Hh = g.Hh;
     const int pyy = py & (H - 1), pxx = px & (W - 1);
     const int ncol = SA + 1;          // slots 0..SA-1 and the Nyquist column
+    // g(+-tx) sums the gc and ws tables (global, L2-resident) against R: a thread's first
+    // task (part, tx) loads its kGTerms table entries now, so that their latency hides
+    // behind the P/Q build. Task (part, tx) covers kx = part + kGParts j.
+    const int ngt = kGParts * g.T1p;
+    float pgc[kGTerms], pws[kGTerms];
+    {
+        const int task = threadIdx.x, part = task / g.T1p, tx = task - part * g.T1p;
+#pragma unroll
+        for (int j = 0; j < kGTerms; ++j) {
+            const int kx = part + kGParts * j;
+            const bool ok = task < ngt && kx < g.Wc;
+            pgc[j] = ok ? __ldg(&g.tB_gc[kx * g.T1p + tx]) : 0.f;
+            pws[j] = ok ? __ldg(&g.tB_ws[kx * g.T1p + tx]) : 0.f;
+        }
+    }
     for (int idx = threadIdx.x; idx < (Hh + 1) * ncol; idx += blockDim.x) {
         const int m = idx / ncol, c = idx - m * ncol;
         const bool nyq = (c == SA);
@@ -573,16 +596,29 @@ static __device__ void build_pq_and_g(const Geom& g, const Smem& S, int py, int 
         R[c == SA ? W / 2 : c] = r;
     }
     __syncthreads();
-    // g(+-tx) = sum_kx gc Rr -+ ws Ri: 4 partial sums per tx, then totals
-    float* gpart = (float*)(Rp + 8 * ncol);          // [4][T1p][2]
-    const int nk = g.Wc;
-    for (int task = threadIdx.x; task < 4 * g.T1p; task += blockDim.x) {
+    // g(+-tx) = sum_kx gc Rr -+ ws Ri: kGParts partial sums per tx, then totals
+    float* gpart = (float*)(Rp + 8 * ncol);          // [kGParts][T1p][2]
+    for (int task = threadIdx.x; task < ngt; task += blockDim.x) {
         const int part = task / g.T1p, tx = task - part * g.T1p;
         float a = 0.f, b = 0.f;
-        for (int kx = nk - 1 - part; kx >= 0; kx -= 4) {
-            const float2 r = R[kx];
-            a = fmaf(__ldg(&g.tB_gc[kx * g.T1p + tx]), r.x, a);
-            b = fmaf(__ldg(&g.tB_ws[kx * g.T1p + tx]), r.y, b);
+        int kx = part + kGParts * (kGTerms - 1);
+        if (task == (int)threadIdx.x) {
+#pragma unroll
+            for (int j = kGTerms - 1; j >= 0; --j, kx -= kGParts) {
+                if (kx < g.Wc) {
+                    const float2 r = R[kx];
+                    a = fmaf(pgc[j], r.x, a);
+                    b = fmaf(pws[j], r.y, b);
+                }
+            }
+        } else {
+            for (; kx >= 0; kx -= kGParts) {
+                if (kx < g.Wc) {
+                    const float2 r = R[kx];
+                    a = fmaf(__ldg(&g.tB_gc[kx * g.T1p + tx]), r.x, a);
+                    b = fmaf(__ldg(&g.tB_ws[kx * g.T1p + tx]), r.y, b);
+                }
+            }
         }
         gpart[2 * task] = a;
         gpart[2 * task + 1] = b;
@@ -590,7 +626,7 @@ static __device__ void build_pq_and_g(const Geom& g, const Smem& S, int py, int 
     __syncthreads();
     for (int tx = threadIdx.x; tx < g.T1p; tx += blockDim.x) {
         float a = 0.f, b = 0.f;
-        for (int part = 3; part >= 0; --part) {
+        for (int part = kGParts - 1; part >= 0; --part) {
             a += gpart[2 * (part * g.T1p + tx)];
             b += gpart[2 * (part * g.T1p + tx) + 1];
         }
@@ -604,7 +640,7 @@ static __device__ void build_pq_and_g(const Geom& g, const Smem& S, int py, int 
 // UV[lt][slot] = (U'r, U'i, Vr, Vi)(t, kx) for t = t0 + lt, lt in [0, TC); UVN the
 // x-Nyquist column. Tiles: 5 t x 2 slots; the Nyquist column uses spare threads.
 __device__ __forceinline__ void stage_a(const Geom& g, const Smem& S, int t0, const float4* tA2) {
-    const int SA = g.SA, Hq = g.Hh / 2, H = g.H, Hh = g.Hh;
+    const int SA = g.SA, Hq = g.Hh / 2, Hh = g.Hh;
     const int ntt = g.TC / 5, nkk = SA / 2;
     const int nmain = ntt * nkk;
     const int ntask = nmain + ntt;                         // + x-Nyquist column in 5-row strips
@@ -1106,9 +1142,10 @@ __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
         const char* frame = (const char*)b.frames + (size_t)f * g.H * b.pitch * elem;
         unsigned flags = 0;
         float scale = 0.f;
-        fft_correlate_t<H, W>(g, S, frame, b.pitch, b.vec_ok, &scale);
-        const int ip = integer_peak(g, S, frame, b.pitch, scale, &flags,
-                                    b.dbg_int ? b.dbg_int + (size_t)f * g.H * g.W : nullptr);
+        TopK<2> t2;
+        fft_correlate_t<H, W>(g, S, frame, b.pitch, b.vec_ok, &scale, t2,
+                              b.dbg_int ? b.dbg_int + (size_t)f * g.H * g.W : nullptr);
+        const int ip = integer_peak(g, S, frame, b.pitch, scale, &flags, t2);
         const float c0 = int_surface(g, S, ip);           // HW * c(p)
         const int py = wrap_shift(ip >> g.logW, g.H), px = wrap_shift(ip & (g.W - 1), g.W);
         __syncthreads();
