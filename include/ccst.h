@@ -74,6 +74,8 @@ extern "C" {
 #define CCST_R_DF64        0x04u /* sub-pixel peak decided from a double-float (~48-bit) product spectrum */
 #define CCST_R_OVERFLOW    0x08u /* too many near-tied points to certify: the FP32 choice is reported */
 #define CCST_R_NONFINITE   0x10u /* the surface held no finite value (non-finite input) */
+#define CCST_R_TIMEOUT     0x20u /* a bounded wait inside the kernel gave up (the staged stage tables never
+                                    arrived); this frame and the rest of its CTA's frames are not tracked */
 
 typedef struct ccst_params {
     int32_t  upsample;   /* u >= 1, default 100 (Sec. III)                          */

@@ -152,6 +152,20 @@ struct TopK {
     }
 };
 
+// The best (value, index) under better() and the runner-up's value, branch-free. The
+// integer search needs the runner-up only to detect near ties.
+struct Best2 {
+    float v1, v2;
+    int j1;
+    __device__ __forceinline__ void init() { v1 = -INFINITY; v2 = -INFINITY; j1 = INT_MAX; }
+    __device__ __forceinline__ void push(float v, int j) {
+        const bool b = better(v, j, v1, j1);
+        v2 = b ? v1 : fmaxf(v2, v);
+        v1 = b ? v : v1;
+        j1 = b ? j : j1;
+    }
+};
+
 // Block-wide (value, index) maximum under better(); every thread gets it.
 // sv/sj: >= 32 entries of scratch.
 __device__ __forceinline__ void block_argmax(float& v, int& j, float* sv, int* sj) {

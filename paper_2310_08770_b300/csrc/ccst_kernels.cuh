@@ -178,6 +178,9 @@ struct Smem {
     float* rv;             // reduction scratch (floats)
     int* rj;               // reduction scratch (ints)
     double* rd;            // reduction scratch (doubles)
+    unsigned long long* bar;  // mbarrier of the bulk table copies
+    float2* ex;            // Wc: e^{2 pi i kx px / W} per column slot (slot W/2 = x-Nyquist column)
+    float2* ey;            // Hh + 1: e^{2 pi i m py / H}, m = 0 .. Hh
     int* cj;               // candidate list
     float* cv;             // candidate values
     int* misc;             // small broadcast ints
@@ -221,7 +224,8 @@ __host__ __device__ inline SmemPlan smem_plan(const Geom& g) {
     const size_t chunk = 2 * (size_t)g.W > (size_t)(g.H + g.Wc) ? 2 * (size_t)g.W : (size_t)(g.H + g.Wc);
     const size_t dfl = sizeof(dfc) * ((size_t)g.H * g.Wcp + (size_t)(g.Ntw / 2) + chunk);
     if (p.r1 + p.r2 < dfl) p.r2 = align_up(dfl - p.r1, 16);
-    p.misc = sizeof(double) * 32 + sizeof(float2) * (size_t)(g.Ntw / 2 + g.H + g.W) + sizeof(int4) * (size_t)(g.Hh / 2) +
+    p.misc = sizeof(double) * 32 + 16 + sizeof(float2) * (size_t)(g.Wc + g.Hh + 1) +
+             sizeof(float2) * (size_t)(g.Ntw / 2 + g.H + g.W) + sizeof(int4) * (size_t)(g.Hh / 2) +
              sizeof(float) * 2 * (size_t)g.T1p + sizeof(float) * 64 + sizeof(int) * 64 +
              (sizeof(int) + sizeof(float)) * kMaxCand + sizeof(int) * 16 + 64;
     p.total = align_up(p.r1 + p.r2 + p.misc, 16);
@@ -245,6 +249,9 @@ static __device__ inline Smem carve(const Geom& g, unsigned char* base) {
     s.r12_bytes = p.r1 + p.r2;
     unsigned char* m = r2 + p.r2;
     s.rd = (double*)m; m += sizeof(double) * 32;
+    s.bar = (unsigned long long*)m; m += 16;
+    s.ex = (float2*)m; m += sizeof(float2) * g.Wc;
+    s.ey = (float2*)m; m += sizeof(float2) * (g.Hh + 1);
     s.tw = (float2*)m; m += sizeof(float2) * (g.Ntw / 2);
     s.t4h = (float2*)m; m += sizeof(float2) * g.H;
     s.t4w = (float2*)m; m += sizeof(float2) * g.W;
@@ -277,10 +284,11 @@ __device__ __forceinline__ int physZ(const Geom& g, int q) {
 
 // ------------------------------------------------------- a1-a4: FFT correlation
 // Also scans the integer surface as the last inverse pass stores it: t2 receives each
-// thread's two best (sense * HW c(y, x), y * W + x); dbg, if set, the whole surface.
+// thread's best (sense * HW c(y, x), y * W + x) and runner-up value; dbg, if set, the
+// whole surface.
 template <int H, int W>
 static __device__ void fft_correlate_t(const Geom& g, const Smem& S, const void* frame, long long pitch, int vec_ok,
-                                float* scale_out, TopK<2>& t2, float* dbg) {
+                                float* scale_out, Best2& t2, float* dbg) {
     constexpr int N1w = Split<W>::N1, N2w = Split<W>::N2, N1h = Split<H>::N1, N2h = Split<H>::N2;
     constexpr int Hh = H / 2, SA = W / 2;
     constexpr int PG = N2w > 1 ? N2w : W;          // padding group of the packed rows
@@ -468,19 +476,18 @@ static __device__ double direct_sum_f64(const Geom& g, const Smem& S, const void
 }
 
 // ------------------------------------------------------ a5: integer extremum
-// t2: each thread's two best points of the integer surface (value, natural flat index),
-// collected while the inverse FFT stored them.
+// t2: each thread's best point of the integer surface (value, natural flat index) and its
+// runner-up value, collected while the inverse FFT stored them.
 __device__ __forceinline__ int integer_peak(const Geom& g, const Smem& S, const void* frame, long long pitch,
-                                            float scale, unsigned* flags, const TopK<2>& t2) {
-    float v1 = t2.v[0];
-    int best = t2.j[0];
+                                            float scale, unsigned* flags, const Best2& t2) {
+    float v1 = t2.v1;
+    int best = t2.j1;
     block_argmax(v1, best, S.rv, S.rj);
     if (!(v1 > -INFINITY)) { *flags |= 0x10u; return 0; }
     const float tau = g.tau_int * scale;
     if (!g.guard) return best;
     // unique unless some other shift lies within tau of the best
-    const int near = __syncthreads_count(t2.v[0] >= v1 - tau && t2.j[0] != best) +
-                     __syncthreads_count(t2.v[1] >= v1 - tau && t2.j[1] != best);
+    const int near = __syncthreads_count((t2.v1 >= v1 - tau && t2.j1 != best) || t2.v2 >= v1 - tau);
     if (near == 0) return best;
     // collect every integer shift within tau of the best
     if (threadIdx.x == 0) S.misc[0] = 0;
@@ -507,25 +514,45 @@ __device__ __forceinline__ int integer_peak(const Geom& g, const Smem& S, const 
     return bestj;
 }
 
-// Copy the stage tables into shared memory (asynchronous 16-byte copies).
-__device__ __forceinline__ void stage_tables_async(const Geom& g, const Smem& S) {
-    if (!g.tables_smem) return;
-    const int na = g.TAB * (g.Hh / 2);                 // float4
-    const int nb = g.Wc * g.T1p / 4;                   // float4 per table
-    for (int i = threadIdx.x; i < na + 2 * nb; i += blockDim.x) {
-        const void* src;
-        void* dst;
-        if (i < na) { src = g.tA2 + i; dst = S.TA + i; }
-        else if (i < na + nb) { src = (const float4*)g.tB_wc + (i - na); dst = (float4*)S.TBc + (i - na); }
-        else { src = (const float4*)g.tB_ws + (i - na - nb); dst = (float4*)S.TBs + (i - na - nb); }
-        const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
+// Stage tables -> shared memory by three bulk copies on the TMA engine (contiguous tables,
+// 16-byte aligned, sizes multiples of 16 bytes), completing on the mbarrier S.bar.
+__device__ __forceinline__ void tables_bar_init(const Smem& S) {
+    if (threadIdx.x == 0) {
+        const unsigned b = (unsigned)__cvta_generic_to_shared(S.bar);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(b) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
-__device__ __forceinline__ void stage_tables_wait(const Geom& g) {
-    if (!g.tables_smem) return;
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+// Issued by thread 0 after a __syncthreads that ends every generic access to the
+// destination area.
+__device__ __forceinline__ void stage_tables_async(const Geom& g, const Smem& S) {
+    if (!g.tables_smem || threadIdx.x != 0) return;
+    const unsigned na = 16u * (unsigned)(g.TAB * (g.Hh / 2)), nb = 4u * (unsigned)(g.Wc * g.T1p);
+    const unsigned b = (unsigned)__cvta_generic_to_shared(S.bar);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b), "r"(na + 2 * nb) : "memory");
+    const void* src[3] = {g.tA2, g.tB_wc, g.tB_ws};
+    const void* dst[3] = {S.TA, S.TBc, S.TBs};
+    const unsigned n[3] = {na, nb, nb};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const unsigned d = (unsigned)__cvta_generic_to_shared(dst[i]);
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                     ::"r"(d), "l"(src[i]), "r"(n[i]), "r"(b) : "memory");
+    }
+}
+// Waits for the copies of phase `parity`. Bounded: returns false if they have not landed
+// after ~2^22 polls (far beyond any real copy time), true otherwise.
+__device__ __forceinline__ bool stage_tables_wait(const Geom& g, const Smem& S, unsigned parity) {
+    if (!g.tables_smem) return true;
+    const unsigned b = (unsigned)__cvta_generic_to_shared(S.bar);
+    for (int it = 0; it < (1 << 22); ++it) {
+        unsigned done;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(b), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
 }
 
 // --------------------------------------------- a6 prologue: X' and P/Q, R, g
@@ -550,43 +577,47 @@ static __device__ void build_pq_and_g(const Geom& g, const Smem& S, int py, int 
             pws[j] = ok ? __ldg(&g.tB_ws[kx * g.T1p + tx]) : 0.f;
         }
     }
-    for (int idx = threadIdx.x; idx < (Hh + 1) * ncol; idx += blockDim.x) {
-        const int m = idx / ncol, c = idx - m * ncol;
-        const bool nyq = (c == SA);
-        const int kx = nyq ? W / 2 : c;
-        const int kxs = signed_k(kx, W);
-        const float2 ex = twiddle_pos(S.tw, (kxs * pxx) & (W - 1), g.logW, g.logNtw);
-        float2* colbase = nyq ? S.XN : S.A + c;
-        const int cstride = nyq ? 1 : SA;
-        if (m == 0 || m == Hh) {
-            const int kys = signed_k(m, H);
-            const float2 ey = twiddle_pos(S.tw, (kys * pyy) & (H - 1), g.logH, g.logNtw);
-            float2* r = colbase + posH(g, m) * cstride;
-            *r = cmul(*r, cmul(ey, ex));
+    // per-frame phase factors: ex(c) for the column slots, ey(m) for m = 0 .. Hh
+    // (ey(-m) = conj ey(m); the Nyquist row's factor (-1)^py is real)
+    for (int i = threadIdx.x; i < ncol + Hh + 1; i += blockDim.x) {
+        if (i < ncol) {
+            const int kx = (i == SA) ? W / 2 : i;
+            S.ex[i] = twiddle_pos(S.tw, (signed_k(kx, W) * pxx) & (W - 1), g.logW, g.logNtw);
         } else {
-            const float2 eyp = twiddle_pos(S.tw, (m * pyy) & (H - 1), g.logH, g.logNtw);
-            const float2 eym = twiddle_pos(S.tw, (-m * pyy) & (H - 1), g.logH, g.logNtw);
-            float2* rp = colbase + posH(g, m) * cstride;
-            float2* rm = colbase + posH(g, H - m) * cstride;
-            const float2 xp = cmul(*rp, cmul(eyp, ex));
-            const float2 xm = cmul(*rm, cmul(eym, ex));
-            *rp = cadd(xp, xm);
-            *rm = csub(xp, xm);
+            const int m = i - ncol;
+            S.ey[m] = twiddle_pos(S.tw, (signed_k(m, H) * pyy) & (H - 1), g.logH, g.logNtw);
         }
     }
     __syncthreads();
-    // R(kx) = X'(0) + sum_{m=1}^{Hh-1} P(m) + X'(Hh), in the (not yet used) UV area:
-    // 8 partial column sums per column, then the column totals
+    // X' = X e^{2 pi i k'.p/N} folded in place into P/Q rows, and 8 partial column sums of
+    // R(kx) = X'(0) + sum_{m=1}^{Hh-1} P(m) + X'(Hh). Task (part, c): rows m = part (mod 8).
     float2* R = (float2*)S.UV;
     float2* Rp = R + g.Wcp;                         // [8][ncol] partials
     for (int task = threadIdx.x; task < 8 * ncol; task += blockDim.x) {
         const int part = task / ncol, c = task - part * ncol;
         const bool nyq = (c == SA);
-        const float2* colbase = nyq ? S.XN : S.A + c;
+        float2* colbase = nyq ? S.XN : S.A + c;
         const int cstride = nyq ? 1 : SA;
+        const float2 ex = S.ex[c];
         float2 r = make_float2(0.f, 0.f);
-        for (int m = Hh - part; m >= 0; m -= 8)          // rows X'(Hh), P(Hh-1) .. P(1), X'(0)
-            r = cadd(r, colbase[posH(g, m) * cstride]);
+        for (int m = part; m <= Hh; m += 8) {
+            const float2 ey = S.ey[m];
+            if (m == 0 || m == Hh) {
+                float2* p = colbase + posH(g, m) * cstride;
+                const float2 x = cmul(*p, cmul(ey, ex));
+                *p = x;
+                r = cadd(r, x);
+            } else {
+                float2* rp = colbase + posH(g, m) * cstride;
+                float2* rm = colbase + posH(g, H - m) * cstride;
+                const float2 xp = cmul(*rp, cmul(ey, ex));
+                const float2 xm = cmul(*rm, cmul(cconj(ey), ex));
+                const float2 pm = cadd(xp, xm);
+                *rp = pm;
+                *rm = csub(xp, xm);
+                r = cadd(r, pm);
+            }
+        }
         Rp[part * ncol + c] = r;
     }
     __syncthreads();
@@ -1131,6 +1162,8 @@ __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
     __syncthreads();
     build_pass_twiddles<H>(S.t4h, S.tw, g.logNtw);
     build_pass_twiddles<W>(S.t4w, S.tw, g.logNtw);
+    tables_bar_init(S);
+    unsigned bar_parity = 0;
     for (int mp = threadIdx.x; mp < g.Hh / 2; mp += blockDim.x) {
         const int m1 = 2 * mp + 1, m2 = 2 * mp + 2;
         S.rowq[mp] = make_int4(posH(g, m1) * g.SA, posH(g, m2) * g.SA, posH(g, g.H - m1) * g.SA,
@@ -1142,7 +1175,7 @@ __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
         const char* frame = (const char*)b.frames + (size_t)f * g.H * b.pitch * elem;
         unsigned flags = 0;
         float scale = 0.f;
-        TopK<2> t2;
+        Best2 t2;
         fft_correlate_t<H, W>(g, S, frame, b.pitch, b.vec_ok, &scale, t2,
                               b.dbg_int ? b.dbg_int + (size_t)f * g.H * g.W : nullptr);
         const int ip = integer_peak(g, S, frame, b.pitch, scale, &flags, t2);
@@ -1151,8 +1184,19 @@ __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
         __syncthreads();
         stage_tables_async(g, S);                          // overlaps the P/Q build
         build_pq_and_g(g, S, py, px);
-        stage_tables_wait(g);
-        __syncthreads();
+        const bool staged = stage_tables_wait(g, S, bar_parity);
+        if (__syncthreads_or(!staged)) {
+            // the copies never completed: report it for this frame and stop this CTA, after
+            // one more bounded wait so that no copy is left writing into this CTA's memory
+            if (threadIdx.x == 0) {
+                (void)stage_tables_wait(g, S, bar_parity);
+                Result r{};
+                r.flags = flags | 0x20u;
+                b.out[f] = r;
+            }
+            return;
+        }
+        bar_parity ^= 1u;
         if (b.dbg_pairs) {
             const int ja = b.dbg_pairs[2 * f], jb = b.dbg_pairs[2 * f + 1];
             const double d64 = pair_difference_f64(g, S, ja, jb, S.rd);
