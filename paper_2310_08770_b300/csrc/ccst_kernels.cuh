@@ -211,7 +211,7 @@ __host__ __device__ inline SmemPlan smem_plan(const Geom& g) {
     // the P/Q build keeps R(kx), its 8 partial sums and the g partial sums here first
     size_t rscr = sizeof(float2) * ((size_t)g.Wcp + 8 * (size_t)(g.SA + 1)) + sizeof(float) * 2 * kGParts * (size_t)g.T1p;
     // ... and afterwards the guard scratch (FP32 pair differences, or the FP64 diagnostic)
-    const size_t gscr = sizeof(float2) * (size_t)(7 * g.H + g.Wc + 6);
+    const size_t gscr = sizeof(float2) * (size_t)(4 * g.Wc + 23 * g.H + 17);   // pair-difference guard
     const size_t dscr = sizeof(double2) * (size_t)(2 * g.H + 2 * g.Wc);
     if (rscr < gscr) rscr = gscr;
     if (rscr < dscr) rscr = dscr;
@@ -875,91 +875,150 @@ __device__ __forceinline__ float2 table_twiddle_y(const Geom& g, int ks, int t) 
 // Decide among the candidates S.cj[0..nc) (S.cj[0] is the FP32 best j1) with exact
 // pair differences D(j) = v(j) - v(j1). Returns the winner; sets *nl2 when the two
 // best remain within tau1, leaving the tied candidates in S.cj[0..*nl2).
-// Every row sum is split four ways over the CTA; the stage-B tables are read from
-// where the contraction left them. Scratch: the UV area (dead after stage B).
+//   v(j) - v(j1) = Re sum_ky [ Ey(ky, ty) F_j(ky) + (Ey(ky, ty) - Ey(ky, ry)) G(ky) ],
+//   G(ky) = sum_kx X'(ky, kx) w Ex(kx, rx),  F_j(ky) = sum_kx X'(ky, kx) w (Ex(kx, tx) - Ex(kx, rx)),
+// with both differences in the small-factor form 2i sin(a) e^{ib}. The row sums of up to
+// kPdGroup factor vectors share one sweep over X' (G rides along with the first group);
+// each row sum is split kPdParts ways over the CTA. Scratch: the UV area (dead after
+// stage B).
+constexpr int kPdGroup = 3, kPdParts = 4;
+
 static __device__ int pair_difference_guard(const Geom& g, const Smem& S, int nc, float scale, int* nl2,
                                             float* dwin) {
-    const int H = g.H, Wc = g.Wc, u = g.u, Hh = g.Hh, T1p = g.T1p;
+    const int H = g.H, Wc = g.Wc, u = g.u, Hh = g.Hh, T1p = g.T1p, SA = g.SA;
     const float* TBc = g.tables_smem ? S.TBc : g.tB_wc;
     const float* TBs = g.tables_smem ? S.TBs : g.tB_ws;
-    float2* G = (float2*)S.UV;         // H      G(ky) = sum_kx w X'(ky,kx) E(kx, rx)
-    float2* Eyc = G + H;               // H      E(ky, ty_c)
-    float2* dEy = Eyc + H;             // H      E(ky, ty_c) - E(ky, ry)
-    float2* dEx = dEy + H;             // Wc     w (E(kx, tx_c) - E(kx, rx))
-    float2* GN = dEx + Wc;             // 1      the Nyquist row's x-Nyquist term of G
-    float2* part = GN + 1;             // 4 x H  partial row sums
-    float2* partN = part + 4 * H;      // 4      partial x-Nyquist terms of the Nyquist row
+    constexpr int NF = kPdGroup + 1;
+    float2* fx = (float2*)S.UV;             // [NF][Wc]   factor vectors over kx (slot 0: G's)
+    float2* Eyc = fx + NF * Wc;             // [kPdGroup][H]  Ey(ky, ty)
+    float2* dEy = Eyc + kPdGroup * H;       // [kPdGroup][H]  Ey(ky, ty) - Ey(ky, ry)
+    float2* G = dEy + kPdGroup * H;         // [H]
+    float2* GN = G + H;                     // [1]  the Nyquist row's x-Nyquist term of G
+    float2* part = GN + 1;                  // [kPdParts][NF][H]
+    float2* partN = part + kPdParts * NF * H;   // [kPdParts][NF]
     const int j1 = S.cj[0];
     const int ry = j1 / g.M - g.h0, rx = j1 % g.M - g.h0;
     const int kn = g.W >> 1;
     const int arx = rx < 0 ? -rx : rx;
-    // row sums over kx of X'(ky, kx) * f(kx), split into 4 interleaved parts
-    auto row_sums = [&](auto factor) {
-        for (int task = threadIdx.x; task < 4 * H; task += blockDim.x) {
-            const int q = task / H, ky = task - q * H;
-            float2 acc = make_float2(0.f, 0.f), accn = make_float2(0.f, 0.f);
-            for (int kx = Wc - 1 - q; kx >= 0; kx -= 4) {
-                const float2 t = cmul(xprime(g, S, ky, kx), factor(kx));
-                if (ky == Hh && kx == kn) accn = t; else acc = cadd(acc, t);
-            }
-            part[q * H + ky] = acc;
-            if (ky == Hh) partN[q] = accn;
-        }
-        __syncthreads();
-    };
-    auto fold = [&](float2* dst, float2* dstN) {
-        for (int ky = threadIdx.x; ky < H; ky += blockDim.x) {
-            dst[ky] = cadd(cadd(part[ky], part[H + ky]), cadd(part[2 * H + ky], part[3 * H + ky]));
-            if (ky == Hh) *dstN = cadd(cadd(partN[0], partN[1]), cadd(partN[2], partN[3]));
-        }
-        __syncthreads();
-    };
-    row_sums([&](int kx) {
-        const float c = TBc[kx * T1p + arx];
-        const float s = TBs[kx * T1p + arx];
-        return make_float2(c, rx < 0 ? -s : s);
-    });
-    fold(G, GN);
     if (threadIdx.x == 0) S.cv[0] = 0.f;
-    for (int c = 1; c < nc; ++c) {
-        const int jc = S.cj[c];
-        const int ty = jc / g.M - g.h0, tx = jc % g.M - g.h0;
-        for (int k = threadIdx.x; k < H + Wc; k += blockDim.x) {
-            if (k < H) {
-                const int ks = signed_k(k, H);
-                Eyc[k] = table_twiddle_y(g, ks, ty);
+    for (int c0 = 1; c0 < nc; c0 += kPdGroup) {
+        const int ng = min(kPdGroup, nc - c0);
+        const bool first = (c0 == 1);
+        // factor vectors and y twiddles of this group (slot 0 = G's factor, first group only)
+        for (int k = threadIdx.x; k < ng * (H + Wc) + (first ? Wc : 0); k += blockDim.x) {
+            if (k >= ng * (H + Wc)) {
+                const int kx = k - ng * (H + Wc);
+                const float c = TBc[kx * T1p + arx], s = TBs[kx * T1p + arx];
+                fx[kx] = make_float2(c, rx < 0 ? -s : s);
+                continue;
+            }
+            const int ci = k / (H + Wc), kk = k - ci * (H + Wc);
+            const int jc = S.cj[c0 + ci];
+            const int ty = jc / g.M - g.h0, tx = jc % g.M - g.h0;
+            if (kk < H) {
+                const int ks = signed_k(kk, H);
+                Eyc[ci * H + kk] = table_twiddle_y(g, ks, ty);
                 // E(ty) - E(ry) = 2i sin(pi k'(ty - ry)/(uH)) exp(i pi k'(ty + ry)/(uH))
                 const float s1 = sin_pi_frac((long long)ks * (ty - ry), (long long)u * H);
                 const float2 e2 = expi_pi_frac((long long)ks * (ty + ry), (long long)u * H);
-                dEy[k] = make_float2(-2.f * s1 * e2.y, 2.f * s1 * e2.x);
+                dEy[ci * H + kk] = make_float2(-2.f * s1 * e2.y, 2.f * s1 * e2.x);
             } else {
-                const int kx = k - H;
+                const int kx = kk - H;
                 const int ks = signed_k(kx, g.W);
                 const float w = (kx == 0 || 2 * kx == g.W) ? 1.f : 2.f;
                 const float s1 = sin_pi_frac((long long)ks * (tx - rx), (long long)u * g.W);
                 const float2 e2 = expi_pi_frac((long long)ks * (tx + rx), (long long)u * g.W);
-                dEx[kx] = make_float2(-2.f * w * s1 * e2.y, 2.f * w * s1 * e2.x);
+                fx[(1 + ci) * Wc + kx] = make_float2(-2.f * w * s1 * e2.y, 2.f * w * s1 * e2.x);
             }
         }
         __syncthreads();
-        row_sums([&](int kx) { return dEx[kx]; });
-        float acc = 0.f;
-        for (int ky = threadIdx.x; ky < H; ky += blockDim.x) {
-            const float2 F = cadd(cadd(part[ky], part[H + ky]), cadd(part[2 * H + ky], part[3 * H + ky]));
-            if (ky == Hh) {
-                const float2 FN = cadd(cadd(partN[0], partN[1]), cadd(partN[2], partN[3]));
-                // real part of the row's y-phase, except in the x-Nyquist column
-                acc += Eyc[ky].x * F.x + dEy[ky].x * G[ky].x;
-                acc += cmul(Eyc[ky], FN).x + cmul(dEy[ky], GN[0]).x;
-            } else {
-                acc += cmul(Eyc[ky], F).x + cmul(dEy[ky], G[ky]).x;
+        // one sweep over X': row sums of the factor vectors f0 (first group) and f1..f_ng
+        const int fbeg = first ? 0 : 1, fend = 1 + ng;
+        for (int task = threadIdx.x; task < kPdParts * H; task += blockDim.x) {
+            const int q = task / H, ky = task - q * H;
+            // X'(ky, .) from the P/Q rows: X' = P (ky = 0, Hh), (P + Q)/2 (ky < Hh), (P - Q)/2
+            int ra, rb;
+            float sb;
+            if (ky == 0 || ky == Hh) { ra = posH(g, ky); rb = ra; sb = 0.f; }
+            else if (ky < Hh) { ra = posH(g, ky); rb = posH(g, H - ky); sb = 1.f; }
+            else { ra = posH(g, H - ky); rb = posH(g, ky); sb = -1.f; }
+            const float sa = (sb == 0.f) ? 1.f : 0.5f;
+            sb *= 0.5f;
+            float2 acc[NF], accn[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) { acc[f] = make_float2(0.f, 0.f); accn[f] = acc[f]; }
+            for (int kx = Wc - 1 - q; kx >= 0; kx -= kPdParts) {
+                float2 p, r;
+                if (kx == kn) { p = S.XN[ra]; r = S.XN[rb]; }
+                else { p = S.A[ra * SA + kx]; r = S.A[rb * SA + kx]; }
+                const float2 xp = make_float2(sa * p.x + sb * r.x, sa * p.y + sb * r.y);
+                const bool nn = (ky == Hh && kx == kn);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    if (f < fbeg || f >= fend) continue;
+                    const float2 t = cmul(xp, fx[f * Wc + kx]);
+                    if (nn) accn[f] = t; else acc[f] = cadd(acc[f], t);
+                }
+            }
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                if (f < fbeg || f >= fend) continue;
+                part[(q * NF + f) * H + ky] = acc[f];
+                if (ky == Hh) partN[q * NF + f] = accn[f];
             }
         }
-        const float D = block_sum(acc, S.rv);
-        if (threadIdx.x == 0) S.cv[c] = g.sense * D;
+        __syncthreads();
+        if (first) {
+            for (int ky = threadIdx.x; ky < H; ky += blockDim.x) {
+                float2 s = make_float2(0.f, 0.f);
+                for (int q = 0; q < kPdParts; ++q) s = cadd(s, part[q * NF * H + ky]);
+                G[ky] = s;
+                if (ky == Hh) {
+                    float2 sn = make_float2(0.f, 0.f);
+                    for (int q = 0; q < kPdParts; ++q) sn = cadd(sn, partN[q * NF]);
+                    *GN = sn;
+                }
+            }
+            __syncthreads();
+        }
+        // D for each candidate of the group: per-thread partial sums, then a block reduction
+        float acc[kPdGroup];
+#pragma unroll
+        for (int ci = 0; ci < kPdGroup; ++ci) acc[ci] = 0.f;
+        for (int ky = threadIdx.x; ky < H; ky += blockDim.x) {
+#pragma unroll
+            for (int ci = 0; ci < kPdGroup; ++ci) {
+                if (ci >= ng) continue;
+                const int f = 1 + ci;
+                float2 F = make_float2(0.f, 0.f);
+                for (int q = 0; q < kPdParts; ++q) F = cadd(F, part[(q * NF + f) * H + ky]);
+                const float2 ey = Eyc[ci * H + ky], dy = dEy[ci * H + ky];
+                if (ky == Hh) {
+                    float2 FN = make_float2(0.f, 0.f);
+                    for (int q = 0; q < kPdParts; ++q) FN = cadd(FN, partN[q * NF + f]);
+                    // real part of the row's y-phase, except in the x-Nyquist column
+                    acc[ci] += ey.x * F.x + dy.x * G[ky].x;
+                    acc[ci] += cmul(ey, FN).x + cmul(dy, GN[0]).x;
+                } else {
+                    acc[ci] += cmul(ey, F).x + cmul(dy, G[ky]).x;
+                }
+            }
+        }
+        // block sums of the group's values (S.rv holds kWarps x kPdGroup partials)
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+        for (int ci = 0; ci < kPdGroup; ++ci) {
+            const float v = warp_sum(acc[ci]);
+            if (lane == 0) S.rv[wid * kPdGroup + ci] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < ng) {
+            float D = 0.f;
+            for (int w = 0; w < nw; ++w) D += S.rv[w * kPdGroup + threadIdx.x];
+            S.cv[c0 + threadIdx.x] = g.sense * D;
+        }
         __syncthreads();
     }
-    __syncthreads();
     // winner and runner-up by (D, lowest index)
     float bv = S.cv[0], sv = -INFINITY;
     int bj = S.cj[0], sj = INT_MAX;
