@@ -47,9 +47,29 @@ __global__ void init_twiddles(int Ntw, double2* tw64, float2* tw32) {
     }
 }
 
-__global__ void init_tables(Geom g, float* cm1, float* sA, float* wc, float* ws, float* gc, float4* tA2) {
+__global__ void init_tables(Geom g, float* cm1, float* sA, float* wc, float* ws, float* gc, uint2* tah, uint2* tbh) {
     const long long Dy = (long long)g.u * g.H, Dx = (long long)g.u * g.W;
-    const int nA = g.Hh * g.T1p, nB = g.Wc * g.T1p, nA2 = g.TAB * (g.Hh / 2);
+    const int nA = g.Hh * g.T1p, nB = g.Wc * g.T1p;
+    const int Hq = g.Hh / 2, SAq = g.SA / 2, T1 = g.T1p, T8 = g.T1p8;
+    const int nAh = 2 * g.TAB * Hq, nBh = 2 * T1 * SAq, nBn = 2 * T8;
+    const float s13 = 8192.f;                                // 2^13: table scale of the fp16 pairs
+    float* bn = (float*)(tbh + nBh);
+    // w cos, w sin and w (cos - 1) of 2 pi kx' t/(uW), kx' the signed frequency (W/2 -> -W/2)
+    auto wcs = [&](int kx, int t, float* a, float* b, float* c) {
+        const int kxs = (kx < g.W / 2) ? kx : kx - g.W;
+        const double w = (kx == 0 || 2 * kx == g.W) ? 1.0 : 2.0;
+        *a = 0.f; *b = 0.f; *c = 0.f;
+        if (t <= g.h0) {
+            long long r = ((long long)kxs * t) % Dx;
+            if (r < 0) r += Dx;
+            double s, co;
+            sincospi(2.0 * (double)r / (double)Dx, &s, &co);
+            const double h = sinpi((double)r / (double)Dx);
+            *a = (float)(w * co);
+            *b = (float)(w * s);
+            *c = (float)(w * (-2.0 * h * h));
+        }
+    };
     auto cm1_s = [&](int m, int t, float* c1, float* s1) {
         *c1 = 0.f;
         *s1 = 0.f;
@@ -60,37 +80,39 @@ __global__ void init_tables(Geom g, float* cm1, float* sA, float* wc, float* ws,
             *s1 = (float)sinpi(2.0 * (double)r / (double)Dy);
         }
     };
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nA + nB + nA2; i += gridDim.x * blockDim.x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nA + nB + nAh + nBh + nBn; i += gridDim.x * blockDim.x) {
         if (i < nA) {
             const int m = i / g.T1p + 1, t = i % g.T1p;
             cm1_s(m, t, &cm1[i], &sA[i]);
         } else if (i < nA + nB) {
             const int k = i - nA;
             const int kx = k / g.T1p, t = k % g.T1p;
-            const int kxs = (kx < g.W / 2) ? kx : kx - g.W;      // W/2 -> -W/2
-            const double w = (kx == 0 || 2 * kx == g.W) ? 1.0 : 2.0;
-            float a = 0.f, b = 0.f, c = 0.f;
-            if (t <= g.h0) {
-                long long r = ((long long)kxs * t) % Dx;
-                if (r < 0) r += Dx;
-                double s, co;
-                sincospi(2.0 * (double)r / (double)Dx, &s, &co);
-                const double h = sinpi((double)r / (double)Dx);
-                a = (float)(w * co);
-                b = (float)(w * s);
-                c = (float)(w * (-2.0 * h * h));
-            }
-            wc[k] = a;
-            ws[k] = b;
-            gc[k] = c;
-        } else {
-            // [t - 1][q]: (cm1, s) of m = 2q+1 and m = 2q+2 at t = 1..TAB (zero beyond h0)
+            wcs(kx, t, &wc[k], &ws[k], &gc[k]);
+        } else if (i < nA + nB + nAh) {
+            // stage-A pairs: [cm1 | s][t - 1][pair p of m = 2p+1, 2p+2], pairs swizzled by row
             const int k = i - nA - nB;
-            const int t = k / (g.Hh / 2) + 1, q = k % (g.Hh / 2);
-            float a, b, c, d;
-            cm1_s(2 * q + 1, t, &a, &b);
-            cm1_s(2 * q + 2, t, &c, &d);
-            tA2[k] = make_float4(a, b, c, d);
+            const int which = k / (g.TAB * Hq), rem = k - which * g.TAB * Hq;
+            const int ta = rem / Hq, p = (rem - ta * Hq) ^ pswz(ta, Hq);
+            float a, b, cc, d;
+            cm1_s(2 * p + 1, ta + 1, &a, &b);
+            cm1_s(2 * p + 2, ta + 1, &cc, &d);
+            tah[k] = which ? split_pair(s13 * b, s13 * d) : split_pair(s13 * a, s13 * cc);
+        } else if (i < nA + nB + nAh + nBh) {
+            // stage-B pairs: [w cos | w sin][tx][pair p of kx = 2p, 2p+1], pairs swizzled by row
+            const int k = i - nA - nB - nAh;
+            const int which = k / (T1 * SAq), rem = k - which * T1 * SAq;
+            const int tx = rem / SAq, p = (rem - tx * SAq) ^ pswz(tx, SAq);
+            float a0, b0, c0, a1, b1, c1;
+            wcs(2 * p, tx, &a0, &b0, &c0);
+            wcs(2 * p + 1, tx, &a1, &b1, &c1);
+            tbh[k] = which ? split_pair(s13 * b0, s13 * b1) : split_pair(s13 * a0, s13 * a1);
+        } else {
+            // kx = W/2 column in FP32: [w cos | w sin][tx], tx < T1p8
+            const int k = i - nA - nB - nAh - nBh;
+            const int which = k / T8, tx = k - which * T8;
+            float a, b, d;
+            wcs(g.W / 2, tx, &a, &b, &d);
+            bn[k] = which ? b : a;
         }
     }
 }
@@ -163,6 +185,7 @@ bool plan_geometry(int H, int W, const ccst_params& p, size_t smem_limit, Geom* 
     if (g.SZ < len) g.SZ += 16;
     g.u = p.upsample; g.M = (3 * p.upsample + 1) / 2; g.h0 = g.M / 2; g.pmax = g.M - 1 - g.h0;
     g.T1p = (g.h0 + 1 + 3) & ~3;
+    g.T1p8 = (g.h0 + 1 + 7) & ~7;
     g.Ntw = H > W ? H : W; g.logNtw = ilog2(g.Ntw);
     g.lN1h = ilog2(split_n1(H)); g.lN2h = ilog2(split_n2(H));
     g.lN1w = ilog2(split_n1(W)); g.lN2w = ilog2(split_n2(W));
@@ -328,7 +351,6 @@ extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pi
 
     const size_t HW = (size_t)H * W, HWc = (size_t)H * g.Wc;
     const size_t tabA = (size_t)g.Hh * g.T1p, tabB = (size_t)g.Wc * g.T1p;
-    const size_t tabA2 = (size_t)g.TAB * (g.Hh / 2);                  // float4
     const size_t l2per = (size_t)(H / 2) * W + (size_t)H * g.Wcp;   // FP64 FFT workspace at create
     const size_t elem = p.in_dtype == CCST_U16 ? 2 : 4;
     const long long Dy = (long long)g.u * H, Dx = (long long)g.u * W;
@@ -344,7 +366,7 @@ extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pi
         {(void**)&c->d_FE32, HWc * sizeof(float2)},
         {(void**)&c->d_tw64, (size_t)(g.Ntw / 2) * sizeof(double2)},
         {(void**)&c->d_tw32, (size_t)(g.Ntw / 2) * sizeof(float2)},
-        {(void**)&c->d_tab, (2 * tabA + 3 * tabB + 4 * tabA2) * sizeof(float)},
+        {(void**)&c->d_tab, (2 * tabA + 3 * tabB) * sizeof(float) + table_bytes(g)},
         {(void**)&c->d_df, ndf * sizeof(dfc)},
         {(void**)&d_work, l2per * sizeof(double2)},
         {(void**)&c->d_frames, (size_t)p.max_batch * HW * elem},
@@ -360,7 +382,8 @@ extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pi
     g.FE32 = c->d_FE32; g.FE64 = c->d_FE64; g.b64 = c->d_b64; g.tw32 = c->d_tw32; g.tw64 = c->d_tw64;
     g.tA_cm1 = c->d_tab; g.tA_s = c->d_tab + tabA;
     g.tB_wc = c->d_tab + 2 * tabA; g.tB_ws = g.tB_wc + tabB; g.tB_gc = g.tB_ws + tabB;
-    g.tA2 = (const float4*)(g.tB_gc + tabB);          // 16-byte aligned: the block sizes above are multiples of 4
+    g.tAh = (const uint2*)(g.tB_gc + tabB);           // 16-byte aligned: the block sizes above are multiples of 4
+    g.tBh = (const uint2*)((const char*)g.tAh + ta_bytes(g));
     dfc* twdf = c->d_df;
     dfc* FEdf = twdf + g.Ntw / 2;
     dfc* eyc = FEdf + HWc;
@@ -378,7 +401,7 @@ extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pi
         return bail_work(CCST_E_CUDA);
     init_twiddles<<<1, 256, 0, c->stream>>>(g.Ntw, c->d_tw64, c->d_tw32);
     init_tables<<<64, 256, 0, c->stream>>>(g, (float*)g.tA_cm1, (float*)g.tA_s, (float*)g.tB_wc,
-                                           (float*)g.tB_ws, (float*)g.tB_gc, (float4*)g.tA2);
+                                           (float*)g.tB_ws, (float*)g.tB_gc, (uint2*)g.tAh, (uint2*)g.tBh);
     init_ref_operand<<<32, 256, 0, c->stream>>>(g, (const float*)c->d_ref32, c->d_b64);
     init_ref_spectrum<<<1, 256, 0, c->stream>>>(g, d_work, c->d_FE64, c->d_FE32);
     init_dfloat<<<32, 256, 0, c->stream>>>(g, c->d_tw64, c->d_FE64, twdf, FEdf, eyc, eyf, exc, exf, ncy, ncx);
@@ -769,7 +792,6 @@ extern "C" int ccst_track_static(const float* ref_dev, int H, int W, const ccst_
     // carve the static array (256-byte aligned regions)
     const size_t HW = (size_t)H * W, HWc = (size_t)H * g.Wc;
     const size_t tabA = (size_t)g.Hh * g.T1p, tabB = (size_t)g.Wc * g.T1p;
-    const size_t tabA2 = (size_t)g.TAB * (g.Hh / 2);
     const size_t ndf = (size_t)(g.Ntw / 2) + HWc + ncy + g.By + ncx + g.Bx;
     const size_t work = (size_t)(H / 2) * W + (size_t)H * g.Wcp;
     size_t off = 0;
@@ -779,7 +801,7 @@ extern "C" int ccst_track_static(const float* ref_dev, int H, int W, const ccst_
     float2* FE32 = (float2*)take(HWc * sizeof(float2));
     double2* tw64 = (double2*)take((size_t)(g.Ntw / 2) * sizeof(double2));
     float2* tw32 = (float2*)take((size_t)(g.Ntw / 2) * sizeof(float2));
-    float* tab = (float*)take((2 * tabA + 3 * tabB + 4 * tabA2) * sizeof(float));
+    float* tab = (float*)take((2 * tabA + 3 * tabB) * sizeof(float) + table_bytes(g));
     dfc* dfb = (dfc*)take(ndf * sizeof(dfc));
     double2* wk = (double2*)take(work * sizeof(double2));
     if (off > kStaticScratchBytes)
@@ -787,7 +809,8 @@ extern "C" int ccst_track_static(const float* ref_dev, int H, int W, const ccst_
                                          "the 2 MiB static array holds (lower upsample)");
     g.FE32 = FE32; g.FE64 = FE64; g.b64 = b64; g.tw32 = tw32; g.tw64 = tw64;
     g.tA_cm1 = tab; g.tA_s = tab + tabA; g.tB_wc = tab + 2 * tabA; g.tB_ws = g.tB_wc + tabB; g.tB_gc = g.tB_ws + tabB;
-    g.tA2 = (const float4*)(g.tB_gc + tabB);
+    g.tAh = (const uint2*)(g.tB_gc + tabB);
+    g.tBh = (const uint2*)((const char*)g.tAh + ta_bytes(g));
     dfc* twdf = dfb;
     dfc* FEdf = twdf + g.Ntw / 2;
     dfc* eyc = FEdf + HWc;
@@ -799,7 +822,7 @@ extern "C" int ccst_track_static(const float* ref_dev, int H, int W, const ccst_
     // every region is rewritten in full below before anything reads it
     init_twiddles<<<1, 256, 0, stream>>>(g.Ntw, tw64, tw32);
     init_tables<<<64, 256, 0, stream>>>(g, tab, tab + tabA, tab + 2 * tabA, tab + 2 * tabA + tabB,
-                                        tab + 2 * tabA + 2 * tabB, (float4*)g.tA2);
+                                        tab + 2 * tabA + 2 * tabB, (uint2*)g.tAh, (uint2*)g.tBh);
     init_ref_operand<<<32, 256, 0, stream>>>(g, ref_dev, b64);
     init_ref_spectrum<<<1, 256, 0, stream>>>(g, wk, FE64, FE32);
     init_dfloat<<<32, 256, 0, stream>>>(g, tw64, FE64, twdf, FEdf, eyc, eyf, exc, exf, ncy, ncx);

@@ -44,6 +44,7 @@
 
 #include "ccst_device.cuh"
 #include "ccst_fft.cuh"
+#include <cuda_fp16.h>
 
 namespace ccst {
 
@@ -57,6 +58,7 @@ struct Geom {
     int SZ;                             // padded row stride (float2) of the packed-row buffer
     int u, M, h0, pmax;                 // grid: M points, offsets t = j - h0 in [-h0, pmax]
     int T1p;                            // table row length for tx in [0, h0] (padded to 4)
+    int T1p8;                           // tx extent of the tensor-core stage-B tables (padded to 8)
     int TAB;                            // t rows 1..TAB of the stage tables (h0 rounded up to 15)
     int TC, nchunk;                     // t rows per stage chunk (multiple of 15) and number of chunks
     int tables_smem;                    // stage tables staged in shared memory (else read from global)
@@ -74,7 +76,8 @@ struct Geom {
     const double2* tw64;
     const float* tA_cm1;                // [Hh][T1p]  cos(2 pi m t/(uH)) - 1, m = 1..Hh
     const float* tA_s;                  // [Hh][T1p]  sin(2 pi m t/(uH))
-    const float4* tA2;                  // [TAB][Hh/2] (cm1, s) for m = 2q+1, 2q+2 at t = 1..TAB
+    const uint2* tAh;                   // stage-A tensor-core tables (layout of Smem::TA)
+    const uint2* tBh;                   // stage-B tensor-core tables (layout of Smem::TB)
     const float* tB_wc;                 // [Wc][T1p]  w cos(2 pi kx' t/(uW))
     const float* tB_ws;                 // [Wc][T1p]  w sin(2 pi kx' t/(uW))
     const float* tB_gc;                 // [Wc][T1p]  w (cos(2 pi kx' t/(uW)) - 1)
@@ -149,6 +152,61 @@ __device__ __forceinline__ double operand_f64(double I, const Geom& g) {
     return ip * ip;
 }
 
+// ------------------------------------------------- fp16 hi/lo operand pairs
+// The contractions run on the tensor cores as m16n8k16 FP16 MMAs with FP32 accumulation.
+// Each FP32 operand x (scaled by a power of two into [2^-14, 2^14]) is stored as
+// x = hi + lo + r, hi = fp16(x), lo = fp16(x - hi), |r| <= 2^-22 |x| (plus the fp16
+// subnormal floor, far below the contraction's error budget after scaling), and a product
+// is accumulated as lo*hi + hi*lo + hi*hi (the dropped lo*lo is below 2^-22 of it). Two
+// consecutive K elements share one 32-bit register as the MMA fragments want them; an
+// operand row is stored as uint2 {hi pair, lo pair} per K pair.
+__device__ __forceinline__ uint2 split_pair(float a, float b) {
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+    return make_uint2(*reinterpret_cast<const unsigned*>(&h), *reinterpret_cast<const unsigned*>(&l));
+}
+__device__ __forceinline__ float2 unsplit_pair(uint2 v) {
+    const float2 h = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+    const float2 l = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+    return make_float2(h.x + l.x, h.y + l.y);
+}
+// Pair-index swizzle of an operand row with kp pairs: pair p of row r sits at p ^ pswz(r).
+// The 16 lanes of a half-warp (4 rows x 4 pairs) of every fragment load then hit distinct
+// 8-byte bank pairs.
+__host__ __device__ __forceinline__ int pswz(int r, int kp) { return ((r & 3) << 2) & (kp - 1); }
+__device__ __forceinline__ void mma_f16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// d += a * b in the three-product split form; a_h/a_l: A fragment halves, b: the two
+// uint2 {hi, lo} of the B fragment
+__device__ __forceinline__ void mma3(float (&d)[4], const unsigned (&ah)[4], const unsigned (&al)[4], uint2 b0,
+                                     uint2 b1) {
+    mma_f16(d, al, b0.x, b1.x);
+    mma_f16(d, ah, b0.y, b1.y);
+    mma_f16(d, ah, b0.x, b1.x);
+}
+// A fragment (rows ra, rb; K pairs kp + tq and kp + tq + 4) of a [row][kpr] operand
+__device__ __forceinline__ void load_afrag(const uint2* P, int kpr, int ra, int rb, int kp, int tq, unsigned (&h)[4],
+                                           unsigned (&l)[4]) {
+    const int sa = pswz(ra, kpr), sb = pswz(rb, kpr);
+    const uint2 v0 = P[ra * kpr + ((kp + tq) ^ sa)], v1 = P[rb * kpr + ((kp + tq) ^ sb)];
+    const uint2 v2 = P[ra * kpr + ((kp + tq + 4) ^ sa)], v3 = P[rb * kpr + ((kp + tq + 4) ^ sb)];
+    h[0] = v0.x; h[1] = v1.x; h[2] = v2.x; h[3] = v3.x;
+    l[0] = v0.y; l[1] = v1.y; l[2] = v2.y; l[3] = v3.y;
+}
+
+// Power-of-two exponent for the per-frame operands: with sum|X| <= scale, every P/Q value
+// is <= 2 scale and every stage-A combination <= 4 scale; 2^kexp brings them to <= 2^14.
+__device__ __forceinline__ int operand_exponent(float scale) {
+    int e = 0;
+    if (scale > 0.f && isfinite(scale)) (void)frexpf(scale, &e);   // scale <= 2^e
+    return max(-120, min(120, 12 - e));
+}
+
 // ------------------------------------------------------------- shared layout
 // R1: A (H x SA float2: the spectrum, later X' with P/Q rows) and XN (H float2: the
 //     x-Nyquist column kx = W/2 of the same).
@@ -162,17 +220,20 @@ struct Smem {
     float2* XN;
     float2* B;
     float2* ZC;
-    float4* TA;
-    float* TBc;
-    float* TBs;
-    float4* UV;
+    uint2* PQ;             // = A after the P/Q build: [4][SA][Hh/2] planes Pr, Pi, Qr, Qi (fp16 pairs)
+    uint2* TA;             // stage-A tables [2][TAB][Hh/2]: 2^13 (cos - 1), 2^13 sin (fp16 pairs)
+    uint2* TB;             // stage-B tables [2][T1p][SA/2]: 2^13 w cos, 2^13 w sin (fp16 pairs),
+                           //   then float [2][T1p8]: w cos, w sin at kx = W/2
+    float4* UV;            // the contraction area, also scratch before and after it
     float4* UVN;
+    uint2* CB;             // = UV: stage-A output [4][TC][SA/2] (C0, C1, E0, E1 as fp16 pairs)
+    float* CBN;            // = UVN: [4][TC] the same at kx = W/2 (FP32)
     unsigned char* r1;     // start of R1
     size_t r12_bytes;      // bytes of R1 + R2
     float2* tw;            // Ntw/2
     float2* t4h;           // H: four-step inter-pass twiddles of length H, [k1][n2]
     float2* t4w;           // W: the same for length W
-    int4* rowq;            // Hh/2: row offsets (x SA) of P(m1), P(m2), Q(m1), Q(m2)
+    float2* X0;            // SA: X'(0, kx)
     float* gP;             // T1p: g(+tx)
     float* gM;             // T1p: g(-tx)
     float* rv;             // reduction scratch (floats)
@@ -189,12 +250,15 @@ struct Smem {
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct SmemPlan {
-    size_t a, xn, r1, b, zc, ta, tbc, tbs, uv, uvn, r2, misc, total;
+    size_t a, xn, r1, b, zc, ta, tb, uv, uvn, r2, misc, total;
 };
 
-__host__ __device__ inline size_t table_bytes(const Geom& g) {
-    return sizeof(float4) * (size_t)g.TAB * (g.Hh / 2) + 2 * sizeof(float) * (size_t)g.Wc * g.T1p;
+// sizes (bytes) of the two tensor-core table blocks
+__host__ __device__ inline size_t ta_bytes(const Geom& g) { return sizeof(uint2) * 2 * (size_t)g.TAB * (g.Hh / 2); }
+__host__ __device__ inline size_t tb_bytes(const Geom& g) {
+    return sizeof(uint2) * 2 * (size_t)g.T1p * (g.SA / 2) + sizeof(float) * 2 * (size_t)g.T1p8;
 }
+__host__ __device__ inline size_t table_bytes(const Geom& g) { return ta_bytes(g) + tb_bytes(g); }
 
 __host__ __device__ inline SmemPlan smem_plan(const Geom& g) {
     SmemPlan p;
@@ -204,10 +268,9 @@ __host__ __device__ inline SmemPlan smem_plan(const Geom& g) {
     p.b = align_up(sizeof(float2) * (size_t)g.H * g.SA, 16);
     p.zc = align_up(sizeof(float2) * (size_t)(g.H / 2) * g.SZ, 16);
     const size_t fft = p.b + p.zc;
-    p.ta = g.tables_smem ? align_up(sizeof(float4) * (size_t)g.TAB * (g.Hh / 2), 16) : 0;
-    p.tbc = g.tables_smem ? align_up(sizeof(float) * (size_t)g.Wc * g.T1p, 16) : 0;
-    p.tbs = p.tbc;
-    p.uv = align_up(sizeof(float4) * (size_t)g.TC * g.SA, 16);
+    p.ta = g.tables_smem ? align_up(ta_bytes(g), 16) : 0;
+    p.tb = g.tables_smem ? align_up(tb_bytes(g), 16) : 0;
+    p.uv = align_up(sizeof(uint2) * 4 * (size_t)g.TC * (g.SA / 2), 16);
     // the P/Q build keeps R(kx), its 8 partial sums and the g partial sums here first
     size_t rscr = sizeof(float2) * ((size_t)g.Wcp + 8 * (size_t)(g.SA + 1)) + sizeof(float) * 2 * kGParts * (size_t)g.T1p;
     // ... and afterwards the guard scratch (FP32 pair differences, or the FP64 diagnostic)
@@ -217,7 +280,7 @@ __host__ __device__ inline SmemPlan smem_plan(const Geom& g) {
     if (rscr < dscr) rscr = dscr;
     if (p.uv < rscr) p.uv = align_up(rscr, 16);
     p.uvn = align_up(sizeof(float4) * (size_t)g.TC, 16);
-    const size_t k6 = p.ta + p.tbc + p.tbs + p.uv + p.uvn;
+    const size_t k6 = p.ta + p.tb + p.uv + p.uvn;
     p.r2 = fft > k6 ? fft : k6;
     // the double-float level needs H x Wcp dfc plus one packed-row chunk (2 rows of W dfc),
     // which later holds the H + Wc candidate twiddles
@@ -225,7 +288,7 @@ __host__ __device__ inline SmemPlan smem_plan(const Geom& g) {
     const size_t dfl = sizeof(dfc) * ((size_t)g.H * g.Wcp + (size_t)(g.Ntw / 2) + chunk);
     if (p.r1 + p.r2 < dfl) p.r2 = align_up(dfl - p.r1, 16);
     p.misc = sizeof(double) * 32 + 16 + sizeof(float2) * (size_t)(g.Wc + g.Hh + 1) +
-             sizeof(float2) * (size_t)(g.Ntw / 2 + g.H + g.W) + sizeof(int4) * (size_t)(g.Hh / 2) +
+             sizeof(float2) * (size_t)(g.Ntw / 2 + g.H + g.W) + sizeof(float2) * (size_t)g.SA +
              sizeof(float) * 2 * (size_t)g.T1p + sizeof(float) * 64 + sizeof(int) * 64 +
              (sizeof(int) + sizeof(float)) * kMaxCand + sizeof(int) * 16 + 64;
     p.total = align_up(p.r1 + p.r2 + p.misc, 16);
@@ -241,11 +304,13 @@ static __device__ inline Smem carve(const Geom& g, unsigned char* base) {
     unsigned char* r2 = base + p.r1;
     s.B = (float2*)r2;
     s.ZC = (float2*)(r2 + p.b);
-    s.TA = (float4*)r2;
-    s.TBc = (float*)(r2 + p.ta);
-    s.TBs = (float*)(r2 + p.ta + p.tbc);
-    s.UV = (float4*)(r2 + p.ta + p.tbc + p.tbs);
-    s.UVN = (float4*)(r2 + p.ta + p.tbc + p.tbs + p.uv);
+    s.PQ = (uint2*)base;
+    s.TA = (uint2*)r2;
+    s.TB = (uint2*)(r2 + p.ta);
+    s.UV = (float4*)(r2 + p.ta + p.tb);
+    s.UVN = (float4*)(r2 + p.ta + p.tb + p.uv);
+    s.CB = (uint2*)s.UV;
+    s.CBN = (float*)s.UVN;
     s.r12_bytes = p.r1 + p.r2;
     unsigned char* m = r2 + p.r2;
     s.rd = (double*)m; m += sizeof(double) * 32;
@@ -255,7 +320,7 @@ static __device__ inline Smem carve(const Geom& g, unsigned char* base) {
     s.tw = (float2*)m; m += sizeof(float2) * (g.Ntw / 2);
     s.t4h = (float2*)m; m += sizeof(float2) * g.H;
     s.t4w = (float2*)m; m += sizeof(float2) * g.W;
-    s.rowq = (int4*)m; m += sizeof(int4) * (g.Hh / 2);
+    s.X0 = (float2*)m; m += sizeof(float2) * g.SA;
     s.gP = (float*)m; m += sizeof(float) * g.T1p;
     s.gM = (float*)m; m += sizeof(float) * g.T1p;
     s.rv = (float*)m; m += sizeof(float) * 64;
@@ -476,23 +541,12 @@ static __device__ double direct_sum_f64(const Geom& g, const Smem& S, const void
 }
 
 // ------------------------------------------------------ a5: integer extremum
-// t2: each thread's best point of the integer surface (value, natural flat index) and its
-// runner-up value, collected while the inverse FFT stored them.
-__device__ __forceinline__ int integer_peak(const Geom& g, const Smem& S, const void* frame, long long pitch,
-                                            float scale, unsigned* flags, const Best2& t2) {
-    float v1 = t2.v1;
-    int best = t2.j1;
-    block_argmax(v1, best, S.rv, S.rj);
-    if (!(v1 > -INFINITY)) { *flags |= 0x10u; return 0; }
-    const float tau = g.tau_int * scale;
-    if (!g.guard) return best;
-    // unique unless some other shift lies within tau of the best
-    const int near = __syncthreads_count((t2.v1 >= v1 - tau && t2.j1 != best) || t2.v2 >= v1 - tau);
-    if (near == 0) return best;
-    // collect every integer shift within tau of the best
+// Rare path of the integer search: collect every integer shift whose FP32 value is >= thr
+// and re-decide among them by FP64 direct sums.
+static __device__ int integer_collect(const Geom& g, const Smem& S, const void* frame, long long pitch,
+                                                   float thr, int best, unsigned* flags) {
     if (threadIdx.x == 0) S.misc[0] = 0;
     __syncthreads();
-    const float thr = v1 - tau;
     for (int idx = threadIdx.x; idx < g.H * g.W; idx += blockDim.x) {
         if (g.sense * int_surface(g, S, idx) >= thr) {
             const int k = atomicAdd(&S.misc[0], 1);
@@ -514,7 +568,24 @@ __device__ __forceinline__ int integer_peak(const Geom& g, const Smem& S, const 
     return bestj;
 }
 
-// Stage tables -> shared memory by three bulk copies on the TMA engine (contiguous tables,
+
+// t2: each thread's best point of the integer surface (value, natural flat index) and its
+// runner-up value, collected while the inverse FFT stored them.
+__device__ __forceinline__ int integer_peak(const Geom& g, const Smem& S, const void* frame, long long pitch,
+                                            float scale, unsigned* flags, const Best2& t2) {
+    float v1 = t2.v1;
+    int best = t2.j1;
+    block_argmax(v1, best, S.rv, S.rj);
+    if (!(v1 > -INFINITY)) { *flags |= 0x10u; return 0; }
+    const float tau = g.tau_int * scale;
+    if (!g.guard) return best;
+    // unique unless some other shift lies within tau of the best
+    const int near = __syncthreads_count((t2.v1 >= v1 - tau && t2.j1 != best) || t2.v2 >= v1 - tau);
+    if (near == 0) return best;
+    return integer_collect(g, S, frame, pitch, v1 - tau, best, flags);
+}
+
+// Stage tables -> shared memory by two bulk copies on the TMA engine (contiguous tables,
 // 16-byte aligned, sizes multiples of 16 bytes), completing on the mbarrier S.bar.
 __device__ __forceinline__ void tables_bar_init(const Smem& S) {
     if (threadIdx.x == 0) {
@@ -527,15 +598,15 @@ __device__ __forceinline__ void tables_bar_init(const Smem& S) {
 // destination area.
 __device__ __forceinline__ void stage_tables_async(const Geom& g, const Smem& S) {
     if (!g.tables_smem || threadIdx.x != 0) return;
-    const unsigned na = 16u * (unsigned)(g.TAB * (g.Hh / 2)), nb = 4u * (unsigned)(g.Wc * g.T1p);
+    const unsigned na = (unsigned)ta_bytes(g), nb = (unsigned)tb_bytes(g);
     const unsigned b = (unsigned)__cvta_generic_to_shared(S.bar);
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b), "r"(na + 2 * nb) : "memory");
-    const void* src[3] = {g.tA2, g.tB_wc, g.tB_ws};
-    const void* dst[3] = {S.TA, S.TBc, S.TBs};
-    const unsigned n[3] = {na, nb, nb};
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b), "r"(na + nb) : "memory");
+    const void* src[2] = {g.tAh, g.tBh};
+    const void* dst[2] = {S.TA, S.TB};
+    const unsigned n[2] = {na, nb};
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 2; ++i) {
         const unsigned d = (unsigned)__cvta_generic_to_shared(dst[i]);
         asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
                      ::"r"(d), "l"(src[i]), "r"(n[i]), "r"(b) : "memory");
@@ -556,9 +627,9 @@ __device__ __forceinline__ bool stage_tables_wait(const Geom& g, const Smem& S, 
 }
 
 // --------------------------------------------- a6 prologue: X' and P/Q, R, g
-// In place over S.A / S.XN (rows at their positions posH): row 0 = X'(0),
-// row Hh = X'(Hh), row m = P(m), row H-m = Q(m). Writes g(+tx), g(-tx).
-static __device__ void build_pq_and_g(const Geom& g, const Smem& S, int py, int px) {
+// Builds the stage-A operand planes S.PQ from the spectrum in S.A (and XN in place),
+// X'(0, kx) in S.X0, R(kx) and g(+-tx).
+static __device__ void build_pq_and_g(const Geom& g, const Smem& S, int py, int px, float scale) {
     const int H = g.H, W = g.W, SA = g.SA, Hh = g.Hh;
     const int pyy = py & (H - 1), pxx = px & (W - 1);
     const int ncol = SA + 1;          // slots 0..SA-1 and the Nyquist column
@@ -589,27 +660,84 @@ static __device__ void build_pq_and_g(const Geom& g, const Smem& S, int py, int 
         }
     }
     __syncthreads();
-    // X' = X e^{2 pi i k'.p/N} folded in place into P/Q rows, and 8 partial column sums of
-    // R(kx) = X'(0) + sum_{m=1}^{Hh-1} P(m) + X'(Hh). Task (part, c): rows m = part (mod 8).
+    // X' = X e^{2 pi i k'.p/N} folded into P(m) = X'(m) + X'(-m), Q(m) = X'(m) - X'(-m),
+    // m = 1 .. Hh (P(Hh) = X'(Hh); Q(Hh) = 0 outside the x-Nyquist column), and 8 partial
+    // column sums of R(kx) = X'(0) + sum_{m<Hh} P(m) + X'(Hh). Regular column c, task
+    // (part, c): the row pairs (2p+1, 2p+2), p = part (mod 8), and row 0 for part 0. The
+    // planes reuse the spectrum's memory, so every task reads into registers first and
+    // writes after a barrier (8 SA <= blockDim: one task per thread). The x-Nyquist column
+    // stays FP32, folded in place in XN.
+    const int Hq = Hh / 2, kexp = operand_exponent(scale);
+    const float sc = ldexpf(1.f, kexp);
+    if (threadIdx.x == 0) S.misc[3] = kexp;
     float2* R = (float2*)S.UV;
     float2* Rp = R + g.Wcp;                         // [8][ncol] partials
-    for (int task = threadIdx.x; task < 8 * ncol; task += blockDim.x) {
-        const int part = task / ncol, c = task - part * ncol;
-        const bool nyq = (c == SA);
-        float2* colbase = nyq ? S.XN : S.A + c;
-        const int cstride = nyq ? 1 : SA;
+    constexpr int kMaxPairs = 4;                    // Hq / 8 (H <= 128)
+    float2 pq[kMaxPairs][4];                        // P(m1), Q(m1), P(m2), Q(m2), scaled
+    const int task = threadIdx.x;
+    const int part = task / SA, c = task - part * SA;
+    const bool mine = task < 8 * SA;
+    if (mine) {
         const float2 ex = S.ex[c];
         float2 r = make_float2(0.f, 0.f);
-        for (int m = part; m <= Hh; m += 8) {
+        if (part == 0) {
+            const float2 x0 = cmul(S.A[posH(g, 0) * SA + c], cmul(S.ey[0], ex));
+            S.X0[c] = x0;
+            r = x0;
+        }
+#pragma unroll
+        for (int j = 0; j < kMaxPairs; ++j) {
+            const int p = part + 8 * j;
+            if (p >= Hq) break;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int m = 2 * p + 1 + h;
+                const float2 ey = S.ey[m];
+                float2 P, Q;
+                if (m == Hh) {
+                    P = cmul(S.A[posH(g, m) * SA + c], cmul(ey, ex));
+                    Q = make_float2(0.f, 0.f);
+                } else {
+                    const float2 xp = cmul(S.A[posH(g, m) * SA + c], cmul(ey, ex));
+                    const float2 xm = cmul(S.A[posH(g, H - m) * SA + c], cmul(cconj(ey), ex));
+                    P = cadd(xp, xm);
+                    Q = csub(xp, xm);
+                }
+                r = cadd(r, P);
+                pq[j][2 * h] = make_float2(P.x * sc, P.y * sc);
+                pq[j][2 * h + 1] = make_float2(Q.x * sc, Q.y * sc);
+            }
+        }
+        Rp[part * ncol + c] = r;
+    }
+    __syncthreads();
+    if (mine) {
+        const int sw = pswz(c, Hq);
+#pragma unroll
+        for (int j = 0; j < kMaxPairs; ++j) {
+            const int p = part + 8 * j;
+            if (p >= Hq) break;
+            const int q = p ^ sw;
+            S.PQ[(0 * SA + c) * Hq + q] = split_pair(pq[j][0].x, pq[j][2].x);     // Pr
+            S.PQ[(1 * SA + c) * Hq + q] = split_pair(pq[j][0].y, pq[j][2].y);     // Pi
+            S.PQ[(2 * SA + c) * Hq + q] = split_pair(pq[j][1].x, pq[j][3].x);     // Qr
+            S.PQ[(3 * SA + c) * Hq + q] = split_pair(pq[j][1].y, pq[j][3].y);     // Qi
+        }
+    }
+    // x-Nyquist column, in place in XN (FP32)
+    for (int pt = threadIdx.x; pt < 8; pt += blockDim.x) {
+        const float2 ex = S.ex[SA];
+        float2 r = make_float2(0.f, 0.f);
+        for (int m = pt; m <= Hh; m += 8) {
             const float2 ey = S.ey[m];
             if (m == 0 || m == Hh) {
-                float2* p = colbase + posH(g, m) * cstride;
+                float2* p = S.XN + posH(g, m);
                 const float2 x = cmul(*p, cmul(ey, ex));
                 *p = x;
                 r = cadd(r, x);
             } else {
-                float2* rp = colbase + posH(g, m) * cstride;
-                float2* rm = colbase + posH(g, H - m) * cstride;
+                float2* rp = S.XN + posH(g, m);
+                float2* rm = S.XN + posH(g, H - m);
                 const float2 xp = cmul(*rp, cmul(ey, ex));
                 const float2 xm = cmul(*rm, cmul(cconj(ey), ex));
                 const float2 pm = cadd(xp, xm);
@@ -618,7 +746,7 @@ static __device__ void build_pq_and_g(const Geom& g, const Smem& S, int py, int 
                 r = cadd(r, pm);
             }
         }
-        Rp[part * ncol + c] = r;
+        Rp[pt * ncol + SA] = r;
     }
     __syncthreads();
     for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
@@ -668,74 +796,137 @@ static __device__ void build_pq_and_g(const Geom& g, const Smem& S, int py, int 
 }
 
 // --------------------------------------------------- a6: stage A (one chunk)
-// UV[lt][slot] = (U'r, U'i, Vr, Vi)(t, kx) for t = t0 + lt, lt in [0, TC); UVN the
-// x-Nyquist column. Tiles: 5 t x 2 slots; the Nyquist column uses spare threads.
-__device__ __forceinline__ void stage_a(const Geom& g, const Smem& S, int t0, const float4* tA2) {
-    const int SA = g.SA, Hq = g.Hh / 2, Hh = g.Hh;
-    const int ntt = g.TC / 5, nkk = SA / 2;
-    const int nmain = ntt * nkk;
-    const int ntask = nmain + ntt;                         // + x-Nyquist column in 5-row strips
-    for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
-        if (task < nmain) {
-            const int tt = task / nkk, kk = task - tt * nkk;
-            const int lt0 = 5 * tt, kb = 2 * kk;
-            float4 acc[5][2];
+// For t = t0 + lt, lt in [0, TC) and every regular column kx < SA:
+//   U'r, U'i = sum_m (cos - 1)(2 pi m t/(uH)) (Pr, Pi)(m, kx),  Vr, Vi = sum_m sin(..) (Qr, Qi)(m, kx),
+// stored as the combinations stage B contracts, C0 = U'r - Vi, C1 = U'r + Vi,
+// E0 = U'i + Vr, E1 = U'i - Vr (scaled by 2^kexp, fp16 pairs, CB); CBN gets them in FP32
+// for the x-Nyquist column, whose Nyquist row keeps the full phase (Q(Hh) = -P(Hh)).
+
+// the four combinations from (U'r, U'i, Vr, Vi)
+__device__ __forceinline__ float4 combos(float ur, float ui, float vr, float vi) {
+    return make_float4(ur - vi, ur + vi, ui + vr, ui - vr);
+}
+
+__device__ __forceinline__ void stage_a_nyquist(const Geom& g, const Smem& S, int t0, const uint2* TA) {
+    const int H = g.H, Hh = g.Hh, Hq = Hh / 2, TC = g.TC;
+    const uint2* Tc = TA;
+    const uint2* Ts = TA + (size_t)g.TAB * Hq;
+    const float un = ldexpf(1.f, -13);
+    for (int lt = threadIdx.x; lt < TC; lt += blockDim.x) {
+        const int ta = t0 - 1 + lt, sw = pswz(ta, Hq);
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int p = Hq - 1; p >= 0; --p) {
+            const int m1 = 2 * p + 1, m2 = 2 * p + 2;
+            const float2 cm = unsplit_pair(Tc[ta * Hq + (p ^ sw)]), sn = unsplit_pair(Ts[ta * Hq + (p ^ sw)]);
+            const float2 p1 = S.XN[posH(g, m1)], p2 = S.XN[posH(g, m2)], q1 = S.XN[posH(g, H - m1)];
+            const float2 q2 = (m2 == Hh) ? make_float2(-p2.x, -p2.y) : S.XN[posH(g, H - m2)];
+            acc.x = fmaf(cm.x * un, p1.x, fmaf(cm.y * un, p2.x, acc.x));
+            acc.y = fmaf(cm.x * un, p1.y, fmaf(cm.y * un, p2.y, acc.y));
+            acc.z = fmaf(sn.x * un, q1.x, fmaf(sn.y * un, q2.x, acc.z));
+            acc.w = fmaf(sn.x * un, q1.y, fmaf(sn.y * un, q2.y, acc.w));
+        }
+        const float4 cb = combos(acc.x, acc.y, acc.z, acc.w);
+        S.CBN[lt] = cb.x;
+        S.CBN[TC + lt] = cb.y;
+        S.CBN[2 * TC + lt] = cb.z;
+        S.CBN[3 * TC + lt] = cb.w;
+    }
+}
+
+// write the combinations of (row lt, K pair kp) of the four accumulators (already in the
+// 2^kexp scale) as fp16 pairs
+__device__ __forceinline__ void store_combo_pairs(const Geom& g, const Smem& S, int lt, int kp, float2 ur, float2 ui,
+                                                  float2 vr, float2 vi) {
+    const int SAq = g.SA / 2, TC = g.TC;
+    const int q = kp ^ pswz(lt, SAq);
+    const float4 a = combos(ur.x, ui.x, vr.x, vi.x), b = combos(ur.y, ui.y, vr.y, vi.y);
+    S.CB[(0 * TC + lt) * SAq + q] = split_pair(a.x, b.x);
+    S.CB[(1 * TC + lt) * SAq + q] = split_pair(a.y, b.y);
+    S.CB[(2 * TC + lt) * SAq + q] = split_pair(a.z, b.z);
+    S.CB[(3 * TC + lt) * SAq + q] = split_pair(a.w, b.w);
+}
+
+// Tensor-core form (Hh a multiple of 16): M = t, N = kx, K = m. A warp task is one t tile
+// of 16 by one kx tile of 8, with the four products (Cm1 Pr, Cm1 Pi, S Qr, S Qi) sharing
+// the A fragments. Rows past the chunk read its last row and are not stored.
+__device__ __forceinline__ void stage_a_mma(const Geom& g, const Smem& S, int t0, const uint2* TA) {
+    const int Hq = g.Hh / 2, SA = g.SA, TC = g.TC;
+    const uint2* Tc = TA;
+    const uint2* Ts = TA + (size_t)g.TAB * Hq;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int gq = lane >> 2, tq = lane & 3;
+    const int ntt = (TC + 15) >> 4, nnt = SA >> 3;
+    const float un = ldexpf(1.f, -13);
+    for (int task = warp; task < ntt * nnt; task += nwarp) {
+        const int tt = task / nnt, nt = task - tt * nnt;
+        if (t0 + 16 * tt > g.h0) continue;                       // warp-uniform: all rows past h0
+        const int r0 = t0 - 1 + min(16 * tt + gq, TC - 1), r1 = t0 - 1 + min(16 * tt + gq + 8, TC - 1);
+        const int kxr = 8 * nt + gq;
+        const int sb = pswz(kxr, Hq);
+        float d[4][4];
 #pragma unroll
-            for (int i = 0; i < 5; ++i) { acc[i][0] = make_float4(0.f, 0.f, 0.f, 0.f); acc[i][1] = acc[i][0]; }
-            const float4* tab = tA2 + (size_t)(t0 - 1 + lt0) * Hq;
-            for (int mp = Hq - 1; mp >= 0; --mp) {
-                const int4 ro = S.rowq[mp];
-                const float4 p1 = *(const float4*)&S.A[ro.x + kb];
-                const float4 p2 = *(const float4*)&S.A[ro.y + kb];
-                const float4 q1 = *(const float4*)&S.A[ro.z + kb];
-                // m2 = 2 mp + 2 = Hh (Nyquist row): no sine part outside the x-Nyquist column
-                const float4 q2 = (2 * mp + 2 == Hh) ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                                     : *(const float4*)&S.A[ro.w + kb];
+        for (int pl = 0; pl < 4; ++pl)
 #pragma unroll
-                for (int i = 0; i < 5; ++i) {
-                    const float4 tw = tab[i * Hq + mp];   // (cm1(m1), s(m1), cm1(m2), s(m2)) at t
-                    acc[i][0].x = fmaf(tw.x, p1.x, fmaf(tw.z, p2.x, acc[i][0].x));
-                    acc[i][0].y = fmaf(tw.x, p1.y, fmaf(tw.z, p2.y, acc[i][0].y));
-                    acc[i][0].z = fmaf(tw.y, q1.x, fmaf(tw.w, q2.x, acc[i][0].z));
-                    acc[i][0].w = fmaf(tw.y, q1.y, fmaf(tw.w, q2.y, acc[i][0].w));
-                    acc[i][1].x = fmaf(tw.x, p1.z, fmaf(tw.z, p2.z, acc[i][1].x));
-                    acc[i][1].y = fmaf(tw.x, p1.w, fmaf(tw.z, p2.w, acc[i][1].y));
-                    acc[i][1].z = fmaf(tw.y, q1.z, fmaf(tw.w, q2.z, acc[i][1].z));
-                    acc[i][1].w = fmaf(tw.y, q1.w, fmaf(tw.w, q2.w, acc[i][1].w));
-                }
+            for (int e = 0; e < 4; ++e) d[pl][e] = 0.f;
+        for (int kp = 0; kp < Hq; kp += 8) {
+            unsigned ch[4], cl[4], sh[4], sl[4];
+            load_afrag(Tc, Hq, r0, r1, kp, tq, ch, cl);
+            load_afrag(Ts, Hq, r0, r1, kp, tq, sh, sl);
+#pragma unroll
+            for (int pl = 0; pl < 4; ++pl) {
+                const uint2* P = S.PQ + (size_t)(pl * SA + kxr) * Hq;
+                const uint2 b0 = P[(kp + tq) ^ sb], b1 = P[(kp + tq + 4) ^ sb];
+                if (pl < 2) mma3(d[pl], ch, cl, b0, b1);
+                else mma3(d[pl], sh, sl, b0, b1);
             }
+        }
+        // element e: row gq + 8 (e >> 1), kx 8 nt + 2 tq + (e & 1)
 #pragma unroll
-            for (int i = 0; i < 5; ++i) {
-                float4* dst = &S.UV[(lt0 + i) * SA + kb];
-                dst[0] = acc[i][0];
-                dst[1] = acc[i][1];
-            }
-        } else {
-            // x-Nyquist column (kx = W/2), rows 5 (task - nmain) .. +4: P/Q from S.XN; its
-            // Nyquist row keeps the full phase
-            const int lt0 = 5 * (task - nmain);
-            float4 acc[5];
-#pragma unroll
-            for (int i = 0; i < 5; ++i) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4* tab = tA2 + (size_t)(t0 - 1 + lt0) * Hq;
-            for (int mp = Hq - 1; mp >= 0; --mp) {
-                const int4 ro = S.rowq[mp];
-                const int lsa = g.logW - 1;                       // SA = W/2
-                const float2 p1 = S.XN[ro.x >> lsa], p2 = S.XN[ro.y >> lsa], q1 = S.XN[ro.z >> lsa];
-                const float2 q2 = (2 * mp + 2 == Hh) ? make_float2(-p2.x, -p2.y) : S.XN[ro.w >> lsa];
-#pragma unroll
-                for (int i = 0; i < 5; ++i) {
-                    const float4 tw = tab[i * Hq + mp];
-                    acc[i].x = fmaf(tw.x, p1.x, fmaf(tw.z, p2.x, acc[i].x));
-                    acc[i].y = fmaf(tw.x, p1.y, fmaf(tw.z, p2.y, acc[i].y));
-                    acc[i].z = fmaf(tw.y, q1.x, fmaf(tw.w, q2.x, acc[i].z));
-                    acc[i].w = fmaf(tw.y, q1.y, fmaf(tw.w, q2.y, acc[i].w));
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < 5; ++i) S.UVN[lt0 + i] = acc[i];
+        for (int h = 0; h < 2; ++h) {
+            const int lt = 16 * tt + gq + 8 * h;
+            if (lt >= TC) continue;
+            store_combo_pairs(g, S, lt, 4 * nt + tq, make_float2(d[0][2 * h] * un, d[0][2 * h + 1] * un),
+                              make_float2(d[1][2 * h] * un, d[1][2 * h + 1] * un),
+                              make_float2(d[2][2 * h] * un, d[2][2 * h + 1] * un),
+                              make_float2(d[3][2 * h] * un, d[3][2 * h + 1] * un));
         }
     }
+}
+
+// Plain form for Hh < 16: one thread per (t, kx pair), operands reconstructed in FP32.
+__device__ __forceinline__ void stage_a_simt(const Geom& g, const Smem& S, int t0, const uint2* TA) {
+    const int Hq = g.Hh / 2, SA = g.SA, SAq = SA / 2, TC = g.TC;
+    const uint2* Tc = TA;
+    const uint2* Ts = TA + (size_t)g.TAB * Hq;
+    const float un = ldexpf(1.f, -13);
+    for (int task = threadIdx.x; task < TC * SAq; task += blockDim.x) {
+        const int lt = task / SAq, kp = task - lt * SAq, ta = t0 - 1 + lt;
+        float2 acc[4] = {};
+        for (int x = 0; x < 2; ++x) {
+            const int kx = 2 * kp + x, sb = pswz(kx, Hq);
+            for (int p = Hq - 1; p >= 0; --p) {
+                const float2 cm = unsplit_pair(Tc[ta * Hq + (p ^ pswz(ta, Hq))]);
+                const float2 sn = unsplit_pair(Ts[ta * Hq + (p ^ pswz(ta, Hq))]);
+                float v[4];
+#pragma unroll
+                for (int pl = 0; pl < 4; ++pl) {
+                    const float2 w = unsplit_pair(S.PQ[(size_t)(pl * SA + kx) * Hq + (p ^ sb)]);
+                    const float2 t = pl < 2 ? cm : sn;
+                    v[pl] = t.x * w.x + t.y * w.y;
+                }
+                if (x == 0) { acc[0].x += v[0]; acc[1].x += v[1]; acc[2].x += v[2]; acc[3].x += v[3]; }
+                else { acc[0].y += v[0]; acc[1].y += v[1]; acc[2].y += v[2]; acc[3].y += v[3]; }
+            }
+        }
+        store_combo_pairs(g, S, lt, kp, make_float2(acc[0].x * un, acc[0].y * un), make_float2(acc[1].x * un, acc[1].y * un),
+                          make_float2(acc[2].x * un, acc[2].y * un), make_float2(acc[3].x * un, acc[3].y * un));
+    }
+}
+
+__device__ __forceinline__ void stage_a(const Geom& g, const Smem& S, int t0, const uint2* TA) {
+    if ((g.Hh & 15) == 0) stage_a_mma(g, S, t0, TA);
+    else stage_a_simt(g, S, t0, TA);
+    stage_a_nyquist(g, S, t0, TA);
     __syncthreads();
 }
 
@@ -744,15 +935,20 @@ __device__ __forceinline__ int grid_index(const Geom& g, int ty, int tx) {
 }
 
 // --------------------------------------------------- a6: stage B (one chunk)
-// Evaluates v = sense * (S + g) at every grid point whose |ty| lies in the chunk
-// (t = t0 .. t0 + TC - 1, t >= 1), feeding the top-K. With kCollect, appends every
-// point with v >= thr to the candidate list instead. Tiles: 3 t x 4 tx.
+// Stage B evaluates v = sense * (S + g) at every grid point whose |ty| lies in the chunk
+// (t = t0 .. t0 + TC - 1, t >= 1) and feeds the top-K (with kCollect: appends every point
+// with v >= thr to the candidate list instead). With the stage-A combinations,
+//   A0 = sum_kx wc C0, B0 = sum_kx ws E0 give S(+t, +-tx) = A0 -+ B0 (+ g(+-tx)),
+//   A1 = sum_kx wc C1, B1 = sum_kx ws E1 give S(-t, +-tx) = A1 -+ B1 (+ g(+-tx)),
+// where wc = w cos(2 pi kx tx/(uW)), ws = w sin(..), w = 1 at kx = 0 and W/2, else 2.
 template <bool kCollect>
-__device__ __forceinline__ void stage_b(const Geom& g, const Smem& S, int t0, const float* TBc, const float* TBs,
-                                        TopK<kTopK>& top, float thr, float* dbg) {
-    const int SA = g.SA, T1p = g.T1p;
-    const int ntt = g.TC / 3, nxx = T1p / 4;
-    auto emit = [&](float raw, int j) {
+struct Emitter {
+    const Geom& g;
+    const Smem& S;
+    TopK<kTopK>& top;
+    float thr;
+    float* dbg;
+    __device__ __forceinline__ void operator()(float raw, int j) const {
         const float v = g.sense * raw;
         if (kCollect) {
             if (v >= thr) {
@@ -763,58 +959,109 @@ __device__ __forceinline__ void stage_b(const Geom& g, const Smem& S, int t0, co
             if (dbg) dbg[j] = raw;
             top.push(v, j);
         }
-    };
-    for (int task = threadIdx.x; task < ntt * nxx; task += blockDim.x) {
-        const int tt = task / nxx, xx = task - tt * nxx;
-        const int lt0 = 3 * tt, xb = 4 * xx;
-        if (t0 + lt0 > g.h0) continue;
-        float aU[3][4], aV[3][4], bU[3][4], bV[3][4];
+    }
+    // the four points of (t, tx) from (A, B) of the sign `sg` (0: +t, 1: -t)
+    __device__ __forceinline__ void quad(int sg, int t, int x, float A, float B) const {
+        const float gp = S.gP[x], gm = S.gM[x];
+        const int ts = sg ? -t : t;
+        if ((sg || t <= g.pmax) && x <= g.pmax) (*this)(A - B + gp, grid_index(g, ts, x));
+        if ((sg || t <= g.pmax) && x >= 1) (*this)(A + B + gm, grid_index(g, ts, -x));
+    }
+};
+
+// Tensor-core form (SA a multiple of 16): M = t, N = tx, K = kx < SA; the x-Nyquist column
+// is a rank-one FP32 term. A warp task is (t tile of 16, sign, two tx tiles of 8). Rows
+// past the chunk (or the tables) read the last row and are discarded. dsc = 2^-(13+kexp)
+// undoes the operand scales.
+template <bool kCollect>
+__device__ __forceinline__ void stage_b_mma(const Geom& g, const Smem& S, int t0, const uint2* TB, float dsc,
+                                            const Emitter<kCollect>& emit) {
+    const int SAq = g.SA / 2, T1 = g.T1p, T8 = g.T1p8, TC = g.TC;
+    const uint2* WC = TB;
+    const uint2* WS = TB + (size_t)T1 * SAq;
+    const float* WCN = (const float*)(TB + 2 * (size_t)T1 * SAq);
+    const float* WSN = WCN + T8;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int gq = lane >> 2, tq = lane & 3;
+    const int ntt = (TC + 15) >> 4, nnt = T8 >> 3, nng = (nnt + 1) >> 1;
+    const int ntask = ntt * 2 * nng;
+    for (int task = warp; task < ntask; task += nwarp) {
+        const int tt = task / (2 * nng);
+        const int rem = task - tt * 2 * nng;
+        const int sg = rem / nng;
+        const int nt0 = 2 * (rem - sg * nng);
+        if (t0 + 16 * tt > g.h0) continue;                       // warp-uniform
+        const bool two = nt0 + 1 < nnt;                          // warp-uniform
+        const uint2* Ca = S.CB + (size_t)sg * TC * SAq;          // C0 / C1
+        const uint2* Eb = S.CB + (size_t)(2 + sg) * TC * SAq;    // E0 / E1
+        const int r0 = min(16 * tt + gq, TC - 1), r1 = min(16 * tt + gq + 8, TC - 1);
+        const int x0 = min(8 * nt0 + gq, T1 - 1), x1 = min(8 * nt0 + 8 + gq, T1 - 1);
+        const int w0 = pswz(x0, SAq), w1 = pswz(x1, SAq);
+        float dA[2][4], dB[2][4];
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 2; ++j)
 #pragma unroll
-            for (int l = 0; l < 4; ++l) { aU[i][l] = 0.f; aV[i][l] = 0.f; bU[i][l] = 0.f; bV[i][l] = 0.f; }
-        auto step = [&](int kx, float4 u0, float4 u1, float4 u2) {
-            const float4 wc = *(const float4*)&TBc[kx * T1p + xb];
-            const float4 ws = *(const float4*)&TBs[kx * T1p + xb];
-            const float wcv[4] = {wc.x, wc.y, wc.z, wc.w};
-            const float wsv[4] = {ws.x, ws.y, ws.z, ws.w};
-            const float4 uv[3] = {u0, u1, u2};
+            for (int e = 0; e < 4; ++e) { dA[j][e] = 0.f; dB[j][e] = 0.f; }
+        for (int kp = 0; kp < SAq; kp += 8) {
+            unsigned ah[4], al[4], eh[4], el[4];
+            load_afrag(Ca, SAq, r0, r1, kp, tq, ah, al);
+            load_afrag(Eb, SAq, r0, r1, kp, tq, eh, el);
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 2; ++j) {
+                if (j == 1 && !two) break;
+                const int x = j ? x1 : x0, w = j ? w1 : w0;
+                const uint2 c0 = WC[x * SAq + ((kp + tq) ^ w)], c1 = WC[x * SAq + ((kp + tq + 4) ^ w)];
+                const uint2 s0 = WS[x * SAq + ((kp + tq) ^ w)], s1 = WS[x * SAq + ((kp + tq + 4) ^ w)];
+                mma3(dA[j], ah, al, c0, c1);
+                mma3(dB[j], eh, el, s0, s1);
+            }
+        }
+        // epilogue: fragment element e sits at row gq + 8 (e >> 1), column 2 tq + (e & 1)
+        const float* CaN = S.CBN + (size_t)sg * TC;
+        const float* EbN = S.CBN + (size_t)(2 + sg) * TC;
 #pragma unroll
-                for (int l = 0; l < 4; ++l) {
-                    aU[i][l] = fmaf(wcv[l], uv[i].x, aU[i][l]);
-                    aV[i][l] = fmaf(wcv[l], uv[i].w, aV[i][l]);
-                    bU[i][l] = fmaf(wsv[l], uv[i].y, bU[i][l]);
-                    bV[i][l] = fmaf(wsv[l], uv[i].z, bV[i][l]);
-                }
-        };
-        // x-Nyquist column first (highest frequency), then slots SA-1 .. 0
-        step(SA, S.UVN[lt0], S.UVN[lt0 + 1], S.UVN[lt0 + 2]);
-        for (int kx = SA - 1; kx >= 0; --kx)
-            step(kx, S.UV[lt0 * SA + kx], S.UV[(lt0 + 1) * SA + kx], S.UV[(lt0 + 2) * SA + kx]);
+        for (int j = 0; j < 2; ++j) {
+            if (j == 1 && !two) break;
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const int t = t0 + lt0 + i;
-            if (t > g.h0) continue;
-#pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                const int x = xb + l;
-                if (x > g.h0) continue;
-                const float gp = S.gP[x], gm = S.gM[x];
-                const float A0 = aU[i][l] - aV[i][l], A1 = aU[i][l] + aV[i][l];
-                if (t <= g.pmax && x <= g.pmax) emit(A0 - bU[i][l] - bV[i][l] + gp, grid_index(g, t, x));
-                if (t <= g.pmax && x >= 1) emit(A0 + bU[i][l] + bV[i][l] + gm, grid_index(g, t, -x));
-                if (x <= g.pmax) emit(A1 - bU[i][l] + bV[i][l] + gp, grid_index(g, -t, x));
-                if (x >= 1) emit(A1 + bU[i][l] - bV[i][l] + gm, grid_index(g, -t, -x));
+            for (int e = 0; e < 4; ++e) {
+                const int lt = 16 * tt + gq + 8 * (e >> 1);
+                const int x = 8 * (nt0 + j) + 2 * tq + (e & 1);
+                const int t = t0 + lt;
+                if (lt >= TC || t > g.h0 || x > g.h0) continue;
+                const float A = fmaf(WCN[x], CaN[lt], dA[j][e] * dsc);
+                const float B = fmaf(WSN[x], EbN[lt], dB[j][e] * dsc);
+                emit.quad(sg, t, x, A, B);
             }
         }
     }
-    // the t = 0 row: S = 0, the surface is g(tx)
-    if (t0 == 1) {
-        for (int x = threadIdx.x; x <= g.h0; x += blockDim.x) {
-            if (x <= g.pmax) emit(S.gP[x], grid_index(g, 0, x));
-            if (x >= 1) emit(S.gM[x], grid_index(g, 0, -x));
+}
+
+// Plain form for SA < 16: one thread per (t, tx), operands reconstructed in FP32.
+template <bool kCollect>
+__device__ __forceinline__ void stage_b_simt(const Geom& g, const Smem& S, int t0, const uint2* TB, float dsc,
+                                             const Emitter<kCollect>& emit) {
+    const int SAq = g.SA / 2, T1 = g.T1p, T8 = g.T1p8, TC = g.TC;
+    const uint2* WC = TB;
+    const uint2* WS = TB + (size_t)T1 * SAq;
+    const float* WCN = (const float*)(TB + 2 * (size_t)T1 * SAq);
+    const float* WSN = WCN + T8;
+    for (int task = threadIdx.x; task < TC * T1; task += blockDim.x) {
+        const int lt = task / T1, x = task - lt * T1, t = t0 + lt;
+        if (t > g.h0 || x > g.h0) continue;
+        const int sl = pswz(lt, SAq), sx = pswz(x, SAq);
+        for (int sg = 0; sg < 2; ++sg) {
+            const uint2* Ca = S.CB + ((size_t)sg * TC + lt) * SAq;
+            const uint2* Eb = S.CB + ((size_t)(2 + sg) * TC + lt) * SAq;
+            float A = 0.f, B = 0.f;
+            for (int kp = SAq - 1; kp >= 0; --kp) {
+                const float2 wc = unsplit_pair(WC[x * SAq + (kp ^ sx)]), ws = unsplit_pair(WS[x * SAq + (kp ^ sx)]);
+                const float2 ca = unsplit_pair(Ca[kp ^ sl]), eb = unsplit_pair(Eb[kp ^ sl]);
+                A += wc.x * ca.x + wc.y * ca.y;
+                B += ws.x * eb.x + ws.y * eb.y;
+            }
+            A = fmaf(WCN[x], S.CBN[sg * TC + lt], A * dsc);
+            B = fmaf(WSN[x], S.CBN[(2 + sg) * TC + lt], B * dsc);
+            emit.quad(sg, t, x, A, B);
         }
     }
 }
@@ -823,31 +1070,71 @@ __device__ __forceinline__ void stage_b(const Geom& g, const Smem& S, int t0, co
 template <bool kCollect>
 __device__ __forceinline__ void upsampled_pass(const Geom& g, const Smem& S, TopK<kTopK>& top, float thr,
                                                float* dbg) {
-    const float4* tA2 = g.tables_smem ? S.TA : g.tA2;
-    const float* TBc = g.tables_smem ? S.TBc : g.tB_wc;
-    const float* TBs = g.tables_smem ? S.TBs : g.tB_ws;
+    const uint2* TA = g.tables_smem ? S.TA : g.tAh;
+    const uint2* TB = g.tables_smem ? S.TB : g.tBh;
+    const float dsc = ldexpf(1.f, -13 - S.misc[3]);
+    const Emitter<kCollect> emit{g, S, top, thr, dbg};
     for (int c = 0; c < g.nchunk; ++c) {
         const int t0 = 1 + c * g.TC;
-        stage_a(g, S, t0, tA2);
-        stage_b<kCollect>(g, S, t0, TBc, TBs, top, thr, dbg);
+        stage_a(g, S, t0, TA);
+        if ((g.SA & 15) == 0) stage_b_mma<kCollect>(g, S, t0, TB, dsc, emit);
+        else stage_b_simt<kCollect>(g, S, t0, TB, dsc, emit);
+        // the t = 0 row: S = 0, the surface is g(tx)
+        if (t0 == 1) {
+            for (int x = threadIdx.x; x <= g.h0; x += blockDim.x) {
+                if (x <= g.pmax) emit(S.gP[x], grid_index(g, 0, x));
+                if (x >= 1) emit(S.gM[x], grid_index(g, 0, -x));
+            }
+        }
         __syncthreads();
     }
 }
 
+// Second surface pass that lists every point with v >= thr (S.cj/S.cv, count returned).
+static __device__ int collect_near(const Geom& g, const Smem& S, float thr) {
+    TopK<kTopK> unused;
+    unused.init();
+    if (threadIdx.x == 0) S.misc[1] = 0;
+    __syncthreads();
+    upsampled_pass<true>(g, S, unused, thr, nullptr);
+    const int nc = S.misc[1];
+    __syncthreads();
+    return nc;
+}
+
 // ---------------------------------- a7 guard: exact FP32 pair differences
 // X'(ky, kx) for any row and column, from the P/Q layout.
+// P(m, kx) and Q(m, kx), m = 1 .. Hh, of a regular column from the fp16 planes (unscaled
+// by inv = 2^-kexp)
+__device__ __forceinline__ void pq_at(const Geom& g, const Smem& S, int m, int kx, float inv, float2* P, float2* Q) {
+    const int SA = g.SA, Hq = g.Hh / 2, k = m - 1, q = (k >> 1) ^ pswz(kx, Hq);
+    const float2 pr = unsplit_pair(S.PQ[(0 * SA + kx) * Hq + q]), pi = unsplit_pair(S.PQ[(1 * SA + kx) * Hq + q]);
+    const float2 qr = unsplit_pair(S.PQ[(2 * SA + kx) * Hq + q]), qi = unsplit_pair(S.PQ[(3 * SA + kx) * Hq + q]);
+    *P = (k & 1) ? make_float2(pr.y * inv, pi.y * inv) : make_float2(pr.x * inv, pi.x * inv);
+    *Q = (k & 1) ? make_float2(qr.y * inv, qi.y * inv) : make_float2(qr.x * inv, qi.x * inv);
+}
+
+// X'(ky, kx) for any row and column: X'(0) from S.X0, X'(Hh) = P(Hh), X'(+-m) = (P -+... ) / 2
+// from the planes, and the x-Nyquist column from the FP32 P/Q rows in XN.
 __device__ __forceinline__ float2 xprime(const Geom& g, const Smem& S, int ky, int kx) {
     const int Hh = g.Hh;
-    const bool nyq = (2 * kx == g.W);
-    const float2* colbase = nyq ? S.XN : S.A + kx;
-    const int cstride = nyq ? 1 : g.SA;
-    if (ky == 0 || ky == Hh) return colbase[posH(g, ky) * cstride];
-    if (ky < Hh) {
-        const float2 p = colbase[posH(g, ky) * cstride], q = colbase[posH(g, g.H - ky) * cstride];
-        return make_float2(0.5f * (p.x + q.x), 0.5f * (p.y + q.y));
+    if (2 * kx == g.W) {
+        const float2* colbase = S.XN;
+        if (ky == 0 || ky == Hh) return colbase[posH(g, ky)];
+        if (ky < Hh) {
+            const float2 p = colbase[posH(g, ky)], q = colbase[posH(g, g.H - ky)];
+            return make_float2(0.5f * (p.x + q.x), 0.5f * (p.y + q.y));
+        }
+        const int m = g.H - ky;
+        const float2 p = colbase[posH(g, m)], q = colbase[posH(g, ky)];
+        return make_float2(0.5f * (p.x - q.x), 0.5f * (p.y - q.y));
     }
-    const int m = g.H - ky;
-    const float2 p = colbase[posH(g, m) * cstride], q = colbase[posH(g, ky) * cstride];
+    if (ky == 0) return S.X0[kx];
+    const float inv = ldexpf(1.f, -S.misc[3]);
+    float2 p, q;
+    pq_at(g, S, ky <= Hh ? ky : g.H - ky, kx, inv, &p, &q);
+    if (ky == Hh) return p;
+    if (ky < Hh) return make_float2(0.5f * (p.x + q.x), 0.5f * (p.y + q.y));
     return make_float2(0.5f * (p.x - q.x), 0.5f * (p.y - q.y));
 }
 
@@ -885,9 +1172,9 @@ constexpr int kPdGroup = 3, kPdParts = 4;
 
 static __device__ int pair_difference_guard(const Geom& g, const Smem& S, int nc, float scale, int* nl2,
                                             float* dwin) {
-    const int H = g.H, Wc = g.Wc, u = g.u, Hh = g.Hh, T1p = g.T1p, SA = g.SA;
-    const float* TBc = g.tables_smem ? S.TBc : g.tB_wc;
-    const float* TBs = g.tables_smem ? S.TBs : g.tB_ws;
+    const int H = g.H, Wc = g.Wc, u = g.u, Hh = g.Hh, T1p = g.T1p;
+    const float* TBc = g.tB_wc;
+    const float* TBs = g.tB_ws;
     constexpr int NF = kPdGroup + 1;
     float2* fx = (float2*)S.UV;             // [NF][Wc]   factor vectors over kx (slot 0: G's)
     float2* Eyc = fx + NF * Wc;             // [kPdGroup][H]  Ey(ky, ty)
@@ -936,22 +1223,11 @@ static __device__ int pair_difference_guard(const Geom& g, const Smem& S, int nc
         const int fbeg = first ? 0 : 1, fend = 1 + ng;
         for (int task = threadIdx.x; task < kPdParts * H; task += blockDim.x) {
             const int q = task / H, ky = task - q * H;
-            // X'(ky, .) from the P/Q rows: X' = P (ky = 0, Hh), (P + Q)/2 (ky < Hh), (P - Q)/2
-            int ra, rb;
-            float sb;
-            if (ky == 0 || ky == Hh) { ra = posH(g, ky); rb = ra; sb = 0.f; }
-            else if (ky < Hh) { ra = posH(g, ky); rb = posH(g, H - ky); sb = 1.f; }
-            else { ra = posH(g, H - ky); rb = posH(g, ky); sb = -1.f; }
-            const float sa = (sb == 0.f) ? 1.f : 0.5f;
-            sb *= 0.5f;
             float2 acc[NF], accn[NF];
 #pragma unroll
             for (int f = 0; f < NF; ++f) { acc[f] = make_float2(0.f, 0.f); accn[f] = acc[f]; }
             for (int kx = Wc - 1 - q; kx >= 0; kx -= kPdParts) {
-                float2 p, r;
-                if (kx == kn) { p = S.XN[ra]; r = S.XN[rb]; }
-                else { p = S.A[ra * SA + kx]; r = S.A[rb * SA + kx]; }
-                const float2 xp = make_float2(sa * p.x + sb * r.x, sa * p.y + sb * r.y);
+                const float2 xp = xprime(g, S, ky, kx);
                 const bool nn = (ky == Hh && kx == kn);
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
@@ -1223,11 +1499,6 @@ __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
     build_pass_twiddles<W>(S.t4w, S.tw, g.logNtw);
     tables_bar_init(S);
     unsigned bar_parity = 0;
-    for (int mp = threadIdx.x; mp < g.Hh / 2; mp += blockDim.x) {
-        const int m1 = 2 * mp + 1, m2 = 2 * mp + 2;
-        S.rowq[mp] = make_int4(posH(g, m1) * g.SA, posH(g, m2) * g.SA, posH(g, g.H - m1) * g.SA,
-                               posH(g, g.H - m2) * g.SA);
-    }
     __syncthreads();
     const size_t elem = g.in_dtype == 0 ? 2 : 4;
     for (long long f = blockIdx.x; f < b.n; f += gridDim.x) {
@@ -1242,7 +1513,7 @@ __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
         const int py = wrap_shift(ip >> g.logW, g.H), px = wrap_shift(ip & (g.W - 1), g.W);
         __syncthreads();
         stage_tables_async(g, S);                          // overlaps the P/Q build
-        build_pq_and_g(g, S, py, px);
+        build_pq_and_g(g, S, py, px, scale);
         const bool staged = stage_tables_wait(g, S, bar_parity);
         if (__syncthreads_or(!staged)) {
             // the copies never completed: report it for this frame and stop this CTA, after
@@ -1311,11 +1582,7 @@ __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
                     __syncthreads();
                 } else {
                     // a thread holds more near-ties than it kept: collect them all with a second pass
-                    if (threadIdx.x == 0) S.misc[1] = 0;
-                    __syncthreads();
-                    upsampled_pass<true>(g, S, top, thr, nullptr);
-                    nc = S.misc[1];
-                    __syncthreads();
+                    nc = collect_near(g, S, thr);
                     if (nc > kMaxCand) {
                         flags |= 0x08u;
                         nc = 1;
