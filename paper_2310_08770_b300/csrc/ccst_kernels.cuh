@@ -175,26 +175,38 @@ __device__ __forceinline__ float2 unsplit_pair(uint2 v) {
 // The 16 lanes of a half-warp (4 rows x 4 pairs) of every fragment load then hit distinct
 // 8-byte bank pairs.
 __host__ __device__ __forceinline__ int pswz(int r, int kp) { return ((r & 3) << 2) & (kp - 1); }
+// (not volatile: the compiler may interleave independent accumulations)
 __device__ __forceinline__ void mma_f16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
                  "{%0,%1,%2,%3};\n"
                  : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
                  : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
-// d += a * b in the three-product split form; a_h/a_l: A fragment halves, b: the two
-// uint2 {hi, lo} of the B fragment
-__device__ __forceinline__ void mma3(float (&d)[4], const unsigned (&ah)[4], const unsigned (&al)[4], uint2 b0,
-                                     uint2 b1) {
-    mma_f16(d, al, b0.x, b1.x);
-    mma_f16(d, ah, b0.y, b1.y);
-    mma_f16(d, ah, b0.x, b1.x);
-}
-// A fragment (rows ra, rb; K pairs kp + tq and kp + tq + 4) of a [row][kpr] operand
-__device__ __forceinline__ void load_afrag(const uint2* P, int kpr, int ra, int rb, int kp, int tq, unsigned (&h)[4],
+// Fragment addressing of a swizzled [row][KP] operand: the thread reads K pairs
+// 8 s + tq and 8 s + tq + 4 of k16 step s. Writing 8 s = 16 a + 8 b, the swizzle only
+// touches bits 2-3, so pair 16 a + ((8 b + 4 h + tq) ^ pswz(r)): the four row offsets
+// o[b][h] are computed once per task and every load is one of them plus 16 a.
+// The operand lives in the kernel's dynamic shared memory; the offsets are 32-bit byte
+// offsets into it, so that each load is one shared load with an immediate displacement.
+extern __shared__ __align__(16) unsigned char ccst_smem[];
+struct RowOffsets {
+    unsigned o[2][2];
+    __device__ __forceinline__ RowOffsets(const uint2* P, int KP, int r, int tq) {
+        const int c = pswz(r, KP);
+        const unsigned base = (unsigned)((const unsigned char*)(P + r * KP) - ccst_smem);
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) o[b][h] = base + 8u * (unsigned)(((8 * b + 4 * h + tq) ^ c) & (KP - 1));
+    }
+    __device__ __forceinline__ uint2 at(int s, int h) const {
+        return *reinterpret_cast<const uint2*>(ccst_smem + o[s & 1][h] + 128 * (s >> 1));
+    }
+};
+// A fragment of k16 step s from rows ra, rb (16-row tile: ra = gq, rb = gq + 8)
+__device__ __forceinline__ void load_afrag(const RowOffsets& ra, const RowOffsets& rb, int s, unsigned (&h)[4],
                                            unsigned (&l)[4]) {
-    const int sa = pswz(ra, kpr), sb = pswz(rb, kpr);
-    const uint2 v0 = P[ra * kpr + ((kp + tq) ^ sa)], v1 = P[rb * kpr + ((kp + tq) ^ sb)];
-    const uint2 v2 = P[ra * kpr + ((kp + tq + 4) ^ sa)], v3 = P[rb * kpr + ((kp + tq + 4) ^ sb)];
+    const uint2 v0 = ra.at(s, 0), v1 = rb.at(s, 0), v2 = ra.at(s, 1), v3 = rb.at(s, 1);
     h[0] = v0.x; h[1] = v1.x; h[2] = v2.x; h[3] = v3.x;
     l[0] = v0.y; l[1] = v1.y; l[2] = v2.y; l[3] = v3.y;
 }
@@ -849,8 +861,10 @@ __device__ __forceinline__ void store_combo_pairs(const Geom& g, const Smem& S, 
 // Tensor-core form (Hh a multiple of 16): M = t, N = kx, K = m. A warp task is one t tile
 // of 16 by one kx tile of 8, with the four products (Cm1 Pr, Cm1 Pi, S Qr, S Qi) sharing
 // the A fragments. Rows past the chunk read its last row and are not stored.
+template <int H>
 __device__ __forceinline__ void stage_a_mma(const Geom& g, const Smem& S, int t0, const uint2* TA) {
-    const int Hq = g.Hh / 2, SA = g.SA, TC = g.TC;
+    constexpr int Hq = H / 4, NKS = Hq / 8;
+    const int SA = g.SA, TC = g.TC;
     const uint2* Tc = TA;
     const uint2* Ts = TA + (size_t)g.TAB * Hq;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -861,24 +875,29 @@ __device__ __forceinline__ void stage_a_mma(const Geom& g, const Smem& S, int t0
         const int tt = task / nnt, nt = task - tt * nnt;
         if (t0 + 16 * tt > g.h0) continue;                       // warp-uniform: all rows past h0
         const int r0 = t0 - 1 + min(16 * tt + gq, TC - 1), r1 = t0 - 1 + min(16 * tt + gq + 8, TC - 1);
+        const RowOffsets c0(Tc, Hq, r0, tq), c1(Tc, Hq, r1, tq), s0(Ts, Hq, r0, tq), s1(Ts, Hq, r1, tq);
         const int kxr = 8 * nt + gq;
-        const int sb = pswz(kxr, Hq);
+        const RowOffsets pr(S.PQ, Hq, kxr, tq), pi(S.PQ + SA * Hq, Hq, kxr, tq), qr(S.PQ + 2 * SA * Hq, Hq, kxr, tq),
+            qi(S.PQ + 3 * SA * Hq, Hq, kxr, tq);
         float d[4][4];
 #pragma unroll
         for (int pl = 0; pl < 4; ++pl)
 #pragma unroll
             for (int e = 0; e < 4; ++e) d[pl][e] = 0.f;
-        for (int kp = 0; kp < Hq; kp += 8) {
-            unsigned ch[4], cl[4], sh[4], sl[4];
-            load_afrag(Tc, Hq, r0, r1, kp, tq, ch, cl);
-            load_afrag(Ts, Hq, r0, r1, kp, tq, sh, sl);
 #pragma unroll
-            for (int pl = 0; pl < 4; ++pl) {
-                const uint2* P = S.PQ + (size_t)(pl * SA + kxr) * Hq;
-                const uint2 b0 = P[(kp + tq) ^ sb], b1 = P[(kp + tq + 4) ^ sb];
-                if (pl < 2) mma3(d[pl], ch, cl, b0, b1);
-                else mma3(d[pl], sh, sl, b0, b1);
-            }
+        for (int s = 0; s < NKS; ++s) {
+            unsigned ch[4], cl[4], sh[4], sl[4];
+            load_afrag(c0, c1, s, ch, cl);
+            load_afrag(s0, s1, s, sh, sl);
+            const uint2 b0[4] = {pr.at(s, 0), pi.at(s, 0), qr.at(s, 0), qi.at(s, 0)};
+            const uint2 b1[4] = {pr.at(s, 1), pi.at(s, 1), qr.at(s, 1), qi.at(s, 1)};
+            // the three split products, each issued across the four independent accumulators
+#pragma unroll
+            for (int pl = 0; pl < 4; ++pl) mma_f16(d[pl], pl < 2 ? cl : sl, b0[pl].x, b1[pl].x);
+#pragma unroll
+            for (int pl = 0; pl < 4; ++pl) mma_f16(d[pl], pl < 2 ? ch : sh, b0[pl].y, b1[pl].y);
+#pragma unroll
+            for (int pl = 0; pl < 4; ++pl) mma_f16(d[pl], pl < 2 ? ch : sh, b0[pl].x, b1[pl].x);
         }
         // element e: row gq + 8 (e >> 1), kx 8 nt + 2 tq + (e & 1)
 #pragma unroll
@@ -923,8 +942,9 @@ __device__ __forceinline__ void stage_a_simt(const Geom& g, const Smem& S, int t
     }
 }
 
+template <int H>
 __device__ __forceinline__ void stage_a(const Geom& g, const Smem& S, int t0, const uint2* TA) {
-    if ((g.Hh & 15) == 0) stage_a_mma(g, S, t0, TA);
+    if (H % 32 == 0 && g.tables_smem) stage_a_mma<H>(g, S, t0, TA);
     else stage_a_simt(g, S, t0, TA);
     stage_a_nyquist(g, S, t0, TA);
     __syncthreads();
@@ -948,24 +968,43 @@ struct Emitter {
     TopK<kTopK>& top;
     float thr;
     float* dbg;
-    __device__ __forceinline__ void operator()(float raw, int j) const {
+    // thr: candidate-list threshold (kCollect), else a lower bound below which no point can
+    // be the maximum or within the near-tie band of it (the (0, 0) point's value minus that
+    // band): most points stop at this one comparison.
+    __device__ __forceinline__ void operator()(float raw, int ty, int tx) const {
         const float v = g.sense * raw;
+        if (!kCollect && dbg) dbg[grid_index(g, ty, tx)] = raw;
+        if (!(v >= thr)) return;
+        const int j = grid_index(g, ty, tx);
         if (kCollect) {
-            if (v >= thr) {
-                const int k = atomicAdd(&S.misc[1], 1);
-                if (k < kMaxCand) { S.cj[k] = j; S.cv[k] = v; }
-            }
+            const int k = atomicAdd(&S.misc[1], 1);
+            if (k < kMaxCand) { S.cj[k] = j; S.cv[k] = v; }
         } else {
-            if (dbg) dbg[j] = raw;
             top.push(v, j);
         }
     }
-    // the four points of (t, tx) from (A, B) of the sign `sg` (0: +t, 1: -t)
+    // the two points (+-tx) of row t of the sign `sg` (0: +t, 1: -t) from (A, B)
     __device__ __forceinline__ void quad(int sg, int t, int x, float A, float B) const {
-        const float gp = S.gP[x], gm = S.gM[x];
+        const float rp = A - B + S.gP[x], rm = A + B + S.gM[x];
+        if (!kCollect && dbg) {
+            const int ts = sg ? -t : t;
+            if ((sg || t <= g.pmax) && x <= g.pmax) dbg[grid_index(g, ts, x)] = rp;
+            if ((sg || t <= g.pmax) && x >= 1) dbg[grid_index(g, ts, -x)] = rm;
+        }
+        if (!(g.sense * rp >= thr) && !(g.sense * rm >= thr)) return;      // the common case
         const int ts = sg ? -t : t;
-        if ((sg || t <= g.pmax) && x <= g.pmax) (*this)(A - B + gp, grid_index(g, ts, x));
-        if ((sg || t <= g.pmax) && x >= 1) (*this)(A + B + gm, grid_index(g, ts, -x));
+        if ((sg || t <= g.pmax) && x <= g.pmax) keep(g.sense * rp, ts, x);
+        if ((sg || t <= g.pmax) && x >= 1) keep(g.sense * rm, ts, -x);
+    }
+    __device__ __forceinline__ void keep(float v, int ty, int tx) const {
+        if (!(v >= thr)) return;
+        const int j = grid_index(g, ty, tx);
+        if (kCollect) {
+            const int k = atomicAdd(&S.misc[1], 1);
+            if (k < kMaxCand) { S.cj[k] = j; S.cv[k] = v; }
+        } else {
+            top.push(v, j);
+        }
     }
 };
 
@@ -973,10 +1012,11 @@ struct Emitter {
 // is a rank-one FP32 term. A warp task is (t tile of 16, sign, two tx tiles of 8). Rows
 // past the chunk (or the tables) read the last row and are discarded. dsc = 2^-(13+kexp)
 // undoes the operand scales.
-template <bool kCollect>
+template <int W, bool kCollect>
 __device__ __forceinline__ void stage_b_mma(const Geom& g, const Smem& S, int t0, const uint2* TB, float dsc,
                                             const Emitter<kCollect>& emit) {
-    const int SAq = g.SA / 2, T1 = g.T1p, T8 = g.T1p8, TC = g.TC;
+    constexpr int SAq = W / 4, NKS = SAq / 8;
+    const int T1 = g.T1p, T8 = g.T1p8, TC = g.TC;
     const uint2* WC = TB;
     const uint2* WS = TB + (size_t)T1 * SAq;
     const float* WCN = (const float*)(TB + 2 * (size_t)T1 * SAq);
@@ -995,42 +1035,52 @@ __device__ __forceinline__ void stage_b_mma(const Geom& g, const Smem& S, int t0
         const uint2* Ca = S.CB + (size_t)sg * TC * SAq;          // C0 / C1
         const uint2* Eb = S.CB + (size_t)(2 + sg) * TC * SAq;    // E0 / E1
         const int r0 = min(16 * tt + gq, TC - 1), r1 = min(16 * tt + gq + 8, TC - 1);
-        const int x0 = min(8 * nt0 + gq, T1 - 1), x1 = min(8 * nt0 + 8 + gq, T1 - 1);
-        const int w0 = pswz(x0, SAq), w1 = pswz(x1, SAq);
+        const int x0 = min(8 * nt0 + gq, T1 - 1), x1 = two ? min(8 * nt0 + 8 + gq, T1 - 1) : x0;
+        const RowOffsets ca0(Ca, SAq, r0, tq), ca1(Ca, SAq, r1, tq), eb0(Eb, SAq, r0, tq), eb1(Eb, SAq, r1, tq);
+        const RowOffsets wc0(WC, SAq, x0, tq), wc1(WC, SAq, x1, tq), ws0(WS, SAq, x0, tq), ws1(WS, SAq, x1, tq);
         float dA[2][4], dB[2][4];
 #pragma unroll
         for (int j = 0; j < 2; ++j)
 #pragma unroll
             for (int e = 0; e < 4; ++e) { dA[j][e] = 0.f; dB[j][e] = 0.f; }
-        for (int kp = 0; kp < SAq; kp += 8) {
-            unsigned ah[4], al[4], eh[4], el[4];
-            load_afrag(Ca, SAq, r0, r1, kp, tq, ah, al);
-            load_afrag(Eb, SAq, r0, r1, kp, tq, eh, el);
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                if (j == 1 && !two) break;
-                const int x = j ? x1 : x0, w = j ? w1 : w0;
-                const uint2 c0 = WC[x * SAq + ((kp + tq) ^ w)], c1 = WC[x * SAq + ((kp + tq + 4) ^ w)];
-                const uint2 s0 = WS[x * SAq + ((kp + tq) ^ w)], s1 = WS[x * SAq + ((kp + tq + 4) ^ w)];
-                mma3(dA[j], ah, al, c0, c1);
-                mma3(dB[j], eh, el, s0, s1);
-            }
+        for (int s = 0; s < NKS; ++s) {
+            unsigned ah[4], al[4], eh[4], el[4];
+            load_afrag(ca0, ca1, s, ah, al);
+            load_afrag(eb0, eb1, s, eh, el);
+            const uint2 c0[2] = {wc0.at(s, 0), wc1.at(s, 0)}, c1[2] = {wc0.at(s, 1), wc1.at(s, 1)};
+            const uint2 s0[2] = {ws0.at(s, 0), ws1.at(s, 0)}, s1[2] = {ws0.at(s, 1), ws1.at(s, 1)};
+            // the three split products, each issued across the four independent accumulators
+            // (for a single tx tile, x1 = x0 repeats a valid row and its results are unused)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) { mma_f16(dA[j], al, c0[j].x, c1[j].x); mma_f16(dB[j], el, s0[j].x, s1[j].x); }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) { mma_f16(dA[j], ah, c0[j].y, c1[j].y); mma_f16(dB[j], eh, s0[j].y, s1[j].y); }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) { mma_f16(dA[j], ah, c0[j].x, c1[j].x); mma_f16(dB[j], eh, s0[j].x, s1[j].x); }
         }
-        // epilogue: fragment element e sits at row gq + 8 (e >> 1), column 2 tq + (e & 1)
+        // epilogue: fragment element e sits at row gq + 8 (e >> 1), column 2 tq + (e & 1).
+        // Per row h: the x-Nyquist terms; per column: the tables' kx = W/2 entries and g(+-x).
         const float* CaN = S.CBN + (size_t)sg * TC;
         const float* EbN = S.CBN + (size_t)(2 + sg) * TC;
+        const int lt0 = 16 * tt + gq;
+        const int ltc[2] = {min(lt0, TC - 1), min(lt0 + 8, TC - 1)};
+        const float can[2] = {CaN[ltc[0]], CaN[ltc[1]]}, ebn[2] = {EbN[ltc[0]], EbN[ltc[1]]};
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             if (j == 1 && !two) break;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int lt = 16 * tt + gq + 8 * (e >> 1);
-                const int x = 8 * (nt0 + j) + 2 * tq + (e & 1);
-                const int t = t0 + lt;
-                if (lt >= TC || t > g.h0 || x > g.h0) continue;
-                const float A = fmaf(WCN[x], CaN[lt], dA[j][e] * dsc);
-                const float B = fmaf(WSN[x], EbN[lt], dB[j][e] * dsc);
-                emit.quad(sg, t, x, A, B);
+            for (int xo = 0; xo < 2; ++xo) {
+                const int x = 8 * (nt0 + j) + 2 * tq + xo;
+                if (x > g.h0) continue;
+                const float wcn = WCN[x], wsn = WSN[x];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int lt = lt0 + 8 * h, t = t0 + lt;
+                    if (lt >= TC || t > g.h0) continue;
+                    const int e = 2 * h + xo;
+                    emit.quad(sg, t, x, fmaf(wcn, can[h], dA[j][e] * dsc), fmaf(wsn, ebn[h], dB[j][e] * dsc));
+                }
             }
         }
     }
@@ -1067,7 +1117,7 @@ __device__ __forceinline__ void stage_b_simt(const Geom& g, const Smem& S, int t
 }
 
 // Full upsampled surface pass (all chunks): top-K, or candidate collection.
-template <bool kCollect>
+template <int H, int W, bool kCollect>
 __device__ __forceinline__ void upsampled_pass(const Geom& g, const Smem& S, TopK<kTopK>& top, float thr,
                                                float* dbg) {
     const uint2* TA = g.tables_smem ? S.TA : g.tAh;
@@ -1076,14 +1126,14 @@ __device__ __forceinline__ void upsampled_pass(const Geom& g, const Smem& S, Top
     const Emitter<kCollect> emit{g, S, top, thr, dbg};
     for (int c = 0; c < g.nchunk; ++c) {
         const int t0 = 1 + c * g.TC;
-        stage_a(g, S, t0, TA);
-        if ((g.SA & 15) == 0) stage_b_mma<kCollect>(g, S, t0, TB, dsc, emit);
+        stage_a<H>(g, S, t0, TA);
+        if (W % 32 == 0 && g.tables_smem) stage_b_mma<W, kCollect>(g, S, t0, TB, dsc, emit);
         else stage_b_simt<kCollect>(g, S, t0, TB, dsc, emit);
         // the t = 0 row: S = 0, the surface is g(tx)
         if (t0 == 1) {
             for (int x = threadIdx.x; x <= g.h0; x += blockDim.x) {
-                if (x <= g.pmax) emit(S.gP[x], grid_index(g, 0, x));
-                if (x >= 1) emit(S.gM[x], grid_index(g, 0, -x));
+                if (x <= g.pmax) emit(S.gP[x], 0, x);
+                if (x >= 1) emit(S.gM[x], 0, -x);
             }
         }
         __syncthreads();
@@ -1091,12 +1141,13 @@ __device__ __forceinline__ void upsampled_pass(const Geom& g, const Smem& S, Top
 }
 
 // Second surface pass that lists every point with v >= thr (S.cj/S.cv, count returned).
+template <int H, int W>
 static __device__ int collect_near(const Geom& g, const Smem& S, float thr) {
     TopK<kTopK> unused;
     unused.init();
     if (threadIdx.x == 0) S.misc[1] = 0;
     __syncthreads();
-    upsampled_pass<true>(g, S, unused, thr, nullptr);
+    upsampled_pass<H, W, true>(g, S, unused, thr, nullptr);
     const int nc = S.misc[1];
     __syncthreads();
     return nc;
@@ -1491,8 +1542,7 @@ static __device__ int df_reevaluate(const Geom& g, const Smem& S, const void* fr
 // One instantiation per frame size (H, W); the host picks it through track_kernel_for().
 template <int H, int W>
 __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Smem S = carve(g, smem_raw);
+    const Smem S = carve(g, ccst_smem);
     for (int k = threadIdx.x; k < g.Ntw / 2; k += blockDim.x) S.tw[k] = g.tw32[k];
     __syncthreads();
     build_pass_twiddles<H>(S.t4h, S.tw, g.logNtw);
@@ -1545,7 +1595,9 @@ __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
         TopK<kTopK> top;
         top.init();
         float* dbg = b.dbg_sub ? b.dbg_sub + (size_t)f * g.M * g.M : nullptr;
-        upsampled_pass<false>(g, S, top, 0.f, dbg);
+        // no point below the (0, 0) point's value minus the near-tie band can matter
+        const float lb = g.sense * S.gP[0] - g.tau0 * scale;
+        upsampled_pass<H, W, false>(g, S, top, lb, dbg);
         float vw = top.v[0];
         int jw = top.j[0];
         block_argmax(vw, jw, S.rv, S.rj);
@@ -1582,7 +1634,7 @@ __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
                     __syncthreads();
                 } else {
                     // a thread holds more near-ties than it kept: collect them all with a second pass
-                    nc = collect_near(g, S, thr);
+                    nc = collect_near<H, W>(g, S, thr);
                     if (nc > kMaxCand) {
                         flags |= 0x08u;
                         nc = 1;
