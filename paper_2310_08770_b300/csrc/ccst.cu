@@ -179,10 +179,7 @@ bool plan_geometry(int H, int W, const ccst_params& p, size_t smem_limit, Geom* 
     g.H = H; g.W = W; g.logH = ilog2(H); g.logW = ilog2(W); g.Hh = H / 2;
     g.Wc = W / 2 + 1; g.Wcp = (g.Wc + 1) & ~1;
     g.SA = W / 2;
-    const int pg = split_n2(W) > 1 ? split_n2(W) : W;   // padding group of the packed rows
-    const int len = W + W / pg;
-    g.SZ = ((len + 7) / 16) * 16 + 8;                    // >= len and = 8 (mod 16): conflict-free passes
-    if (g.SZ < len) g.SZ += 16;
+    g.SZ = packed_row_stride(W);                         // the stride the kernels assume
     g.u = p.upsample; g.M = (3 * p.upsample + 1) / 2; g.h0 = g.M / 2; g.pmax = g.M - 1 - g.h0;
     g.T1p = (g.h0 + 1 + 3) & ~3;
     g.T1p8 = (g.h0 + 1 + 7) & ~7;

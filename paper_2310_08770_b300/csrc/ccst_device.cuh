@@ -187,6 +187,31 @@ __device__ __forceinline__ void block_argmax(float& v, int& j, float* sv, int* s
     __syncthreads();
 }
 
+// block_argmax fused with a block-wide sum of s (returned); sv/sj/ss: >= 32 entries each.
+__device__ __forceinline__ float block_argmax_sum(float& v, int& j, float s, float* sv, int* sj, float* ss) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, j, o);
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (better(ov, oj, v, j)) { v = ov; j = oj; }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) { sv[wid] = v; sj[wid] = j; ss[wid] = s; }
+    __syncthreads();
+    const int nwarps = (blockDim.x + 31) >> 5;
+    v = -INFINITY;
+    j = INT_MAX;
+    float tot = 0.f;
+    for (int w = 0; w < nwarps; ++w) {
+        if (better(sv[w], sj[w], v, j)) { v = sv[w]; j = sj[w]; }
+        tot += ss[w];
+    }
+    __syncthreads();
+    return tot;
+}
+
 // Block-wide top-K; all threads return the merged list. sv/sj: >= kWarps*K entries.
 template <int K>
 __device__ __forceinline__ void block_topk(TopK<K>& t, float* sv, int* sj) {

@@ -261,6 +261,15 @@ struct Smem {
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Stride (float2) of the packed rows: >= W + W/PG (the padded row) and = 8 (mod 16), which
+// keeps the row passes' lane groups on distinct banks.
+__host__ __device__ constexpr int packed_row_stride(int W) {
+    const int pg = split_n2(W) > 1 ? split_n2(W) : W;
+    const int len = W + W / pg;
+    const int sz = ((len + 7) / 16) * 16 + 8;
+    return sz < len ? sz + 16 : sz;
+}
+
 struct SmemPlan {
     size_t a, xn, r1, b, zc, ta, tb, uv, uvn, r2, misc, total;
 };
@@ -362,14 +371,14 @@ __device__ __forceinline__ int physZ(const Geom& g, int q) {
 // ------------------------------------------------------- a1-a4: FFT correlation
 // Also scans the integer surface as the last inverse pass stores it: t2 receives each
 // thread's best (sense * HW c(y, x), y * W + x) and runner-up value; dbg, if set, the
-// whole surface.
+// whole surface. *scale_out gets this thread's part of the spectral sum sum |X|.
 template <int H, int W>
 static __device__ void fft_correlate_t(const Geom& g, const Smem& S, const void* frame, long long pitch, int vec_ok,
                                 float* scale_out, Best2& t2, float* dbg) {
     constexpr int N1w = Split<W>::N1, N2w = Split<W>::N2, N1h = Split<H>::N1, N2h = Split<H>::N2;
     constexpr int Hh = H / 2, SA = W / 2;
     constexpr int PG = N2w > 1 ? N2w : W;          // padding group of the packed rows
-    const int SZ = g.SZ;
+    constexpr int SZ = packed_row_stride(W);
     float2* Z = S.ZC;
     float2* A = S.A;
     float2* B = S.B;
@@ -469,7 +478,7 @@ static __device__ void fft_correlate_t(const Geom& g, const Smem& S, const void*
     __syncthreads();
     for (int q = threadIdx.x; q < H; q += blockDim.x) A[q * SA] = B[q];
     __syncthreads();
-    *scale_out = block_sum(sabs, S.rv);
+    *scale_out = sabs;                    // this thread's part; reduced with the integer argmax
     // a4: inverse column pass 1 (slot 0 packs X(.,0) + i X(.,W/2), whose transforms are real).
     // X(ky) sits at row fft_pos(ky); ky = N2h n1 + n2.
     fft_pass1<N1h, N2h, true, true>(
@@ -583,11 +592,13 @@ static __device__ int integer_collect(const Geom& g, const Smem& S, const void* 
 
 // t2: each thread's best point of the integer surface (value, natural flat index) and its
 // runner-up value, collected while the inverse FFT stored them.
+// *scale: in, this thread's part of the spectral sum; out, the block total.
 __device__ __forceinline__ int integer_peak(const Geom& g, const Smem& S, const void* frame, long long pitch,
-                                            float scale, unsigned* flags, const Best2& t2) {
+                                            float* scale_io, unsigned* flags, const Best2& t2) {
     float v1 = t2.v1;
     int best = t2.j1;
-    block_argmax(v1, best, S.rv, S.rj);
+    const float scale = block_argmax_sum(v1, best, *scale_io, S.rv, S.rj, S.rv + 32);
+    *scale_io = scale;
     if (!(v1 > -INFINITY)) { *flags |= 0x10u; return 0; }
     const float tau = g.tau_int * scale;
     if (!g.guard) return best;
@@ -824,24 +835,38 @@ __device__ __forceinline__ void stage_a_nyquist(const Geom& g, const Smem& S, in
     const uint2* Tc = TA;
     const uint2* Ts = TA + (size_t)g.TAB * Hq;
     const float un = ldexpf(1.f, -13);
-    for (int lt = threadIdx.x; lt < TC; lt += blockDim.x) {
-        const int ta = t0 - 1 + lt, sw = pswz(ta, Hq);
+    // item (lt, part): the m pairs p = part (mod 4); the four parts of one row are adjacent
+    // lanes and are summed by shuffles
+    for (int base = 0; base < 4 * TC; base += blockDim.x) {
+        const int item = base + threadIdx.x, lt = item >> 2, part = item & 3;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int p = Hq - 1; p >= 0; --p) {
-            const int m1 = 2 * p + 1, m2 = 2 * p + 2;
-            const float2 cm = unsplit_pair(Tc[ta * Hq + (p ^ sw)]), sn = unsplit_pair(Ts[ta * Hq + (p ^ sw)]);
-            const float2 p1 = S.XN[posH(g, m1)], p2 = S.XN[posH(g, m2)], q1 = S.XN[posH(g, H - m1)];
-            const float2 q2 = (m2 == Hh) ? make_float2(-p2.x, -p2.y) : S.XN[posH(g, H - m2)];
-            acc.x = fmaf(cm.x * un, p1.x, fmaf(cm.y * un, p2.x, acc.x));
-            acc.y = fmaf(cm.x * un, p1.y, fmaf(cm.y * un, p2.y, acc.y));
-            acc.z = fmaf(sn.x * un, q1.x, fmaf(sn.y * un, q2.x, acc.z));
-            acc.w = fmaf(sn.x * un, q1.y, fmaf(sn.y * un, q2.y, acc.w));
+        if (lt < TC) {
+            const int ta = t0 - 1 + lt, sw = pswz(ta, Hq);
+            for (int p = Hq - 1 - part; p >= 0; p -= 4) {
+                const int m1 = 2 * p + 1, m2 = 2 * p + 2;
+                const float2 cm = unsplit_pair(Tc[ta * Hq + (p ^ sw)]), sn = unsplit_pair(Ts[ta * Hq + (p ^ sw)]);
+                const float2 p1 = S.XN[posH(g, m1)], p2 = S.XN[posH(g, m2)], q1 = S.XN[posH(g, H - m1)];
+                const float2 q2 = (m2 == Hh) ? make_float2(-p2.x, -p2.y) : S.XN[posH(g, H - m2)];
+                acc.x = fmaf(cm.x * un, p1.x, fmaf(cm.y * un, p2.x, acc.x));
+                acc.y = fmaf(cm.x * un, p1.y, fmaf(cm.y * un, p2.y, acc.y));
+                acc.z = fmaf(sn.x * un, q1.x, fmaf(sn.y * un, q2.x, acc.z));
+                acc.w = fmaf(sn.x * un, q1.y, fmaf(sn.y * un, q2.y, acc.w));
+            }
         }
-        const float4 cb = combos(acc.x, acc.y, acc.z, acc.w);
-        S.CBN[lt] = cb.x;
-        S.CBN[TC + lt] = cb.y;
-        S.CBN[2 * TC + lt] = cb.z;
-        S.CBN[3 * TC + lt] = cb.w;
+#pragma unroll
+        for (int o = 1; o < 4; o <<= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+            acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+            acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+        }
+        if (lt < TC && part == 0) {
+            const float4 cb = combos(acc.x, acc.y, acc.z, acc.w);
+            S.CBN[lt] = cb.x;
+            S.CBN[TC + lt] = cb.y;
+            S.CBN[2 * TC + lt] = cb.z;
+            S.CBN[3 * TC + lt] = cb.w;
+        }
     }
 }
 
@@ -1558,7 +1583,7 @@ __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
         Best2 t2;
         fft_correlate_t<H, W>(g, S, frame, b.pitch, b.vec_ok, &scale, t2,
                               b.dbg_int ? b.dbg_int + (size_t)f * g.H * g.W : nullptr);
-        const int ip = integer_peak(g, S, frame, b.pitch, scale, &flags, t2);
+        const int ip = integer_peak(g, S, frame, b.pitch, &scale, &flags, t2);
         const float c0 = int_surface(g, S, ip);           // HW * c(p)
         const int py = wrap_shift(ip >> g.logW, g.H), px = wrap_shift(ip & (g.W - 1), g.W);
         __syncthreads();
