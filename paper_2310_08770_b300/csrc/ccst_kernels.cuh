@@ -202,11 +202,18 @@ struct RowOffsets {
     __device__ __forceinline__ uint2 at(int s, int h) const {
         return *reinterpret_cast<const uint2*>(ccst_smem + o[s & 1][h] + 128 * (s >> 1));
     }
+    // the same pair of row r + dr (same swizzle when dr is a multiple of 4) of an operand
+    // starting `delta` bytes further
+    __device__ __forceinline__ uint2 at(int s, int h, unsigned delta) const {
+        return *reinterpret_cast<const uint2*>(ccst_smem + o[s & 1][h] + delta + 128 * (s >> 1));
+    }
 };
-// A fragment of k16 step s from rows ra, rb (16-row tile: ra = gq, rb = gq + 8)
-__device__ __forceinline__ void load_afrag(const RowOffsets& ra, const RowOffsets& rb, int s, unsigned (&h)[4],
+// A fragment of k16 step s: rows r (offsets ro, plus `delta` bytes) and r + 8 (8 rows of
+// KP pairs further, `r8` bytes)
+__device__ __forceinline__ void load_afrag(const RowOffsets& ro, unsigned delta, unsigned r8, int s, unsigned (&h)[4],
                                            unsigned (&l)[4]) {
-    const uint2 v0 = ra.at(s, 0), v1 = rb.at(s, 0), v2 = ra.at(s, 1), v3 = rb.at(s, 1);
+    const uint2 v0 = ro.at(s, 0, delta), v1 = ro.at(s, 0, delta + r8), v2 = ro.at(s, 1, delta),
+                v3 = ro.at(s, 1, delta + r8);
     h[0] = v0.x; h[1] = v1.x; h[2] = v2.x; h[3] = v3.x;
     l[0] = v0.y; l[1] = v1.y; l[2] = v2.y; l[3] = v3.y;
 }
@@ -312,7 +319,11 @@ __host__ __device__ inline SmemPlan smem_plan(const Geom& g) {
              sizeof(float2) * (size_t)(g.Ntw / 2 + g.H + g.W) + sizeof(float2) * (size_t)g.SA +
              sizeof(float) * 2 * (size_t)g.T1p + sizeof(float) * 64 + sizeof(int) * 64 +
              (sizeof(int) + sizeof(float)) * kMaxCand + sizeof(int) * 16 + 64;
-    p.total = align_up(p.r1 + p.r2 + p.misc, 16);
+    // the tensor-core stages read up to 15 rows past the last stage-A output plane (rows of
+    // the last 16-row tile that feed only discarded outputs): keep them inside the allocation
+    const size_t over = 15 * sizeof(uint2) * (size_t)(g.SA / 2);
+    const size_t tail = p.uvn + p.misc;
+    p.total = align_up(p.r1 + p.r2 + p.misc + (over > tail ? over - tail : 0), 16);
     return p;
 }
 
@@ -886,10 +897,12 @@ __device__ __forceinline__ void store_combo_pairs(const Geom& g, const Smem& S, 
 // Tensor-core form (Hh a multiple of 16): M = t, N = kx, K = m. A warp task is one t tile
 // of 16 by one kx tile of 8, with the four products (Cm1 Pr, Cm1 Pi, S Qr, S Qi) sharing
 // the A fragments. Rows past the chunk read its last row and are not stored.
-template <int H>
+template <int H, int W>
 __device__ __forceinline__ void stage_a_mma(const Geom& g, const Smem& S, int t0, const uint2* TA) {
-    constexpr int Hq = H / 4, NKS = Hq / 8;
-    const int SA = g.SA, TC = g.TC;
+    constexpr int Hq = H / 4, NKS = Hq / 8, SA = W / 2;
+    constexpr unsigned R8 = 8u * Hq * 8u;                        // 8 table rows, bytes
+    constexpr unsigned PL = (unsigned)SA * Hq * 8u;              // one P/Q plane, bytes
+    const int TC = g.TC;
     const uint2* Tc = TA;
     const uint2* Ts = TA + (size_t)g.TAB * Hq;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -899,11 +912,12 @@ __device__ __forceinline__ void stage_a_mma(const Geom& g, const Smem& S, int t0
     for (int task = warp; task < ntt * nnt; task += nwarp) {
         const int tt = task / nnt, nt = task - tt * nnt;
         if (t0 + 16 * tt > g.h0) continue;                       // warp-uniform: all rows past h0
-        const int r0 = t0 - 1 + min(16 * tt + gq, TC - 1), r1 = t0 - 1 + min(16 * tt + gq + 8, TC - 1);
-        const RowOffsets c0(Tc, Hq, r0, tq), c1(Tc, Hq, r1, tq), s0(Ts, Hq, r0, tq), s1(Ts, Hq, r1, tq);
-        const int kxr = 8 * nt + gq;
-        const RowOffsets pr(S.PQ, Hq, kxr, tq), pi(S.PQ + SA * Hq, Hq, kxr, tq), qr(S.PQ + 2 * SA * Hq, Hq, kxr, tq),
-            qi(S.PQ + 3 * SA * Hq, Hq, kxr, tq);
+        // table rows t0 - 1 + lt for lt = 16 tt + gq (+ 8); rows past the chunk read the
+        // following table rows (in bounds: TAB >= t0 - 1 + 16 ceil(TC / 16) or the next
+        // table / region) and are not stored
+        const RowOffsets tr(Tc, Hq, t0 - 1 + 16 * tt + gq, tq);
+        const unsigned dts = (unsigned)((size_t)g.TAB * Hq * 8u);   // Ts - Tc, bytes
+        const RowOffsets pq(S.PQ, Hq, 8 * nt + gq, tq);
         float d[4][4];
 #pragma unroll
         for (int pl = 0; pl < 4; ++pl)
@@ -912,10 +926,10 @@ __device__ __forceinline__ void stage_a_mma(const Geom& g, const Smem& S, int t0
 #pragma unroll
         for (int s = 0; s < NKS; ++s) {
             unsigned ch[4], cl[4], sh[4], sl[4];
-            load_afrag(c0, c1, s, ch, cl);
-            load_afrag(s0, s1, s, sh, sl);
-            const uint2 b0[4] = {pr.at(s, 0), pi.at(s, 0), qr.at(s, 0), qi.at(s, 0)};
-            const uint2 b1[4] = {pr.at(s, 1), pi.at(s, 1), qr.at(s, 1), qi.at(s, 1)};
+            load_afrag(tr, 0u, R8, s, ch, cl);
+            load_afrag(tr, dts, R8, s, sh, sl);
+            const uint2 b0[4] = {pq.at(s, 0), pq.at(s, 0, PL), pq.at(s, 0, 2 * PL), pq.at(s, 0, 3 * PL)};
+            const uint2 b1[4] = {pq.at(s, 1), pq.at(s, 1, PL), pq.at(s, 1, 2 * PL), pq.at(s, 1, 3 * PL)};
             // the three split products, each issued across the four independent accumulators
 #pragma unroll
             for (int pl = 0; pl < 4; ++pl) mma_f16(d[pl], pl < 2 ? cl : sl, b0[pl].x, b1[pl].x);
@@ -967,9 +981,9 @@ __device__ __forceinline__ void stage_a_simt(const Geom& g, const Smem& S, int t
     }
 }
 
-template <int H>
+template <int H, int W>
 __device__ __forceinline__ void stage_a(const Geom& g, const Smem& S, int t0, const uint2* TA) {
-    if (H % 32 == 0 && g.tables_smem) stage_a_mma<H>(g, S, t0, TA);
+    if (H % 32 == 0 && g.tables_smem) stage_a_mma<H, W>(g, S, t0, TA);
     else stage_a_simt(g, S, t0, TA);
     stage_a_nyquist(g, S, t0, TA);
     __syncthreads();
@@ -1041,6 +1055,7 @@ template <int W, bool kCollect>
 __device__ __forceinline__ void stage_b_mma(const Geom& g, const Smem& S, int t0, const uint2* TB, float dsc,
                                             const Emitter<kCollect>& emit) {
     constexpr int SAq = W / 4, NKS = SAq / 8;
+    constexpr unsigned R8 = 8u * SAq * 8u;                       // 8 operand rows, bytes
     const int T1 = g.T1p, T8 = g.T1p8, TC = g.TC;
     const uint2* WC = TB;
     const uint2* WS = TB + (size_t)T1 * SAq;
@@ -1059,10 +1074,13 @@ __device__ __forceinline__ void stage_b_mma(const Geom& g, const Smem& S, int t0
         const bool two = nt0 + 1 < nnt;                          // warp-uniform
         const uint2* Ca = S.CB + (size_t)sg * TC * SAq;          // C0 / C1
         const uint2* Eb = S.CB + (size_t)(2 + sg) * TC * SAq;    // E0 / E1
-        const int r0 = min(16 * tt + gq, TC - 1), r1 = min(16 * tt + gq + 8, TC - 1);
-        const int x0 = min(8 * nt0 + gq, T1 - 1), x1 = two ? min(8 * nt0 + 8 + gq, T1 - 1) : x0;
-        const RowOffsets ca0(Ca, SAq, r0, tq), ca1(Ca, SAq, r1, tq), eb0(Eb, SAq, r0, tq), eb1(Eb, SAq, r1, tq);
-        const RowOffsets wc0(WC, SAq, x0, tq), wc1(WC, SAq, x1, tq), ws0(WS, SAq, x0, tq), ws1(WS, SAq, x1, tq);
+        // rows 16 tt + gq (+ 8) of the combinations and tx rows 8 nt0 + gq (+ 8) of the tables;
+        // rows past the chunk / the tables read the following rows of the shared area (in
+        // bounds) and only feed discarded outputs
+        const RowOffsets ra(Ca, SAq, 16 * tt + gq, tq), rx(WC, SAq, 8 * nt0 + gq, tq);
+        const unsigned deb = (unsigned)((size_t)2 * TC * SAq * 8u);       // Eb - Ca, bytes
+        const unsigned dws = (unsigned)((size_t)T1 * SAq * 8u);           // WS - WC, bytes
+        const unsigned x8 = two ? R8 : 0u;                                // second tx tile
         float dA[2][4], dB[2][4];
 #pragma unroll
         for (int j = 0; j < 2; ++j)
@@ -1071,10 +1089,10 @@ __device__ __forceinline__ void stage_b_mma(const Geom& g, const Smem& S, int t0
 #pragma unroll
         for (int s = 0; s < NKS; ++s) {
             unsigned ah[4], al[4], eh[4], el[4];
-            load_afrag(ca0, ca1, s, ah, al);
-            load_afrag(eb0, eb1, s, eh, el);
-            const uint2 c0[2] = {wc0.at(s, 0), wc1.at(s, 0)}, c1[2] = {wc0.at(s, 1), wc1.at(s, 1)};
-            const uint2 s0[2] = {ws0.at(s, 0), ws1.at(s, 0)}, s1[2] = {ws0.at(s, 1), ws1.at(s, 1)};
+            load_afrag(ra, 0u, R8, s, ah, al);
+            load_afrag(ra, deb, R8, s, eh, el);
+            const uint2 c0[2] = {rx.at(s, 0), rx.at(s, 0, x8)}, c1[2] = {rx.at(s, 1), rx.at(s, 1, x8)};
+            const uint2 s0[2] = {rx.at(s, 0, dws), rx.at(s, 0, dws + x8)}, s1[2] = {rx.at(s, 1, dws), rx.at(s, 1, dws + x8)};
             // the three split products, each issued across the four independent accumulators
             // (for a single tx tile, x1 = x0 repeats a valid row and its results are unused)
 #pragma unroll
@@ -1151,7 +1169,7 @@ __device__ __forceinline__ void upsampled_pass(const Geom& g, const Smem& S, Top
     const Emitter<kCollect> emit{g, S, top, thr, dbg};
     for (int c = 0; c < g.nchunk; ++c) {
         const int t0 = 1 + c * g.TC;
-        stage_a<H>(g, S, t0, TA);
+        stage_a<H, W>(g, S, t0, TA);
         if (W % 32 == 0 && g.tables_smem) stage_b_mma<W, kCollect>(g, S, t0, TB, dsc, emit);
         else stage_b_simt<kCollect>(g, S, t0, TB, dsc, emit);
         // the t = 0 row: S = 0, the surface is g(tx)
