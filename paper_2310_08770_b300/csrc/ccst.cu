@@ -227,6 +227,7 @@ struct ccst_ctx {
     dfc* d_df = nullptr;          // double-float tables in one block
     void* d_frames = nullptr;     // host-path staging
     Result* d_out = nullptr;      // host-path staging
+    unsigned* d_next = nullptr;   // frame counter of the tracking launches
     // graphs keyed by (frames, n, pitch, out), each with its own profiling event pair
     struct GraphEntry {
         cudaGraphExec_t exec = nullptr;
@@ -284,7 +285,7 @@ static void free_all(ccst_ctx* c) {
     for (int i = 0; i < kTickets; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     void* ptrs[] = {c->d_ref32, c->d_b64, c->d_FE64, c->d_FE32, c->d_tw64, c->d_tw32,
-                    c->d_tab,   c->d_df,  c->d_frames, c->d_out};
+                    c->d_tab,   c->d_df,  c->d_frames, c->d_out, c->d_next};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -368,6 +369,7 @@ extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pi
         {(void**)&d_work, l2per * sizeof(double2)},
         {(void**)&c->d_frames, (size_t)p.max_batch * HW * elem},
         {(void**)&c->d_out, (size_t)p.max_batch * sizeof(Result)},
+        {(void**)&c->d_next, 256},
     };
     for (auto& a : allocs) {
         if ((e = cudaMalloc(a.ptr, a.bytes)) != cudaSuccess) {
@@ -453,6 +455,8 @@ static int launch(ccst_ctx* c, const Batch& b) {
     {
         Geom gk = c->g;
         Batch bk = b;
+        bk.next = c->d_next;
+        CK(c, cudaMemsetAsync(c->d_next, 0, sizeof(unsigned), c->stream));
         void* args[] = {&gk, &bk};
         CK(c, cudaLaunchKernel(c->kernel, dim3(grid), dim3(kThreads), args, c->smem, c->stream));
     }
@@ -483,6 +487,7 @@ static int make_batch(ccst_ctx* c, const void* frames, int64_t n, int64_t pitch,
     b->dbg_pairs = nullptr;
     b->dbg_d32 = nullptr;
     b->dbg_d64 = nullptr;
+    b->next = nullptr;
     return CCST_OK;
 }
 

@@ -106,6 +106,9 @@ struct Batch {
     const int* dbg_pairs;  // optional: n x 2 grid indices (ja, jb); then only the pair difference runs
     float* dbg_d32;        // n: v(jb) - v(ja) by the FP32 pair-difference guard
     double* dbg_d64;       // n: the same difference accumulated in FP64 from the FP32 spectrum
+    unsigned* next;        // optional: frame counter (zero at launch); CTAs take frames from it in
+                           // order, so that a slow frame delays no other. Null: CTA i takes frames
+                           // i, i + gridDim.x, ...
 };
 
 // --------------------------------------------------------------------- helpers
@@ -1594,7 +1597,16 @@ __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
     unsigned bar_parity = 0;
     __syncthreads();
     const size_t elem = g.in_dtype == 0 ? 2 : 4;
-    for (long long f = blockIdx.x; f < b.n; f += gridDim.x) {
+    // next frame: from the shared counter (every thread has read the current index at the
+    // barrier before thread 0 fetches the next), else grid-stride
+    auto fetch = [&](long long cur) -> long long {
+        if (!b.next) return cur < 0 ? (long long)blockIdx.x : cur + gridDim.x;
+        __syncthreads();
+        if (threadIdx.x == 0) S.misc[4] = (int)atomicAdd(b.next, 1u);
+        __syncthreads();
+        return S.misc[4];
+    };
+    for (long long f = fetch(-1); f < b.n; f = fetch(f)) {
         const char* frame = (const char*)b.frames + (size_t)f * g.H * b.pitch * elem;
         unsigned flags = 0;
         float scale = 0.f;
