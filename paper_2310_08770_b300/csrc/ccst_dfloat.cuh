@@ -49,6 +49,18 @@ __device__ __forceinline__ df df_add(df a, df b) {
     return {s, e};
 }
 __device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+
+// The cheaper double-word sum (one TwoSum on the high parts, the low parts added in FP32,
+// one renormalisation): its error is bounded absolutely, by about 2^-46 (|a| + |b|), not
+// relative to |a + b|. That is the bound an FFT or a long dot product needs (errors measured
+// against the magnitudes being combined), at about half the cost of df_add.
+__device__ __forceinline__ df df_add_abs(df a, df b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    fast_two_sum(s, e, s, e);
+    return {s, e};
+}
 __device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
 
 __device__ __forceinline__ df df_mul(df a, df b) {
@@ -64,10 +76,13 @@ __device__ __forceinline__ df df_scale(df a, float k) {   // k a power of two: e
     return {a.hi * k, a.lo * k};
 }
 
-__device__ __forceinline__ dfc cadd(dfc a, dfc b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
-__device__ __forceinline__ dfc csub(dfc a, dfc b) { return {df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
+// complex double-word arithmetic with the absolute-error sum (FFT butterflies, phases)
+__device__ __forceinline__ dfc cadd(dfc a, dfc b) { return {df_add_abs(a.re, b.re), df_add_abs(a.im, b.im)}; }
+__device__ __forceinline__ dfc csub(dfc a, dfc b) {
+    return {df_add_abs(a.re, df_neg(b.re)), df_add_abs(a.im, df_neg(b.im))};
+}
 __device__ __forceinline__ dfc cmul(dfc a, dfc b) {
-    return {df_sub(df_mul(a.re, b.re), df_mul(a.im, b.im)), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+    return {df_add_abs(df_mul(a.re, b.re), df_neg(df_mul(a.im, b.im))), df_add_abs(df_mul(a.re, b.im), df_mul(a.im, b.re))};
 }
 __device__ __forceinline__ dfc cconj(dfc a) { return {a.re, df_neg(a.im)}; }
 

@@ -1573,7 +1573,7 @@ static __device__ int df_reevaluate(const Geom& g, const Smem& S, const void* fr
             if (ky == Hh && 2 * kx != W) ey.im = {0.f, 0.f};   // real part of the Nyquist row's phase
             const dfc e = cmul(ey, Ex[kx]);
             const dfc x = Xd[ky * Wcp + kx];
-            acc = df_add(acc, df_sub(df_mul(x.re, e.re), df_mul(x.im, e.im)));
+            acc = df_add_abs(acc, df_add_abs(df_mul(x.re, e.re), df_neg(df_mul(x.im, e.im))));
         }
         const double v = df_to_double(block_sum_df(acc, S.rd));
         const double sv = (double)g.sense * v;
