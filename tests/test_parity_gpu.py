@@ -174,8 +174,12 @@ def test_frame_stream_full_size_sampled(torch):
 
 
 # ------------------------------------------------------------------ shapes, u, methods
+# (128, 128, 120): the refinement grid no longer fits one chunk, stages A/B run in chunks;
+# (128, 128, 200): the stage tables no longer fit shared memory, the plain-FP32 stages read
+# them from global memory
 @pytest.mark.parametrize("H,W,u", [(8, 8, 7), (16, 16, 1), (16, 32, 2), (32, 32, 37), (64, 32, 100),
-                                   (32, 128, 100), (128, 64, 50), (64, 64, 256), (128, 128, 11)])
+                                   (32, 128, 100), (128, 64, 50), (64, 64, 256), (128, 128, 11),
+                                   (128, 128, 120), (128, 128, 200)])
 @pytest.mark.parametrize("method", [oracle.CC_U, oracle.CC_SN])
 def test_shapes_and_upsampling(torch, H, W, u, method):
     rng = np.random.default_rng(H * 1000 + W + u)
