@@ -178,4 +178,132 @@ __device__ __forceinline__ void fft_pass2(int nseq, LD ld, ST st) {
     }
 }
 
+
+// ------------------------------------------------------------------ double-float passes
+// The same four-step passes over double-float complex values (the last guard level):
+// register DFTs built from 2- and 4-point butterflies, twiddles W_N^{n2 k1} from a
+// [k1][n2] table. Sums use the absolute-error double-word addition (an FFT's error bound).
+namespace dfk {
+constexpr double kC1 = 0.92387953251128675613;      // cos(pi/8)
+constexpr double kS1 = 0.38268343236508977173;      // sin(pi/8)
+constexpr double kR2 = 0.70710678118654752440;      // sqrt(1/2)
+}  // namespace dfk
+
+__device__ __forceinline__ df df_const(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+// cos / sin of 2 pi k / 16, k = 0..7
+__device__ __forceinline__ df df_c16(int k) {
+    return k == 0 ? df_const(1.0) : k == 1 ? df_const(dfk::kC1) : k == 2 ? df_const(dfk::kR2)
+         : k == 3 ? df_const(dfk::kS1) : k == 4 ? df_const(0.0) : k == 5 ? df_const(-dfk::kS1)
+         : k == 6 ? df_const(-dfk::kR2) : df_const(-dfk::kC1);
+}
+__device__ __forceinline__ df df_s16(int k) {
+    return k == 0 ? df_const(0.0) : k == 1 ? df_const(dfk::kS1) : k == 2 ? df_const(dfk::kR2)
+         : k == 3 ? df_const(dfk::kC1) : k == 4 ? df_const(1.0) : k == 5 ? df_const(dfk::kC1)
+         : k == 6 ? df_const(dfk::kR2) : df_const(dfk::kS1);
+}
+// x * exp(-+ 2 pi i idx / 16), idx a compile-time constant after unrolling
+template <bool INV>
+__device__ __forceinline__ dfc mul_w16_df(dfc x, int idx) {
+    idx &= 15;
+    if (idx >= 8) { x = {df_neg(x.re), df_neg(x.im)}; idx -= 8; }
+    if (idx == 0) return x;
+    if (idx == 4) return INV ? dfc{df_neg(x.im), x.re} : dfc{x.im, df_neg(x.re)};
+    const df c = df_c16(idx), s = INV ? df_s16(idx) : df_neg(df_s16(idx));
+    return cmul(x, dfc{c, s});
+}
+template <bool INV>
+__device__ __forceinline__ void dft2_df(dfc& a, dfc& b) {
+    const dfc t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+template <bool INV>
+__device__ __forceinline__ void dft4_df(dfc& a, dfc& b, dfc& c, dfc& d) {
+    const dfc s0 = cadd(a, c), d0 = csub(a, c), s1 = cadd(b, d), d1 = csub(b, d);
+    const dfc r = INV ? dfc{df_neg(d1.im), d1.re} : dfc{d1.im, df_neg(d1.re)};     // -+ i d1
+    a = cadd(s0, s1);
+    c = csub(s0, s1);
+    b = cadd(d0, r);
+    d = csub(d0, r);
+}
+// In-register DFT of R = 1, 2, 4, 8 or 16 points (the splits of dft_reg)
+template <int R, bool INV>
+__device__ __forceinline__ void dft_reg_df(dfc (&v)[R]) {
+    if constexpr (R == 2) {
+        dft2_df<INV>(v[0], v[1]);
+    } else if constexpr (R == 4) {
+        dft4_df<INV>(v[0], v[1], v[2], v[3]);
+    } else if constexpr (R == 8 || R == 16) {
+        constexpr int R1 = R / 4, R2 = 4;
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) {
+            if constexpr (R1 == 2) dft2_df<INV>(v[n2], v[R2 + n2]);
+            else dft4_df<INV>(v[n2], v[R2 + n2], v[2 * R2 + n2], v[3 * R2 + n2]);
+        }
+#pragma unroll
+        for (int k1 = 1; k1 < R1; ++k1)
+#pragma unroll
+            for (int n2 = 1; n2 < R2; ++n2)
+                v[R2 * k1 + n2] = mul_w16_df<INV>(v[R2 * k1 + n2], n2 * k1 * (16 / R));
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) dft4_df<INV>(v[R2 * k1], v[R2 * k1 + 1], v[R2 * k1 + 2], v[R2 * k1 + 3]);
+        dfc t[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) t[i] = v[i];
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1)
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) v[k1 + R1 * k2] = t[R2 * k1 + k2];
+    }
+}
+// W_N^{n2 k1} (forward) laid out [k1][n2], from twd[k] = exp(-2 pi i k / Ntw), k < Ntw/2
+template <int N>
+__device__ __forceinline__ void build_pass_twiddles_df(dfc* t4, const dfc* twd, int logNtw) {
+    constexpr int N2 = Split<N>::N2, lg = log2_c(N);
+    const int sh = logNtw - lg;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int k1 = i / N2, n2 = i - k1 * N2, e = (n2 * k1) & (N - 1);
+        dfc t = e < (N >> 1) ? twd[e << sh] : twd[(e - (N >> 1)) << sh];
+        if (e >= (N >> 1)) t = {df_neg(t.re), df_neg(t.im)};
+        t4[i] = t;
+    }
+}
+template <int N1, int N2, bool kSeqFast, class LD, class ST>
+__device__ __forceinline__ void fft_pass1_df(int nseq, const dfc* t4, LD ld, ST st) {
+    const int ntask = nseq * N2;
+    for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
+        int s, n2;
+        if (kSeqFast) { n2 = task / nseq; s = task - n2 * nseq; }
+        else { s = task / N2; n2 = task - s * N2; }
+        dfc v[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) v[n1] = ld(s, n2, n1);
+        dft_reg_df<N1, false>(v);
+        if (N2 > 1) {
+#pragma unroll
+            for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul(v[k1], t4[k1 * N2 + n2]);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) st(s, n2, k1, v[k1]);
+    }
+}
+template <int N1, int N2, bool kSeqFast, class LD, class ST>
+__device__ __forceinline__ void fft_pass2_df(int nseq, LD ld, ST st) {
+    const int ntask = nseq * N1;
+    for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
+        int s, k1;
+        if (kSeqFast) { k1 = task / nseq; s = task - k1 * nseq; }
+        else { s = task / N1; k1 = task - s * N1; }
+        dfc w[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) w[n2] = ld(s, k1, n2);
+        dft_reg_df<N2, false>(w);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) st(s, k1, k2, w[k2]);
+    }
+}
+
 }  // namespace ccst

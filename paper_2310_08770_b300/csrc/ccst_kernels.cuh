@@ -313,10 +313,11 @@ __host__ __device__ inline SmemPlan smem_plan(const Geom& g) {
     p.uvn = align_up(sizeof(float4) * (size_t)g.TC, 16);
     const size_t k6 = p.ta + p.tb + p.uv + p.uvn;
     p.r2 = fft > k6 ? fft : k6;
-    // the double-float level needs H x Wcp dfc plus one packed-row chunk (2 rows of W dfc),
-    // which later holds the H + Wc candidate twiddles
-    const size_t chunk = 2 * (size_t)g.W > (size_t)(g.H + g.Wc) ? 2 * (size_t)g.W : (size_t)(g.H + g.Wc);
-    const size_t dfl = sizeof(dfc) * ((size_t)g.H * g.Wcp + (size_t)(g.Ntw / 2) + chunk);
+    // the double-float level needs H x Wcp dfc, the FFT twiddles (Ntw/2 + W + H) and one
+    // packed-row chunk (at least one row of W dfc), which later holds the H + Wc candidate
+    // twiddles
+    const size_t chunk = (size_t)g.W > (size_t)(g.H + g.Wc) ? (size_t)g.W : (size_t)(g.H + g.Wc);
+    const size_t dfl = sizeof(dfc) * ((size_t)g.H * g.Wcp + (size_t)(g.Ntw / 2) + g.W + g.H + chunk);
     if (p.r1 + p.r2 < dfl) p.r2 = align_up(dfl - p.r1, 16);
     p.misc = sizeof(double) * 32 + 16 + sizeof(float2) * (size_t)(g.Wc + g.Hh + 1) +
              sizeof(float2) * (size_t)(g.Ntw / 2 + g.H + g.W) + sizeof(float2) * (size_t)g.SA +
@@ -1494,55 +1495,86 @@ static __device__ df block_sum_df(df v, double* red) {
 //   cu(j) = Re sum_{ky,kx} w X(ky,kx) E_y(ky, py u + ty) E_x(kx, px u + tx)
 // with exactly reduced angles. Returns the winner (sense-adjusted maximum,
 // lowest index on ties) and its unnormalised value in *val.
+template <int H, int W>
 static __device__ int df_reevaluate(const Geom& g, const Smem& S, const void* frame, long long pitch,
-                             int py, int px, int nc, double* val) {
-    const int H = g.H, W = g.W, Wc = g.Wc, Wcp = g.Wcp, Hh = g.Hh;
-    dfc* Xd = (dfc*)S.r1;
+                                    int py, int px, int nc, double* val) {
+    constexpr int N1w = Split<W>::N1, N2w = Split<W>::N2, N1h = Split<H>::N1, N2h = Split<H>::N2;
+    constexpr int Hh = H / 2, Wc = W / 2 + 1;
+    const int Wcp = g.Wcp;
+    dfc* Xd = (dfc*)S.r1;                      // [H][Wcp]; after the column passes row fft_pos(ky) holds X(ky, .)
     dfc* twd = Xd + (size_t)H * Wcp;           // Ntw/2 FFT twiddles, staged from global
-    dfc* Zc = twd + g.Ntw / 2;
-    const long long cbytes = (long long)S.r12_bytes - (long long)sizeof(dfc) * ((long long)H * Wcp + g.Ntw / 2);
+    dfc* t4w = twd + g.Ntw / 2;                // W: inter-pass twiddles of length W
+    dfc* t4h = t4w + W;                        // H: the same for length H
+    dfc* Zc = t4h + H;                         // packed-row chunk, later the candidate phases
+    const long long cbytes =
+        (long long)S.r12_bytes - (long long)sizeof(dfc) * ((long long)H * Wcp + g.Ntw / 2 + W + H);
     for (int k2 = threadIdx.x; k2 < g.Ntw / 2; k2 += blockDim.x) twd[k2] = g.twdf[k2];
-    int R = 1;
-    while (2 * R <= Hh && 2LL * R * W * (long long)sizeof(dfc) <= cbytes) R *= 2;
-    for (int r0 = 0; r0 < Hh; r0 += R) {
-        for (int idx = threadIdx.x; idx < 2 * R * W; idx += blockDim.x) {
-            const int yl = idx / W, x = idx - yl * W;
-            const int y = 2 * r0 + yl;
-            const float I = pixel_f32(frame, g.in_dtype, (long long)y * pitch + x);
-            df a = df_make(I);
-            if (g.method != 0) {
-                float s, e;
-                two_sum(I, g.eps, s, e);
-                const df ip = {s, e};
-                a = df_mul(ip, ip);
-            }
-            dfc* z = &Zc[(yl >> 1) * W + brev(x, g.logW)];
-            if (y & 1) z->im = a; else z->re = a;
-        }
-        __syncthreads();
-        fft_r2_passes(Zc, g.logW, R, W, 1, twd, g.logNtw, false);
-        for (int idx = threadIdx.x; idx < R * Wcp; idx += blockDim.x) {
-            const int rl = idx / Wcp, kx = idx - rl * Wcp;
-            dfc fe = {{0.f, 0.f}, {0.f, 0.f}}, fo = fe;
-            if (kx < Wc) {
-                const dfc z = Zc[rl * W + kx];
-                const dfc zc = cconj(Zc[rl * W + ((W - kx) & (W - 1))]);
-                const dfc sp = cadd(z, zc), dm = csub(z, zc);
-                fe = {df_scale(sp.re, 0.5f), df_scale(sp.im, 0.5f)};
-                fo = {df_scale(dm.im, 0.5f), df_scale(df_neg(dm.re), 0.5f)};   // (z - zc) / (2i)
-            }
-            const int r = r0 + rl;
-            Xd[brev(2 * r, g.logH) * Wcp + kx] = fe;
-            Xd[brev(2 * r + 1, g.logH) * Wcp + kx] = fo;
-        }
-        __syncthreads();
-    }
-    fft_r2_passes(Xd, g.logH, Wc, 1, Wcp, twd, g.logNtw, false);
-    for (int idx = threadIdx.x; idx < H * Wc; idx += blockDim.x) {
-        const int ky = idx / Wc, kx = idx - ky * Wc;
-        Xd[ky * Wcp + kx] = cmul(Xd[ky * Wcp + kx], cconj(g.FEdf[idx]));
-    }
     __syncthreads();
+    build_pass_twiddles_df<W>(t4w, twd, g.logNtw);
+    build_pass_twiddles_df<H>(t4h, twd, g.logNtw);
+    int R = 1;                                 // packed rows per chunk
+    while (2 * R <= Hh && 2LL * R * W * (long long)sizeof(dfc) <= cbytes) R *= 2;
+    __syncthreads();
+    // rows: packed pair (2r, 2r+1) as one complex row, four-step passes, then the split into
+    // the two real rows' half spectra, stored in natural row order
+    for (int r0 = 0; r0 < Hh; r0 += R) {
+        for (int idx = threadIdx.x; idx < R * W; idx += blockDim.x) {
+            const int rl = idx / W, x = idx - rl * W;
+            const int y = 2 * (r0 + rl);
+            df a[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float I = pixel_f32(frame, g.in_dtype, (long long)(y + h) * pitch + x);
+                a[h] = df_make(I);
+                if (g.method != 0) {
+                    float s, e;
+                    two_sum(I, g.eps, s, e);
+                    const df ip = {s, e};
+                    a[h] = df_mul(ip, ip);
+                }
+            }
+            Zc[rl * W + x] = dfc{a[0], a[1]};
+        }
+        __syncthreads();
+        fft_pass1_df<N1w, N2w, false>(
+            R, t4w, [&](int s, int n2, int n1) { return Zc[s * W + N2w * n1 + n2]; },
+            [&](int s, int n2, int k1, dfc v) { Zc[s * W + N2w * k1 + n2] = v; });
+        __syncthreads();
+        if (N2w > 1) {
+            fft_pass2_df<N1w, N2w, false>(
+                R, [&](int s, int k1, int n2) { return Zc[s * W + N2w * k1 + n2]; },
+                [&](int s, int k1, int k2, dfc v) { Zc[s * W + N2w * k1 + k2] = v; });
+            __syncthreads();
+        }
+        for (int idx = threadIdx.x; idx < R * Wc; idx += blockDim.x) {
+            const int rl = idx / Wc, kx = idx - rl * Wc;
+            const dfc z = Zc[rl * W + fft_pos(kx & (W - 1), N1w, N2w)];
+            const dfc zc = cconj(Zc[rl * W + fft_pos((W - kx) & (W - 1), N1w, N2w)]);
+            const dfc sp = cadd(z, zc), dm = csub(z, zc);
+            const int r = r0 + rl;
+            Xd[(2 * r) * Wcp + kx] = {df_scale(sp.re, 0.5f), df_scale(sp.im, 0.5f)};
+            Xd[(2 * r + 1) * Wcp + kx] = {df_scale(dm.im, 0.5f), df_scale(df_neg(dm.re), 0.5f)};   // (z - zc)/(2i)
+        }
+        __syncthreads();
+    }
+    // columns, with the product X = F[a] conj F[b] fused into the last pass
+    auto product = [&](int ky, int kx, dfc v) { return cmul(v, cconj(g.FEdf[ky * Wc + kx])); };
+    fft_pass1_df<N1h, N2h, true>(
+        Wc, t4h, [&](int s, int n2, int n1) { return Xd[(N2h * n1 + n2) * Wcp + s]; },
+        [&](int s, int n2, int k1, dfc v) {
+            if (N2h == 1) v = product(k1, s, v);
+            Xd[(N2h * k1 + n2) * Wcp + s] = v;
+        });
+    __syncthreads();
+    if (N2h > 1) {
+        fft_pass2_df<N1h, N2h, true>(
+            Wc, [&](int s, int k1, int n2) { return Xd[(N2h * k1 + n2) * Wcp + s]; },
+            [&](int s, int k1, int k2, dfc v) { Xd[(N2h * k1 + k2) * Wcp + s] = product(k1 + N1h * k2, s, v); });
+        __syncthreads();
+    }
+    // candidates: v(j) = Re sum_ky Ey(ky) sum_kx X(ky, kx) Ex(kx), the Nyquist row taking only
+    // the real part of its phase outside the x-Nyquist column; row sums split kParts ways
+    constexpr int kParts = (H * 4 <= 512) ? 4 : 2;
     dfc* Ey = Zc;            // H
     dfc* Ex = Zc + H;        // Wc
     const long long Dy = (long long)g.u * H, Dx = (long long)g.u * W;
@@ -1567,17 +1599,27 @@ static __device__ int df_reevaluate(const Geom& g, const Smem& S, const void* fr
         }
         __syncthreads();
         df acc = {0.f, 0.f};
-        for (int idx = threadIdx.x; idx < H * Wc; idx += blockDim.x) {
-            const int ky = idx / Wc, kx = idx - ky * Wc;
-            dfc ey = Ey[ky];
-            if (ky == Hh && 2 * kx != W) ey.im = {0.f, 0.f};   // real part of the Nyquist row's phase
-            const dfc e = cmul(ey, Ex[kx]);
-            const dfc x = Xd[ky * Wcp + kx];
-            acc = df_add_abs(acc, df_add_abs(df_mul(x.re, e.re), df_neg(df_mul(x.im, e.im))));
+        for (int task = threadIdx.x; task < H * kParts; task += blockDim.x) {
+            const int ky = task / kParts, part = task - ky * kParts;
+            const dfc* xr = Xd + (size_t)fft_pos(ky, N1h, N2h) * Wcp;
+            dfc F = {{0.f, 0.f}, {0.f, 0.f}}, FN = F;
+            for (int kx = part; kx < Wc; kx += kParts) {
+                const dfc t = cmul(xr[kx], Ex[kx]);
+                if (2 * kx == W) FN = t; else F = cadd(F, t);
+            }
+            const dfc ey = Ey[ky];
+            df v;
+            if (ky == Hh) {
+                v = df_add_abs(df_mul(ey.re, F.re), cmul(ey, FN).re);     // real part of the phase only
+            } else {
+                const dfc t = cmul(ey, cadd(F, FN));
+                v = t.re;
+            }
+            acc = df_add_abs(acc, v);
         }
-        const double v = df_to_double(block_sum_df(acc, S.rd));
-        const double sv = (double)g.sense * v;
-        if (sv > bestv || (sv == bestv && j < bestj)) { bestv = sv; bestj = j; bestraw = v; }
+        const double vv = df_to_double(block_sum_df(acc, S.rd));
+        const double sv = (double)g.sense * vv;
+        if (sv > bestv || (sv == bestv && j < bestj)) { bestv = sv; bestj = j; bestraw = vv; }
         __syncthreads();
     }
     *val = bestraw;
@@ -1708,7 +1750,7 @@ __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
         float peak = (c0 + ((flags & 0x10u) ? 0.f : g.sense * (vw + dwin))) / (float)(g.H * g.W);
         if (nl2 > 0) {
             double raw = 0.0;
-            jw = df_reevaluate(g, S, frame, b.pitch, py, px, nl2, &raw);
+            jw = df_reevaluate<H, W>(g, S, frame, b.pitch, py, px, nl2, &raw);
             peak = (float)(raw / ((double)g.H * g.W));
             flags |= 0x04u;
         }
