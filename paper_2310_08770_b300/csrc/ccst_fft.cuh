@@ -183,11 +183,11 @@ __device__ __forceinline__ void fft_pass2(int nseq, LD ld, ST st) {
 // The same four-step passes over double-float complex values (the last guard level):
 // register DFTs built from 2- and 4-point butterflies, twiddles W_N^{n2 k1} from a
 // [k1][n2] table. Sums use the absolute-error double-word addition (an FFT's error bound).
-namespace dfk {
+namespace dfconst {
 constexpr double kC1 = 0.92387953251128675613;      // cos(pi/8)
 constexpr double kS1 = 0.38268343236508977173;      // sin(pi/8)
 constexpr double kR2 = 0.70710678118654752440;      // sqrt(1/2)
-}  // namespace dfk
+}  // namespace dfconst
 
 __device__ __forceinline__ df df_const(double x) {
     const float h = (float)x;
@@ -195,14 +195,14 @@ __device__ __forceinline__ df df_const(double x) {
 }
 // cos / sin of 2 pi k / 16, k = 0..7
 __device__ __forceinline__ df df_c16(int k) {
-    return k == 0 ? df_const(1.0) : k == 1 ? df_const(dfk::kC1) : k == 2 ? df_const(dfk::kR2)
-         : k == 3 ? df_const(dfk::kS1) : k == 4 ? df_const(0.0) : k == 5 ? df_const(-dfk::kS1)
-         : k == 6 ? df_const(-dfk::kR2) : df_const(-dfk::kC1);
+    return k == 0 ? df_const(1.0) : k == 1 ? df_const(dfconst::kC1) : k == 2 ? df_const(dfconst::kR2)
+         : k == 3 ? df_const(dfconst::kS1) : k == 4 ? df_const(0.0) : k == 5 ? df_const(-dfconst::kS1)
+         : k == 6 ? df_const(-dfconst::kR2) : df_const(-dfconst::kC1);
 }
 __device__ __forceinline__ df df_s16(int k) {
-    return k == 0 ? df_const(0.0) : k == 1 ? df_const(dfk::kS1) : k == 2 ? df_const(dfk::kR2)
-         : k == 3 ? df_const(dfk::kC1) : k == 4 ? df_const(1.0) : k == 5 ? df_const(dfk::kC1)
-         : k == 6 ? df_const(dfk::kR2) : df_const(dfk::kS1);
+    return k == 0 ? df_const(0.0) : k == 1 ? df_const(dfconst::kS1) : k == 2 ? df_const(dfconst::kR2)
+         : k == 3 ? df_const(dfconst::kC1) : k == 4 ? df_const(1.0) : k == 5 ? df_const(dfconst::kC1)
+         : k == 6 ? df_const(dfconst::kR2) : df_const(dfconst::kS1);
 }
 // x * exp(-+ 2 pi i idx / 16), idx a compile-time constant after unrolling
 template <bool INV>
