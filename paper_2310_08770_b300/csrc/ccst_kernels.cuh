@@ -163,15 +163,25 @@ __device__ __forceinline__ double operand_f64(double I, const Geom& g) {
 // is accumulated as lo*hi + hi*lo + hi*hi (the dropped lo*lo is below 2^-22 of it). Two
 // consecutive K elements share one 32-bit register as the MMA fragments want them; an
 // operand row is stored as uint2 {hi pair, lo pair} per K pair.
+// two floats -> one register of two fp16 (a in the low half), round to nearest; and back
+__device__ __forceinline__ unsigned pack_f16x2(float a, float b) {
+    unsigned r;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+    return r;
+}
+__device__ __forceinline__ float2 unpack_f16x2(unsigned v) {
+    float a, b;
+    asm("{\n.reg .f16 lo, hi;\nmov.b32 {lo, hi}, %2;\ncvt.f32.f16 %0, lo;\ncvt.f32.f16 %1, hi;\n}"
+        : "=f"(a), "=f"(b) : "r"(v));
+    return make_float2(a, b);
+}
 __device__ __forceinline__ uint2 split_pair(float a, float b) {
-    const __half2 h = __floats2half2_rn(a, b);
-    const float2 hf = __half22float2(h);
-    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
-    return make_uint2(*reinterpret_cast<const unsigned*>(&h), *reinterpret_cast<const unsigned*>(&l));
+    const unsigned h = pack_f16x2(a, b);
+    const float2 hf = unpack_f16x2(h);
+    return make_uint2(h, pack_f16x2(a - hf.x, b - hf.y));
 }
 __device__ __forceinline__ float2 unsplit_pair(uint2 v) {
-    const float2 h = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
-    const float2 l = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+    const float2 h = unpack_f16x2(v.x), l = unpack_f16x2(v.y);
     return make_float2(h.x + l.x, h.y + l.y);
 }
 // Pair-index swizzle of an operand row with kp pairs: pair p of row r sits at p ^ pswz(r).
@@ -1247,6 +1257,43 @@ __device__ __forceinline__ float2 expi_pi_frac(long long n, long long D) {
 __device__ __forceinline__ float sin_pi_frac(long long n, long long D) {
     return sinpif((float)n / (float)D);
 }
+// the same in 32-bit integers (u <= 16384, H, W <= 128: |n| and 2D stay below 2^31)
+__device__ __forceinline__ float2 expi_pi_frac32(int n, int D) {
+    int r = n % (2 * D);
+    if (r < 0) r += 2 * D;
+    float s, c;
+    sincospif((float)r / (float)D, &s, &c);
+    return make_float2(c, s);
+}
+
+// X'(ky, kx) along one row over the regular columns kx < W/2, with the row's case and its
+// plane pair resolved once: X'(0) from S.X0, X'(Hh) = P(Hh), X'(+-m) = (P +- Q)/2.
+struct XRow {
+    int mode;          // 0: row 0; 1: the Nyquist row (P only); 2: (P + Q)/2; 3: (P - Q)/2
+    int p, h;          // pair index of m = |row| and its half
+    float sa, sb;      // weights of P and Q, including the 2^-kexp unscale
+    __device__ __forceinline__ XRow(const Geom& g, const Smem& S, int ky) {
+        const int Hh = g.Hh, m = ky <= Hh ? ky : g.H - ky;
+        const float inv = ldexpf(1.f, -S.misc[3]);
+        mode = ky == 0 ? 0 : (ky == Hh ? 1 : (ky < Hh ? 2 : 3));
+        p = (m - 1) >> 1;
+        h = (m - 1) & 1;
+        sa = mode == 1 ? inv : 0.5f * inv;
+        sb = mode == 2 ? 0.5f * inv : (mode == 3 ? -0.5f * inv : 0.f);
+    }
+    __device__ __forceinline__ float2 at(const Geom& g, const Smem& S, int kx) const {
+        if (mode == 0) return S.X0[kx];
+        const int SA = g.SA, Hq = g.Hh / 2, q = p ^ pswz(kx, Hq);
+        auto half = [&](uint2 v) {
+            const float2 hh = unpack_f16x2(v.x), ll = unpack_f16x2(v.y);
+            return h ? hh.y + ll.y : hh.x + ll.x;
+        };
+        const float pr = half(S.PQ[(0 * SA + kx) * Hq + q]), pi = half(S.PQ[(1 * SA + kx) * Hq + q]);
+        if (mode == 1) return make_float2(sa * pr, sa * pi);
+        const float qr = half(S.PQ[(2 * SA + kx) * Hq + q]), qi = half(S.PQ[(3 * SA + kx) * Hq + q]);
+        return make_float2(fmaf(sa, pr, sb * qr), fmaf(sa, pi, sb * qi));
+    }
+};
 
 // Full twiddle exp(2 pi i k' t / (uH)) of the stage tables (FP64-rounded values).
 __device__ __forceinline__ float2 table_twiddle_y(const Geom& g, int ks, int t) {
@@ -1304,15 +1351,15 @@ static __device__ int pair_difference_guard(const Geom& g, const Smem& S, int nc
                 const int ks = signed_k(kk, H);
                 Eyc[ci * H + kk] = table_twiddle_y(g, ks, ty);
                 // E(ty) - E(ry) = 2i sin(pi k'(ty - ry)/(uH)) exp(i pi k'(ty + ry)/(uH))
-                const float s1 = sin_pi_frac((long long)ks * (ty - ry), (long long)u * H);
-                const float2 e2 = expi_pi_frac((long long)ks * (ty + ry), (long long)u * H);
+                const float s1 = sinpif((float)(ks * (ty - ry)) / (float)(u * H));
+                const float2 e2 = expi_pi_frac32(ks * (ty + ry), u * H);
                 dEy[ci * H + kk] = make_float2(-2.f * s1 * e2.y, 2.f * s1 * e2.x);
             } else {
                 const int kx = kk - H;
                 const int ks = signed_k(kx, g.W);
                 const float w = (kx == 0 || 2 * kx == g.W) ? 1.f : 2.f;
-                const float s1 = sin_pi_frac((long long)ks * (tx - rx), (long long)u * g.W);
-                const float2 e2 = expi_pi_frac((long long)ks * (tx + rx), (long long)u * g.W);
+                const float s1 = sinpif((float)(ks * (tx - rx)) / (float)(u * g.W));
+                const float2 e2 = expi_pi_frac32(ks * (tx + rx), u * g.W);
                 fx[(1 + ci) * Wc + kx] = make_float2(-2.f * w * s1 * e2.y, 2.f * w * s1 * e2.x);
             }
         }
@@ -1324,8 +1371,9 @@ static __device__ int pair_difference_guard(const Geom& g, const Smem& S, int nc
             float2 acc[NF], accn[NF];
 #pragma unroll
             for (int f = 0; f < NF; ++f) { acc[f] = make_float2(0.f, 0.f); accn[f] = acc[f]; }
+            const XRow xr(g, S, ky);
             for (int kx = Wc - 1 - q; kx >= 0; kx -= kPdParts) {
-                const float2 xp = xprime(g, S, ky, kx);
+                const float2 xp = kx == kn ? xprime(g, S, ky, kx) : xr.at(g, S, kx);
                 const bool nn = (ky == Hh && kx == kn);
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
