@@ -144,6 +144,22 @@ int ccst_track(ccst_ctx* ctx, const void* frames_dev, int64_t n, int64_t pitch_e
 int ccst_track_host(ccst_ctx* ctx, const void* frames_host, int64_t n, int64_t pitch_elems,
                     ccst_result* out_host);
 
+/* Pipelined host form for streaming from host memory (not in the paper: the serving side
+ * of a camera link). It enqueues, without waiting: the copy of n frames host -> device,
+ * the tracking, and the copy of the results to out_host. It returns a ticket for
+ * ccst_poll, and the results are in out_host once that ticket is done.
+ *   Submissions rotate over four device staging slots on two internal streams. The
+ *   copies of one batch therefore overlap the tracking of the previous one.
+ *   Submitting into a slot whose previous batch is still running blocks until it ends.
+ *   The internal streams start after the work already issued on the context's stream.
+ *   They are not ordered against later work on it: use the tickets.
+ *   frames_host and out_host must stay valid until the ticket is done. They must be
+ *   pinned host memory for the copies to be asynchronous.
+ * Errors: as ccst_track, plus CCST_E_BUSY when all tickets are in flight and CCST_E_NOMEM
+ * when the staging slots (4 x max_batch frames) cannot be allocated on first use. */
+int ccst_submit_host(ccst_ctx* ctx, const void* frames_host, int64_t n, int64_t pitch_elems,
+                     ccst_result* out_host, uint64_t* ticket);
+
 /* Work on `stream` (a cudaStream_t) from now on. The caller orders this
  * against earlier work. */
 int ccst_set_stream(ccst_ctx* ctx, void* stream);

@@ -68,6 +68,8 @@ _SIGS = [
     ("ccst_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                    ctypes.POINTER(ctypes.c_uint64)]),
     ("ccst_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("ccst_submit_host", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                        ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
     ("ccst_backward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p]),
     ("ccst_destroy", None, [ctypes.c_void_p]),
@@ -159,6 +161,13 @@ def ccst_sync(ctx) -> None:
 def ccst_submit(ctx, frames_dev, n: int, out_dev) -> int:
     t = ctypes.c_uint64()
     _check(lib().ccst_submit(ctx, _ptr(frames_dev), int(n), _ptr(out_dev), ctypes.byref(t)), ctx)
+    return t.value
+
+
+def ccst_submit_host(ctx, frames_host, n: int, pitch_elems: int, out_host) -> int:
+    t = ctypes.c_uint64()
+    _check(lib().ccst_submit_host(ctx, _ptr(frames_host), int(n), int(pitch_elems), _ptr(out_host),
+                                  ctypes.byref(t)), ctx)
     return t.value
 
 

@@ -25,6 +25,7 @@ static_assert(sizeof(ccst_result) == 24, "result record is 24 bytes");
 namespace {
 
 constexpr int kTickets = 64;      // in-flight submissions per context
+constexpr int kHostSlots = 4;     // staging slots of the pipelined host path
 constexpr size_t kMaxGraphs = 512;
 
 // Guard thresholds, in units of the FP32 unit roundoff times sum w|X| (see DESIGN notes
@@ -244,6 +245,14 @@ struct ccst_ctx {
     bool busy[kTickets] = {};
     uint64_t ticket_of[kTickets] = {};
     uint64_t next_ticket = 1;
+    // pipelined host path: per slot a device staging area, a frame counter and the ticket
+    // using it; slots alternate between two streams
+    cudaStream_t hstream[2] = {nullptr, nullptr};
+    void* h_frames[kHostSlots] = {};
+    Result* h_out[kHostSlots] = {};
+    unsigned* h_next = nullptr;
+    uint64_t h_ticket[kHostSlots] = {};
+    uint64_t h_count = 0;
 };
 
 static int fail(ccst_ctx* c, int code, const std::string& msg) {
@@ -284,6 +293,13 @@ static void free_all(ccst_ctx* c) {
     c->prof1.clear();
     for (int i = 0; i < kTickets; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    for (int i = 0; i < kHostSlots; ++i) {
+        if (c->h_frames[i]) cudaFree(c->h_frames[i]);
+        if (c->h_out[i]) cudaFree(c->h_out[i]);
+    }
+    if (c->h_next) cudaFree(c->h_next);
+    for (int i = 0; i < 2; ++i)
+        if (c->hstream[i]) cudaStreamDestroy(c->hstream[i]);
     void* ptrs[] = {c->d_ref32, c->d_b64, c->d_FE64, c->d_FE32, c->d_tw64, c->d_tw32,
                     c->d_tab,   c->d_df,  c->d_frames, c->d_out, c->d_next};
     for (void* p : ptrs)
@@ -465,6 +481,20 @@ static int launch(ccst_ctx* c, const Batch& b) {
     return CCST_OK;
 }
 
+// Plain launch on `stream` with its own frame counter (the pipelined host path).
+static int launch_on(ccst_ctx* c, const Batch& b, cudaStream_t stream, unsigned* counter) {
+    if (b.n == 0) return CCST_OK;
+    const int grid = (int)(b.n < c->grid_main ? b.n : c->grid_main);
+    Geom gk = c->g;
+    Batch bk = b;
+    bk.next = counter;
+    CK(c, cudaMemsetAsync(counter, 0, sizeof(unsigned), stream));
+    void* args[] = {&gk, &bk};
+    CK(c, cudaLaunchKernel(c->kernel, dim3(grid), dim3(kThreads), args, c->smem, stream));
+    CK(c, cudaGetLastError());
+    return CCST_OK;
+}
+
 static int check_ctx(ccst_ctx* c) {
     if (!c) return CCST_E_INVALID;
     if (c->dead) return CCST_E_CUDA;
@@ -544,6 +574,62 @@ extern "C" int ccst_track_host(ccst_ctx* c, const void* frames_host, int64_t n, 
     if ((rc = ccst_track(c, c->d_frames, n, 0, (ccst_result*)c->d_out))) return rc;
     CK(c, cudaMemcpyAsync(out_host, c->d_out, (size_t)n * sizeof(Result), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
+    return CCST_OK;
+}
+
+extern "C" int ccst_submit_host(ccst_ctx* c, const void* frames_host, int64_t n, int64_t pitch_elems,
+                                ccst_result* out_host, uint64_t* ticket) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!ticket) return fail(c, CCST_E_INVALID, "null ticket");
+    if (n < 0 || n > c->p.max_batch) return fail(c, CCST_E_INVALID, "n outside [0, max_batch]");
+    if (n > 0 && (!frames_host || !out_host)) return fail(c, CCST_E_INVALID, "null frames or out");
+    if (pitch_elems == 0) pitch_elems = c->g.W;
+    if (pitch_elems < c->g.W) return fail(c, CCST_E_INVALID, "pitch_elems < W");
+    const size_t elem = c->p.in_dtype == CCST_U16 ? 2 : 4;
+    const size_t row = (size_t)c->g.W * elem;
+    if (!c->h_next) {                    // first use: streams and staging areas
+        for (int i = 0; i < 2; ++i) CK(c, cudaStreamCreateWithFlags(&c->hstream[i], cudaStreamNonBlocking));
+        for (int i = 0; i < kHostSlots; ++i) {
+            cudaError_t e = cudaMalloc(&c->h_frames[i], (size_t)c->p.max_batch * c->g.H * row);
+            if (e == cudaSuccess) e = cudaMalloc((void**)&c->h_out[i], (size_t)c->p.max_batch * sizeof(Result));
+            if (e != cudaSuccess)
+                return fail(c, e == cudaErrorMemoryAllocation ? CCST_E_NOMEM : CCST_E_CUDA,
+                            std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        CK(c, cudaMalloc((void**)&c->h_next, 256 * kHostSlots));
+        // the work on the internal streams follows everything issued on the context's stream
+        cudaEvent_t e0;
+        CK(c, cudaEventCreateWithFlags(&e0, cudaEventDisableTiming));
+        CK(c, cudaEventRecord(e0, c->stream));
+        for (int i = 0; i < 2; ++i) CK(c, cudaStreamWaitEvent(c->hstream[i], e0, 0));
+        CK(c, cudaEventDestroy(e0));
+    }
+    const int hs = (int)(c->h_count % kHostSlots);
+    // the slot's previous submission must be finished before its staging area is reused
+    if (c->h_ticket[hs]) {
+        const int ts = (int)(c->h_ticket[hs] % kTickets);
+        if (c->busy[ts] && c->ticket_of[ts] == c->h_ticket[hs]) CK(c, cudaEventSynchronize(c->ev[ts]));
+    }
+    const uint64_t t = c->next_ticket;
+    const int slot = (int)(t % kTickets);
+    if (c->busy[slot]) return fail(c, CCST_E_BUSY, "all submission slots in flight");
+    cudaStream_t st = c->hstream[hs & 1];
+    if (n > 0) {
+        CK(c, cudaMemcpy2DAsync(c->h_frames[hs], row, frames_host, (size_t)pitch_elems * elem, row,
+                                (size_t)n * c->g.H, cudaMemcpyHostToDevice, st));
+        Batch b;
+        if ((rc = make_batch(c, c->h_frames[hs], n, 0, (ccst_result*)c->h_out[hs], &b))) return rc;
+        if ((rc = launch_on(c, b, st, c->h_next + 64 * hs))) return rc;
+        CK(c, cudaMemcpyAsync(out_host, c->h_out[hs], (size_t)n * sizeof(Result), cudaMemcpyDeviceToHost, st));
+    }
+    CK(c, cudaEventRecord(c->ev[slot], st));
+    c->busy[slot] = true;
+    c->ticket_of[slot] = t;
+    c->next_ticket = t + 1;
+    c->h_ticket[hs] = t;
+    ++c->h_count;
+    *ticket = t;
     return CCST_OK;
 }
 

@@ -293,6 +293,32 @@ def test_host_path_graphs_and_submit_match_device_path(torch):
     t.close()
 
 
+def test_pipelined_host_path_matches_device_path(torch):
+    """ccst_submit_host: six batches (two full rounds of its staging slots, a ragged last
+    one) with three in flight; every batch's results equal the device path's."""
+    s = synth.frame_stream(seed=4, n=1400, count=1400)
+    sizes = [256, 256, 100, 256, 256, 200]
+    starts = np.cumsum([0] + sizes[:-1])
+    base = run_gpu(torch, s.ref, s.frames, u=100)
+    t = C.Tracker(s.ref, upsample=100)
+    pinned = torch.from_numpy(s.frames.view(np.int16)).pin_memory().numpy().view(np.uint16)
+    outs = [torch.empty((256 * 24,), dtype=torch.uint8).pin_memory().numpy().view(C.RESULT_DTYPE)
+            for _ in sizes]
+    pending = []
+    for k, (lo, n) in enumerate(zip(starts, sizes)):
+        pending.append((k, C.ccst_submit_host(t.ctx, pinned[lo:lo + n], n, 0, outs[k])))
+        if len(pending) == 3:
+            k0, tk = pending.pop(0)
+            while not C.ccst_poll(t.ctx, tk, 100000):
+                pass
+    for k0, tk in pending:
+        while not C.ccst_poll(t.ctx, tk, 100000):
+            pass
+    for k, (lo, n) in enumerate(zip(starts, sizes)):
+        assert np.array_equal(outs[k][:n], base[lo:lo + n]), f"batch {k}"
+    t.close()
+
+
 def test_edge_cases(torch):
     H = W = 32
     ref = synth.gaussian_spot(H, W, 16.0, 16.0, 2.0, 500.0, 5.0).astype(np.float32)
