@@ -270,6 +270,17 @@ const char* ccst_static_last_error(void);
 int ccst_debug_pairs(ccst_ctx* ctx, const void* frames_dev, int64_t n, int64_t pitch_elems,
                      const int32_t* pairs_dev, float* d32_dev, double* d64_dev);
 
+/* Diagnostic entry, for tests of the kernel's bounded waits. It runs ccst_track's
+ * kernel with the bulk copies of the stage tables withheld, so the wait for them must run
+ * out (after 2^10 polls here; 2^22 in normal runs).
+ *   Each frame a CTA reached gets CCST_R_TIMEOUT, and that CTA stops.
+ *   Frames no CTA reached keep their previous out_dev contents.
+ *   With n <= the number of SMs, every frame is reached.
+ * No fault is raised; the context stays usable.
+ * Errors: as ccst_track. */
+int ccst_debug_timeout(ccst_ctx* ctx, const void* frames_dev, int64_t n, int64_t pitch_elems,
+                       ccst_result* out_dev);
+
 #ifdef __cplusplus
 }
 #endif

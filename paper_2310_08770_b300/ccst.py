@@ -80,6 +80,8 @@ _SIGS = [
     ("ccst_profile_reset", ctypes.c_int, [ctypes.c_void_p]),
     ("ccst_debug_surfaces", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("ccst_debug_timeout", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.c_void_p]),
     ("ccst_debug_pairs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("ccst_track_static", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ccst_params),
@@ -214,6 +216,10 @@ def _check_nonneg(v, ctx):
 def ccst_debug_surfaces(ctx, frames_dev, n, pitch_elems, out_dev, int_surf_dev, sub_surf_dev) -> None:
     _check(lib().ccst_debug_surfaces(ctx, _ptr(frames_dev), int(n), int(pitch_elems), _ptr(out_dev),
                                      _ptr(int_surf_dev), _ptr(sub_surf_dev)), ctx)
+
+
+def ccst_debug_timeout(ctx, frames_dev, n, pitch_elems, out_dev) -> None:
+    _check(lib().ccst_debug_timeout(ctx, _ptr(frames_dev), int(n), int(pitch_elems), _ptr(out_dev)), ctx)
 
 
 def ccst_debug_pairs(ctx, frames_dev, n, pitch_elems, pairs_dev, d32_dev, d64_dev) -> None:

@@ -518,6 +518,7 @@ static int make_batch(ccst_ctx* c, const void* frames, int64_t n, int64_t pitch,
     b->dbg_d32 = nullptr;
     b->dbg_d64 = nullptr;
     b->next = nullptr;
+    b->dbg_no_copy = 0;
     return CCST_OK;
 }
 
@@ -763,6 +764,23 @@ extern "C" int ccst_debug_pairs(ccst_ctx* c, const void* frames_dev, int64_t n, 
     b.dbg_pairs = pairs_dev;
     b.dbg_d32 = d32_dev;
     b.dbg_d64 = d64_dev;
+    if (n == 0) return CCST_OK;
+    const int grid = (int)(n < c->grid_main ? n : c->grid_main);
+    Geom gk = c->g;
+    void* args[] = {&gk, &b};
+    CK(c, cudaLaunchKernel(c->kernel, dim3(grid), dim3(kThreads), args, c->smem, c->stream));
+    return CCST_OK;
+}
+
+// Diagnostic entry (tests only): tracks with the table copies withheld, so that the first
+// bounded wait of every CTA runs out; the frames reached report CCST_R_TIMEOUT.
+extern "C" int ccst_debug_timeout(ccst_ctx* c, const void* frames_dev, int64_t n, int64_t pitch_elems,
+                                  ccst_result* out_dev) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    Batch b;
+    if ((rc = make_batch(c, frames_dev, n, pitch_elems, out_dev, &b))) return rc;
+    b.dbg_no_copy = 1;
     if (n == 0) return CCST_OK;
     const int grid = (int)(n < c->grid_main ? n : c->grid_main);
     Geom gk = c->g;

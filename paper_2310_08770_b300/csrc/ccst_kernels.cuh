@@ -106,6 +106,7 @@ struct Batch {
     const int* dbg_pairs;  // optional: n x 2 grid indices (ja, jb); then only the pair difference runs
     float* dbg_d32;        // n: v(jb) - v(ja) by the FP32 pair-difference guard
     double* dbg_d64;       // n: the same difference accumulated in FP64 from the FP32 spectrum
+    int dbg_no_copy;       // tests of the bounded wait: withhold the table copies (the wait runs out)
     unsigned* next;        // optional: frame counter (zero at launch); CTAs take frames from it in
                            // order, so that a slow frame delays no other. Null: CTA i takes frames
                            // i, i + gridDim.x, ...
@@ -661,11 +662,12 @@ __device__ __forceinline__ void stage_tables_async(const Geom& g, const Smem& S)
     }
 }
 // Waits for the copies of phase `parity`. Bounded: returns false if they have not landed
-// after ~2^22 polls (far beyond any real copy time), true otherwise.
-__device__ __forceinline__ bool stage_tables_wait(const Geom& g, const Smem& S, unsigned parity) {
+// after `limit` polls (2^22 normally, far beyond any real copy time), true otherwise.
+__device__ __forceinline__ bool stage_tables_wait(const Geom& g, const Smem& S, unsigned parity,
+                                                  int limit = 1 << 22) {
     if (!g.tables_smem) return true;
     const unsigned b = (unsigned)__cvta_generic_to_shared(S.bar);
-    for (int it = 0; it < (1 << 22); ++it) {
+    for (int it = 0; it < limit; ++it) {
         unsigned done;
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
                      : "=r"(done) : "r"(b), "r"(parity) : "memory");
@@ -1707,14 +1709,15 @@ __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
         const float c0 = int_surface(g, S, ip);           // HW * c(p)
         const int py = wrap_shift(ip >> g.logW, g.H), px = wrap_shift(ip & (g.W - 1), g.W);
         __syncthreads();
-        stage_tables_async(g, S);                          // overlaps the P/Q build
+        if (!b.dbg_no_copy) stage_tables_async(g, S);      // overlaps the P/Q build
         build_pq_and_g(g, S, py, px, scale);
-        const bool staged = stage_tables_wait(g, S, bar_parity);
+        const int wait_limit = b.dbg_no_copy ? (1 << 10) : (1 << 22);
+        const bool staged = stage_tables_wait(g, S, bar_parity, wait_limit);
         if (__syncthreads_or(!staged)) {
             // the copies never completed: report it for this frame and stop this CTA, after
             // one more bounded wait so that no copy is left writing into this CTA's memory
             if (threadIdx.x == 0) {
-                (void)stage_tables_wait(g, S, bar_parity);
+                (void)stage_tables_wait(g, S, bar_parity, wait_limit);
                 Result r{};
                 r.flags = flags | 0x20u;
                 b.out[f] = r;

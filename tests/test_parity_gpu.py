@@ -319,6 +319,25 @@ def test_pipelined_host_path_matches_device_path(torch):
     t.close()
 
 
+def test_bounded_table_wait_reports_timeout_and_context_survives(torch):
+    """With the table copies withheld, every CTA's bounded wait runs out: each frame it
+    reached reports CCST_R_TIMEOUT, nothing faults, and the context still tracks."""
+    s = synth.frame_stream(seed=5, n=64, count=16)
+    base = run_gpu(torch, s.ref, s.frames, u=100)
+    t = C.Tracker(s.ref, upsample=100, max_batch=16)
+    dev = torch.from_numpy(s.frames.view(np.int16)).cuda().view(torch.uint16)
+    out = torch.zeros((16, 24), dtype=torch.uint8, device="cuda")
+    C.ccst_debug_timeout(t.ctx, dev, 16, 0, out)
+    C.ccst_sync(t.ctx)
+    res = C.decode(out)
+    assert np.all(res["flags"] & C.R_TIMEOUT), res["flags"]
+    out2 = torch.zeros((16, 24), dtype=torch.uint8, device="cuda")
+    C.ccst_track(t.ctx, dev, 16, 0, out2)
+    C.ccst_sync(t.ctx)
+    assert np.array_equal(C.decode(out2), base)
+    t.close()
+
+
 def test_edge_cases(torch):
     H = W = 32
     ref = synth.gaussian_spot(H, W, 16.0, 16.0, 2.0, 500.0, 5.0).astype(np.float32)
