@@ -643,10 +643,10 @@ __device__ __forceinline__ void tables_bar_init(const Smem& S) {
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
 }
-// Issued by thread 0 after a __syncthreads that ends every generic access to the
-// destination area.
+// Issued by lane 0 of the last warp (idle in the step that follows, so the proxy fence's
+// latency hides) after a __syncthreads that ends every generic access to the destination.
 __device__ __forceinline__ void stage_tables_async(const Geom& g, const Smem& S) {
-    if (!g.tables_smem || threadIdx.x != 0) return;
+    if (!g.tables_smem || threadIdx.x != blockDim.x - 32) return;     // the last warp idles next
     const unsigned na = (unsigned)ta_bytes(g), nb = (unsigned)tb_bytes(g);
     const unsigned b = (unsigned)__cvta_generic_to_shared(S.bar);
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -760,6 +760,40 @@ static __device__ void build_pq_and_g(const Geom& g, const Smem& S, int py, int 
         }
         Rp[part * ncol + c] = r;
     }
+    // x-Nyquist column, folded in place in XN (FP32) by the last two warps, one row m (and
+    // its mirror H - m) per thread; their P sums are reduced per warp into parts 0 and 1
+    {
+        const int l = (int)threadIdx.x - ((int)blockDim.x - 64);
+        if (l >= 0) {
+            const float2 ex = S.ex[SA];
+            float2 r = make_float2(0.f, 0.f);
+            for (int m = l; m <= Hh; m += 64) {
+                const float2 ey = S.ey[m];
+                if (m == 0 || m == Hh) {
+                    float2* p = S.XN + posH(g, m);
+                    const float2 x = cmul(*p, cmul(ey, ex));
+                    *p = x;
+                    r = cadd(r, x);
+                } else {
+                    float2* rp = S.XN + posH(g, m);
+                    float2* rm = S.XN + posH(g, H - m);
+                    const float2 xp = cmul(*rp, cmul(ey, ex));
+                    const float2 xm = cmul(*rm, cmul(cconj(ey), ex));
+                    const float2 pm = cadd(xp, xm);
+                    *rp = pm;
+                    *rm = csub(xp, xm);
+                    r = cadd(r, pm);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                r.x += __shfl_xor_sync(0xffffffffu, r.x, o);
+                r.y += __shfl_xor_sync(0xffffffffu, r.y, o);
+            }
+            if ((l & 31) == 0) Rp[(l >> 5) * ncol + SA] = r;
+            if (l < 6) Rp[(2 + l) * ncol + SA] = make_float2(0.f, 0.f);
+        }
+    }
     __syncthreads();
     if (mine) {
         const int sw = pswz(c, Hq);
@@ -773,30 +807,6 @@ static __device__ void build_pq_and_g(const Geom& g, const Smem& S, int py, int 
             S.PQ[(2 * SA + c) * Hq + q] = split_pair(pq[j][1].x, pq[j][3].x);     // Qr
             S.PQ[(3 * SA + c) * Hq + q] = split_pair(pq[j][1].y, pq[j][3].y);     // Qi
         }
-    }
-    // x-Nyquist column, in place in XN (FP32)
-    for (int pt = threadIdx.x; pt < 8; pt += blockDim.x) {
-        const float2 ex = S.ex[SA];
-        float2 r = make_float2(0.f, 0.f);
-        for (int m = pt; m <= Hh; m += 8) {
-            const float2 ey = S.ey[m];
-            if (m == 0 || m == Hh) {
-                float2* p = S.XN + posH(g, m);
-                const float2 x = cmul(*p, cmul(ey, ex));
-                *p = x;
-                r = cadd(r, x);
-            } else {
-                float2* rp = S.XN + posH(g, m);
-                float2* rm = S.XN + posH(g, H - m);
-                const float2 xp = cmul(*rp, cmul(ey, ex));
-                const float2 xm = cmul(*rm, cmul(cconj(ey), ex));
-                const float2 pm = cadd(xp, xm);
-                *rp = pm;
-                *rm = csub(xp, xm);
-                r = cadd(r, pm);
-            }
-        }
-        Rp[pt * ncol + SA] = r;
     }
     __syncthreads();
     for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
