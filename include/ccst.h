@@ -178,6 +178,51 @@ int ccst_submit(ccst_ctx* ctx, const void* frames_dev, int64_t n, ccst_result* o
  *   CCST_E_INVALID   unknown ticket. */
 int ccst_poll(ccst_ctx* ctx, uint64_t ticket, int timeout_us, int* done);
 
+/* Real-time reference (Sec. III B, Eq. (9)): start a filtered reference from frame 0.
+ *   frame0_dev   device memory, one H x W frame of the context's in_dtype, rows
+ *                pitch_elems apart (0 means W). Read during the call's stream work.
+ *   a0, b1       the filter's coefficients, a0 = 1 - exp(-T/tau), b1 = exp(-T/tau)
+ *                for frame period T and time constant tau. Any finite values.
+ * Sets F[E_0] = F[I_0] (CC-SN: F[I_0 + eps]) and makes E_0 the context's reference,
+ * replacing the one given to ccst_create. The first call allocates the filter
+ * state (2 x H x (W/2+1) complex doubles), owned and freed by the context.
+ * Stream-ordered and asynchronous.
+ * Errors: CCST_E_INVALID (null frame, pitch < W, a0 or b1 not finite),
+ * CCST_E_NOMEM, CCST_E_CUDA. */
+int ccst_rt_begin(ccst_ctx* ctx, const void* frame0_dev, int64_t pitch_elems, double a0, double b1);
+
+/* Real-time tracking (Sec. III B): for i = 0 .. n-1, track frame i against the
+ * current reference E, then update it with the frame aligned by the displacement
+ * d just found, Eq. (9):
+ *   F[E] <- a0 F[I_i](k) e^{+2 pi i (ky' dy / H + kx' dx / W)} + b1 F[E],
+ * with fftfreq-signed ky', kx'; an even axis's Nyquist bin takes cos(pi d). The
+ * aligned frame I_i(r + d) is the frame moved back onto the reference. CC-SN
+ * filters E' = E + eps on I_i + eps and tracks against the operand 1/E'.
+ * d is the record's displacement taken exactly, (p u + t) / u in FP64; a record
+ * flagged CCST_R_TIMEOUT leaves E unchanged.
+ *   frames_dev   device memory, n frames of H rows pitch_elems apart (0 means W).
+ *   out_dev      device memory, n records, as for ccst_track.
+ * Each call continues the filter where the previous one ended. The frames are
+ * sequential by construction: one frame is tracked at a time (latency, not
+ * throughput, is this mode's figure). Stream-ordered and asynchronous.
+ * Errors: CCST_E_INVALID (no ccst_rt_begin yet, n < 0, null pointers, pitch < W),
+ * CCST_E_CUDA. */
+int ccst_rt_track(ccst_ctx* ctx, const void* frames_dev, int64_t n, int64_t pitch_elems,
+                  ccst_result* out_dev);
+
+/* Drift removal (Sec. III B) over n tracking records, r_i = (dx_i, dy_i).
+ *   alpha <= 0   Eq. (10): R_0 = a0 r_0, R_i = a0 r_i + b1 R_{i-1}.
+ *   alpha > 0    Eqs. (11)-(12): the step a0 r_i + (b1 - 1) R_{i-1} of R is cut to
+ *                length alpha / u when longer; R_0 = a0 r_0 as in Eq. (10).
+ * Writes out_dev[2i] = dx_i - R_i.x, out_dev[2i+1] = dy_i - R_i.y (doubles).
+ *   rec_dev, out_dev   device memory owned by the caller.
+ *   stream             cudaStream_t to run on (NULL: the default stream).
+ * The recurrence is sequential; one GPU thread runs it. Asynchronous.
+ * Errors: CCST_E_INVALID (n < 0, null pointers, non-finite a0/b1, NaN alpha,
+ * alpha > 0 with u < 1), CCST_E_CUDA. */
+int ccst_drift_correct(const ccst_result* rec_dev, int64_t n, double a0, double b1, double alpha, int u,
+                       double* out_dev, void* stream);
+
 /* Vector-Jacobian product of the displacement with respect to the frame pixels
  * and the reference. Not implemented in this build: returns CCST_E_UNSUPPORTED. */
 int ccst_backward(ccst_ctx* ctx, const void* frames_dev, int64_t n, const float* g_dxdy_dev,

@@ -80,6 +80,12 @@ _SIGS = [
     ("ccst_profile_reset", ctypes.c_int, [ctypes.c_void_p]),
     ("ccst_debug_surfaces", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("ccst_rt_begin", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
+                                     ctypes.c_double]),
+    ("ccst_rt_track", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                     ctypes.c_void_p]),
+    ("ccst_drift_correct", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     ("ccst_debug_timeout", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                           ctypes.c_void_p]),
     ("ccst_debug_pairs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
@@ -180,6 +186,23 @@ def ccst_poll(ctx, ticket: int, timeout_us: int) -> bool:
         return False
     _check(rc, ctx)
     return bool(done.value)
+
+
+def ccst_rt_begin(ctx, frame0_dev, pitch_elems, a0, b1) -> None:
+    _check(lib().ccst_rt_begin(ctx, _ptr(frame0_dev), int(pitch_elems), float(a0), float(b1)), ctx)
+
+
+def ccst_rt_track(ctx, frames_dev, n, pitch_elems, out_dev) -> None:
+    _check(lib().ccst_rt_track(ctx, _ptr(frames_dev), int(n), int(pitch_elems), _ptr(out_dev)), ctx)
+
+
+def ccst_drift_correct(rec_dev, n, a0, b1, alpha, u, out_dev, stream=None) -> None:
+    s = ctypes.c_void_p(0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream")
+                                                  else int(stream)))
+    rc = lib().ccst_drift_correct(_ptr(rec_dev), int(n), float(a0), float(b1), float(alpha), int(u),
+                                  _ptr(out_dev), s)
+    if rc != OK:
+        raise CcstError(rc, "ccst_drift_correct failed")
 
 
 def ccst_backward(ctx, frames_dev, n, g_dxdy_dev, g_frames_dev, g_ref_dev) -> None:
@@ -295,6 +318,19 @@ class Tracker:
         for s in range(0, n, self.max_batch):
             e = min(n, s + self.max_batch)
             ccst_track(self.ctx, frames[s:e], e - s, 0, out[s:e])
+        ccst_sync(self.ctx)
+        return decode(out)
+
+    def rt_begin(self, frame0, a0: float, b1: float | None = None) -> None:
+        """Start the real-time reference (Sec. III B) from frame0, a CUDA tensor (H, W)."""
+        ccst_rt_begin(self.ctx, frame0, 0, a0, 1.0 - a0 if b1 is None else b1)
+
+    def rt_track(self, frames) -> np.ndarray:
+        """Real-time tracking of frames (n, H, W) CUDA tensor, one frame after another,
+        the reference updated after each (Eq. (9)); returns RESULT_DTYPE records."""
+        n = frames.shape[0]
+        out = self.empty_results(n)
+        ccst_rt_track(self.ctx, frames, n, 0, out)
         ccst_sync(self.ctx)
         return decode(out)
 

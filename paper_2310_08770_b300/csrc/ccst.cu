@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <cmath>
 #include <mutex>
 #include <new>
 #include <string>
@@ -204,6 +205,143 @@ bool plan_geometry(int H, int W, const ccst_params& p, size_t smem_limit, Geom* 
     return false;
 }
 
+
+// ------------------------------------------------- real-time reference (Sec. III B)
+// FP64 2-D transforms over the H x (W/2+1) half spectrum, one CTA per packed row pair or
+// per column, radix-2 in shared memory with the FP64 twiddle table of the context.
+// Y (work) and E (the filtered reference spectrum) are [H][W/2+1] double2.
+
+// rows, forward: packed pair (2r, 2r+1) of a real input; source: frame pixels (+ off) when
+// src64 is null, else the FP64 image src64
+__global__ void rt_rows_fwd(Geom g, const void* frame, long long pitch, double off, const double* src64,
+                            double2* Y) {
+    __shared__ double2 z[128];
+    const int W = g.W, Wc = g.Wc, r = blockIdx.x;
+    for (int x = threadIdx.x; x < W; x += blockDim.x) {
+        double a0, a1;
+        if (src64) {
+            a0 = src64[(2 * r) * W + x];
+            a1 = src64[(2 * r + 1) * W + x];
+        } else {
+            a0 = (double)pixel_f32(frame, g.in_dtype, (long long)(2 * r) * pitch + x) + off;
+            a1 = (double)pixel_f32(frame, g.in_dtype, (long long)(2 * r + 1) * pitch + x) + off;
+        }
+        z[brev(x, g.logW)] = make_double2(a0, a1);
+    }
+    __syncthreads();
+    fft_r2_passes(z, g.logW, 1, W, 1, g.tw64, g.logNtw, false);
+    for (int kx = threadIdx.x; kx < Wc; kx += blockDim.x) {
+        const double2 zk = z[kx], zc = cconj(z[(W - kx) & (W - 1)]);
+        Y[(2 * r) * Wc + kx] = make_double2(0.5 * (zk.x + zc.x), 0.5 * (zk.y + zc.y));
+        Y[(2 * r + 1) * Wc + kx] = make_double2(0.5 * (zk.y - zc.y), -0.5 * (zk.x - zc.x));   // (zk - zc)/(2i)
+    }
+}
+
+// e^{+2 pi i k' d / N} on one axis, the Nyquist bin of an even N taking cos(pi d)
+__device__ inline double2 rt_axis_phase(int k, int N, double d) {
+    double s, co;
+    if (2 * k == N) return make_double2(cospi(d), 0.0);
+    const int ks = k < (N >> 1) ? k : k - N;
+    sincospi(2.0 * ks * d / N, &s, &co);
+    return make_double2(co, s);
+}
+
+// the displacement the record carries, exactly: d = (p u + t) / u in FP64
+__device__ inline double rt_exact_d(float dx, int px, int u) {
+    const double t = rint((double)dx * u - (double)px * u);
+    return ((double)px * u + t) / u;
+}
+
+// columns, forward. With `upd`: E = a0 F[I](r + d) + b1 E (Eq. 9), d the displacement in
+// the record (a record that timed out leaves E as it was); else E = F[input]. E may be null,
+// and the reference spectra FE64 / FE32 / FEdf, when given, receive the result.
+__global__ void rt_cols_fwd(Geom g, const double2* Y, double2* E, int upd, const Result* rec, double a0, double b1,
+                            double2* FE64, float2* FE32, dfc* FEdf) {
+    __shared__ double2 col[128];
+    const int H = g.H, Wc = g.Wc, kx = blockIdx.x;
+    for (int ky = threadIdx.x; ky < H; ky += blockDim.x) col[brev(ky, g.logH)] = Y[ky * Wc + kx];
+    __syncthreads();
+    fft_r2_passes(col, g.logH, 1, H, 1, g.tw64, g.logNtw, false);
+    double2 phx = make_double2(1.0, 0.0);
+    double dy = 0.0;
+    if (upd) {
+        const Result q = *rec;
+        if (q.flags & 0x20u) return;
+        dy = rt_exact_d(q.dy, q.ipy, g.u);
+        phx = rt_axis_phase(kx, g.W, rt_exact_d(q.dx, q.ipx, g.u));
+    }
+    for (int ky = threadIdx.x; ky < H; ky += blockDim.x) {
+        double2 e = col[ky];
+        if (upd) {
+            const double2 a = cmul(e, cmul(rt_axis_phase(ky, H, dy), phx)), p = E[ky * Wc + kx];
+            e = make_double2(a0 * a.x + b1 * p.x, a0 * a.y + b1 * p.y);
+        }
+        if (E) E[ky * Wc + kx] = e;
+        if (FE64) {
+            FE64[ky * Wc + kx] = e;
+            FE32[ky * Wc + kx] = make_float2((float)e.x, (float)e.y);
+            FEdf[ky * Wc + kx] = dfc{df_from_double(e.x), df_from_double(e.y)};
+        }
+    }
+}
+
+// columns, inverse: Y = F_y^-1 E (unscaled)
+__global__ void rt_cols_inv(Geom g, const double2* E, double2* Y) {
+    __shared__ double2 col[128];
+    const int H = g.H, Wc = g.Wc, kx = blockIdx.x;
+    for (int ky = threadIdx.x; ky < H; ky += blockDim.x) col[brev(ky, g.logH)] = E[ky * Wc + kx];
+    __syncthreads();
+    fft_r2_passes(col, g.logH, 1, H, 1, g.tw64, g.logNtw, true);
+    for (int ky = threadIdx.x; ky < H; ky += blockDim.x) Y[ky * Wc + kx] = col[ky];
+}
+
+// rows, inverse, to the real image: b64 = E (CC-U) or 1 / E' (CC-SN), scaled by 1/(HW)
+__global__ void rt_rows_inv(Geom g, const double2* Y, double* b64) {
+    __shared__ double2 z[128];
+    const int W = g.W, Wc = g.Wc, r = blockIdx.x;
+    for (int kx = threadIdx.x; kx < W; kx += blockDim.x) {
+        double2 ye, yo;
+        if (kx < Wc) { ye = Y[(2 * r) * Wc + kx]; yo = Y[(2 * r + 1) * Wc + kx]; }
+        else { ye = cconj(Y[(2 * r) * Wc + W - kx]); yo = cconj(Y[(2 * r + 1) * Wc + W - kx]); }
+        z[brev(kx, g.logW)] = make_double2(ye.x - yo.y, ye.y + yo.x);     // ye + i yo
+    }
+    __syncthreads();
+    fft_r2_passes(z, g.logW, 1, W, 1, g.tw64, g.logNtw, true);
+    const double s = 1.0 / ((double)g.H * W);
+    for (int x = threadIdx.x; x < W; x += blockDim.x) {
+        const double e0 = z[x].x * s, e1 = z[x].y * s;
+        b64[(2 * r) * W + x] = g.method == 0 ? e0 : 1.0 / e0;
+        b64[(2 * r + 1) * W + x] = g.method == 0 ? e1 : 1.0 / e1;
+    }
+}
+
+
+// Drift removal over n records (Sec. III B). The recurrence is sequential, so one thread
+// runs it: Eq. 10 when lim <= 0, else Eqs. 11-12 with each step of R cut to length lim.
+// R_0 = a0 r_0 in both forms; out[2i], out[2i+1] = r_i - R_i for r = (dx, dy).
+__global__ void rt_drift(const Result* rec, long long n, double a0, double b1, double lim, double* out) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double Rx = 0.0, Ry = 0.0;
+    for (long long i = 0; i < n; ++i) {
+        const double rx = rec[i].dx, ry = rec[i].dy;
+        if (i == 0) {
+            Rx = a0 * rx;
+            Ry = a0 * ry;
+        } else if (lim <= 0.0) {
+            Rx = a0 * rx + b1 * Rx;
+            Ry = a0 * ry + b1 * Ry;
+        } else {
+            const double sx = a0 * rx + (b1 - 1.0) * Rx, sy = a0 * ry + (b1 - 1.0) * Ry;
+            const double len = hypot(sx, sy);
+            const double f = len > lim ? lim / len : 1.0;
+            Rx += f * sx;
+            Ry += f * sy;
+        }
+        out[2 * i] = rx - Rx;
+        out[2 * i + 1] = ry - Ry;
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- context
@@ -229,6 +367,11 @@ struct ccst_ctx {
     void* d_frames = nullptr;     // host-path staging
     Result* d_out = nullptr;      // host-path staging
     unsigned* d_next = nullptr;   // frame counter of the tracking launches
+    // real-time reference (Sec. III B): the filtered spectrum F[E] (CC-SN: F[E + eps]) and a
+    // work spectrum, [H][W/2+1] double2 each; the filter's a0, b1
+    double2* d_rtE = nullptr;
+    double2* d_rtY = nullptr;
+    double rt_a0 = 0.0, rt_b1 = 1.0;
     // graphs keyed by (frames, n, pitch, out), each with its own profiling event pair
     struct GraphEntry {
         cudaGraphExec_t exec = nullptr;
@@ -301,7 +444,7 @@ static void free_all(ccst_ctx* c) {
     for (int i = 0; i < 2; ++i)
         if (c->hstream[i]) cudaStreamDestroy(c->hstream[i]);
     void* ptrs[] = {c->d_ref32, c->d_b64, c->d_FE64, c->d_FE32, c->d_tw64, c->d_tw32,
-                    c->d_tab,   c->d_df,  c->d_frames, c->d_out, c->d_next};
+                    c->d_tab,   c->d_df,  c->d_frames, c->d_out, c->d_next, c->d_rtE, c->d_rtY};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -787,6 +930,81 @@ extern "C" int ccst_debug_timeout(ccst_ctx* c, const void* frames_dev, int64_t n
     void* args[] = {&gk, &b};
     CK(c, cudaLaunchKernel(c->kernel, dim3(grid), dim3(kThreads), args, c->smem, c->stream));
     return CCST_OK;
+}
+
+// ------------------------------------------------------- real-time reference (Sec. III B)
+// E (the filtered spectrum) -> the reference operand b64 and its spectra FE64 / FE32 / FEdf:
+// inverse 2-D transform to the real E (CC-SN: E' = E + eps, operand 1/E'), then forward.
+static int rt_refresh(ccst_ctx* c) {
+    const Geom& g = c->g;
+    cudaStream_t s = c->stream;
+    rt_cols_inv<<<g.Wc, 128, 0, s>>>(g, c->d_rtE, c->d_rtY);
+    rt_rows_inv<<<g.H / 2, 128, 0, s>>>(g, c->d_rtY, c->d_b64);
+    rt_rows_fwd<<<g.H / 2, 128, 0, s>>>(g, nullptr, 0, 0.0, c->d_b64, c->d_rtY);
+    rt_cols_fwd<<<g.Wc, 128, 0, s>>>(g, c->d_rtY, nullptr, 0, nullptr, 0.0, 0.0, c->d_FE64, c->d_FE32,
+                                      const_cast<dfc*>(g.FEdf));
+    CK(c, cudaGetLastError());
+    return CCST_OK;
+}
+
+extern "C" int ccst_rt_begin(ccst_ctx* c, const void* frame0_dev, int64_t pitch_elems, double a0, double b1) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!frame0_dev) return fail(c, CCST_E_INVALID, "ccst_rt_begin: null frame");
+    if (pitch_elems == 0) pitch_elems = c->g.W;
+    if (pitch_elems < c->g.W) return fail(c, CCST_E_INVALID, "ccst_rt_begin: pitch_elems < W");
+    if (!std::isfinite(a0) || !std::isfinite(b1)) return fail(c, CCST_E_INVALID, "ccst_rt_begin: a0, b1 not finite");
+    const Geom& g = c->g;
+    const size_t HWc = (size_t)g.H * g.Wc;
+    if (!c->d_rtE) {
+        CK(c, cudaMalloc(&c->d_rtE, HWc * sizeof(double2)));
+        CK(c, cudaMalloc(&c->d_rtY, HWc * sizeof(double2)));
+    }
+    c->rt_a0 = a0;
+    c->rt_b1 = b1;
+    const double off = g.method == CCST_CC_SN ? (double)g.eps : 0.0;
+    rt_rows_fwd<<<g.H / 2, 128, 0, c->stream>>>(g, frame0_dev, pitch_elems, off, nullptr, c->d_rtY);
+    rt_cols_fwd<<<g.Wc, 128, 0, c->stream>>>(g, c->d_rtY, c->d_rtE, 0, nullptr, 0.0, 0.0, nullptr, nullptr, nullptr);
+    CK(c, cudaGetLastError());
+    return rt_refresh(c);
+}
+
+extern "C" int ccst_rt_track(ccst_ctx* c, const void* frames_dev, int64_t n, int64_t pitch_elems,
+                             ccst_result* out_dev) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!c->d_rtE) return fail(c, CCST_E_INVALID, "ccst_rt_track: no real-time reference (ccst_rt_begin)");
+    if (n < 0) return fail(c, CCST_E_INVALID, "ccst_rt_track: n < 0");
+    if (n == 0) return CCST_OK;
+    if (!frames_dev || !out_dev) return fail(c, CCST_E_INVALID, "ccst_rt_track: null frames or out");
+    if (pitch_elems == 0) pitch_elems = c->g.W;
+    if (pitch_elems < c->g.W) return fail(c, CCST_E_INVALID, "ccst_rt_track: pitch_elems < W");
+    const Geom& g = c->g;
+    const size_t fbytes = (size_t)g.H * pitch_elems * (c->p.in_dtype == CCST_U16 ? 2 : 4);
+    const double off = g.method == CCST_CC_SN ? (double)g.eps : 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const void* frame = (const char*)frames_dev + (size_t)i * fbytes;
+        Batch b;
+        if ((rc = make_batch(c, frame, 1, pitch_elems, out_dev + i, &b))) return rc;
+        if ((rc = launch(c, b))) return rc;                  // frame i against E_{i-1}
+        rt_rows_fwd<<<g.H / 2, 128, 0, c->stream>>>(g, frame, pitch_elems, off, nullptr, c->d_rtY);
+        rt_cols_fwd<<<g.Wc, 128, 0, c->stream>>>(g, c->d_rtY, c->d_rtE, 1, (const Result*)(out_dev + i), c->rt_a0,
+                                                  c->rt_b1, nullptr, nullptr, nullptr);
+        CK(c, cudaGetLastError());
+        if ((rc = rt_refresh(c))) return rc;                 // E_i
+    }
+    return CCST_OK;
+}
+
+extern "C" int ccst_drift_correct(const ccst_result* rec_dev, int64_t n, double a0, double b1, double alpha,
+                                  int u, double* out_dev, void* stream) {
+    if (n < 0 || (n > 0 && (!rec_dev || !out_dev))) return CCST_E_INVALID;
+    if (!std::isfinite(a0) || !std::isfinite(b1) || !(alpha == alpha) || (alpha > 0.0 && u < 1))
+        return CCST_E_INVALID;
+    if (n == 0) return CCST_OK;
+    const double lim = alpha > 0.0 ? alpha / u : 0.0;
+    rt_drift<<<1, 32, 0, (cudaStream_t)stream>>>((const Result*)rec_dev, (long long)n, a0, b1, lim, out_dev);
+    return cudaGetLastError() == cudaSuccess ? CCST_OK : CCST_E_CUDA;
 }
 
 // Grid size M of the refinement square for this context (tests and bindings).
