@@ -207,6 +207,65 @@ def cpu_baseline(frames, ref, budget_s=15.0):
                            f"{cores} spawn workers with one BLAS thread each"}
 
 
+RT_FRAMES = 1024                 # real-time leg: frames after frame 0
+RT_A0 = 0.05                     # its filter, a0 = 1 - exp(-T/tau)
+RT_ORACLE_FRAMES = 48
+
+
+def realtime_leg(C, torch, s, stream):
+    """Real-time reference mode (Sec. III B): frames of the same stream tracked one after
+    another, the reference updated after each (Eq. (9)). Throughput over one call of
+    RT_FRAMES frames; latency from one call per frame."""
+    n = RT_FRAMES + 1
+    frames = torch.from_numpy(s.frames[:n].view(np.int16)).cuda().view(torch.uint16)
+    t = C.Tracker(s.ref, upsample=U, method="ccu", in_dtype="u16", max_batch=1, stream=stream)
+    out = t.empty_results(n - 1)
+    ev = lambda: torch.cuda.Event(enable_timing=True)          # noqa: E731
+    with torch.cuda.stream(stream):
+        C.ccst_rt_begin(t.ctx, frames[0], 0, RT_A0, 1 - RT_A0)
+        C.ccst_rt_track(t.ctx, frames[1:9], 8, 0, out[:8])       # warm-up
+        torch.cuda.synchronize()
+        C.ccst_rt_begin(t.ctx, frames[0], 0, RT_A0, 1 - RT_A0)
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        C.ccst_rt_track(t.ctx, frames[1:], n - 1, 0, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        thr_ms = e0.elapsed_time(e1)
+        res = C.decode(out)
+        C.ccst_rt_begin(t.ctx, frames[0], 0, RT_A0, 1 - RT_A0)
+        k = 256
+        starts, ends = [ev() for _ in range(k)], [ev() for _ in range(k)]
+        for i in range(k):
+            starts[i].record(stream)
+            C.ccst_rt_track(t.ctx, frames[1 + i:2 + i], 1, 0, out[i:i + 1])
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        lat_us = np.array([a.elapsed_time(b) * 1e3 for a, b in zip(starts, ends)])
+    again = C.decode(out)[:k]
+    t.close()
+    return {"workload": f"frames 0..{RT_FRAMES} of the same stream, u={U}, CC-U, a0={RT_A0}, b1={1 - RT_A0}",
+            "value": (n - 1) / (thr_ms / 1e3), "unit": "frames/s", "frames": n - 1,
+            "p50_us": float(np.percentile(lat_us, 50)), "p99_us": float(np.percentile(lat_us, 99)),
+            "same_records_per_frame_calls": bool(again.tobytes() == res[:k].tobytes()),
+            "gpu_launches_per_frame": 2, "memsets_per_frame": 1}, res
+
+
+def realtime_cpu_baseline(frames, res):
+    """The FP64 real-time oracle, as it stands, on the first RT_ORACLE_FRAMES frames: its
+    rate, and parity of the GPU records with it."""
+    from oracle import rt_oracle
+    t0 = time.perf_counter()
+    orc = rt_oracle.rt_track(frames[:RT_ORACLE_FRAMES + 1].astype(np.float64), u=U, a0=RT_A0)
+    dt = time.perf_counter() - t0
+    mism = sum(1 for a, o in zip(res, orc)
+               if (int(a["ipy"]), int(a["ipx"])) != (o["ipy"], o["ipx"])
+               or abs(float(a["dx"]) - o["dx32"]) > 1e-3 or abs(float(a["dy"]) - o["dy32"]) > 1e-3)
+    return ({"value": len(orc) / dt, "unit": "frames/s", "cores": 1, "kind": "oracle",
+             "sample": f"first {len(orc)} frames after frame 0, FP64 numpy real-time oracle, one process"},
+            {"frames": len(orc), "mismatches": mism, "tolerance_px": 1e-3})
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -335,7 +394,13 @@ def run_ours(args):
                   "sub": int(np.sum((flags & C.R_SUB_GUARD) != 0)), "df64": int(np.sum((flags & C.R_DF64) != 0)),
                   "overflow": int(np.sum((flags & C.R_OVERFLOW) != 0))},
     }
+    rt_line = rt_res = None
+    if rank == 0 and not args.no_realtime:
+        rt_line, rt_res = realtime_leg(C, torch, s, stream)
+        line["realtime"] = rt_line
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        if rt_res is not None:
+            rt_line["cpu_baseline"], rt_line["parity"] = realtime_cpu_baseline(s.frames, rt_res)
         orc, cb = cpu_baseline(s.frames, s.ref)
         n = len(orc)
         g = res_all[:n]
@@ -424,6 +489,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-realtime", action="store_true")
     ap.add_argument("--frames", type=int, default=N_FRAMES,
                     help="frames of the stream to stage (the workload is 10000; smaller only for profiler captures)")
     args = ap.parse_args()

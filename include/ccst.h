@@ -76,6 +76,9 @@ extern "C" {
 #define CCST_R_NONFINITE   0x10u /* the surface held no finite value (non-finite input) */
 #define CCST_R_TIMEOUT     0x20u /* a bounded wait inside the kernel gave up (the staged stage tables never
                                     arrived); this frame and the rest of its CTA's frames are not tracked */
+#define CCST_R_RT_STALE    0x40u /* real-time mode: the reference update after this frame did not complete
+                                    (a bounded wait gave up, now or earlier); the reference stays stale
+                                    until the next ccst_rt_begin */
 
 typedef struct ccst_params {
     int32_t  upsample;   /* u >= 1, default 100 (Sec. III)                          */
@@ -186,9 +189,10 @@ int ccst_poll(ccst_ctx* ctx, uint64_t ticket, int timeout_us, int* done);
  * Sets F[E_0] = F[I_0] (CC-SN: F[I_0 + eps]) and makes E_0 the context's reference,
  * replacing the one given to ccst_create. The first call allocates the filter
  * state (2 x H x (W/2+1) complex doubles), owned and freed by the context.
- * Stream-ordered and asynchronous.
+ * Each reference update is one cooperative launch of at most W/2+1 CTAs whose grid
+ * barriers wait a bounded time (see CCST_R_RT_STALE). Stream-ordered and asynchronous.
  * Errors: CCST_E_INVALID (null frame, pitch < W, a0 or b1 not finite),
- * CCST_E_NOMEM, CCST_E_CUDA. */
+ * CCST_E_UNSUPPORTED (no cooperative launch on the device), CCST_E_NOMEM, CCST_E_CUDA. */
 int ccst_rt_begin(ccst_ctx* ctx, const void* frame0_dev, int64_t pitch_elems, double a0, double b1);
 
 /* Real-time tracking (Sec. III B): for i = 0 .. n-1, track frame i against the
@@ -199,7 +203,8 @@ int ccst_rt_begin(ccst_ctx* ctx, const void* frame0_dev, int64_t pitch_elems, do
  * aligned frame I_i(r + d) is the frame moved back onto the reference. CC-SN
  * filters E' = E + eps on I_i + eps and tracks against the operand 1/E'.
  * d is the record's displacement taken exactly, (p u + t) / u in FP64; a record
- * flagged CCST_R_TIMEOUT leaves E unchanged.
+ * flagged CCST_R_TIMEOUT leaves E unchanged. A record flagged CCST_R_RT_STALE was
+ * tracked, but the update after it did not complete.
  *   frames_dev   device memory, n frames of H rows pitch_elems apart (0 means W).
  *   out_dev      device memory, n records, as for ccst_track.
  * Each call continues the filter where the previous one ended. The frames are
@@ -314,6 +319,16 @@ const char* ccst_static_last_error(void);
  * Errors: as ccst_track, plus CCST_E_INVALID for NULL buffers. */
 int ccst_debug_pairs(ccst_ctx* ctx, const void* frames_dev, int64_t n, int64_t pitch_elems,
                      const int32_t* pairs_dev, float* d32_dev, double* d64_dev);
+
+/* Diagnostic entry, for tests of the real-time update's bounded waits. It runs one
+ * reference update for the frame frame_dev (record rec_dev) with grid barriers that wait
+ * for one more CTA than the launch has, so every wait must run out (after 2^12 polls here;
+ * 2^22 in normal runs).
+ *   The record gains CCST_R_RT_STALE; so does every later ccst_rt_track record, and the
+ *   reference is left as it was or partly updated, until ccst_rt_begin starts it again.
+ * No fault is raised; the context stays usable.
+ * Errors: CCST_E_INVALID (no ccst_rt_begin yet, null pointers, pitch < W), CCST_E_CUDA. */
+int ccst_debug_rt_timeout(ccst_ctx* ctx, const void* frame_dev, int64_t pitch_elems, ccst_result* rec_dev);
 
 /* Diagnostic entry, for tests of the kernel's bounded waits. It runs ccst_track's
  * kernel with the bulk copies of the stage tables withheld, so the wait for them must run

@@ -25,6 +25,7 @@ R_DF64 = 0x04
 R_OVERFLOW = 0x08
 R_NONFINITE = 0x10
 R_TIMEOUT = 0x20
+R_RT_STALE = 0x40
 
 OK, E_INVALID, E_SHAPE, E_UNSUPPORTED, E_NOMEM, E_CUDA, E_TIMEOUT, E_BUSY = 0, -1, -2, -3, -4, -5, -6, -7
 _CODES = {0: "OK", -1: "E_INVALID", -2: "E_SHAPE", -3: "E_UNSUPPORTED", -4: "E_NOMEM",
@@ -86,6 +87,7 @@ _SIGS = [
                                      ctypes.c_void_p]),
     ("ccst_drift_correct", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    ("ccst_debug_rt_timeout", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     ("ccst_debug_timeout", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                           ctypes.c_void_p]),
     ("ccst_debug_pairs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
@@ -239,6 +241,10 @@ def _check_nonneg(v, ctx):
 def ccst_debug_surfaces(ctx, frames_dev, n, pitch_elems, out_dev, int_surf_dev, sub_surf_dev) -> None:
     _check(lib().ccst_debug_surfaces(ctx, _ptr(frames_dev), int(n), int(pitch_elems), _ptr(out_dev),
                                      _ptr(int_surf_dev), _ptr(sub_surf_dev)), ctx)
+
+
+def ccst_debug_rt_timeout(ctx, frame_dev, pitch_elems, rec_dev) -> None:
+    _check(lib().ccst_debug_rt_timeout(ctx, _ptr(frame_dev), int(pitch_elems), _ptr(rec_dev)), ctx)
 
 
 def ccst_debug_timeout(ctx, frames_dev, n, pitch_elems, out_dev) -> None:

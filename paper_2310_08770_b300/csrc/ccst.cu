@@ -207,34 +207,61 @@ bool plan_geometry(int H, int W, const ccst_params& p, size_t smem_limit, Geom* 
 
 
 // ------------------------------------------------- real-time reference (Sec. III B)
-// FP64 2-D transforms over the H x (W/2+1) half spectrum, one CTA per packed row pair or
-// per column, radix-2 in shared memory with the FP64 twiddle table of the context.
-// Y (work) and E (the filtered reference spectrum) are [H][W/2+1] double2.
+// One cooperative launch refreshes the reference after each frame: FP64 2-D transforms
+// over the H x (W/2+1) half spectrum, row pairs and columns spread over the CTAs, with
+// three grid barriers between the phases:
+//   rows:    Y = F_x[frame + off], two real rows packed into one complex row
+//   columns: F = F_y Y; E = a0 F(k) e^{+2 pi i (ky' dy/H + kx' dx/W)} + b1 E (Eq. 9), or
+//            E = F when starting; Y = F_y^-1 E
+//   rows:    b64 = F_x^-1 Y / (HW) (CC-SN: 1 / that); Y = F_x b64
+//   columns: FE64 / FE32 / FEdf = F_y Y
+// Buffers written by other CTAs in the launch are read with L2-only loads.
+struct RtArgs {
+    const void* frame;          // device frame (in_dtype), rows `pitch` elements apart
+    long long pitch;
+    double off;                 // added to every pixel (CC-SN: eps)
+    int upd;                    // 1: Eq. 9 update with the displacement of *rec; 0: E = F[frame]
+    double a0, b1;
+    Result* rec;                // record of the frame (upd): flags gain 0x40 when the update fails
+    double2* E;                 // [H][Wc] filtered spectrum (filter state)
+    double2* Y;                 // [H][Wc] work spectrum
+    double* b64;                // [H][W]  reference operand
+    double2* FE64;
+    float2* FE32;
+    dfc* FEdf;
+    unsigned* sync;             // [0] arrivals, [1] generation, [2] sticky error
+    unsigned extra;             // arrivals the barriers wait for beyond the grid (0; tests: 1)
+    unsigned limit;             // polls before a barrier gives up
+};
 
-// rows, forward: packed pair (2r, 2r+1) of a real input; source: frame pixels (+ off) when
-// src64 is null, else the FP64 image src64
-__global__ void rt_rows_fwd(Geom g, const void* frame, long long pitch, double off, const double* src64,
-                            double2* Y) {
-    __shared__ double2 z[128];
-    const int W = g.W, Wc = g.Wc, r = blockIdx.x;
-    for (int x = threadIdx.x; x < W; x += blockDim.x) {
-        double a0, a1;
-        if (src64) {
-            a0 = src64[(2 * r) * W + x];
-            a1 = src64[(2 * r + 1) * W + x];
+constexpr unsigned kRtStale = 0x40u;     // the reference update after this frame did not run
+
+// Grid barrier with a bounded wait. Returns false (and sets the sticky error) when the
+// other CTAs do not arrive within the limit; the CTA must then leave the kernel.
+__device__ bool rt_grid_barrier(unsigned* sync, unsigned extra, unsigned limit) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = sync + 1;
+        const unsigned g0 = *gen;
+        __threadfence();
+        bool good = true;
+        if (atomicAdd(sync, 1u) == gridDim.x - 1 + extra) {
+            atomicExch(sync, 0u);
+            __threadfence();
+            atomicAdd(sync + 1, 1u);
         } else {
-            a0 = (double)pixel_f32(frame, g.in_dtype, (long long)(2 * r) * pitch + x) + off;
-            a1 = (double)pixel_f32(frame, g.in_dtype, (long long)(2 * r + 1) * pitch + x) + off;
+            unsigned it = 0;
+            while (*gen == g0) {
+                if (++it > limit) { good = false; atomicOr(sync + 2, 1u); break; }
+                __nanosleep(64);
+            }
         }
-        z[brev(x, g.logW)] = make_double2(a0, a1);
+        __threadfence();
+        ok = good;
     }
     __syncthreads();
-    fft_r2_passes(z, g.logW, 1, W, 1, g.tw64, g.logNtw, false);
-    for (int kx = threadIdx.x; kx < Wc; kx += blockDim.x) {
-        const double2 zk = z[kx], zc = cconj(z[(W - kx) & (W - 1)]);
-        Y[(2 * r) * Wc + kx] = make_double2(0.5 * (zk.x + zc.x), 0.5 * (zk.y + zc.y));
-        Y[(2 * r + 1) * Wc + kx] = make_double2(0.5 * (zk.y - zc.y), -0.5 * (zk.x - zc.x));   // (zk - zc)/(2i)
-    }
+    return ok != 0;
 }
 
 // e^{+2 pi i k' d / N} on one axis, the Nyquist bin of an even N taking cos(pi d)
@@ -252,69 +279,112 @@ __device__ inline double rt_exact_d(float dx, int px, int u) {
     return ((double)px * u + t) / u;
 }
 
-// columns, forward. With `upd`: E = a0 F[I](r + d) + b1 E (Eq. 9), d the displacement in
-// the record (a record that timed out leaves E as it was); else E = F[input]. E may be null,
-// and the reference spectra FE64 / FE32 / FEdf, when given, receive the result.
-__global__ void rt_cols_fwd(Geom g, const double2* Y, double2* E, int upd, const Result* rec, double a0, double b1,
-                            double2* FE64, float2* FE32, dfc* FEdf) {
-    __shared__ double2 col[128];
-    const int H = g.H, Wc = g.Wc, kx = blockIdx.x;
-    for (int ky = threadIdx.x; ky < H; ky += blockDim.x) col[brev(ky, g.logH)] = Y[ky * Wc + kx];
-    __syncthreads();
-    fft_r2_passes(col, g.logH, 1, H, 1, g.tw64, g.logNtw, false);
-    double2 phx = make_double2(1.0, 0.0);
-    double dy = 0.0;
-    if (upd) {
-        const Result q = *rec;
-        if (q.flags & 0x20u) return;
-        dy = rt_exact_d(q.dy, q.ipy, g.u);
-        phx = rt_axis_phase(kx, g.W, rt_exact_d(q.dx, q.ipx, g.u));
-    }
-    for (int ky = threadIdx.x; ky < H; ky += blockDim.x) {
-        double2 e = col[ky];
-        if (upd) {
-            const double2 a = cmul(e, cmul(rt_axis_phase(ky, H, dy), phx)), p = E[ky * Wc + kx];
-            e = make_double2(a0 * a.x + b1 * p.x, a0 * a.y + b1 * p.y);
-        }
-        if (E) E[ky * Wc + kx] = e;
-        if (FE64) {
-            FE64[ky * Wc + kx] = e;
-            FE32[ky * Wc + kx] = make_float2((float)e.x, (float)e.y);
-            FEdf[ky * Wc + kx] = dfc{df_from_double(e.x), df_from_double(e.y)};
-        }
-    }
-}
-
-// columns, inverse: Y = F_y^-1 E (unscaled)
-__global__ void rt_cols_inv(Geom g, const double2* E, double2* Y) {
-    __shared__ double2 col[128];
-    const int H = g.H, Wc = g.Wc, kx = blockIdx.x;
-    for (int ky = threadIdx.x; ky < H; ky += blockDim.x) col[brev(ky, g.logH)] = E[ky * Wc + kx];
-    __syncthreads();
-    fft_r2_passes(col, g.logH, 1, H, 1, g.tw64, g.logNtw, true);
-    for (int ky = threadIdx.x; ky < H; ky += blockDim.x) Y[ky * Wc + kx] = col[ky];
-}
-
-// rows, inverse, to the real image: b64 = E (CC-U) or 1 / E' (CC-SN), scaled by 1/(HW)
-__global__ void rt_rows_inv(Geom g, const double2* Y, double* b64) {
-    __shared__ double2 z[128];
-    const int W = g.W, Wc = g.Wc, r = blockIdx.x;
-    for (int kx = threadIdx.x; kx < W; kx += blockDim.x) {
-        double2 ye, yo;
-        if (kx < Wc) { ye = Y[(2 * r) * Wc + kx]; yo = Y[(2 * r + 1) * Wc + kx]; }
-        else { ye = cconj(Y[(2 * r) * Wc + W - kx]); yo = cconj(Y[(2 * r + 1) * Wc + W - kx]); }
-        z[brev(kx, g.logW)] = make_double2(ye.x - yo.y, ye.y + yo.x);     // ye + i yo
-    }
-    __syncthreads();
-    fft_r2_passes(z, g.logW, 1, W, 1, g.tw64, g.logNtw, true);
-    const double s = 1.0 / ((double)g.H * W);
+// forward transform of the frame's real row pair (2r, 2r+1) into Y
+__device__ void rt_row_pair_fwd(const Geom& g, const RtArgs& a, int r, double2* z) {
+    const int W = g.W, Wc = g.Wc;
     for (int x = threadIdx.x; x < W; x += blockDim.x) {
-        const double e0 = z[x].x * s, e1 = z[x].y * s;
-        b64[(2 * r) * W + x] = g.method == 0 ? e0 : 1.0 / e0;
-        b64[(2 * r + 1) * W + x] = g.method == 0 ? e1 : 1.0 / e1;
+        const double v0 = (double)pixel_f32(a.frame, g.in_dtype, (long long)(2 * r) * a.pitch + x) + a.off;
+        const double v1 = (double)pixel_f32(a.frame, g.in_dtype, (long long)(2 * r + 1) * a.pitch + x) + a.off;
+        z[brev(x, g.logW)] = make_double2(v0, v1);
     }
+    __syncthreads();
+    fft_r2_passes(z, g.logW, 1, W, 1, g.tw64, g.logNtw, false);
+    for (int kx = threadIdx.x; kx < Wc; kx += blockDim.x) {
+        const double2 zk = z[kx], zc = cconj(z[(W - kx) & (W - 1)]);
+        __stcg(a.Y + (2 * r) * Wc + kx, make_double2(0.5 * (zk.x + zc.x), 0.5 * (zk.y + zc.y)));
+        __stcg(a.Y + (2 * r + 1) * Wc + kx, make_double2(0.5 * (zk.y - zc.y), -0.5 * (zk.x - zc.x)));
+    }
+    __syncthreads();
 }
 
+// column kx of Y, transformed over y (in natural order in z)
+__device__ void rt_col_fwd(const Geom& g, const RtArgs& a, int kx, double2* z) {
+    for (int ky = threadIdx.x; ky < g.H; ky += blockDim.x) z[brev(ky, g.logH)] = __ldcg(a.Y + ky * g.Wc + kx);
+    __syncthreads();
+    fft_r2_passes(z, g.logH, 1, g.H, 1, g.tw64, g.logNtw, false);
+}
+
+__global__ void __launch_bounds__(128) rt_update(Geom g, RtArgs a) {
+    __shared__ double2 z[128];
+    const int H = g.H, W = g.W, Wc = g.Wc, Hp = H / 2;
+    if (__ldcg(a.sync + 2) != 0) {                         // an earlier update failed: E is stale
+        if (a.upd && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.rec->flags, kRtStale);
+        return;
+    }
+    double dy = 0.0, dx = 0.0;
+    if (a.upd) {
+        const Result q = *a.rec;
+        if (q.flags & 0x20u) return;                       // no displacement: E stays
+        dy = rt_exact_d(q.dy, q.ipy, g.u);
+        dx = rt_exact_d(q.dx, q.ipx, g.u);
+    }
+    auto failed = [&]() {
+        if (a.upd && threadIdx.x == 0) atomicOr(&a.rec->flags, kRtStale);
+    };
+    for (int r = blockIdx.x; r < Hp; r += gridDim.x) rt_row_pair_fwd(g, a, r, z);
+    if (!rt_grid_barrier(a.sync, a.extra, a.limit)) return failed();
+    for (int kx = blockIdx.x; kx < Wc; kx += gridDim.x) {
+        rt_col_fwd(g, a, kx, z);
+        const double2 phx = a.upd ? rt_axis_phase(kx, W, dx) : make_double2(1.0, 0.0);
+        for (int ky = threadIdx.x; ky < H; ky += blockDim.x) {
+            double2 e = z[ky];
+            if (a.upd) {
+                const double2 s = cmul(e, cmul(rt_axis_phase(ky, H, dy), phx)), p = a.E[ky * Wc + kx];
+                e = make_double2(a.a0 * s.x + a.b1 * p.x, a.a0 * s.y + a.b1 * p.y);
+            }
+            a.E[ky * Wc + kx] = e;                          // column kx is this CTA's alone
+            z[brev(ky, g.logH)] = e;
+        }
+        __syncthreads();
+        fft_r2_passes(z, g.logH, 1, H, 1, g.tw64, g.logNtw, true);
+        for (int ky = threadIdx.x; ky < H; ky += blockDim.x) __stcg(a.Y + ky * Wc + kx, z[ky]);
+        __syncthreads();
+    }
+    if (!rt_grid_barrier(a.sync, a.extra, a.limit)) return failed();
+    const double sc = 1.0 / ((double)H * W);
+    for (int r = blockIdx.x; r < Hp; r += gridDim.x) {
+        // Y rows 2r, 2r+1 are Hermitian in kx: one complex inverse gives both real rows
+        for (int kx = threadIdx.x; kx < W; kx += blockDim.x) {
+            double2 ye, yo;
+            if (kx < Wc) {
+                ye = __ldcg(a.Y + (2 * r) * Wc + kx);
+                yo = __ldcg(a.Y + (2 * r + 1) * Wc + kx);
+            } else {
+                ye = cconj(__ldcg(a.Y + (2 * r) * Wc + W - kx));
+                yo = cconj(__ldcg(a.Y + (2 * r + 1) * Wc + W - kx));
+            }
+            z[brev(kx, g.logW)] = make_double2(ye.x - yo.y, ye.y + yo.x);   // ye + i yo
+        }
+        __syncthreads();
+        fft_r2_passes(z, g.logW, 1, W, 1, g.tw64, g.logNtw, true);
+        for (int x = threadIdx.x; x < W; x += blockDim.x) {
+            const double e0 = z[x].x * sc, e1 = z[x].y * sc;
+            const double b0 = g.method == 0 ? e0 : 1.0 / e0, b1v = g.method == 0 ? e1 : 1.0 / e1;
+            __stcg(a.b64 + (2 * r) * W + x, b0);
+            __stcg(a.b64 + (2 * r + 1) * W + x, b1v);
+            z[brev(x, g.logW)] = make_double2(b0, b1v);
+        }
+        __syncthreads();
+        fft_r2_passes(z, g.logW, 1, W, 1, g.tw64, g.logNtw, false);
+        for (int kx = threadIdx.x; kx < Wc; kx += blockDim.x) {
+            const double2 zk = z[kx], zc = cconj(z[(W - kx) & (W - 1)]);
+            __stcg(a.Y + (2 * r) * Wc + kx, make_double2(0.5 * (zk.x + zc.x), 0.5 * (zk.y + zc.y)));
+            __stcg(a.Y + (2 * r + 1) * Wc + kx, make_double2(0.5 * (zk.y - zc.y), -0.5 * (zk.x - zc.x)));
+        }
+        __syncthreads();
+    }
+    if (!rt_grid_barrier(a.sync, a.extra, a.limit)) return failed();
+    for (int kx = blockIdx.x; kx < Wc; kx += gridDim.x) {
+        rt_col_fwd(g, a, kx, z);
+        for (int ky = threadIdx.x; ky < H; ky += blockDim.x) {
+            const double2 e = z[ky];
+            a.FE64[ky * Wc + kx] = e;
+            a.FE32[ky * Wc + kx] = make_float2((float)e.x, (float)e.y);
+            a.FEdf[ky * Wc + kx] = dfc{df_from_double(e.x), df_from_double(e.y)};
+        }
+        __syncthreads();
+    }
+}
 
 // Drift removal over n records (Sec. III B). The recurrence is sequential, so one thread
 // runs it: Eq. 10 when lim <= 0, else Eqs. 11-12 with each step of R cut to length lim.
@@ -371,6 +441,8 @@ struct ccst_ctx {
     // work spectrum, [H][W/2+1] double2 each; the filter's a0, b1
     double2* d_rtE = nullptr;
     double2* d_rtY = nullptr;
+    unsigned* d_rtSync = nullptr;     // grid barrier of the update: arrivals, generation, error
+    int rt_grid = 0;
     double rt_a0 = 0.0, rt_b1 = 1.0;
     // graphs keyed by (frames, n, pitch, out), each with its own profiling event pair
     struct GraphEntry {
@@ -444,7 +516,7 @@ static void free_all(ccst_ctx* c) {
     for (int i = 0; i < 2; ++i)
         if (c->hstream[i]) cudaStreamDestroy(c->hstream[i]);
     void* ptrs[] = {c->d_ref32, c->d_b64, c->d_FE64, c->d_FE32, c->d_tw64, c->d_tw32,
-                    c->d_tab,   c->d_df,  c->d_frames, c->d_out, c->d_next, c->d_rtE, c->d_rtY};
+                    c->d_tab,   c->d_df,  c->d_frames, c->d_out, c->d_next, c->d_rtE, c->d_rtY, c->d_rtSync};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -933,17 +1005,29 @@ extern "C" int ccst_debug_timeout(ccst_ctx* c, const void* frames_dev, int64_t n
 }
 
 // ------------------------------------------------------- real-time reference (Sec. III B)
-// E (the filtered spectrum) -> the reference operand b64 and its spectra FE64 / FE32 / FEdf:
-// inverse 2-D transform to the real E (CC-SN: E' = E + eps, operand 1/E'), then forward.
-static int rt_refresh(ccst_ctx* c) {
+// One reference update (rt_update) on the context's stream; rec null when starting.
+static int rt_launch(ccst_ctx* c, const void* frame, long long pitch, ccst_result* rec, unsigned extra = 0) {
     const Geom& g = c->g;
-    cudaStream_t s = c->stream;
-    rt_cols_inv<<<g.Wc, 128, 0, s>>>(g, c->d_rtE, c->d_rtY);
-    rt_rows_inv<<<g.H / 2, 128, 0, s>>>(g, c->d_rtY, c->d_b64);
-    rt_rows_fwd<<<g.H / 2, 128, 0, s>>>(g, nullptr, 0, 0.0, c->d_b64, c->d_rtY);
-    rt_cols_fwd<<<g.Wc, 128, 0, s>>>(g, c->d_rtY, nullptr, 0, nullptr, 0.0, 0.0, c->d_FE64, c->d_FE32,
-                                      const_cast<dfc*>(g.FEdf));
-    CK(c, cudaGetLastError());
+    RtArgs a;
+    a.frame = frame;
+    a.pitch = pitch;
+    a.off = g.method == CCST_CC_SN ? (double)g.eps : 0.0;
+    a.upd = rec ? 1 : 0;
+    a.a0 = c->rt_a0;
+    a.b1 = c->rt_b1;
+    a.rec = (Result*)rec;
+    a.E = c->d_rtE;
+    a.Y = c->d_rtY;
+    a.b64 = c->d_b64;
+    a.FE64 = c->d_FE64;
+    a.FE32 = c->d_FE32;
+    a.FEdf = const_cast<dfc*>(g.FEdf);
+    a.sync = c->d_rtSync;
+    a.extra = extra;
+    a.limit = extra ? (1u << 12) : (1u << 22);
+    Geom gk = g;
+    void* args[] = {&gk, &a};
+    CK(c, cudaLaunchCooperativeKernel((const void*)rt_update, dim3(c->rt_grid), dim3(128), args, 0, c->stream));
     return CCST_OK;
 }
 
@@ -957,16 +1041,21 @@ extern "C" int ccst_rt_begin(ccst_ctx* c, const void* frame0_dev, int64_t pitch_
     const Geom& g = c->g;
     const size_t HWc = (size_t)g.H * g.Wc;
     if (!c->d_rtE) {
+        int coop = 0, per_sm = 0, sms = 0;
+        CK(c, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device));
+        CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+        CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt_update, 128, 0));
+        const int want = g.Wc > g.H / 2 ? g.Wc : g.H / 2;
+        if (!coop || per_sm < 1) return fail(c, CCST_E_UNSUPPORTED, "ccst_rt_begin: no cooperative launch");
+        c->rt_grid = want < per_sm * sms ? want : per_sm * sms;
+        CK(c, cudaMalloc(&c->d_rtSync, 4 * sizeof(unsigned)));
         CK(c, cudaMalloc(&c->d_rtE, HWc * sizeof(double2)));
         CK(c, cudaMalloc(&c->d_rtY, HWc * sizeof(double2)));
     }
     c->rt_a0 = a0;
     c->rt_b1 = b1;
-    const double off = g.method == CCST_CC_SN ? (double)g.eps : 0.0;
-    rt_rows_fwd<<<g.H / 2, 128, 0, c->stream>>>(g, frame0_dev, pitch_elems, off, nullptr, c->d_rtY);
-    rt_cols_fwd<<<g.Wc, 128, 0, c->stream>>>(g, c->d_rtY, c->d_rtE, 0, nullptr, 0.0, 0.0, nullptr, nullptr, nullptr);
-    CK(c, cudaGetLastError());
-    return rt_refresh(c);
+    CK(c, cudaMemsetAsync(c->d_rtSync, 0, 4 * sizeof(unsigned), c->stream));
+    return rt_launch(c, frame0_dev, pitch_elems, nullptr);
 }
 
 extern "C" int ccst_rt_track(ccst_ctx* c, const void* frames_dev, int64_t n, int64_t pitch_elems,
@@ -981,19 +1070,25 @@ extern "C" int ccst_rt_track(ccst_ctx* c, const void* frames_dev, int64_t n, int
     if (pitch_elems < c->g.W) return fail(c, CCST_E_INVALID, "ccst_rt_track: pitch_elems < W");
     const Geom& g = c->g;
     const size_t fbytes = (size_t)g.H * pitch_elems * (c->p.in_dtype == CCST_U16 ? 2 : 4);
-    const double off = g.method == CCST_CC_SN ? (double)g.eps : 0.0;
     for (int64_t i = 0; i < n; ++i) {
         const void* frame = (const char*)frames_dev + (size_t)i * fbytes;
         Batch b;
         if ((rc = make_batch(c, frame, 1, pitch_elems, out_dev + i, &b))) return rc;
         if ((rc = launch(c, b))) return rc;                  // frame i against E_{i-1}
-        rt_rows_fwd<<<g.H / 2, 128, 0, c->stream>>>(g, frame, pitch_elems, off, nullptr, c->d_rtY);
-        rt_cols_fwd<<<g.Wc, 128, 0, c->stream>>>(g, c->d_rtY, c->d_rtE, 1, (const Result*)(out_dev + i), c->rt_a0,
-                                                  c->rt_b1, nullptr, nullptr, nullptr);
-        CK(c, cudaGetLastError());
-        if ((rc = rt_refresh(c))) return rc;                 // E_i
+        if ((rc = rt_launch(c, frame, pitch_elems, out_dev + i))) return rc;   // E_i
     }
     return CCST_OK;
+}
+
+extern "C" int ccst_debug_rt_timeout(ccst_ctx* c, const void* frame_dev, int64_t pitch_elems,
+                                     ccst_result* rec_dev) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!c->d_rtE) return fail(c, CCST_E_INVALID, "ccst_debug_rt_timeout: no real-time reference (ccst_rt_begin)");
+    if (!frame_dev || !rec_dev) return fail(c, CCST_E_INVALID, "ccst_debug_rt_timeout: null frame or record");
+    if (pitch_elems == 0) pitch_elems = c->g.W;
+    if (pitch_elems < c->g.W) return fail(c, CCST_E_INVALID, "ccst_debug_rt_timeout: pitch_elems < W");
+    return rt_launch(c, frame_dev, pitch_elems, rec_dev, 1);
 }
 
 extern "C" int ccst_drift_correct(const ccst_result* rec_dev, int64_t n, double a0, double b1, double alpha,

@@ -168,3 +168,30 @@ def test_drift_correct_errors(torch):
     for args in [(-1, 0.1, 0.9, 0.0, 100), (4, float("inf"), 0.9, 0.0, 100), (4, 0.1, 0.9, 0.5, 0)]:
         with pytest.raises(C.CcstError):
             C.ccst_drift_correct(dev, *args, out)
+
+
+def test_rt_bounded_barrier_marks_records_stale_and_begin_recovers(torch):
+    # the update's grid barriers wait for one CTA too many: every wait runs out, the record
+    # and all later ones carry CCST_R_RT_STALE, and ccst_rt_begin starts afresh
+    frames, _ = spot_stream(6, 32, 32, 0.4, seed=14)
+    fresh = rt_gpu(torch, frames, 20, 0.3)
+    t = C.Tracker(np.zeros((32, 32), np.float32), upsample=20, in_dtype="u16")
+    dev = to_device(torch, frames)
+    out = t.empty_results(5)
+    with pytest.raises(C.CcstError):
+        C.ccst_debug_rt_timeout(t.ctx, dev[1], 0, out[0:1])      # no ccst_rt_begin yet
+    C.ccst_rt_begin(t.ctx, dev[0], 0, 0.3, 0.7)
+    C.ccst_rt_track(t.ctx, dev[1:3], 2, 0, out[0:2])
+    C.ccst_debug_rt_timeout(t.ctx, dev[2], 0, out[1:2])
+    C.ccst_rt_track(t.ctx, dev[3:6], 3, 0, out[2:5])
+    C.ccst_sync(t.ctx)
+    r = C.decode(out)
+    stale = (r["flags"] & C.R_RT_STALE) != 0
+    assert stale.tolist() == [False, True, True, True, True]
+    # frame 2 was tracked before its update failed: its record matches the undisturbed run
+    assert r[1]["ipy"] == fresh[1]["ipy"] and r[1]["dx"] == fresh[1]["dx"]
+    C.ccst_rt_begin(t.ctx, dev[0], 0, 0.3, 0.7)
+    C.ccst_rt_track(t.ctx, dev[1:6], 5, 0, out)
+    C.ccst_sync(t.ctx)
+    assert C.decode(out).tobytes() == fresh.tobytes()
+    t.close()
