@@ -215,7 +215,51 @@ int ccst_rt_begin(ccst_ctx* ctx, const void* frame0_dev, int64_t pitch_elems, do
 int ccst_rt_track(ccst_ctx* ctx, const void* frames_dev, int64_t n, int64_t pitch_elems,
                   ccst_result* out_dev);
 
-/* Drift removal (Sec. III B) over n tracking records, r_i = (dx_i, dy_i).
+/* Make frame_dev the reference: F[E] = F[frame] (CC-SN: F[frame + eps]), the E_0 of
+ * Eqs. (8) and (9). It replaces the reference given to ccst_create (or any later one).
+ *   frame_dev    device memory, one H x W frame of the context's in_dtype, rows
+ *                pitch_elems apart (0 means W).
+ * The first call of this, ccst_rt_begin or ccst_offline_update allocates the FP64 filter
+ * state (2 x H x (W/2+1) complex doubles), owned by the context. Clears a stale flag (see
+ * ccst_reference_status). Stream-ordered and asynchronous.
+ * Errors: CCST_E_INVALID (null frame, pitch < W), CCST_E_UNSUPPORTED (no cooperative
+ * launch on the device), CCST_E_NOMEM, CCST_E_CUDA. */
+int ccst_set_reference_frame(ccst_ctx* ctx, const void* frame_dev, int64_t pitch_elems);
+
+/* Offline reference update (Sec. III A, Eq. (8)): make the context's reference the mean, in
+ * Fourier space, of the n frames each moved back by its displacement,
+ *   F[E] = (1/N) sum_i F[I_i](k) e^{+2 pi i (ky' dy_i / H + kx' dx_i / W)},
+ * with d_i the displacement of record i (from tracking frame i against the previous
+ * reference), taken exactly as (p u + t) / u in FP64, and the signed frequencies and
+ * Nyquist bins of ccst_rt_track. CC-SN takes the mean of I_i + eps and tracks against
+ * the operand 1 / that. Records flagged CCST_R_TIMEOUT are left out of the sum and of N;
+ * with none left the reference stays.
+ *   frames_dev   device memory, n frames of H rows pitch_elems apart (0 means W).
+ *   rec_dev      device memory, n records (ccst_track's output for these frames).
+ * The sum runs in FP64 in one CTA per SM (per-CTA partial sums, added in a fixed order:
+ * the result does not depend on timing). The first call allocates 2 x SMs x H x (W/2+1)
+ * complex doubles of workspace, owned by the context. Stream-ordered and asynchronous.
+ * Errors: CCST_E_INVALID (n < 0, null pointers, pitch < W), CCST_E_UNSUPPORTED,
+ * CCST_E_NOMEM, CCST_E_CUDA. */
+int ccst_offline_update(ccst_ctx* ctx, const void* frames_dev, int64_t n, int64_t pitch_elems,
+                        const ccst_result* rec_dev);
+
+/* The offline method of Sec. III A: E_0 = frame 0; for p = 0 .. passes, track all n frames
+ * against E_p (in batches of max_batch) and, for p < passes, set E_{p+1} by
+ * ccst_offline_update. out_dev receives the records of the last pass (against E_passes);
+ * the reference stays E_passes. n may exceed max_batch.
+ * Errors: CCST_E_INVALID (n < 1, passes < 0, null pointers, pitch < W), and those of
+ * ccst_set_reference_frame and ccst_offline_update. */
+int ccst_offline_track(ccst_ctx* ctx, const void* frames_dev, int64_t n, int64_t pitch_elems, int passes,
+                       ccst_result* out_dev);
+
+/* Whether a reference update of ccst_rt_track or ccst_offline_update gave up at a bounded
+ * wait since the last ccst_set_reference_frame / ccst_rt_begin (*stale = 1): the reference
+ * is then out of date. Synchronises the context's stream.
+ * Errors: CCST_E_INVALID (null stale), CCST_E_CUDA. */
+int ccst_reference_status(ccst_ctx* ctx, int* stale);
+
+/* Drift removal (Sec. III B) over n tracking records/* Drift removal (Sec. III B) over n tracking records, r_i = (dx_i, dy_i).
  *   alpha <= 0   Eq. (10): R_0 = a0 r_0, R_i = a0 r_i + b1 R_{i-1}.
  *   alpha > 0    Eqs. (11)-(12): the step a0 r_i + (b1 - 1) R_{i-1} of R is cut to
  *                length alpha / u when longer; R_0 = a0 r_0 as in Eq. (10).
@@ -319,6 +363,11 @@ const char* ccst_static_last_error(void);
  * Errors: as ccst_track, plus CCST_E_INVALID for NULL buffers. */
 int ccst_debug_pairs(ccst_ctx* ctx, const void* frames_dev, int64_t n, int64_t pitch_elems,
                      const int32_t* pairs_dev, float* d32_dev, double* d64_dev);
+
+/* Diagnostic copy of the context's FP64 reference operand, H x W doubles into ref_dev
+ * (device memory): E for CC-U, 1 / (E + eps) for CC-SN. Stream-ordered.
+ * Errors: CCST_E_INVALID (null buffer), CCST_E_CUDA. */
+int ccst_debug_reference(ccst_ctx* ctx, double* ref_dev);
 
 /* Diagnostic entry, for tests of the real-time update's bounded waits. It runs one
  * reference update for the frame frame_dev (record rec_dev) with grid barriers that wait

@@ -87,6 +87,13 @@ _SIGS = [
                                      ctypes.c_void_p]),
     ("ccst_drift_correct", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    ("ccst_set_reference_frame", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    ("ccst_offline_update", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                           ctypes.c_void_p]),
+    ("ccst_offline_track", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.c_int, ctypes.c_void_p]),
+    ("ccst_reference_status", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    ("ccst_debug_reference", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ccst_debug_rt_timeout", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     ("ccst_debug_timeout", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                           ctypes.c_void_p]),
@@ -196,6 +203,30 @@ def ccst_rt_begin(ctx, frame0_dev, pitch_elems, a0, b1) -> None:
 
 def ccst_rt_track(ctx, frames_dev, n, pitch_elems, out_dev) -> None:
     _check(lib().ccst_rt_track(ctx, _ptr(frames_dev), int(n), int(pitch_elems), _ptr(out_dev)), ctx)
+
+
+def ccst_set_reference_frame(ctx, frame_dev, pitch_elems=0) -> None:
+    _check(lib().ccst_set_reference_frame(ctx, _ptr(frame_dev), int(pitch_elems)), ctx)
+
+
+def ccst_offline_update(ctx, frames_dev, n, pitch_elems, rec_dev) -> None:
+    _check(lib().ccst_offline_update(ctx, _ptr(frames_dev), int(n), int(pitch_elems), _ptr(rec_dev)), ctx)
+
+
+def ccst_offline_track(ctx, frames_dev, n, pitch_elems, passes, out_dev) -> None:
+    _check(lib().ccst_offline_track(ctx, _ptr(frames_dev), int(n), int(pitch_elems), int(passes), _ptr(out_dev)),
+           ctx)
+
+
+def ccst_reference_status(ctx) -> bool:
+    """True when a reference update gave up at a bounded wait (the reference is stale)."""
+    st = ctypes.c_int()
+    _check(lib().ccst_reference_status(ctx, ctypes.byref(st)), ctx)
+    return bool(st.value)
+
+
+def ccst_debug_reference(ctx, ref_dev) -> None:
+    _check(lib().ccst_debug_reference(ctx, _ptr(ref_dev)), ctx)
 
 
 def ccst_drift_correct(rec_dev, n, a0, b1, alpha, u, out_dev, stream=None) -> None:
@@ -337,6 +368,15 @@ class Tracker:
         n = frames.shape[0]
         out = self.empty_results(n)
         ccst_rt_track(self.ctx, frames, n, 0, out)
+        ccst_sync(self.ctx)
+        return decode(out)
+
+    def offline_track(self, frames, passes: int = 5) -> np.ndarray:
+        """The offline method (Sec. III A) over frames (n, H, W) CUDA tensor: reference from
+        frame 0, `passes` Eq. (8) updates; returns the records of the last pass."""
+        n = frames.shape[0]
+        out = self.empty_results(n)
+        ccst_offline_track(self.ctx, frames, n, 0, passes, out)
         ccst_sync(self.ctx)
         return decode(out)
 

@@ -207,20 +207,22 @@ bool plan_geometry(int H, int W, const ccst_params& p, size_t smem_limit, Geom* 
 
 
 // ------------------------------------------------- real-time reference (Sec. III B)
-// One cooperative launch refreshes the reference after each frame: FP64 2-D transforms
-// over the H x (W/2+1) half spectrum, row pairs and columns spread over the CTAs, with
-// three grid barriers between the phases:
+// One cooperative launch sets the reference spectrum E and refreshes the reference from
+// it: FP64 2-D transforms over the H x (W/2+1) half spectrum, row pairs and columns
+// spread over the CTAs, with three grid barriers between the phases:
 //   rows:    Y = F_x[frame + off], two real rows packed into one complex row
+//            (mean mode: E = the sum of the partial spectra / the frame count, Eq. 8)
 //   columns: F = F_y Y; E = a0 F(k) e^{+2 pi i (ky' dy/H + kx' dx/W)} + b1 E (Eq. 9), or
-//            E = F when starting; Y = F_y^-1 E
+//            E = F when starting (mean mode: E as it is); Y = F_y^-1 E
 //   rows:    b64 = F_x^-1 Y / (HW) (CC-SN: 1 / that); Y = F_x b64
 //   columns: FE64 / FE32 / FEdf = F_y Y
-// Buffers written by other CTAs in the launch are read with L2-only loads.
+// Buffers written by other CTAs in the launch are read with L2-only loads. One thread per
+// element of a row or column: blockDim (128) >= H, W.
 struct RtArgs {
     const void* frame;          // device frame (in_dtype), rows `pitch` elements apart
     long long pitch;
     double off;                 // added to every pixel (CC-SN: eps)
-    int upd;                    // 1: Eq. 9 update with the displacement of *rec; 0: E = F[frame]
+    int mode;                   // kRtStart: E = F[frame]; kRtUpdate: Eq. 9 with *rec; kRtMean: Eq. 8
     double a0, b1;
     Result* rec;                // record of the frame (upd): flags gain 0x40 when the update fails
     double2* E;                 // [H][Wc] filtered spectrum (filter state)
@@ -232,7 +234,12 @@ struct RtArgs {
     unsigned* sync;             // [0] arrivals, [1] generation, [2] sticky error
     unsigned extra;             // arrivals the barriers wait for beyond the grid (0; tests: 1)
     unsigned limit;             // polls before a barrier gives up
+    const double2* part;        // kRtMean: nparts partial sums [nparts][H][Wc] ...
+    int nparts;
+    const unsigned* count;      // ... over *count frames
 };
+
+constexpr int kRtStart = 0, kRtUpdate = 1, kRtMean = 2;
 
 constexpr unsigned kRtStale = 0x40u;     // the reference update after this frame did not run
 
@@ -306,84 +313,169 @@ __device__ void rt_col_fwd(const Geom& g, const RtArgs& a, int kx, double2* z) {
 
 __global__ void __launch_bounds__(128) rt_update(Geom g, RtArgs a) {
     __shared__ double2 z[128];
-    const int H = g.H, W = g.W, Wc = g.Wc, Hp = H / 2;
+    const int H = g.H, W = g.W, Wc = g.Wc, Hp = H / 2, HWc = H * Wc;
+    const bool upd = a.mode == kRtUpdate;
     if (__ldcg(a.sync + 2) != 0) {                         // an earlier update failed: E is stale
-        if (a.upd && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.rec->flags, kRtStale);
+        if (upd && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.rec->flags, kRtStale);
         return;
     }
     double dy = 0.0, dx = 0.0;
-    if (a.upd) {
+    if (upd) {
         const Result q = *a.rec;
         if (q.flags & 0x20u) return;                       // no displacement: E stays
         dy = rt_exact_d(q.dy, q.ipy, g.u);
         dx = rt_exact_d(q.dx, q.ipx, g.u);
     }
     auto failed = [&]() {
-        if (a.upd && threadIdx.x == 0) atomicOr(&a.rec->flags, kRtStale);
+        if (upd && threadIdx.x == 0) atomicOr(&a.rec->flags, kRtStale);
     };
-    for (int r = blockIdx.x; r < Hp; r += gridDim.x) rt_row_pair_fwd(g, a, r, z);
-    if (!rt_grid_barrier(a.sync, a.extra, a.limit)) return failed();
-    for (int kx = blockIdx.x; kx < Wc; kx += gridDim.x) {
-        rt_col_fwd(g, a, kx, z);
-        const double2 phx = a.upd ? rt_axis_phase(kx, W, dx) : make_double2(1.0, 0.0);
-        for (int ky = threadIdx.x; ky < H; ky += blockDim.x) {
-            double2 e = z[ky];
-            if (a.upd) {
-                const double2 s = cmul(e, cmul(rt_axis_phase(ky, H, dy), phx)), p = a.E[ky * Wc + kx];
-                e = make_double2(a.a0 * s.x + a.b1 * p.x, a.a0 * s.y + a.b1 * p.y);
+    if (a.mode == kRtMean) {
+        // E = (1/N) sum of the partial spectra, in a fixed order; no frames: E stays
+        const unsigned cnt = __ldcg(a.count);
+        if (cnt == 0) return;
+        const double inv = 1.0 / (double)cnt;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < HWc; i += gridDim.x * blockDim.x) {
+            double2 s = make_double2(0.0, 0.0);
+            for (int b = 0; b < a.nparts; ++b) {
+                const double2 v = __ldcg(a.part + (size_t)b * HWc + i);
+                s.x += v.x;
+                s.y += v.y;
             }
-            a.E[ky * Wc + kx] = e;                          // column kx is this CTA's alone
-            z[brev(ky, g.logH)] = e;
+            __stcg(a.E + i, make_double2(s.x * inv, s.y * inv));
+        }
+    } else {
+        for (int r = blockIdx.x; r < Hp; r += gridDim.x) rt_row_pair_fwd(g, a, r, z);
+    }
+    if (!rt_grid_barrier(a.sync, a.extra, a.limit)) return failed();
+    const int t = threadIdx.x;
+    for (int kx = blockIdx.x; kx < Wc; kx += gridDim.x) {
+        double2 e = make_double2(0.0, 0.0);
+        if (a.mode == kRtMean) {
+            if (t < H) e = __ldcg(a.E + t * Wc + kx);
+        } else {
+            rt_col_fwd(g, a, kx, z);
+            if (t < H) {
+                e = z[t];
+                if (upd) {
+                    const double2 s = cmul(e, cmul(rt_axis_phase(t, H, dy), rt_axis_phase(kx, W, dx)));
+                    const double2 p = __ldcg(a.E + t * Wc + kx);
+                    e = make_double2(a.a0 * s.x + a.b1 * p.x, a.a0 * s.y + a.b1 * p.y);
+                }
+                __stcg(a.E + t * Wc + kx, e);
+            }
         }
         __syncthreads();
+        if (t < H) z[brev(t, g.logH)] = e;
+        __syncthreads();
         fft_r2_passes(z, g.logH, 1, H, 1, g.tw64, g.logNtw, true);
-        for (int ky = threadIdx.x; ky < H; ky += blockDim.x) __stcg(a.Y + ky * Wc + kx, z[ky]);
+        if (t < H) __stcg(a.Y + t * Wc + kx, z[t]);
         __syncthreads();
     }
     if (!rt_grid_barrier(a.sync, a.extra, a.limit)) return failed();
     const double sc = 1.0 / ((double)H * W);
     for (int r = blockIdx.x; r < Hp; r += gridDim.x) {
         // Y rows 2r, 2r+1 are Hermitian in kx: one complex inverse gives both real rows
-        for (int kx = threadIdx.x; kx < W; kx += blockDim.x) {
+        if (t < W) {
             double2 ye, yo;
-            if (kx < Wc) {
-                ye = __ldcg(a.Y + (2 * r) * Wc + kx);
-                yo = __ldcg(a.Y + (2 * r + 1) * Wc + kx);
+            if (t < Wc) {
+                ye = __ldcg(a.Y + (2 * r) * Wc + t);
+                yo = __ldcg(a.Y + (2 * r + 1) * Wc + t);
             } else {
-                ye = cconj(__ldcg(a.Y + (2 * r) * Wc + W - kx));
-                yo = cconj(__ldcg(a.Y + (2 * r + 1) * Wc + W - kx));
+                ye = cconj(__ldcg(a.Y + (2 * r) * Wc + W - t));
+                yo = cconj(__ldcg(a.Y + (2 * r + 1) * Wc + W - t));
             }
-            z[brev(kx, g.logW)] = make_double2(ye.x - yo.y, ye.y + yo.x);   // ye + i yo
+            z[brev(t, g.logW)] = make_double2(ye.x - yo.y, ye.y + yo.x);   // ye + i yo
         }
         __syncthreads();
         fft_r2_passes(z, g.logW, 1, W, 1, g.tw64, g.logNtw, true);
-        for (int x = threadIdx.x; x < W; x += blockDim.x) {
-            const double e0 = z[x].x * sc, e1 = z[x].y * sc;
-            const double b0 = g.method == 0 ? e0 : 1.0 / e0, b1v = g.method == 0 ? e1 : 1.0 / e1;
-            __stcg(a.b64 + (2 * r) * W + x, b0);
-            __stcg(a.b64 + (2 * r + 1) * W + x, b1v);
-            z[brev(x, g.logW)] = make_double2(b0, b1v);
+        double b0 = 0.0, b1v = 0.0;
+        if (t < W) {
+            const double e0 = z[t].x * sc, e1 = z[t].y * sc;
+            b0 = g.method == 0 ? e0 : 1.0 / e0;
+            b1v = g.method == 0 ? e1 : 1.0 / e1;
+            __stcg(a.b64 + (2 * r) * W + t, b0);
+            __stcg(a.b64 + (2 * r + 1) * W + t, b1v);
         }
         __syncthreads();
+        if (t < W) z[brev(t, g.logW)] = make_double2(b0, b1v);
+        __syncthreads();
         fft_r2_passes(z, g.logW, 1, W, 1, g.tw64, g.logNtw, false);
-        for (int kx = threadIdx.x; kx < Wc; kx += blockDim.x) {
-            const double2 zk = z[kx], zc = cconj(z[(W - kx) & (W - 1)]);
-            __stcg(a.Y + (2 * r) * Wc + kx, make_double2(0.5 * (zk.x + zc.x), 0.5 * (zk.y + zc.y)));
-            __stcg(a.Y + (2 * r + 1) * Wc + kx, make_double2(0.5 * (zk.y - zc.y), -0.5 * (zk.x - zc.x)));
+        if (t < Wc) {
+            const double2 zk = z[t], zc = cconj(z[(W - t) & (W - 1)]);
+            __stcg(a.Y + (2 * r) * Wc + t, make_double2(0.5 * (zk.x + zc.x), 0.5 * (zk.y + zc.y)));
+            __stcg(a.Y + (2 * r + 1) * Wc + t, make_double2(0.5 * (zk.y - zc.y), -0.5 * (zk.x - zc.x)));
         }
         __syncthreads();
     }
     if (!rt_grid_barrier(a.sync, a.extra, a.limit)) return failed();
     for (int kx = blockIdx.x; kx < Wc; kx += gridDim.x) {
         rt_col_fwd(g, a, kx, z);
-        for (int ky = threadIdx.x; ky < H; ky += blockDim.x) {
-            const double2 e = z[ky];
-            a.FE64[ky * Wc + kx] = e;
-            a.FE32[ky * Wc + kx] = make_float2((float)e.x, (float)e.y);
-            a.FEdf[ky * Wc + kx] = dfc{df_from_double(e.x), df_from_double(e.y)};
+        if (t < H) {
+            const double2 e = z[t];
+            a.FE64[t * Wc + kx] = e;
+            a.FE32[t * Wc + kx] = make_float2((float)e.x, (float)e.y);
+            a.FEdf[t * Wc + kx] = dfc{df_from_double(e.x), df_from_double(e.y)};
         }
         __syncthreads();
     }
+}
+
+// Eq. 8, the sum: CTA b adds F[I_f + off](k) e^{+2 pi i (ky' dy_f/H + kx' dx_f/W)} over its
+// frames f = b, b + gridDim.x, ... into its own partial spectrum part[b] ([H][Wc], FP64),
+// d_f the displacement of record f taken exactly. Records flagged CCST_R_TIMEOUT are left
+// out; *count gains the number of frames taken. scratch[b] holds the row transforms of the
+// frame in flight. Shared memory: max(H/2 * W, Wc * H) + H + Wc double2.
+__global__ void __launch_bounds__(512) off_accumulate(Geom g, const void* frames, long long n, long long pitch,
+                                                      double off, const Result* rec, double2* scratch,
+                                                      double2* part, unsigned* count) {
+    extern __shared__ double2 ccst_rt_smem[];
+    const int H = g.H, W = g.W, Wc = g.Wc, Hp = H / 2, HWc = H * Wc;
+    const int nbuf = Hp * W > Wc * H ? Hp * W : Wc * H;
+    double2* buf = ccst_rt_smem;
+    double2* py = buf + nbuf;
+    double2* px = py + H;
+    double2* S = scratch + (size_t)blockIdx.x * HWc;
+    double2* P = part + (size_t)blockIdx.x * HWc;
+    for (int i = threadIdx.x; i < HWc; i += blockDim.x) P[i] = make_double2(0.0, 0.0);
+    const size_t fbytes = (size_t)H * pitch * (g.in_dtype == 0 ? 2 : 4);
+    unsigned taken = 0;
+    for (long long f = blockIdx.x; f < n; f += gridDim.x) {
+        const Result q = rec[f];
+        if (q.flags & 0x20u) continue;
+        ++taken;
+        const double dy = rt_exact_d(q.dy, q.ipy, g.u), dx = rt_exact_d(q.dx, q.ipx, g.u);
+        const void* fr = (const char*)frames + (size_t)f * fbytes;
+        for (int k = threadIdx.x; k < H; k += blockDim.x) py[k] = rt_axis_phase(k, H, dy);
+        for (int k = threadIdx.x; k < Wc; k += blockDim.x) px[k] = rt_axis_phase(k, W, dx);
+        for (int i = threadIdx.x; i < Hp * W; i += blockDim.x) {
+            const int r = i / W, x = i - r * W;
+            const double v0 = (double)pixel_f32(fr, g.in_dtype, (long long)(2 * r) * pitch + x) + off;
+            const double v1 = (double)pixel_f32(fr, g.in_dtype, (long long)(2 * r + 1) * pitch + x) + off;
+            buf[r * W + brev(x, g.logW)] = make_double2(v0, v1);
+        }
+        __syncthreads();
+        fft_r2_passes(buf, g.logW, Hp, W, 1, g.tw64, g.logNtw, false);
+        for (int i = threadIdx.x; i < Hp * Wc; i += blockDim.x) {
+            const int r = i / Wc, kx = i - r * Wc;
+            const double2 zk = buf[r * W + kx], zc = cconj(buf[r * W + ((W - kx) & (W - 1))]);
+            S[(2 * r) * Wc + kx] = make_double2(0.5 * (zk.x + zc.x), 0.5 * (zk.y + zc.y));
+            S[(2 * r + 1) * Wc + kx] = make_double2(0.5 * (zk.y - zc.y), -0.5 * (zk.x - zc.x));
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < HWc; i += blockDim.x) {
+            const int ky = i / Wc, kx = i - ky * Wc;
+            buf[kx * H + brev(ky, g.logH)] = S[i];
+        }
+        __syncthreads();
+        fft_r2_passes(buf, g.logH, Wc, H, 1, g.tw64, g.logNtw, false);
+        for (int i = threadIdx.x; i < HWc; i += blockDim.x) {      // element i is this thread's in every frame
+            const int ky = i / Wc, kx = i - ky * Wc;
+            const double2 v = cmul(buf[kx * H + ky], cmul(py[ky], px[kx])), p = P[i];
+            P[i] = make_double2(p.x + v.x, p.y + v.y);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && taken) atomicAdd(count, taken);
 }
 
 // Drift removal over n records (Sec. III B). The recurrence is sequential, so one thread
@@ -443,7 +535,13 @@ struct ccst_ctx {
     double2* d_rtY = nullptr;
     unsigned* d_rtSync = nullptr;     // grid barrier of the update: arrivals, generation, error
     int rt_grid = 0;
+    // offline reference (Sec. III A): per-CTA partial sums and row scratch, [off_parts][H][Wc]
+    double2* d_offPart = nullptr;
+    double2* d_offScratch = nullptr;
+    int off_parts = 0;                // partial sums written by the last accumulation
+    int off_max_parts = 0;
     double rt_a0 = 0.0, rt_b1 = 1.0;
+    bool rt_on = false;               // ccst_rt_begin has run
     // graphs keyed by (frames, n, pitch, out), each with its own profiling event pair
     struct GraphEntry {
         cudaGraphExec_t exec = nullptr;
@@ -516,7 +614,8 @@ static void free_all(ccst_ctx* c) {
     for (int i = 0; i < 2; ++i)
         if (c->hstream[i]) cudaStreamDestroy(c->hstream[i]);
     void* ptrs[] = {c->d_ref32, c->d_b64, c->d_FE64, c->d_FE32, c->d_tw64, c->d_tw32,
-                    c->d_tab,   c->d_df,  c->d_frames, c->d_out, c->d_next, c->d_rtE, c->d_rtY, c->d_rtSync};
+                    c->d_tab,   c->d_df,  c->d_frames, c->d_out, c->d_next, c->d_rtE, c->d_rtY, c->d_rtSync,
+                    c->d_offPart, c->d_offScratch};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -1006,13 +1105,14 @@ extern "C" int ccst_debug_timeout(ccst_ctx* c, const void* frames_dev, int64_t n
 
 // ------------------------------------------------------- real-time reference (Sec. III B)
 // One reference update (rt_update) on the context's stream; rec null when starting.
-static int rt_launch(ccst_ctx* c, const void* frame, long long pitch, ccst_result* rec, unsigned extra = 0) {
+static int rt_launch(ccst_ctx* c, int mode, const void* frame, long long pitch, ccst_result* rec,
+                     unsigned extra = 0) {
     const Geom& g = c->g;
     RtArgs a;
     a.frame = frame;
     a.pitch = pitch;
     a.off = g.method == CCST_CC_SN ? (double)g.eps : 0.0;
-    a.upd = rec ? 1 : 0;
+    a.mode = mode;
     a.a0 = c->rt_a0;
     a.b1 = c->rt_b1;
     a.rec = (Result*)rec;
@@ -1025,44 +1125,67 @@ static int rt_launch(ccst_ctx* c, const void* frame, long long pitch, ccst_resul
     a.sync = c->d_rtSync;
     a.extra = extra;
     a.limit = extra ? (1u << 12) : (1u << 22);
+    a.part = c->d_offPart;
+    a.nparts = c->off_parts;
+    a.count = c->d_rtSync + 3;
     Geom gk = g;
     void* args[] = {&gk, &a};
     CK(c, cudaLaunchCooperativeKernel((const void*)rt_update, dim3(c->rt_grid), dim3(128), args, 0, c->stream));
     return CCST_OK;
 }
 
+// Filter state and grid-barrier words of the reference updates, on first use.
+static int rt_prepare(ccst_ctx* c) {
+    if (c->d_rtE) return CCST_OK;
+    const Geom& g = c->g;
+    const size_t HWc = (size_t)g.H * g.Wc;
+    int coop = 0, per_sm = 0, sms = 0;
+    CK(c, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device));
+    CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt_update, 128, 0));
+    if (!coop || per_sm < 1) return fail(c, CCST_E_UNSUPPORTED, "reference update: no cooperative launch");
+    const int want = g.Wc > g.H / 2 ? g.Wc : g.H / 2;
+    c->rt_grid = want < per_sm * sms ? want : per_sm * sms;
+    CK(c, cudaMalloc(&c->d_rtSync, 4 * sizeof(unsigned)));
+    CK(c, cudaMemsetAsync(c->d_rtSync, 0, 4 * sizeof(unsigned), c->stream));
+    CK(c, cudaMalloc(&c->d_rtY, HWc * sizeof(double2)));
+    CK(c, cudaMalloc(&c->d_rtE, HWc * sizeof(double2)));
+    return CCST_OK;
+}
+
+static int check_frame(ccst_ctx* c, const void* frame, int64_t* pitch, const char* who) {
+    if (!frame) return fail(c, CCST_E_INVALID, std::string(who) + ": null frame");
+    if (*pitch == 0) *pitch = c->g.W;
+    if (*pitch < c->g.W) return fail(c, CCST_E_INVALID, std::string(who) + ": pitch_elems < W");
+    return CCST_OK;
+}
+
+extern "C" int ccst_set_reference_frame(ccst_ctx* c, const void* frame_dev, int64_t pitch_elems) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if ((rc = check_frame(c, frame_dev, &pitch_elems, "ccst_set_reference_frame"))) return rc;
+    if ((rc = rt_prepare(c))) return rc;
+    CK(c, cudaMemsetAsync(c->d_rtSync, 0, 4 * sizeof(unsigned), c->stream));
+    return rt_launch(c, kRtStart, frame_dev, pitch_elems, nullptr);
+}
+
 extern "C" int ccst_rt_begin(ccst_ctx* c, const void* frame0_dev, int64_t pitch_elems, double a0, double b1) {
     int rc = check_ctx(c);
     if (rc) return rc;
-    if (!frame0_dev) return fail(c, CCST_E_INVALID, "ccst_rt_begin: null frame");
-    if (pitch_elems == 0) pitch_elems = c->g.W;
-    if (pitch_elems < c->g.W) return fail(c, CCST_E_INVALID, "ccst_rt_begin: pitch_elems < W");
     if (!std::isfinite(a0) || !std::isfinite(b1)) return fail(c, CCST_E_INVALID, "ccst_rt_begin: a0, b1 not finite");
-    const Geom& g = c->g;
-    const size_t HWc = (size_t)g.H * g.Wc;
-    if (!c->d_rtE) {
-        int coop = 0, per_sm = 0, sms = 0;
-        CK(c, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device));
-        CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-        CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rt_update, 128, 0));
-        const int want = g.Wc > g.H / 2 ? g.Wc : g.H / 2;
-        if (!coop || per_sm < 1) return fail(c, CCST_E_UNSUPPORTED, "ccst_rt_begin: no cooperative launch");
-        c->rt_grid = want < per_sm * sms ? want : per_sm * sms;
-        CK(c, cudaMalloc(&c->d_rtSync, 4 * sizeof(unsigned)));
-        CK(c, cudaMalloc(&c->d_rtE, HWc * sizeof(double2)));
-        CK(c, cudaMalloc(&c->d_rtY, HWc * sizeof(double2)));
-    }
+    if ((rc = check_frame(c, frame0_dev, &pitch_elems, "ccst_rt_begin"))) return rc;
+    if ((rc = ccst_set_reference_frame(c, frame0_dev, pitch_elems))) return rc;
     c->rt_a0 = a0;
     c->rt_b1 = b1;
-    CK(c, cudaMemsetAsync(c->d_rtSync, 0, 4 * sizeof(unsigned), c->stream));
-    return rt_launch(c, frame0_dev, pitch_elems, nullptr);
+    c->rt_on = true;
+    return CCST_OK;
 }
 
 extern "C" int ccst_rt_track(ccst_ctx* c, const void* frames_dev, int64_t n, int64_t pitch_elems,
                              ccst_result* out_dev) {
     int rc = check_ctx(c);
     if (rc) return rc;
-    if (!c->d_rtE) return fail(c, CCST_E_INVALID, "ccst_rt_track: no real-time reference (ccst_rt_begin)");
+    if (!c->rt_on) return fail(c, CCST_E_INVALID, "ccst_rt_track: no real-time reference (ccst_rt_begin)");
     if (n < 0) return fail(c, CCST_E_INVALID, "ccst_rt_track: n < 0");
     if (n == 0) return CCST_OK;
     if (!frames_dev || !out_dev) return fail(c, CCST_E_INVALID, "ccst_rt_track: null frames or out");
@@ -1075,8 +1198,95 @@ extern "C" int ccst_rt_track(ccst_ctx* c, const void* frames_dev, int64_t n, int
         Batch b;
         if ((rc = make_batch(c, frame, 1, pitch_elems, out_dev + i, &b))) return rc;
         if ((rc = launch(c, b))) return rc;                  // frame i against E_{i-1}
-        if ((rc = rt_launch(c, frame, pitch_elems, out_dev + i))) return rc;   // E_i
+        if ((rc = rt_launch(c, kRtUpdate, frame, pitch_elems, out_dev + i))) return rc;   // E_i
     }
+    return CCST_OK;
+}
+
+// ---------------------------------------------------------- offline reference (Sec. III A)
+static size_t off_smem_bytes(const Geom& g) {
+    const int nbuf = (g.H / 2) * g.W > g.Wc * g.H ? (g.H / 2) * g.W : g.Wc * g.H;
+    return (size_t)(nbuf + g.H + g.Wc) * sizeof(double2);
+}
+
+static int off_prepare(ccst_ctx* c) {
+    if (c->d_offPart) return CCST_OK;
+    const Geom& g = c->g;
+    const size_t smem = off_smem_bytes(g);
+    CK(c, cudaFuncSetAttribute(off_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0, sms = 0;
+    CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, off_accumulate, 512, smem));
+    if (per_sm < 1) return fail(c, CCST_E_SHAPE, "ccst_offline_update: the frame transform does not fit on an SM");
+    c->off_max_parts = per_sm * sms;
+    const size_t bytes = (size_t)c->off_max_parts * g.H * g.Wc * sizeof(double2);
+    CK(c, cudaMalloc(&c->d_offPart, bytes));
+    CK(c, cudaMalloc(&c->d_offScratch, bytes));
+    return CCST_OK;
+}
+
+extern "C" int ccst_offline_update(ccst_ctx* c, const void* frames_dev, int64_t n, int64_t pitch_elems,
+                                   const ccst_result* rec_dev) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (n < 0) return fail(c, CCST_E_INVALID, "ccst_offline_update: n < 0");
+    if (n == 0) return CCST_OK;
+    if (!rec_dev) return fail(c, CCST_E_INVALID, "ccst_offline_update: null records");
+    if ((rc = check_frame(c, frames_dev, &pitch_elems, "ccst_offline_update"))) return rc;
+    if ((rc = rt_prepare(c)) || (rc = off_prepare(c))) return rc;
+    const Geom& g = c->g;
+    const int grid = (int)(n < c->off_max_parts ? n : c->off_max_parts);
+    c->off_parts = grid;
+    const double off = g.method == CCST_CC_SN ? (double)g.eps : 0.0;
+    CK(c, cudaMemsetAsync(c->d_rtSync + 3, 0, sizeof(unsigned), c->stream));
+    off_accumulate<<<grid, 512, off_smem_bytes(g), c->stream>>>(g, frames_dev, (long long)n, (long long)pitch_elems,
+                                                                 off, (const Result*)rec_dev, c->d_offScratch,
+                                                                 c->d_offPart, c->d_rtSync + 3);
+    CK(c, cudaGetLastError());
+    return rt_launch(c, kRtMean, nullptr, 0, nullptr);
+}
+
+extern "C" int ccst_offline_track(ccst_ctx* c, const void* frames_dev, int64_t n, int64_t pitch_elems, int passes,
+                                  ccst_result* out_dev) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (n < 1 || passes < 0) return fail(c, CCST_E_INVALID, "ccst_offline_track: n < 1 or passes < 0");
+    if (!out_dev) return fail(c, CCST_E_INVALID, "ccst_offline_track: null out");
+    if ((rc = check_frame(c, frames_dev, &pitch_elems, "ccst_offline_track"))) return rc;
+    if ((rc = ccst_set_reference_frame(c, frames_dev, pitch_elems))) return rc;          // E_0 = I_0
+    const size_t fbytes = (size_t)c->g.H * pitch_elems * (c->p.in_dtype == CCST_U16 ? 2 : 4);
+    for (int p = 0; p <= passes; ++p) {
+        for (int64_t s = 0; s < n; s += c->p.max_batch) {                           // every frame against E_p
+            const int64_t m = n - s < c->p.max_batch ? n - s : c->p.max_batch;
+            Batch b;
+            if ((rc = make_batch(c, (const char*)frames_dev + (size_t)s * fbytes, m, pitch_elems, out_dev + s, &b)))
+                return rc;
+            if ((rc = launch(c, b))) return rc;
+        }
+        if (p < passes && (rc = ccst_offline_update(c, frames_dev, n, pitch_elems, out_dev))) return rc;   // E_{p+1}
+    }
+    return CCST_OK;
+}
+
+extern "C" int ccst_reference_status(ccst_ctx* c, int* stale) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!stale) return fail(c, CCST_E_INVALID, "ccst_reference_status: null stale");
+    *stale = 0;
+    if (!c->d_rtSync) return CCST_OK;
+    unsigned err = 0;
+    CK(c, cudaStreamSynchronize(c->stream));
+    CK(c, cudaMemcpy(&err, c->d_rtSync + 2, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    *stale = err != 0;
+    return CCST_OK;
+}
+
+extern "C" int ccst_debug_reference(ccst_ctx* c, double* ref_dev) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!ref_dev) return fail(c, CCST_E_INVALID, "ccst_debug_reference: null buffer");
+    CK(c, cudaMemcpyAsync(ref_dev, c->d_b64, (size_t)c->g.H * c->g.W * sizeof(double), cudaMemcpyDeviceToDevice,
+                          c->stream));
     return CCST_OK;
 }
 
@@ -1084,11 +1294,11 @@ extern "C" int ccst_debug_rt_timeout(ccst_ctx* c, const void* frame_dev, int64_t
                                      ccst_result* rec_dev) {
     int rc = check_ctx(c);
     if (rc) return rc;
-    if (!c->d_rtE) return fail(c, CCST_E_INVALID, "ccst_debug_rt_timeout: no real-time reference (ccst_rt_begin)");
+    if (!c->rt_on) return fail(c, CCST_E_INVALID, "ccst_debug_rt_timeout: no real-time reference (ccst_rt_begin)");
     if (!frame_dev || !rec_dev) return fail(c, CCST_E_INVALID, "ccst_debug_rt_timeout: null frame or record");
     if (pitch_elems == 0) pitch_elems = c->g.W;
     if (pitch_elems < c->g.W) return fail(c, CCST_E_INVALID, "ccst_debug_rt_timeout: pitch_elems < W");
-    return rt_launch(c, frame_dev, pitch_elems, rec_dev, 1);
+    return rt_launch(c, kRtUpdate, frame_dev, pitch_elems, rec_dev, 1);
 }
 
 extern "C" int ccst_drift_correct(const ccst_result* rec_dev, int64_t n, double a0, double b1, double alpha,
