@@ -266,6 +266,75 @@ def realtime_cpu_baseline(frames, res):
             {"frames": len(orc), "mismatches": mism, "tolerance_px": 1e-3})
 
 
+OFF_PASSES = 5                   # offline leg: reference updates (the paper's fifth reference)
+OFF_ORACLE_FRAMES = 32
+FP64_PEAK_TFLOPS = 1.25          # nominal B300 FP64 rate (no measured figure on this machine)
+
+
+def off_flop_per_frame(h=H, w=W):
+    """FP64 flop of one frame's share of the Eq. (8) sum: a real 2-D FFT (2.5 HW log2 HW)
+    plus the phase product and the accumulation over the half spectrum (8 per bin)."""
+    return 2.5 * h * w * math.log2(h * w) + 8 * h * (w // 2 + 1)
+
+
+def offline_leg(C, torch, s, frames_dev, n, stream):
+    """Offline method (Sec. III A) over the whole stream: reference from frame 0, then
+    OFF_PASSES rounds of track-all + Eq. (8) update, and a last track-all."""
+    t = C.Tracker(s.ref, upsample=U, method="ccu", in_dtype="u16", max_batch=BATCH, stream=stream)
+    out = t.empty_results(n)
+    ev = lambda: torch.cuda.Event(enable_timing=True)          # noqa: E731
+    with torch.cuda.stream(stream):
+        C.ccst_offline_track(t.ctx, frames_dev, min(n, 1024), 0, 1, out[:min(n, 1024)])     # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        C.ccst_offline_track(t.ctx, frames_dev, n, 0, OFF_PASSES, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms = e0.elapsed_time(e1)
+        reps = 3
+        u0, u1 = ev(), ev()
+        u0.record(stream)
+        for _ in range(reps):
+            C.ccst_offline_update(t.ctx, frames_dev, n, 0, out)
+        u1.record(stream)
+        torch.cuda.synchronize()
+        upd_ms = u0.elapsed_time(u1) / reps
+    stale = C.ccst_reference_status(t.ctx)
+    t.close()
+    achieved = off_flop_per_frame() * n / (upd_ms / 1e3) / 1e12
+    return {"workload": f"all {n} frames of the stream, u={U}, CC-U, reference from frame 0, {OFF_PASSES} Eq. (8) "
+                        f"passes, {OFF_PASSES + 1} track-all passes",
+            "value": n * (OFF_PASSES + 1) / (total_ms / 1e3), "unit": "frame-trackings/s",
+            "ms_total": total_ms, "ms_per_pass": total_ms / (OFF_PASSES + 1), "update_ms": upd_ms,
+            "update_share": OFF_PASSES * upd_ms / total_ms, "stale": stale,
+            "roofline_update": {"bound": "fp64", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                "frac": achieved / FP64_PEAK_TFLOPS, "kernel": "off_accumulate + rt_update",
+                                "flop_per_frame": off_flop_per_frame(),
+                                "peak_basis": "nominal B300 FP64 1.25 TFLOP/s (not measured)"}}
+
+
+def offline_cpu_baseline(C, torch, s, stream):
+    """The FP64 offline oracle, as it stands, on the first OFF_ORACLE_FRAMES frames with two
+    passes: its rate, and parity of the GPU's last-pass records on the same sample."""
+    from oracle import offline_oracle
+    fr = s.frames[:OFF_ORACLE_FRAMES]
+    t0 = time.perf_counter()
+    ores, _ = offline_oracle.offline_track(fr.astype(np.float64), u=U, passes=2)
+    dt = time.perf_counter() - t0
+    t = C.Tracker(s.ref, upsample=U, method="ccu", in_dtype="u16", max_batch=BATCH, stream=stream)
+    with torch.cuda.stream(stream):
+        got = t.offline_track(torch.from_numpy(fr.view(np.int16)).cuda().view(torch.uint16), passes=2)
+    t.close()
+    mism = sum(1 for a, o in zip(got, ores[2])
+               if (int(a["ipy"]), int(a["ipx"])) != (o["ipy"], o["ipx"])
+               or abs(float(a["dx"]) - o["dx32"]) > 1e-3 or abs(float(a["dy"]) - o["dy32"]) > 1e-3)
+    return ({"value": 3 * len(fr) / dt, "unit": "frame-trackings/s", "cores": 1, "kind": "oracle",
+             "sample": f"first {len(fr)} frames, 2 Eq. (8) passes (3 track-all passes), FP64 numpy offline "
+                       "oracle, one process"},
+            {"frames": len(fr), "passes": 2, "mismatches": mism, "tolerance_px": 1e-3})
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -398,7 +467,11 @@ def run_ours(args):
     if rank == 0 and not args.no_realtime:
         rt_line, rt_res = realtime_leg(C, torch, s, stream)
         line["realtime"] = rt_line
+    if rank == 0 and not args.no_offline:
+        line["offline"] = offline_leg(C, torch, s, frames_dev, n_frames, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        if "offline" in line:
+            line["offline"]["cpu_baseline"], line["offline"]["parity"] = offline_cpu_baseline(C, torch, s, stream)
         if rt_res is not None:
             rt_line["cpu_baseline"], rt_line["parity"] = realtime_cpu_baseline(s.frames, rt_res)
         orc, cb = cpu_baseline(s.frames, s.ref)
@@ -490,6 +563,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-realtime", action="store_true")
+    ap.add_argument("--no-offline", action="store_true")
     ap.add_argument("--frames", type=int, default=N_FRAMES,
                     help="frames of the stream to stage (the workload is 10000; smaller only for profiler captures)")
     args = ap.parse_args()
