@@ -248,7 +248,7 @@ def realtime_leg(C, torch, s, stream, rt_frames=RT_FRAMES):
             "value": (n - 1) / (thr_ms / 1e3), "unit": "frames/s", "frames": n - 1,
             "p50_us": float(np.percentile(lat_us, 50)), "p99_us": float(np.percentile(lat_us, 99)),
             "same_records_per_frame_calls": bool(again.tobytes() == res[:k].tobytes()),
-            "gpu_launches_per_frame": 2, "memsets_per_frame": 1}, res
+            "gpu_launches_per_frame": 2, "memsets_per_call": 1}, res
 
 
 def realtime_cpu_baseline(frames, res):

@@ -232,62 +232,67 @@ struct RtArgs {
     float2* FE32;
     dfc* FEdf;
     unsigned* sync;             // [0] arrivals, [1] generation, [2] sticky error
+    unsigned base;              // 3 G s: arrivals before this launch (s launches since the reset)
     unsigned extra;             // arrivals the barriers wait for beyond the grid (0; tests: 1)
     unsigned limit;             // polls before a barrier gives up
     const double2* part;        // kRtMean: nparts partial sums [nparts][H][Wc] ...
     int nparts;
     const unsigned* count;      // ... over *count frames
+    unsigned* next;             // frame counter of the tracking kernel, zeroed here (or null)
 };
 
 constexpr int kRtStart = 0, kRtUpdate = 1, kRtMean = 2;
 
 constexpr unsigned kRtStale = 0x40u;     // the reference update after this frame did not run
 
-// Grid barrier with a bounded wait. Returns false (and sets the sticky error) when the
-// other CTAs do not arrive within the limit; the CTA must then leave the kernel.
-__device__ bool rt_grid_barrier(unsigned* sync, unsigned extra, unsigned limit) {
+// Grid barrier with a bounded wait: a count-up barrier on sync[0]. Barrier k (1, 2, 3) of
+// the launch numbered s since the counter was zeroed completes when the counter reaches
+// 3 s G + k G (+ extra), G = gridDim.x: each CTA adds one arrival with release semantics
+// and polls with acquire loads. Returns false (and sets the sticky error sync[2]) when the
+// others do not arrive within the limit; the CTA must then leave the kernel.
+__device__ bool rt_grid_barrier(unsigned* sync, unsigned target, unsigned limit) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned* gen = sync + 1;
-        const unsigned g0 = *gen;
-        __threadfence();
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(sync) : "memory");
         bool good = true;
-        if (atomicAdd(sync, 1u) == gridDim.x - 1 + extra) {
-            atomicExch(sync, 0u);
-            __threadfence();
-            atomicAdd(sync + 1, 1u);
-        } else {
-            unsigned it = 0;
-            while (*gen == g0) {
-                if (++it > limit) { good = false; atomicOr(sync + 2, 1u); break; }
-                __nanosleep(64);
-            }
+        unsigned v, it = 0;
+        for (;;) {
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(sync) : "memory");
+            if ((int)(v - target) >= 0) break;
+            if (++it > limit) { good = false; atomicOr(sync + 2, 1u); break; }
         }
-        __threadfence();
         ok = good;
     }
     __syncthreads();
     return ok != 0;
 }
 
-// e^{+2 pi i k' d / N} on one axis, the Nyquist bin of an even N taking cos(pi d)
-__device__ inline double2 rt_axis_phase(int k, int N, double d) {
-    double s, co;
-    if (2 * k == N) return make_double2(cospi(d), 0.0);
-    const int ks = k < (N >> 1) ? k : k - N;
-    sincospi(2.0 * ks * d / N, &s, &co);
-    return make_double2(co, s);
+// A launch that leaves before its barriers still counts its three arrivals.
+__device__ inline void rt_skip_barriers(unsigned* sync) {
+    if (threadIdx.x == 0) atomicAdd(sync, 3u);
 }
 
-// the displacement the record carries, exactly: d = (p u + t) / u in FP64
-__device__ inline double rt_exact_d(float dx, int px, int u) {
-    const double t = rint((double)dx * u - (double)px * u);
-    return ((double)px * u + t) / u;
+// The displacement a record carries is d = (p u + t) / u exactly; this is p u + t.
+__device__ inline long long rt_grid_index(float d, int p, int u) {
+    return (long long)p * u + llrint((double)d * u - (double)p * u);
+}
+
+// e^{+2 pi i k' d / N} on one axis of length N, d = q / u (q = p u + t), from the context's
+// two-level table of e^{2 pi i n / D}, D = u N, with n = k' q mod D reduced exactly in
+// integers. The Nyquist bin of an even N takes the real part, cos(pi d).
+__device__ inline double2 rt_axis_phase(int k, int N, long long q, long long D, const dfc* coarse, const dfc* fine,
+                                        int B) {
+    const bool nyq = 2 * k == N;
+    const long long ks = (nyq || k < (N >> 1)) ? k : k - N;
+    long long n = (ks * q) % D;
+    if (n < 0) n += D;
+    const dfc e = df_twiddle(coarse, fine, B, n);
+    return make_double2(df_to_double(e.re), nyq ? 0.0 : df_to_double(e.im));
 }
 
 // forward transform of the frame's real row pair (2r, 2r+1) into Y
-__device__ void rt_row_pair_fwd(const Geom& g, const RtArgs& a, int r, double2* z) {
+__device__ void rt_row_pair_fwd(const Geom& g, const RtArgs& a, int r, double2* z, const double2* tw) {
     const int W = g.W, Wc = g.Wc;
     for (int x = threadIdx.x; x < W; x += blockDim.x) {
         const double v0 = (double)pixel_f32(a.frame, g.in_dtype, (long long)(2 * r) * a.pitch + x) + a.off;
@@ -295,7 +300,7 @@ __device__ void rt_row_pair_fwd(const Geom& g, const RtArgs& a, int r, double2* 
         z[brev(x, g.logW)] = make_double2(v0, v1);
     }
     __syncthreads();
-    fft_r2_passes(z, g.logW, 1, W, 1, g.tw64, g.logNtw, false);
+    fft_r2_passes(z, g.logW, 1, W, 1, tw, g.logNtw, false);
     for (int kx = threadIdx.x; kx < Wc; kx += blockDim.x) {
         const double2 zk = z[kx], zc = cconj(z[(W - kx) & (W - 1)]);
         __stcg(a.Y + (2 * r) * Wc + kx, make_double2(0.5 * (zk.x + zc.x), 0.5 * (zk.y + zc.y)));
@@ -305,34 +310,40 @@ __device__ void rt_row_pair_fwd(const Geom& g, const RtArgs& a, int r, double2* 
 }
 
 // column kx of Y, transformed over y (in natural order in z)
-__device__ void rt_col_fwd(const Geom& g, const RtArgs& a, int kx, double2* z) {
+__device__ void rt_col_fwd(const Geom& g, const RtArgs& a, int kx, double2* z, const double2* tw) {
     for (int ky = threadIdx.x; ky < g.H; ky += blockDim.x) z[brev(ky, g.logH)] = __ldcg(a.Y + ky * g.Wc + kx);
     __syncthreads();
-    fft_r2_passes(z, g.logH, 1, g.H, 1, g.tw64, g.logNtw, false);
+    fft_r2_passes(z, g.logH, 1, g.H, 1, tw, g.logNtw, false);
 }
 
 __global__ void __launch_bounds__(128) rt_update(Geom g, RtArgs a) {
     __shared__ double2 z[128];
+    __shared__ double2 tw[64];                             // FFT twiddles, Ntw/2 <= 64
     const int H = g.H, W = g.W, Wc = g.Wc, Hp = H / 2, HWc = H * Wc;
     const bool upd = a.mode == kRtUpdate;
+    if (a.next && blockIdx.x == 0 && threadIdx.x == 0) *a.next = 0;   // frame counter of the next tracking launch
     if (__ldcg(a.sync + 2) != 0) {                         // an earlier update failed: E is stale
         if (upd && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.rec->flags, kRtStale);
-        return;
+        return rt_skip_barriers(a.sync);
     }
-    double dy = 0.0, dx = 0.0;
+    long long qy = 0, qx = 0;
     if (upd) {
         const Result q = *a.rec;
-        if (q.flags & 0x20u) return;                       // no displacement: E stays
-        dy = rt_exact_d(q.dy, q.ipy, g.u);
-        dx = rt_exact_d(q.dx, q.ipx, g.u);
+        if (q.flags & 0x20u) return rt_skip_barriers(a.sync);   // no displacement: E stays
+        qy = rt_grid_index(q.dy, q.ipy, g.u);
+        qx = rt_grid_index(q.dx, q.ipx, g.u);
     }
+    const long long Dy = (long long)g.u * H, Dx = (long long)g.u * W;
+    for (int k = threadIdx.x; k < g.Ntw / 2; k += blockDim.x) tw[k] = g.tw64[k];
+    __syncthreads();
+    const unsigned G = gridDim.x, b1t = a.base + G + a.extra, b2t = b1t + G, b3t = b2t + G;
     auto failed = [&]() {
         if (upd && threadIdx.x == 0) atomicOr(&a.rec->flags, kRtStale);
     };
     if (a.mode == kRtMean) {
         // E = (1/N) sum of the partial spectra, in a fixed order; no frames: E stays
         const unsigned cnt = __ldcg(a.count);
-        if (cnt == 0) return;
+        if (cnt == 0) return rt_skip_barriers(a.sync);
         const double inv = 1.0 / (double)cnt;
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < HWc; i += gridDim.x * blockDim.x) {
             double2 s = make_double2(0.0, 0.0);
@@ -344,20 +355,21 @@ __global__ void __launch_bounds__(128) rt_update(Geom g, RtArgs a) {
             __stcg(a.E + i, make_double2(s.x * inv, s.y * inv));
         }
     } else {
-        for (int r = blockIdx.x; r < Hp; r += gridDim.x) rt_row_pair_fwd(g, a, r, z);
+        for (int r = blockIdx.x; r < Hp; r += gridDim.x) rt_row_pair_fwd(g, a, r, z, tw);
     }
-    if (!rt_grid_barrier(a.sync, a.extra, a.limit)) return failed();
+    if (!rt_grid_barrier(a.sync, b1t, a.limit)) return failed();
     const int t = threadIdx.x;
     for (int kx = blockIdx.x; kx < Wc; kx += gridDim.x) {
         double2 e = make_double2(0.0, 0.0);
         if (a.mode == kRtMean) {
             if (t < H) e = __ldcg(a.E + t * Wc + kx);
         } else {
-            rt_col_fwd(g, a, kx, z);
+            rt_col_fwd(g, a, kx, z, tw);
             if (t < H) {
                 e = z[t];
                 if (upd) {
-                    const double2 s = cmul(e, cmul(rt_axis_phase(t, H, dy), rt_axis_phase(kx, W, dx)));
+                    const double2 s = cmul(e, cmul(rt_axis_phase(t, H, qy, Dy, g.eyc, g.eyf, g.By),
+                                                   rt_axis_phase(kx, W, qx, Dx, g.exc, g.exf, g.Bx)));
                     const double2 p = __ldcg(a.E + t * Wc + kx);
                     e = make_double2(a.a0 * s.x + a.b1 * p.x, a.a0 * s.y + a.b1 * p.y);
                 }
@@ -367,11 +379,11 @@ __global__ void __launch_bounds__(128) rt_update(Geom g, RtArgs a) {
         __syncthreads();
         if (t < H) z[brev(t, g.logH)] = e;
         __syncthreads();
-        fft_r2_passes(z, g.logH, 1, H, 1, g.tw64, g.logNtw, true);
+        fft_r2_passes(z, g.logH, 1, H, 1, tw, g.logNtw, true);
         if (t < H) __stcg(a.Y + t * Wc + kx, z[t]);
         __syncthreads();
     }
-    if (!rt_grid_barrier(a.sync, a.extra, a.limit)) return failed();
+    if (!rt_grid_barrier(a.sync, b2t, a.limit)) return failed();
     const double sc = 1.0 / ((double)H * W);
     for (int r = blockIdx.x; r < Hp; r += gridDim.x) {
         // Y rows 2r, 2r+1 are Hermitian in kx: one complex inverse gives both real rows
@@ -387,7 +399,7 @@ __global__ void __launch_bounds__(128) rt_update(Geom g, RtArgs a) {
             z[brev(t, g.logW)] = make_double2(ye.x - yo.y, ye.y + yo.x);   // ye + i yo
         }
         __syncthreads();
-        fft_r2_passes(z, g.logW, 1, W, 1, g.tw64, g.logNtw, true);
+        fft_r2_passes(z, g.logW, 1, W, 1, tw, g.logNtw, true);
         double b0 = 0.0, b1v = 0.0;
         if (t < W) {
             const double e0 = z[t].x * sc, e1 = z[t].y * sc;
@@ -399,7 +411,7 @@ __global__ void __launch_bounds__(128) rt_update(Geom g, RtArgs a) {
         __syncthreads();
         if (t < W) z[brev(t, g.logW)] = make_double2(b0, b1v);
         __syncthreads();
-        fft_r2_passes(z, g.logW, 1, W, 1, g.tw64, g.logNtw, false);
+        fft_r2_passes(z, g.logW, 1, W, 1, tw, g.logNtw, false);
         if (t < Wc) {
             const double2 zk = z[t], zc = cconj(z[(W - t) & (W - 1)]);
             __stcg(a.Y + (2 * r) * Wc + t, make_double2(0.5 * (zk.x + zc.x), 0.5 * (zk.y + zc.y)));
@@ -407,9 +419,9 @@ __global__ void __launch_bounds__(128) rt_update(Geom g, RtArgs a) {
         }
         __syncthreads();
     }
-    if (!rt_grid_barrier(a.sync, a.extra, a.limit)) return failed();
+    if (!rt_grid_barrier(a.sync, b3t, a.limit)) return failed();
     for (int kx = blockIdx.x; kx < Wc; kx += gridDim.x) {
-        rt_col_fwd(g, a, kx, z);
+        rt_col_fwd(g, a, kx, z, tw);
         if (t < H) {
             const double2 e = z[t];
             a.FE64[t * Wc + kx] = e;
@@ -443,10 +455,12 @@ __global__ void __launch_bounds__(512) off_accumulate(Geom g, const void* frames
         const Result q = rec[f];
         if (q.flags & 0x20u) continue;
         ++taken;
-        const double dy = rt_exact_d(q.dy, q.ipy, g.u), dx = rt_exact_d(q.dx, q.ipx, g.u);
+        const long long qy = rt_grid_index(q.dy, q.ipy, g.u), qx = rt_grid_index(q.dx, q.ipx, g.u);
         const void* fr = (const char*)frames + (size_t)f * fbytes;
-        for (int k = threadIdx.x; k < H; k += blockDim.x) py[k] = rt_axis_phase(k, H, dy);
-        for (int k = threadIdx.x; k < Wc; k += blockDim.x) px[k] = rt_axis_phase(k, W, dx);
+        for (int k = threadIdx.x; k < H; k += blockDim.x)
+            py[k] = rt_axis_phase(k, H, qy, (long long)g.u * H, g.eyc, g.eyf, g.By);
+        for (int k = threadIdx.x; k < Wc; k += blockDim.x)
+            px[k] = rt_axis_phase(k, W, qx, (long long)g.u * W, g.exc, g.exf, g.Bx);
         for (int i = threadIdx.x; i < Hp * W; i += blockDim.x) {
             const int r = i / W, x = i - r * W;
             const double v0 = (double)pixel_f32(fr, g.in_dtype, (long long)(2 * r) * pitch + x) + off;
@@ -535,6 +549,7 @@ struct ccst_ctx {
     double2* d_rtY = nullptr;
     unsigned* d_rtSync = nullptr;     // grid barrier of the update: arrivals, generation, error
     int rt_grid = 0;
+    unsigned rt_seq = 0;              // update launches since the barrier counter was zeroed
     // offline reference (Sec. III A): per-CTA partial sums and row scratch, [off_parts][H][Wc]
     double2* d_offPart = nullptr;
     double2* d_offScratch = nullptr;
@@ -765,7 +780,7 @@ extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pi
     return CCST_OK;
 }
 
-static int launch(ccst_ctx* c, const Batch& b) {
+static int launch(ccst_ctx* c, const Batch& b, bool reset_counter = true) {
     if (b.n == 0) return CCST_OK;
     const int grid = (int)(b.n < c->grid_main ? b.n : c->grid_main);
     const bool prof = (c->p.flags & CCST_FLAG_PROFILE) != 0;
@@ -786,7 +801,7 @@ static int launch(ccst_ctx* c, const Batch& b) {
         Geom gk = c->g;
         Batch bk = b;
         bk.next = c->d_next;
-        CK(c, cudaMemsetAsync(c->d_next, 0, sizeof(unsigned), c->stream));
+        if (reset_counter) CK(c, cudaMemsetAsync(c->d_next, 0, sizeof(unsigned), c->stream));
         void* args[] = {&gk, &bk};
         CK(c, cudaLaunchKernel(c->kernel, dim3(grid), dim3(kThreads), args, c->smem, c->stream));
     }
@@ -1124,10 +1139,12 @@ static int rt_launch(ccst_ctx* c, int mode, const void* frame, long long pitch, 
     a.FEdf = const_cast<dfc*>(g.FEdf);
     a.sync = c->d_rtSync;
     a.extra = extra;
+    a.base = 3u * (unsigned)c->rt_grid * c->rt_seq++;
     a.limit = extra ? (1u << 12) : (1u << 22);
     a.part = c->d_offPart;
     a.nparts = c->off_parts;
     a.count = c->d_rtSync + 3;
+    a.next = c->d_next;
     Geom gk = g;
     void* args[] = {&gk, &a};
     CK(c, cudaLaunchCooperativeKernel((const void*)rt_update, dim3(c->rt_grid), dim3(128), args, 0, c->stream));
@@ -1148,6 +1165,7 @@ static int rt_prepare(ccst_ctx* c) {
     c->rt_grid = want < per_sm * sms ? want : per_sm * sms;
     CK(c, cudaMalloc(&c->d_rtSync, 4 * sizeof(unsigned)));
     CK(c, cudaMemsetAsync(c->d_rtSync, 0, 4 * sizeof(unsigned), c->stream));
+    c->rt_seq = 0;
     CK(c, cudaMalloc(&c->d_rtY, HWc * sizeof(double2)));
     CK(c, cudaMalloc(&c->d_rtE, HWc * sizeof(double2)));
     return CCST_OK;
@@ -1166,6 +1184,7 @@ extern "C" int ccst_set_reference_frame(ccst_ctx* c, const void* frame_dev, int6
     if ((rc = check_frame(c, frame_dev, &pitch_elems, "ccst_set_reference_frame"))) return rc;
     if ((rc = rt_prepare(c))) return rc;
     CK(c, cudaMemsetAsync(c->d_rtSync, 0, 4 * sizeof(unsigned), c->stream));
+    c->rt_seq = 0;
     return rt_launch(c, kRtStart, frame_dev, pitch_elems, nullptr);
 }
 
@@ -1197,7 +1216,8 @@ extern "C" int ccst_rt_track(ccst_ctx* c, const void* frames_dev, int64_t n, int
         const void* frame = (const char*)frames_dev + (size_t)i * fbytes;
         Batch b;
         if ((rc = make_batch(c, frame, 1, pitch_elems, out_dev + i, &b))) return rc;
-        if ((rc = launch(c, b))) return rc;                  // frame i against E_{i-1}
+        if ((rc = launch(c, b, i == 0))) return rc;          // frame i against E_{i-1}; the update zeroes
+                                                             // the frame counter for the next one
         if ((rc = rt_launch(c, kRtUpdate, frame, pitch_elems, out_dev + i))) return rc;   // E_i
     }
     return CCST_OK;
