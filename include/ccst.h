@@ -272,10 +272,45 @@ int ccst_reference_status(ccst_ctx* ctx, int* stale);
 int ccst_drift_correct(const ccst_result* rec_dev, int64_t n, double a0, double b1, double alpha, int u,
                        double* out_dev, void* stream);
 
-/* Vector-Jacobian product of the displacement with respect to the frame pixels
- * and the reference. Not implemented in this build: returns CCST_E_UNSUPPORTED. */
-int ccst_backward(ccst_ctx* ctx, const void* frames_dev, int64_t n, const float* g_dxdy_dev,
-                  float* g_frames_dev, float* g_ref_dev);
+/* Continuous peak: the stationary point s* of the band-limited interpolant of the
+ * correlation surface (Sec. III; Eqs. (4), (7)),
+ *   f(s) = (1/HW) Re sum_k X(k) e^{2 pi i (ky' sy / H + kx' sx / W)},
+ * over all H x W frequencies (fftfreq-signed), X the product spectrum of the method,
+ * found by Newton's method in FP64 from the grid peak of each record: the u -> infinity
+ * limit of the tracker's estimate, and the quantity ccst_backward differentiates. The
+ * paper's estimate itself is the grid point; this is an addition to it.
+ *   frames_dev   device memory, n frames of H rows pitch_elems apart (0 means W).
+ *   rec_dev      device memory, the n records ccst_track gave for these frames against
+ *                the context's current reference.
+ *   peak_dev     device memory, n x 2 doubles (dx, dy) of s*, or NULL.
+ *   status_dev   device memory, n words, or NULL: 0, or a sum of 1 (Newton did not
+ *                settle in 50 steps), 2 (s* is not a maximum for CC-U / minimum for
+ *                CC-SN), 4 (s* is more than 1 px from the grid peak).
+ * One CTA per frame (up to one per SM, frames strided), FP64 throughout. The first call
+ * allocates the workspace of ccst_offline_update plus H x (W/2+1) complex doubles.
+ * Stream-ordered and asynchronous.
+ * Errors: CCST_E_INVALID (n < 0, null pointers, no output, pitch < W), CCST_E_NOMEM,
+ * CCST_E_CUDA. */
+int ccst_peak_continuous(ccst_ctx* ctx, const void* frames_dev, int64_t n, int64_t pitch_elems,
+                         const ccst_result* rec_dev, double* peak_dev, int32_t* status_dev);
+
+/* Vector-Jacobian product of the continuous peak (ccst_peak_continuous) with respect to
+ * the frame pixels and the reference. From grad f(s*) = 0: with the Hessian Hf of f at
+ * s* and the upstream gradient g = dL/ds*, w = -Hf^{-1} g and
+ *   dL/da(r) = (1/HW) Re sum_k (2 pi i w.k'/N) conj F[b](k) e^{2 pi i k.(s* - r)/N},
+ *   dL/db(r) = (1/HW) Re sum_k (2 pi i w.k'/N) F[a](k) e^{2 pi i k.(s* + r)/N},
+ * for the surface operands (a, b) = (I, E) (CC-U) or ((I + eps)^2, 1/(E + eps)) (CC-SN),
+ * then the chain rule to I and E.
+ *   frames_dev, rec_dev   as for ccst_peak_continuous.
+ *   g_dxdy_dev    device memory, n x 2 floats (dL/ddx, dL/ddy).
+ *   g_frames_dev  device memory, n x H x W floats dL/dI (row-major, pitch W), or NULL.
+ *   g_ref_dev     device memory, H x W floats dL/dE summed over the n frames, or NULL.
+ * A frame whose status would be non-zero contributes zero gradient. The sum over frames
+ * runs in per-CTA partials added in a fixed order: the result does not depend on timing.
+ * Stream-ordered and asynchronous.
+ * Errors: CCST_E_INVALID (n < 0, null pointers, pitch < W), CCST_E_NOMEM, CCST_E_CUDA. */
+int ccst_backward(ccst_ctx* ctx, const void* frames_dev, int64_t n, int64_t pitch_elems,
+                  const ccst_result* rec_dev, const float* g_dxdy_dev, float* g_frames_dev, float* g_ref_dev);
 
 /* Free everything the context owns. NULL is a no-op. Synchronises its stream first. */
 void ccst_destroy(ccst_ctx* ctx);

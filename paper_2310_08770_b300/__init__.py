@@ -9,8 +9,9 @@ _BINDING = ("CC_SN", "CC_U", "Tracker", "CcstError", "RESULT_DTYPE", "decode", "
             "ccst_version", "ccst_default_params", "ccst_create", "ccst_track", "ccst_track_host",
             "ccst_set_stream", "ccst_sync", "ccst_submit", "ccst_poll", "ccst_backward",
             "ccst_destroy", "ccst_grid_size", "ccst_debug_surfaces", "ccst_profile_kernel_ms",
-            "ccst_profile_reset", "ccst_debug_pairs",
-            "ccst_track_static")
+            "ccst_profile_reset", "ccst_debug_pairs", "ccst_track_static",
+            "ccst_rt_begin", "ccst_rt_track", "ccst_drift_correct", "ccst_set_reference_frame",
+            "ccst_offline_update", "ccst_offline_track", "ccst_reference_status", "ccst_peak_continuous")
 
 
 def __getattr__(name):

@@ -71,8 +71,10 @@ _SIGS = [
     ("ccst_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("ccst_submit_host", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
-    ("ccst_backward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
-                                     ctypes.c_void_p, ctypes.c_void_p]),
+    ("ccst_peak_continuous", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("ccst_backward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("ccst_destroy", None, [ctypes.c_void_p]),
     ("ccst_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("ccst_grid_size", ctypes.c_int, [ctypes.c_void_p]),
@@ -238,9 +240,14 @@ def ccst_drift_correct(rec_dev, n, a0, b1, alpha, u, out_dev, stream=None) -> No
         raise CcstError(rc, "ccst_drift_correct failed")
 
 
-def ccst_backward(ctx, frames_dev, n, g_dxdy_dev, g_frames_dev, g_ref_dev) -> None:
-    _check(lib().ccst_backward(ctx, _ptr(frames_dev), int(n), _ptr(g_dxdy_dev), _ptr(g_frames_dev),
-                               _ptr(g_ref_dev)), ctx)
+def ccst_peak_continuous(ctx, frames_dev, n, pitch_elems, rec_dev, peak_dev, status_dev=None) -> None:
+    _check(lib().ccst_peak_continuous(ctx, _ptr(frames_dev), int(n), int(pitch_elems), _ptr(rec_dev),
+                                      _ptr(peak_dev), _ptr(status_dev)), ctx)
+
+
+def ccst_backward(ctx, frames_dev, n, pitch_elems, rec_dev, g_dxdy_dev, g_frames_dev, g_ref_dev) -> None:
+    _check(lib().ccst_backward(ctx, _ptr(frames_dev), int(n), int(pitch_elems), _ptr(rec_dev), _ptr(g_dxdy_dev),
+                               _ptr(g_frames_dev), _ptr(g_ref_dev)), ctx)
 
 
 def ccst_destroy(ctx) -> None:

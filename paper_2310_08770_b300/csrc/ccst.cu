@@ -17,6 +17,7 @@
 
 #include "ccst.h"
 #include "ccst_kernels.cuh"
+#include "ccst_adjoint.cuh"
 
 using namespace ccst;
 
@@ -555,6 +556,7 @@ struct ccst_ctx {
     double2* d_offScratch = nullptr;
     int off_parts = 0;                // partial sums written by the last accumulation
     int off_max_parts = 0;
+    double2* d_adjY = nullptr;        // adjoint: [H][Wc] column-inverse of the summed dL/db spectra
     double rt_a0 = 0.0, rt_b1 = 1.0;
     bool rt_on = false;               // ccst_rt_begin has run
     // graphs keyed by (frames, n, pitch, out), each with its own profiling event pair
@@ -630,7 +632,7 @@ static void free_all(ccst_ctx* c) {
         if (c->hstream[i]) cudaStreamDestroy(c->hstream[i]);
     void* ptrs[] = {c->d_ref32, c->d_b64, c->d_FE64, c->d_FE32, c->d_tw64, c->d_tw32,
                     c->d_tab,   c->d_df,  c->d_frames, c->d_out, c->d_next, c->d_rtE, c->d_rtY, c->d_rtSync,
-                    c->d_offPart, c->d_offScratch};
+                    c->d_offPart, c->d_offScratch, c->d_adjY};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -1016,10 +1018,63 @@ extern "C" int ccst_poll(ccst_ctx* c, uint64_t ticket, int timeout_us, int* done
     }
 }
 
-extern "C" int ccst_backward(ccst_ctx* c, const void*, int64_t, const float*, float*, float*) {
+// ------------------------------------------------------------ continuous peak and adjoint
+static int off_prepare(ccst_ctx* c);
+
+static int adj_run(ccst_ctx* c, const void* frames, int64_t n, int64_t pitch, const ccst_result* rec,
+                   const float* gdxdy, double* peak, int32_t* status, float* g_frames, float* g_ref,
+                   const char* who) {
     int rc = check_ctx(c);
     if (rc) return rc;
-    return fail(c, CCST_E_UNSUPPORTED, "ccst_backward is not implemented in this build");
+    if (n < 0) return fail(c, CCST_E_INVALID, std::string(who) + ": n < 0");
+    if (n > 0 && (!rec || !frames)) return fail(c, CCST_E_INVALID, std::string(who) + ": null frames or records");
+    if (pitch == 0) pitch = c->g.W;
+    if (pitch < c->g.W) return fail(c, CCST_E_INVALID, std::string(who) + ": pitch_elems < W");
+    const Geom& g = c->g;
+    if (g_ref) CK(c, cudaMemsetAsync(g_ref, 0, (size_t)g.H * g.W * sizeof(float), c->stream));
+    if (n == 0) return CCST_OK;
+    if ((rc = off_prepare(c))) return rc;
+    const size_t smem = adj_smem_bytes(g.H, g.W);
+    if (!c->d_adjY) {
+        CK(c, cudaFuncSetAttribute(adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CK(c, cudaMalloc(&c->d_adjY, (size_t)g.H * g.Wc * sizeof(double2)));
+    }
+    const int grid = (int)(n < c->off_max_parts ? n : c->off_max_parts);
+    AdjArgs a;
+    a.frames = frames;
+    a.n = n;
+    a.pitch = pitch;
+    a.rec = (const Result*)rec;
+    a.g = gdxdy;
+    a.peak = peak;
+    a.status = status;
+    a.g_frames = g_frames;
+    a.scratch = c->d_offScratch;
+    a.part = g_ref ? c->d_offPart : nullptr;
+    adj_kernel<<<grid, 512, smem, c->stream>>>(g, a);
+    CK(c, cudaGetLastError());
+    if (g_ref) {
+        adj_ref_cols<<<g.Wc, 128, 0, c->stream>>>(g, c->d_offPart, grid, c->d_adjY);
+        adj_ref_rows<<<g.H / 2, 128, 0, c->stream>>>(g, c->d_adjY, g_ref);
+        CK(c, cudaGetLastError());
+    }
+    return CCST_OK;
+}
+
+extern "C" int ccst_peak_continuous(ccst_ctx* c, const void* frames_dev, int64_t n, int64_t pitch_elems,
+                                    const ccst_result* rec_dev, double* peak_dev, int32_t* status_dev) {
+    if (c && n > 0 && !peak_dev && !status_dev)
+        return fail(c, CCST_E_INVALID, "ccst_peak_continuous: no output");
+    return adj_run(c, frames_dev, n, pitch_elems, rec_dev, nullptr, peak_dev, status_dev, nullptr, nullptr,
+                   "ccst_peak_continuous");
+}
+
+extern "C" int ccst_backward(ccst_ctx* c, const void* frames_dev, int64_t n, int64_t pitch_elems,
+                             const ccst_result* rec_dev, const float* g_dxdy_dev, float* g_frames_dev,
+                             float* g_ref_dev) {
+    if (c && n > 0 && !g_dxdy_dev) return fail(c, CCST_E_INVALID, "ccst_backward: null upstream gradient");
+    return adj_run(c, frames_dev, n, pitch_elems, rec_dev, g_dxdy_dev, nullptr, nullptr, g_frames_dev, g_ref_dev,
+                   "ccst_backward");
 }
 
 extern "C" void ccst_destroy(ccst_ctx* c) {

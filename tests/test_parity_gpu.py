@@ -351,8 +351,8 @@ def test_edge_cases(torch):
     with pytest.raises(C.CcstError):
         C.ccst_track(t.ctx, frames, 1, W - 1, out)               # pitch < W
     with pytest.raises(C.CcstError) as e:
-        C.ccst_backward(t.ctx, frames, 1, None, None, None)
-    assert e.value.code == C.E_UNSUPPORTED
+        C.ccst_backward(t.ctx, frames, 1, 0, out, None, None, None)     # no upstream gradient
+    assert e.value.code == C.E_INVALID
     # constant frame: every point ties; lowest index everywhere, as in the oracle
     frames[0] = 7.0
     C.ccst_track(t.ctx, frames, 1, 0, out)
