@@ -335,6 +335,125 @@ def offline_cpu_baseline(C, torch, s, stream):
             {"frames": len(fr), "passes": 2, "mismatches": mism, "tolerance_px": 1e-3})
 
 
+ADJ_PAIRS = 1024                 # adjoint leg: 64 x 64 FP32 pairs
+ADJ_REPS = 20
+ADJ_ORACLE_PAIRS = 32
+
+
+def adj_flop_per_pair(h=64, w=64, newton_steps=4):
+    """FP64 flop of one pair, forward + backward: three real 2-D transforms (the frame's
+    spectrum in each pass, the complex-to-real return of dL/dI) at 2.5 HW log2 HW, and
+    2 x newton_steps Newton steps at 16 flop per half-spectrum bin."""
+    return 3 * 2.5 * h * w * math.log2(h * w) + 2 * newton_steps * 16 * h * (w // 2 + 1)
+
+
+def adjoint_leg(C, torch, stream):
+    """Continuous peak and its adjoint (ccst_peak_continuous, ccst_backward) over 1024 pairs:
+    forward = tracking + Newton refinement, backward = the VJP into frames and reference."""
+    from paper_2310_08770_b300 import synth
+    p = synth.adjoint_pairs(seed=0, n=ADJ_PAIRS)
+    n, H, W = p.frames.shape
+    t = C.Tracker(p.ref, upsample=U, method="ccu", in_dtype="f32", max_batch=n, stream=stream)
+    fr = torch.from_numpy(p.frames).cuda()
+    rec = t.empty_results(n)
+    peak = torch.empty((n, 2), dtype=torch.float64, device="cuda")
+    status = torch.empty((n,), dtype=torch.int32, device="cuda")
+    g = torch.ones((n, 2), dtype=torch.float32, device="cuda")
+    gI = torch.empty((n, H, W), dtype=torch.float32, device="cuda")
+    gE = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)          # noqa: E731
+
+    def fwd():
+        C.ccst_track(t.ctx, fr, n, 0, rec)
+        C.ccst_peak_continuous(t.ctx, fr, n, 0, rec, peak, status)
+
+    def bwd():
+        C.ccst_backward(t.ctx, fr, n, 0, rec, g, gI, gE)
+    times = {}
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            fwd()
+            bwd()
+        torch.cuda.synchronize()
+        for name, fn in (("forward", fwd), ("backward", bwd)):
+            a, b = ev(), ev()
+            a.record(stream)
+            for _ in range(ADJ_REPS):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            times[name] = a.elapsed_time(b) / ADJ_REPS
+        bad = int((status != 0).sum().item())
+        # Poisson-propagated spread of s* at the expected frames: sum_r (ds*/dI(r))^2 mu(r)
+        mu = torch.from_numpy(p.mu).cuda()
+        C.ccst_track(t.ctx, mu, n, 0, rec)
+        sd = []
+        for gv in ((1.0, 0.0), (0.0, 1.0)):
+            g.copy_(torch.tensor(gv, dtype=torch.float32).expand(n, 2))
+            C.ccst_backward(t.ctx, mu, n, 0, rec, g, gI, None)
+            sd.append(torch.sqrt((gI.double() ** 2 * mu.double()).sum(dim=(1, 2))).cpu().numpy())
+        torch.cuda.synchronize()
+    t.close()
+    flop = adj_flop_per_pair(H, W)
+    achieved = flop * n / ((times["forward"] + times["backward"]) / 1e3) / 1e12
+    return {"workload": f"{n} pairs, 64x64 FP32, noise-free reference (sigma 3, peak 1000, bg 10), Poisson frames "
+                        "shifted uniformly in [-2, 2] px, u=100, CC-U; dL/dd = 1",
+            "value": n / ((times["forward"] + times["backward"]) / 1e3), "unit": "pairs/s (forward + backward)",
+            "forward_ms": times["forward"], "backward_ms": times["backward"], "status_nonzero": bad,
+            "roofline": {"bound": "fp64", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "flop_per_pair": flop,
+                         "kernel": "adj_kernel (+ track_kernel in forward)",
+                         "peak_basis": "nominal B300 FP64 1.25 TFLOP/s (not measured)"}}, (p, sd)
+
+
+def adjoint_cpu_baseline(C, torch, stream, p, sd):
+    """The FP64 adjoint oracle on the first ADJ_ORACLE_PAIRS pairs: its rate, parity of the
+    GPU's s* and dL/dI there, and the propagated spread against the Cramer-Rao bound."""
+    from oracle import adjoint_oracle, cc_oracle
+    from paper_2310_08770_b300 import synth
+    k = ADJ_ORACLE_PAIRS
+    ref = p.ref.astype(np.float64)
+    t = C.Tracker(p.ref, upsample=U, method="ccu", in_dtype="f32", max_batch=k, stream=stream)
+    fr = torch.from_numpy(p.frames[:k]).cuda()
+    rec = t.empty_results(k)
+    peak = torch.empty((k, 2), dtype=torch.float64, device="cuda")
+    gI = torch.empty((k, 64, 64), dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        C.ccst_track(t.ctx, fr, k, 0, rec)
+        C.ccst_peak_continuous(t.ctx, fr, k, 0, rec, peak, None)
+        C.ccst_backward(t.ctx, fr, k, 0, rec, torch.ones((k, 2), dtype=torch.float32, device="cuda"), gI, None)
+        torch.cuda.synchronize()
+    recs, pk_gpu, gI_gpu = C.decode(rec), peak.cpu().numpy(), gI.cpu().numpy()
+    t.close()
+    t0 = time.perf_counter()
+    ds, dg = 0.0, 0.0
+    for i in range(k):
+        f = p.frames[i].astype(np.float64)
+        orec = cc_oracle.track_one(f, ref, U)
+        pk, a, _ = adjoint_oracle.peak_and_vjp(f, ref, orec, (1.0, 1.0))
+        ds = max(ds, abs(pk["s"][1] - pk_gpu[i, 0]), abs(pk["s"][0] - pk_gpu[i, 1]))
+        dg = max(dg, float(np.max(np.abs(a - gI_gpu[i])) / np.abs(a).max()))
+    dt = time.perf_counter() - t0
+    ratio = []
+    for i in range(k):
+        h = 1e-4
+        d = p.d_true[i]
+
+        def spot(dy, dx):
+            return synth.gaussian_spot(64, 64, 32 + d[1] + dy, 32 + d[0] + dx, 3.0, 1000.0, 10.0)
+        b = adjoint_oracle.crlb(p.mu[i].astype(np.float64), (spot(h, 0) - spot(-h, 0)) / (2 * h),
+                                (spot(0, h) - spot(0, -h)) / (2 * h))
+        ratio.append((sd[0][i] / b[1], sd[1][i] / b[0]))
+    ratio = np.array(ratio)
+    del recs
+    return ({"value": k / dt, "unit": "pairs/s (forward + backward)", "cores": 1, "kind": "oracle",
+             "sample": f"first {k} pairs: FP64 oracle tracking, Newton peak and VJP, one process"},
+            {"pairs": k, "max_abs_ds_px": ds, "max_rel_dLdI": dg},
+            {"pairs": k, "propagated_std_over_crlb_x": float(ratio[:, 0].mean()),
+             "propagated_std_over_crlb_y": float(ratio[:, 1].mean()),
+             "min_ratio": float(ratio.min())})
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -469,7 +588,13 @@ def run_ours(args):
         line["realtime"] = rt_line
     if rank == 0 and not args.no_offline:
         line["offline"] = offline_leg(C, torch, s, frames_dev, n_frames, stream)
+    adj_extra = None
+    if rank == 0 and not args.no_adjoint:
+        line["adjoint"], adj_extra = adjoint_leg(C, torch, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        if adj_extra is not None:
+            (line["adjoint"]["cpu_baseline"], line["adjoint"]["parity"],
+             line["adjoint"]["cramer_rao"]) = adjoint_cpu_baseline(C, torch, stream, *adj_extra)
         if "offline" in line:
             line["offline"]["cpu_baseline"], line["offline"]["parity"] = offline_cpu_baseline(C, torch, s, stream)
         if rt_res is not None:
@@ -564,6 +689,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-realtime", action="store_true")
     ap.add_argument("--no-offline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--rt-frames", type=int, default=RT_FRAMES)
     ap.add_argument("--frames", type=int, default=N_FRAMES,
                     help="frames of the stream to stage (the workload is 10000; smaller only for profiler captures)")

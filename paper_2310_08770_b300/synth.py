@@ -140,3 +140,24 @@ def frame_stream(seed: int = 0, n: int = 10_000, H: int = 128, W: int = 128, sig
         if t >= start:
             frames[t - start] = np.minimum(f, 65535).astype(np.uint16)
     return FrameStream(ref.astype(np.float32), frames, d[start:start + count].copy())
+
+
+@dataclass
+class AdjointPairs:
+    ref: np.ndarray        # float32 (H, W), noise-free spot at the centre
+    frames: np.ndarray     # float32 (n, H, W), Poisson
+    mu: np.ndarray         # float32 (n, H, W), the frames' expected values
+    d_true: np.ndarray     # float64 (n, 2) = (dx, dy) per frame
+
+
+def adjoint_pairs(seed: int = 0, n: int = 1024, H: int = 64, W: int = 64, sigma: float = 3.0,
+                  amplitude: float = 1000.0, background: float = 10.0, spread: float = 2.0) -> AdjointPairs:
+    """Gradient workload: one noise-free reference, n Poisson frames of the same spot moved by
+    (dx, dy) uniform in [-spread, spread] per axis. Draws: shifts, then noise frame by frame."""
+    rng = np.random.default_rng(seed)
+    d = rng.uniform(-spread, spread, size=(n, 2))
+    cy, cx = H / 2.0, W / 2.0
+    ref = gaussian_spot(H, W, cy, cx, sigma, amplitude, background)
+    mu = np.array([gaussian_spot(H, W, cy + p[1], cx + p[0], sigma, amplitude, background) for p in d])
+    frames = np.array([poisson_frame(rng, m) for m in mu])
+    return AdjointPairs(ref.astype(np.float32), frames.astype(np.float32), mu.astype(np.float32), d)
