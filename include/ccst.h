@@ -100,6 +100,15 @@ typedef struct ccst_result {
     uint32_t flags;      /* CCST_R_*                                                */
 } ccst_result;
 
+/* One region of interest of an uneven batch (ccst_track_rois): 32 bytes. */
+typedef struct ccst_roi {
+    const void* frame;      /* device memory: H rows pitch_elems apart, the context's in_dtype */
+    int32_t  H, W;          /* must equal the size of reference ref_id                        */
+    int64_t  pitch_elems;   /* 0 means W                                                       */
+    int32_t  ref_id;        /* 0: the context's reference; others from ccst_add_reference      */
+    int32_t  reserved;      /* 0                                                               */
+} ccst_roi;
+
 typedef struct ccst_ctx ccst_ctx;
 
 /* Library version, CCST_VERSION. */
@@ -180,6 +189,29 @@ int ccst_submit(ccst_ctx* ctx, const void* frames_dev, int64_t n, ccst_result* o
  *   CCST_E_TIMEOUT   *done = 0; poll again later.
  *   CCST_E_INVALID   unknown ticket. */
 int ccst_poll(ccst_ctx* ctx, uint64_t ticket, int timeout_us, int* done);
+
+/* Add a reference for uneven-ROI batches (ccst_track_rois) and return its id in *ref_id.
+ *   ref      H*W float32, row-major, host or device memory; copied.
+ *   H, W     square, 16, 32, 64 or 128 pixels a side (the sizes the ROI kernel is
+ *            built for); others return CCST_E_SHAPE.
+ * The first reference of a new size also creates that size's plan (geometry, FFT
+ * twiddles, upsampling tables) with the context's parameters (u, method, eps). Each
+ * reference keeps its spectra resident (FP32, FP64 and double-float) and its FP64
+ * operand: about 26 H*W bytes of device memory, owned by the context. The context's own
+ * reference is id 0, usable when its frames are one of the sizes above. Synchronous.
+ * Errors: CCST_E_INVALID (null pointers), CCST_E_SHAPE, CCST_E_NOMEM, CCST_E_CUDA. */
+int ccst_add_reference(ccst_ctx* ctx, const float* ref, int H, int W, int* ref_id);
+
+/* Track an uneven batch: n ROIs of mixed sizes, each against its own reference (Secs. II-III
+ * per ROI, as ccst_track), in ONE persistent launch.
+ *   rois      host memory, n descriptors (read during the call).
+ *   out_dev   device memory, n records; record i belongs to rois[i].
+ * Work items run largest ROI first; each CTA takes the next item from a counter and
+ * re-plans its shared memory when the size changes. The records are identical to those of
+ * ccst_track on a context made for that ROI's reference. Stream-ordered and asynchronous.
+ * Errors: CCST_E_INVALID (null pointers, n < 0, unknown ref_id, pitch < W), CCST_E_SHAPE (a
+ * ROI whose size differs from its reference's), CCST_E_NOMEM, CCST_E_CUDA. */
+int ccst_track_rois(ccst_ctx* ctx, const ccst_roi* rois, int64_t n, ccst_result* out_dev);
 
 /* Real-time reference (Sec. III B, Eq. (9)): start a filtered reference from frame 0.
  *   frame0_dev   device memory, one H x W frame of the context's in_dtype, rows

@@ -35,6 +35,11 @@ RESULT_DTYPE = np.dtype([("dx", "<f4"), ("dy", "<f4"), ("peak", "<f4"),
                          ("ipy", "<i4"), ("ipx", "<i4"), ("flags", "<u4")])
 
 
+class ccst_roi(ctypes.Structure):
+    _fields_ = [("frame", ctypes.c_void_p), ("H", ctypes.c_int32), ("W", ctypes.c_int32),
+                ("pitch_elems", ctypes.c_int64), ("ref_id", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class ccst_params(ctypes.Structure):
     _fields_ = [("upsample", ctypes.c_int32), ("method", ctypes.c_int32), ("eps", ctypes.c_float),
                 ("in_dtype", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("max_H", ctypes.c_int32),
@@ -83,6 +88,9 @@ _SIGS = [
     ("ccst_profile_reset", ctypes.c_int, [ctypes.c_void_p]),
     ("ccst_debug_surfaces", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("ccst_add_reference", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int)]),
+    ("ccst_track_rois", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ccst_roi), ctypes.c_int64, ctypes.c_void_p]),
     ("ccst_rt_begin", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
                                      ctypes.c_double]),
     ("ccst_rt_track", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
@@ -197,6 +205,30 @@ def ccst_poll(ctx, ticket: int, timeout_us: int) -> bool:
         return False
     _check(rc, ctx)
     return bool(done.value)
+
+
+def ccst_add_reference(ctx, ref, H: int, W: int) -> int:
+    """Add a reference (float32 H x W, numpy or torch, host or device) for ccst_track_rois."""
+    if not hasattr(ref, "data_ptr"):
+        ref = np.ascontiguousarray(ref, dtype=np.float32)
+    rid = ctypes.c_int()
+    _check(lib().ccst_add_reference(ctx, _ptr(ref), int(H), int(W), ctypes.byref(rid)), ctx)
+    return rid.value
+
+
+def make_rois(frames, ref_ids) -> ctypes.Array:
+    """ccst_roi descriptors for a list of (H, W) CUDA tensors and their reference ids."""
+    arr = (ccst_roi * len(frames))()
+    for i, (f, r) in enumerate(zip(frames, ref_ids)):
+        arr[i].frame = f.data_ptr()
+        arr[i].H, arr[i].W = int(f.shape[-2]), int(f.shape[-1])
+        arr[i].pitch_elems = int(f.stride(-2))
+        arr[i].ref_id = int(r)
+    return arr
+
+
+def ccst_track_rois(ctx, rois, n, out_dev) -> None:
+    _check(lib().ccst_track_rois(ctx, rois, int(n), _ptr(out_dev)), ctx)
 
 
 def ccst_rt_begin(ctx, frame0_dev, pitch_elems, a0, b1) -> None:

@@ -1,5 +1,6 @@
 // ccst.cu -- the C ABI of libccst (declared in include/ccst.h): context set-up,
 // launches, CUDA-graph replay of batches and the serving tickets.
+#include <algorithm>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -559,6 +560,29 @@ struct ccst_ctx {
     double2* d_adjY = nullptr;        // adjoint: [H][Wc] column-inverse of the summed dL/db spectra
     double rt_a0 = 0.0, rt_b1 = 1.0;
     bool rt_on = false;               // ccst_rt_begin has run
+    // uneven-ROI batches: size classes (plan 0 = this context's size) and references
+    // (ref 0 = this context's reference), their device copies, and the work-item buffer
+    struct SizePlan {
+        Geom g;
+        int ncy = 0, ncx = 0;         // double-float table lengths
+        std::vector<void*> mem;       // owned allocations (none for plan 0)
+    };
+    struct RefEntry {
+        int cls = -1;                 // size class, -1 if not usable by ccst_track_rois
+        RefSpectra r{};
+        std::vector<void*> mem;       // owned allocations (none for ref 0)
+    };
+    std::vector<SizePlan> plans;
+    std::vector<RefEntry> refs;
+    Geom* d_geoms = nullptr;
+    RefSpectra* d_refs = nullptr;
+    size_t geoms_cap = 0, refs_cap = 0;
+    RoiItem* d_items = nullptr;
+    size_t items_cap = 0;
+    std::vector<RoiItem> h_items;
+    bool rois_dirty = true;
+    size_t rois_smem = 0;
+    int rois_grid = 0;
     // graphs keyed by (frames, n, pitch, out), each with its own profiling event pair
     struct GraphEntry {
         cudaGraphExec_t exec = nullptr;
@@ -630,9 +654,15 @@ static void free_all(ccst_ctx* c) {
     if (c->h_next) cudaFree(c->h_next);
     for (int i = 0; i < 2; ++i)
         if (c->hstream[i]) cudaStreamDestroy(c->hstream[i]);
+    for (auto& pl : c->plans)
+        for (void* p : pl.mem) cudaFree(p);
+    for (auto& re : c->refs)
+        for (void* p : re.mem) cudaFree(p);
+    c->plans.clear();
+    c->refs.clear();
     void* ptrs[] = {c->d_ref32, c->d_b64, c->d_FE64, c->d_FE32, c->d_tw64, c->d_tw32,
                     c->d_tab,   c->d_df,  c->d_frames, c->d_out, c->d_next, c->d_rtE, c->d_rtY, c->d_rtSync,
-                    c->d_offPart, c->d_offScratch, c->d_adjY};
+                    c->d_offPart, c->d_offScratch, c->d_adjY, c->d_geoms, c->d_refs, c->d_items};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -1385,6 +1415,244 @@ extern "C" int ccst_drift_correct(const ccst_result* rec_dev, int64_t n, double 
     const double lim = alpha > 0.0 ? alpha / u : 0.0;
     rt_drift<<<1, 32, 0, (cudaStream_t)stream>>>((const Result*)rec_dev, (long long)n, a0, b1, lim, out_dev);
     return cudaGetLastError() == cudaSuccess ? CCST_OK : CCST_E_CUDA;
+}
+
+// ------------------------------------------------------------------ uneven-ROI batches
+static bool rois_size_ok(int H, int W) { return H == W && (H == 16 || H == 32 || H == 64 || H == 128); }
+
+static void df_lengths(const Geom& g, int* ncy, int* ncx) {
+    const long long Dy = (long long)g.u * g.H, Dx = (long long)g.u * g.W;
+    *ncy = (int)((Dy + g.By - 1) / g.By);
+    *ncx = (int)((Dx + g.Bx - 1) / g.Bx);
+}
+
+// Plan 0 and ref 0 are the context's own size and reference.
+static void rois_init(ccst_ctx* c) {
+    if (!c->plans.empty()) return;
+    ccst_ctx::SizePlan p0;
+    p0.g = c->g;
+    df_lengths(c->g, &p0.ncy, &p0.ncx);
+    c->plans.push_back(p0);
+    ccst_ctx::RefEntry r0;
+    r0.cls = rois_size_ok(c->g.H, c->g.W) ? 0 : -1;
+    r0.r = RefSpectra{c->d_FE32, c->d_FE64, c->d_b64, c->g.FEdf};
+    c->refs.push_back(r0);
+}
+
+// The size class of H x W, made on first use: geometry, twiddles, stage tables and the
+// double-float tables, as ccst_create makes them for the context's own size.
+static int rois_plan(ccst_ctx* c, int H, int W, int* cls) {
+    for (size_t i = 0; i < c->plans.size(); ++i)
+        if (c->plans[i].g.H == H && c->plans[i].g.W == W) {
+            *cls = (int)i;
+            return CCST_OK;
+        }
+    int limit = 0;
+    CK(c, cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    ccst_ctx::SizePlan sp;
+    Geom& g = sp.g;
+    if (!plan_geometry(H, W, c->p, (size_t)limit, &g)) return fail(c, CCST_E_SHAPE, "ccst_add_reference: frame too large");
+    const long long Dy = (long long)g.u * H, Dx = (long long)g.u * W;
+    g.By = 1; while ((long long)g.By * g.By < Dy) ++g.By;
+    g.Bx = 1; while ((long long)g.Bx * g.Bx < Dx) ++g.Bx;
+    df_lengths(g, &sp.ncy, &sp.ncx);
+    const size_t HWc = (size_t)H * g.Wc;
+    const size_t tabA = (size_t)g.Hh * g.T1p, tabB = (size_t)g.Wc * g.T1p;
+    const size_t ndf = (size_t)(g.Ntw / 2) + HWc + sp.ncy + g.By + sp.ncx + g.Bx;
+    double2* tw64 = nullptr;
+    float2* tw32 = nullptr;
+    float* tab = nullptr;
+    dfc* df = nullptr;
+    struct { void** ptr; size_t bytes; } allocs[] = {
+        {(void**)&tw64, (size_t)(g.Ntw / 2) * sizeof(double2)},
+        {(void**)&tw32, (size_t)(g.Ntw / 2) * sizeof(float2)},
+        {(void**)&tab, (2 * tabA + 3 * tabB) * sizeof(float) + table_bytes(g)},
+        {(void**)&df, ndf * sizeof(dfc)},
+    };
+    for (auto& a : allocs) {
+        const cudaError_t e = cudaMalloc(a.ptr, a.bytes);
+        if (e != cudaSuccess) {
+            for (void* p : sp.mem) cudaFree(p);
+            return fail(c, e == cudaErrorMemoryAllocation ? CCST_E_NOMEM : CCST_E_CUDA,
+                        std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        sp.mem.push_back(*a.ptr);
+    }
+    g.tw64 = tw64; g.tw32 = tw32;
+    g.tA_cm1 = tab; g.tA_s = tab + tabA;
+    g.tB_wc = tab + 2 * tabA; g.tB_ws = g.tB_wc + tabB; g.tB_gc = g.tB_ws + tabB;
+    g.tAh = (const uint2*)(g.tB_gc + tabB);
+    g.tBh = (const uint2*)((const char*)g.tAh + ta_bytes(g));
+    g.twdf = df;
+    g.FEdf = df + g.Ntw / 2;                               // the first reference's slot (unused)
+    g.eyc = g.FEdf + HWc; g.eyf = g.eyc + sp.ncy; g.exc = g.eyf + g.By; g.exf = g.exc + sp.ncx;
+    init_twiddles<<<1, 256, 0, c->stream>>>(g.Ntw, tw64, tw32);
+    init_tables<<<64, 256, 0, c->stream>>>(g, (float*)g.tA_cm1, (float*)g.tA_s, (float*)g.tB_wc, (float*)g.tB_ws,
+                                           (float*)g.tB_gc, (uint2*)g.tAh, (uint2*)g.tBh);
+    CK(c, cudaGetLastError());
+    c->plans.push_back(sp);
+    *cls = (int)c->plans.size() - 1;
+    c->rois_dirty = true;
+    return CCST_OK;
+}
+
+extern "C" int ccst_add_reference(ccst_ctx* c, const float* ref, int H, int W, int* ref_id) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!ref || !ref_id) return fail(c, CCST_E_INVALID, "ccst_add_reference: null ref or ref_id");
+    if (!rois_size_ok(H, W))
+        return fail(c, CCST_E_SHAPE, "ccst_add_reference: ROIs are square, 16, 32, 64 or 128 pixels a side");
+    rois_init(c);
+    int cls = 0;
+    if ((rc = rois_plan(c, H, W, &cls))) return rc;
+    const Geom pg = c->plans[cls].g;
+    const size_t HW = (size_t)H * W, HWc = (size_t)H * pg.Wc;
+    const size_t l2per = (size_t)(H / 2) * W + (size_t)H * pg.Wcp;
+    ccst_ctx::RefEntry re;
+    re.cls = cls;
+    float* ref32 = nullptr;
+    double* b64 = nullptr;
+    double2* FE64 = nullptr;
+    float2* FE32 = nullptr;
+    dfc* FEdf = nullptr;
+    double2* work = nullptr;
+    struct { void** ptr; size_t bytes; bool keep; } allocs[] = {
+        {(void**)&b64, HW * sizeof(double), true},     {(void**)&FE64, HWc * sizeof(double2), true},
+        {(void**)&FE32, HWc * sizeof(float2), true},   {(void**)&FEdf, HWc * sizeof(dfc), true},
+        {(void**)&ref32, HW * sizeof(float), false},   {(void**)&work, l2per * sizeof(double2), false},
+    };
+    std::vector<void*> tmp;
+    auto undo = [&]() {
+        for (void* p : re.mem) cudaFree(p);
+        for (void* p : tmp) cudaFree(p);
+    };
+    for (auto& a : allocs) {
+        const cudaError_t e = cudaMalloc(a.ptr, a.bytes);
+        if (e != cudaSuccess) {
+            undo();
+            return fail(c, e == cudaErrorMemoryAllocation ? CCST_E_NOMEM : CCST_E_CUDA,
+                        std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        (a.keep ? re.mem : tmp).push_back(*a.ptr);
+    }
+    Geom gt = pg;
+    gt.b64 = b64;
+    cudaError_t e = cudaMemcpyAsync(ref32, ref, HW * sizeof(float), cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess) {
+        init_ref_operand<<<32, 256, 0, c->stream>>>(gt, ref32, b64);
+        init_ref_spectrum<<<1, 256, 0, c->stream>>>(gt, work, FE64, FE32);
+        const int ncy = c->plans[cls].ncy, ncx = c->plans[cls].ncx;
+        init_dfloat<<<32, 256, 0, c->stream>>>(gt, pg.tw64, FE64, (dfc*)pg.twdf, FEdf, (dfc*)pg.eyc, (dfc*)pg.eyf,
+                                               (dfc*)pg.exc, (dfc*)pg.exf, ncy, ncx);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    for (void* p : tmp) cudaFree(p);
+    tmp.clear();
+    if (e != cudaSuccess) {
+        undo();
+        return fail(c, CCST_E_CUDA, std::string("ccst_add_reference: ") + cudaGetErrorString(e));
+    }
+    re.r = RefSpectra{FE32, FE64, b64, FEdf};
+    c->refs.push_back(re);
+    c->rois_dirty = true;
+    *ref_id = (int)c->refs.size() - 1;
+    return CCST_OK;
+}
+
+// Device copies of the plans and references, the kernel's shared-memory size and grid.
+static int rois_upload(ccst_ctx* c) {
+    if (!c->rois_dirty) return CCST_OK;
+    if (c->geoms_cap < c->plans.size()) {
+        if (c->d_geoms) cudaFree(c->d_geoms);
+        c->d_geoms = nullptr;
+        c->geoms_cap = 0;
+        CK(c, cudaMalloc(&c->d_geoms, 2 * c->plans.size() * sizeof(Geom)));
+        c->geoms_cap = 2 * c->plans.size();
+    }
+    if (c->refs_cap < c->refs.size()) {
+        if (c->d_refs) cudaFree(c->d_refs);
+        c->d_refs = nullptr;
+        c->refs_cap = 0;
+        CK(c, cudaMalloc(&c->d_refs, 2 * c->refs.size() * sizeof(RefSpectra)));
+        c->refs_cap = 2 * c->refs.size();
+    }
+    std::vector<Geom> gs;
+    size_t smem = 0;
+    for (auto& pl : c->plans) {
+        gs.push_back(pl.g);
+        if (rois_size_ok(pl.g.H, pl.g.W)) smem = std::max(smem, smem_plan(pl.g).total);
+    }
+    std::vector<RefSpectra> rs;
+    for (auto& re : c->refs) rs.push_back(re.r);
+    CK(c, cudaMemcpy(c->d_geoms, gs.data(), gs.size() * sizeof(Geom), cudaMemcpyHostToDevice));
+    CK(c, cudaMemcpy(c->d_refs, rs.data(), rs.size() * sizeof(RefSpectra), cudaMemcpyHostToDevice));
+    const void* k = track_rois_kernel_ptr();
+    int limit = 0, occ = 0, sms = 0;
+    CK(c, cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    CK(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, limit - (int)sizeof(Geom) - 64));
+    CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kThreads, smem));
+    if (occ < 1) return fail(c, CCST_E_SHAPE, "ccst_track_rois: the ROI kernel does not fit on an SM");
+    c->rois_smem = smem;
+    c->rois_grid = occ * sms;
+    c->rois_dirty = false;
+    return CCST_OK;
+}
+
+extern "C" int ccst_track_rois(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccst_result* out_dev) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (n < 0) return fail(c, CCST_E_INVALID, "ccst_track_rois: n < 0");
+    if (n == 0) return CCST_OK;
+    if (!rois || !out_dev) return fail(c, CCST_E_INVALID, "ccst_track_rois: null rois or out");
+    rois_init(c);
+    const size_t elem = c->p.in_dtype == CCST_U16 ? 2 : 4;
+    c->h_items.resize((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        const ccst_roi& q = rois[i];
+        if (q.ref_id < 0 || q.ref_id >= (int)c->refs.size() || c->refs[q.ref_id].cls < 0)
+            return fail(c, CCST_E_INVALID, "ccst_track_rois: unknown or unusable ref_id");
+        const Geom& pg = c->plans[c->refs[q.ref_id].cls].g;
+        if (q.H != pg.H || q.W != pg.W) return fail(c, CCST_E_SHAPE, "ccst_track_rois: ROI size differs from its reference");
+        const int64_t pitch = q.pitch_elems == 0 ? q.W : q.pitch_elems;
+        if (!q.frame || pitch < q.W) return fail(c, CCST_E_INVALID, "ccst_track_rois: null frame or pitch < W");
+        RoiItem& it = c->h_items[(size_t)i];
+        it.frame = q.frame;
+        it.pitch = pitch;
+        it.out_index = i;
+        it.cls = c->refs[q.ref_id].cls;
+        it.ref = q.ref_id;
+        it.vec_ok = ((uintptr_t)q.frame % 16 == 0) && ((size_t)pitch * elem % 16 == 0) ? 1 : 0;
+        it.pad = 0;
+    }
+    // largest ROIs first (longest work first balances the CTAs); size classes stay contiguous
+    std::stable_sort(c->h_items.begin(), c->h_items.end(), [&](const RoiItem& a, const RoiItem& b) {
+        return c->plans[a.cls].g.H > c->plans[b.cls].g.H;
+    });
+    if ((rc = rois_upload(c))) return rc;
+    if (c->items_cap < (size_t)n) {
+        if (c->d_items) cudaFree(c->d_items);
+        c->d_items = nullptr;
+        c->items_cap = 0;
+        CK(c, cudaMalloc(&c->d_items, (size_t)n * sizeof(RoiItem)));
+        c->items_cap = (size_t)n;
+    }
+    CK(c, cudaMemcpyAsync(c->d_items, c->h_items.data(), (size_t)n * sizeof(RoiItem), cudaMemcpyHostToDevice,
+                          c->stream));
+    unsigned* counter = c->d_next + 16;
+    CK(c, cudaMemsetAsync(counter, 0, sizeof(unsigned), c->stream));
+    RoiBatch rb;
+    rb.items = c->d_items;
+    rb.n = n;
+    rb.geoms = c->d_geoms;
+    rb.refs = c->d_refs;
+    rb.out = (Result*)out_dev;
+    rb.next = counter;
+    const int grid = (int)(n < c->rois_grid ? n : c->rois_grid);
+    void* args[] = {&rb};
+    CK(c, cudaLaunchKernel(track_rois_kernel_ptr(), dim3(grid), dim3(kThreads), args, c->rois_smem, c->stream));
+    return CCST_OK;
 }
 
 // Grid size M of the refinement square for this context (tests and bindings).

@@ -89,6 +89,36 @@ struct Geom {
     int By, Bx;
 };
 
+// Uneven-ROI batches (ccst_track_rois): resident spectra of one reference, one work item per
+// ROI, and the launch's arguments.
+struct RefSpectra {
+    const float2* FE32;
+    const double2* FE64;
+    const double* b64;
+    const dfc* FEdf;
+};
+
+struct Result;
+
+struct RoiItem {
+    const void* frame;      // the ROI's pixels (in_dtype), rows `pitch` elements apart
+    long long pitch;
+    long long out_index;    // record slot
+    int cls;                // size class: index into RoiBatch::geoms
+    int ref;                // reference: index into RoiBatch::refs
+    int vec_ok;             // 16-byte vector loads allowed
+    int pad;
+};
+
+struct RoiBatch {
+    const RoiItem* items;   // largest size first
+    long long n;
+    const struct Geom* geoms;
+    const RefSpectra* refs;
+    Result* out;
+    unsigned* next;         // item counter, zeroed before the launch
+};
+
 struct Result {  // mirrors ccst_result
     float dx, dy, peak;
     int ipy, ipx;
@@ -1688,13 +1718,146 @@ static __device__ int df_reevaluate(const Geom& g, const Smem& S, const void* fr
 
 // ---------------------------------------------------------- the FP32 kernel
 // One instantiation per frame size (H, W); the host picks it through track_kernel_for().
+// Per-CTA set-up for frames of size H x W: FFT twiddles and the four-step pass twiddles.
 template <int H, int W>
-__global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
-    const Smem S = carve(g, ccst_smem);
+__device__ __forceinline__ void track_setup(const Geom& g, const Smem& S) {
     for (int k = threadIdx.x; k < g.Ntw / 2; k += blockDim.x) S.tw[k] = g.tw32[k];
     __syncthreads();
     build_pass_twiddles<H>(S.t4h, S.tw, g.logNtw);
     build_pass_twiddles<W>(S.t4w, S.tw, g.logNtw);
+}
+
+// a1-a7 for one frame (rows b.pitch elements apart) against the reference of g; the record
+// goes to b.out[f], and f indexes the optional debug outputs of b. Returns false when the
+// stage tables never arrived (the record says so; the CTA must stop).
+template <int H, int W>
+__device__ __forceinline__ bool track_frame(const Geom& g, const Batch& b, const Smem& S, long long f,
+                                            const char* frame, unsigned& bar_parity) {
+    unsigned flags = 0;
+    float scale = 0.f;
+    Best2 t2;
+    fft_correlate_t<H, W>(g, S, frame, b.pitch, b.vec_ok, &scale, t2,
+                          b.dbg_int ? b.dbg_int + (size_t)f * g.H * g.W : nullptr);
+    const int ip = integer_peak(g, S, frame, b.pitch, &scale, &flags, t2);
+    const float c0 = int_surface(g, S, ip);           // HW * c(p)
+    const int py = wrap_shift(ip >> g.logW, g.H), px = wrap_shift(ip & (g.W - 1), g.W);
+    __syncthreads();
+    if (!b.dbg_no_copy) stage_tables_async(g, S);      // overlaps the P/Q build
+    build_pq_and_g(g, S, py, px, scale);
+    const int wait_limit = b.dbg_no_copy ? (1 << 10) : (1 << 22);
+    const bool staged = stage_tables_wait(g, S, bar_parity, wait_limit);
+    if (__syncthreads_or(!staged)) {
+        // the copies never completed: report it for this frame and stop this CTA, after
+        // one more bounded wait so that no copy is left writing into this CTA's memory
+        if (threadIdx.x == 0) {
+            (void)stage_tables_wait(g, S, bar_parity, wait_limit);
+            Result r{};
+            r.flags = flags | 0x20u;
+            b.out[f] = r;
+        }
+        return false;
+    }
+    bar_parity ^= 1u;
+    if (b.dbg_pairs) {
+        const int ja = b.dbg_pairs[2 * f], jb = b.dbg_pairs[2 * f + 1];
+        const double d64 = pair_difference_f64(g, S, ja, jb, S.rd);
+        if (threadIdx.x == 0) { S.cj[0] = ja; S.cj[1] = jb; }
+        __syncthreads();
+        int nl2dummy = 0;
+        float dw = 0.f;
+        pair_difference_guard(g, S, 2, 0.f, &nl2dummy, &dw);
+        if (threadIdx.x == 0) {
+            b.dbg_d32[f] = g.sense * S.cv[1];
+            b.dbg_d64[f] = d64;
+        }
+        __syncthreads();
+        return true;
+    }
+    TopK<kTopK> top;
+    top.init();
+    float* dbg = b.dbg_sub ? b.dbg_sub + (size_t)f * g.M * g.M : nullptr;
+    // no point below the (0, 0) point's value minus the near-tie band can matter
+    const float lb = g.sense * S.gP[0] - g.tau0 * scale;
+    upsampled_pass<H, W, false>(g, S, top, lb, dbg);
+    float vw = top.v[0];
+    int jw = top.j[0];
+    block_argmax(vw, jw, S.rv, S.rj);
+    float dwin = 0.f;
+    int nl2 = 0;
+    if (!(vw > -INFINITY)) {
+        flags |= 0x10u;
+        jw = 0;
+    } else if (g.guard) {
+        const float thr = vw - g.tau0 * scale;
+        // each thread kept its best kTopK points; count those within tau0 of the maximum
+        int nc = 0;
+        unsigned mine = 0;
+#pragma unroll
+        for (int k = 0; k < kTopK; ++k) {
+            const bool q = top.v[k] >= thr;
+            mine |= (q ? 1u : 0u) << k;
+            nc += __syncthreads_count(q);
+        }
+        const bool full = __syncthreads_or(top.v[kTopK - 1] >= thr);
+        if (nc > 1) {
+            flags |= 0x02u;
+            if (!full && nc <= kMaxCand) {
+                // every point within tau0 is among the kept ones: gather them, j1 first
+                if (threadIdx.x == 0) { S.misc[1] = 1; S.cj[0] = jw; S.cv[0] = vw; }
+                __syncthreads();
+#pragma unroll
+                for (int k = 0; k < kTopK; ++k)
+                    if (((mine >> k) & 1u) && top.j[k] != jw) {
+                        const int slot = atomicAdd(&S.misc[1], 1);
+                        S.cj[slot] = top.j[k];
+                        S.cv[slot] = top.v[k];
+                    }
+                __syncthreads();
+            } else {
+                // a thread holds more near-ties than it kept: collect them all with a second pass
+                nc = collect_near<H, W>(g, S, thr);
+                if (nc > kMaxCand) {
+                    flags |= 0x08u;
+                    nc = 1;
+                } else if (threadIdx.x == 0) {
+                    // put the FP32 best first
+                    for (int k = 0; k < nc; ++k)
+                        if (S.cj[k] == jw) { S.cj[k] = S.cj[0]; S.cj[0] = jw; }
+                }
+                __syncthreads();
+            }
+            if (nc > 1) jw = pair_difference_guard(g, S, nc, scale, &nl2, &dwin);
+        }
+    }
+    __syncthreads();
+    // raw value at the winner: c(p) + sense * (v(j1) + D(winner))
+    float peak = (c0 + ((flags & 0x10u) ? 0.f : g.sense * (vw + dwin))) / (float)(g.H * g.W);
+    if (nl2 > 0) {
+        double raw = 0.0;
+        jw = df_reevaluate<H, W>(g, S, frame, b.pitch, py, px, nl2, &raw);
+        peak = (float)(raw / ((double)g.H * g.W));
+        flags |= 0x04u;
+    }
+    if (threadIdx.x == 0) {
+        const int jy = jw / g.M, jx = jw % g.M;
+        const int ty = jy - g.h0, tx = jx - g.h0;
+        Result r;
+        r.dy = (float)(((double)py * g.u + ty) / g.u);
+        r.dx = (float)(((double)px * g.u + tx) / g.u);
+        r.peak = peak;
+        r.ipy = py;
+        r.ipx = px;
+        r.flags = flags;
+        b.out[f] = r;
+    }
+    __syncthreads();
+    return true;
+}
+
+template <int H, int W>
+__global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
+    const Smem S = carve(g, ccst_smem);
+    track_setup<H, W>(g, S);
     tables_bar_init(S);
     unsigned bar_parity = 0;
     __syncthreads();
@@ -1710,126 +1873,12 @@ __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
     };
     for (long long f = fetch(-1); f < b.n; f = fetch(f)) {
         const char* frame = (const char*)b.frames + (size_t)f * g.H * b.pitch * elem;
-        unsigned flags = 0;
-        float scale = 0.f;
-        Best2 t2;
-        fft_correlate_t<H, W>(g, S, frame, b.pitch, b.vec_ok, &scale, t2,
-                              b.dbg_int ? b.dbg_int + (size_t)f * g.H * g.W : nullptr);
-        const int ip = integer_peak(g, S, frame, b.pitch, &scale, &flags, t2);
-        const float c0 = int_surface(g, S, ip);           // HW * c(p)
-        const int py = wrap_shift(ip >> g.logW, g.H), px = wrap_shift(ip & (g.W - 1), g.W);
-        __syncthreads();
-        if (!b.dbg_no_copy) stage_tables_async(g, S);      // overlaps the P/Q build
-        build_pq_and_g(g, S, py, px, scale);
-        const int wait_limit = b.dbg_no_copy ? (1 << 10) : (1 << 22);
-        const bool staged = stage_tables_wait(g, S, bar_parity, wait_limit);
-        if (__syncthreads_or(!staged)) {
-            // the copies never completed: report it for this frame and stop this CTA, after
-            // one more bounded wait so that no copy is left writing into this CTA's memory
-            if (threadIdx.x == 0) {
-                (void)stage_tables_wait(g, S, bar_parity, wait_limit);
-                Result r{};
-                r.flags = flags | 0x20u;
-                b.out[f] = r;
-            }
-            return;
-        }
-        bar_parity ^= 1u;
-        if (b.dbg_pairs) {
-            const int ja = b.dbg_pairs[2 * f], jb = b.dbg_pairs[2 * f + 1];
-            const double d64 = pair_difference_f64(g, S, ja, jb, S.rd);
-            if (threadIdx.x == 0) { S.cj[0] = ja; S.cj[1] = jb; }
-            __syncthreads();
-            int nl2dummy = 0;
-            float dw = 0.f;
-            pair_difference_guard(g, S, 2, 0.f, &nl2dummy, &dw);
-            if (threadIdx.x == 0) {
-                b.dbg_d32[f] = g.sense * S.cv[1];
-                b.dbg_d64[f] = d64;
-            }
-            __syncthreads();
-            continue;
-        }
-        TopK<kTopK> top;
-        top.init();
-        float* dbg = b.dbg_sub ? b.dbg_sub + (size_t)f * g.M * g.M : nullptr;
-        // no point below the (0, 0) point's value minus the near-tie band can matter
-        const float lb = g.sense * S.gP[0] - g.tau0 * scale;
-        upsampled_pass<H, W, false>(g, S, top, lb, dbg);
-        float vw = top.v[0];
-        int jw = top.j[0];
-        block_argmax(vw, jw, S.rv, S.rj);
-        float dwin = 0.f;
-        int nl2 = 0;
-        if (!(vw > -INFINITY)) {
-            flags |= 0x10u;
-            jw = 0;
-        } else if (g.guard) {
-            const float thr = vw - g.tau0 * scale;
-            // each thread kept its best kTopK points; count those within tau0 of the maximum
-            int nc = 0;
-            unsigned mine = 0;
-#pragma unroll
-            for (int k = 0; k < kTopK; ++k) {
-                const bool q = top.v[k] >= thr;
-                mine |= (q ? 1u : 0u) << k;
-                nc += __syncthreads_count(q);
-            }
-            const bool full = __syncthreads_or(top.v[kTopK - 1] >= thr);
-            if (nc > 1) {
-                flags |= 0x02u;
-                if (!full && nc <= kMaxCand) {
-                    // every point within tau0 is among the kept ones: gather them, j1 first
-                    if (threadIdx.x == 0) { S.misc[1] = 1; S.cj[0] = jw; S.cv[0] = vw; }
-                    __syncthreads();
-#pragma unroll
-                    for (int k = 0; k < kTopK; ++k)
-                        if (((mine >> k) & 1u) && top.j[k] != jw) {
-                            const int slot = atomicAdd(&S.misc[1], 1);
-                            S.cj[slot] = top.j[k];
-                            S.cv[slot] = top.v[k];
-                        }
-                    __syncthreads();
-                } else {
-                    // a thread holds more near-ties than it kept: collect them all with a second pass
-                    nc = collect_near<H, W>(g, S, thr);
-                    if (nc > kMaxCand) {
-                        flags |= 0x08u;
-                        nc = 1;
-                    } else if (threadIdx.x == 0) {
-                        // put the FP32 best first
-                        for (int k = 0; k < nc; ++k)
-                            if (S.cj[k] == jw) { S.cj[k] = S.cj[0]; S.cj[0] = jw; }
-                    }
-                    __syncthreads();
-                }
-                if (nc > 1) jw = pair_difference_guard(g, S, nc, scale, &nl2, &dwin);
-            }
-        }
-        __syncthreads();
-        // raw value at the winner: c(p) + sense * (v(j1) + D(winner))
-        float peak = (c0 + ((flags & 0x10u) ? 0.f : g.sense * (vw + dwin))) / (float)(g.H * g.W);
-        if (nl2 > 0) {
-            double raw = 0.0;
-            jw = df_reevaluate<H, W>(g, S, frame, b.pitch, py, px, nl2, &raw);
-            peak = (float)(raw / ((double)g.H * g.W));
-            flags |= 0x04u;
-        }
-        if (threadIdx.x == 0) {
-            const int jy = jw / g.M, jx = jw % g.M;
-            const int ty = jy - g.h0, tx = jx - g.h0;
-            Result r;
-            r.dy = (float)(((double)py * g.u + ty) / g.u);
-            r.dx = (float)(((double)px * g.u + tx) / g.u);
-            r.peak = peak;
-            r.ipy = py;
-            r.ipx = px;
-            r.flags = flags;
-            b.out[f] = r;
-        }
-        __syncthreads();
+        if (!track_frame<H, W>(g, b, S, f, frame, bar_parity)) return;
     }
 }
+
+// Address of the uneven-ROI kernel (ccst_rois.cu).
+const void* track_rois_kernel_ptr();
 
 // Address of track_kernel<H, W> (defined in the per-height translation units).
 const void* track_kernel_h8(int W);
