@@ -454,6 +454,79 @@ def adjoint_cpu_baseline(C, torch, stream, p, sd):
              "min_ratio": float(ratio.min())})
 
 
+ROIS_N = 4096                    # uneven-ROI leg
+ROIS_SIDES = (32, 64, 128)       # the square sizes built (48 and 96 would need radix-3 FFTs)
+ROIS_REPS = 10
+ROIS_ORACLE = 48
+
+
+def rois_leg(C, torch, stream):
+    """Uneven batch: 4096 FP32 ROIs of mixed sizes, each against its own reference, in one
+    persistent launch (ccst_track_rois), against the same ROIs as one launch each."""
+    import ctypes
+    from paper_2310_08770_b300 import synth
+    r = synth.uneven_rois(seed=0, n=ROIS_N, sides=ROIS_SIDES)
+    n = len(r.frames)
+    t = C.Tracker(r.refs[0], upsample=U, method="ccu", in_dtype="f32", stream=stream)
+    t0 = time.perf_counter()
+    ids = [0] + [C.ccst_add_reference(t.ctx, ref, ref.shape[0], ref.shape[1]) for ref in r.refs[1:]]
+    setup_s = time.perf_counter() - t0
+    frames = [torch.from_numpy(f).cuda() for f in r.frames]
+    rois = C.make_rois(frames, ids)
+    out = t.empty_results(n)
+    ev = lambda: torch.cuda.Event(enable_timing=True)          # noqa: E731
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            C.ccst_track_rois(t.ctx, rois, n, out)
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(stream)
+        for _ in range(ROIS_REPS):
+            C.ccst_track_rois(t.ctx, rois, n, out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        batched_ms = a.elapsed_time(b) / ROIS_REPS
+        res = C.decode(out)
+        a, b = ev(), ev()
+        a.record(stream)
+        for i in range(n):                                      # the plain form: one launch per ROI
+            C.ccst_track_rois(t.ctx, ctypes.byref(rois[i]), 1, out[i:i + 1])
+        b.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = a.elapsed_time(b)
+    same = bool(C.decode(out).tobytes() == res.tobytes())
+    t.close()
+    flop = sum(flop_per_frame(f.shape[0], f.shape[1], U) for f in r.frames)
+    achieved = flop / (batched_ms / 1e3) / 1e12
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    sizes = {s: int(sum(1 for f in r.frames if f.shape[0] == s)) for s in ROIS_SIDES}
+    return {"workload": f"{n} FP32 square ROIs, sides uniform over {list(ROIS_SIDES)} ({sizes}), per-ROI noise-free "
+                        "reference (sigma U(1.5,4), peak U(200,5000), bg U(5,50)), Poisson frames shifted U(-3,3)^2 px, "
+                        f"u={U}, CC-U",
+            "value": n / (batched_ms / 1e3), "unit": "ROIs/s", "ms_per_batch": batched_ms,
+            "plain_per_roi_launch": {"value": n / (plain_ms / 1e3), "unit": "ROIs/s", "ms": plain_ms},
+            "speedup_vs_plain": plain_ms / batched_ms, "records_equal_to_plain": same,
+            "reference_setup_s": setup_s,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "kernel": "track_rois_kernel", "flop_total": flop,
+                         "peak_basis": "148 SMs x 128 FP32 FMA lanes x 2 x 2032 MHz (nominal max clock)"}}, (r, res)
+
+
+def rois_cpu_baseline(r, res):
+    """The FP64 oracle on the first ROIS_ORACLE ROIs: its rate and parity with the batch."""
+    import oracle
+    k = ROIS_ORACLE
+    t0 = time.perf_counter()
+    orc = [oracle.track_one(r.frames[i].astype(np.float64), r.refs[i].astype(np.float64), U) for i in range(k)]
+    dt = time.perf_counter() - t0
+    mism = sum(1 for a, o in zip(res[:k], orc)
+               if (int(a["ipy"]), int(a["ipx"])) != (o["ipy"], o["ipx"])
+               or abs(float(a["dx"]) - o["dx32"]) > 1e-3 or abs(float(a["dy"]) - o["dy32"]) > 1e-3)
+    return ({"value": k / dt, "unit": "ROIs/s", "cores": 1, "kind": "oracle",
+             "sample": f"first {k} ROIs of the uneven batch, FP64 numpy oracle, one process"},
+            {"rois": k, "mismatches": mism, "tolerance_px": 1e-3})
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -588,10 +661,15 @@ def run_ours(args):
         line["realtime"] = rt_line
     if rank == 0 and not args.no_offline:
         line["offline"] = offline_leg(C, torch, s, frames_dev, n_frames, stream)
+    rois_extra = None
+    if rank == 0 and not args.no_rois:
+        line["rois"], rois_extra = rois_leg(C, torch, stream)
     adj_extra = None
     if rank == 0 and not args.no_adjoint:
         line["adjoint"], adj_extra = adjoint_leg(C, torch, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        if rois_extra is not None:
+            line["rois"]["cpu_baseline"], line["rois"]["parity"] = rois_cpu_baseline(*rois_extra)
         if adj_extra is not None:
             (line["adjoint"]["cpu_baseline"], line["adjoint"]["parity"],
              line["adjoint"]["cramer_rao"]) = adjoint_cpu_baseline(C, torch, stream, *adj_extra)
@@ -690,6 +768,7 @@ def main():
     ap.add_argument("--no-realtime", action="store_true")
     ap.add_argument("--no-offline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-rois", action="store_true")
     ap.add_argument("--rt-frames", type=int, default=RT_FRAMES)
     ap.add_argument("--frames", type=int, default=N_FRAMES,
                     help="frames of the stream to stage (the workload is 10000; smaller only for profiler captures)")

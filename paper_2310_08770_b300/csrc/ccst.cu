@@ -583,6 +583,8 @@ struct ccst_ctx {
     bool rois_dirty = true;
     size_t rois_smem = 0;
     int rois_grid = 0;
+    void* d_addref_tmp = nullptr;     // ccst_add_reference: reference copy and FFT workspace
+    size_t addref_tmp_bytes = 0;
     // graphs keyed by (frames, n, pitch, out), each with its own profiling event pair
     struct GraphEntry {
         cudaGraphExec_t exec = nullptr;
@@ -662,7 +664,7 @@ static void free_all(ccst_ctx* c) {
     c->refs.clear();
     void* ptrs[] = {c->d_ref32, c->d_b64, c->d_FE64, c->d_FE32, c->d_tw64, c->d_tw32,
                     c->d_tab,   c->d_df,  c->d_frames, c->d_out, c->d_next, c->d_rtE, c->d_rtY, c->d_rtSync,
-                    c->d_offPart, c->d_offScratch, c->d_adjY, c->d_geoms, c->d_refs, c->d_items};
+                    c->d_offPart, c->d_offScratch, c->d_adjY, c->d_geoms, c->d_refs, c->d_items, c->d_addref_tmp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -1510,34 +1512,36 @@ extern "C" int ccst_add_reference(ccst_ctx* c, const float* ref, int H, int W, i
     const size_t l2per = (size_t)(H / 2) * W + (size_t)H * pg.Wcp;
     ccst_ctx::RefEntry re;
     re.cls = cls;
-    float* ref32 = nullptr;
-    double* b64 = nullptr;
-    double2* FE64 = nullptr;
-    float2* FE32 = nullptr;
-    dfc* FEdf = nullptr;
-    double2* work = nullptr;
-    struct { void** ptr; size_t bytes; bool keep; } allocs[] = {
-        {(void**)&b64, HW * sizeof(double), true},     {(void**)&FE64, HWc * sizeof(double2), true},
-        {(void**)&FE32, HWc * sizeof(float2), true},   {(void**)&FEdf, HWc * sizeof(dfc), true},
-        {(void**)&ref32, HW * sizeof(float), false},   {(void**)&work, l2per * sizeof(double2), false},
-    };
-    std::vector<void*> tmp;
-    auto undo = [&]() {
-        for (void* p : re.mem) cudaFree(p);
-        for (void* p : tmp) cudaFree(p);
-    };
-    for (auto& a : allocs) {
-        const cudaError_t e = cudaMalloc(a.ptr, a.bytes);
+    // one block per reference: b64 | FE64 | FE32 | FEdf (each size a multiple of 16 bytes);
+    // the reference copy and the FFT workspace live in a scratch block the context keeps
+    const size_t nb64 = HW * sizeof(double), nFE64 = HWc * sizeof(double2), nFE32 = (HWc * sizeof(float2) + 15) & ~(size_t)15;
+    const size_t ntmp = HW * sizeof(float) + l2per * sizeof(double2);
+    char* blk = nullptr;
+    cudaError_t e = cudaMalloc(&blk, nb64 + nFE64 + nFE32 + HWc * sizeof(dfc));
+    if (e != cudaSuccess)
+        return fail(c, e == cudaErrorMemoryAllocation ? CCST_E_NOMEM : CCST_E_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    re.mem.push_back(blk);
+    double* b64 = (double*)blk;
+    double2* FE64 = (double2*)(blk + nb64);
+    float2* FE32 = (float2*)(blk + nb64 + nFE64);
+    dfc* FEdf = (dfc*)(blk + nb64 + nFE64 + nFE32);
+    auto undo = [&]() { for (void* p : re.mem) cudaFree(p); };
+    if (c->addref_tmp_bytes < ntmp) {
+        if (c->d_addref_tmp) cudaFree(c->d_addref_tmp);
+        c->d_addref_tmp = nullptr;
+        c->addref_tmp_bytes = 0;
+        e = cudaMalloc(&c->d_addref_tmp, ntmp);
         if (e != cudaSuccess) {
             undo();
-            return fail(c, e == cudaErrorMemoryAllocation ? CCST_E_NOMEM : CCST_E_CUDA,
-                        std::string("cudaMalloc: ") + cudaGetErrorString(e));
+            return fail(c, e == cudaErrorMemoryAllocation ? CCST_E_NOMEM : CCST_E_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
         }
-        (a.keep ? re.mem : tmp).push_back(*a.ptr);
+        c->addref_tmp_bytes = ntmp;
     }
+    double2* work = (double2*)c->d_addref_tmp;
+    float* ref32 = (float*)((char*)c->d_addref_tmp + l2per * sizeof(double2));
     Geom gt = pg;
     gt.b64 = b64;
-    cudaError_t e = cudaMemcpyAsync(ref32, ref, HW * sizeof(float), cudaMemcpyDefault, c->stream);
+    e = cudaMemcpyAsync(ref32, ref, HW * sizeof(float), cudaMemcpyDefault, c->stream);
     if (e == cudaSuccess) {
         init_ref_operand<<<32, 256, 0, c->stream>>>(gt, ref32, b64);
         init_ref_spectrum<<<1, 256, 0, c->stream>>>(gt, work, FE64, FE32);
@@ -1547,8 +1551,6 @@ extern "C" int ccst_add_reference(ccst_ctx* c, const float* ref, int H, int W, i
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     }
-    for (void* p : tmp) cudaFree(p);
-    tmp.clear();
     if (e != cudaSuccess) {
         undo();
         return fail(c, CCST_E_CUDA, std::string("ccst_add_reference: ") + cudaGetErrorString(e));

@@ -161,3 +161,27 @@ def adjoint_pairs(seed: int = 0, n: int = 1024, H: int = 64, W: int = 64, sigma:
     mu = np.array([gaussian_spot(H, W, cy + p[1], cx + p[0], sigma, amplitude, background) for p in d])
     frames = np.array([poisson_frame(rng, m) for m in mu])
     return AdjointPairs(ref.astype(np.float32), frames.astype(np.float32), mu.astype(np.float32), d)
+
+
+@dataclass
+class UnevenRois:
+    refs: list             # float32 (N_i, N_i) noise-free, one per ROI
+    frames: list           # float32 (N_i, N_i), Poisson
+    d_true: np.ndarray     # float64 (n, 2) = (dx, dy)
+
+
+def uneven_rois(seed: int = 0, n: int = 4096, sides=(32, 64, 128)) -> UnevenRois:
+    """ROIs of mixed square sizes, each with its own noise-free reference: side uniform over
+    `sides`, sigma ~ U(1.5, 4), peak ~ U(200, 5000), background ~ U(5, 50), shift ~ U(-3, 3)^2.
+    Draws, per ROI: side, sigma, peak, background, shift, then the noise frame."""
+    rng = np.random.default_rng(seed)
+    refs, frames, d = [], [], np.zeros((n, 2))
+    for i in range(n):
+        N = int(rng.choice(np.asarray(sides)))
+        sigma, amp, bg = rng.uniform(1.5, 4.0), rng.uniform(200.0, 5000.0), rng.uniform(5.0, 50.0)
+        dx, dy = rng.uniform(-3.0, 3.0, size=2)
+        d[i] = (dx, dy)
+        refs.append(gaussian_spot(N, N, N / 2.0, N / 2.0, sigma, amp, bg).astype(np.float32))
+        frames.append(poisson_frame(rng, gaussian_spot(N, N, N / 2.0 + dy, N / 2.0 + dx, sigma, amp, bg))
+                      .astype(np.float32))
+    return UnevenRois(refs, frames, d)
