@@ -213,6 +213,61 @@ int ccst_add_reference(ccst_ctx* ctx, const float* ref, int H, int W, int* ref_i
  * ROI whose size differs from its reference's), CCST_E_NOMEM, CCST_E_CUDA. */
 int ccst_track_rois(ccst_ctx* ctx, const ccst_roi* rois, int64_t n, ccst_result* out_dev);
 
+/* ---- Serving: continuous batching of single frames from several cameras.
+ *
+ * A server runs a worker thread over a context. Each camera is a reference of the
+ * context (id 0 or from ccst_add_reference): its frames have that reference's size. A
+ * submitted frame is copied into one of `slots` device slots reserved at creation; a
+ * submit without a free slot is refused with CCST_E_BUSY (admission by device memory).
+ * The worker takes everything pending (up to max_batch frames, any cameras and sizes) as
+ * one ccst_track_rois batch on its own stream, with up to 4 batches in flight, so frames
+ * that arrive while others run are admitted as slots free up and their work overlaps on
+ * the device. Each result equals that of the frame tracked alone (the batch changes only
+ * which CTA runs it). While a server exists its context must not be used by other calls
+ * (nor references added). */
+typedef struct ccst_server ccst_server;
+
+typedef struct ccst_server_stats {
+    uint64_t submitted, completed, rejected;   /* since the last reset                       */
+    uint64_t batches;                          /* kernel launches                            */
+    double   mean_batch;                       /* frames per launch                          */
+    double   p50_us, p99_us, max_us;           /* submit -> result available (host clock)   */
+    int64_t  in_flight;                        /* admitted, not yet completed               */
+} ccst_server_stats;
+
+/* Start a server over ctx (ctx keeps ownership of its references and must outlive it).
+ * Errors: CCST_E_INVALID (slots or max_batch < 1, no reference usable by ROI batches),
+ * CCST_E_NOMEM, CCST_E_CUDA. */
+int ccst_server_create(ccst_ctx* ctx, int slots, int max_batch, ccst_server** out);
+
+/* Submit one frame of camera ref_id from host memory (rows pitch_elems apart, 0 = W; copied
+ * before the call returns). With ticket non-NULL the result is kept for ccst_server_poll;
+ * with NULL it is only counted in the statistics. Thread-safe.
+ * Errors: CCST_E_INVALID, CCST_E_BUSY (no free slot: retry later), CCST_E_CUDA. */
+int ccst_server_submit(ccst_server* srv, int ref_id, const void* frame_host, int64_t pitch_elems,
+                       uint64_t* ticket);
+
+/* Wait up to timeout_us for a ticket's result. CCST_OK: *done = 1, *out holds the record
+ * and the ticket is released. CCST_E_TIMEOUT: *done = 0. CCST_E_INVALID: unknown ticket.
+ * Thread-safe. */
+int ccst_server_poll(ccst_server* srv, uint64_t ticket, int timeout_us, ccst_result* out, int* done);
+
+/* Statistics since the last reset (reset != 0 clears them after reading). Returns the
+ * server's sticky error, if any. */
+int ccst_server_read_stats(ccst_server* srv, int reset, ccst_server_stats* out);
+
+/* Measurement helper: offered load from ncams host threads. Camera k submits frames of
+ * its pool (pool_len[k] frames of its size, contiguous, host memory), cycled, at
+ * exponential inter-arrival times of mean 1/rates_hz[k] for `seconds`, seeded by seed;
+ * refused frames are dropped and counted. Returns after all admitted frames completed,
+ * with the statistics of the run in *out. */
+int ccst_server_loadgen(ccst_server* srv, int ncams, const int* ref_ids, const double* rates_hz,
+                        const void* const* pools, const int* pool_len, double seconds, uint64_t seed,
+                        ccst_server_stats* out);
+
+/* Stop the worker after the admitted frames complete, and free the server. NULL is a no-op. */
+void ccst_server_destroy(ccst_server* srv);
+
 /* Real-time reference (Sec. III B, Eq. (9)): start a filtered reference from frame 0.
  *   frame0_dev   device memory, one H x W frame of the context's in_dtype, rows
  *                pitch_elems apart (0 means W). Read during the call's stream work.

@@ -40,6 +40,12 @@ class ccst_roi(ctypes.Structure):
                 ("pitch_elems", ctypes.c_int64), ("ref_id", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class ccst_server_stats_t(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("mean_batch", ctypes.c_double), ("p50_us", ctypes.c_double),
+                ("p99_us", ctypes.c_double), ("max_us", ctypes.c_double), ("in_flight", ctypes.c_int64)]
+
+
 class ccst_params(ctypes.Structure):
     _fields_ = [("upsample", ctypes.c_int32), ("method", ctypes.c_int32), ("eps", ctypes.c_float),
                 ("in_dtype", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("max_H", ctypes.c_int32),
@@ -91,6 +97,18 @@ _SIGS = [
     ("ccst_add_reference", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_int)]),
     ("ccst_track_rois", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ccst_roi), ctypes.c_int64, ctypes.c_void_p]),
+    ("ccst_server_create", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_void_p)]),
+    ("ccst_server_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.POINTER(ctypes.c_uint64)]),
+    ("ccst_server_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_int)]),
+    ("ccst_server_read_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ccst_server_stats_t)]),
+    ("ccst_server_loadgen", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_void_p),
+                                           ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_uint64,
+                                           ctypes.POINTER(ccst_server_stats_t)]),
+    ("ccst_server_destroy", None, [ctypes.c_void_p]),
     ("ccst_rt_begin", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
                                      ctypes.c_double]),
     ("ccst_rt_track", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
@@ -229,6 +247,63 @@ def make_rois(frames, ref_ids) -> ctypes.Array:
 
 def ccst_track_rois(ctx, rois, n, out_dev) -> None:
     _check(lib().ccst_track_rois(ctx, rois, int(n), _ptr(out_dev)), ctx)
+
+
+def ccst_server_create(ctx, slots: int, max_batch: int):
+    out = ctypes.c_void_p()
+    _check(lib().ccst_server_create(ctx, int(slots), int(max_batch), ctypes.byref(out)), ctx)
+    return out.value
+
+
+def ccst_server_submit(srv, ref_id: int, frame_host, pitch_elems: int = 0, keep: bool = True):
+    """Submit one host frame (numpy); returns the ticket (keep) or None. Raises CcstError
+    (E_BUSY when no slot is free)."""
+    t = ctypes.c_uint64()
+    rc = lib().ccst_server_submit(srv, int(ref_id), _ptr(frame_host), int(pitch_elems),
+                                  ctypes.byref(t) if keep else None)
+    if rc != OK:
+        raise CcstError(rc, "ccst_server_submit")
+    return t.value if keep else None
+
+
+def ccst_server_poll(srv, ticket: int, timeout_us: int):
+    """The record (RESULT_DTYPE) of a finished ticket, or None on timeout."""
+    rec = np.zeros(1, dtype=RESULT_DTYPE)
+    done = ctypes.c_int()
+    rc = lib().ccst_server_poll(srv, ctypes.c_uint64(ticket), int(timeout_us), rec.ctypes.data, ctypes.byref(done))
+    if rc == E_TIMEOUT:
+        return None
+    if rc != OK:
+        raise CcstError(rc, "ccst_server_poll")
+    return rec[0]
+
+
+def ccst_server_read_stats(srv, reset: bool = False) -> dict:
+    st = ccst_server_stats_t()
+    rc = lib().ccst_server_read_stats(srv, int(reset), ctypes.byref(st))
+    if rc != OK:
+        raise CcstError(rc, "ccst_server_read_stats")
+    return {k: getattr(st, k) for k, _ in st._fields_}
+
+
+def ccst_server_loadgen(srv, ref_ids, rates_hz, pools, seconds: float, seed: int = 0) -> dict:
+    """Offered load from one host thread per camera; pools[k] is a contiguous numpy array
+    (n_k, H_k, W_k) of camera k's frames in the context's dtype."""
+    n = len(ref_ids)
+    pools = [np.ascontiguousarray(p) for p in pools]
+    st = ccst_server_stats_t()
+    rc = lib().ccst_server_loadgen(srv, n, (ctypes.c_int * n)(*ref_ids), (ctypes.c_double * n)(*rates_hz),
+                                   (ctypes.c_void_p * n)(*[p.ctypes.data for p in pools]),
+                                   (ctypes.c_int * n)(*[p.shape[0] for p in pools]), float(seconds),
+                                   ctypes.c_uint64(seed), ctypes.byref(st))
+    if rc != OK:
+        raise CcstError(rc, "ccst_server_loadgen")
+    return {k: getattr(st, k) for k, _ in st._fields_}
+
+
+def ccst_server_destroy(srv) -> None:
+    if srv:
+        lib().ccst_server_destroy(srv)
 
 
 def ccst_rt_begin(ctx, frame0_dev, pitch_elems, a0, b1) -> None:

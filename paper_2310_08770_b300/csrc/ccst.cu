@@ -1,6 +1,11 @@
 // ccst.cu -- the C ABI of libccst (declared in include/ccst.h): context set-up,
 // launches, CUDA-graph replay of batches and the serving tickets.
 #include <algorithm>
+#include <condition_variable>
+#include <deque>
+#include <random>
+#include <unordered_map>
+#include <atomic>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -1602,6 +1607,31 @@ static int rois_upload(ccst_ctx* c) {
     return CCST_OK;
 }
 
+// Sort items largest first (the longest work starts first; size classes stay contiguous),
+// copy them to items_dev (n slots) and launch the ROI kernel on `stream` with `counter`.
+// The host items must stay valid until the copy has been issued (it is staged at once).
+static int rois_launch(ccst_ctx* c, RoiItem* items, int64_t n, Result* out, cudaStream_t stream, RoiItem* items_dev,
+                       unsigned* counter) {
+    std::stable_sort(items, items + n, [&](const RoiItem& a, const RoiItem& b) {
+        return c->plans[a.cls].g.H > c->plans[b.cls].g.H;
+    });
+    int rc = rois_upload(c);
+    if (rc) return rc;
+    CK(c, cudaMemcpyAsync(items_dev, items, (size_t)n * sizeof(RoiItem), cudaMemcpyHostToDevice, stream));
+    CK(c, cudaMemsetAsync(counter, 0, sizeof(unsigned), stream));
+    RoiBatch rb;
+    rb.items = items_dev;
+    rb.n = n;
+    rb.geoms = c->d_geoms;
+    rb.refs = c->d_refs;
+    rb.out = out;
+    rb.next = counter;
+    const int grid = (int)(n < c->rois_grid ? n : c->rois_grid);
+    void* args[] = {&rb};
+    CK(c, cudaLaunchKernel(track_rois_kernel_ptr(), dim3(grid), dim3(kThreads), args, c->rois_smem, stream));
+    return CCST_OK;
+}
+
 extern "C" int ccst_track_rois(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccst_result* out_dev) {
     int rc = check_ctx(c);
     if (rc) return rc;
@@ -1628,11 +1658,6 @@ extern "C" int ccst_track_rois(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccs
         it.vec_ok = ((uintptr_t)q.frame % 16 == 0) && ((size_t)pitch * elem % 16 == 0) ? 1 : 0;
         it.pad = 0;
     }
-    // largest ROIs first (longest work first balances the CTAs); size classes stay contiguous
-    std::stable_sort(c->h_items.begin(), c->h_items.end(), [&](const RoiItem& a, const RoiItem& b) {
-        return c->plans[a.cls].g.H > c->plans[b.cls].g.H;
-    });
-    if ((rc = rois_upload(c))) return rc;
     if (c->items_cap < (size_t)n) {
         if (c->d_items) cudaFree(c->d_items);
         c->d_items = nullptr;
@@ -1640,21 +1665,347 @@ extern "C" int ccst_track_rois(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccs
         CK(c, cudaMalloc(&c->d_items, (size_t)n * sizeof(RoiItem)));
         c->items_cap = (size_t)n;
     }
-    CK(c, cudaMemcpyAsync(c->d_items, c->h_items.data(), (size_t)n * sizeof(RoiItem), cudaMemcpyHostToDevice,
-                          c->stream));
-    unsigned* counter = c->d_next + 16;
-    CK(c, cudaMemsetAsync(counter, 0, sizeof(unsigned), c->stream));
-    RoiBatch rb;
-    rb.items = c->d_items;
-    rb.n = n;
-    rb.geoms = c->d_geoms;
-    rb.refs = c->d_refs;
-    rb.out = (Result*)out_dev;
-    rb.next = counter;
-    const int grid = (int)(n < c->rois_grid ? n : c->rois_grid);
-    void* args[] = {&rb};
-    CK(c, cudaLaunchKernel(track_rois_kernel_ptr(), dim3(grid), dim3(kThreads), args, c->rois_smem, c->stream));
+    return rois_launch(c, c->h_items.data(), n, (Result*)out_dev, c->stream, c->d_items, c->d_next + 16);
+}
+
+// ---------------------------------------------------------------------- serving
+// Continuous batching over the uneven-ROI kernel: clients submit single frames of any of
+// the context's references (cameras); a worker thread takes everything pending as one
+// batch, copies the frames into their device slots and launches one ROI kernel per batch,
+// up to kRing batches in flight on their own streams. Frame slots are device memory
+// reserved at creation; a submit without a free slot is refused (admission control).
+struct ccst_server {
+    static constexpr int kRing = 4;
+    struct Req {
+        int ref = 0, slot = 0;
+        uint64_t ticket = 0;
+        bool keep = false;
+        std::chrono::steady_clock::time_point t0;
+    };
+    struct InFlight {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        Result* d_out = nullptr;
+        Result* h_out = nullptr;
+        RoiItem* d_items = nullptr;
+        std::vector<RoiItem> items;
+        std::vector<Req> reqs;
+        bool busy = false;
+    };
+    ccst_ctx* c = nullptr;
+    int slots = 0, max_batch = 0;
+    size_t slot_bytes = 0, elem = 0;
+    char* d_frames = nullptr;
+    char* h_frames = nullptr;          // pinned staging, one slot per device slot
+    unsigned* d_counters = nullptr;    // one item counter per ring entry
+    InFlight ring[kRing];
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Req> pending;
+    std::vector<int> free_slots;
+    std::unordered_map<uint64_t, std::pair<bool, Result>> results;
+    uint64_t next_ticket = 1, submitted = 0, completed = 0, rejected = 0, batches = 0, batched = 0;
+    std::vector<float> lat_us;
+    int error = 0;
+    bool stop = false;
+    std::thread worker;
+};
+
+static void server_fail(ccst_server* s, int code) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (!s->error) s->error = code;
+    s->cv_done.notify_all();
+}
+
+// Retire the ring entry if its batch has finished (or `block`: wait for it).
+static bool server_retire(ccst_server* s, ccst_server::InFlight& b, bool block) {
+    if (!b.busy) return false;
+    const cudaError_t q = block ? cudaEventSynchronize(b.ev) : cudaEventQuery(b.ev);
+    if (q == cudaErrorNotReady) return false;
+    if (q != cudaSuccess) {
+        server_fail(s, CCST_E_CUDA);
+        return false;
+    }
+    const auto t1 = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (size_t i = 0; i < b.reqs.size(); ++i) {
+            const auto& r = b.reqs[i];
+            s->lat_us.push_back(std::chrono::duration<float, std::micro>(t1 - r.t0).count());
+            if (r.keep) s->results[r.ticket] = {true, b.h_out[i]};
+            s->free_slots.push_back(r.slot);
+            ++s->completed;
+        }
+    }
+    b.reqs.clear();
+    b.busy = false;
+    s->cv_done.notify_all();
+    return true;
+}
+
+static void server_loop(ccst_server* s) {
+    ccst_ctx* c = s->c;
+    int next = 0;
+    for (;;) {
+        bool any_busy = false;
+        for (auto& b : s->ring) {
+            server_retire(s, b, false);
+            any_busy |= b.busy;
+        }
+        ccst_server::InFlight& b = s->ring[next];
+        std::vector<ccst_server::Req> take;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            if (s->stop && s->pending.empty() && !any_busy) return;
+            if (s->error) {
+                if (s->stop) return;
+                s->cv_work.wait_for(lk, std::chrono::milliseconds(10));
+                continue;
+            }
+            if (!b.busy && !s->pending.empty()) {
+                const size_t m = std::min(s->pending.size(), (size_t)s->max_batch);
+                take.assign(s->pending.begin(), s->pending.begin() + m);
+                s->pending.erase(s->pending.begin(), s->pending.begin() + m);
+            } else if (!any_busy && s->pending.empty()) {
+                s->cv_work.wait_for(lk, std::chrono::milliseconds(10));
+                continue;
+            }
+        }
+        if (take.empty()) {
+            if (b.busy) server_retire(s, b, true);      // the ring is full: wait for its oldest
+            else std::this_thread::yield();
+            continue;
+        }
+        const int m = (int)take.size();
+        b.items.resize(m);
+        bool ok = true;
+        for (int i = 0; i < m && ok; ++i) {
+            const auto& r = take[i];
+            const Geom& pg = c->plans[c->refs[r.ref].cls].g;
+            char* d = s->d_frames + (size_t)r.slot * s->slot_bytes;
+            ok = cudaMemcpyAsync(d, s->h_frames + (size_t)r.slot * s->slot_bytes, (size_t)pg.H * pg.W * s->elem,
+                                 cudaMemcpyHostToDevice, b.st) == cudaSuccess;
+            b.items[i] = RoiItem{d, (long long)pg.W, i, c->refs[r.ref].cls, r.ref, 1, 0};
+        }
+        // the kernel writes record i of the batch to d_out[i]; out_index survives the sort
+        ok = ok && rois_launch(c, b.items.data(), m, b.d_out, b.st, b.d_items, s->d_counters + next) == CCST_OK;
+        ok = ok && cudaMemcpyAsync(b.h_out, b.d_out, (size_t)m * sizeof(Result), cudaMemcpyDeviceToHost, b.st) ==
+                       cudaSuccess;
+        ok = ok && cudaEventRecord(b.ev, b.st) == cudaSuccess;
+        if (!ok) {
+            server_fail(s, CCST_E_CUDA);
+            continue;
+        }
+        b.reqs = std::move(take);
+        b.busy = true;
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            ++s->batches;
+            s->batched += (uint64_t)m;
+        }
+        next = (next + 1) % ccst_server::kRing;
+    }
+}
+
+static void server_free(ccst_server* s) {
+    for (auto& b : s->ring) {
+        if (b.st) cudaStreamSynchronize(b.st);
+        if (b.ev) cudaEventDestroy(b.ev);
+        if (b.st) cudaStreamDestroy(b.st);
+        if (b.d_out) cudaFree(b.d_out);
+        if (b.h_out) cudaFreeHost(b.h_out);
+        if (b.d_items) cudaFree(b.d_items);
+    }
+    if (s->d_frames) cudaFree(s->d_frames);
+    if (s->h_frames) cudaFreeHost(s->h_frames);
+    if (s->d_counters) cudaFree(s->d_counters);
+}
+
+extern "C" int ccst_server_create(ccst_ctx* c, int slots, int max_batch, ccst_server** out) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!out || slots < 1 || max_batch < 1) return fail(c, CCST_E_INVALID, "ccst_server_create: bad arguments");
+    *out = nullptr;
+    rois_init(c);
+    if ((rc = rois_upload(c))) return rc;
+    ccst_server* s = new (std::nothrow) ccst_server();
+    if (!s) return fail(c, CCST_E_NOMEM, "ccst_server_create: host allocation failed");
+    s->c = c;
+    s->slots = slots;
+    s->max_batch = std::min(max_batch, slots);
+    s->elem = c->p.in_dtype == CCST_U16 ? 2 : 4;
+    for (auto& re : c->refs)
+        if (re.cls >= 0) {
+            const Geom& pg = c->plans[re.cls].g;
+            s->slot_bytes = std::max(s->slot_bytes, ((size_t)pg.H * pg.W * s->elem + 255) & ~(size_t)255);
+        }
+    if (s->slot_bytes == 0) {
+        delete s;
+        return fail(c, CCST_E_INVALID, "ccst_server_create: no reference usable by ROI batches");
+    }
+    auto bad = [&](cudaError_t e) {
+        server_free(s);
+        delete s;
+        return fail(c, e == cudaErrorMemoryAllocation ? CCST_E_NOMEM : CCST_E_CUDA,
+                    std::string("ccst_server_create: ") + cudaGetErrorString(e));
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&s->d_frames, (size_t)slots * s->slot_bytes)) != cudaSuccess) return bad(e);
+    if ((e = cudaHostAlloc(&s->h_frames, (size_t)slots * s->slot_bytes, cudaHostAllocDefault)) != cudaSuccess)
+        return bad(e);
+    if ((e = cudaMalloc(&s->d_counters, ccst_server::kRing * sizeof(unsigned))) != cudaSuccess) return bad(e);
+    for (auto& b : s->ring) {
+        if ((e = cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking)) != cudaSuccess) return bad(e);
+        if ((e = cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming)) != cudaSuccess) return bad(e);
+        if ((e = cudaMalloc(&b.d_out, (size_t)s->max_batch * sizeof(Result))) != cudaSuccess) return bad(e);
+        if ((e = cudaHostAlloc(&b.h_out, (size_t)s->max_batch * sizeof(Result), cudaHostAllocDefault)) != cudaSuccess)
+            return bad(e);
+        if ((e = cudaMalloc(&b.d_items, (size_t)s->max_batch * sizeof(RoiItem))) != cudaSuccess) return bad(e);
+    }
+    for (int i = slots - 1; i >= 0; --i) s->free_slots.push_back(i);
+    s->worker = std::thread(server_loop, s);
+    *out = s;
     return CCST_OK;
+}
+
+extern "C" int ccst_server_submit(ccst_server* s, int ref_id, const void* frame_host, int64_t pitch_elems,
+                                  uint64_t* ticket) {
+    if (!s || !frame_host) return CCST_E_INVALID;
+    ccst_ctx* c = s->c;
+    if (ref_id < 0 || ref_id >= (int)c->refs.size() || c->refs[ref_id].cls < 0) return CCST_E_INVALID;
+    const Geom& pg = c->plans[c->refs[ref_id].cls].g;
+    if (pitch_elems == 0) pitch_elems = pg.W;
+    if (pitch_elems < pg.W) return CCST_E_INVALID;
+    ccst_server::Req r;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->error) return s->error;
+        if (s->free_slots.empty()) {
+            ++s->rejected;
+            return CCST_E_BUSY;
+        }
+        r.slot = s->free_slots.back();
+        s->free_slots.pop_back();
+    }
+    char* dst = s->h_frames + (size_t)r.slot * s->slot_bytes;
+    const size_t row = (size_t)pg.W * s->elem;
+    for (int y = 0; y < pg.H; ++y) std::memcpy(dst + y * row, (const char*)frame_host + (size_t)y * pitch_elems * s->elem, row);
+    r.ref = ref_id;
+    r.keep = ticket != nullptr;
+    r.t0 = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        r.ticket = s->next_ticket++;
+        if (r.keep) {
+            s->results[r.ticket] = {false, Result{}};
+            *ticket = r.ticket;
+        }
+        s->pending.push_back(r);
+        ++s->submitted;
+    }
+    s->cv_work.notify_one();
+    return CCST_OK;
+}
+
+extern "C" int ccst_server_poll(ccst_server* s, uint64_t ticket, int timeout_us, ccst_result* out, int* done) {
+    if (!s || !done) return CCST_E_INVALID;
+    *done = 0;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->results.find(ticket);
+    if (it == s->results.end()) return CCST_E_INVALID;
+    const auto until = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us > 0 ? timeout_us : 0);
+    while (!it->second.first && !s->error) {
+        if (s->cv_done.wait_until(lk, until) == std::cv_status::timeout) break;
+        it = s->results.find(ticket);
+    }
+    if (!it->second.first) return s->error ? s->error : CCST_E_TIMEOUT;
+    if (out) std::memcpy(out, &it->second.second, sizeof(Result));
+    s->results.erase(it);
+    *done = 1;
+    return CCST_OK;
+}
+
+extern "C" int ccst_server_read_stats(ccst_server* s, int reset, ccst_server_stats* out) {
+    if (!s || !out) return CCST_E_INVALID;
+    std::lock_guard<std::mutex> lk(s->mu);
+    out->submitted = s->submitted;
+    out->completed = s->completed;
+    out->rejected = s->rejected;
+    out->batches = s->batches;
+    out->mean_batch = s->batches ? (double)s->batched / (double)s->batches : 0.0;
+    std::vector<float> v = s->lat_us;
+    std::sort(v.begin(), v.end());
+    auto pct = [&](double q) { return v.empty() ? 0.0 : (double)v[std::min(v.size() - 1, (size_t)(q * v.size()))]; };
+    out->p50_us = pct(0.50);
+    out->p99_us = pct(0.99);
+    out->max_us = v.empty() ? 0.0 : (double)v.back();
+    out->in_flight = (int64_t)(s->submitted - s->completed);
+    if (reset) {
+        s->lat_us.clear();
+        s->submitted = s->completed = s->rejected = s->batches = s->batched = 0;
+    }
+    return s->error;
+}
+
+extern "C" void ccst_server_destroy(ccst_server* s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    server_free(s);
+    delete s;
+}
+
+// Offered-load generator for measuring the server: one host thread per camera submits frames
+// of its pool (cycled) at exponential inter-arrival times of mean 1/rate for `seconds`,
+// without tickets (results are counted, not kept); refused submits are counted and dropped.
+// Then it waits for all admitted frames and reports the server's statistics.
+extern "C" int ccst_server_loadgen(ccst_server* s, int ncams, const int* ref_ids, const double* rates_hz,
+                                   const void* const* pools, const int* pool_len, double seconds, uint64_t seed,
+                                   ccst_server_stats* out) {
+    if (!s || ncams < 1 || !ref_ids || !rates_hz || !pools || !pool_len || !(seconds > 0) || !out)
+        return CCST_E_INVALID;
+    ccst_server_stats dummy;
+    ccst_server_read_stats(s, 1, &dummy);
+    std::atomic<int> err{0};
+    std::vector<std::thread> th;
+    const auto t_start = std::chrono::steady_clock::now() + std::chrono::milliseconds(5);
+    for (int k = 0; k < ncams; ++k) {
+        th.emplace_back([&, k]() {
+            std::mt19937_64 rng(seed + 7919u * (uint64_t)k);
+            std::exponential_distribution<double> gap(rates_hz[k]);
+            const Geom& pg = s->c->plans[s->c->refs[ref_ids[k]].cls].g;
+            const size_t fb = (size_t)pg.H * pg.W * s->elem;
+            double t = 0.0;
+            for (int64_t i = 0;; ++i) {
+                t += gap(rng);
+                if (t >= seconds) break;
+                const auto at = t_start + std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                                              std::chrono::duration<double>(t));
+                while (std::chrono::steady_clock::now() < at) {
+                }
+                const char* f = (const char*)pools[k] + (size_t)(i % pool_len[k]) * fb;
+                const int rc = ccst_server_submit(s, ref_ids[k], f, 0, nullptr);
+                if (rc && rc != CCST_E_BUSY) {
+                    err = rc;
+                    return;
+                }
+            }
+        });
+    }
+    for (auto& t : th) t.join();
+    for (int it = 0; it < 200000; ++it) {                   // drain: admitted frames finish
+        ccst_server_stats st;
+        const int rc = ccst_server_read_stats(s, 0, &st);
+        if (rc) return rc;
+        if (st.in_flight == 0) break;
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    const int rc = ccst_server_read_stats(s, 0, out);
+    return err ? (int)err : rc;
 }
 
 // Grid size M of the refinement square for this context (tests and bindings).

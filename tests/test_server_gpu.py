@@ -1,0 +1,153 @@
+"""Serving (ccst_server_*): continuous batching of single frames from several cameras of
+different sizes. Each result must be the same alone and in the mix; admission refuses
+frames when the device slots are full; the load generator accounts for every frame."""
+import threading
+
+import numpy as np
+import pytest
+
+from paper_2310_08770_b300 import ccst as C
+from paper_2310_08770_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    if not _t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_08770_b300 import build
+    build.build()
+    return _t
+
+
+def cameras(seed=0, sides=(64, 128, 32), n=24):
+    rng = np.random.default_rng(seed)
+    cams = []
+    for N in sides:
+        ref = synth.gaussian_spot(N, N, N / 2, N / 2, 3.0, 2000.0, 20.0).astype(np.float32)
+        d = rng.uniform(-3, 3, size=(n, 2))
+        frames = np.array([rng.poisson(synth.gaussian_spot(N, N, N / 2 + p[0], N / 2 + p[1], 3.0, 2000.0, 20.0))
+                           for p in d]).astype(np.uint16)
+        cams.append((ref, frames))
+    return cams
+
+
+def make_server(cams, slots=64, max_batch=64):
+    t = C.Tracker(cams[0][0], upsample=100, in_dtype="u16")
+    ids = [0] + [C.ccst_add_reference(t.ctx, ref, *ref.shape) for ref, _ in cams[1:]]
+    srv = C.ccst_server_create(t.ctx, slots, max_batch)
+    return t, ids, srv
+
+
+def submit_wait(srv, ref_id, frame):
+    while True:
+        try:
+            return C.ccst_server_submit(srv, ref_id, frame)
+        except C.CcstError as e:
+            if e.code != C.E_BUSY:
+                raise
+
+
+def test_each_result_is_the_same_alone_and_in_the_mix(torch):
+    cams = cameras()
+    t, ids, srv = make_server(cams)
+    try:
+        alone = {}
+        for k, (_, frames) in enumerate(cams):
+            for i in range(len(frames)):
+                tk = C.ccst_server_submit(srv, ids[k], frames[i])
+                alone[(k, i)] = C.ccst_server_poll(srv, tk, 5_000_000).tobytes()
+        # the mix: three client threads, one per camera, each frame submitted three times
+        got = {}
+        lock = threading.Lock()
+
+        def client(k):
+            frames = cams[k][1]
+            tickets = [(i, submit_wait(srv, ids[k], frames[i])) for _ in range(3) for i in range(len(frames))]
+            for i, tk in tickets:
+                r = C.ccst_server_poll(srv, tk, 5_000_000)
+                with lock:
+                    got.setdefault((k, i), []).append(r.tobytes())
+        th = [threading.Thread(target=client, args=(k,)) for k in range(len(cams))]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
+        assert set(got) == set(alone)
+        for key, rs in got.items():
+            assert len(rs) == 3 and all(r == alone[key] for r in rs), key
+        st = C.ccst_server_read_stats(srv)
+        assert st["completed"] == st["submitted"] and st["in_flight"] == 0
+        assert st["mean_batch"] > 1.0                  # the mix was batched
+    finally:
+        C.ccst_server_destroy(srv)
+        t.close()
+
+
+def test_result_equals_the_context_path(torch):
+    cams = cameras(seed=1, sides=(64, 128), n=6)
+    t, ids, srv = make_server(cams)
+    try:
+        for k, (ref, frames) in enumerate(cams):
+            single = C.Tracker(ref, upsample=100, in_dtype="u16", max_batch=len(frames))
+            out = single.empty_results(len(frames))
+            C.ccst_track(single.ctx, torch.from_numpy(frames.view(np.int16)).cuda().view(torch.uint16),
+                         len(frames), 0, out)
+            C.ccst_sync(single.ctx)
+            want = C.decode(out)
+            single.close()
+            for i in range(len(frames)):
+                r = C.ccst_server_poll(srv, C.ccst_server_submit(srv, ids[k], frames[i]), 5_000_000)
+                assert r.tobytes() == want[i].tobytes()
+    finally:
+        C.ccst_server_destroy(srv)
+        t.close()
+
+
+def test_admission_refuses_when_slots_are_full(torch):
+    cams = cameras(seed=2, sides=(128,), n=8)
+    t, ids, srv = make_server(cams, slots=2, max_batch=2)
+    try:
+        tickets, refused = [], 0
+        for i in range(400):
+            try:
+                tickets.append(C.ccst_server_submit(srv, 0, cams[0][1][i % 8]))
+            except C.CcstError as e:
+                assert e.code == C.E_BUSY
+                refused += 1
+        for tk in tickets:
+            assert C.ccst_server_poll(srv, tk, 5_000_000) is not None
+        st = C.ccst_server_read_stats(srv)
+        assert refused > 0 and st["rejected"] == refused and st["completed"] == len(tickets)
+    finally:
+        C.ccst_server_destroy(srv)
+        t.close()
+
+
+def test_loadgen_accounts_for_every_frame(torch):
+    cams = cameras(seed=3, sides=(64, 128, 32), n=16)
+    t, ids, srv = make_server(cams, slots=256, max_batch=256)
+    try:
+        st = C.ccst_server_loadgen(srv, ids, [2000.0, 5000.0, 10000.0], [f for _, f in cams], 0.3, seed=4)
+        assert st["in_flight"] == 0 and st["completed"] == st["submitted"] and st["submitted"] > 3000
+        assert 0 < st["p50_us"] <= st["p99_us"] <= st["max_us"]
+    finally:
+        C.ccst_server_destroy(srv)
+        t.close()
+
+
+def test_server_errors(torch):
+    cams = cameras(seed=5, sides=(32,), n=2)
+    t, ids, srv = make_server(cams, slots=4, max_batch=4)
+    try:
+        with pytest.raises(C.CcstError):
+            C.ccst_server_submit(srv, 9, cams[0][1][0])          # unknown camera
+        with pytest.raises(C.CcstError):
+            C.ccst_server_poll(srv, 123456, 10)                   # unknown ticket
+        tk = C.ccst_server_submit(srv, 0, cams[0][1][0])
+        assert C.ccst_server_poll(srv, tk, 5_000_000) is not None
+    finally:
+        C.ccst_server_destroy(srv)
+        t.close()
