@@ -527,6 +527,37 @@ def rois_cpu_baseline(r, res):
             {"rois": k, "mismatches": mism, "tolerance_px": 1e-3})
 
 
+SERVE_SIDES = (64, 64, 128, 128, 128, 64, 128, 128)   # stand-ins for 64, 96, 128, 192, 256, 64, 128, 256
+SERVE_RATES_HZ = (1e3, 2e3, 5e3, 10e3, 20e3, 50e3, 100e3, 100e3)
+SERVE_POOL = 512
+SERVE_SECONDS = 5.0
+
+
+def serving_leg(C, torch):
+    """8 simulated cameras at Poisson rates of 1-100 kHz for SERVE_SECONDS through one server
+    (continuous batching over the uneven-ROI kernel); host-clock submit-to-result latency."""
+    from paper_2310_08770_b300 import synth
+    pools = [synth.camera_pool(seed=k, n=SERVE_POOL, N=N) for k, N in enumerate(SERVE_SIDES)]
+    t = C.Tracker(pools[0][0], upsample=U, method="ccu", in_dtype="u16")
+    ids = [0] + [C.ccst_add_reference(t.ctx, ref, ref.shape[0], ref.shape[1]) for ref, _ in pools[1:]]
+    srv = C.ccst_server_create(t.ctx, 4096, 1024)
+    try:
+        C.ccst_server_loadgen(srv, ids, SERVE_RATES_HZ, [f for _, f in pools], 0.2, seed=99)     # warm-up
+        st = C.ccst_server_loadgen(srv, ids, SERVE_RATES_HZ, [f for _, f in pools], SERVE_SECONDS, seed=0)
+    finally:
+        C.ccst_server_destroy(srv)
+        t.close()
+    return {"workload": f"8 cameras, sides {list(SERVE_SIDES)} (stand-ins for 64, 96, 128, 192, 256, 64, 128, 256), "
+                        f"uint16 spot frames (sigma 3, peak 2000, bg 20, shifts U(-3,3)^2), pools of {SERVE_POOL} "
+                        f"frames, Poisson arrivals at {[int(r) for r in SERVE_RATES_HZ]} Hz for {SERVE_SECONDS} s, "
+                        "u=100, CC-U; 4096 device slots, batches of up to 1024",
+            "offered_hz": sum(SERVE_RATES_HZ), "value": st["completed"] / SERVE_SECONDS, "unit": "frames/s",
+            "p50_us": st["p50_us"], "p99_us": st["p99_us"], "max_us": st["max_us"],
+            "submitted": st["submitted"], "rejected": st["rejected"], "batches": st["batches"],
+            "mean_batch": st["mean_batch"],
+            "latency": "host clock, submit call to the worker seeing the batch's completion event"}
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -661,6 +692,8 @@ def run_ours(args):
         line["realtime"] = rt_line
     if rank == 0 and not args.no_offline:
         line["offline"] = offline_leg(C, torch, s, frames_dev, n_frames, stream)
+    if rank == 0 and not args.no_serving:
+        line["serving"] = serving_leg(C, torch)
     rois_extra = None
     if rank == 0 and not args.no_rois:
         line["rois"], rois_extra = rois_leg(C, torch, stream)
@@ -769,6 +802,7 @@ def main():
     ap.add_argument("--no-offline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-rois", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--rt-frames", type=int, default=RT_FRAMES)
     ap.add_argument("--frames", type=int, default=N_FRAMES,
                     help="frames of the stream to stage (the workload is 10000; smaller only for profiler captures)")

@@ -217,8 +217,10 @@ int ccst_track_rois(ccst_ctx* ctx, const ccst_roi* rois, int64_t n, ccst_result*
  *
  * A server runs a worker thread over a context. Each camera is a reference of the
  * context (id 0 or from ccst_add_reference): its frames have that reference's size. A
- * submitted frame is copied into one of `slots` device slots reserved at creation; a
- * submit without a free slot is refused with CCST_E_BUSY (admission by device memory).
+ * submitted frame is copied into one of `slots` frame slots reserved at creation (pinned
+ * host memory mapped into the device's address space: the kernel reads each frame in
+ * place, with no per-frame copy); a submit without a free slot is refused with
+ * CCST_E_BUSY (admission by reserved memory).
  * The worker takes everything pending (up to max_batch frames, any cameras and sizes) as
  * one ccst_track_rois batch on its own stream, with up to 4 batches in flight, so frames
  * that arrive while others run are admitted as slots free up and their work overlaps on

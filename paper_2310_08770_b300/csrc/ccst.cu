@@ -1671,9 +1671,11 @@ extern "C" int ccst_track_rois(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccs
 // ---------------------------------------------------------------------- serving
 // Continuous batching over the uneven-ROI kernel: clients submit single frames of any of
 // the context's references (cameras); a worker thread takes everything pending as one
-// batch, copies the frames into their device slots and launches one ROI kernel per batch,
-// up to kRing batches in flight on their own streams. Frame slots are device memory
-// reserved at creation; a submit without a free slot is refused (admission control).
+// batch and launches one ROI kernel per batch, up to kRing batches in flight on their own
+// streams. Frame slots are pinned host memory mapped into the device's address space,
+// reserved at creation: the submit copies a frame into its slot and the kernel reads it in
+// place, so the worker issues no per-frame copy. A submit without a free slot is refused
+// (admission control).
 struct ccst_server {
     static constexpr int kRing = 4;
     struct Req {
@@ -1688,15 +1690,15 @@ struct ccst_server {
         Result* d_out = nullptr;
         Result* h_out = nullptr;
         RoiItem* d_items = nullptr;
-        std::vector<RoiItem> items;
+        RoiItem* h_items = nullptr;    // pinned, so the item upload is asynchronous
         std::vector<Req> reqs;
         bool busy = false;
     };
     ccst_ctx* c = nullptr;
     int slots = 0, max_batch = 0;
     size_t slot_bytes = 0, elem = 0;
-    char* d_frames = nullptr;
-    char* h_frames = nullptr;          // pinned staging, one slot per device slot
+    char* h_frames = nullptr;          // pinned, mapped: slot i at h_frames + i * slot_bytes
+    char* d_frames = nullptr;          // the same memory as the device addresses it
     unsigned* d_counters = nullptr;    // one item counter per ring entry
     InFlight ring[kRing];
     std::mutex mu;
@@ -1777,18 +1779,15 @@ static void server_loop(ccst_server* s) {
             continue;
         }
         const int m = (int)take.size();
-        b.items.resize(m);
         bool ok = true;
-        for (int i = 0; i < m && ok; ++i) {
+        for (int i = 0; i < m; ++i) {
             const auto& r = take[i];
             const Geom& pg = c->plans[c->refs[r.ref].cls].g;
-            char* d = s->d_frames + (size_t)r.slot * s->slot_bytes;
-            ok = cudaMemcpyAsync(d, s->h_frames + (size_t)r.slot * s->slot_bytes, (size_t)pg.H * pg.W * s->elem,
-                                 cudaMemcpyHostToDevice, b.st) == cudaSuccess;
-            b.items[i] = RoiItem{d, (long long)pg.W, i, c->refs[r.ref].cls, r.ref, 1, 0};
+            b.h_items[i] = RoiItem{s->d_frames + (size_t)r.slot * s->slot_bytes, (long long)pg.W, i, c->refs[r.ref].cls,
+                                   r.ref, 1, 0};
         }
         // the kernel writes record i of the batch to d_out[i]; out_index survives the sort
-        ok = ok && rois_launch(c, b.items.data(), m, b.d_out, b.st, b.d_items, s->d_counters + next) == CCST_OK;
+        ok = rois_launch(c, b.h_items, m, b.d_out, b.st, b.d_items, s->d_counters + next) == CCST_OK;
         ok = ok && cudaMemcpyAsync(b.h_out, b.d_out, (size_t)m * sizeof(Result), cudaMemcpyDeviceToHost, b.st) ==
                        cudaSuccess;
         ok = ok && cudaEventRecord(b.ev, b.st) == cudaSuccess;
@@ -1815,8 +1814,8 @@ static void server_free(ccst_server* s) {
         if (b.d_out) cudaFree(b.d_out);
         if (b.h_out) cudaFreeHost(b.h_out);
         if (b.d_items) cudaFree(b.d_items);
+        if (b.h_items) cudaFreeHost(b.h_items);
     }
-    if (s->d_frames) cudaFree(s->d_frames);
     if (s->h_frames) cudaFreeHost(s->h_frames);
     if (s->d_counters) cudaFree(s->d_counters);
 }
@@ -1850,9 +1849,9 @@ extern "C" int ccst_server_create(ccst_ctx* c, int slots, int max_batch, ccst_se
                     std::string("ccst_server_create: ") + cudaGetErrorString(e));
     };
     cudaError_t e;
-    if ((e = cudaMalloc(&s->d_frames, (size_t)slots * s->slot_bytes)) != cudaSuccess) return bad(e);
-    if ((e = cudaHostAlloc(&s->h_frames, (size_t)slots * s->slot_bytes, cudaHostAllocDefault)) != cudaSuccess)
+    if ((e = cudaHostAlloc(&s->h_frames, (size_t)slots * s->slot_bytes, cudaHostAllocMapped)) != cudaSuccess)
         return bad(e);
+    if ((e = cudaHostGetDevicePointer((void**)&s->d_frames, s->h_frames, 0)) != cudaSuccess) return bad(e);
     if ((e = cudaMalloc(&s->d_counters, ccst_server::kRing * sizeof(unsigned))) != cudaSuccess) return bad(e);
     for (auto& b : s->ring) {
         if ((e = cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking)) != cudaSuccess) return bad(e);
@@ -1861,6 +1860,8 @@ extern "C" int ccst_server_create(ccst_ctx* c, int slots, int max_batch, ccst_se
         if ((e = cudaHostAlloc(&b.h_out, (size_t)s->max_batch * sizeof(Result), cudaHostAllocDefault)) != cudaSuccess)
             return bad(e);
         if ((e = cudaMalloc(&b.d_items, (size_t)s->max_batch * sizeof(RoiItem))) != cudaSuccess) return bad(e);
+        if ((e = cudaHostAlloc(&b.h_items, (size_t)s->max_batch * sizeof(RoiItem), cudaHostAllocDefault)) != cudaSuccess)
+            return bad(e);
     }
     for (int i = slots - 1; i >= 0; --i) s->free_slots.push_back(i);
     s->worker = std::thread(server_loop, s);

@@ -185,3 +185,15 @@ def uneven_rois(seed: int = 0, n: int = 4096, sides=(32, 64, 128)) -> UnevenRois
         frames.append(poisson_frame(rng, gaussian_spot(N, N, N / 2.0 + dy, N / 2.0 + dx, sigma, amp, bg))
                       .astype(np.float32))
     return UnevenRois(refs, frames, d)
+
+
+def camera_pool(seed: int, n: int, N: int, sigma: float = 3.0, amplitude: float = 2000.0,
+                background: float = 20.0, spread: float = 3.0):
+    """One simulated camera: noise-free reference at the centre and n uint16 Poisson frames
+    of the spot moved by (dx, dy) uniform in [-spread, spread]. Draws: shifts, then noise."""
+    rng = np.random.default_rng(seed)
+    d = rng.uniform(-spread, spread, size=(n, 2))
+    ref = gaussian_spot(N, N, N / 2.0, N / 2.0, sigma, amplitude, background).astype(np.float32)
+    frames = np.array([poisson_frame(rng, gaussian_spot(N, N, N / 2.0 + p[1], N / 2.0 + p[0], sigma, amplitude,
+                                                        background)) for p in d]).astype(np.uint16)
+    return ref, frames
