@@ -460,12 +460,12 @@ ROIS_REPS = 10
 ROIS_ORACLE = 48
 
 
-def rois_leg(C, torch, stream):
+def rois_leg(C, torch, stream, n_rois=ROIS_N):
     """Uneven batch: 4096 FP32 ROIs of mixed sizes, each against its own reference, in one
     persistent launch (ccst_track_rois), against the same ROIs as one launch each."""
     import ctypes
     from paper_2310_08770_b300 import synth
-    r = synth.uneven_rois(seed=0, n=ROIS_N, sides=ROIS_SIDES)
+    r = synth.uneven_rois(seed=0, n=n_rois, sides=ROIS_SIDES)
     n = len(r.frames)
     t = C.Tracker(r.refs[0], upsample=U, method="ccu", in_dtype="f32", stream=stream)
     t0 = time.perf_counter()
@@ -696,7 +696,7 @@ def run_ours(args):
         line["serving"] = serving_leg(C, torch)
     rois_extra = None
     if rank == 0 and not args.no_rois:
-        line["rois"], rois_extra = rois_leg(C, torch, stream)
+        line["rois"], rois_extra = rois_leg(C, torch, stream, args.rois_n)
     adj_extra = None
     if rank == 0 and not args.no_adjoint:
         line["adjoint"], adj_extra = adjoint_leg(C, torch, stream)
@@ -803,6 +803,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-rois", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--rois-n", type=int, default=ROIS_N)
     ap.add_argument("--rt-frames", type=int, default=RT_FRAMES)
     ap.add_argument("--frames", type=int, default=N_FRAMES,
                     help="frames of the stream to stage (the workload is 10000; smaller only for profiler captures)")
