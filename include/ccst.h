@@ -65,7 +65,9 @@ extern "C" {
 
 /* ccst_params.flags */
 #define CCST_FLAG_TIE_GUARD 0x1u  /* resolve near-ties of the FP32 surfaces in higher precision (default on) */
-#define CCST_FLAG_GRAPHS    0x2u  /* ccst_track replays one captured CUDA graph per (frames, n, pitch, out) */
+#define CCST_FLAG_GRAPHS    0x2u  /* ccst_track replays one captured CUDA graph per (frames, n, pitch, out);
+                                      each graph has its own frame counter, so graphs of different
+                                      batches may run at once on different streams (ccst_set_stream) */
 #define CCST_FLAG_PROFILE   0x4u  /* record CUDA events around each launch of the tracking kernel */
 
 /* ccst_result.flags (per frame) */

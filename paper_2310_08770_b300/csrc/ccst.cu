@@ -591,10 +591,13 @@ struct ccst_ctx {
     void* d_addref_tmp = nullptr;     // ccst_add_reference: reference copy and FFT workspace
     size_t addref_tmp_bytes = 0;
     // graphs keyed by (frames, n, pitch, out), each with its own profiling event pair
+    // and its own frame counter, so graphs of different batches can run at once on
+    // different streams
     struct GraphEntry {
         cudaGraphExec_t exec = nullptr;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
     };
+    unsigned* d_graph_counters = nullptr;   // kMaxGraphs counters, one per captured graph
     std::map<std::tuple<const void*, long long, long long, void*>, GraphEntry> graphs;
     // profiling ring for direct launches
     std::vector<cudaEvent_t> prof0, prof1;
@@ -669,7 +672,8 @@ static void free_all(ccst_ctx* c) {
     c->refs.clear();
     void* ptrs[] = {c->d_ref32, c->d_b64, c->d_FE64, c->d_FE32, c->d_tw64, c->d_tw32,
                     c->d_tab,   c->d_df,  c->d_frames, c->d_out, c->d_next, c->d_rtE, c->d_rtY, c->d_rtSync,
-                    c->d_offPart, c->d_offScratch, c->d_adjY, c->d_geoms, c->d_refs, c->d_items, c->d_addref_tmp};
+                    c->d_offPart, c->d_offScratch, c->d_adjY, c->d_geoms, c->d_refs, c->d_items, c->d_addref_tmp,
+                    c->d_graph_counters};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -819,7 +823,7 @@ extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pi
     return CCST_OK;
 }
 
-static int launch(ccst_ctx* c, const Batch& b, bool reset_counter = true) {
+static int launch(ccst_ctx* c, const Batch& b, bool reset_counter = true, unsigned* counter = nullptr) {
     if (b.n == 0) return CCST_OK;
     const int grid = (int)(b.n < c->grid_main ? b.n : c->grid_main);
     const bool prof = (c->p.flags & CCST_FLAG_PROFILE) != 0;
@@ -839,8 +843,8 @@ static int launch(ccst_ctx* c, const Batch& b, bool reset_counter = true) {
     {
         Geom gk = c->g;
         Batch bk = b;
-        bk.next = c->d_next;
-        if (reset_counter) CK(c, cudaMemsetAsync(c->d_next, 0, sizeof(unsigned), c->stream));
+        bk.next = counter ? counter : c->d_next;
+        if (reset_counter) CK(c, cudaMemsetAsync(bk.next, 0, sizeof(unsigned), c->stream));
         void* args[] = {&gk, &bk};
         CK(c, cudaLaunchKernel(c->kernel, dim3(grid), dim3(kThreads), args, c->smem, c->stream));
     }
@@ -903,6 +907,8 @@ extern "C" int ccst_track(ccst_ctx* c, const void* frames_dev, int64_t n, int64_
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
         if (c->graphs.size() >= kMaxGraphs) drop_graphs(c);
+        if (!c->d_graph_counters) CK(c, cudaMalloc(&c->d_graph_counters, kMaxGraphs * sizeof(unsigned)));
+        unsigned* counter = c->d_graph_counters + c->graphs.size();
         ccst_ctx::GraphEntry ent;
         if (c->p.flags & CCST_FLAG_PROFILE) {
             CK(c, cudaEventCreate(&ent.e0));
@@ -913,7 +919,7 @@ extern "C" int ccst_track(ccst_ctx* c, const void* frames_dev, int64_t n, int64_
         c->capturing = true;
         c->cap_e0 = ent.e0;
         c->cap_e1 = ent.e1;
-        const int lrc = launch(c, b);
+        const int lrc = launch(c, b, true, counter);
         c->capturing = false;
         cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
         if (lrc) return lrc;
