@@ -598,6 +598,10 @@ struct ccst_ctx {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
     };
     unsigned* d_graph_counters = nullptr;   // kMaxGraphs counters, one per captured graph
+    // direct launches take counters from a ring of kTickets, so launches on different
+    // streams do not share one (d_next stays the real-time path's counter)
+    unsigned* d_launch_counters = nullptr;
+    unsigned launch_seq = 0;
     std::map<std::tuple<const void*, long long, long long, void*>, GraphEntry> graphs;
     // profiling ring for direct launches
     std::vector<cudaEvent_t> prof0, prof1;
@@ -673,7 +677,7 @@ static void free_all(ccst_ctx* c) {
     void* ptrs[] = {c->d_ref32, c->d_b64, c->d_FE64, c->d_FE32, c->d_tw64, c->d_tw32,
                     c->d_tab,   c->d_df,  c->d_frames, c->d_out, c->d_next, c->d_rtE, c->d_rtY, c->d_rtSync,
                     c->d_offPart, c->d_offScratch, c->d_adjY, c->d_geoms, c->d_refs, c->d_items, c->d_addref_tmp,
-                    c->d_graph_counters};
+                    c->d_graph_counters, c->d_launch_counters};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -758,6 +762,7 @@ extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pi
         {(void**)&c->d_frames, (size_t)p.max_batch * HW * elem},
         {(void**)&c->d_out, (size_t)p.max_batch * sizeof(Result)},
         {(void**)&c->d_next, 256},
+        {(void**)&c->d_launch_counters, kTickets * sizeof(unsigned)},
     };
     for (auto& a : allocs) {
         if ((e = cudaMalloc(a.ptr, a.bytes)) != cudaSuccess) {
@@ -843,7 +848,8 @@ static int launch(ccst_ctx* c, const Batch& b, bool reset_counter = true, unsign
     {
         Geom gk = c->g;
         Batch bk = b;
-        bk.next = counter ? counter : c->d_next;
+        if (!counter) counter = c->d_launch_counters + (c->launch_seq++ % kTickets);
+        bk.next = counter;
         if (reset_counter) CK(c, cudaMemsetAsync(bk.next, 0, sizeof(unsigned), c->stream));
         void* args[] = {&gk, &bk};
         CK(c, cudaLaunchKernel(c->kernel, dim3(grid), dim3(kThreads), args, c->smem, c->stream));
@@ -1314,8 +1320,8 @@ extern "C" int ccst_rt_track(ccst_ctx* c, const void* frames_dev, int64_t n, int
         const void* frame = (const char*)frames_dev + (size_t)i * fbytes;
         Batch b;
         if ((rc = make_batch(c, frame, 1, pitch_elems, out_dev + i, &b))) return rc;
-        if ((rc = launch(c, b, i == 0))) return rc;          // frame i against E_{i-1}; the update zeroes
-                                                             // the frame counter for the next one
+        if ((rc = launch(c, b, i == 0, c->d_next))) return rc;   // frame i against E_{i-1}; the update
+                                                                 // zeroes d_next for the next frame
         if ((rc = rt_launch(c, kRtUpdate, frame, pitch_elems, out_dev + i))) return rc;   // E_i
     }
     return CCST_OK;

@@ -415,3 +415,25 @@ def test_pair_difference_error_is_far_below_tau1(torch):
     print(f"pair-difference error / (eps32 sum|X|): FP32 guard {worst32 / eps32:.3g}, "
           f"FP64 over the FP32 spectrum {worst64 / eps32:.3g}")
     assert worst32 < 0.05 * eps32 / 8          # tau1 = 0.05 eps32 with an 8x margin
+
+
+@pytest.mark.parametrize("graphs", [False, True])
+def test_batches_in_flight_on_several_streams_match_one_at_a_time(torch, graphs):
+    # every graph, and every direct launch, has its own frame counter: batches that overlap on
+    # different streams give the records of batches run one at a time
+    s = synth.frame_stream(seed=0, n=10_000, count=768)
+    dev = torch.from_numpy(s.frames.view(np.int16)).cuda().view(torch.uint16)
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    t = C.Tracker(s.ref, upsample=100, in_dtype="u16", max_batch=256, graphs=graphs, stream=streams[0])
+    one = t.empty_results(768)
+    for b in range(3):
+        C.ccst_track(t.ctx, dev[256 * b:256 * (b + 1)], 256, 0, one[256 * b:256 * (b + 1)])
+    C.ccst_sync(t.ctx)
+    many = t.empty_results(768)
+    for rep in range(3):
+        for b in range(3):
+            C.ccst_set_stream(t.ctx, streams[b].cuda_stream)
+            C.ccst_track(t.ctx, dev[256 * b:256 * (b + 1)], 256, 0, many[256 * b:256 * (b + 1)])
+    torch.cuda.synchronize()
+    assert C.decode(many).tobytes() == C.decode(one).tobytes()
+    t.close()
