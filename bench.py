@@ -308,10 +308,12 @@ def offline_leg(C, torch, s, frames_dev, n, stream):
             "value": n * (OFF_PASSES + 1) / (total_ms / 1e3), "unit": "frame-trackings/s",
             "ms_total": total_ms, "ms_per_pass": total_ms / (OFF_PASSES + 1), "update_ms": upd_ms,
             "update_share": OFF_PASSES * upd_ms / total_ms, "stale": stale,
-            "roofline_update": {"bound": "fp64", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                                "frac": achieved / FP64_PEAK_TFLOPS, "kernel": "off_accumulate + rt_update",
-                                "flop_per_frame": off_flop_per_frame(),
-                                "peak_basis": "nominal B300 FP64 1.25 TFLOP/s (not measured)"}}
+            "roofline_update": {"bound": "fp64-equivalent", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                                "kernel": "off_accumulate + rt_update", "flop_per_frame": off_flop_per_frame(),
+                                "peak_basis": "nominal B300 FP64 1.25 TFLOP/s (not measured); the transforms run "
+                                              "in double-float on the FP32 pipes, so the FP64-equivalent rate is "
+                                              "compared with what the FP64 pipe could give"}}
 
 
 def offline_cpu_baseline(C, torch, s, stream):

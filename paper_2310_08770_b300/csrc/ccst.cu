@@ -298,6 +298,18 @@ __device__ inline double2 rt_axis_phase(int k, int N, long long q, long long D, 
     return make_double2(df_to_double(e.re), nyq ? 0.0 : df_to_double(e.im));
 }
 
+// The same phase as a complex double-float.
+__device__ inline dfc rt_axis_phase_df(int k, int N, long long q, long long D, const dfc* coarse, const dfc* fine,
+                                       int B) {
+    const bool nyq = 2 * k == N;
+    const long long ks = (nyq || k < (N >> 1)) ? k : k - N;
+    long long n = (ks * q) % D;
+    if (n < 0) n += D;
+    dfc e = df_twiddle(coarse, fine, B, n);
+    if (nyq) e.im = df{0.f, 0.f};
+    return e;
+}
+
 // forward transform of the frame's real row pair (2r, 2r+1) into Y
 __device__ void rt_row_pair_fwd(const Geom& g, const RtArgs& a, int r, double2* z, const double2* tw) {
     const int W = g.W, Wc = g.Wc;
@@ -443,20 +455,24 @@ __global__ void __launch_bounds__(128) rt_update(Geom g, RtArgs a) {
 // frames f = b, b + gridDim.x, ... into its own partial spectrum part[b] ([H][Wc], FP64),
 // d_f the displacement of record f taken exactly. Records flagged CCST_R_TIMEOUT are left
 // out; *count gains the number of frames taken. scratch[b] holds the row transforms of the
-// frame in flight. Shared memory: max(H/2 * W, Wc * H) + H + Wc double2.
+// frame in flight. The transforms and phase products run in double-float on the FP32
+// pipes (about 2^-46 per butterfly, against magnitudes), the accumulation in FP64.
+// Shared memory: max(H/2 * W, Wc * H) + H + Wc complex double-floats (16 bytes each).
 __global__ void __launch_bounds__(512) off_accumulate(Geom g, const void* frames, long long n, long long pitch,
                                                       double off, const Result* rec, double2* scratch,
                                                       double2* part, unsigned* count) {
     extern __shared__ double2 ccst_rt_smem[];
     const int H = g.H, W = g.W, Wc = g.Wc, Hp = H / 2, HWc = H * Wc;
     const int nbuf = Hp * W > Wc * H ? Hp * W : Wc * H;
-    double2* buf = ccst_rt_smem;
-    double2* py = buf + nbuf;
-    double2* px = py + H;
-    double2* S = scratch + (size_t)blockIdx.x * HWc;
+    dfc* buf = (dfc*)ccst_rt_smem;
+    dfc* py = buf + nbuf;
+    dfc* px = py + H;
+    dfc* S = (dfc*)(scratch + (size_t)blockIdx.x * HWc);
     double2* P = part + (size_t)blockIdx.x * HWc;
     for (int i = threadIdx.x; i < HWc; i += blockDim.x) P[i] = make_double2(0.0, 0.0);
     const size_t fbytes = (size_t)H * pitch * (g.in_dtype == 0 ? 2 : 4);
+    const df offd = df_from_double(off);
+    const df half = {0.5f, 0.f};
     unsigned taken = 0;
     for (long long f = blockIdx.x; f < n; f += gridDim.x) {
         const Result q = rec[f];
@@ -465,22 +481,24 @@ __global__ void __launch_bounds__(512) off_accumulate(Geom g, const void* frames
         const long long qy = rt_grid_index(q.dy, q.ipy, g.u), qx = rt_grid_index(q.dx, q.ipx, g.u);
         const void* fr = (const char*)frames + (size_t)f * fbytes;
         for (int k = threadIdx.x; k < H; k += blockDim.x)
-            py[k] = rt_axis_phase(k, H, qy, (long long)g.u * H, g.eyc, g.eyf, g.By);
+            py[k] = rt_axis_phase_df(k, H, qy, (long long)g.u * H, g.eyc, g.eyf, g.By);
         for (int k = threadIdx.x; k < Wc; k += blockDim.x)
-            px[k] = rt_axis_phase(k, W, qx, (long long)g.u * W, g.exc, g.exf, g.Bx);
+            px[k] = rt_axis_phase_df(k, W, qx, (long long)g.u * W, g.exc, g.exf, g.Bx);
         for (int i = threadIdx.x; i < Hp * W; i += blockDim.x) {
             const int r = i / W, x = i - r * W;
-            const double v0 = (double)pixel_f32(fr, g.in_dtype, (long long)(2 * r) * pitch + x) + off;
-            const double v1 = (double)pixel_f32(fr, g.in_dtype, (long long)(2 * r + 1) * pitch + x) + off;
-            buf[r * W + brev(x, g.logW)] = make_double2(v0, v1);
+            const df v0 = df_add(df_make(pixel_f32(fr, g.in_dtype, (long long)(2 * r) * pitch + x)), offd);
+            const df v1 = df_add(df_make(pixel_f32(fr, g.in_dtype, (long long)(2 * r + 1) * pitch + x)), offd);
+            buf[r * W + brev(x, g.logW)] = dfc{v0, v1};
         }
         __syncthreads();
-        fft_r2_passes(buf, g.logW, Hp, W, 1, g.tw64, g.logNtw, false);
+        fft_r2_passes(buf, g.logW, Hp, W, 1, g.twdf, g.logNtw, false);
         for (int i = threadIdx.x; i < Hp * Wc; i += blockDim.x) {
             const int r = i / Wc, kx = i - r * Wc;
-            const double2 zk = buf[r * W + kx], zc = cconj(buf[r * W + ((W - kx) & (W - 1))]);
-            S[(2 * r) * Wc + kx] = make_double2(0.5 * (zk.x + zc.x), 0.5 * (zk.y + zc.y));
-            S[(2 * r + 1) * Wc + kx] = make_double2(0.5 * (zk.y - zc.y), -0.5 * (zk.x - zc.x));
+            const dfc zk = buf[r * W + kx], zc = cconj(buf[r * W + ((W - kx) & (W - 1))]);
+            // rows 2r and 2r+1: (zk + zc) / 2 and (zk - zc) / (2i)
+            S[(2 * r) * Wc + kx] = dfc{df_mul(df_add_abs(zk.re, zc.re), half), df_mul(df_add_abs(zk.im, zc.im), half)};
+            S[(2 * r + 1) * Wc + kx] = dfc{df_mul(df_add_abs(zk.im, df_neg(zc.im)), half),
+                                           df_neg(df_mul(df_add_abs(zk.re, df_neg(zc.re)), half))};
         }
         __syncthreads();
         for (int i = threadIdx.x; i < HWc; i += blockDim.x) {
@@ -488,11 +506,12 @@ __global__ void __launch_bounds__(512) off_accumulate(Geom g, const void* frames
             buf[kx * H + brev(ky, g.logH)] = S[i];
         }
         __syncthreads();
-        fft_r2_passes(buf, g.logH, Wc, H, 1, g.tw64, g.logNtw, false);
+        fft_r2_passes(buf, g.logH, Wc, H, 1, g.twdf, g.logNtw, false);
         for (int i = threadIdx.x; i < HWc; i += blockDim.x) {      // element i is this thread's in every frame
             const int ky = i / Wc, kx = i - ky * Wc;
-            const double2 v = cmul(buf[kx * H + ky], cmul(py[ky], px[kx])), p = P[i];
-            P[i] = make_double2(p.x + v.x, p.y + v.y);
+            const dfc v = cmul(buf[kx * H + ky], cmul(py[ky], px[kx]));
+            const double2 p = P[i];
+            P[i] = make_double2(p.x + df_to_double(v.re), p.y + df_to_double(v.im));
         }
         __syncthreads();
     }
