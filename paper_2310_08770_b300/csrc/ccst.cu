@@ -310,34 +310,54 @@ __device__ inline dfc rt_axis_phase_df(int k, int N, long long q, long long D, c
     return e;
 }
 
+// Y (work spectrum) holds complex double-floats in its 16-byte slots, read and written
+// around L1.
+__device__ __forceinline__ dfc ld_dfc_cg(const double2* p) {
+    const float4 v = __ldcg((const float4*)p);
+    return dfc{df{v.x, v.y}, df{v.z, v.w}};
+}
+__device__ __forceinline__ void st_dfc_cg(double2* p, dfc v) {
+    __stcg((float4*)p, make_float4(v.re.hi, v.re.lo, v.im.hi, v.im.lo));
+}
+__device__ __forceinline__ dfc dfc_from(double2 v) { return dfc{df_from_double(v.x), df_from_double(v.y)}; }
+__device__ __forceinline__ double2 dfc_to(dfc v) { return make_double2(df_to_double(v.re), df_to_double(v.im)); }
+
+// the two real rows held in z = Y[2r] + i Y[2r+1] after a row transform, split and stored
+__device__ __forceinline__ void rt_store_row_pair(const RtArgs& a, int W, int Wc, int r, const dfc* z, int kx) {
+    const df half = {0.5f, 0.f};
+    const dfc zk = z[kx], zc = cconj(z[(W - kx) & (W - 1)]);
+    st_dfc_cg(a.Y + (2 * r) * Wc + kx, dfc{df_mul(df_add_abs(zk.re, zc.re), half), df_mul(df_add_abs(zk.im, zc.im), half)});
+    st_dfc_cg(a.Y + (2 * r + 1) * Wc + kx, dfc{df_mul(df_add_abs(zk.im, df_neg(zc.im)), half),
+                                                df_neg(df_mul(df_add_abs(zk.re, df_neg(zc.re)), half))});
+}
+
 // forward transform of the frame's real row pair (2r, 2r+1) into Y
-__device__ void rt_row_pair_fwd(const Geom& g, const RtArgs& a, int r, double2* z, const double2* tw) {
+__device__ void rt_row_pair_fwd(const Geom& g, const RtArgs& a, int r, dfc* z, const dfc* tw) {
     const int W = g.W, Wc = g.Wc;
+    const df off = df_from_double(a.off);
     for (int x = threadIdx.x; x < W; x += blockDim.x) {
-        const double v0 = (double)pixel_f32(a.frame, g.in_dtype, (long long)(2 * r) * a.pitch + x) + a.off;
-        const double v1 = (double)pixel_f32(a.frame, g.in_dtype, (long long)(2 * r + 1) * a.pitch + x) + a.off;
-        z[brev(x, g.logW)] = make_double2(v0, v1);
+        const df v0 = df_add(df_make(pixel_f32(a.frame, g.in_dtype, (long long)(2 * r) * a.pitch + x)), off);
+        const df v1 = df_add(df_make(pixel_f32(a.frame, g.in_dtype, (long long)(2 * r + 1) * a.pitch + x)), off);
+        z[brev(x, g.logW)] = dfc{v0, v1};
     }
     __syncthreads();
     fft_r2_passes(z, g.logW, 1, W, 1, tw, g.logNtw, false);
-    for (int kx = threadIdx.x; kx < Wc; kx += blockDim.x) {
-        const double2 zk = z[kx], zc = cconj(z[(W - kx) & (W - 1)]);
-        __stcg(a.Y + (2 * r) * Wc + kx, make_double2(0.5 * (zk.x + zc.x), 0.5 * (zk.y + zc.y)));
-        __stcg(a.Y + (2 * r + 1) * Wc + kx, make_double2(0.5 * (zk.y - zc.y), -0.5 * (zk.x - zc.x)));
-    }
+    for (int kx = threadIdx.x; kx < Wc; kx += blockDim.x) rt_store_row_pair(a, W, Wc, r, z, kx);
     __syncthreads();
 }
 
 // column kx of Y, transformed over y (in natural order in z)
-__device__ void rt_col_fwd(const Geom& g, const RtArgs& a, int kx, double2* z, const double2* tw) {
-    for (int ky = threadIdx.x; ky < g.H; ky += blockDim.x) z[brev(ky, g.logH)] = __ldcg(a.Y + ky * g.Wc + kx);
+__device__ void rt_col_fwd(const Geom& g, const RtArgs& a, int kx, dfc* z, const dfc* tw) {
+    for (int ky = threadIdx.x; ky < g.H; ky += blockDim.x) z[brev(ky, g.logH)] = ld_dfc_cg(a.Y + ky * g.Wc + kx);
     __syncthreads();
     fft_r2_passes(z, g.logH, 1, g.H, 1, tw, g.logNtw, false);
 }
 
+// The transforms run in double-float on the FP32 pipes (FP64 chains in two warps were the
+// update's latency); the filter state E and the operand b64 stay FP64.
 __global__ void __launch_bounds__(128) rt_update(Geom g, RtArgs a) {
-    __shared__ double2 z[128];
-    __shared__ double2 tw[64];                             // FFT twiddles, Ntw/2 <= 64
+    __shared__ dfc z[128];
+    __shared__ dfc tw[64];                                 // FFT twiddles, Ntw/2 <= 64
     const int H = g.H, W = g.W, Wc = g.Wc, Hp = H / 2, HWc = H * Wc;
     const bool upd = a.mode == kRtUpdate;
     if (a.next && blockIdx.x == 0 && threadIdx.x == 0) *a.next = 0;   // frame counter of the next tracking launch
@@ -353,7 +373,7 @@ __global__ void __launch_bounds__(128) rt_update(Geom g, RtArgs a) {
         qx = rt_grid_index(q.dx, q.ipx, g.u);
     }
     const long long Dy = (long long)g.u * H, Dx = (long long)g.u * W;
-    for (int k = threadIdx.x; k < g.Ntw / 2; k += blockDim.x) tw[k] = g.tw64[k];
+    for (int k = threadIdx.x; k < g.Ntw / 2; k += blockDim.x) tw[k] = g.twdf[k];
     __syncthreads();
     const unsigned G = gridDim.x, b1t = a.base + G + a.extra, b2t = b1t + G, b3t = b2t + G;
     auto failed = [&]() {
@@ -379,73 +399,71 @@ __global__ void __launch_bounds__(128) rt_update(Geom g, RtArgs a) {
     if (!rt_grid_barrier(a.sync, b1t, a.limit)) return failed();
     const int t = threadIdx.x;
     for (int kx = blockIdx.x; kx < Wc; kx += gridDim.x) {
-        double2 e = make_double2(0.0, 0.0);
+        dfc e = dfc{df{0.f, 0.f}, df{0.f, 0.f}};
         if (a.mode == kRtMean) {
-            if (t < H) e = __ldcg(a.E + t * Wc + kx);
+            if (t < H) e = dfc_from(__ldcg(a.E + t * Wc + kx));
         } else {
             rt_col_fwd(g, a, kx, z, tw);
             if (t < H) {
                 e = z[t];
+                double2 ed = dfc_to(e);
                 if (upd) {
-                    const double2 s = cmul(e, cmul(rt_axis_phase(t, H, qy, Dy, g.eyc, g.eyf, g.By),
-                                                   rt_axis_phase(kx, W, qx, Dx, g.exc, g.exf, g.Bx)));
+                    const double2 s = dfc_to(cmul(e, cmul(rt_axis_phase_df(t, H, qy, Dy, g.eyc, g.eyf, g.By),
+                                                          rt_axis_phase_df(kx, W, qx, Dx, g.exc, g.exf, g.Bx))));
                     const double2 p = __ldcg(a.E + t * Wc + kx);
-                    e = make_double2(a.a0 * s.x + a.b1 * p.x, a.a0 * s.y + a.b1 * p.y);
+                    ed = make_double2(a.a0 * s.x + a.b1 * p.x, a.a0 * s.y + a.b1 * p.y);
+                    e = dfc_from(ed);
                 }
-                __stcg(a.E + t * Wc + kx, e);
+                __stcg(a.E + t * Wc + kx, ed);
             }
         }
         __syncthreads();
         if (t < H) z[brev(t, g.logH)] = e;
         __syncthreads();
         fft_r2_passes(z, g.logH, 1, H, 1, tw, g.logNtw, true);
-        if (t < H) __stcg(a.Y + t * Wc + kx, z[t]);
+        if (t < H) st_dfc_cg(a.Y + t * Wc + kx, z[t]);
         __syncthreads();
     }
     if (!rt_grid_barrier(a.sync, b2t, a.limit)) return failed();
-    const double sc = 1.0 / ((double)H * W);
+    const float sc = 1.0f / ((float)H * W);                // a power of two: exact on a double-float
     for (int r = blockIdx.x; r < Hp; r += gridDim.x) {
         // Y rows 2r, 2r+1 are Hermitian in kx: one complex inverse gives both real rows
         if (t < W) {
-            double2 ye, yo;
+            dfc ye, yo;
             if (t < Wc) {
-                ye = __ldcg(a.Y + (2 * r) * Wc + t);
-                yo = __ldcg(a.Y + (2 * r + 1) * Wc + t);
+                ye = ld_dfc_cg(a.Y + (2 * r) * Wc + t);
+                yo = ld_dfc_cg(a.Y + (2 * r + 1) * Wc + t);
             } else {
-                ye = cconj(__ldcg(a.Y + (2 * r) * Wc + W - t));
-                yo = cconj(__ldcg(a.Y + (2 * r + 1) * Wc + W - t));
+                ye = cconj(ld_dfc_cg(a.Y + (2 * r) * Wc + W - t));
+                yo = cconj(ld_dfc_cg(a.Y + (2 * r + 1) * Wc + W - t));
             }
-            z[brev(t, g.logW)] = make_double2(ye.x - yo.y, ye.y + yo.x);   // ye + i yo
+            z[brev(t, g.logW)] = dfc{df_add_abs(ye.re, df_neg(yo.im)), df_add_abs(ye.im, yo.re)};   // ye + i yo
         }
         __syncthreads();
         fft_r2_passes(z, g.logW, 1, W, 1, tw, g.logNtw, true);
-        double b0 = 0.0, b1v = 0.0;
+        dfc bz = dfc{df{0.f, 0.f}, df{0.f, 0.f}};
         if (t < W) {
-            const double e0 = z[t].x * sc, e1 = z[t].y * sc;
-            b0 = g.method == 0 ? e0 : 1.0 / e0;
-            b1v = g.method == 0 ? e1 : 1.0 / e1;
+            const double e0 = df_to_double(df_scale(z[t].re, sc)), e1 = df_to_double(df_scale(z[t].im, sc));
+            const double b0 = g.method == 0 ? e0 : 1.0 / e0, b1v = g.method == 0 ? e1 : 1.0 / e1;
             __stcg(a.b64 + (2 * r) * W + t, b0);
             __stcg(a.b64 + (2 * r + 1) * W + t, b1v);
+            bz = dfc{df_from_double(b0), df_from_double(b1v)};
         }
         __syncthreads();
-        if (t < W) z[brev(t, g.logW)] = make_double2(b0, b1v);
+        if (t < W) z[brev(t, g.logW)] = bz;
         __syncthreads();
         fft_r2_passes(z, g.logW, 1, W, 1, tw, g.logNtw, false);
-        if (t < Wc) {
-            const double2 zk = z[t], zc = cconj(z[(W - t) & (W - 1)]);
-            __stcg(a.Y + (2 * r) * Wc + t, make_double2(0.5 * (zk.x + zc.x), 0.5 * (zk.y + zc.y)));
-            __stcg(a.Y + (2 * r + 1) * Wc + t, make_double2(0.5 * (zk.y - zc.y), -0.5 * (zk.x - zc.x)));
-        }
+        if (t < Wc) rt_store_row_pair(a, W, Wc, r, z, t);
         __syncthreads();
     }
     if (!rt_grid_barrier(a.sync, b3t, a.limit)) return failed();
     for (int kx = blockIdx.x; kx < Wc; kx += gridDim.x) {
         rt_col_fwd(g, a, kx, z, tw);
         if (t < H) {
-            const double2 e = z[t];
-            a.FE64[t * Wc + kx] = e;
-            a.FE32[t * Wc + kx] = make_float2((float)e.x, (float)e.y);
-            a.FEdf[t * Wc + kx] = dfc{df_from_double(e.x), df_from_double(e.y)};
+            const dfc e = z[t];
+            a.FE64[t * Wc + kx] = dfc_to(e);
+            a.FE32[t * Wc + kx] = make_float2(e.re.hi, e.im.hi);
+            a.FEdf[t * Wc + kx] = e;
         }
         __syncthreads();
     }
