@@ -1,5 +1,6 @@
 // ccst_adjoint.cuh -- the continuous peak of the cross-correlation interpolant and its
-// vector-Jacobian product (the adjoint of the displacement), FP64.
+// vector-Jacobian product (the adjoint of the displacement). Newton's sums and the VJP
+// spectra are FP64; the 2-D transforms run in double-float on the FP32 pipes.
 //
 // The tracker's estimate is the extremum of the interpolant of Sec. III on the 1/u grid,
 // a piecewise-constant function of the pixels. The differentiable quantity is the
@@ -83,8 +84,9 @@ __host__ __device__ inline size_t adj_smem_bytes(int H, int W) {
 __global__ void __launch_bounds__(512) adj_kernel(Geom g, AdjArgs a) {
     extern __shared__ double2 adj_smem[];
     const int H = g.H, W = g.W, Wc = g.Wc, Hp = H / 2, HWc = H * Wc, t = threadIdx.x;
-    double2* buf = adj_smem;
-    double2* Ay = buf + adj_nbuf(H, W);
+    dfc* buf = (dfc*)adj_smem;                 // transforms in double-float ...
+    double2* Xs = adj_smem;                    // ... then X in FP64 in the same 16-byte slots
+    double2* Ay = adj_smem + adj_nbuf(H, W);
     double2* Bx = Ay + H;
     double2* R = Bx + Wc;                      // [H][3], then the y-Nyquist middle part [3]
     double* red = (double*)(R + 3 * H + 3);    // [16 warps][6]
@@ -93,14 +95,19 @@ __global__ void __launch_bounds__(512) adj_kernel(Geom g, AdjArgs a) {
     const double eps = (double)g.eps, inv_hw = 1.0 / ((double)H * W);
     const double2* Fb = g.FE64;
     double2* S = a.scratch + (size_t)blockIdx.x * HWc;
+    dfc* Sd = (dfc*)S;                         // S as double-float scratch between the passes
     double2* P = a.part ? a.part + (size_t)blockIdx.x * HWc : nullptr;
     if (P)
         for (int i = t; i < HWc; i += blockDim.x) P[i] = make_double2(0.0, 0.0);
     const size_t fbytes = (size_t)H * a.pitch * (g.in_dtype == 0 ? 2 : 4);
+    const df eps_d = df_from_double(eps);
     auto operand = [&](const void* fr, int y, int x) {
-        const double I = (double)pixel_f32(fr, g.in_dtype, (long long)y * a.pitch + x);
-        return g.method == 0 ? I : (I + eps) * (I + eps);
+        const df I = df_make(pixel_f32(fr, g.in_dtype, (long long)y * a.pitch + x));
+        if (g.method == 0) return I;
+        const df ip = df_add(I, eps_d);
+        return df_mul(ip, ip);
     };
+    const df half = {0.5f, 0.f};
     // rows of tpr consecutive lanes each, for the per-row sums over kx
     const int tpr = (int)(blockDim.x / H) < 32 ? (int)(blockDim.x / H) : 32;
     for (long long f = blockIdx.x; f < a.n; f += gridDim.x) {
@@ -108,31 +115,34 @@ __global__ void __launch_bounds__(512) adj_kernel(Geom g, AdjArgs a) {
         // ---- F[a]: row pairs in buf, unpacked to S, columns in buf (column-major [Wc][H])
         for (int i = t; i < Hp * W; i += blockDim.x) {
             const int r = i / W, x = i - r * W;
-            buf[r * W + brev(x, g.logW)] = make_double2(operand(fr, 2 * r, x), operand(fr, 2 * r + 1, x));
+            buf[r * W + brev(x, g.logW)] = dfc{operand(fr, 2 * r, x), operand(fr, 2 * r + 1, x)};
         }
         __syncthreads();
-        fft_r2_passes(buf, g.logW, Hp, W, 1, g.tw64, g.logNtw, false);
+        fft_r2_passes(buf, g.logW, Hp, W, 1, g.twdf, g.logNtw, false);
         for (int i = t; i < Hp * Wc; i += blockDim.x) {
             const int r = i / Wc, kx = i - r * Wc;
-            const double2 zk = buf[r * W + kx], zc = cconj(buf[r * W + ((W - kx) & (W - 1))]);
-            S[(2 * r) * Wc + kx] = make_double2(0.5 * (zk.x + zc.x), 0.5 * (zk.y + zc.y));
-            S[(2 * r + 1) * Wc + kx] = make_double2(0.5 * (zk.y - zc.y), -0.5 * (zk.x - zc.x));
+            const dfc zk = buf[r * W + kx], zc = cconj(buf[r * W + ((W - kx) & (W - 1))]);
+            Sd[(2 * r) * Wc + kx] = dfc{df_mul(df_add_abs(zk.re, zc.re), half), df_mul(df_add_abs(zk.im, zc.im), half)};
+            Sd[(2 * r + 1) * Wc + kx] = dfc{df_mul(df_add_abs(zk.im, df_neg(zc.im)), half),
+                                            df_neg(df_mul(df_add_abs(zk.re, df_neg(zc.re)), half))};
         }
         __syncthreads();
         for (int i = t; i < HWc; i += blockDim.x) {
             const int ky = i / Wc, kx = i - ky * Wc;
-            buf[kx * H + brev(ky, g.logH)] = S[i];
+            buf[kx * H + brev(ky, g.logH)] = Sd[i];
         }
         __syncthreads();
-        fft_r2_passes(buf, g.logH, Wc, H, 1, g.tw64, g.logNtw, false);
-        // S keeps F[a] (row-major); buf takes X = F[a] conj F[b] with the fold weight c
+        fft_r2_passes(buf, g.logH, Wc, H, 1, g.twdf, g.logNtw, false);
+        // S keeps F[a] in FP64 (row-major); the buffer takes X = F[a] conj F[b] in FP64 with
+        // the fold weight c (each thread rewrites the slot it read)
         for (int i = t; i < HWc; i += blockDim.x) {
             const int ky = i / Wc, kx = i - ky * Wc;
-            const double2 fa = buf[kx * H + ky];
+            const dfc fd = buf[kx * H + ky];
+            const double2 fa = make_double2(df_to_double(fd.re), df_to_double(fd.im));
             S[i] = fa;
             const double c = (kx == 0 || 2 * kx == W) ? 1.0 : 2.0;
             const double2 x = cmul(fa, cconj(Fb[i]));
-            buf[kx * H + ky] = make_double2(c * x.x, c * x.y);
+            Xs[kx * H + ky] = make_double2(c * x.x, c * x.y);
         }
         if (t == 0) {
             const Result q = a.rec[f];
@@ -168,7 +178,7 @@ __global__ void __launch_bounds__(512) adj_kernel(Geom g, AdjArgs a) {
                     const bool nyq_row = 2 * row == H;
                     for (int kx = j; kx < Wc; kx += tpr) {
                         const double kap = 2.0 * CUDART_PI * adj_freq(kx, W) / W;
-                        const double2 xb = cmul(buf[kx * H + row], Bx[kx]);
+                        const double2 xb = cmul(Xs[kx * H + row], Bx[kx]);
                         const double2 x1 = adj_i_times(kap, xb);
                         const double2 x2 = make_double2(-kap * kap * xb.x, -kap * kap * xb.y);
                         if (nyq_row && kx != 0 && 2 * kx != W) {
@@ -274,28 +284,29 @@ __global__ void __launch_bounds__(512) adj_kernel(Geom g, AdjArgs a) {
                 const double2 z = adj_i_times(wy * my + wx * mx, cmul(ph, cconj(fb)));     // Z(k)
                 const double2 zp = adj_i_times(wy * pmy + wx * pmx, cmul(pph, fb));         // Z(pair)
                 // V = conj Z; V_h = (V(k) + conj V(pair)) / 2 = (conj Z(k) + Z(pair)) / 2
-                buf[kx * H + brev(ky, g.logH)] = make_double2(0.5 * (z.x + zp.x), 0.5 * (-z.y + zp.y));
+                const double2 vh = make_double2(0.5 * (z.x + zp.x), 0.5 * (-z.y + zp.y));
+                buf[kx * H + brev(ky, g.logH)] = dfc{df_from_double(vh.x), df_from_double(vh.y)};
             }
             __syncthreads();
-            fft_r2_passes(buf, g.logH, Wc, H, 1, g.tw64, g.logNtw, true);
+            fft_r2_passes(buf, g.logH, Wc, H, 1, g.twdf, g.logNtw, true);
             for (int i = t; i < HWc; i += blockDim.x) {
                 const int ky = i / Wc, kx = i - ky * Wc;
-                S[i] = buf[kx * H + ky];
+                Sd[i] = buf[kx * H + ky];
             }
             __syncthreads();
             for (int i = t; i < Hp * W; i += blockDim.x) {
                 const int r = i / W, kx = i - r * W;
-                double2 ye, yo;
-                if (kx < Wc) { ye = S[(2 * r) * Wc + kx]; yo = S[(2 * r + 1) * Wc + kx]; }
-                else { ye = cconj(S[(2 * r) * Wc + W - kx]); yo = cconj(S[(2 * r + 1) * Wc + W - kx]); }
-                buf[r * W + brev(kx, g.logW)] = make_double2(ye.x - yo.y, ye.y + yo.x);     // ye + i yo
+                dfc ye, yo;
+                if (kx < Wc) { ye = Sd[(2 * r) * Wc + kx]; yo = Sd[(2 * r + 1) * Wc + kx]; }
+                else { ye = cconj(Sd[(2 * r) * Wc + W - kx]); yo = cconj(Sd[(2 * r + 1) * Wc + W - kx]); }
+                buf[r * W + brev(kx, g.logW)] = dfc{df_add_abs(ye.re, df_neg(yo.im)), df_add_abs(ye.im, yo.re)};
             }
             __syncthreads();
-            fft_r2_passes(buf, g.logW, Hp, W, 1, g.tw64, g.logNtw, true);
+            fft_r2_passes(buf, g.logW, Hp, W, 1, g.twdf, g.logNtw, true);
             float* gI = a.g_frames + (size_t)f * H * W;
             for (int i = t; i < Hp * W; i += blockDim.x) {
                 const int r = i / W, x = i - r * W;
-                double d0 = buf[r * W + x].x * inv_hw, d1 = buf[r * W + x].y * inv_hw;
+                double d0 = df_to_double(buf[r * W + x].re) * inv_hw, d1 = df_to_double(buf[r * W + x].im) * inv_hw;
                 if (g.method != 0) {
                     d0 *= 2.0 * ((double)pixel_f32(fr, g.in_dtype, (long long)(2 * r) * a.pitch + x) + eps);
                     d1 *= 2.0 * ((double)pixel_f32(fr, g.in_dtype, (long long)(2 * r + 1) * a.pitch + x) + eps);
