@@ -703,18 +703,18 @@ def run_ours(args):
                   "overflow": int(np.sum((flags & C.R_OVERFLOW) != 0))},
     }
     rt_line = rt_res = None
-    if rank == 0 and not args.no_realtime:
+    if world == 1 and not args.no_realtime:         # the extra legs are single-GPU measurements
         rt_line, rt_res = realtime_leg(C, torch, s, stream, args.rt_frames)
         line["realtime"] = rt_line
-    if rank == 0 and not args.no_offline:
+    if world == 1 and not args.no_offline:
         line["offline"] = offline_leg(C, torch, s, frames_dev, n_frames, stream)
-    if rank == 0 and not args.no_serving:
+    if world == 1 and not args.no_serving:
         line["serving"] = serving_leg(C, torch)
     rois_extra = None
-    if rank == 0 and not args.no_rois:
+    if world == 1 and not args.no_rois:
         line["rois"], rois_extra = rois_leg(C, torch, stream, args.rois_n)
     adj_extra = None
-    if rank == 0 and not args.no_adjoint:
+    if world == 1 and not args.no_adjoint:
         line["adjoint"], adj_extra = adjoint_leg(C, torch, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         if rois_extra is not None:
