@@ -475,13 +475,14 @@ __global__ void __launch_bounds__(128) rt_update(Geom g, RtArgs a) {
 // out; *count gains the number of frames taken. scratch[b] holds the row transforms of the
 // frame in flight. The transforms and phase products run in double-float on the FP32
 // pipes (about 2^-46 per butterfly, against magnitudes), the accumulation in FP64.
-// Shared memory: max(H/2 * W, Wc * H) + H + Wc complex double-floats (16 bytes each).
+// Shared memory: max(H/2 * W, Wc * (H + 1)) + H + Wc complex double-floats (16 bytes each).
 __global__ void __launch_bounds__(512) off_accumulate(Geom g, const void* frames, long long n, long long pitch,
                                                       double off, const Result* rec, double2* scratch,
                                                       double2* part, unsigned* count) {
     extern __shared__ double2 ccst_rt_smem[];
     const int H = g.H, W = g.W, Wc = g.Wc, Hp = H / 2, HWc = H * Wc;
-    const int nbuf = Hp * W > Wc * H ? Hp * W : Wc * H;
+    const int CS = H + 1;                               // column stride, padded against bank conflicts
+    const int nbuf = Hp * W > Wc * CS ? Hp * W : Wc * CS;
     dfc* buf = (dfc*)ccst_rt_smem;
     dfc* py = buf + nbuf;
     dfc* px = py + H;
@@ -521,13 +522,13 @@ __global__ void __launch_bounds__(512) off_accumulate(Geom g, const void* frames
         __syncthreads();
         for (int i = threadIdx.x; i < HWc; i += blockDim.x) {
             const int ky = i / Wc, kx = i - ky * Wc;
-            buf[kx * H + brev(ky, g.logH)] = S[i];
+            buf[kx * CS + brev(ky, g.logH)] = S[i];
         }
         __syncthreads();
-        fft_r2_passes(buf, g.logH, Wc, H, 1, g.twdf, g.logNtw, false);
+        fft_r2_passes(buf, g.logH, Wc, CS, 1, g.twdf, g.logNtw, false);
         for (int i = threadIdx.x; i < HWc; i += blockDim.x) {      // element i is this thread's in every frame
             const int ky = i / Wc, kx = i - ky * Wc;
-            const dfc v = cmul(buf[kx * H + ky], cmul(py[ky], px[kx]));
+            const dfc v = cmul(buf[kx * CS + ky], cmul(py[ky], px[kx]));
             const double2 p = P[i];
             P[i] = make_double2(p.x + df_to_double(v.re), p.y + df_to_double(v.im));
         }
@@ -1366,7 +1367,7 @@ extern "C" int ccst_rt_track(ccst_ctx* c, const void* frames_dev, int64_t n, int
 
 // ---------------------------------------------------------- offline reference (Sec. III A)
 static size_t off_smem_bytes(const Geom& g) {
-    const int nbuf = (g.H / 2) * g.W > g.Wc * g.H ? (g.H / 2) * g.W : g.Wc * g.H;
+    const int nbuf = (g.H / 2) * g.W > g.Wc * (g.H + 1) ? (g.H / 2) * g.W : g.Wc * (g.H + 1);
     return (size_t)(nbuf + g.H + g.Wc) * sizeof(double2);
 }
 

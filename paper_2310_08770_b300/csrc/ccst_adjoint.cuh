@@ -73,7 +73,7 @@ __device__ void adj_block_sum6(double v[6], double* red) {
 // Shared memory of adj_kernel, in double2: the transform buffer, Ay[H], Bx[Wc], the row
 // sums R[H][3] (+3 for the y-Nyquist row's middle columns), and 6 doubles per warp.
 __host__ __device__ inline int adj_nbuf(int H, int W) {
-    const int a = (H / 2) * W, b = (W / 2 + 1) * H;
+    const int a = (H / 2) * W, b = (W / 2 + 1) * (H + 1);
     return a > b ? a : b;
 }
 __host__ __device__ inline size_t adj_smem_bytes(int H, int W) {
@@ -84,6 +84,7 @@ __host__ __device__ inline size_t adj_smem_bytes(int H, int W) {
 __global__ void __launch_bounds__(512) adj_kernel(Geom g, AdjArgs a) {
     extern __shared__ double2 adj_smem[];
     const int H = g.H, W = g.W, Wc = g.Wc, Hp = H / 2, HWc = H * Wc, t = threadIdx.x;
+    const int CS = H + 1;                      // column stride of the buffer, padded against bank conflicts
     dfc* buf = (dfc*)adj_smem;                 // transforms in double-float ...
     double2* Xs = adj_smem;                    // ... then X in FP64 in the same 16-byte slots
     double2* Ay = adj_smem + adj_nbuf(H, W);
@@ -129,20 +130,20 @@ __global__ void __launch_bounds__(512) adj_kernel(Geom g, AdjArgs a) {
         __syncthreads();
         for (int i = t; i < HWc; i += blockDim.x) {
             const int ky = i / Wc, kx = i - ky * Wc;
-            buf[kx * H + brev(ky, g.logH)] = Sd[i];
+            buf[kx * CS + brev(ky, g.logH)] = Sd[i];
         }
         __syncthreads();
-        fft_r2_passes(buf, g.logH, Wc, H, 1, g.twdf, g.logNtw, false);
+        fft_r2_passes(buf, g.logH, Wc, CS, 1, g.twdf, g.logNtw, false);
         // S keeps F[a] in FP64 (row-major); the buffer takes X = F[a] conj F[b] in FP64 with
         // the fold weight c (each thread rewrites the slot it read)
         for (int i = t; i < HWc; i += blockDim.x) {
             const int ky = i / Wc, kx = i - ky * Wc;
-            const dfc fd = buf[kx * H + ky];
+            const dfc fd = buf[kx * CS + ky];
             const double2 fa = make_double2(df_to_double(fd.re), df_to_double(fd.im));
             S[i] = fa;
             const double c = (kx == 0 || 2 * kx == W) ? 1.0 : 2.0;
             const double2 x = cmul(fa, cconj(Fb[i]));
-            Xs[kx * H + ky] = make_double2(c * x.x, c * x.y);
+            Xs[kx * CS + ky] = make_double2(c * x.x, c * x.y);
         }
         if (t == 0) {
             const Result q = a.rec[f];
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(512) adj_kernel(Geom g, AdjArgs a) {
                     const bool nyq_row = 2 * row == H;
                     for (int kx = j; kx < Wc; kx += tpr) {
                         const double kap = 2.0 * CUDART_PI * adj_freq(kx, W) / W;
-                        const double2 xb = cmul(Xs[kx * H + row], Bx[kx]);
+                        const double2 xb = cmul(Xs[kx * CS + row], Bx[kx]);
                         const double2 x1 = adj_i_times(kap, xb);
                         const double2 x2 = make_double2(-kap * kap * xb.x, -kap * kap * xb.y);
                         if (nyq_row && kx != 0 && 2 * kx != W) {
@@ -285,13 +286,13 @@ __global__ void __launch_bounds__(512) adj_kernel(Geom g, AdjArgs a) {
                 const double2 zp = adj_i_times(wy * pmy + wx * pmx, cmul(pph, fb));         // Z(pair)
                 // V = conj Z; V_h = (V(k) + conj V(pair)) / 2 = (conj Z(k) + Z(pair)) / 2
                 const double2 vh = make_double2(0.5 * (z.x + zp.x), 0.5 * (-z.y + zp.y));
-                buf[kx * H + brev(ky, g.logH)] = dfc{df_from_double(vh.x), df_from_double(vh.y)};
+                buf[kx * CS + brev(ky, g.logH)] = dfc{df_from_double(vh.x), df_from_double(vh.y)};
             }
             __syncthreads();
-            fft_r2_passes(buf, g.logH, Wc, H, 1, g.twdf, g.logNtw, true);
+            fft_r2_passes(buf, g.logH, Wc, CS, 1, g.twdf, g.logNtw, true);
             for (int i = t; i < HWc; i += blockDim.x) {
                 const int ky = i / Wc, kx = i - ky * Wc;
-                Sd[i] = buf[kx * H + ky];
+                Sd[i] = buf[kx * CS + ky];
             }
             __syncthreads();
             for (int i = t; i < Hp * W; i += blockDim.x) {
