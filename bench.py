@@ -207,6 +207,9 @@ def cpu_baseline(frames, ref, budget_s=15.0):
                            f"{cores} spawn workers with one BLAS thread each"}
 
 
+WORKLOAD = ("frame stream: 10000 uint16 128x128 Gaussian-spot frames (sigma 2.5, peak 2000, bg 20, Poisson), "
+            "Brownian trajectory step 0.3 px, u=100, CC-U, 256-frame CUDA-graph batches, consecutive batches on "
+            "alternating streams")
 RT_FRAMES = 1024                 # real-time leg: frames after frame 0
 RT_A0 = 0.05                     # its filter, a0 = 1 - exp(-T/tau)
 RT_ORACLE_FRAMES = 48
@@ -681,9 +684,7 @@ def run_ours(args):
         "ms_per_step": total_ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "p50_us": weighted_percentile(lat_ms * 1e3, sizes, 50), "p99_us": weighted_percentile(lat_ms * 1e3, sizes, 99),
-        "config": {"workload": "frame stream: 10000 uint16 128x128 Gaussian-spot frames (sigma 2.5, peak 2000, "
-                               "bg 20, Poisson), Brownian trajectory step 0.3 px, u=100, CC-U, "
-                               "256-frame CUDA-graph batches, consecutive batches on alternating streams",
+        "config": {"workload": WORKLOAD,
                    "global_batch": BATCH * world, "frames_per_rank": n_frames, "upsample": U,
                    "streams": len(streams),
                    "parallelism": f"replicas x{world} (independent streams)",
@@ -797,9 +798,8 @@ def run_reference(args):
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "p50_us": float(np.median(lat)) * 1e6, "p99_us": float(np.percentile(lat, 99)) * 1e6,
-        "config": {"workload": "frame stream: 10000 uint16 128x128 Gaussian-spot frames, u=100, CC-U "
-                               "(bounded per-step sample on the host)", "global_batch": per_step,
-                   "upsample": U, "parallelism": "host cores"},
+        "config": {"workload": WORKLOAD, "global_batch": BATCH, "frames_per_step_timed": per_step,
+                   "upsample": U, "parallelism": "host cores (a bounded sample of each batch per step)"},
         "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores if use_pool else 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
