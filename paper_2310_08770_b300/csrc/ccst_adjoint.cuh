@@ -50,6 +50,13 @@ __device__ __forceinline__ double2 adj_i_times(double kappa, double2 z) {   // i
     return make_double2(-kappa * z.y, kappa * z.x);
 }
 
+__device__ __forceinline__ double2 dfc_double(dfc v) { return make_double2(df_to_double(v.re), df_to_double(v.im)); }
+
+__device__ __forceinline__ dfc shfl_xor_dfc(dfc v, int o) {
+    return dfc{df{__shfl_xor_sync(0xffffffffu, v.re.hi, o), __shfl_xor_sync(0xffffffffu, v.re.lo, o)},
+               df{__shfl_xor_sync(0xffffffffu, v.im.hi, o), __shfl_xor_sync(0xffffffffu, v.im.lo, o)}};
+}
+
 // Deterministic block sum of 6 doubles; the result is valid in thread 0.
 __device__ void adj_block_sum6(double v[6], double* red) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -70,14 +77,15 @@ __device__ void adj_block_sum6(double v[6], double* red) {
     __syncthreads();
 }
 
-// Shared memory of adj_kernel, in double2: the transform buffer, Ay[H], Bx[Wc], the row
-// sums R[H][3] (+3 for the y-Nyquist row's middle columns), and 6 doubles per warp.
+// Shared memory of adj_kernel, in double2: the transform buffer (then X as double-floats),
+// Ay[H], Bx[Wc], the row sums R[H][3] (+3 for the y-Nyquist row's middle columns), 6
+// doubles per warp, and the double-float column phases and factors BxF, kap, -kap^2 [Wc].
 __host__ __device__ inline int adj_nbuf(int H, int W) {
     const int a = (H / 2) * W, b = (W / 2 + 1) * (H + 1);
     return a > b ? a : b;
 }
 __host__ __device__ inline size_t adj_smem_bytes(int H, int W) {
-    return (size_t)(adj_nbuf(H, W) + H + (W / 2 + 1) + 3 * H + 3 + 3 * 16 + 8) * sizeof(double2);
+    return (size_t)(adj_nbuf(H, W) + H + (W / 2 + 1) + 3 * H + 3 + 3 * 16 + 8 + 2 * (W / 2 + 1) + 2) * sizeof(double2);
 }
 
 // One CTA per frame f = blockIdx.x, blockIdx.x + gridDim.x, ... (blockDim.x = 512).
@@ -85,12 +93,15 @@ __global__ void __launch_bounds__(512) adj_kernel(Geom g, AdjArgs a) {
     extern __shared__ double2 adj_smem[];
     const int H = g.H, W = g.W, Wc = g.Wc, Hp = H / 2, HWc = H * Wc, t = threadIdx.x;
     const int CS = H + 1;                      // column stride of the buffer, padded against bank conflicts
-    dfc* buf = (dfc*)adj_smem;                 // transforms in double-float ...
-    double2* Xs = adj_smem;                    // ... then X in FP64 in the same 16-byte slots
+    dfc* buf = (dfc*)adj_smem;                 // transforms in double-float, then X (weighted)
     double2* Ay = adj_smem + adj_nbuf(H, W);
     double2* Bx = Ay + H;
     double2* R = Bx + Wc;                      // [H][3], then the y-Nyquist middle part [3]
     double* red = (double*)(R + 3 * H + 3);    // [16 warps][6]
+    dfc* BxF = (dfc*)(red + 6 * 16 + 16);      // [Wc] Bx as double-floats
+    df* kapd = (df*)(BxF + Wc);                // [Wc] 2 pi kx' / W
+    df* kap2d = kapd + Wc;                     // [Wc] -(2 pi kx' / W)^2
+    __shared__ int sdf;                        // Newton's sums in double-float (1) or FP64 (0)
     __shared__ double st[8];                   // sy, sx, hyy, hxy, hxx, step, f
     __shared__ int sflag;
     const double eps = (double)g.eps, inv_hw = 1.0 / ((double)H * W);
@@ -134,8 +145,8 @@ __global__ void __launch_bounds__(512) adj_kernel(Geom g, AdjArgs a) {
         }
         __syncthreads();
         fft_r2_passes(buf, g.logH, Wc, CS, 1, g.twdf, g.logNtw, false);
-        // S keeps F[a] in FP64 (row-major); the buffer takes X = F[a] conj F[b] in FP64 with
-        // the fold weight c (each thread rewrites the slot it read)
+        // S keeps F[a] in FP64 (row-major); the buffer takes X = F[a] conj F[b] (FP64 product,
+        // kept as a double-float) with the fold weight c; each thread rewrites the slot it read
         for (int i = t; i < HWc; i += blockDim.x) {
             const int ky = i / Wc, kx = i - ky * Wc;
             const dfc fd = buf[kx * CS + ky];
@@ -143,13 +154,19 @@ __global__ void __launch_bounds__(512) adj_kernel(Geom g, AdjArgs a) {
             S[i] = fa;
             const double c = (kx == 0 || 2 * kx == W) ? 1.0 : 2.0;
             const double2 x = cmul(fa, cconj(Fb[i]));
-            Xs[kx * CS + ky] = make_double2(c * x.x, c * x.y);
+            buf[kx * CS + ky] = dfc{df_from_double(c * x.x), df_from_double(c * x.y)};
+        }
+        for (int k = t; k < Wc; k += blockDim.x) {
+            const double kap = 2.0 * CUDART_PI * adj_freq(k, W) / W;
+            kapd[k] = df_from_double(kap);
+            kap2d[k] = df_from_double(-kap * kap);
         }
         if (t == 0) {
             const Result q = a.rec[f];
             st[0] = ((double)q.ipy * g.u + rint((double)q.dy * g.u - (double)q.ipy * g.u)) / g.u;
             st[1] = ((double)q.ipx * g.u + rint((double)q.dx * g.u - (double)q.ipx * g.u)) / g.u;
             sflag = 0;
+            sdf = 1;
         }
         __syncthreads();
         const double sy0 = st[0], sx0 = st[1];
@@ -168,18 +185,47 @@ __global__ void __launch_bounds__(512) adj_kernel(Geom g, AdjArgs a) {
                 double sn, cs;
                 sincospi(2.0 * adj_freq(k, W) * sx / W, &sn, &cs);
                 Bx[k] = make_double2(cs, sn);
+                BxF[k] = dfc{df_from_double(cs), df_from_double(sn)};
             }
             __syncthreads();
             if (done) break;                                    // Ay, Bx now at s*
-            // row sums R0 = sum c X B, R1 = sum c X (i kx) B, R2 = sum c X (-kx^2) B
-            {
+            // row sums R0 = sum c X B, R1 = sum c X (i kx) B, R2 = sum c X (-kx^2) B: in double-float
+            // while the steps are large, in FP64 for the last ones
+            if (sdf) {
+                const int row = t / tpr, j = t - row * tpr;
+                if (row < H) {
+                    const dfc z0 = dfc{df{0.f, 0.f}, df{0.f, 0.f}};
+                    dfc r0 = z0, r1 = z0, r2 = z0, m0 = z0, m1 = z0, m2 = z0;
+                    const bool nyq_row = 2 * row == H;
+                    for (int kx = j; kx < Wc; kx += tpr) {
+                        const dfc xb = cmul(buf[kx * CS + row], BxF[kx]);
+                        const df kap = kapd[kx], kap2 = kap2d[kx];
+                        const dfc x1 = dfc{df_neg(df_mul(kap, xb.im)), df_mul(kap, xb.re)};
+                        const dfc x2 = dfc{df_mul(kap2, xb.re), df_mul(kap2, xb.im)};
+                        if (nyq_row && kx != 0 && 2 * kx != W) {
+                            m0 = cadd(m0, xb); m1 = cadd(m1, x1); m2 = cadd(m2, x2);
+                        } else {
+                            r0 = cadd(r0, xb); r1 = cadd(r1, x1); r2 = cadd(r2, x2);
+                        }
+                    }
+                    for (int o = tpr >> 1; o > 0; o >>= 1) {
+                        r0 = cadd(r0, shfl_xor_dfc(r0, o)); r1 = cadd(r1, shfl_xor_dfc(r1, o));
+                        r2 = cadd(r2, shfl_xor_dfc(r2, o)); m0 = cadd(m0, shfl_xor_dfc(m0, o));
+                        m1 = cadd(m1, shfl_xor_dfc(m1, o)); m2 = cadd(m2, shfl_xor_dfc(m2, o));
+                    }
+                    if (j == 0) {
+                        R[3 * row] = dfc_double(r0); R[3 * row + 1] = dfc_double(r1); R[3 * row + 2] = dfc_double(r2);
+                        if (nyq_row) { R[3 * H] = dfc_double(m0); R[3 * H + 1] = dfc_double(m1); R[3 * H + 2] = dfc_double(m2); }
+                    }
+                }
+            } else {
                 const int row = t / tpr, j = t - row * tpr;
                 if (row < H) {
                     double2 r0 = {0, 0}, r1 = {0, 0}, r2 = {0, 0}, m0 = {0, 0}, m1 = {0, 0}, m2 = {0, 0};
                     const bool nyq_row = 2 * row == H;
                     for (int kx = j; kx < Wc; kx += tpr) {
                         const double kap = 2.0 * CUDART_PI * adj_freq(kx, W) / W;
-                        const double2 xb = cmul(Xs[kx * CS + row], Bx[kx]);
+                        const double2 xb = cmul(dfc_double(buf[kx * CS + row]), Bx[kx]);
                         const double2 x1 = adj_i_times(kap, xb);
                         const double2 x2 = make_double2(-kap * kap * xb.x, -kap * kap * xb.y);
                         if (nyq_row && kx != 0 && 2 * kx != W) {
@@ -230,8 +276,15 @@ __global__ void __launch_bounds__(512) adj_kernel(Geom g, AdjArgs a) {
                 st[1] = sx - dx;
                 st[2] = hyy; st[3] = hxy; st[4] = hxx;
                 ++iters;
-                if (!(fmax(fabs(dy), fabs(dx)) >= 1e-13)) sflag = 1;        // settled (or NaN: stop)
-                else if (iters >= kAdjIters) sflag = 2;
+                const double step = fmax(fabs(dy), fabs(dx));
+                if (sdf) {
+                    if (!(step >= 1e-9)) sdf = 0;                           // finish in FP64
+                    if (iters >= kAdjIters) sflag = 2;
+                } else if (!(step >= 1e-13)) {
+                    sflag = 1;                                             // settled (or NaN: stop)
+                } else if (iters >= kAdjIters) {
+                    sflag = 2;
+                }
             }
             __syncthreads();
             done = sflag != 0;
