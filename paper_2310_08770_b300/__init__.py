@@ -11,7 +11,9 @@ _BINDING = ("CC_SN", "CC_U", "Tracker", "CcstError", "RESULT_DTYPE", "decode", "
             "ccst_destroy", "ccst_grid_size", "ccst_debug_surfaces", "ccst_profile_kernel_ms",
             "ccst_profile_reset", "ccst_debug_pairs", "ccst_track_static",
             "ccst_rt_begin", "ccst_rt_track", "ccst_drift_correct", "ccst_set_reference_frame",
-            "ccst_offline_update", "ccst_offline_track", "ccst_reference_status", "ccst_peak_continuous")
+            "ccst_offline_update", "ccst_offline_track", "ccst_reference_status", "ccst_peak_continuous",
+            "ccst_add_reference", "ccst_track_rois", "make_rois", "ccst_server_create", "ccst_server_submit",
+            "ccst_server_poll", "ccst_server_read_stats", "ccst_server_loadgen", "ccst_server_destroy")
 
 
 def __getattr__(name):

@@ -78,3 +78,39 @@ def test_python_binding_raises_cleanly_without_device(lib):
         pass
     with pytest.raises(C.CcstError):
         C.ccst_create(np.zeros((64, 64), np.float32), 64, 64)
+
+
+def test_new_record_layouts_match_the_header():
+    # ccst_roi: {const void* frame; int32 H, W; int64 pitch_elems; int32 ref_id, reserved}
+    assert ctypes.sizeof(C.ccst_roi) == 32
+    assert (C.ccst_roi.frame.offset, C.ccst_roi.H.offset, C.ccst_roi.W.offset, C.ccst_roi.pitch_elems.offset,
+            C.ccst_roi.ref_id.offset) == (0, 8, 12, 16, 24)
+    # ccst_server_stats: 4 x uint64, 4 x double, int64
+    assert ctypes.sizeof(C.ccst_server_stats_t) == 72 and C.ccst_server_stats_t.in_flight.offset == 64
+
+
+def test_null_handles_are_rejected_without_gpu(lib):
+    n = None
+    assert lib.ccst_rt_begin(n, n, 0, 0.1, 0.9) == C.E_INVALID
+    assert lib.ccst_rt_track(n, n, 1, 0, n) == C.E_INVALID
+    assert lib.ccst_set_reference_frame(n, n, 0) == C.E_INVALID
+    assert lib.ccst_offline_update(n, n, 1, 0, n) == C.E_INVALID
+    assert lib.ccst_offline_track(n, n, 1, 0, 1, n) == C.E_INVALID
+    assert lib.ccst_reference_status(n, n) == C.E_INVALID
+    assert lib.ccst_peak_continuous(n, n, 1, 0, n, n, n) == C.E_INVALID
+    assert lib.ccst_backward(n, n, 1, 0, n, n, n, n) == C.E_INVALID
+    assert lib.ccst_drift_correct(n, 5, 0.1, 0.9, 0.0, 100, n, n) == C.E_INVALID
+    assert lib.ccst_drift_correct(n, -1, 0.1, 0.9, 0.0, 100, n, n) == C.E_INVALID
+    rid = ctypes.c_int()
+    assert lib.ccst_add_reference(n, n, 32, 32, ctypes.byref(rid)) == C.E_INVALID
+    assert lib.ccst_track_rois(n, n, 1, n) == C.E_INVALID
+    out = ctypes.c_void_p()
+    assert lib.ccst_server_create(n, 4, 4, ctypes.byref(out)) == C.E_INVALID
+    assert lib.ccst_server_submit(n, 0, n, 0, n) == C.E_INVALID
+    done = ctypes.c_int()
+    assert lib.ccst_server_poll(n, 1, 0, n, ctypes.byref(done)) == C.E_INVALID
+    st = C.ccst_server_stats_t()
+    assert lib.ccst_server_read_stats(n, 0, ctypes.byref(st)) == C.E_INVALID
+    lib.ccst_server_destroy(n)
+    assert lib.ccst_debug_rt_timeout(n, n, 0, n) == C.E_INVALID
+    assert lib.ccst_debug_reference(n, n) == C.E_INVALID
