@@ -78,6 +78,8 @@ extern "C" {
 #define CCST_R_NONFINITE   0x10u /* the surface held no finite value (non-finite input) */
 #define CCST_R_TIMEOUT     0x20u /* a bounded wait inside the kernel gave up (the staged stage tables never
                                     arrived); this frame and the rest of its CTA's frames are not tracked */
+#define CCST_R_GENERIC     0x80u /* tracked by the general-size path (ccst_track_rois, sides other than
+                                    16, 32, 64, 128): direct DFTs in double-float, no near-tie levels */
 #define CCST_R_RT_STALE    0x40u /* real-time mode: the reference update after this frame did not complete
                                     (a bounded wait gave up, now or earlier); the reference stays stale
                                     until the next ccst_rt_begin */
@@ -194,13 +196,19 @@ int ccst_poll(ccst_ctx* ctx, uint64_t ticket, int timeout_us, int* done);
 
 /* Add a reference for uneven-ROI batches (ccst_track_rois) and return its id in *ref_id.
  *   ref      H*W float32, row-major, host or device memory; copied.
- *   H, W     square, 16, 32, 64 or 128 pixels a side (the sizes the ROI kernel is
- *            built for); others return CCST_E_SHAPE.
+ *   H, W     square, 8 to 256 pixels a side; others return CCST_E_SHAPE.
+ *            16, 32, 64 and 128 run on the power-of-two ROI kernel (FP32 surfaces with the
+ *            near-tie levels, as ccst_track). Every other side (8, 48, 96, 192, 256, odd
+ *            sides, ...) runs on the general-size path: direct DFTs and the full-grid
+ *            upsampled sum in double-float (about 2^-46 per term), slower (O(N^3) per ROI)
+ *            but needing no near-tie levels; its records carry CCST_R_GENERIC.
  * The first reference of a new size also creates that size's plan (geometry, FFT
- * twiddles, upsampling tables) with the context's parameters (u, method, eps). Each
- * reference keeps its spectra resident (FP32, FP64 and double-float) and its FP64
- * operand: about 26 H*W bytes of device memory, owned by the context. The context's own
- * reference is id 0, usable when its frames are one of the sizes above. Synchronous.
+ * twiddles, upsampling tables) with the context's parameters (u, method, eps); for the
+ * general path u * N must not exceed 2^22. Each power-of-two reference keeps its spectra
+ * resident (FP32, FP64 and double-float) and its FP64 operand, about 26 H*W bytes; a
+ * general-size reference keeps its full N x N double-float spectrum, 16 N^2 bytes. All of
+ * it is owned by the context. The context's own reference is id 0, usable when its frames
+ * are one of the power-of-two sizes above. Synchronous.
  * Errors: CCST_E_INVALID (null pointers), CCST_E_SHAPE, CCST_E_NOMEM, CCST_E_CUDA. */
 int ccst_add_reference(ccst_ctx* ctx, const float* ref, int H, int W, int* ref_id);
 
@@ -209,8 +217,11 @@ int ccst_add_reference(ccst_ctx* ctx, const float* ref, int H, int W, int* ref_i
  *   rois      host memory, n descriptors (read during the call).
  *   out_dev   device memory, n records; record i belongs to rois[i].
  * Work items run largest ROI first; each CTA takes the next item from a counter and
- * re-plans its shared memory when the size changes. The records are identical to those of
- * ccst_track on a context made for that ROI's reference. Stream-ordered and asynchronous.
+ * re-plans its shared memory when the size changes. The records of power-of-two ROIs are
+ * identical to those of ccst_track on a context made for that ROI's reference. ROIs of
+ * general sizes run as a second persistent launch, on an internal stream, concurrently
+ * with the first; the call's work is complete when the context's stream reaches it.
+ * Stream-ordered and asynchronous.
  * Errors: CCST_E_INVALID (null pointers, n < 0, unknown ref_id, pitch < W), CCST_E_SHAPE (a
  * ROI whose size differs from its reference's), CCST_E_NOMEM, CCST_E_CUDA. */
 int ccst_track_rois(ccst_ctx* ctx, const ccst_roi* rois, int64_t n, ccst_result* out_dev);

@@ -8,12 +8,13 @@ import os
 import shutil
 import subprocess
 import sys
+import tempfile
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libccst.so")
-SOURCES = ["ccst.cu", "ccst_rois.cu"] + [f"ccst_track_h{h}.cu" for h in (8, 16, 32, 64, 128)]
+SOURCES = ["ccst.cu", "ccst_rois.cu", "ccst_generic.cu"] + [f"ccst_track_h{h}.cu" for h in (8, 16, 32, 64, 128)]
 DEPS = SOURCES + ["ccst_kernels.cuh", "ccst_device.cuh", "ccst_dfloat.cuh", "ccst_fft.cuh", "ccst_adjoint.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -37,8 +38,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     """Compile every translation unit (in parallel) and link libccst.so."""
     if not force and not _stale():
         return LIB
-    objdir = os.path.join(PKG, "_build")
-    os.makedirs(objdir, exist_ok=True)
+    objdir = tempfile.mkdtemp(prefix="ccst_build_")          # objects are not kept: every build compiles all
     flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
     if verbose:
         flags.append("-Xptxas=-v")
@@ -50,12 +50,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if verbose:
             print(" ".join(cmd))
         procs.append((src, subprocess.Popen(cmd)))
-    failed = [src for src, p in procs if p.wait() != 0]
-    if failed:
-        raise RuntimeError(f"nvcc failed for {failed}")
-    tmp = LIB + ".tmp"
-    subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp] + objs, check=True)
-    os.replace(tmp, LIB)
+    try:
+        failed = [src for src, p in procs if p.wait() != 0]
+        if failed:
+            raise RuntimeError(f"nvcc failed for {failed}")
+        tmp = LIB + ".tmp"
+        subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp] + objs, check=True)
+        os.replace(tmp, LIB)
+    finally:
+        shutil.rmtree(objdir, ignore_errors=True)
     return LIB
 
 

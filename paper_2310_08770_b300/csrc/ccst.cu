@@ -611,12 +611,31 @@ struct ccst_ctx {
         std::vector<void*> mem;       // owned allocations (none for plan 0)
     };
     struct RefEntry {
-        int cls = -1;                 // size class, -1 if not usable by ccst_track_rois
+        int cls = -1;                 // power-of-two size class, -1 if none
+        int gcls = -1;                // general size class (ccst_generic.cu), -1 if none
         RefSpectra r{};
+        const dfc* gFb = nullptr;     // general size: the full N x N F[b]
         std::vector<void*> mem;       // owned allocations (none for ref 0)
+    };
+    struct GenPlanH {
+        GenPlan p;
+        std::vector<void*> mem;
     };
     std::vector<SizePlan> plans;
     std::vector<RefEntry> refs;
+    std::vector<GenPlanH> gplans;
+    GenPlan* d_gplans = nullptr;
+    const dfc** d_grefs = nullptr;
+    size_t gplans_cap = 0, grefs_cap = 0;
+    GenItem* d_gitems = nullptr;
+    size_t gitems_cap = 0;
+    std::vector<GenItem> h_gitems;
+    dfc* d_gscratch = nullptr;
+    size_t gscratch_elems = 0;
+    cudaStream_t gstream = nullptr;   // the general-size kernel runs here, beside the main one
+    cudaEvent_t gfork = nullptr, gjoin = nullptr;
+    int gen_grid = 0;
+    bool gen_dirty = true;            // plans or references changed since the last upload
     Geom* d_geoms = nullptr;
     RefSpectra* d_refs = nullptr;
     size_t geoms_cap = 0, refs_cap = 0;
@@ -710,12 +729,19 @@ static void free_all(ccst_ctx* c) {
         for (void* p : pl.mem) cudaFree(p);
     for (auto& re : c->refs)
         for (void* p : re.mem) cudaFree(p);
+    for (auto& gp : c->gplans)
+        for (void* p : gp.mem) cudaFree(p);
     c->plans.clear();
     c->refs.clear();
+    c->gplans.clear();
+    if (c->gstream) cudaStreamDestroy(c->gstream);
+    if (c->gfork) cudaEventDestroy(c->gfork);
+    if (c->gjoin) cudaEventDestroy(c->gjoin);
     void* ptrs[] = {c->d_ref32, c->d_b64, c->d_FE64, c->d_FE32, c->d_tw64, c->d_tw32,
                     c->d_tab,   c->d_df,  c->d_frames, c->d_out, c->d_next, c->d_rtE, c->d_rtY, c->d_rtSync,
                     c->d_offPart, c->d_offScratch, c->d_adjY, c->d_geoms, c->d_refs, c->d_items, c->d_addref_tmp,
-                    c->d_graph_counters, c->d_launch_counters};
+                    c->d_graph_counters, c->d_launch_counters, c->d_gplans, c->d_grefs,
+                    c->d_gitems, c->d_gscratch};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -1553,12 +1579,19 @@ static int rois_plan(ccst_ctx* c, int H, int W, int* cls) {
     return CCST_OK;
 }
 
+static bool generic_size_ok(int H, int W) { return H == W && H >= 8 && H <= 256 && !rois_size_ok(H, W); }
+static int add_generic_reference(ccst_ctx* c, const float* ref, int N, int* ref_id);
+
 extern "C" int ccst_add_reference(ccst_ctx* c, const float* ref, int H, int W, int* ref_id) {
     int rc = check_ctx(c);
     if (rc) return rc;
     if (!ref || !ref_id) return fail(c, CCST_E_INVALID, "ccst_add_reference: null ref or ref_id");
+    if (generic_size_ok(H, W)) {
+        rois_init(c);
+        return add_generic_reference(c, ref, H, ref_id);
+    }
     if (!rois_size_ok(H, W))
-        return fail(c, CCST_E_SHAPE, "ccst_add_reference: ROIs are square, 16, 32, 64 or 128 pixels a side");
+        return fail(c, CCST_E_SHAPE, "ccst_add_reference: ROIs are square, 8 to 256 pixels a side");
     rois_init(c);
     int cls = 0;
     if ((rc = rois_plan(c, H, W, &cls))) return rc;
@@ -1613,6 +1646,7 @@ extern "C" int ccst_add_reference(ccst_ctx* c, const float* ref, int H, int W, i
     re.r = RefSpectra{FE32, FE64, b64, FEdf};
     c->refs.push_back(re);
     c->rois_dirty = true;
+    c->gen_dirty = true;
     *ref_id = (int)c->refs.size() - 1;
     return CCST_OK;
 }
@@ -1657,6 +1691,168 @@ static int rois_upload(ccst_ctx* c) {
     return CCST_OK;
 }
 
+// ---------------------------------------------------- uneven-ROI batches: general sizes
+// A side N outside the power-of-two ROI kernel (8, 48, 96, 192, 256, ...) gets a plan of
+// the double-float path: e^{-2 pi i m / N} and e^{+2 pi i m / (uN)} tables.
+static int gen_plan(ccst_ctx* c, int N, int* gcls) {
+    for (size_t i = 0; i < c->gplans.size(); ++i)
+        if (c->gplans[i].p.N == N) {
+            *gcls = (int)i;
+            return CCST_OK;
+        }
+    const long long D = (long long)c->p.upsample * N;
+    if (D > (1LL << 22)) return fail(c, CCST_E_SHAPE, "ccst_add_reference: u x N above 2^22 for a general size");
+    ccst_ctx::GenPlanH gp;
+    GenPlan& pl = gp.p;
+    pl.N = N;
+    pl.u = c->p.upsample;
+    pl.M = c->g.M;
+    pl.h0 = c->g.h0;
+    pl.method = c->p.method;
+    pl.in_dtype = c->p.in_dtype;
+    pl.eps = c->p.eps;
+    pl.sense = c->p.method == CCST_CC_SN ? -1.f : 1.f;
+    dfc* tab = nullptr;
+    CK(c, cudaMalloc(&tab, (size_t)(N + D) * sizeof(dfc)));
+    gp.mem.push_back(tab);
+    pl.wN = tab;
+    pl.wU = tab + N;
+    dfc* wU = tab + N;
+    void* a2[] = {&N, &pl.u, &tab, &wU};
+    CK(c, cudaLaunchKernel(gen_init_tables_ptr(), dim3(64), dim3(256), a2, 0, c->stream));
+    c->gplans.push_back(gp);
+    *gcls = (int)c->gplans.size() - 1;
+    c->rois_dirty = true;
+    c->gen_dirty = true;
+    return CCST_OK;
+}
+
+static int add_generic_reference(ccst_ctx* c, const float* ref, int N, int* ref_id) {
+    int gcls = 0, rc;
+    if ((rc = gen_plan(c, N, &gcls))) return rc;
+    const size_t NN = (size_t)N * N;
+    ccst_ctx::RefEntry re;
+    re.gcls = gcls;
+    dfc* Fb = nullptr;
+    cudaError_t e = cudaMalloc(&Fb, NN * sizeof(dfc));
+    if (e != cudaSuccess)
+        return fail(c, e == cudaErrorMemoryAllocation ? CCST_E_NOMEM : CCST_E_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    re.mem.push_back(Fb);
+    const size_t ntmp = NN * sizeof(float) + NN * sizeof(double2);
+    if (c->addref_tmp_bytes < ntmp) {
+        if (c->d_addref_tmp) cudaFree(c->d_addref_tmp);
+        c->d_addref_tmp = nullptr;
+        c->addref_tmp_bytes = 0;
+        e = cudaMalloc(&c->d_addref_tmp, ntmp);
+        if (e != cudaSuccess) {
+            cudaFree(Fb);
+            return fail(c, e == cudaErrorMemoryAllocation ? CCST_E_NOMEM : CCST_E_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        c->addref_tmp_bytes = ntmp;
+    }
+    double2* R = (double2*)c->d_addref_tmp;
+    float* ref32 = (float*)((char*)c->d_addref_tmp + NN * sizeof(double2));
+    int method = c->p.method;
+    float eps = c->p.eps;
+    e = cudaMemcpyAsync(ref32, ref, NN * sizeof(float), cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess) {
+        void* ar[] = {&N, &method, &eps, &ref32, &R};
+        e = cudaLaunchKernel(gen_ref_rows_ptr(), dim3(64), dim3(256), ar, 0, c->stream);
+    }
+    if (e == cudaSuccess) {
+        void* ac[] = {&N, &R, &Fb};
+        e = cudaLaunchKernel(gen_ref_cols_ptr(), dim3(64), dim3(256), ac, 0, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaFree(Fb);
+        return fail(c, CCST_E_CUDA, std::string("ccst_add_reference: ") + cudaGetErrorString(e));
+    }
+    re.gFb = Fb;
+    c->refs.push_back(re);
+    c->rois_dirty = true;
+    c->gen_dirty = true;
+    *ref_id = (int)c->refs.size() - 1;
+    return CCST_OK;
+}
+
+// Launch the general-size items on the context's second stream, forked from the context's
+// stream; the caller joins it back (gjoin) after issuing the power-of-two batch.
+static int gen_launch(ccst_ctx* c, int64_t n, Result* out) {
+    if (n == 0) return CCST_OK;
+    if (!c->gstream) {
+        CK(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+        CK(c, cudaEventCreateWithFlags(&c->gfork, cudaEventDisableTiming));
+        CK(c, cudaEventCreateWithFlags(&c->gjoin, cudaEventDisableTiming));
+        int sms = 0;
+        CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+        c->gen_grid = sms;
+    }
+    if (c->gplans_cap < c->gplans.size()) {
+        if (c->d_gplans) cudaFree(c->d_gplans);
+        c->d_gplans = nullptr;
+        c->gplans_cap = 0;
+        CK(c, cudaMalloc(&c->d_gplans, 2 * c->gplans.size() * sizeof(GenPlan)));
+        c->gplans_cap = 2 * c->gplans.size();
+    }
+    if (c->grefs_cap < c->refs.size()) {
+        if (c->d_grefs) cudaFree(c->d_grefs);
+        c->d_grefs = nullptr;
+        c->grefs_cap = 0;
+        CK(c, cudaMalloc(&c->d_grefs, 2 * c->refs.size() * sizeof(dfc*)));
+        c->grefs_cap = 2 * c->refs.size();
+    }
+    size_t stride = 0;
+    for (auto& g : c->gplans) stride = std::max(stride, 2 * (size_t)g.p.N * g.p.N + (size_t)g.p.N * g.p.M);
+    if (c->gen_dirty) {
+        std::vector<GenPlan> gp;
+        for (auto& g : c->gplans) gp.push_back(g.p);
+        std::vector<const dfc*> gr;
+        for (auto& re : c->refs) gr.push_back(re.gFb);
+        CK(c, cudaMemcpy(c->d_gplans, gp.data(), gp.size() * sizeof(GenPlan), cudaMemcpyHostToDevice));
+        CK(c, cudaMemcpy(c->d_grefs, gr.data(), gr.size() * sizeof(dfc*), cudaMemcpyHostToDevice));
+        c->gen_dirty = false;
+    }
+    const int grid = (int)(n < c->gen_grid ? n : c->gen_grid);
+    if (c->gscratch_elems < (size_t)grid * stride) {
+        if (c->d_gscratch) cudaFree(c->d_gscratch);
+        c->d_gscratch = nullptr;
+        c->gscratch_elems = 0;
+        CK(c, cudaMalloc(&c->d_gscratch, (size_t)grid * stride * sizeof(dfc)));
+        c->gscratch_elems = (size_t)grid * stride;
+    }
+    if (c->gitems_cap < (size_t)n) {
+        if (c->d_gitems) cudaFree(c->d_gitems);
+        c->d_gitems = nullptr;
+        c->gitems_cap = 0;
+        CK(c, cudaMalloc(&c->d_gitems, (size_t)n * sizeof(GenItem)));
+        c->gitems_cap = (size_t)n;
+    }
+    CK(c, cudaEventRecord(c->gfork, c->stream));
+    CK(c, cudaStreamWaitEvent(c->gstream, c->gfork, 0));
+    // largest sides first
+    std::stable_sort(c->h_gitems.begin(), c->h_gitems.begin() + n, [&](const GenItem& a, const GenItem& b) {
+        return c->gplans[a.plan].p.N > c->gplans[b.plan].p.N;
+    });
+    CK(c, cudaMemcpyAsync(c->d_gitems, c->h_gitems.data(), (size_t)n * sizeof(GenItem), cudaMemcpyHostToDevice,
+                          c->gstream));
+    unsigned* counter = c->d_next + 24;
+    CK(c, cudaMemsetAsync(counter, 0, sizeof(unsigned), c->gstream));
+    GenBatch gb;
+    gb.items = c->d_gitems;
+    gb.n = n;
+    gb.plans = c->d_gplans;
+    gb.refs = c->d_grefs;
+    gb.out = out;
+    gb.next = counter;
+    gb.scratch = c->d_gscratch;
+    gb.scratch_stride = (long long)stride;
+    void* args[] = {&gb};
+    CK(c, cudaLaunchKernel(track_generic_kernel_ptr(), dim3(grid), dim3(512), args, 0, c->gstream));
+    CK(c, cudaEventRecord(c->gjoin, c->gstream));
+    return CCST_OK;
+}
+
 // Sort items largest first (the longest work starts first; size classes stay contiguous),
 // copy them to items_dev (n slots) and launch the ROI kernel on `stream` with `counter`.
 // The host items must stay valid until the copy has been issued (it is staged at once).
@@ -1691,31 +1887,45 @@ extern "C" int ccst_track_rois(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccs
     rois_init(c);
     const size_t elem = c->p.in_dtype == CCST_U16 ? 2 : 4;
     c->h_items.resize((size_t)n);
+    c->h_gitems.resize((size_t)n);
+    int64_t np = 0, ng = 0;
     for (int64_t i = 0; i < n; ++i) {
         const ccst_roi& q = rois[i];
-        if (q.ref_id < 0 || q.ref_id >= (int)c->refs.size() || c->refs[q.ref_id].cls < 0)
+        if (q.ref_id < 0 || q.ref_id >= (int)c->refs.size() || (c->refs[q.ref_id].cls < 0 && c->refs[q.ref_id].gcls < 0))
             return fail(c, CCST_E_INVALID, "ccst_track_rois: unknown or unusable ref_id");
-        const Geom& pg = c->plans[c->refs[q.ref_id].cls].g;
-        if (q.H != pg.H || q.W != pg.W) return fail(c, CCST_E_SHAPE, "ccst_track_rois: ROI size differs from its reference");
+        const auto& re = c->refs[q.ref_id];
+        const int side = re.cls >= 0 ? c->plans[re.cls].g.H : c->gplans[re.gcls].p.N;
+        if (q.H != side || q.W != side) return fail(c, CCST_E_SHAPE, "ccst_track_rois: ROI size differs from its reference");
         const int64_t pitch = q.pitch_elems == 0 ? q.W : q.pitch_elems;
         if (!q.frame || pitch < q.W) return fail(c, CCST_E_INVALID, "ccst_track_rois: null frame or pitch < W");
-        RoiItem& it = c->h_items[(size_t)i];
+        if (re.gcls >= 0) {
+            c->h_gitems[(size_t)ng++] = GenItem{q.frame, (long long)pitch, i, re.gcls, q.ref_id};
+            continue;
+        }
+        RoiItem& it = c->h_items[(size_t)np++];
         it.frame = q.frame;
         it.pitch = pitch;
         it.out_index = i;
-        it.cls = c->refs[q.ref_id].cls;
+        it.cls = re.cls;
         it.ref = q.ref_id;
         it.vec_ok = ((uintptr_t)q.frame % 16 == 0) && ((size_t)pitch * elem % 16 == 0) ? 1 : 0;
         it.pad = 0;
     }
-    if (c->items_cap < (size_t)n) {
-        if (c->d_items) cudaFree(c->d_items);
-        c->d_items = nullptr;
-        c->items_cap = 0;
-        CK(c, cudaMalloc(&c->d_items, (size_t)n * sizeof(RoiItem)));
-        c->items_cap = (size_t)n;
+    if ((rc = gen_launch(c, ng, (Result*)out_dev))) return rc;
+    if (np > 0) {
+        n = np;
+        if (c->items_cap < (size_t)n) {
+            if (c->d_items) cudaFree(c->d_items);
+            c->d_items = nullptr;
+            c->items_cap = 0;
+            CK(c, cudaMalloc(&c->d_items, (size_t)n * sizeof(RoiItem)));
+            c->items_cap = (size_t)n;
+        }
+        if ((rc = rois_launch(c, c->h_items.data(), n, (Result*)out_dev, c->stream, c->d_items, c->d_next + 16)))
+            return rc;
     }
-    return rois_launch(c, c->h_items.data(), n, (Result*)out_dev, c->stream, c->d_items, c->d_next + 16);
+    if (ng > 0) CK(c, cudaStreamWaitEvent(c->stream, c->gjoin, 0));     // both batches done
+    return CCST_OK;
 }
 
 // ---------------------------------------------------------------------- serving

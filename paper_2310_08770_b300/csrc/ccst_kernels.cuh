@@ -119,6 +119,33 @@ struct RoiBatch {
     unsigned* next;         // item counter, zeroed before the launch
 };
 
+// General square sizes (ccst_generic.cu): one plan per side N, items, launch arguments.
+struct GenPlan {
+    int N, u, M, h0, method, in_dtype;
+    float eps, sense;
+    const dfc* wN;          // N:    e^{-2 pi i m / N}
+    const dfc* wU;          // u N:  e^{+2 pi i m / (u N)}
+};
+
+struct GenItem {
+    const void* frame;
+    long long pitch;
+    long long out_index;
+    int plan;
+    int ref;
+};
+
+struct GenBatch {
+    const GenItem* items;
+    long long n;
+    const GenPlan* plans;
+    const dfc* const* refs;  // full N x N F[b] per reference (double-float)
+    Result* out;
+    unsigned* next;
+    dfc* scratch;            // per CTA: scratch_stride complex double-floats
+    long long scratch_stride;
+};
+
 struct Result {  // mirrors ccst_result
     float dx, dy, peak;
     int ipy, ipx;
@@ -1879,6 +1906,11 @@ __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
 
 // Address of the uneven-ROI kernel (ccst_rois.cu).
 const void* track_rois_kernel_ptr();
+// The general-size path (ccst_generic.cu).
+const void* track_generic_kernel_ptr();
+const void* gen_init_tables_ptr();
+const void* gen_ref_rows_ptr();
+const void* gen_ref_cols_ptr();
 
 // Address of track_kernel<H, W> (defined in the per-height translation units).
 const void* track_kernel_h8(int W);

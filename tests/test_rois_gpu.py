@@ -107,7 +107,7 @@ def test_rois_errors(torch):
     ref = synth.gaussian_spot(32, 32, 16, 16, 2.0, 800.0, 10.0).astype(np.float32)
     t = C.Tracker(ref, upsample=20, in_dtype="f32")
     with pytest.raises(C.CcstError) as e:
-        C.ccst_add_reference(t.ctx, np.zeros((48, 48), np.float32), 48, 48)   # no radix-3 sizes
+        C.ccst_add_reference(t.ctx, np.zeros((300, 300), np.float32), 300, 300)   # above 256
     assert e.value.code == C.E_SHAPE
     with pytest.raises(C.CcstError):
         C.ccst_add_reference(t.ctx, np.zeros((32, 64), np.float32), 32, 64)   # not square
