@@ -566,6 +566,21 @@ __global__ void rt_drift(const Result* rec, long long n, double a0, double b1, d
 }  // namespace
 
 // ---------------------------------------------------------------- context
+// Scratch of the general-size kernel for one stream of launches: launches that share a
+// lane must run one after another (their CTAs reuse the same scratch).
+struct GenLane {
+    dfc* scratch = nullptr;
+    size_t scratch_elems = 0;
+    GenItem* d_items = nullptr;
+    size_t items_cap = 0;
+};
+
+static void lane_free(GenLane& l) {
+    if (l.scratch) cudaFree(l.scratch);
+    if (l.d_items) cudaFree(l.d_items);
+    l = GenLane{};
+}
+
 struct ccst_ctx {
     Geom g{};
     ccst_params p{};
@@ -614,7 +629,7 @@ struct ccst_ctx {
         int cls = -1;                 // power-of-two size class, -1 if none
         int gcls = -1;                // general size class (ccst_generic.cu), -1 if none
         RefSpectra r{};
-        const dfc* gFb = nullptr;     // general size: the full N x N F[b]
+        const dfc* gFb = nullptr;     // general size: the half spectrum F[b], H x (W/2 + 1)
         std::vector<void*> mem;       // owned allocations (none for ref 0)
     };
     struct GenPlanH {
@@ -627,15 +642,15 @@ struct ccst_ctx {
     GenPlan* d_gplans = nullptr;
     const dfc** d_grefs = nullptr;
     size_t gplans_cap = 0, grefs_cap = 0;
-    GenItem* d_gitems = nullptr;
-    size_t gitems_cap = 0;
     std::vector<GenItem> h_gitems;
-    dfc* d_gscratch = nullptr;
-    size_t gscratch_elems = 0;
-    cudaStream_t gstream = nullptr;   // the general-size kernel runs here, beside the main one
+    // lane 0: ccst_track and ccst_track_rois (ordered through the context's stream);
+    // lanes 1 and 2: the two streams of the pipelined host path
+    GenLane glane[3];
+    cudaStream_t gstream = nullptr;   // ROI batches run their general sizes here, beside the main kernel
     cudaEvent_t gfork = nullptr, gjoin = nullptr;
     int gen_grid = 0;
     bool gen_dirty = true;            // plans or references changed since the last upload
+    bool general = false;             // every frame of this context takes the general-size kernel
     Geom* d_geoms = nullptr;
     RefSpectra* d_refs = nullptr;
     size_t geoms_cap = 0, refs_cap = 0;
@@ -740,11 +755,16 @@ static void free_all(ccst_ctx* c) {
     void* ptrs[] = {c->d_ref32, c->d_b64, c->d_FE64, c->d_FE32, c->d_tw64, c->d_tw32,
                     c->d_tab,   c->d_df,  c->d_frames, c->d_out, c->d_next, c->d_rtE, c->d_rtY, c->d_rtSync,
                     c->d_offPart, c->d_offScratch, c->d_adjY, c->d_geoms, c->d_refs, c->d_items, c->d_addref_tmp,
-                    c->d_graph_counters, c->d_launch_counters, c->d_gplans, c->d_grefs,
-                    c->d_gitems, c->d_gscratch};
+                    c->d_graph_counters, c->d_launch_counters, c->d_gplans, c->d_grefs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    for (auto& l : c->glane) lane_free(l);
 }
+
+static int gen_track(ccst_ctx* c, const Batch& b, cudaStream_t stream, GenLane& lane, unsigned* counter);
+static int gen_ref_spectrum(ccst_ctx* c, int H, int W, const void* src, int frame_kind, long long pitch, dfc* Fb);
+static int add_generic_reference(ccst_ctx* c, const float* ref, int H, int W, int* ref_id);
+static int not_general(ccst_ctx* c, const char* who);
 
 extern "C" int ccst_version(void) { return CCST_VERSION; }
 
@@ -761,13 +781,66 @@ extern "C" int ccst_default_params(ccst_params* p) {
     return CCST_OK;
 }
 
+// A general-shape context (H, W in [8, 256], not both powers of two up to 128): plan 0 is
+// its shape, ref 0 its reference as a half spectrum for the general-size kernel, which
+// every batch of the context runs on.
+static int create_general(const float* ref, int H, int W, const ccst_params& p, ccst_ctx** out) {
+    ccst_ctx* c = new (std::nothrow) ccst_ctx();
+    if (!c) return fail(nullptr, CCST_E_NOMEM, "ccst_create: host allocation failed");
+    c->p = p;
+    c->stream = (cudaStream_t)p.stream;
+    c->general = true;
+    auto bail = [&](int code) {
+        fail(nullptr, code, "ccst_create: " + c->err);
+        free_all(c);
+        delete c;
+        return code;
+    };
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+        c->err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+        return bail(CCST_E_CUDA);
+    }
+    Geom& g = c->g;
+    g.H = H; g.W = W; g.Wc = W / 2 + 1;
+    g.u = p.upsample; g.M = (3 * p.upsample + 1) / 2; g.h0 = g.M / 2; g.pmax = g.M - 1 - g.h0;
+    g.method = p.method; g.in_dtype = p.in_dtype; g.eps = p.eps;
+    g.sense = p.method == CCST_CC_U ? 1.f : -1.f;
+    const size_t elem = p.in_dtype == CCST_U16 ? 2 : 4;
+    struct { void** ptr; size_t bytes; } allocs[] = {
+        {(void**)&c->d_frames, (size_t)p.max_batch * H * W * elem},
+        {(void**)&c->d_out, (size_t)p.max_batch * sizeof(Result)},
+        {(void**)&c->d_next, 256},
+        {(void**)&c->d_launch_counters, kTickets * sizeof(unsigned)},
+    };
+    for (auto& a : allocs)
+        if ((e = cudaMalloc(a.ptr, a.bytes)) != cudaSuccess) {
+            c->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+            return bail(e == cudaErrorMemoryAllocation ? CCST_E_NOMEM : CCST_E_CUDA);
+        }
+    for (int i = 0; i < kTickets; ++i)
+        if ((e = cudaEventCreateWithFlags(&c->ev[i], cudaEventDisableTiming)) != cudaSuccess) {
+            c->err = std::string("event: ") + cudaGetErrorString(e);
+            return bail(CCST_E_CUDA);
+        }
+    ccst_ctx::SizePlan p0;
+    p0.g = g;
+    c->plans.push_back(p0);
+    int id = -1;
+    const int rc = add_generic_reference(c, ref, H, W, &id);
+    if (rc) return bail(rc);
+    *out = c;
+    return CCST_OK;
+}
+
 extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pin, ccst_ctx** out) {
     if (!ref || !out) return fail(nullptr, CCST_E_INVALID, "ccst_create: null ref or out");
     *out = nullptr;
     ccst_params p;
     if (pin) p = *pin; else ccst_default_params(&p);
-    if (!is_pow2(H) || !is_pow2(W) || H < 8 || W < 8 || H > 128 || W > 128)
-        return fail(nullptr, CCST_E_SHAPE, "ccst_create: H and W must be powers of two in [8, 128]");
+    const bool fast = is_pow2(H) && is_pow2(W) && H >= 8 && W >= 8 && H <= 128 && W <= 128;
+    if (H < 8 || W < 8 || H > 256 || W > 256)
+        return fail(nullptr, CCST_E_SHAPE, "ccst_create: H and W must be in [8, 256]");
     if (p.upsample < 1 || p.upsample > 16384)
         return fail(nullptr, CCST_E_INVALID, "ccst_create: upsample must be in [1, 16384]");
     if (p.method != CCST_CC_U && p.method != CCST_CC_SN)
@@ -777,6 +850,7 @@ extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pi
     if (p.max_batch < 1) return fail(nullptr, CCST_E_INVALID, "ccst_create: max_batch must be > 0");
     if (p.method == CCST_CC_SN && !(p.eps == p.eps))
         return fail(nullptr, CCST_E_INVALID, "ccst_create: eps is NaN");
+    if (!fast) return create_general(ref, H, W, p, out);
 
     ccst_ctx* c = new (std::nothrow) ccst_ctx();
     if (!c) return fail(nullptr, CCST_E_NOMEM, "ccst_create: host allocation failed");
@@ -971,6 +1045,7 @@ extern "C" int ccst_track(ccst_ctx* c, const void* frames_dev, int64_t n, int64_
     Batch b;
     if ((rc = make_batch(c, frames_dev, n, pitch_elems, out_dev, &b))) return rc;
     if (n == 0) return CCST_OK;
+    if (c->general) return gen_track(c, b, c->stream, c->glane[0], c->d_launch_counters + (c->launch_seq++ % kTickets));
     const bool graphs = (c->p.flags & CCST_FLAG_GRAPHS) && c->stream != nullptr;
     if (!graphs) return launch(c, b);
     auto key = std::make_tuple(frames_dev, (long long)n, (long long)b.pitch, (void*)out_dev);
@@ -1065,7 +1140,9 @@ extern "C" int ccst_submit_host(ccst_ctx* c, const void* frames_host, int64_t n,
                                 (size_t)n * c->g.H, cudaMemcpyHostToDevice, st));
         Batch b;
         if ((rc = make_batch(c, c->h_frames[hs], n, 0, (ccst_result*)c->h_out[hs], &b))) return rc;
-        if ((rc = launch_on(c, b, st, c->h_next + 64 * hs))) return rc;
+        rc = c->general ? gen_track(c, b, st, c->glane[1 + (hs & 1)], c->h_next + 64 * hs)
+                        : launch_on(c, b, st, c->h_next + 64 * hs);
+        if (rc) return rc;
         CK(c, cudaMemcpyAsync(out_host, c->h_out[hs], (size_t)n * sizeof(Result), cudaMemcpyDeviceToHost, st));
     }
     CK(c, cudaEventRecord(c->ev[slot], st));
@@ -1139,6 +1216,7 @@ static int adj_run(ccst_ctx* c, const void* frames, int64_t n, int64_t pitch, co
                    const char* who) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if ((rc = not_general(c, who))) return rc;
     if (n < 0) return fail(c, CCST_E_INVALID, std::string(who) + ": n < 0");
     if (n > 0 && (!rec || !frames)) return fail(c, CCST_E_INVALID, std::string(who) + ": null frames or records");
     if (pitch == 0) pitch = c->g.W;
@@ -1210,6 +1288,7 @@ extern "C" int ccst_debug_surfaces(ccst_ctx* c, const void* frames_dev, int64_t 
                                    ccst_result* out_dev, float* int_surf_dev, float* sub_surf_dev) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if ((rc = not_general(c, "ccst_debug_surfaces"))) return rc;
     Batch b;
     if ((rc = make_batch(c, frames_dev, n, pitch_elems, out_dev, &b))) return rc;
     b.dbg_int = int_surf_dev;
@@ -1220,6 +1299,7 @@ extern "C" int ccst_debug_surfaces(ccst_ctx* c, const void* frames_dev, int64_t 
 extern "C" int ccst_profile_kernel_ms(ccst_ctx* c, double* sum_ms, int64_t* launches) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if ((rc = not_general(c, "ccst_profile_kernel_ms"))) return rc;
     if (!(c->p.flags & CCST_FLAG_PROFILE) || !sum_ms || !launches)
         return fail(c, CCST_E_INVALID, "profiling is off or null output");
     CK(c, cudaStreamSynchronize(c->stream));
@@ -1243,6 +1323,7 @@ extern "C" int ccst_profile_kernel_ms(ccst_ctx* c, double* sum_ms, int64_t* laun
 extern "C" int ccst_profile_reset(ccst_ctx* c) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if ((rc = not_general(c, "ccst_profile_reset"))) return rc;
     c->prof_used = 0;
     c->prof_next = 0;
     return CCST_OK;
@@ -1255,6 +1336,7 @@ extern "C" int ccst_debug_pairs(ccst_ctx* c, const void* frames_dev, int64_t n, 
                                 const int32_t* pairs_dev, float* d32_dev, double* d64_dev) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if ((rc = not_general(c, "ccst_debug_pairs"))) return rc;
     if (!pairs_dev || !d32_dev || !d64_dev) return fail(c, CCST_E_INVALID, "null pair buffers");
     Batch b;
     if ((rc = make_batch(c, frames_dev, n, pitch_elems, (ccst_result*)c->d_out, &b))) return rc;
@@ -1275,6 +1357,7 @@ extern "C" int ccst_debug_timeout(ccst_ctx* c, const void* frames_dev, int64_t n
                                   ccst_result* out_dev) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if ((rc = not_general(c, "ccst_debug_timeout"))) return rc;
     Batch b;
     if ((rc = make_batch(c, frames_dev, n, pitch_elems, out_dev, &b))) return rc;
     b.dbg_no_copy = 1;
@@ -1350,6 +1433,8 @@ extern "C" int ccst_set_reference_frame(ccst_ctx* c, const void* frame_dev, int6
     int rc = check_ctx(c);
     if (rc) return rc;
     if ((rc = check_frame(c, frame_dev, &pitch_elems, "ccst_set_reference_frame"))) return rc;
+    if (c->general)
+        return gen_ref_spectrum(c, c->g.H, c->g.W, frame_dev, 1, pitch_elems, (dfc*)c->refs[0].gFb);
     if ((rc = rt_prepare(c))) return rc;
     CK(c, cudaMemsetAsync(c->d_rtSync, 0, 4 * sizeof(unsigned), c->stream));
     c->rt_seq = 0;
@@ -1359,6 +1444,7 @@ extern "C" int ccst_set_reference_frame(ccst_ctx* c, const void* frame_dev, int6
 extern "C" int ccst_rt_begin(ccst_ctx* c, const void* frame0_dev, int64_t pitch_elems, double a0, double b1) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if ((rc = not_general(c, "ccst_rt_begin"))) return rc;
     if (!std::isfinite(a0) || !std::isfinite(b1)) return fail(c, CCST_E_INVALID, "ccst_rt_begin: a0, b1 not finite");
     if ((rc = check_frame(c, frame0_dev, &pitch_elems, "ccst_rt_begin"))) return rc;
     if ((rc = ccst_set_reference_frame(c, frame0_dev, pitch_elems))) return rc;
@@ -1372,6 +1458,7 @@ extern "C" int ccst_rt_track(ccst_ctx* c, const void* frames_dev, int64_t n, int
                              ccst_result* out_dev) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if ((rc = not_general(c, "ccst_rt_track"))) return rc;
     if (!c->rt_on) return fail(c, CCST_E_INVALID, "ccst_rt_track: no real-time reference (ccst_rt_begin)");
     if (n < 0) return fail(c, CCST_E_INVALID, "ccst_rt_track: n < 0");
     if (n == 0) return CCST_OK;
@@ -1417,6 +1504,7 @@ extern "C" int ccst_offline_update(ccst_ctx* c, const void* frames_dev, int64_t 
                                    const ccst_result* rec_dev) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if ((rc = not_general(c, "ccst_offline_update"))) return rc;
     if (n < 0) return fail(c, CCST_E_INVALID, "ccst_offline_update: n < 0");
     if (n == 0) return CCST_OK;
     if (!rec_dev) return fail(c, CCST_E_INVALID, "ccst_offline_update: null records");
@@ -1438,6 +1526,7 @@ extern "C" int ccst_offline_track(ccst_ctx* c, const void* frames_dev, int64_t n
                                   ccst_result* out_dev) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if ((rc = not_general(c, "ccst_offline_track"))) return rc;
     if (n < 1 || passes < 0) return fail(c, CCST_E_INVALID, "ccst_offline_track: n < 1 or passes < 0");
     if (!out_dev) return fail(c, CCST_E_INVALID, "ccst_offline_track: null out");
     if ((rc = check_frame(c, frames_dev, &pitch_elems, "ccst_offline_track"))) return rc;
@@ -1472,6 +1561,7 @@ extern "C" int ccst_reference_status(ccst_ctx* c, int* stale) {
 extern "C" int ccst_debug_reference(ccst_ctx* c, double* ref_dev) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if ((rc = not_general(c, "ccst_debug_reference"))) return rc;
     if (!ref_dev) return fail(c, CCST_E_INVALID, "ccst_debug_reference: null buffer");
     CK(c, cudaMemcpyAsync(ref_dev, c->d_b64, (size_t)c->g.H * c->g.W * sizeof(double), cudaMemcpyDeviceToDevice,
                           c->stream));
@@ -1482,6 +1572,7 @@ extern "C" int ccst_debug_rt_timeout(ccst_ctx* c, const void* frame_dev, int64_t
                                      ccst_result* rec_dev) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if ((rc = not_general(c, "ccst_debug_rt_timeout"))) return rc;
     if (!c->rt_on) return fail(c, CCST_E_INVALID, "ccst_debug_rt_timeout: no real-time reference (ccst_rt_begin)");
     if (!frame_dev || !rec_dev) return fail(c, CCST_E_INVALID, "ccst_debug_rt_timeout: null frame or record");
     if (pitch_elems == 0) pitch_elems = c->g.W;
@@ -1580,7 +1671,6 @@ static int rois_plan(ccst_ctx* c, int H, int W, int* cls) {
 }
 
 static bool generic_size_ok(int H, int W) { return H == W && H >= 8 && H <= 256 && !rois_size_ok(H, W); }
-static int add_generic_reference(ccst_ctx* c, const float* ref, int N, int* ref_id);
 
 extern "C" int ccst_add_reference(ccst_ctx* c, const float* ref, int H, int W, int* ref_id) {
     int rc = check_ctx(c);
@@ -1588,7 +1678,7 @@ extern "C" int ccst_add_reference(ccst_ctx* c, const float* ref, int H, int W, i
     if (!ref || !ref_id) return fail(c, CCST_E_INVALID, "ccst_add_reference: null ref or ref_id");
     if (generic_size_ok(H, W)) {
         rois_init(c);
-        return add_generic_reference(c, ref, H, ref_id);
+        return add_generic_reference(c, ref, H, W, ref_id);
     }
     if (!rois_size_ok(H, W))
         return fail(c, CCST_E_SHAPE, "ccst_add_reference: ROIs are square, 8 to 256 pixels a side");
@@ -1691,35 +1781,44 @@ static int rois_upload(ccst_ctx* c) {
     return CCST_OK;
 }
 
-// ---------------------------------------------------- uneven-ROI batches: general sizes
-// A side N outside the power-of-two ROI kernel (8, 48, 96, 192, 256, ...) gets a plan of
-// the double-float path: e^{-2 pi i m / N} and e^{+2 pi i m / (uN)} tables.
-static int gen_plan(ccst_ctx* c, int N, int* gcls) {
+// ------------------------------------------------------------------- general sizes
+// A shape outside the power-of-two kernel (48, 96, 192, 256, 256 x 128, ...) gets a plan
+// of the double-float path: e^{-2 pi i m / H}, e^{-2 pi i m / W}, e^{+2 pi i m / (uH)} and
+// e^{+2 pi i m / (uW)} in one table block.
+static int gen_plan(ccst_ctx* c, int H, int W, int* gcls) {
     for (size_t i = 0; i < c->gplans.size(); ++i)
-        if (c->gplans[i].p.N == N) {
+        if (c->gplans[i].p.H == H && c->gplans[i].p.W == W) {
             *gcls = (int)i;
             return CCST_OK;
         }
-    const long long D = (long long)c->p.upsample * N;
-    if (D > (1LL << 22)) return fail(c, CCST_E_SHAPE, "ccst_add_reference: u x N above 2^22 for a general size");
+    int u = c->p.upsample;
+    const long long DH = (long long)u * H, DW = (long long)u * W;
+    if (DH > (1LL << 22) || DW > (1LL << 22))
+        return fail(c, CCST_E_SHAPE, "general size: u x N above 2^22");
     ccst_ctx::GenPlanH gp;
     GenPlan& pl = gp.p;
-    pl.N = N;
-    pl.u = c->p.upsample;
-    pl.M = c->g.M;
-    pl.h0 = c->g.h0;
+    pl.H = H;
+    pl.W = W;
+    pl.u = u;
+    pl.M = (3 * u + 1) / 2;
+    pl.h0 = pl.M / 2;
     pl.method = c->p.method;
     pl.in_dtype = c->p.in_dtype;
     pl.eps = c->p.eps;
     pl.sense = c->p.method == CCST_CC_SN ? -1.f : 1.f;
     dfc* tab = nullptr;
-    CK(c, cudaMalloc(&tab, (size_t)(N + D) * sizeof(dfc)));
+    CK(c, cudaMalloc(&tab, (size_t)(H + W + DH + DW) * sizeof(dfc)));
     gp.mem.push_back(tab);
-    pl.wN = tab;
-    pl.wU = tab + N;
-    dfc* wU = tab + N;
-    void* a2[] = {&N, &pl.u, &tab, &wU};
-    CK(c, cudaLaunchKernel(gen_init_tables_ptr(), dim3(64), dim3(256), a2, 0, c->stream));
+    pl.wH = tab;
+    pl.wW = tab + H;
+    pl.uH = tab + H + W;
+    pl.uW = tab + H + W + DH;
+    void* a2[] = {&H, &W, &u, &tab};
+    const cudaError_t e = cudaLaunchKernel(gen_init_tables_ptr(), dim3(64), dim3(256), a2, 0, c->stream);
+    if (e != cudaSuccess) {
+        cudaFree(tab);
+        return fail(c, CCST_E_CUDA, std::string("gen_init_tables: ") + cudaGetErrorString(e));
+    }
     c->gplans.push_back(gp);
     *gcls = (int)c->gplans.size() - 1;
     c->rois_dirty = true;
@@ -1727,47 +1826,55 @@ static int gen_plan(ccst_ctx* c, int N, int* gcls) {
     return CCST_OK;
 }
 
-static int add_generic_reference(ccst_ctx* c, const float* ref, int N, int* ref_id) {
-    int gcls = 0, rc;
-    if ((rc = gen_plan(c, N, &gcls))) return rc;
-    const size_t NN = (size_t)N * N;
-    ccst_ctx::RefEntry re;
-    re.gcls = gcls;
-    dfc* Fb = nullptr;
-    cudaError_t e = cudaMalloc(&Fb, NN * sizeof(dfc));
-    if (e != cudaSuccess)
-        return fail(c, e == cudaErrorMemoryAllocation ? CCST_E_NOMEM : CCST_E_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-    re.mem.push_back(Fb);
-    const size_t ntmp = NN * sizeof(float) + NN * sizeof(double2);
+// The half spectrum F[b] of a reference into Fb (H x (W/2 + 1) double-floats), from an FP32
+// image (host or device, `frame_kind` 0) or from a frame on the device in the context's
+// input type with row pitch `pitch` (`frame_kind` 1). Synchronous on the context's stream.
+static int gen_ref_spectrum(ccst_ctx* c, int H, int W, const void* src, int frame_kind, long long pitch, dfc* Fb) {
+    const size_t HW = (size_t)H * W, HWh = (size_t)H * (W / 2 + 1);
+    const size_t ntmp = HWh * sizeof(double2) + HW * sizeof(float);
     if (c->addref_tmp_bytes < ntmp) {
         if (c->d_addref_tmp) cudaFree(c->d_addref_tmp);
         c->d_addref_tmp = nullptr;
         c->addref_tmp_bytes = 0;
-        e = cudaMalloc(&c->d_addref_tmp, ntmp);
-        if (e != cudaSuccess) {
-            cudaFree(Fb);
-            return fail(c, e == cudaErrorMemoryAllocation ? CCST_E_NOMEM : CCST_E_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-        }
+        CK(c, cudaMalloc(&c->d_addref_tmp, ntmp));
         c->addref_tmp_bytes = ntmp;
     }
     double2* R = (double2*)c->d_addref_tmp;
-    float* ref32 = (float*)((char*)c->d_addref_tmp + NN * sizeof(double2));
-    int method = c->p.method;
+    float* ref32 = (float*)((char*)c->d_addref_tmp + HWh * sizeof(double2));
+    int method = c->p.method, in_dtype = c->p.in_dtype;
     float eps = c->p.eps;
-    e = cudaMemcpyAsync(ref32, ref, NN * sizeof(float), cudaMemcpyDefault, c->stream);
+    cudaError_t e;
+    if (frame_kind == 0) {
+        e = cudaMemcpyAsync(ref32, src, HW * sizeof(float), cudaMemcpyDefault, c->stream);
+    } else {
+        void* af[] = {&H, &W, &in_dtype, (void*)&src, &pitch, &ref32};
+        e = cudaLaunchKernel(gen_frame_to_f32_ptr(), dim3(64), dim3(256), af, 0, c->stream);
+    }
     if (e == cudaSuccess) {
-        void* ar[] = {&N, &method, &eps, &ref32, &R};
+        void* ar[] = {&H, &W, &method, &eps, &ref32, &R};
         e = cudaLaunchKernel(gen_ref_rows_ptr(), dim3(64), dim3(256), ar, 0, c->stream);
     }
     if (e == cudaSuccess) {
-        void* ac[] = {&N, &R, &Fb};
+        void* ac[] = {&H, &W, &R, &Fb};
         e = cudaLaunchKernel(gen_ref_cols_ptr(), dim3(64), dim3(256), ac, 0, c->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) {
+    if (e != cudaSuccess) return fail(c, CCST_E_CUDA, std::string("general-size reference: ") + cudaGetErrorString(e));
+    return CCST_OK;
+}
+
+static int add_generic_reference(ccst_ctx* c, const float* ref, int H, int W, int* ref_id) {
+    int gcls = 0, rc;
+    if ((rc = gen_plan(c, H, W, &gcls))) return rc;
+    ccst_ctx::RefEntry re;
+    re.gcls = gcls;
+    dfc* Fb = nullptr;
+    CK(c, cudaMalloc(&Fb, (size_t)H * (W / 2 + 1) * sizeof(dfc)));
+    if ((rc = gen_ref_spectrum(c, H, W, ref, 0, W, Fb))) {
         cudaFree(Fb);
-        return fail(c, CCST_E_CUDA, std::string("ccst_add_reference: ") + cudaGetErrorString(e));
+        return rc;
     }
+    re.mem.push_back(Fb);
     re.gFb = Fb;
     c->refs.push_back(re);
     c->rois_dirty = true;
@@ -1776,18 +1883,16 @@ static int add_generic_reference(ccst_ctx* c, const float* ref, int N, int* ref_
     return CCST_OK;
 }
 
-// Launch the general-size items on the context's second stream, forked from the context's
-// stream; the caller joins it back (gjoin) after issuing the power-of-two batch.
-static int gen_launch(ccst_ctx* c, int64_t n, Result* out) {
-    if (n == 0) return CCST_OK;
-    if (!c->gstream) {
-        CK(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
-        CK(c, cudaEventCreateWithFlags(&c->gfork, cudaEventDisableTiming));
-        CK(c, cudaEventCreateWithFlags(&c->gjoin, cudaEventDisableTiming));
-        int sms = 0;
+// The kernel's grid (CTAs per SM x SMs) and the device copies of the plans and references.
+static int gen_prepare(ccst_ctx* c) {
+    if (!c->gen_grid) {
+        int sms = 0, occ = 0;
         CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-        c->gen_grid = sms;
+        CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, track_generic_kernel_ptr(), 512, 0));
+        if (occ < 1) return fail(c, CCST_E_SHAPE, "the general-size kernel does not fit on an SM");
+        c->gen_grid = sms * occ;
     }
+    if (!c->gen_dirty) return CCST_OK;
     if (c->gplans_cap < c->gplans.size()) {
         if (c->d_gplans) cudaFree(c->d_gplans);
         c->d_gplans = nullptr;
@@ -1802,54 +1907,82 @@ static int gen_launch(ccst_ctx* c, int64_t n, Result* out) {
         CK(c, cudaMalloc(&c->d_grefs, 2 * c->refs.size() * sizeof(dfc*)));
         c->grefs_cap = 2 * c->refs.size();
     }
-    size_t stride = 0;
-    for (auto& g : c->gplans) stride = std::max(stride, 2 * (size_t)g.p.N * g.p.N + (size_t)g.p.N * g.p.M);
-    if (c->gen_dirty) {
-        std::vector<GenPlan> gp;
-        for (auto& g : c->gplans) gp.push_back(g.p);
-        std::vector<const dfc*> gr;
-        for (auto& re : c->refs) gr.push_back(re.gFb);
-        CK(c, cudaMemcpy(c->d_gplans, gp.data(), gp.size() * sizeof(GenPlan), cudaMemcpyHostToDevice));
-        CK(c, cudaMemcpy(c->d_grefs, gr.data(), gr.size() * sizeof(dfc*), cudaMemcpyHostToDevice));
-        c->gen_dirty = false;
+    std::vector<GenPlan> gp;
+    for (auto& g : c->gplans) gp.push_back(g.p);
+    std::vector<const dfc*> gr;
+    for (auto& re : c->refs) gr.push_back(re.gFb);
+    CK(c, cudaMemcpy(c->d_gplans, gp.data(), gp.size() * sizeof(GenPlan), cudaMemcpyHostToDevice));
+    CK(c, cudaMemcpy(c->d_grefs, gr.data(), gr.size() * sizeof(dfc*), cudaMemcpyHostToDevice));
+    c->gen_dirty = false;
+    return CCST_OK;
+}
+
+// Launch the general-size kernel on `stream` over gb.n frames: the work list `items_host`
+// (copied to the lane at once; the caller orders it) or, if null, the uniform batch that
+// gb describes. gb.out is set by the caller; the rest is filled in here.
+static int gen_launch(ccst_ctx* c, GenLane& lane, GenBatch gb, const GenItem* items_host, cudaStream_t stream,
+                      unsigned* counter) {
+    if (gb.n == 0) return CCST_OK;
+    int rc = gen_prepare(c);
+    if (rc) return rc;
+    long long stride = 0;
+    for (auto& g : c->gplans) stride = std::max(stride, gen_scratch_stride(g.p.H, g.p.W, g.p.M));
+    const int grid = (int)(gb.n < c->gen_grid ? gb.n : c->gen_grid);
+    if (lane.scratch_elems < (size_t)grid * stride) {
+        if (lane.scratch) cudaFree(lane.scratch);
+        lane.scratch = nullptr;
+        lane.scratch_elems = 0;
+        CK(c, cudaMalloc(&lane.scratch, (size_t)grid * stride * sizeof(dfc)));
+        lane.scratch_elems = (size_t)grid * stride;
     }
-    const int grid = (int)(n < c->gen_grid ? n : c->gen_grid);
-    if (c->gscratch_elems < (size_t)grid * stride) {
-        if (c->d_gscratch) cudaFree(c->d_gscratch);
-        c->d_gscratch = nullptr;
-        c->gscratch_elems = 0;
-        CK(c, cudaMalloc(&c->d_gscratch, (size_t)grid * stride * sizeof(dfc)));
-        c->gscratch_elems = (size_t)grid * stride;
+    gb.items = nullptr;
+    if (items_host) {
+        if (lane.items_cap < (size_t)gb.n) {
+            if (lane.d_items) cudaFree(lane.d_items);
+            lane.d_items = nullptr;
+            lane.items_cap = 0;
+            CK(c, cudaMalloc(&lane.d_items, (size_t)gb.n * sizeof(GenItem)));
+            lane.items_cap = (size_t)gb.n;
+        }
+        CK(c, cudaMemcpyAsync(lane.d_items, items_host, (size_t)gb.n * sizeof(GenItem), cudaMemcpyHostToDevice, stream));
+        gb.items = lane.d_items;
     }
-    if (c->gitems_cap < (size_t)n) {
-        if (c->d_gitems) cudaFree(c->d_gitems);
-        c->d_gitems = nullptr;
-        c->gitems_cap = 0;
-        CK(c, cudaMalloc(&c->d_gitems, (size_t)n * sizeof(GenItem)));
-        c->gitems_cap = (size_t)n;
-    }
-    CK(c, cudaEventRecord(c->gfork, c->stream));
-    CK(c, cudaStreamWaitEvent(c->gstream, c->gfork, 0));
-    // largest sides first
-    std::stable_sort(c->h_gitems.begin(), c->h_gitems.begin() + n, [&](const GenItem& a, const GenItem& b) {
-        return c->gplans[a.plan].p.N > c->gplans[b.plan].p.N;
-    });
-    CK(c, cudaMemcpyAsync(c->d_gitems, c->h_gitems.data(), (size_t)n * sizeof(GenItem), cudaMemcpyHostToDevice,
-                          c->gstream));
-    unsigned* counter = c->d_next + 24;
-    CK(c, cudaMemsetAsync(counter, 0, sizeof(unsigned), c->gstream));
-    GenBatch gb;
-    gb.items = c->d_gitems;
-    gb.n = n;
+    CK(c, cudaMemsetAsync(counter, 0, sizeof(unsigned), stream));
     gb.plans = c->d_gplans;
     gb.refs = c->d_grefs;
-    gb.out = out;
     gb.next = counter;
-    gb.scratch = c->d_gscratch;
-    gb.scratch_stride = (long long)stride;
+    gb.scratch = lane.scratch;
+    gb.scratch_stride = stride;
     void* args[] = {&gb};
-    CK(c, cudaLaunchKernel(track_generic_kernel_ptr(), dim3(grid), dim3(512), args, 0, c->gstream));
-    CK(c, cudaEventRecord(c->gjoin, c->gstream));
+    CK(c, cudaLaunchKernel(track_generic_kernel_ptr(), dim3(grid), dim3(512), args, 0, stream));
+    return CCST_OK;
+}
+
+// Largest frames first (the longest work starts first; equal shapes stay together).
+static void gen_sort(ccst_ctx* c, GenItem* items, int64_t n) {
+    std::stable_sort(items, items + n, [&](const GenItem& a, const GenItem& b) {
+        const GenPlan &pa = c->gplans[a.plan].p, &pb = c->gplans[b.plan].p;
+        return pa.H * pa.W > pb.H * pb.W;
+    });
+}
+
+// A batch of a general-shape context: frame i at frames + i * H * pitch elements.
+static int gen_track(ccst_ctx* c, const Batch& b, cudaStream_t stream, GenLane& lane, unsigned* counter) {
+    const size_t elem = c->p.in_dtype == CCST_U16 ? 2 : 4;
+    GenBatch gb{};
+    gb.n = b.n;
+    gb.out = b.out;
+    gb.frames = b.frames;
+    gb.frame_bytes = (long long)c->g.H * b.pitch * (long long)elem;
+    gb.pitch = b.pitch;
+    gb.plan = c->refs[0].gcls;
+    gb.ref = 0;
+    return gen_launch(c, lane, gb, nullptr, stream, counter);
+}
+
+static int not_general(ccst_ctx* c, const char* who) {
+    if (c && c->general)
+        return fail(c, CCST_E_UNSUPPORTED, std::string(who) + ": not available on a general-shape context");
     return CCST_OK;
 }
 
@@ -1894,8 +2027,9 @@ extern "C" int ccst_track_rois(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccs
         if (q.ref_id < 0 || q.ref_id >= (int)c->refs.size() || (c->refs[q.ref_id].cls < 0 && c->refs[q.ref_id].gcls < 0))
             return fail(c, CCST_E_INVALID, "ccst_track_rois: unknown or unusable ref_id");
         const auto& re = c->refs[q.ref_id];
-        const int side = re.cls >= 0 ? c->plans[re.cls].g.H : c->gplans[re.gcls].p.N;
-        if (q.H != side || q.W != side) return fail(c, CCST_E_SHAPE, "ccst_track_rois: ROI size differs from its reference");
+        const int rh = re.cls >= 0 ? c->plans[re.cls].g.H : c->gplans[re.gcls].p.H;
+        const int rw = re.cls >= 0 ? c->plans[re.cls].g.W : c->gplans[re.gcls].p.W;
+        if (q.H != rh || q.W != rw) return fail(c, CCST_E_SHAPE, "ccst_track_rois: ROI size differs from its reference");
         const int64_t pitch = q.pitch_elems == 0 ? q.W : q.pitch_elems;
         if (!q.frame || pitch < q.W) return fail(c, CCST_E_INVALID, "ccst_track_rois: null frame or pitch < W");
         if (re.gcls >= 0) {
@@ -1911,7 +2045,22 @@ extern "C" int ccst_track_rois(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccs
         it.vec_ok = ((uintptr_t)q.frame % 16 == 0) && ((size_t)pitch * elem % 16 == 0) ? 1 : 0;
         it.pad = 0;
     }
-    if ((rc = gen_launch(c, ng, (Result*)out_dev))) return rc;
+    if (ng > 0) {
+        // the general sizes run on their own stream, forked here and joined below
+        if (!c->gstream) {
+            CK(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+            CK(c, cudaEventCreateWithFlags(&c->gfork, cudaEventDisableTiming));
+            CK(c, cudaEventCreateWithFlags(&c->gjoin, cudaEventDisableTiming));
+        }
+        gen_sort(c, c->h_gitems.data(), ng);
+        CK(c, cudaEventRecord(c->gfork, c->stream));
+        CK(c, cudaStreamWaitEvent(c->gstream, c->gfork, 0));
+        GenBatch gb{};
+        gb.n = ng;
+        gb.out = (Result*)out_dev;
+        if ((rc = gen_launch(c, c->glane[0], gb, c->h_gitems.data(), c->gstream, c->d_next + 24))) return rc;
+        CK(c, cudaEventRecord(c->gjoin, c->gstream));
+    }
     if (np > 0) {
         n = np;
         if (c->items_cap < (size_t)n) {
@@ -1951,6 +2100,8 @@ struct ccst_server {
         Result* h_out = nullptr;
         RoiItem* d_items = nullptr;
         RoiItem* h_items = nullptr;    // pinned, so the item upload is asynchronous
+        GenItem* h_gitems = nullptr;   // pinned: the batch's general-size frames
+        GenLane lane;                  // the general-size kernel's scratch for this entry
         std::vector<Req> reqs;
         bool busy = false;
     };
@@ -1959,7 +2110,7 @@ struct ccst_server {
     size_t slot_bytes = 0, elem = 0;
     char* h_frames = nullptr;          // pinned, mapped: slot i at h_frames + i * slot_bytes
     char* d_frames = nullptr;          // the same memory as the device addresses it
-    unsigned* d_counters = nullptr;    // one item counter per ring entry
+    unsigned* d_counters = nullptr;    // two item counters per ring entry (power-of-two, general)
     InFlight ring[kRing];
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -1972,6 +2123,22 @@ struct ccst_server {
     bool stop = false;
     std::thread worker;
 };
+
+// The frame shape of reference `ref`, for either kernel.
+static void ref_shape(const ccst_ctx* c, int ref, int* H, int* W) {
+    const auto& re = c->refs[ref];
+    if (re.cls >= 0) {
+        *H = c->plans[re.cls].g.H;
+        *W = c->plans[re.cls].g.W;
+    } else {
+        *H = c->gplans[re.gcls].p.H;
+        *W = c->gplans[re.gcls].p.W;
+    }
+}
+
+static bool ref_usable(const ccst_ctx* c, int ref) {
+    return ref >= 0 && ref < (int)c->refs.size() && (c->refs[ref].cls >= 0 || c->refs[ref].gcls >= 0);
+}
 
 static void server_fail(ccst_server* s, int code) {
     std::lock_guard<std::mutex> lk(s->mu);
@@ -2039,15 +2206,26 @@ static void server_loop(ccst_server* s) {
             continue;
         }
         const int m = (int)take.size();
-        bool ok = true;
+        int np = 0, ng = 0;
         for (int i = 0; i < m; ++i) {
             const auto& r = take[i];
-            const Geom& pg = c->plans[c->refs[r.ref].cls].g;
-            b.h_items[i] = RoiItem{s->d_frames + (size_t)r.slot * s->slot_bytes, (long long)pg.W, i, c->refs[r.ref].cls,
-                                   r.ref, 1, 0};
+            const auto& re = c->refs[r.ref];
+            int H = 0, W = 0;
+            ref_shape(c, r.ref, &H, &W);
+            const char* frame = s->d_frames + (size_t)r.slot * s->slot_bytes;
+            if (re.cls >= 0) b.h_items[np++] = RoiItem{frame, (long long)W, i, re.cls, r.ref, 1, 0};
+            else b.h_gitems[ng++] = GenItem{frame, (long long)W, i, re.gcls, r.ref};
         }
-        // the kernel writes record i of the batch to d_out[i]; out_index survives the sort
-        ok = rois_launch(c, b.h_items, m, b.d_out, b.st, b.d_items, s->d_counters + next) == CCST_OK;
+        // each kernel writes record i of the batch to d_out[i]; out_index survives the sorts
+        bool ok = true;
+        if (np > 0) ok = rois_launch(c, b.h_items, np, b.d_out, b.st, b.d_items, s->d_counters + 2 * next) == CCST_OK;
+        if (ok && ng > 0) {
+            gen_sort(c, b.h_gitems, ng);
+            GenBatch gb{};
+            gb.n = ng;
+            gb.out = b.d_out;
+            ok = gen_launch(c, b.lane, gb, b.h_gitems, b.st, s->d_counters + 2 * next + 1) == CCST_OK;
+        }
         ok = ok && cudaMemcpyAsync(b.h_out, b.d_out, (size_t)m * sizeof(Result), cudaMemcpyDeviceToHost, b.st) ==
                        cudaSuccess;
         ok = ok && cudaEventRecord(b.ev, b.st) == cudaSuccess;
@@ -2075,6 +2253,8 @@ static void server_free(ccst_server* s) {
         if (b.h_out) cudaFreeHost(b.h_out);
         if (b.d_items) cudaFree(b.d_items);
         if (b.h_items) cudaFreeHost(b.h_items);
+        if (b.h_gitems) cudaFreeHost(b.h_gitems);
+        lane_free(b.lane);
     }
     if (s->h_frames) cudaFreeHost(s->h_frames);
     if (s->d_counters) cudaFree(s->d_counters);
@@ -2087,16 +2267,18 @@ extern "C" int ccst_server_create(ccst_ctx* c, int slots, int max_batch, ccst_se
     *out = nullptr;
     rois_init(c);
     if ((rc = rois_upload(c))) return rc;
+    if (!c->gplans.empty() && (rc = gen_prepare(c))) return rc;
     ccst_server* s = new (std::nothrow) ccst_server();
     if (!s) return fail(c, CCST_E_NOMEM, "ccst_server_create: host allocation failed");
     s->c = c;
     s->slots = slots;
     s->max_batch = std::min(max_batch, slots);
     s->elem = c->p.in_dtype == CCST_U16 ? 2 : 4;
-    for (auto& re : c->refs)
-        if (re.cls >= 0) {
-            const Geom& pg = c->plans[re.cls].g;
-            s->slot_bytes = std::max(s->slot_bytes, ((size_t)pg.H * pg.W * s->elem + 255) & ~(size_t)255);
+    for (int i = 0; i < (int)c->refs.size(); ++i)
+        if (ref_usable(c, i)) {
+            int H = 0, W = 0;
+            ref_shape(c, i, &H, &W);
+            s->slot_bytes = std::max(s->slot_bytes, ((size_t)H * W * s->elem + 255) & ~(size_t)255);
         }
     if (s->slot_bytes == 0) {
         delete s;
@@ -2112,7 +2294,7 @@ extern "C" int ccst_server_create(ccst_ctx* c, int slots, int max_batch, ccst_se
     if ((e = cudaHostAlloc(&s->h_frames, (size_t)slots * s->slot_bytes, cudaHostAllocMapped)) != cudaSuccess)
         return bad(e);
     if ((e = cudaHostGetDevicePointer((void**)&s->d_frames, s->h_frames, 0)) != cudaSuccess) return bad(e);
-    if ((e = cudaMalloc(&s->d_counters, ccst_server::kRing * sizeof(unsigned))) != cudaSuccess) return bad(e);
+    if ((e = cudaMalloc(&s->d_counters, 2 * ccst_server::kRing * sizeof(unsigned))) != cudaSuccess) return bad(e);
     for (auto& b : s->ring) {
         if ((e = cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking)) != cudaSuccess) return bad(e);
         if ((e = cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming)) != cudaSuccess) return bad(e);
@@ -2121,6 +2303,8 @@ extern "C" int ccst_server_create(ccst_ctx* c, int slots, int max_batch, ccst_se
             return bad(e);
         if ((e = cudaMalloc(&b.d_items, (size_t)s->max_batch * sizeof(RoiItem))) != cudaSuccess) return bad(e);
         if ((e = cudaHostAlloc(&b.h_items, (size_t)s->max_batch * sizeof(RoiItem), cudaHostAllocDefault)) != cudaSuccess)
+            return bad(e);
+        if ((e = cudaHostAlloc(&b.h_gitems, (size_t)s->max_batch * sizeof(GenItem), cudaHostAllocDefault)) != cudaSuccess)
             return bad(e);
     }
     for (int i = slots - 1; i >= 0; --i) s->free_slots.push_back(i);
@@ -2133,10 +2317,12 @@ extern "C" int ccst_server_submit(ccst_server* s, int ref_id, const void* frame_
                                   uint64_t* ticket) {
     if (!s || !frame_host) return CCST_E_INVALID;
     ccst_ctx* c = s->c;
-    if (ref_id < 0 || ref_id >= (int)c->refs.size() || c->refs[ref_id].cls < 0) return CCST_E_INVALID;
-    const Geom& pg = c->plans[c->refs[ref_id].cls].g;
-    if (pitch_elems == 0) pitch_elems = pg.W;
-    if (pitch_elems < pg.W) return CCST_E_INVALID;
+    if (!ref_usable(c, ref_id)) return CCST_E_INVALID;
+    int H = 0, W = 0;
+    ref_shape(c, ref_id, &H, &W);
+    if ((size_t)H * W * s->elem > s->slot_bytes) return CCST_E_INVALID;    // added after the server
+    if (pitch_elems == 0) pitch_elems = W;
+    if (pitch_elems < W) return CCST_E_INVALID;
     ccst_server::Req r;
     {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -2149,8 +2335,8 @@ extern "C" int ccst_server_submit(ccst_server* s, int ref_id, const void* frame_
         s->free_slots.pop_back();
     }
     char* dst = s->h_frames + (size_t)r.slot * s->slot_bytes;
-    const size_t row = (size_t)pg.W * s->elem;
-    for (int y = 0; y < pg.H; ++y) std::memcpy(dst + y * row, (const char*)frame_host + (size_t)y * pitch_elems * s->elem, row);
+    const size_t row = (size_t)W * s->elem;
+    for (int y = 0; y < H; ++y) std::memcpy(dst + y * row, (const char*)frame_host + (size_t)y * pitch_elems * s->elem, row);
     r.ref = ref_id;
     r.keep = ticket != nullptr;
     r.t0 = std::chrono::steady_clock::now();
@@ -2229,6 +2415,8 @@ extern "C" int ccst_server_loadgen(ccst_server* s, int ncams, const int* ref_ids
                                    ccst_server_stats* out) {
     if (!s || ncams < 1 || !ref_ids || !rates_hz || !pools || !pool_len || !(seconds > 0) || !out)
         return CCST_E_INVALID;
+    for (int k = 0; k < ncams; ++k)
+        if (!ref_usable(s->c, ref_ids[k]) || !(rates_hz[k] > 0) || !pools[k] || pool_len[k] < 1) return CCST_E_INVALID;
     ccst_server_stats dummy;
     ccst_server_read_stats(s, 1, &dummy);
     std::atomic<int> err{0};
@@ -2238,8 +2426,9 @@ extern "C" int ccst_server_loadgen(ccst_server* s, int ncams, const int* ref_ids
         th.emplace_back([&, k]() {
             std::mt19937_64 rng(seed + 7919u * (uint64_t)k);
             std::exponential_distribution<double> gap(rates_hz[k]);
-            const Geom& pg = s->c->plans[s->c->refs[ref_ids[k]].cls].g;
-            const size_t fb = (size_t)pg.H * pg.W * s->elem;
+            int H = 0, W = 0;
+            ref_shape(s->c, ref_ids[k], &H, &W);
+            const size_t fb = (size_t)H * W * s->elem;
             double t = 0.0;
             for (int64_t i = 0;; ++i) {
                 t += gap(rng);

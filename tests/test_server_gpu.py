@@ -151,3 +151,32 @@ def test_server_errors(torch):
     finally:
         C.ccst_server_destroy(srv)
         t.close()
+
+
+def test_general_size_cameras_equal_the_roi_path(torch):
+    # the first camera (96 px) makes a general-shape context; 48 and 192 px cameras take the
+    # general-size kernel too, 64 px the power-of-two kernel, all in the same batches
+    cams = cameras(seed=9, sides=(96, 64, 48, 192), n=8)
+    t, ids, srv = make_server(cams)
+    try:
+        want = {}
+        for k, (_, frames) in enumerate(cams):
+            d = torch.from_numpy(frames.view(np.int16)).cuda().view(torch.uint16)
+            out = t.empty_results(len(frames))
+            C.ccst_track_rois(t.ctx, C.make_rois([d[i] for i in range(len(frames))], [ids[k]] * len(frames)),
+                              len(frames), out)
+            C.ccst_sync(t.ctx)
+            for i, r in enumerate(C.decode(out)):
+                assert bool(r["flags"] & C.R_GENERIC) == (frames.shape[-1] != 64)
+                want[(k, i)] = r.tobytes()
+        tickets = [((k, i), submit_wait(srv, ids[k], cams[k][1][i])) for i in range(8) for k in range(len(cams))]
+        for key, tk in tickets:
+            assert C.ccst_server_poll(srv, tk, 20_000_000).tobytes() == want[key], key
+        st = C.ccst_server_read_stats(srv)
+        assert st["completed"] == st["submitted"] and st["in_flight"] == 0
+        # the load generator over the same cameras accounts for every frame
+        st = C.ccst_server_loadgen(srv, ids, [500.0, 2000.0, 1000.0, 200.0], [f for _, f in cams], 0.2, seed=3)
+        assert st["in_flight"] == 0 and st["completed"] == st["submitted"] > 0
+    finally:
+        C.ccst_server_destroy(srv)
+        t.close()
