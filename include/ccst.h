@@ -127,13 +127,26 @@ int ccst_default_params(ccst_params* p);
  * Arguments:
  *   ref   H*W float32, row-major, host or device memory (detected). It is copied;
  *         the caller keeps ownership.
- *   H, W  powers of two, 8 <= H, W <= 128 in this build. Other sizes return
+ *   H, W  8 <= H, W <= 256, any factors (H != W allowed). Other sizes return
  *         CCST_E_SHAPE.
+ *         - Powers of two up to 128 (8, 16, 32, 64, 128 per axis) make a power-of-two
+ *           context: FP32 FFTs, the upsampled contraction on tensor cores, the near-tie
+ *           levels, and every entry point below.
+ *         - Every other shape (48 x 48, 96 x 96, 256 x 128, 256 x 256, 100 x 60, ...)
+ *           makes a general-shape context. Its batches run on the general-size kernel:
+ *           direct DFTs over the Hermitian half and the full-grid upsampled sum, in
+ *           double-float (about 2^-46 per term, so no near-tie levels are needed).
+ *           Records carry CCST_R_GENERIC. ccst_track, ccst_track_host, ccst_submit,
+ *           ccst_submit_host, ccst_poll, ccst_set_reference_frame, ccst_add_reference,
+ *           ccst_track_rois and the server work on it. The real-time and offline
+ *           reference, the continuous peak, the adjoint, profiling and the debug entry
+ *           points return CCST_E_UNSUPPORTED.
  *   p     parameters; NULL means the defaults.
  *   out   receives the context.
  *
- * The context owns the reference spectrum (FP32 and FP64, Eq. (4)/(7) right-hand
- * side), the upsampling tables and all device workspace. Synchronous.
+ * The context owns the reference spectrum (power-of-two: FP32 and FP64; general: double-
+ * float; Eq. (4)/(7) right-hand side), the upsampling tables and all device workspace.
+ * Synchronous.
  * Errors: CCST_E_INVALID, CCST_E_SHAPE, CCST_E_NOMEM, CCST_E_CUDA. */
 int ccst_create(const float* ref, int H, int W, const ccst_params* p, ccst_ctx** out);
 
@@ -199,16 +212,16 @@ int ccst_poll(ccst_ctx* ctx, uint64_t ticket, int timeout_us, int* done);
  *   H, W     square, 8 to 256 pixels a side; others return CCST_E_SHAPE.
  *            16, 32, 64 and 128 run on the power-of-two ROI kernel (FP32 surfaces with the
  *            near-tie levels, as ccst_track). Every other side (8, 48, 96, 192, 256, odd
- *            sides, ...) runs on the general-size path: direct DFTs and the full-grid
- *            upsampled sum in double-float (about 2^-46 per term), slower (O(N^3) per ROI)
- *            but needing no near-tie levels; its records carry CCST_R_GENERIC.
+ *            sides, ...) runs on the general-size kernel of general-shape contexts (see
+ *            ccst_create): slower (O(N^3) per ROI) but needing no near-tie levels; its
+ *            records carry CCST_R_GENERIC.
  * The first reference of a new size also creates that size's plan (geometry, FFT
  * twiddles, upsampling tables) with the context's parameters (u, method, eps); for the
  * general path u * N must not exceed 2^22. Each power-of-two reference keeps its spectra
  * resident (FP32, FP64 and double-float) and its FP64 operand, about 26 H*W bytes; a
- * general-size reference keeps its full N x N double-float spectrum, 16 N^2 bytes. All of
- * it is owned by the context. The context's own reference is id 0, usable when its frames
- * are one of the power-of-two sizes above. Synchronous.
+ * general-size reference keeps its half spectrum in double-float, 16 N (N/2 + 1) bytes.
+ * All of it is owned by the context. The context's own reference is id 0, usable unless
+ * it is a power-of-two context of a non-square or 8 x 8 shape. Synchronous.
  * Errors: CCST_E_INVALID (null pointers), CCST_E_SHAPE, CCST_E_NOMEM, CCST_E_CUDA. */
 int ccst_add_reference(ccst_ctx* ctx, const float* ref, int H, int W, int* ref_id);
 
@@ -235,7 +248,9 @@ int ccst_track_rois(ccst_ctx* ctx, const ccst_roi* rois, int64_t n, ccst_result*
  * place, with no per-frame copy); a submit without a free slot is refused with
  * CCST_E_BUSY (admission by reserved memory).
  * The worker takes everything pending (up to max_batch frames, any cameras and sizes) as
- * one ccst_track_rois batch on its own stream, with up to 4 batches in flight, so frames
+ * one batch on its own stream: the power-of-two ROI kernel for cameras of 16, 32, 64 or
+ * 128 px, then the general-size kernel for the others (each ring entry has its own
+ * scratch for it). Up to 4 batches are in flight, so frames
  * that arrive while others run are admitted as slots free up and their work overlaps on
  * the device. Each result equals that of the frame tracked alone (the batch changes only
  * which CTA runs it). While a server exists its context must not be used by other calls
@@ -251,6 +266,8 @@ typedef struct ccst_server_stats {
 } ccst_server_stats;
 
 /* Start a server over ctx (ctx keeps ownership of its references and must outlive it).
+ * The frame slots are sized for the largest reference present at creation; a camera
+ * added later must not be larger (its submits return CCST_E_INVALID).
  * Errors: CCST_E_INVALID (slots or max_batch < 1, no reference usable by ROI batches),
  * CCST_E_NOMEM, CCST_E_CUDA. */
 int ccst_server_create(ccst_ctx* ctx, int slots, int max_batch, ccst_server** out);
