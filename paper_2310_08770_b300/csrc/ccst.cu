@@ -24,6 +24,7 @@
 #include "ccst.h"
 #include "ccst_kernels.cuh"
 #include "ccst_adjoint.cuh"
+#include "ccst_generic.cuh"
 
 using namespace ccst;
 

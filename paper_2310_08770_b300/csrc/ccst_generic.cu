@@ -24,7 +24,7 @@
 // signed-frequency sum), with one rule: in the columns 0 < kx < W/2 the y-Nyquist row
 // (ky = H/2, H even) pairs with itself at -kx, so its y-phase enters only through its
 // real part cos(pi sy).
-#include "ccst_kernels.cuh"
+#include "ccst_generic.cuh"
 
 namespace ccst {
 
