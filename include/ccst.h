@@ -69,6 +69,10 @@ extern "C" {
                                       each graph has its own frame counter, so graphs of different
                                       batches may run at once on different streams (ccst_set_stream) */
 #define CCST_FLAG_PROFILE   0x4u  /* record CUDA events around each launch of the tracking kernel */
+#define CCST_FLAG_EXHAUSTIVE 0x8u /* general-size kernel (ccst_create): evaluate the whole upsampled
+                                     grid in double-float, instead of FP32 with a rounding bound and
+                                     double-float re-evaluation of the points the bound cannot rule
+                                     out. The records are the same; this is for verification. */
 
 /* ccst_result.flags (per frame) */
 #define CCST_R_INT_GUARD   0x01u /* integer peak re-decided by FP64 direct sums */

@@ -18,6 +18,7 @@ F32 = 1
 FLAG_TIE_GUARD = 0x1
 FLAG_GRAPHS = 0x2
 FLAG_PROFILE = 0x4
+FLAG_EXHAUSTIVE = 0x8
 
 R_INT_GUARD = 0x01
 R_SUB_GUARD = 0x02
@@ -423,7 +424,7 @@ class Tracker:
 
     def __init__(self, ref, upsample: int = 100, method: str | int = "ccu", eps: float = 200.0,
                  in_dtype: str | int = "u16", max_batch: int = 256, stream=None, graphs: bool = False,
-                 tie_guard: bool = True, profile: bool = False):
+                 tie_guard: bool = True, profile: bool = False, exhaustive: bool = False):
         import torch
         ref_np = ref.detach().cpu().numpy() if hasattr(ref, "detach") else np.asarray(ref)
         ref_np = np.ascontiguousarray(ref_np, dtype=np.float32)
@@ -438,7 +439,7 @@ class Tracker:
             stream = torch.cuda.current_stream()
         p.stream = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
         p.flags = (FLAG_TIE_GUARD if tie_guard else 0) | (FLAG_GRAPHS if graphs else 0) | \
-            (FLAG_PROFILE if profile else 0)
+            (FLAG_PROFILE if profile else 0) | (FLAG_EXHAUSTIVE if exhaustive else 0)
         self.params = p
         self.max_batch = int(max_batch)
         self.ctx = ccst_create(ref_np, self.H, self.W, p)

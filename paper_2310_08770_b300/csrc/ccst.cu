@@ -1807,14 +1807,23 @@ static int gen_plan(ccst_ctx* c, int H, int W, int* gcls) {
     pl.in_dtype = c->p.in_dtype;
     pl.eps = c->p.eps;
     pl.sense = c->p.method == CCST_CC_SN ? -1.f : 1.f;
+    pl.exhaustive = (c->p.flags & CCST_FLAG_EXHAUSTIVE) ? 1 : 0;
+    pl.H1 = gen_split(H);
+    pl.H2 = H / pl.H1;
+    pl.W1 = gen_split(W);
+    pl.W2 = W / pl.W1;
     dfc* tab = nullptr;
-    CK(c, cudaMalloc(&tab, (size_t)(H + W + DH + DW) * sizeof(dfc)));
+    const size_t ntab = (size_t)(H + W + DH + DW);
+    CK(c, cudaMalloc(&tab, ntab * sizeof(dfc) + (size_t)(DH + DW) * sizeof(float2)));
     gp.mem.push_back(tab);
     pl.wH = tab;
     pl.wW = tab + H;
     pl.uH = tab + H + W;
     pl.uW = tab + H + W + DH;
-    void* a2[] = {&H, &W, &u, &tab};
+    float2* tab32 = (float2*)(tab + ntab);
+    pl.uH32 = tab32;
+    pl.uW32 = tab32 + DH;
+    void* a2[] = {&H, &W, &u, &tab, &tab32};
     const cudaError_t e = cudaLaunchKernel(gen_init_tables_ptr(), dim3(64), dim3(256), a2, 0, c->stream);
     if (e != cudaSuccess) {
         cudaFree(tab);

@@ -29,6 +29,8 @@
 namespace ccst {
 
 constexpr unsigned kRGeneric = 0x80u;   // record flag: tracked by this path
+constexpr unsigned kRNonFinite = 0x10u; // record flag: the surface was not finite
+constexpr int kGenCand = 64;            // most upsampled-grid candidates re-evaluated in double-float
 
 // Block extremum of (value, index): the largest value, the lowest index on ties.
 __device__ void gen_block_best(double& v, long long& j, double* sv, long long* sj) {
@@ -62,11 +64,62 @@ __device__ __forceinline__ df gen_re_mul(dfc a, dfc b) {
     return df_add_abs(df_mul(a.re, b.re), df_neg(df_mul(a.im, b.im)));
 }
 
+// Block sum and maximum of one double per thread (sv: 32 doubles of shared memory).
+__device__ double gen_block_sum(double v, double* sv) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sv[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += sv[w];
+    __syncthreads();
+    return s;
+}
+__device__ double gen_block_max(double v, double* sv) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) sv[wid] = v;
+    __syncthreads();
+    double s = sv[0];
+    for (int w = 1; w < nw; ++w) s = fmax(s, sv[w]);
+    __syncthreads();
+    return s;
+}
+
+// One point of the upsampled grid in FP32: sum_kx g(kx) Re V32[kx] e^{2 pi i kx' q / (uW)},
+// q = px u + jx - h0, by a fixed chain of FMAs (the two passes over the grid get the same
+// value). Angle indices as in the double-float evaluation, in 32 bits (uW <= 2^22).
+__device__ __forceinline__ float gen_cu32(const float2* V, const float2* tab, int Wh, int W, int jx, int px, int u,
+                                          int h0, int DW) {
+    int q = (px * u + jx - h0) % DW;
+    if (q < 0) q += DW;
+    const int nq = (int)(((long long)W * q) % DW);
+    float acc = 0.f;
+    int m = 0;
+    for (int kx = 0; kx < Wh; ++kx) {
+        int ms = m;
+        if (2 * kx >= W) { ms -= nq; if (ms < 0) ms += DW; }
+        const float2 v = V[kx], e = tab[ms];
+        const float g = (kx != 0 && 2 * kx != W) ? 2.f : 1.f;
+        acc = __fmaf_rn(g * v.x, e.x, acc);
+        acc = __fmaf_rn(-g * v.y, e.y, acc);
+        m += q;
+        if (m >= DW) m -= DW;
+    }
+    return acc;
+}
+
 __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
     __shared__ double sv[32];
     __shared__ long long sj[32];
     __shared__ long long s_item;
     __shared__ dfc s_wH[256], s_wW[256];                       // e^{-2 pi i m / H}, e^{-2 pi i m / W}
+    __shared__ int s_nc, s_cand[kGenCand];                     // upsampled-grid candidates
+    __shared__ double s_cval[kGenCand];
     dfc* const X = gb.scratch + (size_t)blockIdx.x * gb.scratch_stride;
     for (;;) {
         __syncthreads();
@@ -89,8 +142,10 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
         const long long DH = (long long)u * H, DW = (long long)u * W;
         const int nyq_y = (H % 2 == 0) ? H / 2 : -1;              // the y-Nyquist row, if any
         const dfc* Fb = gb.refs[it.ref];                           // H x Wh
+        const int H1 = pl.H1, H2 = pl.H2, W1 = pl.W1, W2 = pl.W2;
         dfc* B = X + (size_t)H * Wh;                               // R, then Q, then V
         df* a = (df*)(B + (size_t)(H > M ? H : M) * Wh);           // operand plane, H x W
+        dfc* T = (dfc*)a + ((size_t)H * W + 1) / 2;                // inner DFT levels, H x W
         const dfc zero = dfc{df{0.f, 0.f}, df{0.f, 0.f}};
         const df epsd = df_from_double((double)pl.eps);
         for (int m = threadIdx.x; m < H; m += blockDim.x) s_wH[m] = pl.wH[m];
@@ -106,58 +161,116 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
             }
         }
         __syncthreads();
-        // R[y][kx] = sum_x a(y, x) wW^(x kx)
-        for (int o = threadIdx.x; o < H * Wh; o += blockDim.x) {
-            const int y = o / Wh, kx = o - y * Wh;
+        // The four DFTs, each in two levels N = N1 N2 (k = k1 + N1 k2, n = N2 n1 + n2):
+        // sum_n f(n) w^(n k) = sum_n2 w^(n2 k) [sum_n1 f(N2 n1 + n2) w^(N2 n1 k1)], the inner
+        // sums being N1-point DFTs and the outer twiddle w^(n2 k) the product of the
+        // classic twiddle and the N2-point kernel.
+        // R[y][kx] = sum_x a(y, x) wW^(x kx); first T[y][n2][k1], then kx < Wh
+        for (int o = threadIdx.x; o < H * W; o += blockDim.x) {
+            const int y = o / W, r = o - y * W, n2 = r / W1, k1 = r - n2 * W1;
+            const int step = (W2 * k1) % W;
             dfc acc = zero;
             int m = 0;
-            for (int x = 0; x < W; ++x) {
-                const df v = a[y * W + x];
+            for (int n1 = 0; n1 < W1; ++n1) {
+                const df v = a[y * W + W2 * n1 + n2];
                 const dfc t = s_wW[m];
                 acc = cadd(acc, dfc{df_mul(v, t.re), df_mul(v, t.im)});
+                m += step;
+                if (m >= W) m -= W;
+            }
+            T[o] = acc;
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < H * Wh; o += blockDim.x) {
+            const int y = o / Wh, kx = o - y * Wh, k1 = kx % W1;
+            dfc acc = zero;
+            int m = 0;
+            for (int n2 = 0; n2 < W2; ++n2) {
+                acc = cadd(acc, cmul(T[y * W + n2 * W1 + k1], s_wW[m]));
                 m += kx;
                 if (m >= W) m -= W;
             }
             B[o] = acc;
         }
         __syncthreads();
-        // X[ky][kx] = (sum_y R[y][kx] wH^(y ky)) conj F[b](ky, kx)
+        // X[ky][kx] = (sum_y R[y][kx] wH^(y ky)) conj F[b](ky, kx); T[n2][k1][kx] first
         for (int o = threadIdx.x; o < H * Wh; o += blockDim.x) {
-            const int ky = o / Wh, kx = o - ky * Wh;
+            const int r = o / Wh, kx = o - r * Wh, n2 = r / H1, k1 = r - n2 * H1;
+            const int step = (H2 * k1) % H;
             dfc acc = zero;
             int m = 0;
-            for (int y = 0; y < H; ++y) {
-                acc = cadd(acc, cmul(B[y * Wh + kx], s_wH[m]));
+            for (int n1 = 0; n1 < H1; ++n1) {
+                acc = cadd(acc, cmul(B[(H2 * n1 + n2) * Wh + kx], s_wH[m]));
+                m += step;
+                if (m >= H) m -= H;
+            }
+            T[o] = acc;
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < H * Wh; o += blockDim.x) {
+            const int ky = o / Wh, kx = o - ky * Wh, k1 = ky % H1;
+            dfc acc = zero;
+            int m = 0;
+            for (int n2 = 0; n2 < H2; ++n2) {
+                acc = cadd(acc, cmul(T[(n2 * H1 + k1) * Wh + kx], s_wH[m]));
                 m += ky;
                 if (m >= H) m -= H;
             }
             X[o] = cmul(acc, cconj(Fb[o]));
         }
         __syncthreads();
-        // Q[y][kx] = sum_ky X[ky][kx] wH^-(ky y)
+        // Q[y][kx] = sum_ky X[ky][kx] wH^-(ky y); T[n2][y1][kx] first
         for (int o = threadIdx.x; o < H * Wh; o += blockDim.x) {
-            const int y = o / Wh, kx = o - y * Wh;
+            const int r = o / Wh, kx = o - r * Wh, n2 = r / H1, y1 = r - n2 * H1;
+            const int step = (H2 * y1) % H;
             dfc acc = zero;
             int m = 0;
-            for (int ky = 0; ky < H; ++ky) {
-                acc = cadd(acc, cmul(X[ky * Wh + kx], cconj(s_wH[m])));
+            for (int n1 = 0; n1 < H1; ++n1) {
+                acc = cadd(acc, cmul(X[(H2 * n1 + n2) * Wh + kx], cconj(s_wH[m])));
+                m += step;
+                if (m >= H) m -= H;
+            }
+            T[o] = acc;
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < H * Wh; o += blockDim.x) {
+            const int y = o / Wh, kx = o - y * Wh, y1 = y % H1;
+            dfc acc = zero;
+            int m = 0;
+            for (int n2 = 0; n2 < H2; ++n2) {
+                acc = cadd(acc, cmul(T[(n2 * H1 + y1) * Wh + kx], cconj(s_wH[m])));
                 m += y;
                 if (m >= H) m -= H;
             }
             B[o] = acc;
         }
         __syncthreads();
-        // c(y, x) = sum_kx g(kx) Re Q[y][kx] wW^-(kx x); the extremum, lowest flat index on ties
+        // c(y, x) = Re sum_{k < W} Q[y][k] wW^-(k x), the row completed by Q[y][W - k] =
+        // conj Q[y][k] (X is the spectrum of a real surface); T[y][n2][x1] first. The
+        // extremum, lowest flat index on ties
+        for (int o = threadIdx.x; o < H * W; o += blockDim.x) {
+            const int y = o / W, r = o - y * W, n2 = r / W1, x1 = r - n2 * W1;
+            const int step = (W2 * x1) % W;
+            dfc acc = zero;
+            int m = 0;
+            for (int n1 = 0; n1 < W1; ++n1) {
+                const int k = W2 * n1 + n2;
+                const dfc qv = k < Wh ? B[y * Wh + k] : cconj(B[y * Wh + W - k]);
+                acc = cadd(acc, cmul(qv, cconj(s_wW[m])));
+                m += step;
+                if (m >= W) m -= W;
+            }
+            T[o] = acc;
+        }
+        __syncthreads();
         double best = -INFINITY;
         long long bj = 0x7fffffffffffffffLL;
         for (int o = threadIdx.x; o < H * W; o += blockDim.x) {
-            const int y = o / W, x = o - y * W;
+            const int y = o / W, x = o - y * W, x1 = x % W1;
             df acc = df{0.f, 0.f};
             int m = 0;
-            for (int kx = 0; kx < Wh; ++kx) {
-                df t = gen_re_mul(B[y * Wh + kx], cconj(s_wW[m]));
-                if (kx != 0 && 2 * kx != W) t = df_scale(t, 2.f);
-                acc = df_add_abs(acc, t);
+            for (int n2 = 0; n2 < W2; ++n2) {
+                acc = df_add_abs(acc, gen_re_mul(T[y * W + n2 * W1 + x1], cconj(s_wW[m])));
                 m += x;
                 if (m >= W) m -= W;
             }
@@ -168,47 +281,174 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
         const int iy = (int)(bj / W), ix = (int)(bj % W);
         const int py = iy > H / 2 ? iy - H : iy;
         const int px = ix > W / 2 ? ix - W : ix;
-        // V[jy][kx] = sum_ky X[ky][kx] e^{2 pi i ky' q / (uH)}, q = py u + jy - h0: the index
-        // ky q mod uH advances by q per row, and the negative rows subtract H q mod uH
-        for (int o = threadIdx.x; o < M * Wh; o += blockDim.x) {
-            const int jy = o / Wh, kx = o - jy * Wh;
-            const long long q = gen_mod((long long)py * u + jy - h0, DH), nq = gen_mod((long long)H * q, DH);
-            const bool folded = kx != 0 && 2 * kx != W;
-            dfc acc = zero;
-            long long m = 0;
-            for (int ky = 0; ky < H; ++ky) {
-                long long ms = m;
-                if (2 * ky >= H) { ms -= nq; if (ms < 0) ms += DH; }
-                dfc e = pl.uH[ms];
-                if (ky == nyq_y && folded) e.im = df{0.f, 0.f};
-                acc = cadd(acc, cmul(X[ky * Wh + kx], e));
-                m += q;
-                if (m >= DH) m -= DH;
+        // The upsampled grid. First in FP32 with a rounding bound Bnd: every point whose FP32
+        // value is within 2 Bnd of the FP32 best is a candidate, and only the candidates are
+        // evaluated in double-float, by the same operations and order as the exhaustive
+        // evaluation below (so the record is the one that evaluation gives). Too many
+        // candidates, or the exhaustive flag: the whole grid in double-float.
+        const int kcap = kGenCand < 2 * (H > M ? H : M) ? kGenCand : 2 * (H > M ? H : M);
+        bool full = pl.exhaustive != 0;
+        if (!full) {
+            float2* X32 = (float2*)a;                              // X rounded to FP32, H x Wh
+            float2* V32 = (float2*)B;                              // M x Wh
+            for (int o = threadIdx.x; o < H * Wh; o += blockDim.x) X32[o] = make_float2(X[o].re.hi, X[o].im.hi);
+            __syncthreads();
+            // V32[jy][kx] = sum_ky X32[ky][kx] e32^{2 pi i ky' q / (uH)}
+            for (int o = threadIdx.x; o < M * Wh; o += blockDim.x) {
+                const int jy = o / Wh, kx = o - jy * Wh;
+                const int q = (int)gen_mod((long long)py * u + jy - h0, DH), nq = (int)gen_mod((long long)H * q, DH);
+                const bool folded = kx != 0 && 2 * kx != W;
+                float ar = 0.f, ai = 0.f;
+                int m = 0;
+                for (int ky = 0; ky < H; ++ky) {
+                    int ms = m;
+                    if (2 * ky >= H) { ms -= nq; if (ms < 0) ms += (int)DH; }
+                    float2 e = pl.uH32[ms];
+                    if (ky == nyq_y && folded) e.y = 0.f;
+                    const float2 x = X32[ky * Wh + kx];
+                    ar = __fmaf_rn(x.x, e.x, ar);
+                    ar = __fmaf_rn(-x.y, e.y, ar);
+                    ai = __fmaf_rn(x.x, e.y, ai);
+                    ai = __fmaf_rn(x.y, e.x, ai);
+                    m += q;
+                    if (m >= (int)DH) m -= (int)DH;
+                }
+                V32[o] = make_float2(ar, ai);
             }
-            B[o] = acc;
-        }
-        __syncthreads();
-        // cu(jy, jx) = sum_kx g(kx) Re V[jy][kx] e^{2 pi i kx' q / (uW)}, q = px u + jx - h0
-        best = -INFINITY;
-        bj = 0x7fffffffffffffffLL;
-        for (int o = threadIdx.x; o < M * M; o += blockDim.x) {
-            const int jy = o / M, jx = o - jy * M;
-            const long long q = gen_mod((long long)px * u + jx - h0, DW), nq = gen_mod((long long)W * q, DW);
-            df acc = df{0.f, 0.f};
-            long long m = 0;
-            for (int kx = 0; kx < Wh; ++kx) {
-                long long ms = m;
-                if (2 * kx >= W) { ms -= nq; if (ms < 0) ms += DW; }
-                df t = gen_re_mul(B[jy * Wh + kx], pl.uW[ms]);
-                if (kx != 0 && 2 * kx != W) t = df_scale(t, 2.f);
-                acc = df_add_abs(acc, t);
-                m += q;
-                if (m >= DW) m -= DW;
+            // bound ingredients: sum_kx g A(kx), A(kx) = sum_ky |X32(ky, kx)|_1, and
+            // max_jy S(jy), S(jy) = sum_kx g |V32(jy, kx)|_1
+            double sA = 0.0, sS = 0.0;
+            for (int kx = threadIdx.x; kx < Wh; kx += blockDim.x) {
+                double s = 0.0;
+                for (int ky = 0; ky < H; ++ky) s += fabs((double)X32[ky * Wh + kx].x) + fabs((double)X32[ky * Wh + kx].y);
+                sA += (kx != 0 && 2 * kx != W) ? 2.0 * s : s;
             }
-            const double v = pl.sense * df_to_double(acc);
-            if (v > best || (v == best && o < bj)) { best = v; bj = o; }
+            __syncthreads();
+            for (int jy = threadIdx.x; jy < M; jy += blockDim.x) {
+                double s = 0.0;
+                for (int kx = 0; kx < Wh; ++kx) {
+                    const double t = fabs((double)V32[jy * Wh + kx].x) + fabs((double)V32[jy * Wh + kx].y);
+                    s += (kx != 0 && 2 * kx != W) ? 2.0 * t : t;
+                }
+                sS = fmax(sS, s);
+            }
+            const double sumA = gen_block_sum(sA, sv), maxS = gen_block_max(sS, sv);
+            const double u32 = 0x1p-24;
+            const double Bnd = 1.01 * ((2.0 * Wh + 3.0) * u32 * maxS + (4.0 * H + 6.0) * u32 * sumA) +
+                               0x1p-30 * (maxS + sumA);
+            // pass 1: the FP32 best (the values kept when the grid is small enough); pass 2:
+            // the candidates
+            float* G = (float*)(T + (size_t)H * W);
+            const bool keep = M * M <= kGenGridKeep;
+            float b32 = -INFINITY;
+            for (int o = threadIdx.x; o < M * M; o += blockDim.x) {
+                const int jy = o / M, jx = o - jy * M;
+                const float v = pl.sense * gen_cu32(V32 + jy * Wh, pl.uW32, Wh, W, jx, px, u, h0, (int)DW);
+                if (keep) G[o] = v;
+                b32 = fmaxf(b32, v);
+            }
+            const double thr = gen_block_max((double)b32, sv) - 2.0 * Bnd;
+            if (threadIdx.x == 0) s_nc = 0;
+            __syncthreads();
+            for (int o = threadIdx.x; o < M * M; o += blockDim.x) {
+                const int jy = o / M, jx = o - jy * M;
+                const float v = keep ? G[o] : pl.sense * gen_cu32(V32 + jy * Wh, pl.uW32, Wh, W, jx, px, u, h0, (int)DW);
+                if ((double)v >= thr) {
+                    const int k = atomicAdd(&s_nc, 1);
+                    if (k < kcap) s_cand[k] = o;
+                }
+            }
+            __syncthreads();
+            const int nc = s_nc;
+            if (nc == 0 || nc > kcap) {                            // none: a non-finite grid
+                full = true;
+            } else {
+                // candidate c, column kx: g(kx) Re V(jy_c, kx) e^{2 pi i kx' q / (uW)} in double-float
+                df* P = (df*)B;                                    // nc x Wh (V32 is no longer read)
+                __syncthreads();
+                for (int t = threadIdx.x; t < nc * Wh; t += blockDim.x) {
+                    const int cidx = t / Wh, kx = t - cidx * Wh;
+                    const int o = s_cand[cidx], jy = o / M, jx = o - jy * M;
+                    const long long q = gen_mod((long long)py * u + jy - h0, DH), nq = gen_mod((long long)H * q, DH);
+                    const bool folded = kx != 0 && 2 * kx != W;
+                    dfc acc = zero;
+                    long long m = 0;
+                    for (int ky = 0; ky < H; ++ky) {
+                        long long ms = m;
+                        if (2 * ky >= H) { ms -= nq; if (ms < 0) ms += DH; }
+                        dfc e = pl.uH[ms];
+                        if (ky == nyq_y && folded) e.im = df{0.f, 0.f};
+                        acc = cadd(acc, cmul(X[ky * Wh + kx], e));
+                        m += q;
+                        if (m >= DH) m -= DH;
+                    }
+                    const long long qx = gen_mod((long long)px * u + jx - h0, DW);
+                    long long mx = gen_mod((long long)kx * qx, DW);
+                    if (2 * kx >= W) { mx -= gen_mod((long long)W * qx, DW); if (mx < 0) mx += DW; }
+                    df term = gen_re_mul(acc, pl.uW[mx]);
+                    if (folded) term = df_scale(term, 2.f);
+                    P[t] = term;
+                }
+                __syncthreads();
+                if (threadIdx.x < nc) {
+                    df acc = df{0.f, 0.f};
+                    for (int kx = 0; kx < Wh; ++kx) acc = df_add_abs(acc, P[threadIdx.x * Wh + kx]);
+                    s_cval[threadIdx.x] = pl.sense * df_to_double(acc);
+                }
+                __syncthreads();
+                best = -INFINITY;
+                bj = 0x7fffffffffffffffLL;
+                for (int k = 0; k < nc; ++k) {
+                    const double v = s_cval[k];
+                    const long long j = s_cand[k];
+                    if (v > best || (v == best && j < bj)) { best = v; bj = j; }
+                }
+                __syncthreads();
+            }
         }
-        gen_block_best(best, bj, sv, sj);
+        if (full) {
+            // V[jy][kx] = sum_ky X[ky][kx] e^{2 pi i ky' q / (uH)}, q = py u + jy - h0: the index
+            // ky q mod uH advances by q per row, and the negative rows subtract H q mod uH
+            for (int o = threadIdx.x; o < M * Wh; o += blockDim.x) {
+                const int jy = o / Wh, kx = o - jy * Wh;
+                const long long q = gen_mod((long long)py * u + jy - h0, DH), nq = gen_mod((long long)H * q, DH);
+                const bool folded = kx != 0 && 2 * kx != W;
+                dfc acc = zero;
+                long long m = 0;
+                for (int ky = 0; ky < H; ++ky) {
+                    long long ms = m;
+                    if (2 * ky >= H) { ms -= nq; if (ms < 0) ms += DH; }
+                    dfc e = pl.uH[ms];
+                    if (ky == nyq_y && folded) e.im = df{0.f, 0.f};
+                    acc = cadd(acc, cmul(X[ky * Wh + kx], e));
+                    m += q;
+                    if (m >= DH) m -= DH;
+                }
+                B[o] = acc;
+            }
+            __syncthreads();
+            // cu(jy, jx) = sum_kx g(kx) Re V[jy][kx] e^{2 pi i kx' q / (uW)}, q = px u + jx - h0
+            best = -INFINITY;
+            bj = 0x7fffffffffffffffLL;
+            for (int o = threadIdx.x; o < M * M; o += blockDim.x) {
+                const int jy = o / M, jx = o - jy * M;
+                const long long q = gen_mod((long long)px * u + jx - h0, DW), nq = gen_mod((long long)W * q, DW);
+                df acc = df{0.f, 0.f};
+                long long m = 0;
+                for (int kx = 0; kx < Wh; ++kx) {
+                    long long ms = m;
+                    if (2 * kx >= W) { ms -= nq; if (ms < 0) ms += DW; }
+                    df t = gen_re_mul(B[jy * Wh + kx], pl.uW[ms]);
+                    if (kx != 0 && 2 * kx != W) t = df_scale(t, 2.f);
+                    acc = df_add_abs(acc, t);
+                    m += q;
+                    if (m >= DW) m -= DW;
+                }
+                const double v = pl.sense * df_to_double(acc);
+                if (v > best || (v == best && o < bj)) { best = v; bj = o; }
+            }
+            gen_block_best(best, bj, sv, sj);
+        }
         if (threadIdx.x == 0) {
             const int jy = (int)(bj / M), jx = (int)(bj % M);
             Result r;
@@ -217,7 +457,7 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
             r.peak = (float)(pl.sense * best / ((double)H * W));
             r.ipy = py;
             r.ipx = px;
-            r.flags = kRGeneric;
+            r.flags = kRGeneric | (best > -INFINITY && best < INFINITY ? 0u : kRNonFinite);
             gb.out[it.out_index] = r;
         }
     }
@@ -225,8 +465,8 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
 
 // Tables of one general shape: e^{-2 pi i m / H} (m < H), e^{-2 pi i m / W} (m < W),
 // e^{+2 pi i m / (uH)} (m < uH) and e^{+2 pi i m / (uW)} (m < uW), one block of
-// H + W + uH + uW entries.
-__global__ void gen_init_tables(int H, int W, int u, dfc* tab) {
+// H + W + uH + uW double-floats; tab32 holds the last two rounded to FP32 (uH + uW).
+__global__ void gen_init_tables(int H, int W, int u, dfc* tab, float2* tab32) {
     const long long DH = (long long)u * H, DW = (long long)u * W, n = H + W + DH + DW;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         double s, c;
@@ -240,6 +480,7 @@ __global__ void gen_init_tables(int H, int W, int u, dfc* tab) {
             sincospi(2.0 * (double)(i - H - W - DH) / (double)DW, &s, &c);
         }
         tab[i] = dfc{df_from_double(c), df_from_double(s)};
+        if (i >= H + W) tab32[i - H - W] = make_float2((float)c, (float)s);
     }
 }
 

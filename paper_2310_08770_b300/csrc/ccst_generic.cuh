@@ -8,11 +8,15 @@ namespace ccst {
 
 struct GenPlan {
     int H, W, u, M, h0, method, in_dtype;
+    int H1, H2, W1, W2;     // H = H1 H2, W = W1 W2: the two levels of each DFT
     float eps, sense;
+    int exhaustive;         // 1: the whole upsampled grid in double-float (verification)
     const dfc* wH;          // H:    e^{-2 pi i m / H}
     const dfc* wW;          // W:    e^{-2 pi i m / W}
     const dfc* uH;          // u H:  e^{+2 pi i m / (u H)}
     const dfc* uW;          // u W:  e^{+2 pi i m / (u W)}
+    const float2* uH32;     // the same two tables rounded to FP32
+    const float2* uW32;
 };
 
 struct GenItem {
@@ -23,11 +27,24 @@ struct GenItem {
     int ref;
 };
 
+// Upsampled grids of at most this many points keep their FP32 values between the two passes.
+constexpr int kGenGridKeep = 65536;
+
 // Scratch of one CTA of the general-size kernel, in complex double-floats: X (H x Wh), the
-// work array (max(H, M) x Wh) and the operand plane (H x W double-floats), Wh = W/2 + 1.
+// work array (max(H, M) x Wh), the operand plane (H x W double-floats), the inner DFT
+// levels (H x W) and the FP32 grid values (M x M floats, if kept), Wh = W/2 + 1.
 inline long long gen_scratch_stride(int H, int W, int M) {
-    const long long Wh = W / 2 + 1;
-    return (long long)H * Wh + (long long)(H > M ? H : M) * Wh + ((long long)H * W + 1) / 2;
+    const long long Wh = W / 2 + 1, MM = (long long)M * M;
+    return (long long)H * Wh + (long long)(H > M ? H : M) * Wh + ((long long)H * W + 1) / 2 + (long long)H * W +
+           (MM <= kGenGridKeep ? (MM + 3) / 4 : 0);
+}
+
+// The two levels of an N-point DFT: N1 the largest divisor of N not above sqrt(N).
+inline int gen_split(int N) {
+    int n1 = 1;
+    for (int d = 1; d * d <= N; ++d)
+        if (N % d == 0) n1 = d;
+    return n1;
 }
 
 struct GenBatch {

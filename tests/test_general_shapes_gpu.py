@@ -170,3 +170,36 @@ def test_shapes_outside_the_range_are_refused(torch):
         with pytest.raises(C.CcstError) as e:
             C.Tracker(np.ones((H, W), np.float32), upsample=10, in_dtype="f32")
         assert e.value.code == C.E_SHAPE
+
+
+@pytest.mark.parametrize("H,W,u,method", [(96, 96, 100, oracle.CC_U), (48, 80, 64, oracle.CC_SN),
+                                          (30, 30, 100, oracle.CC_U), (256, 128, 50, oracle.CC_U),
+                                          (12, 8, 3, oracle.CC_SN)])
+def test_fp32_grid_with_candidates_equals_the_exhaustive_grid(torch, H, W, u, method):
+    # the FP32 pass only chooses which points the double-float evaluation visits: records
+    # must be byte-identical to evaluating the whole grid in double-float. Extra frames: the
+    # reference itself (peak at offset 0), a noise-free frame shifted by half a grid step
+    # (two points tie in exact arithmetic) and a flat frame (every point ties: more
+    # candidates than the list holds, so the kernel falls back to the whole grid)
+    ref, frames = pairs(H, W, 16, seed=H + W + u, u16=False)
+    half = synth.gaussian_spot(H, W, H / 2 + 0.5 / u, W / 2 - 0.5 / u, 2.5, 1500.0, 10.0)
+    extra = np.array([ref, half, np.full((H, W), 7.0)], np.float32)
+    frames = np.concatenate([frames, extra])
+    recs = []
+    for exhaustive in (False, True):
+        t = C.Tracker(ref, upsample=u, method=method, in_dtype="f32", max_batch=64, exhaustive=exhaustive)
+        recs.append(track(torch, t, frames))
+        t.close()
+    assert recs[0].tobytes() == recs[1].tobytes()
+    check(ref, frames[:16], recs[0][:16], u, method)
+
+
+def test_non_finite_frame_is_flagged(torch):
+    ref, frames = pairs(40, 40, 3, seed=9, u16=False)
+    frames[1, 7, 9] = np.nan
+    t = tracker(ref, 50, oracle.CC_U, False)
+    res = track(torch, t, frames)
+    t.close()
+    assert res[1]["flags"] & C.R_NONFINITE and res[1]["flags"] & C.R_GENERIC
+    assert not (res[0]["flags"] & C.R_NONFINITE) and not (res[2]["flags"] & C.R_NONFINITE)
+    check(ref, frames[[0, 2]], res[[0, 2]], 50, oracle.CC_U)
