@@ -707,7 +707,13 @@ def run_ours(args):
                      "ms_per_launch": total_ms / args.steps,
                      "achieved_basis": f"flop/frame x frames / timed region; {len(streams)} batches in flight "
                                        "on alternating streams, so launch spans overlap",
-                     "peak_basis": "148 SMs x 128 FP32 FMA lanes x 2 x 2032 MHz (nominal max clock)"},
+                     "peak_basis": "148 SMs x 128 FP32 FMA lanes x 2 x 2032 MHz (nominal max clock)",
+                     "ingest": {"achieved": value / world * (H * W * 2 + 24) / 1e9,
+                                "peak": load_peaks().get("hbm_gbs"), "unit": "GB/s",
+                                "frac": (value / world * (H * W * 2 + 24) / 1e9 / load_peaks()["hbm_gbs"]
+                                         if load_peaks().get("hbm_gbs") else None),
+                                "basis": "algorithmic HBM bytes per frame (uint16 input + 24-byte record) x "
+                                         "frames/s per GPU, against the measured copy bandwidth"}},
         "clocks": clk,
         "e2e": e2e,
         "gpu_launches": args.steps,                     # one tracking kernel per batch

@@ -59,6 +59,22 @@ __device__ __forceinline__ long long gen_mod(long long a, long long m) {
     a %= m;
     return a < 0 ? a + m : a;
 }
+// 16- and 8-byte vector accesses: every complex double-float array of this kernel starts on
+// a 16-byte boundary (allocation bases and offsets in whole complex elements), so one access
+// moves one element instead of four (two).
+__device__ __forceinline__ dfc ldc(const dfc* p) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    return dfc{df{v.x, v.y}, df{v.z, v.w}};
+}
+__device__ __forceinline__ void stc(dfc* p, dfc v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v.re.hi, v.re.lo, v.im.hi, v.im.lo);
+}
+__device__ __forceinline__ df ldd(const df* p) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    return df{v.x, v.y};
+}
+__device__ __forceinline__ void std_(df* p, df v) { *reinterpret_cast<float2*>(p) = make_float2(v.hi, v.lo); }
+
 // Re(a b) in double-float
 __device__ __forceinline__ df gen_re_mul(dfc a, dfc b) {
     return df_add_abs(df_mul(a.re, b.re), df_neg(df_mul(a.im, b.im)));
@@ -117,7 +133,7 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
     __shared__ double sv[32];
     __shared__ long long sj[32];
     __shared__ long long s_item;
-    __shared__ dfc s_wH[256], s_wW[256];                       // e^{-2 pi i m / H}, e^{-2 pi i m / W}
+    __shared__ __align__(16) dfc s_wH[256], s_wW[256];                       // e^{-2 pi i m / H}, e^{-2 pi i m / W}
     __shared__ int s_nc, s_cand[kGenCand];                     // upsampled-grid candidates
     __shared__ double s_cval[kGenCand];
     dfc* const X = gb.scratch + (size_t)blockIdx.x * gb.scratch_stride;
@@ -148,16 +164,16 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
         dfc* T = (dfc*)a + ((size_t)H * W + 1) / 2;                // inner DFT levels, H x W
         const dfc zero = dfc{df{0.f, 0.f}, df{0.f, 0.f}};
         const df epsd = df_from_double((double)pl.eps);
-        for (int m = threadIdx.x; m < H; m += blockDim.x) s_wH[m] = pl.wH[m];
-        for (int m = threadIdx.x; m < W; m += blockDim.x) s_wW[m] = pl.wW[m];
+        for (int m = threadIdx.x; m < H; m += blockDim.x) stc(s_wH + m, ldc(pl.wH + m));
+        for (int m = threadIdx.x; m < W; m += blockDim.x) stc(s_wW + m, ldc(pl.wW + m));
         for (int o = threadIdx.x; o < H * W; o += blockDim.x) {
             const int y = o / W, x = o - y * W;
             const df I = df_make(pixel_f32(it.frame, pl.in_dtype, (long long)y * it.pitch + x));
             if (pl.method == 0) {
-                a[o] = I;
+                std_(a + o, I);
             } else {
                 const df ip = df_add(I, epsd);
-                a[o] = df_mul(ip, ip);
+                std_(a + o, df_mul(ip, ip));
             }
         }
         __syncthreads();
@@ -172,13 +188,13 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
             dfc acc = zero;
             int m = 0;
             for (int n1 = 0; n1 < W1; ++n1) {
-                const df v = a[y * W + W2 * n1 + n2];
-                const dfc t = s_wW[m];
+                const df v = ldd(a + y * W + W2 * n1 + n2);
+                const dfc t = ldc(s_wW + m);
                 acc = cadd(acc, dfc{df_mul(v, t.re), df_mul(v, t.im)});
                 m += step;
                 if (m >= W) m -= W;
             }
-            T[o] = acc;
+            stc(T + o, acc);
         }
         __syncthreads();
         for (int o = threadIdx.x; o < H * Wh; o += blockDim.x) {
@@ -186,11 +202,11 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
             dfc acc = zero;
             int m = 0;
             for (int n2 = 0; n2 < W2; ++n2) {
-                acc = cadd(acc, cmul(T[y * W + n2 * W1 + k1], s_wW[m]));
+                acc = cadd(acc, cmul(ldc(T + (y * W + n2 * W1 + k1)), ldc(s_wW + m)));
                 m += kx;
                 if (m >= W) m -= W;
             }
-            B[o] = acc;
+            stc(B + o, acc);
         }
         __syncthreads();
         // X[ky][kx] = (sum_y R[y][kx] wH^(y ky)) conj F[b](ky, kx); T[n2][k1][kx] first
@@ -200,11 +216,11 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
             dfc acc = zero;
             int m = 0;
             for (int n1 = 0; n1 < H1; ++n1) {
-                acc = cadd(acc, cmul(B[(H2 * n1 + n2) * Wh + kx], s_wH[m]));
+                acc = cadd(acc, cmul(ldc(B + ((H2 * n1 + n2) * Wh + kx)), ldc(s_wH + m)));
                 m += step;
                 if (m >= H) m -= H;
             }
-            T[o] = acc;
+            stc(T + o, acc);
         }
         __syncthreads();
         for (int o = threadIdx.x; o < H * Wh; o += blockDim.x) {
@@ -212,11 +228,11 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
             dfc acc = zero;
             int m = 0;
             for (int n2 = 0; n2 < H2; ++n2) {
-                acc = cadd(acc, cmul(T[(n2 * H1 + k1) * Wh + kx], s_wH[m]));
+                acc = cadd(acc, cmul(ldc(T + ((n2 * H1 + k1) * Wh + kx)), ldc(s_wH + m)));
                 m += ky;
                 if (m >= H) m -= H;
             }
-            X[o] = cmul(acc, cconj(Fb[o]));
+            stc(X + o, cmul(acc, cconj(ldc(Fb + o))));
         }
         __syncthreads();
         // Q[y][kx] = sum_ky X[ky][kx] wH^-(ky y); T[n2][y1][kx] first
@@ -226,11 +242,11 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
             dfc acc = zero;
             int m = 0;
             for (int n1 = 0; n1 < H1; ++n1) {
-                acc = cadd(acc, cmul(X[(H2 * n1 + n2) * Wh + kx], cconj(s_wH[m])));
+                acc = cadd(acc, cmul(ldc(X + ((H2 * n1 + n2) * Wh + kx)), cconj(ldc(s_wH + m))));
                 m += step;
                 if (m >= H) m -= H;
             }
-            T[o] = acc;
+            stc(T + o, acc);
         }
         __syncthreads();
         for (int o = threadIdx.x; o < H * Wh; o += blockDim.x) {
@@ -238,11 +254,11 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
             dfc acc = zero;
             int m = 0;
             for (int n2 = 0; n2 < H2; ++n2) {
-                acc = cadd(acc, cmul(T[(n2 * H1 + y1) * Wh + kx], cconj(s_wH[m])));
+                acc = cadd(acc, cmul(ldc(T + ((n2 * H1 + y1) * Wh + kx)), cconj(ldc(s_wH + m))));
                 m += y;
                 if (m >= H) m -= H;
             }
-            B[o] = acc;
+            stc(B + o, acc);
         }
         __syncthreads();
         // c(y, x) = Re sum_{k < W} Q[y][k] wW^-(k x), the row completed by Q[y][W - k] =
@@ -255,12 +271,12 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
             int m = 0;
             for (int n1 = 0; n1 < W1; ++n1) {
                 const int k = W2 * n1 + n2;
-                const dfc qv = k < Wh ? B[y * Wh + k] : cconj(B[y * Wh + W - k]);
-                acc = cadd(acc, cmul(qv, cconj(s_wW[m])));
+                const dfc qv = k < Wh ? ldc(B + (y * Wh + k)) : cconj(ldc(B + (y * Wh + W - k)));
+                acc = cadd(acc, cmul(qv, cconj(ldc(s_wW + m))));
                 m += step;
                 if (m >= W) m -= W;
             }
-            T[o] = acc;
+            stc(T + o, acc);
         }
         __syncthreads();
         double best = -INFINITY;
@@ -270,7 +286,7 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
             df acc = df{0.f, 0.f};
             int m = 0;
             for (int n2 = 0; n2 < W2; ++n2) {
-                acc = df_add_abs(acc, gen_re_mul(T[y * W + n2 * W1 + x1], cconj(s_wW[m])));
+                acc = df_add_abs(acc, gen_re_mul(ldc(T + (y * W + n2 * W1 + x1)), cconj(ldc(s_wW + m))));
                 m += x;
                 if (m >= W) m -= W;
             }
@@ -291,7 +307,10 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
         if (!full) {
             float2* X32 = (float2*)a;                              // X rounded to FP32, H x Wh
             float2* V32 = (float2*)B;                              // M x Wh
-            for (int o = threadIdx.x; o < H * Wh; o += blockDim.x) X32[o] = make_float2(X[o].re.hi, X[o].im.hi);
+            for (int o = threadIdx.x; o < H * Wh; o += blockDim.x) {
+                const dfc xv = ldc(X + o);
+                X32[o] = make_float2(xv.re.hi, xv.im.hi);
+            }
             __syncthreads();
             // V32[jy][kx] = sum_ky X32[ky][kx] e32^{2 pi i ky' q / (uH)}
             for (int o = threadIdx.x; o < M * Wh; o += blockDim.x) {
@@ -376,23 +395,23 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
                     for (int ky = 0; ky < H; ++ky) {
                         long long ms = m;
                         if (2 * ky >= H) { ms -= nq; if (ms < 0) ms += DH; }
-                        dfc e = pl.uH[ms];
+                        dfc e = ldc(pl.uH + ms);
                         if (ky == nyq_y && folded) e.im = df{0.f, 0.f};
-                        acc = cadd(acc, cmul(X[ky * Wh + kx], e));
+                        acc = cadd(acc, cmul(ldc(X + (ky * Wh + kx)), e));
                         m += q;
                         if (m >= DH) m -= DH;
                     }
                     const long long qx = gen_mod((long long)px * u + jx - h0, DW);
                     long long mx = gen_mod((long long)kx * qx, DW);
                     if (2 * kx >= W) { mx -= gen_mod((long long)W * qx, DW); if (mx < 0) mx += DW; }
-                    df term = gen_re_mul(acc, pl.uW[mx]);
+                    df term = gen_re_mul(acc, ldc(pl.uW + mx));
                     if (folded) term = df_scale(term, 2.f);
-                    P[t] = term;
+                    std_(P + t, term);
                 }
                 __syncthreads();
                 if (threadIdx.x < nc) {
                     df acc = df{0.f, 0.f};
-                    for (int kx = 0; kx < Wh; ++kx) acc = df_add_abs(acc, P[threadIdx.x * Wh + kx]);
+                    for (int kx = 0; kx < Wh; ++kx) acc = df_add_abs(acc, ldd(P + threadIdx.x * Wh + kx));
                     s_cval[threadIdx.x] = pl.sense * df_to_double(acc);
                 }
                 __syncthreads();
@@ -418,13 +437,13 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
                 for (int ky = 0; ky < H; ++ky) {
                     long long ms = m;
                     if (2 * ky >= H) { ms -= nq; if (ms < 0) ms += DH; }
-                    dfc e = pl.uH[ms];
+                    dfc e = ldc(pl.uH + ms);
                     if (ky == nyq_y && folded) e.im = df{0.f, 0.f};
-                    acc = cadd(acc, cmul(X[ky * Wh + kx], e));
+                    acc = cadd(acc, cmul(ldc(X + (ky * Wh + kx)), e));
                     m += q;
                     if (m >= DH) m -= DH;
                 }
-                B[o] = acc;
+                stc(B + o, acc);
             }
             __syncthreads();
             // cu(jy, jx) = sum_kx g(kx) Re V[jy][kx] e^{2 pi i kx' q / (uW)}, q = px u + jx - h0
@@ -438,7 +457,7 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
                 for (int kx = 0; kx < Wh; ++kx) {
                     long long ms = m;
                     if (2 * kx >= W) { ms -= nq; if (ms < 0) ms += DW; }
-                    df t = gen_re_mul(B[jy * Wh + kx], pl.uW[ms]);
+                    df t = gen_re_mul(ldc(B + (jy * Wh + kx)), ldc(pl.uW + ms));
                     if (kx != 0 && 2 * kx != W) t = df_scale(t, 2.f);
                     acc = df_add_abs(acc, t);
                     m += q;
