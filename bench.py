@@ -469,7 +469,8 @@ ROIS_ORACLE = 48
 def rois_leg(C, torch, stream, n_rois=ROIS_N, sides=ROIS_SIDES, plain=True):
     """Uneven batch: FP32 ROIs of mixed sizes, each against its own reference, in one
     ccst_track_rois call (the power-of-two kernel and the general-size kernel run side by
-    side), against the same ROIs as one call each."""
+    side), against the same ROIs as one call each. Timed with the default general-size
+    schedule, then after ccst_autotune (the reported value)."""
     import ctypes
     from paper_2310_08770_b300 import synth
     r = synth.uneven_rois(seed=0, n=n_rois, sides=sides)
@@ -482,7 +483,7 @@ def rois_leg(C, torch, stream, n_rois=ROIS_N, sides=ROIS_SIDES, plain=True):
     rois = C.make_rois(frames, ids)
     out = t.empty_results(n)
     ev = lambda: torch.cuda.Event(enable_timing=True)          # noqa: E731
-    with torch.cuda.stream(stream):
+    def batched():
         for _ in range(3):
             C.ccst_track_rois(t.ctx, rois, n, out)
         torch.cuda.synchronize()
@@ -492,7 +493,14 @@ def rois_leg(C, torch, stream, n_rois=ROIS_N, sides=ROIS_SIDES, plain=True):
             C.ccst_track_rois(t.ctx, rois, n, out)
         b.record(stream)
         torch.cuda.synchronize()
-        batched_ms = a.elapsed_time(b) / ROIS_REPS
+        return a.elapsed_time(b) / ROIS_REPS
+
+    with torch.cuda.stream(stream):
+        default_ms = batched()
+        t0 = time.perf_counter()
+        tuned = C.ccst_autotune(t.ctx, 3, rois, n) if any(s not in (16, 32, 64, 128) for s in sides) else []
+        tune_s = time.perf_counter() - t0
+        batched_ms = batched() if tuned else default_ms
         res = C.decode(out)
         plain_ms = None
         if plain:
@@ -514,6 +522,9 @@ def rois_leg(C, torch, stream, n_rois=ROIS_N, sides=ROIS_SIDES, plain=True):
                         f"u={U}, CC-U",
             "value": n / (batched_ms / 1e3), "unit": "ROIs/s", "ms_per_batch": batched_ms,
             "reference_setup_s": setup_s,
+            "autotune": {"ms_per_batch_default_schedule": default_ms, "seconds": tune_s,
+                         "plans": [{k: x[k] for k in ("H", "W", "H1", "W1", "threads", "us_per_frame")}
+                                   for x in tuned]},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "kernel": "track_rois_kernel + track_generic_kernel", "flop_total": flop,
                          "flop_basis": "the folded formulation's algorithmic flops for every ROI (the general-size "

@@ -243,6 +243,35 @@ int ccst_add_reference(ccst_ctx* ctx, const float* ref, int H, int W, int* ref_i
  * ROI whose size differs from its reference's), CCST_E_NOMEM, CCST_E_CUDA. */
 int ccst_track_rois(ccst_ctx* ctx, const ccst_roi* rois, int64_t n, ccst_result* out_dev);
 
+/* One tuned general-size plan (ccst_autotune): 32 bytes. */
+typedef struct ccst_tune_result {
+    int32_t H, W;           /* the plan's frame shape                                        */
+    int32_t H1, W1;         /* chosen two-level splits: H = H1 (H / H1), W = W1 (W / W1)     */
+    int32_t threads;        /* chosen CTA size of the general-size kernel (the context's)    */
+    int32_t timed;          /* configurations timed in the call                              */
+    double   us_per_frame;  /* the chosen splits' time per frame (512 threads, two grid waves) */
+} ccst_tune_result;
+
+/* Autotune the general-size kernel (NEXT-2: the size-dependent choices of the uneven-ROI
+ * path). For every general-size plan of the context (shapes added by ccst_create or
+ * ccst_add_reference outside the power-of-two kernel) it times, on synthetic frames of the
+ * plan's shape and one of its references, each two-level split of the row and column DFTs
+ * (the default: the largest divisor of N not above sqrt(N); its cofactor; the next divisor
+ * below) as the best of `reps` launches of two grid waves after a warm-up, and keeps the
+ * fastest. Then it times both CTA sizes (512 and 256 threads, one per launch) and keeps the
+ * faster: on the caller's ROI batch `rois` (n_rois > 0; run through ccst_track_rois, both
+ * kernels, as the caller will run it), else on a work list of every plan's frames, largest
+ * first. Later launches of the context (ccst_track, ccst_track_rois, the server) use them.
+ *   rois     host, n_rois descriptors as for ccst_track_rois, or NULL with n_rois = 0. The splits change only the rounding order of the double-float DFTs: records
+ * keep the parity bar and stay the same alone and in a batch. Power-of-two shapes have
+ * nothing to tune (one compiled schedule per size).
+ *   out      host, max_out records (may be NULL when max_out is 0), one per general plan.
+ *   n_out    receives the number of records written (may be NULL).
+ * Synchronous; the context must not be in use by a server or other calls meanwhile.
+ * Errors: CCST_E_INVALID, CCST_E_NOMEM, CCST_E_CUDA. */
+int ccst_autotune(ccst_ctx* ctx, int reps, const ccst_roi* rois, int64_t n_rois, ccst_tune_result* out,
+                  int max_out, int* n_out);
+
 /* ---- Serving: continuous batching of single frames from several cameras.
  *
  * A server runs a worker thread over a context. Each camera is a reference of the

@@ -48,6 +48,11 @@ class ccst_server_stats_t(ctypes.Structure):
                 ("p99_us", ctypes.c_double), ("max_us", ctypes.c_double), ("in_flight", ctypes.c_int64)]
 
 
+class ccst_tune_result(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("H1", ctypes.c_int32), ("W1", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("timed", ctypes.c_int32), ("us_per_frame", ctypes.c_double)]
+
+
 class ccst_params(ctypes.Structure):
     _fields_ = [("upsample", ctypes.c_int32), ("method", ctypes.c_int32), ("eps", ctypes.c_float),
                 ("in_dtype", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("max_H", ctypes.c_int32),
@@ -111,6 +116,8 @@ _SIGS = [
                                            ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_uint64,
                                            ctypes.POINTER(ccst_server_stats_t)]),
     ("ccst_server_destroy", None, [ctypes.c_void_p]),
+    ("ccst_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                                     ctypes.POINTER(ccst_tune_result), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("ccst_rt_begin", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
                                      ctypes.c_double]),
     ("ccst_rt_track", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
@@ -361,6 +368,16 @@ def ccst_backward(ctx, frames_dev, n, pitch_elems, rec_dev, g_dxdy_dev, g_frames
 
 def ccst_destroy(ctx) -> None:
     lib().ccst_destroy(ctx)
+
+
+def ccst_autotune(ctx, reps: int = 3, rois=None, n_rois: int = 0) -> list:
+    """Autotune the context's general-size plans (optionally on a ccst_roi batch from
+    make_rois); one dict per plan (shape, splits, CTA size)."""
+    arr = (ccst_tune_result * 64)()
+    n = ctypes.c_int()
+    _check(lib().ccst_autotune(ctx, int(reps), ctypes.cast(rois, ctypes.c_void_p) if rois is not None else None,
+                               int(n_rois), arr, 64, ctypes.byref(n)), ctx)
+    return [{k: getattr(arr[i], k) for k, _ in ccst_tune_result._fields_} for i in range(n.value)]
 
 
 def ccst_grid_size(ctx) -> int:

@@ -650,6 +650,7 @@ struct ccst_ctx {
     cudaStream_t gstream = nullptr;   // ROI batches run their general sizes here, beside the main kernel
     cudaEvent_t gfork = nullptr, gjoin = nullptr;
     int gen_grid = 0;
+    int gen_threads = 512;            // CTA size of the general-size kernel (ccst_autotune may lower it)
     bool gen_dirty = true;            // plans or references changed since the last upload
     bool general = false;             // every frame of this context takes the general-size kernel
     Geom* d_geoms = nullptr;
@@ -1898,7 +1899,7 @@ static int gen_prepare(ccst_ctx* c) {
     if (!c->gen_grid) {
         int sms = 0, occ = 0;
         CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-        CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, track_generic_kernel_ptr(), 512, 0));
+        CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, track_generic_kernel_ptr(), c->gen_threads, 0));
         if (occ < 1) return fail(c, CCST_E_SHAPE, "the general-size kernel does not fit on an SM");
         c->gen_grid = sms * occ;
     }
@@ -1964,7 +1965,7 @@ static int gen_launch(ccst_ctx* c, GenLane& lane, GenBatch gb, const GenItem* it
     gb.scratch = lane.scratch;
     gb.scratch_stride = stride;
     void* args[] = {&gb};
-    CK(c, cudaLaunchKernel(track_generic_kernel_ptr(), dim3(grid), dim3(512), args, 0, stream));
+    CK(c, cudaLaunchKernel(track_generic_kernel_ptr(), dim3(grid), dim3(c->gen_threads), args, 0, stream));
     return CCST_OK;
 }
 
@@ -1988,6 +1989,180 @@ static int gen_track(ccst_ctx* c, const Batch& b, cudaStream_t stream, GenLane& 
     gb.plan = c->refs[0].gcls;
     gb.ref = 0;
     return gen_launch(c, lane, gb, nullptr, stream, counter);
+}
+
+// Two-level splits worth timing for an N-point DFT: the default (largest divisor not above
+// sqrt(N)), its cofactor, and the next divisor below the default.
+static std::vector<int> split_candidates(int N) {
+    const int d0 = gen_split(N);
+    std::vector<int> out = {d0};
+    if (N / d0 != d0) out.push_back(N / d0);
+    for (int d = d0 - 1; d > 1; --d)
+        if (N % d == 0) {
+            out.push_back(d);
+            break;
+        }
+    return out;
+}
+
+extern "C" int ccst_track_rois(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccst_result* out_dev);
+
+extern "C" int ccst_autotune(ccst_ctx* c, int reps, const ccst_roi* rois, int64_t n_rois, ccst_tune_result* out,
+                             int max_out, int* n_out) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (reps < 1 || max_out < 0 || (max_out > 0 && !out) || n_rois < 0 || (n_rois > 0 && !rois))
+        return fail(c, CCST_E_INVALID, "ccst_autotune: bad arguments");
+    if (n_out) *n_out = 0;
+    const int np = (int)c->gplans.size();
+    if (np == 0) return CCST_OK;
+    std::vector<int> ref_of(np, -1);
+    for (int i = 0; i < (int)c->refs.size(); ++i)
+        if (c->refs[i].gcls >= 0 && ref_of[c->refs[i].gcls] < 0) ref_of[c->refs[i].gcls] = i;
+    CK(c, cudaStreamSynchronize(c->stream));
+    const size_t elem = c->p.in_dtype == CCST_U16 ? 2 : 4;
+    std::vector<void*> frames(np, nullptr);
+    Result* recs = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    GenLane lane;
+    unsigned* counter = c->d_next + 32;
+    std::vector<std::pair<int, int>> saved(np);
+    for (int p = 0; p < np; ++p) saved[p] = {c->gplans[p].p.H1, c->gplans[p].p.W1};
+    const int saved_threads = c->gen_threads;
+    auto set_split = [&](int p, int h1, int w1) {
+        GenPlan& pl = c->gplans[p].p;
+        pl.H1 = h1; pl.H2 = pl.H / h1; pl.W1 = w1; pl.W2 = pl.W / w1;
+        c->gen_dirty = true;
+    };
+    auto cleanup = [&]() {
+        for (void* f : frames)
+            if (f) cudaFree(f);
+        if (recs) cudaFree(recs);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        lane_free(lane);
+    };
+    auto bail = [&](int code) {
+        cleanup();
+        for (int p = 0; p < np; ++p) set_split(p, saved[p].first, saved[p].second);
+        c->gen_threads = saved_threads;
+        c->gen_grid = 0;
+        return code;
+    };
+    // the best of `reps` timed launches (after one untimed), in ms
+    auto time_launch = [&](GenBatch gb, const GenItem* items, double* ms_out) -> int {
+        double best = 1e300;
+        for (int r = -1; r < reps; ++r) {
+            if (cudaEventRecord(e0, c->stream) != cudaSuccess) return fail(c, CCST_E_CUDA, "ccst_autotune: event");
+            const int lrc = gen_launch(c, lane, gb, items, c->stream, counter);
+            if (lrc) return lrc;
+            if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+                return fail(c, CCST_E_CUDA, "ccst_autotune: launch");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r >= 0) best = std::min(best, (double)ms);
+        }
+        *ms_out = best;
+        return CCST_OK;
+    };
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return bail(fail(c, CCST_E_CUDA, "ccst_autotune: event"));
+    // synthetic frames: two waves of the 512-thread grid per plan
+    c->gen_threads = 512;
+    c->gen_grid = 0;
+    if ((rc = gen_prepare(c))) return bail(rc);
+    const long long nf = 2LL * c->gen_grid;
+    if (cudaMalloc(&recs, std::max((size_t)nf * np, (size_t)n_rois) * sizeof(Result)) != cudaSuccess)
+        return bail(fail(c, CCST_E_NOMEM, "ccst_autotune: records"));
+    for (int p = 0; p < np; ++p) {
+        if (ref_of[p] < 0) continue;
+        int H = c->gplans[p].p.H, W = c->gplans[p].p.W, dt = c->p.in_dtype;
+        long long n = nf;
+        if (cudaMalloc(&frames[p], (size_t)nf * H * W * elem) != cudaSuccess)
+            return bail(fail(c, CCST_E_NOMEM, "ccst_autotune: frames"));
+        void* af[] = {&H, &W, &dt, &n, &frames[p]};
+        if (cudaLaunchKernel(gen_fill_synthetic_ptr(), dim3(256), dim3(256), af, 0, c->stream) != cudaSuccess)
+            return bail(fail(c, CCST_E_CUDA, "ccst_autotune: synthetic frames"));
+    }
+    // 1. per plan, with 512-thread CTAs: the two-level splits, on a uniform batch of the plan
+    int timed = 0;
+    std::vector<double> us(np, 0.0);
+    for (int p = 0; p < np; ++p) {
+        if (ref_of[p] < 0) continue;
+        const int H = c->gplans[p].p.H, W = c->gplans[p].p.W;
+        GenBatch gb{};
+        gb.n = nf;
+        gb.out = recs;
+        gb.frames = frames[p];
+        gb.frame_bytes = (long long)H * W * (long long)elem;
+        gb.pitch = W;
+        gb.plan = p;
+        gb.ref = ref_of[p];
+        double best = 1e300;
+        int bh = saved[p].first, bw = saved[p].second;
+        for (int h1 : split_candidates(H))
+            for (int w1 : split_candidates(W)) {
+                set_split(p, h1, w1);
+                double ms = 0.0;
+                if ((rc = time_launch(gb, nullptr, &ms))) return bail(rc);
+                ++timed;
+                if (ms < best) { best = ms; bh = h1; bw = w1; }
+            }
+        set_split(p, bh, bw);
+        us[p] = 1e3 * best / (double)nf;
+    }
+    // 2. the CTA size (one per launch): on the caller's ROI batch through ccst_track_rois, or
+    // else on a work list of every plan's frames, largest first (as a mixed ROI batch runs)
+    const int threads[2] = {512, 256};
+    double tms[2] = {0.0, 0.0};
+    if (n_rois > 0) {
+        for (int ti = 0; ti < 2; ++ti) {
+            c->gen_threads = threads[ti];
+            c->gen_grid = 0;
+            double best = 1e300;
+            for (int r = -1; r < reps; ++r) {
+                if (cudaEventRecord(e0, c->stream) != cudaSuccess) return bail(fail(c, CCST_E_CUDA, "ccst_autotune: event"));
+                if ((rc = ccst_track_rois(c, rois, n_rois, (ccst_result*)recs))) return bail(rc);
+                if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+                    return bail(fail(c, CCST_E_CUDA, "ccst_autotune: ROI batch"));
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (r >= 0) best = std::min(best, (double)ms);
+            }
+            tms[ti] = best;
+            ++timed;
+        }
+    }
+    std::vector<GenItem> items;
+    for (int p = 0; p < np; ++p) {
+        if (ref_of[p] < 0) continue;
+        const GenPlan& pl = c->gplans[p].p;
+        for (long long i = 0; i < nf; ++i)
+            items.push_back(GenItem{(const char*)frames[p] + (size_t)i * pl.H * pl.W * elem, (long long)pl.W,
+                                    (long long)items.size(), p, ref_of[p]});
+    }
+    gen_sort(c, items.data(), (int64_t)items.size());
+    for (int ti = 0; ti < 2 && n_rois == 0; ++ti) {
+        c->gen_threads = threads[ti];
+        c->gen_grid = 0;
+        GenBatch gb{};
+        gb.n = (long long)items.size();
+        gb.out = recs;
+        if ((rc = time_launch(gb, items.data(), &tms[ti]))) return bail(rc);
+        ++timed;
+    }
+    cleanup();
+    c->gen_threads = tms[1] < tms[0] ? 256 : 512;
+    c->gen_grid = 0;
+    c->gen_dirty = true;
+    if ((rc = gen_prepare(c))) return rc;
+    int n = 0;
+    for (int p = 0; p < np && n < max_out; ++p) {
+        const GenPlan& pl = c->gplans[p].p;
+        out[n++] = ccst_tune_result{pl.H, pl.W, pl.H1, pl.W1, c->gen_threads, timed, us[p]};
+    }
+    if (n_out) *n_out = n;
+    return CCST_OK;
 }
 
 static int not_general(ccst_ctx* c, const char* who) {

@@ -563,6 +563,27 @@ __global__ void gen_frame_to_f32(int H, int W, int in_dtype, const void* frame, 
     }
 }
 
+// Synthetic frames for timing (the autotuner): a spot of sigma 3 on a background, moved per
+// frame, plus a hash-based pseudo-noise, in the context's input type. The kernel's work per
+// frame does not depend on the values.
+__global__ void gen_fill_synthetic(int H, int W, int in_dtype, long long n, void* frames) {
+    const long long total = n * H * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const long long f = i / ((long long)H * W);
+        const int r = (int)(i - f * H * W), y = r / W, x = r - y * W;
+        const float cy = 0.5f * H + (float)(f % 7) * 0.37f - 1.1f, cx = 0.5f * W - (float)(f % 5) * 0.29f + 0.6f;
+        const float d2 = (y - cy) * (y - cy) + (x - cx) * (x - cx);
+        unsigned h = (unsigned)i * 2654435761u;
+        h ^= h >> 15;
+        h *= 2246822519u;
+        h ^= h >> 13;
+        const float v = 20.f + 1500.f * __expf(-d2 / 18.f) + (float)(h & 15u);
+        if (in_dtype == 0) ((unsigned short*)frames)[i] = (unsigned short)v;
+        else ((float*)frames)[i] = v;
+    }
+}
+
+const void* gen_fill_synthetic_ptr() { return (const void*)gen_fill_synthetic; }
 const void* gen_ref_rows_ptr() { return (const void*)gen_ref_rows; }
 const void* gen_ref_cols_ptr() { return (const void*)gen_ref_cols; }
 const void* track_generic_kernel_ptr() { return (const void*)track_generic_kernel; }

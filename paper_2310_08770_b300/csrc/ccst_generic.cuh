@@ -70,5 +70,6 @@ const void* gen_init_tables_ptr();
 const void* gen_frame_to_f32_ptr();
 const void* gen_ref_rows_ptr();
 const void* gen_ref_cols_ptr();
+const void* gen_fill_synthetic_ptr();
 
 }  // namespace ccst

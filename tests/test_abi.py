@@ -87,6 +87,8 @@ def test_new_record_layouts_match_the_header():
             C.ccst_roi.ref_id.offset) == (0, 8, 12, 16, 24)
     # ccst_server_stats: 4 x uint64, 4 x double, int64
     assert ctypes.sizeof(C.ccst_server_stats_t) == 72 and C.ccst_server_stats_t.in_flight.offset == 64
+    # ccst_tune_result: 6 x int32, double
+    assert ctypes.sizeof(C.ccst_tune_result) == 32 and C.ccst_tune_result.us_per_frame.offset == 24
 
 
 def test_null_handles_are_rejected_without_gpu(lib):
@@ -113,4 +115,5 @@ def test_null_handles_are_rejected_without_gpu(lib):
     assert lib.ccst_server_read_stats(n, 0, ctypes.byref(st)) == C.E_INVALID
     lib.ccst_server_destroy(n)
     assert lib.ccst_debug_rt_timeout(n, n, 0, n) == C.E_INVALID
+    assert lib.ccst_autotune(n, 3, n, 0, n, 0, n) == C.E_INVALID
     assert lib.ccst_debug_reference(n, n) == C.E_INVALID

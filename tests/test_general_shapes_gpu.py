@@ -203,3 +203,33 @@ def test_non_finite_frame_is_flagged(torch):
     assert res[1]["flags"] & C.R_NONFINITE and res[1]["flags"] & C.R_GENERIC
     assert not (res[0]["flags"] & C.R_NONFINITE) and not (res[2]["flags"] & C.R_NONFINITE)
     check(ref, frames[[0, 2]], res[[0, 2]], 50, oracle.CC_U)
+
+
+def test_autotune_keeps_parity_and_batch_identity(torch):
+    # a context of 96 x 96 with references of 48, 30 and 97 (prime: a single DFT level
+    # is one of the candidates) added for ROI batches
+    ref, frames = pairs(96, 96, 6, seed=11, u16=True)
+    t = tracker(ref, 100, oracle.CC_U, True)
+    extra = [pairs(N, N, 6, seed=12 + N, u16=True) for N in (48, 30, 97)]
+    ids = [0] + [C.ccst_add_reference(t.ctx, r, *r.shape) for r, _ in extra]
+    tuned = C.ccst_autotune(t.ctx, reps=2)
+    assert len(tuned) == 4 and {(x["H"], x["W"]) for x in tuned} == {(96, 96), (48, 48), (30, 30), (97, 97)}
+    for x in tuned:
+        assert x["H"] % x["H1"] == 0 and x["W"] % x["W1"] == 0 and x["threads"] in (256, 512)
+        assert x["us_per_frame"] > 0 and x["timed"] > 0
+    sets = [(ref, frames)] + extra
+    devs = [dev(torch, f) for _, f in sets]
+    rois = [d[i] for d in devs for i in range(6)]
+    rid = [ids[k] for k in range(4) for _ in range(6)]
+    batch = C.make_rois(rois, rid)
+    assert len(C.ccst_autotune(t.ctx, 2, batch, len(rois))) == 4          # tuned on this batch
+    out = t.empty_results(len(rois))
+    C.ccst_track_rois(t.ctx, batch, len(rois), out)
+    C.ccst_sync(t.ctx)
+    mixed = C.decode(out)
+    res = track(torch, t, frames)
+    check(ref, frames, res, 100, oracle.CC_U)
+    assert mixed[:6].tobytes() == res.tobytes()                  # ROI path = tracking path
+    for k, (r, f) in enumerate(extra, start=1):
+        check(r, f, mixed[6 * k:6 * (k + 1)], 100, oracle.CC_U)
+    t.close()
