@@ -106,25 +106,30 @@ __device__ double gen_block_max(double v, double* sv) {
     return s;
 }
 
-// One point of the upsampled grid in FP32: sum_kx g(kx) Re V32[kx] e^{2 pi i kx' q / (uW)},
-// q = px u + jx - h0, by a fixed chain of FMAs (the two passes over the grid get the same
-// value). Angle indices as in the double-float evaluation, in 32 bits (uW <= 2^22).
-__device__ __forceinline__ float gen_cu32(const float2* V, const float2* tab, int Wh, int W, int jx, int px, int u,
-                                          int h0, int DW) {
+// One point of the upsampled grid in FP32: sum_kx Re V32[kx] e^{2 pi i kx' q / (uW)},
+// q = px u + jx - h0, V32 already carrying the fold weight g(kx). Angle indices as in the
+// double-float evaluation, in 32 bits (uW <= 2^22); the x-Nyquist column (W even, the last
+// one, kx' = -W/2) is taken after the loop.
+__device__ __forceinline__ float gen_cu32(const float2* V, const float2* tab, int W, int jx, int px, int u, int h0,
+                                          int DW) {
     int q = (px * u + jx - h0) % DW;
     if (q < 0) q += DW;
-    const int nq = (int)(((long long)W * q) % DW);
+    const int kpos = (W + 1) / 2;                           // kx < kpos: kx' = kx
     float acc = 0.f;
     int m = 0;
-    for (int kx = 0; kx < Wh; ++kx) {
-        int ms = m;
-        if (2 * kx >= W) { ms -= nq; if (ms < 0) ms += DW; }
-        const float2 v = V[kx], e = tab[ms];
-        const float g = (kx != 0 && 2 * kx != W) ? 2.f : 1.f;
-        acc = __fmaf_rn(g * v.x, e.x, acc);
-        acc = __fmaf_rn(-g * v.y, e.y, acc);
+    for (int kx = 0; kx < kpos; ++kx) {
+        const float2 v = V[kx], e = tab[m];
+        acc = __fmaf_rn(v.x, e.x, acc);
+        acc = __fmaf_rn(-v.y, e.y, acc);
         m += q;
         if (m >= DW) m -= DW;
+    }
+    if ((W & 1) == 0) {                                     // here m = (W/2) q mod uW
+        int ms = m - (int)(((long long)W * q) % DW);
+        if (ms < 0) ms += DW;
+        const float2 v = V[kpos], e = tab[ms];
+        acc = __fmaf_rn(v.x, e.x, acc);
+        acc = __fmaf_rn(-v.y, e.y, acc);
     }
     return acc;
 }
@@ -317,22 +322,45 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
                 const int jy = o / Wh, kx = o - jy * Wh;
                 const int q = (int)gen_mod((long long)py * u + jy - h0, DH), nq = (int)gen_mod((long long)H * q, DH);
                 const bool folded = kx != 0 && 2 * kx != W;
+                const int D = (int)DH, hp = (H + 1) / 2;           // ky < hp: ky' = ky
+                const float2* xc = X32 + kx;
                 float ar = 0.f, ai = 0.f;
                 int m = 0;
-                for (int ky = 0; ky < H; ++ky) {
-                    int ms = m;
-                    if (2 * ky >= H) { ms -= nq; if (ms < 0) ms += (int)DH; }
-                    float2 e = pl.uH32[ms];
-                    if (ky == nyq_y && folded) e.y = 0.f;
-                    const float2 x = X32[ky * Wh + kx];
+                for (int ky = 0; ky < hp; ++ky) {
+                    const float2 e = pl.uH32[m], x = xc[ky * Wh];
                     ar = __fmaf_rn(x.x, e.x, ar);
                     ar = __fmaf_rn(-x.y, e.y, ar);
                     ai = __fmaf_rn(x.x, e.y, ai);
                     ai = __fmaf_rn(x.y, e.x, ai);
                     m += q;
-                    if (m >= (int)DH) m -= (int)DH;
+                    if (m >= D) m -= D;
                 }
-                V32[o] = make_float2(ar, ai);
+                m -= nq;                                           // ky' = ky - H from here on
+                if (m < 0) m += D;
+                int ky = hp;
+                if (ky == nyq_y) {                                 // the y-Nyquist row (H even)
+                    float2 e = pl.uH32[m];
+                    if (folded) e.y = 0.f;
+                    const float2 x = xc[ky * Wh];
+                    ar = __fmaf_rn(x.x, e.x, ar);
+                    ar = __fmaf_rn(-x.y, e.y, ar);
+                    ai = __fmaf_rn(x.x, e.y, ai);
+                    ai = __fmaf_rn(x.y, e.x, ai);
+                    m += q;
+                    if (m >= D) m -= D;
+                    ++ky;
+                }
+                for (; ky < H; ++ky) {
+                    const float2 e = pl.uH32[m], x = xc[ky * Wh];
+                    ar = __fmaf_rn(x.x, e.x, ar);
+                    ar = __fmaf_rn(-x.y, e.y, ar);
+                    ai = __fmaf_rn(x.x, e.y, ai);
+                    ai = __fmaf_rn(x.y, e.x, ai);
+                    m += q;
+                    if (m >= D) m -= D;
+                }
+                const float gw = folded ? 2.f : 1.f;               // the fold weight, exact
+                V32[o] = make_float2(gw * ar, gw * ai);
             }
             // bound ingredients: sum_kx g A(kx), A(kx) = sum_ky |X32(ky, kx)|_1, and
             // max_jy S(jy), S(jy) = sum_kx g |V32(jy, kx)|_1
@@ -345,10 +373,7 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
             __syncthreads();
             for (int jy = threadIdx.x; jy < M; jy += blockDim.x) {
                 double s = 0.0;
-                for (int kx = 0; kx < Wh; ++kx) {
-                    const double t = fabs((double)V32[jy * Wh + kx].x) + fabs((double)V32[jy * Wh + kx].y);
-                    s += (kx != 0 && 2 * kx != W) ? 2.0 * t : t;
-                }
+                for (int kx = 0; kx < Wh; ++kx) s += fabs((double)V32[jy * Wh + kx].x) + fabs((double)V32[jy * Wh + kx].y);
                 sS = fmax(sS, s);
             }
             const double sumA = gen_block_sum(sA, sv), maxS = gen_block_max(sS, sv);
@@ -362,7 +387,7 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
             float b32 = -INFINITY;
             for (int o = threadIdx.x; o < M * M; o += blockDim.x) {
                 const int jy = o / M, jx = o - jy * M;
-                const float v = pl.sense * gen_cu32(V32 + jy * Wh, pl.uW32, Wh, W, jx, px, u, h0, (int)DW);
+                const float v = pl.sense * gen_cu32(V32 + jy * Wh, pl.uW32, W, jx, px, u, h0, (int)DW);
                 if (keep) G[o] = v;
                 b32 = fmaxf(b32, v);
             }
@@ -371,7 +396,7 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
             __syncthreads();
             for (int o = threadIdx.x; o < M * M; o += blockDim.x) {
                 const int jy = o / M, jx = o - jy * M;
-                const float v = keep ? G[o] : pl.sense * gen_cu32(V32 + jy * Wh, pl.uW32, Wh, W, jx, px, u, h0, (int)DW);
+                const float v = keep ? G[o] : pl.sense * gen_cu32(V32 + jy * Wh, pl.uW32, W, jx, px, u, h0, (int)DW);
                 if ((double)v >= thr) {
                     const int k = atomicAdd(&s_nc, 1);
                     if (k < kcap) s_cand[k] = o;
