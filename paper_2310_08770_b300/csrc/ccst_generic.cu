@@ -31,6 +31,7 @@ namespace ccst {
 constexpr unsigned kRGeneric = 0x80u;   // record flag: tracked by this path
 constexpr unsigned kRNonFinite = 0x10u; // record flag: the surface was not finite
 constexpr int kGenCand = 64;            // most upsampled-grid candidates re-evaluated in double-float
+constexpr int kIntCand = 8;             // most integer-surface candidates re-evaluated in double-float
 
 // Block extremum of (value, index): the largest value, the lowest index on ties.
 __device__ void gen_block_best(double& v, long long& j, double* sv, long long* sj) {
@@ -141,6 +142,9 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
     __shared__ __align__(16) dfc s_wH[256], s_wW[256];                       // e^{-2 pi i m / H}, e^{-2 pi i m / W}
     __shared__ int s_nc, s_cand[kGenCand];                     // upsampled-grid candidates
     __shared__ double s_cval[kGenCand];
+    __shared__ float2 s_wH32[256], s_wW32[256];                // the same twiddles in FP32
+    __shared__ int s_nci, s_candi[kIntCand];                   // integer-surface candidates
+    __shared__ double s_cvali[kIntCand];
     dfc* const X = gb.scratch + (size_t)blockIdx.x * gb.scratch_stride;
     for (;;) {
         __syncthreads();
@@ -240,65 +244,245 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
             stc(X + o, cmul(acc, cconj(ldc(Fb + o))));
         }
         __syncthreads();
-        // Q[y][kx] = sum_ky X[ky][kx] wH^-(ky y); T[n2][y1][kx] first
-        for (int o = threadIdx.x; o < H * Wh; o += blockDim.x) {
-            const int r = o / Wh, kx = o - r * Wh, n2 = r / H1, y1 = r - n2 * H1;
-            const int step = (H2 * y1) % H;
-            dfc acc = zero;
-            int m = 0;
-            for (int n1 = 0; n1 < H1; ++n1) {
-                acc = cadd(acc, cmul(ldc(X + ((H2 * n1 + n2) * Wh + kx)), cconj(ldc(s_wH + m))));
-                m += step;
-                if (m >= H) m -= H;
-            }
-            stc(T + o, acc);
-        }
-        __syncthreads();
-        for (int o = threadIdx.x; o < H * Wh; o += blockDim.x) {
-            const int y = o / Wh, kx = o - y * Wh, y1 = y % H1;
-            dfc acc = zero;
-            int m = 0;
-            for (int n2 = 0; n2 < H2; ++n2) {
-                acc = cadd(acc, cmul(ldc(T + ((n2 * H1 + y1) * Wh + kx)), cconj(ldc(s_wH + m))));
-                m += y;
-                if (m >= H) m -= H;
-            }
-            stc(B + o, acc);
-        }
-        __syncthreads();
-        // c(y, x) = Re sum_{k < W} Q[y][k] wW^-(k x), the row completed by Q[y][W - k] =
-        // conj Q[y][k] (X is the spectrum of a real surface); T[y][n2][x1] first. The
-        // extremum, lowest flat index on ties
-        for (int o = threadIdx.x; o < H * W; o += blockDim.x) {
-            const int y = o / W, r = o - y * W, n2 = r / W1, x1 = r - n2 * W1;
-            const int step = (W2 * x1) % W;
-            dfc acc = zero;
-            int m = 0;
-            for (int n1 = 0; n1 < W1; ++n1) {
-                const int k = W2 * n1 + n2;
-                const dfc qv = k < Wh ? ldc(B + (y * Wh + k)) : cconj(ldc(B + (y * Wh + W - k)));
-                acc = cadd(acc, cmul(qv, cconj(ldc(s_wW + m))));
-                m += step;
-                if (m >= W) m -= W;
-            }
-            stc(T + o, acc);
-        }
-        __syncthreads();
+        // The integer surface. Without the exhaustive flag it is first evaluated in FP32 (X
+        // rounded once, the same two-level inverses) with a rounding bound Bi; the points within
+        // 2 Bi of the FP32 best are then evaluated in double-float by the exhaustive
+        // evaluation's own operations, in its order (at most icap of them; more, none, or the
+        // flag: the exhaustive evaluation over the whole surface).
+        float2* X32 = (float2*)a;                                  // X rounded to FP32, H x Wh
+        double sumA = 0.0;                                         // sum_k |X32(k)|_1, full spectrum
         double best = -INFINITY;
         long long bj = 0x7fffffffffffffffLL;
-        for (int o = threadIdx.x; o < H * W; o += blockDim.x) {
-            const int y = o / W, x = o - y * W, x1 = x % W1;
-            df acc = df{0.f, 0.f};
-            int m = 0;
-            for (int n2 = 0; n2 < W2; ++n2) {
-                acc = df_add_abs(acc, gen_re_mul(ldc(T + (y * W + n2 * W1 + x1)), cconj(ldc(s_wW + m))));
-                m += x;
-                if (m >= W) m -= W;
+        bool int_full = pl.exhaustive != 0;
+        if (!int_full) {
+            for (int o = threadIdx.x; o < H * Wh; o += blockDim.x) {
+                const dfc xv = ldc(X + o);
+                X32[o] = make_float2(xv.re.hi, xv.im.hi);
             }
-            const double v = pl.sense * df_to_double(acc);
-            if (v > best || (v == best && o < bj)) { best = v; bj = o; }
+            for (int m = threadIdx.x; m < H; m += blockDim.x) s_wH32[m] = make_float2(s_wH[m].re.hi, s_wH[m].im.hi);
+            for (int m = threadIdx.x; m < W; m += blockDim.x) s_wW32[m] = make_float2(s_wW[m].re.hi, s_wW[m].im.hi);
+            __syncthreads();
+            double sA = 0.0;
+            for (int kx = threadIdx.x; kx < Wh; kx += blockDim.x) {
+                double s = 0.0;
+                for (int ky = 0; ky < H; ++ky) s += fabs((double)X32[ky * Wh + kx].x) + fabs((double)X32[ky * Wh + kx].y);
+                sA += (kx != 0 && 2 * kx != W) ? 2.0 * s : s;
+            }
+            sumA = gen_block_sum(sA, sv);
+            float2* T32 = (float2*)T;                              // column level H x Wh, then row level H x W
+            float2* Q32 = (float2*)B;                              // H x Wh
+            // columns: T32[n2][y1][kx] = sum_n1 X32[H2 n1 + n2][kx] wH^-(H2 n1 y1), then Q32
+            for (int o = threadIdx.x; o < H * Wh; o += blockDim.x) {
+                const int r = o / Wh, kx = o - r * Wh, n2 = r / H1, y1 = r - n2 * H1;
+                const int step = (H2 * y1) % H;
+                float ar = 0.f, ai = 0.f;
+                int m = 0;
+                for (int n1 = 0; n1 < H1; ++n1) {
+                    const float2 x = X32[(H2 * n1 + n2) * Wh + kx], w = s_wH32[m];
+                    ar = __fmaf_rn(x.x, w.x, ar);
+                    ar = __fmaf_rn(x.y, w.y, ar);
+                    ai = __fmaf_rn(x.y, w.x, ai);
+                    ai = __fmaf_rn(-x.x, w.y, ai);
+                    m += step;
+                    if (m >= H) m -= H;
+                }
+                T32[o] = make_float2(ar, ai);
+            }
+            __syncthreads();
+            for (int o = threadIdx.x; o < H * Wh; o += blockDim.x) {
+                const int y = o / Wh, kx = o - y * Wh, y1 = y % H1;
+                float ar = 0.f, ai = 0.f;
+                int m = 0;
+                for (int n2 = 0; n2 < H2; ++n2) {
+                    const float2 t = T32[(n2 * H1 + y1) * Wh + kx], w = s_wH32[m];
+                    ar = __fmaf_rn(t.x, w.x, ar);
+                    ar = __fmaf_rn(t.y, w.y, ar);
+                    ai = __fmaf_rn(t.y, w.x, ai);
+                    ai = __fmaf_rn(-t.x, w.y, ai);
+                    m += y;
+                    if (m >= H) m -= H;
+                }
+                Q32[o] = make_float2(ar, ai);
+            }
+            __syncthreads();
+            // rows, Hermitian-completed: T32[y][n2][x1] = sum_n1 Q(y, W2 n1 + n2) wW^-(W2 n1 x1)
+            for (int o = threadIdx.x; o < H * W; o += blockDim.x) {
+                const int y = o / W, r = o - y * W, n2 = r / W1, x1 = r - n2 * W1;
+                const int step = (W2 * x1) % W;
+                float ar = 0.f, ai = 0.f;
+                int m = 0;
+                for (int n1 = 0; n1 < W1; ++n1) {
+                    const int k = W2 * n1 + n2;
+                    float2 q = k < Wh ? Q32[y * Wh + k] : Q32[y * Wh + W - k];
+                    if (k >= Wh) q.y = -q.y;
+                    const float2 w = s_wW32[m];
+                    ar = __fmaf_rn(q.x, w.x, ar);
+                    ar = __fmaf_rn(q.y, w.y, ar);
+                    ai = __fmaf_rn(q.y, w.x, ai);
+                    ai = __fmaf_rn(-q.x, w.y, ai);
+                    m += step;
+                    if (m >= W) m -= W;
+                }
+                T32[o] = make_float2(ar, ai);
+            }
+            __syncthreads();
+            // c32(y, x) = Re sum_n2 T32[y][n2][x mod W1] wW^-(n2 x), one fixed FMA chain (both passes)
+            auto c32 = [&](int o) -> float {
+                const int y = o / W, x = o - y * W, x1 = x % W1;
+                float acc = 0.f;
+                int m = 0;
+                for (int n2 = 0; n2 < W2; ++n2) {
+                    const float2 t = T32[y * W + n2 * W1 + x1], w = s_wW32[m];
+                    acc = __fmaf_rn(t.x, w.x, acc);
+                    acc = __fmaf_rn(t.y, w.y, acc);
+                    m += x;
+                    if (m >= W) m -= W;
+                }
+                return pl.sense * acc;
+            };
+            float b32 = -INFINITY;
+            for (int o = threadIdx.x; o < H * W; o += blockDim.x) b32 = fmaxf(b32, c32(o));
+            // |c32 - c| <= Bi: rounding of X and the tables, gamma_n per FMA chain, sqrt(2) per
+            // complex product in the 1-norm, through both levels of both inverses
+            const double Bi = 1.1 * (8.0 * (W1 + W2) + 16.0 + 9.0 * (H1 + H2) + 22.0) * 0x1p-24 * sumA + 0x1p-30 * sumA;
+            const double thr_i = gen_block_max((double)b32, sv) - 2.0 * Bi;
+            if (threadIdx.x == 0) s_nci = 0;
+            __syncthreads();
+            const int icap_raw = (H * W) / (H2 * Wh + W2);
+            const int icap = icap_raw < 1 ? 1 : (icap_raw > kIntCand ? kIntCand : icap_raw);
+            for (int o = threadIdx.x; o < H * W; o += blockDim.x)
+                if ((double)c32(o) >= thr_i) {
+                    const int k = atomicAdd(&s_nci, 1);
+                    if (k < icap) s_candi[k] = o;
+                }
+            __syncthreads();
+            const int nci = s_nci;
+            if (nci == 0 || nci > icap) {
+                int_full = true;
+            } else {
+                dfc* P1 = T;                                       // nci x H2 x Wh: column level 1
+                dfc* P3 = T + (size_t)nci * H2 * Wh;               // nci x W2: row level 1
+                dfc* P2 = B;                                       // nci x Wh: the candidate's row of Q
+                for (int t = threadIdx.x; t < nci * H2 * Wh; t += blockDim.x) {
+                    const int cidx = t / (H2 * Wh), r = t - cidx * H2 * Wh, n2 = r / Wh, kx = r - n2 * Wh;
+                    const int y1 = (s_candi[cidx] / W) % H1, step = (H2 * y1) % H;
+                    dfc acc = zero;
+                    int m = 0;
+                    for (int n1 = 0; n1 < H1; ++n1) {
+                        acc = cadd(acc, cmul(ldc(X + ((H2 * n1 + n2) * Wh + kx)), cconj(ldc(s_wH + m))));
+                        m += step;
+                        if (m >= H) m -= H;
+                    }
+                    stc(P1 + t, acc);
+                }
+                __syncthreads();
+                for (int t = threadIdx.x; t < nci * Wh; t += blockDim.x) {
+                    const int cidx = t / Wh, kx = t - cidx * Wh, y = s_candi[cidx] / W;
+                    dfc acc = zero;
+                    int m = 0;
+                    for (int n2 = 0; n2 < H2; ++n2) {
+                        acc = cadd(acc, cmul(ldc(P1 + ((size_t)(cidx * H2 + n2) * Wh + kx)), cconj(ldc(s_wH + m))));
+                        m += y;
+                        if (m >= H) m -= H;
+                    }
+                    stc(P2 + t, acc);
+                }
+                __syncthreads();
+                for (int t = threadIdx.x; t < nci * W2; t += blockDim.x) {
+                    const int cidx = t / W2, n2 = t - cidx * W2, x1 = (s_candi[cidx] % W) % W1;
+                    const int step = (W2 * x1) % W;
+                    const dfc* q = P2 + (size_t)cidx * Wh;
+                    dfc acc = zero;
+                    int m = 0;
+                    for (int n1 = 0; n1 < W1; ++n1) {
+                        const int k = W2 * n1 + n2;
+                        const dfc qv = k < Wh ? ldc(q + k) : cconj(ldc(q + (W - k)));
+                        acc = cadd(acc, cmul(qv, cconj(ldc(s_wW + m))));
+                        m += step;
+                        if (m >= W) m -= W;
+                    }
+                    stc(P3 + t, acc);
+                }
+                __syncthreads();
+                if (threadIdx.x < nci) {
+                    const int x = s_candi[threadIdx.x] % W;
+                    df acc = df{0.f, 0.f};
+                    int m = 0;
+                    for (int n2 = 0; n2 < W2; ++n2) {
+                        acc = df_add_abs(acc, gen_re_mul(ldc(P3 + (size_t)threadIdx.x * W2 + n2), cconj(ldc(s_wW + m))));
+                        m += x;
+                        if (m >= W) m -= W;
+                    }
+                    s_cvali[threadIdx.x] = pl.sense * df_to_double(acc);
+                }
+                __syncthreads();
+                for (int k = 0; k < nci; ++k) {
+                    const double v = s_cvali[k];
+                    const long long j = s_candi[k];
+                    if (v > best || (v == best && j < bj)) { best = v; bj = j; }
+                }
+                __syncthreads();
+            }
         }
-        gen_block_best(best, bj, sv, sj);
+        if (int_full) {
+            // Q[y][kx] = sum_ky X[ky][kx] wH^-(ky y); T[n2][y1][kx] first
+            for (int o = threadIdx.x; o < H * Wh; o += blockDim.x) {
+                const int r = o / Wh, kx = o - r * Wh, n2 = r / H1, y1 = r - n2 * H1;
+                const int step = (H2 * y1) % H;
+                dfc acc = zero;
+                int m = 0;
+                for (int n1 = 0; n1 < H1; ++n1) {
+                    acc = cadd(acc, cmul(ldc(X + ((H2 * n1 + n2) * Wh + kx)), cconj(ldc(s_wH + m))));
+                    m += step;
+                    if (m >= H) m -= H;
+                }
+                stc(T + o, acc);
+            }
+            __syncthreads();
+            for (int o = threadIdx.x; o < H * Wh; o += blockDim.x) {
+                const int y = o / Wh, kx = o - y * Wh, y1 = y % H1;
+                dfc acc = zero;
+                int m = 0;
+                for (int n2 = 0; n2 < H2; ++n2) {
+                    acc = cadd(acc, cmul(ldc(T + ((n2 * H1 + y1) * Wh + kx)), cconj(ldc(s_wH + m))));
+                    m += y;
+                    if (m >= H) m -= H;
+                }
+                stc(B + o, acc);
+            }
+            __syncthreads();
+            // c(y, x) = Re sum_{k < W} Q[y][k] wW^-(k x), the row completed by Q[y][W - k] =
+            // conj Q[y][k] (X is the spectrum of a real surface); T[y][n2][x1] first. The
+            // extremum, lowest flat index on ties
+            for (int o = threadIdx.x; o < H * W; o += blockDim.x) {
+                const int y = o / W, r = o - y * W, n2 = r / W1, x1 = r - n2 * W1;
+                const int step = (W2 * x1) % W;
+                dfc acc = zero;
+                int m = 0;
+                for (int n1 = 0; n1 < W1; ++n1) {
+                    const int k = W2 * n1 + n2;
+                    const dfc qv = k < Wh ? ldc(B + (y * Wh + k)) : cconj(ldc(B + (y * Wh + W - k)));
+                    acc = cadd(acc, cmul(qv, cconj(ldc(s_wW + m))));
+                    m += step;
+                    if (m >= W) m -= W;
+                }
+                stc(T + o, acc);
+            }
+            __syncthreads();
+            for (int o = threadIdx.x; o < H * W; o += blockDim.x) {
+                const int y = o / W, x = o - y * W, x1 = x % W1;
+                df acc = df{0.f, 0.f};
+                int m = 0;
+                for (int n2 = 0; n2 < W2; ++n2) {
+                    acc = df_add_abs(acc, gen_re_mul(ldc(T + (y * W + n2 * W1 + x1)), cconj(ldc(s_wW + m))));
+                    m += x;
+                    if (m >= W) m -= W;
+                }
+                const double v = pl.sense * df_to_double(acc);
+                if (v > best || (v == best && o < bj)) { best = v; bj = o; }
+            }
+            gen_block_best(best, bj, sv, sj);
+        }
         const int iy = (int)(bj / W), ix = (int)(bj % W);
         const int py = iy > H / 2 ? iy - H : iy;
         const int px = ix > W / 2 ? ix - W : ix;
@@ -310,13 +494,7 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
         const int kcap = kGenCand < 2 * (H > M ? H : M) ? kGenCand : 2 * (H > M ? H : M);
         bool full = pl.exhaustive != 0;
         if (!full) {
-            float2* X32 = (float2*)a;                              // X rounded to FP32, H x Wh
-            float2* V32 = (float2*)B;                              // M x Wh
-            for (int o = threadIdx.x; o < H * Wh; o += blockDim.x) {
-                const dfc xv = ldc(X + o);
-                X32[o] = make_float2(xv.re.hi, xv.im.hi);
-            }
-            __syncthreads();
+            float2* V32 = (float2*)B;                              // M x Wh (X32, sumA: from the integer stage)
             // V32[jy][kx] = sum_ky X32[ky][kx] e32^{2 pi i ky' q / (uH)}
             for (int o = threadIdx.x; o < M * Wh; o += blockDim.x) {
                 const int jy = o / Wh, kx = o - jy * Wh;
@@ -362,21 +540,16 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
                 const float gw = folded ? 2.f : 1.f;               // the fold weight, exact
                 V32[o] = make_float2(gw * ar, gw * ai);
             }
-            // bound ingredients: sum_kx g A(kx), A(kx) = sum_ky |X32(ky, kx)|_1, and
-            // max_jy S(jy), S(jy) = sum_kx g |V32(jy, kx)|_1
-            double sA = 0.0, sS = 0.0;
-            for (int kx = threadIdx.x; kx < Wh; kx += blockDim.x) {
-                double s = 0.0;
-                for (int ky = 0; ky < H; ++ky) s += fabs((double)X32[ky * Wh + kx].x) + fabs((double)X32[ky * Wh + kx].y);
-                sA += (kx != 0 && 2 * kx != W) ? 2.0 * s : s;
-            }
+            // bound ingredients: sumA (above) and max_jy S(jy), S(jy) = sum_kx |V32(jy, kx)|_1
+            // (V32 carries the fold weight)
+            double sS = 0.0;
             __syncthreads();
             for (int jy = threadIdx.x; jy < M; jy += blockDim.x) {
                 double s = 0.0;
                 for (int kx = 0; kx < Wh; ++kx) s += fabs((double)V32[jy * Wh + kx].x) + fabs((double)V32[jy * Wh + kx].y);
                 sS = fmax(sS, s);
             }
-            const double sumA = gen_block_sum(sA, sv), maxS = gen_block_max(sS, sv);
+            const double maxS = gen_block_max(sS, sv);
             const double u32 = 0x1p-24;
             const double Bnd = 1.01 * ((2.0 * Wh + 3.0) * u32 * maxS + (4.0 * H + 6.0) * u32 * sumA) +
                                0x1p-30 * (maxS + sumA);
