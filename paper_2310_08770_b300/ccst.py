@@ -491,6 +491,16 @@ class Tracker:
         ccst_sync(self.ctx)
         return decode(out)
 
+    def track_tensor(self, frames):
+        """Device-side form: a float32 CUDA tensor (n, 3) of (dx, dy, peak), a view of the
+        24-byte records (no host copy), valid once the context's stream has reached it."""
+        n = frames.shape[0]
+        out = self.empty_results(n)
+        for s in range(0, n, self.max_batch):
+            e = min(n, s + self.max_batch)
+            ccst_track(self.ctx, frames[s:e], e - s, 0, out[s:e])
+        return out.view(self._torch.float32)[:, :3]
+
     def rt_begin(self, frame0, a0: float, b1: float | None = None) -> None:
         """Start the real-time reference (Sec. III B) from frame0, a CUDA tensor (H, W)."""
         ccst_rt_begin(self.ctx, frame0, 0, a0, 1.0 - a0 if b1 is None else b1)

@@ -112,3 +112,18 @@ def test_server_with_float32_frames(torch):
         C.ccst_server_destroy(srv)
         t.close()
     assert all(g.tobytes() == w.tobytes() for g, w in zip(got, want))
+
+
+def test_track_tensor_is_a_view_of_the_records(torch):
+    fr = frames_of(300, 32, seed=6, u16=True)
+    ref = synth.gaussian_spot(32, 32, 16, 16, 2.5, 900.0, 15.0).astype(np.float32)
+    t = C.Tracker(ref, upsample=100, in_dtype="u16", max_batch=128)
+    d = dev(torch, fr)
+    rec = t.track(d)
+    ten = t.track_tensor(d)
+    torch.cuda.synchronize()
+    t.close()
+    assert ten.shape == (300, 3) and ten.dtype == torch.float32 and ten.is_cuda
+    got = ten.cpu().numpy()
+    assert np.array_equal(got[:, 0], rec["dx"]) and np.array_equal(got[:, 1], rec["dy"])
+    assert np.array_equal(got[:, 2], rec["peak"])
