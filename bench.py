@@ -741,7 +741,7 @@ def run_ours(args):
     if world == 1 and not args.no_serving:
         line["serving"] = serving_leg(C, torch, note=" (power-of-two stand-ins for 64, 96, 128, 192, 256, 64, "
                                                      "128, 256)")
-        # the survey's sides: 96, 192 and 256 run on the double-float general-size kernel
+        # the workload's own sides: 96, 192 and 256 run on the double-float general-size kernel
         line["serving"]["true_sides"] = serving_leg(C, torch, SERVE_TRUE_SIDES, SERVE_TRUE_SECONDS, 2048,
                                                     " (96, 192, 256 on the general-size kernel)")
     rois_extra = None
