@@ -586,6 +586,36 @@ def serving_leg(C, torch, sides=SERVE_SIDES, seconds=SERVE_SECONDS, slots=4096, 
             "latency": "host clock, submit call to the worker seeing the batch's completion event"}
 
 
+PLAIN_FRAMES = 1024
+
+
+def plain_leg(C, torch, s, frames_dev, stream):
+    """The plain form: one direct launch per frame (no batching, no graph) on one stream, for
+    the first PLAIN_FRAMES frames; each frame's latency is its own launch (CUDA events)."""
+    t = C.Tracker(s.ref, upsample=U, method="ccu", in_dtype="u16", max_batch=1, stream=stream)
+    out = t.empty_results(PLAIN_FRAMES)
+    n = min(PLAIN_FRAMES, frames_dev.shape[0])
+    with torch.cuda.stream(stream):
+        for i in range(8):
+            C.ccst_track(t.ctx, frames_dev[i:i + 1], 1, 0, out[i:i + 1])
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i in range(n):
+            ev[i][0].record(stream)
+            C.ccst_track(t.ctx, frames_dev[i:i + 1], 1, 0, out[i:i + 1])
+            ev[i][1].record(stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+    lat = np.array([e0.elapsed_time(e1) * 1e3 for e0, e1 in ev])
+    total_ms = a.elapsed_time(b)
+    t.close()
+    return {"workload": f"frames 0..{n} of the stream, one ccst_track launch per frame (no graph), one stream",
+            "value": n / (total_ms / 1e3), "unit": "frames/s", "p50_us": float(np.percentile(lat, 50)),
+            "p99_us": float(np.percentile(lat, 99)), "gpu_launches": n}
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -733,6 +763,8 @@ def run_ours(args):
                   "overflow": int(np.sum((flags & C.R_OVERFLOW) != 0))},
     }
     rt_line = rt_res = None
+    if world == 1:
+        line["plain_per_frame_launch"] = plain_leg(C, torch, s, frames_dev, stream)
     if world == 1 and not args.no_realtime:         # the extra legs are single-GPU measurements
         rt_line, rt_res = realtime_leg(C, torch, s, stream, args.rt_frames)
         line["realtime"] = rt_line
