@@ -1,10 +1,12 @@
 // ccst_generic.cu -- the tracking path of Secs. II-III for every frame shape the
 // power-of-two kernel does not take: H and W from 8 to 256, any factors (48, 96, 192, 256,
-// 256 x 128, ...). Direct DFTs over the Hermitian half of the real-input spectrum and the
-// full-grid upsampled sum, all in double-float on the FP32 pipes. Slower than the
-// power-of-two kernel, but general, and precise enough (about 2^-46 per term) that no
-// near-tie guard is needed: its decisions are those of an FP64 evaluation except on
-// genuine ties.
+// 256 x 128, ...). Two-level DFTs over the Hermitian half of the real-input spectrum and
+// the full-grid upsampled sum, in double-float on the FP32 pipes (about 2^-46 per term):
+// its decisions are those of an FP64 evaluation except on genuine ties. The integer
+// surface and the upsampled grid are first evaluated in FP32 with a rounding bound, and
+// only the points the bound cannot rule out are evaluated in double-float, by the same
+// operations as the exhaustive double-float evaluation (CCST_FLAG_EXHAUSTIVE), so the
+// records are the ones that evaluation gives.
 //
 // Per frame (one CTA of 512 threads; a CTA takes frames from a counter), Wh = W/2 + 1,
 // g(kx) = 1 at kx = 0 and kx = W/2, 2 elsewhere (the fold of the Hermitian pair):
