@@ -32,7 +32,9 @@ namespace ccst {
 
 constexpr unsigned kRGeneric = 0x80u;   // record flag: tracked by this path
 constexpr unsigned kRNonFinite = 0x10u; // record flag: the surface was not finite
-constexpr int kGenCand = 64;            // most upsampled-grid candidates re-evaluated in double-float
+constexpr int kGridCap = 8192;          // most upsampled-grid candidates re-evaluated in double-float
+constexpr int kRowCap = 256;            // most distinct grid rows among them
+constexpr int kRowWords = 769;          // row bitmap words: M = ceil(1.5 u) <= 24577 for u <= 16384
 constexpr int kIntCand = 8;             // most integer-surface candidates re-evaluated in double-float
 
 // Block extremum of (value, index): the largest value, the lowest index on ties.
@@ -142,8 +144,9 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
     __shared__ long long sj[32];
     __shared__ long long s_item;
     __shared__ __align__(16) dfc s_wH[256], s_wW[256];                       // e^{-2 pi i m / H}, e^{-2 pi i m / W}
-    __shared__ int s_nc, s_cand[kGenCand];                     // upsampled-grid candidates
-    __shared__ double s_cval[kGenCand];
+    __shared__ int s_nc, s_nrows;                              // upsampled-grid candidates and their rows
+    __shared__ unsigned s_rowbits[kRowWords];
+    __shared__ int s_rowpre[kRowWords], s_rowof[kRowCap];
     __shared__ float2 s_wH32[256], s_wW32[256];                // the same twiddles in FP32
     __shared__ int s_nci, s_candi[kIntCand];                   // integer-surface candidates
     __shared__ double s_cvali[kIntCand];
@@ -493,7 +496,6 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
         // evaluated in double-float, by the same operations and order as the exhaustive
         // evaluation below (so the record is the one that evaluation gives). Too many
         // candidates, or the exhaustive flag: the whole grid in double-float.
-        const int kcap = kGenCand < 2 * (H > M ? H : M) ? kGenCand : 2 * (H > M ? H : M);
         bool full = pl.exhaustive != 0;
         if (!full) {
             float2* V32 = (float2*)B;                              // M x Wh (X32, sumA: from the integer stage)
@@ -567,6 +569,9 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
                 b32 = fmaxf(b32, v);
             }
             const double thr = gen_block_max((double)b32, sv) - 2.0 * Bnd;
+            // pass 2: the candidates, listed in the T region (free by now: ints, gcap of them)
+            int* cand = (int*)T;
+            const int gcap = kGridCap < 4 * H * W ? kGridCap : 4 * H * W;
             if (threadIdx.x == 0) s_nc = 0;
             __syncthreads();
             for (int o = threadIdx.x; o < M * M; o += blockDim.x) {
@@ -574,55 +579,91 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
                 const float v = keep ? G[o] : pl.sense * gen_cu32(V32 + jy * Wh, pl.uW32, W, jx, px, u, h0, (int)DW);
                 if ((double)v >= thr) {
                     const int k = atomicAdd(&s_nc, 1);
-                    if (k < kcap) s_cand[k] = o;
+                    if (k < gcap) cand[k] = o;
                 }
             }
             __syncthreads();
             const int nc = s_nc;
-            if (nc == 0 || nc > kcap) {                            // none: a non-finite grid
+            const int nwords = (M + 31) >> 5;
+            if (nc == 0 || nc > gcap || nwords > kRowWords) {      // none: a non-finite grid
                 full = true;
             } else {
-                // candidate c, column kx: g(kx) Re V(jy_c, kx) e^{2 pi i kx' q / (uW)} in double-float
-                df* P = (df*)B;                                    // nc x Wh (V32 is no longer read)
+                // the candidates' rows: a bitmap over jy, then slot(jy) = rows below jy (in
+                // order, so the slots do not depend on the order the candidates were listed)
+                for (int w = threadIdx.x; w < nwords; w += blockDim.x) s_rowbits[w] = 0u;
                 __syncthreads();
-                for (int t = threadIdx.x; t < nc * Wh; t += blockDim.x) {
-                    const int cidx = t / Wh, kx = t - cidx * Wh;
-                    const int o = s_cand[cidx], jy = o / M, jx = o - jy * M;
-                    const long long q = gen_mod((long long)py * u + jy - h0, DH), nq = gen_mod((long long)H * q, DH);
-                    const bool folded = kx != 0 && 2 * kx != W;
-                    dfc acc = zero;
-                    long long m = 0;
-                    for (int ky = 0; ky < H; ++ky) {
-                        long long ms = m;
-                        if (2 * ky >= H) { ms -= nq; if (ms < 0) ms += DH; }
-                        dfc e = ldc(pl.uH + ms);
-                        if (ky == nyq_y && folded) e.im = df{0.f, 0.f};
-                        acc = cadd(acc, cmul(ldc(X + (ky * Wh + kx)), e));
-                        m += q;
-                        if (m >= DH) m -= DH;
+                for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+                    const int jy = cand[k] / M;
+                    atomicOr(&s_rowbits[jy >> 5], 1u << (jy & 31));
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    int sum = 0;
+                    for (int w = 0; w < nwords; ++w) {
+                        s_rowpre[w] = sum;
+                        sum += __popc(s_rowbits[w]);
                     }
-                    const long long qx = gen_mod((long long)px * u + jx - h0, DW);
-                    long long mx = gen_mod((long long)kx * qx, DW);
-                    if (2 * kx >= W) { mx -= gen_mod((long long)W * qx, DW); if (mx < 0) mx += DW; }
-                    df term = gen_re_mul(acc, ldc(pl.uW + mx));
-                    if (folded) term = df_scale(term, 2.f);
-                    std_(P + t, term);
+                    s_nrows = sum;
                 }
                 __syncthreads();
-                if (threadIdx.x < nc) {
-                    df acc = df{0.f, 0.f};
-                    for (int kx = 0; kx < Wh; ++kx) acc = df_add_abs(acc, ldd(P + threadIdx.x * Wh + kx));
-                    s_cval[threadIdx.x] = pl.sense * df_to_double(acc);
+                const int nrows = s_nrows;
+                if (nrows > kRowCap) {
+                    full = true;
+                } else {
+                    for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
+                        unsigned bits = s_rowbits[w];
+                        int slot = s_rowpre[w];
+                        while (bits) {
+                            s_rowof[slot++] = 32 * w + __ffs(bits) - 1;
+                            bits &= bits - 1;
+                        }
+                    }
+                    __syncthreads();
+                    // V(jy, kx) in double-float for the candidates' rows, by the exhaustive
+                    // evaluation's operations (V32 is no longer read)
+                    for (int t = threadIdx.x; t < nrows * Wh; t += blockDim.x) {
+                        const int slot = t / Wh, kx = t - slot * Wh, jy = s_rowof[slot];
+                        const long long q = gen_mod((long long)py * u + jy - h0, DH), nq = gen_mod((long long)H * q, DH);
+                        const bool folded = kx != 0 && 2 * kx != W;
+                        dfc acc = zero;
+                        long long m = 0;
+                        for (int ky = 0; ky < H; ++ky) {
+                            long long ms = m;
+                            if (2 * ky >= H) { ms -= nq; if (ms < 0) ms += DH; }
+                            dfc e = ldc(pl.uH + ms);
+                            if (ky == nyq_y && folded) e.im = df{0.f, 0.f};
+                            acc = cadd(acc, cmul(ldc(X + (ky * Wh + kx)), e));
+                            m += q;
+                            if (m >= DH) m -= DH;
+                        }
+                        stc(B + t, acc);
+                    }
+                    __syncthreads();
+                    // each candidate: the exhaustive evaluation's sum over kx of its row
+                    best = -INFINITY;
+                    bj = 0x7fffffffffffffffLL;
+                    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+                        const int o = cand[k], jy = o / M, jx = o - jy * M;
+                        const int w = jy >> 5;
+                        const int slot = s_rowpre[w] + __popc(s_rowbits[w] & ((1u << (jy & 31)) - 1u));
+                        const long long q = gen_mod((long long)px * u + jx - h0, DW), nq = gen_mod((long long)W * q, DW);
+                        const dfc* vrow = B + (size_t)slot * Wh;
+                        df acc = df{0.f, 0.f};
+                        long long m = 0;
+                        for (int kx = 0; kx < Wh; ++kx) {
+                            long long ms = m;
+                            if (2 * kx >= W) { ms -= nq; if (ms < 0) ms += DW; }
+                            df t = gen_re_mul(ldc(vrow + kx), ldc(pl.uW + ms));
+                            if (kx != 0 && 2 * kx != W) t = df_scale(t, 2.f);
+                            acc = df_add_abs(acc, t);
+                            m += q;
+                            if (m >= DW) m -= DW;
+                        }
+                        const double v = pl.sense * df_to_double(acc);
+                        if (v > best || (v == best && o < bj)) { best = v; bj = o; }
+                    }
+                    gen_block_best(best, bj, sv, sj);
                 }
-                __syncthreads();
-                best = -INFINITY;
-                bj = 0x7fffffffffffffffLL;
-                for (int k = 0; k < nc; ++k) {
-                    const double v = s_cval[k];
-                    const long long j = s_cand[k];
-                    if (v > best || (v == best && j < bj)) { best = v; bj = j; }
-                }
-                __syncthreads();
             }
         }
         if (full) {
