@@ -1815,17 +1815,22 @@ static int gen_plan(ccst_ctx* c, int H, int W, int* gcls) {
     pl.W2 = W / pl.W1;
     dfc* tab = nullptr;
     const size_t ntab = (size_t)(H + W + DH + DW);
-    CK(c, cudaMalloc(&tab, ntab * sizeof(dfc) + (size_t)(DH + DW) * sizeof(float2)));
+    int M = pl.M, h0 = pl.h0;
+    const size_t ngrid = (size_t)(H + W / 2 + 1) * M;
+    CK(c, cudaMalloc(&tab, ntab * sizeof(dfc) + ngrid * sizeof(float2)));
     gp.mem.push_back(tab);
     pl.wH = tab;
     pl.wW = tab + H;
     pl.uH = tab + H + W;
     pl.uW = tab + H + W + DH;
-    float2* tab32 = (float2*)(tab + ntab);
-    pl.uH32 = tab32;
-    pl.uW32 = tab32 + DH;
-    void* a2[] = {&H, &W, &u, &tab, &tab32};
-    const cudaError_t e = cudaLaunchKernel(gen_init_tables_ptr(), dim3(64), dim3(256), a2, 0, c->stream);
+    float2* EY = (float2*)(tab + ntab);
+    float2* EX = EY + (size_t)H * M;
+    pl.EY = EY;
+    pl.EX = EX;
+    void* a2[] = {&H, &W, &u, &tab};
+    void* a3[] = {&H, &W, &u, &M, &h0, &EY, &EX};
+    cudaError_t e = cudaLaunchKernel(gen_init_tables_ptr(), dim3(64), dim3(256), a2, 0, c->stream);
+    if (e == cudaSuccess) e = cudaLaunchKernel(gen_init_grid_tables_ptr(), dim3(128), dim3(256), a3, 0, c->stream);
     if (e != cudaSuccess) {
         cudaFree(tab);
         return fail(c, CCST_E_CUDA, std::string("gen_init_tables: ") + cudaGetErrorString(e));

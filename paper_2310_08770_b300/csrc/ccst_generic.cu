@@ -111,28 +111,13 @@ __device__ double gen_block_max(double v, double* sv) {
     return s;
 }
 
-// One point of the upsampled grid in FP32: sum_kx Re V32[kx] e^{2 pi i kx' q / (uW)},
-// q = px u + jx - h0, V32 already carrying the fold weight g(kx). Angle indices as in the
-// double-float evaluation, in 32 bits (uW <= 2^22); the x-Nyquist column (W even, the last
-// one, kx' = -W/2) is taken after the loop.
-__device__ __forceinline__ float gen_cu32(const float2* V, const float2* tab, int W, int jx, int px, int u, int h0,
-                                          int DW) {
-    int q = (px * u + jx - h0) % DW;
-    if (q < 0) q += DW;
-    const int kpos = (W + 1) / 2;                           // kx < kpos: kx' = kx
+// One point of the upsampled grid in FP32: sum_kx Re V32[kx] EX[kx][jx], V32 carrying the
+// fold weight g(kx) and the x-phase of the integer shift; ex = EX + jx, rows M apart (the
+// lanes of a warp read consecutive jx: coalesced).
+__device__ __forceinline__ float gen_cu32(const float2* V, const float2* ex, int Wh, int M) {
     float acc = 0.f;
-    int m = 0;
-    for (int kx = 0; kx < kpos; ++kx) {
-        const float2 v = V[kx], e = tab[m];
-        acc = __fmaf_rn(v.x, e.x, acc);
-        acc = __fmaf_rn(-v.y, e.y, acc);
-        m += q;
-        if (m >= DW) m -= DW;
-    }
-    if ((W & 1) == 0) {                                     // here m = (W/2) q mod uW
-        int ms = m - (int)(((long long)W * q) % DW);
-        if (ms < 0) ms += DW;
-        const float2 v = V[kpos], e = tab[ms];
+    for (int kx = 0; kx < Wh; ++kx) {
+        const float2 v = V[kx], e = ex[(size_t)kx * M];
         acc = __fmaf_rn(v.x, e.x, acc);
         acc = __fmaf_rn(-v.y, e.y, acc);
     }
@@ -499,47 +484,51 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
         bool full = pl.exhaustive != 0;
         if (!full) {
             float2* V32 = (float2*)B;                              // M x Wh (X32, sumA: from the integer stage)
-            // V32[jy][kx] = sum_ky X32[ky][kx] e32^{2 pi i ky' q / (uH)}
+            // X32 <- X32 e^{2 pi i (ky py / H + kx px / W)}: the integer shift's phase (periodic in
+            // k, so unsigned k serves; real (+-1) on the Nyquist row and column), leaving the
+            // frame-independent tables EY, EX for the grid offsets
+            {
+                const int pyy = ((py % H) + H) % H, pxx = ((px % W) + W) % W;
+                for (int o = threadIdx.x; o < H * Wh; o += blockDim.x) {
+                    const int ky = o / Wh, kx = o - ky * Wh;
+                    const float2 a = s_wH32[(int)(((long long)ky * pyy) % H)], b = s_wW32[(int)(((long long)kx * pxx) % W)];
+                    const float2 ph = make_float2(a.x * b.x - a.y * b.y, -(a.x * b.y + a.y * b.x));   // conj(a b)
+                    const float2 x = X32[o];
+                    X32[o] = make_float2(x.x * ph.x - x.y * ph.y, x.x * ph.y + x.y * ph.x);
+                }
+                __syncthreads();
+            }
+            // V32[jy][kx] = g(kx) sum_ky X32[ky][kx] EY[ky][jy]; in the weight-2 columns the
+            // y-Nyquist row (H even) takes the real part of EY only
             for (int o = threadIdx.x; o < M * Wh; o += blockDim.x) {
                 const int jy = o / Wh, kx = o - jy * Wh;
-                const int q = (int)gen_mod((long long)py * u + jy - h0, DH), nq = (int)gen_mod((long long)H * q, DH);
                 const bool folded = kx != 0 && 2 * kx != W;
-                const int D = (int)DH, hp = (H + 1) / 2;           // ky < hp: ky' = ky
                 const float2* xc = X32 + kx;
+                const float2* ey = pl.EY + jy;
+                const int k1 = nyq_y >= 0 ? nyq_y : H;                 // rows before the Nyquist row
                 float ar = 0.f, ai = 0.f;
-                int m = 0;
-                for (int ky = 0; ky < hp; ++ky) {
-                    const float2 e = pl.uH32[m], x = xc[ky * Wh];
+                for (int ky = 0; ky < k1; ++ky) {
+                    const float2 e = ey[(size_t)ky * M], x = xc[ky * Wh];
                     ar = __fmaf_rn(x.x, e.x, ar);
                     ar = __fmaf_rn(-x.y, e.y, ar);
                     ai = __fmaf_rn(x.x, e.y, ai);
                     ai = __fmaf_rn(x.y, e.x, ai);
-                    m += q;
-                    if (m >= D) m -= D;
                 }
-                m -= nq;                                           // ky' = ky - H from here on
-                if (m < 0) m += D;
-                int ky = hp;
-                if (ky == nyq_y) {                                 // the y-Nyquist row (H even)
-                    float2 e = pl.uH32[m];
+                if (nyq_y >= 0) {
+                    float2 e = ey[(size_t)nyq_y * M];
                     if (folded) e.y = 0.f;
-                    const float2 x = xc[ky * Wh];
+                    const float2 x = xc[nyq_y * Wh];
                     ar = __fmaf_rn(x.x, e.x, ar);
                     ar = __fmaf_rn(-x.y, e.y, ar);
                     ai = __fmaf_rn(x.x, e.y, ai);
                     ai = __fmaf_rn(x.y, e.x, ai);
-                    m += q;
-                    if (m >= D) m -= D;
-                    ++ky;
-                }
-                for (; ky < H; ++ky) {
-                    const float2 e = pl.uH32[m], x = xc[ky * Wh];
-                    ar = __fmaf_rn(x.x, e.x, ar);
-                    ar = __fmaf_rn(-x.y, e.y, ar);
-                    ai = __fmaf_rn(x.x, e.y, ai);
-                    ai = __fmaf_rn(x.y, e.x, ai);
-                    m += q;
-                    if (m >= D) m -= D;
+                    for (int ky = nyq_y + 1; ky < H; ++ky) {
+                        const float2 e2 = ey[(size_t)ky * M], x2 = xc[ky * Wh];
+                        ar = __fmaf_rn(x2.x, e2.x, ar);
+                        ar = __fmaf_rn(-x2.y, e2.y, ar);
+                        ai = __fmaf_rn(x2.x, e2.y, ai);
+                        ai = __fmaf_rn(x2.y, e2.x, ai);
+                    }
                 }
                 const float gw = folded ? 2.f : 1.f;               // the fold weight, exact
                 V32[o] = make_float2(gw * ar, gw * ai);
@@ -555,7 +544,8 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
             }
             const double maxS = gen_block_max(sS, sv);
             const double u32 = 0x1p-24;
-            const double Bnd = 1.01 * ((2.0 * Wh + 3.0) * u32 * maxS + (4.0 * H + 6.0) * u32 * sumA) +
+            // (sumA was taken before the phase rotation, which can grow a 1-norm by sqrt(2))
+            const double Bnd = 1.01 * ((2.0 * Wh + 3.0) * u32 * maxS + 1.42 * (4.0 * H + 16.0) * u32 * sumA) +
                                0x1p-30 * (maxS + sumA);
             // pass 1: the FP32 best (the values kept when the grid is small enough); pass 2:
             // the candidates
@@ -564,7 +554,7 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
             float b32 = -INFINITY;
             for (int o = threadIdx.x; o < M * M; o += blockDim.x) {
                 const int jy = o / M, jx = o - jy * M;
-                const float v = pl.sense * gen_cu32(V32 + jy * Wh, pl.uW32, W, jx, px, u, h0, (int)DW);
+                const float v = pl.sense * gen_cu32(V32 + jy * Wh, pl.EX + jx, Wh, M);
                 if (keep) G[o] = v;
                 b32 = fmaxf(b32, v);
             }
@@ -576,7 +566,7 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
             __syncthreads();
             for (int o = threadIdx.x; o < M * M; o += blockDim.x) {
                 const int jy = o / M, jx = o - jy * M;
-                const float v = keep ? G[o] : pl.sense * gen_cu32(V32 + jy * Wh, pl.uW32, W, jx, px, u, h0, (int)DW);
+                const float v = keep ? G[o] : pl.sense * gen_cu32(V32 + jy * Wh, pl.EX + jx, Wh, M);
                 if ((double)v >= thr) {
                     const int k = atomicAdd(&s_nc, 1);
                     if (k < gcap) cand[k] = o;
@@ -723,10 +713,32 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
     }
 }
 
+// The FP32 grid tables of one general shape: EY[ky][jy] = e^{2 pi i ky' (jy - h0) / (uH)} and
+// EX[kx][jx] = e^{2 pi i kx' (jx - h0) / (uW)}, k' the fftfreq-signed frequency (the x-Nyquist
+// column kx = W/2 is -W/2), every angle index reduced exactly in integers.
+__global__ void gen_init_grid_tables(int H, int W, int u, int M, int h0, float2* EY, float2* EX) {
+    const int Wh = W / 2 + 1;
+    const long long DH = (long long)u * H, DW = (long long)u * W, ny = (long long)H * M;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ny + (long long)Wh * M;
+         i += (long long)gridDim.x * blockDim.x) {
+        const bool y = i < ny;
+        const long long r = y ? i : i - ny;
+        const int k = (int)(r / M), j = (int)(r - (long long)k * M);
+        const int N = y ? H : W;
+        const long long D = y ? DH : DW;
+        const long long ks = 2 * k >= N ? k - N : k;
+        long long m = (ks * (j - h0)) % D;
+        if (m < 0) m += D;
+        double s, c;
+        sincospi(2.0 * (double)m / (double)D, &s, &c);
+        (y ? EY : EX)[r] = make_float2((float)c, (float)s);
+    }
+}
+
 // Tables of one general shape: e^{-2 pi i m / H} (m < H), e^{-2 pi i m / W} (m < W),
 // e^{+2 pi i m / (uH)} (m < uH) and e^{+2 pi i m / (uW)} (m < uW), one block of
-// H + W + uH + uW double-floats; tab32 holds the last two rounded to FP32 (uH + uW).
-__global__ void gen_init_tables(int H, int W, int u, dfc* tab, float2* tab32) {
+// H + W + uH + uW double-floats.
+__global__ void gen_init_tables(int H, int W, int u, dfc* tab) {
     const long long DH = (long long)u * H, DW = (long long)u * W, n = H + W + DH + DW;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         double s, c;
@@ -740,7 +752,6 @@ __global__ void gen_init_tables(int H, int W, int u, dfc* tab, float2* tab32) {
             sincospi(2.0 * (double)(i - H - W - DH) / (double)DW, &s, &c);
         }
         tab[i] = dfc{df_from_double(c), df_from_double(s)};
-        if (i >= H + W) tab32[i - H - W] = make_float2((float)c, (float)s);
     }
 }
 
@@ -825,6 +836,7 @@ __global__ void gen_fill_synthetic(int H, int W, int in_dtype, long long n, void
 }
 
 const void* gen_fill_synthetic_ptr() { return (const void*)gen_fill_synthetic; }
+const void* gen_init_grid_tables_ptr() { return (const void*)gen_init_grid_tables; }
 const void* gen_ref_rows_ptr() { return (const void*)gen_ref_rows; }
 const void* gen_ref_cols_ptr() { return (const void*)gen_ref_cols; }
 const void* track_generic_kernel_ptr() { return (const void*)track_generic_kernel; }

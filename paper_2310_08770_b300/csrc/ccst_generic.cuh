@@ -15,8 +15,8 @@ struct GenPlan {
     const dfc* wW;          // W:    e^{-2 pi i m / W}
     const dfc* uH;          // u H:  e^{+2 pi i m / (u H)}
     const dfc* uW;          // u W:  e^{+2 pi i m / (u W)}
-    const float2* uH32;     // the same two tables rounded to FP32
-    const float2* uW32;
+    const float2* EY;       // H x M, FP32: e^{2 pi i ky' (jy - h0) / (uH)}, fftfreq-signed ky'
+    const float2* EX;       // (W/2 + 1) x M, FP32: e^{2 pi i kx' (jx - h0) / (uW)} (kx = W/2: -W/2)
 };
 
 struct GenItem {
@@ -71,5 +71,6 @@ const void* gen_frame_to_f32_ptr();
 const void* gen_ref_rows_ptr();
 const void* gen_ref_cols_ptr();
 const void* gen_fill_synthetic_ptr();
+const void* gen_init_grid_tables_ptr();
 
 }  // namespace ccst
