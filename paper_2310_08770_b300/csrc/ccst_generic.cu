@@ -615,16 +615,26 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
                         const int slot = t / Wh, kx = t - slot * Wh, jy = s_rowof[slot];
                         const long long q = gen_mod((long long)py * u + jy - h0, DH), nq = gen_mod((long long)H * q, DH);
                         const bool folded = kx != 0 && 2 * kx != W;
+                        // the operands of row ky + 1 are loaded while row ky is accumulated (the
+                        // table and X live in L2); the arithmetic is the exhaustive loop's
+                        auto table_index = [&](int ky, long long mm) {
+                            if (2 * ky >= H) { mm -= nq; if (mm < 0) mm += DH; }
+                            return mm;
+                        };
                         dfc acc = zero;
                         long long m = 0;
+                        dfc en = ldc(pl.uH + table_index(0, 0)), xn = ldc(X + kx);
                         for (int ky = 0; ky < H; ++ky) {
-                            long long ms = m;
-                            if (2 * ky >= H) { ms -= nq; if (ms < 0) ms += DH; }
-                            dfc e = ldc(pl.uH + ms);
-                            if (ky == nyq_y && folded) e.im = df{0.f, 0.f};
-                            acc = cadd(acc, cmul(ldc(X + (ky * Wh + kx)), e));
+                            dfc e = en;
+                            const dfc x = xn;
                             m += q;
                             if (m >= DH) m -= DH;
+                            if (ky + 1 < H) {
+                                en = ldc(pl.uH + table_index(ky + 1, m));
+                                xn = ldc(X + ((ky + 1) * Wh + kx));
+                            }
+                            if (ky == nyq_y && folded) e.im = df{0.f, 0.f};
+                            acc = cadd(acc, cmul(x, e));
                         }
                         stc(B + t, acc);
                     }
