@@ -286,20 +286,10 @@ __device__ inline long long rt_grid_index(float d, int p, int u) {
     return (long long)p * u + llrint((double)d * u - (double)p * u);
 }
 
-// e^{+2 pi i k' d / N} on one axis of length N, d = q / u (q = p u + t), from the context's
-// two-level table of e^{2 pi i n / D}, D = u N, with n = k' q mod D reduced exactly in
-// integers. The Nyquist bin of an even N takes the real part, cos(pi d).
-__device__ inline double2 rt_axis_phase(int k, int N, long long q, long long D, const dfc* coarse, const dfc* fine,
-                                        int B) {
-    const bool nyq = 2 * k == N;
-    const long long ks = (nyq || k < (N >> 1)) ? k : k - N;
-    long long n = (ks * q) % D;
-    if (n < 0) n += D;
-    const dfc e = df_twiddle(coarse, fine, B, n);
-    return make_double2(df_to_double(e.re), nyq ? 0.0 : df_to_double(e.im));
-}
-
-// The same phase as a complex double-float.
+// e^{+2 pi i k' d / N} on one axis of length N as a complex double-float, d = q / u
+// (q = p u + t), from the context's two-level table of e^{2 pi i n / D}, D = u N, with
+// n = k' q mod D reduced exactly in integers. The Nyquist bin of an even N takes the real
+// part, cos(pi d).
 __device__ inline dfc rt_axis_phase_df(int k, int N, long long q, long long D, const dfc* coarse, const dfc* fine,
                                        int B) {
     const bool nyq = 2 * k == N;
