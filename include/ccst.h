@@ -64,6 +64,8 @@ extern "C" {
 #define CCST_F32 1
 
 /* ccst_params.flags */
+/* TIE_GUARD, GRAPHS and PROFILE concern power-of-two contexts; a general-shape context
+ * (see ccst_create) needs no near-tie levels, launches directly, and has no profiling. */
 #define CCST_FLAG_TIE_GUARD 0x1u  /* resolve near-ties of the FP32 surfaces in higher precision (default on) */
 #define CCST_FLAG_GRAPHS    0x2u  /* ccst_track replays one captured CUDA graph per (frames, n, pitch, out);
                                       each graph has its own frame counter, so graphs of different
