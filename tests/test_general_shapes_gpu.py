@@ -174,7 +174,10 @@ def test_shapes_outside_the_range_are_refused(torch):
 
 @pytest.mark.parametrize("H,W,u,method", [(96, 96, 100, oracle.CC_U), (48, 80, 64, oracle.CC_SN),
                                           (30, 30, 100, oracle.CC_U), (256, 128, 50, oracle.CC_U),
-                                          (12, 8, 3, oracle.CC_SN)])
+                                          (12, 8, 3, oracle.CC_SN),
+                                          # grids above 256 points a side: pass 2 recomputes the
+                                          # FP32 values, and the row bitmap spans many words
+                                          (40, 24, 200, oracle.CC_U), (20, 20, 1000, oracle.CC_SN)])
 def test_fp32_grid_with_candidates_equals_the_exhaustive_grid(torch, H, W, u, method):
     # the FP32 pass only chooses which points the double-float evaluation visits: records
     # must be byte-identical to evaluating the whole grid in double-float. Extra frames: the
