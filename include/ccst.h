@@ -219,8 +219,8 @@ int ccst_poll(ccst_ctx* ctx, uint64_t ticket, int timeout_us, int* done);
  *            16, 32, 64 and 128 run on the power-of-two ROI kernel (FP32 surfaces with the
  *            near-tie levels, as ccst_track). Every other side (8, 48, 96, 192, 256, odd
  *            sides, ...) runs on the general-size kernel of general-shape contexts (see
- *            ccst_create): slower (O(N^3) per ROI) but needing no near-tie levels; its
- *            records carry CCST_R_GENERIC.
+ *            ccst_create): about ten times slower per pixel than the power-of-two
+ *            kernel, but general; its records carry CCST_R_GENERIC.
  * The first reference of a new size also creates that size's plan (geometry, FFT
  * twiddles, upsampling tables) with the context's parameters (u, method, eps); for the
  * general path u * N must not exceed 2^22. Each power-of-two reference keeps its spectra
