@@ -67,9 +67,10 @@ extern "C" {
 /* TIE_GUARD, GRAPHS and PROFILE concern power-of-two contexts; a general-shape context
  * (see ccst_create) needs no near-tie levels, launches directly, and has no profiling. */
 #define CCST_FLAG_TIE_GUARD 0x1u  /* resolve near-ties of the FP32 surfaces in higher precision (default on) */
-#define CCST_FLAG_GRAPHS    0x2u  /* ccst_track replays one captured CUDA graph per (frames, n, pitch, out);
-                                      each graph has its own frame counter, so graphs of different
-                                      batches may run at once on different streams (ccst_set_stream) */
+#define CCST_FLAG_GRAPHS    0x2u  /* ccst_track replays one captured CUDA graph per (stream, frames, n,
+                                      pitch, out); each graph owns its frame counter, so graphs of
+                                      different batches may run at once on different streams
+                                      (ccst_set_stream) */
 #define CCST_FLAG_PROFILE   0x4u  /* record CUDA events around each launch of the tracking kernel */
 #define CCST_FLAG_EXHAUSTIVE 0x8u /* general-size kernel (ccst_create): evaluate the whole upsampled
                                      grid in double-float, instead of FP32 with a rounding bound and
@@ -196,8 +197,24 @@ int ccst_submit_host(ccst_ctx* ctx, const void* frames_host, int64_t n, int64_t 
                      ccst_result* out_host, uint64_t* ticket);
 
 /* Work on `stream` (a cudaStream_t) from now on. The caller orders this
- * against earlier work. */
+ * against earlier work. Cached graphs (CCST_FLAG_GRAPHS) are keyed by stream as well as
+ * by batch, so switching streams drops none of them: each (stream, batch) pair is
+ * captured once and then replayed. Every cached graph owns a frame counter that no other
+ * graph or launch uses, and direct launches wait for the previous user of their counter,
+ * so batches in flight at once on different streams never share a frame counter.
+ * Calls that use the context's shared buffers (ccst_track_rois; ccst_track on a
+ * general-shape context) are ordered after the previous such call, on any stream. */
 int ccst_set_stream(ccst_ctx* ctx, void* stream);
+
+/* Graph-cache statistics of a context (CCST_FLAG_GRAPHS):
+ *   instantiations  graphs captured and instantiated so far;
+ *   replays         graph launches so far;
+ *   cached          graphs held now (at most 512; when full, the cache waits for the
+ *                   cached graphs' last replays, destroys them and starts again).
+ * Not in the paper: a measure of the batching machinery (Sec. III makes frames
+ * independent under a fixed reference, so batches may run on several streams at once).
+ * Errors: CCST_E_INVALID (null context or output). */
+int ccst_graph_stats(ccst_ctx* ctx, int64_t* instantiations, int64_t* replays, int64_t* cached);
 
 /* Block until all work issued on the context's stream has finished. */
 int ccst_sync(ccst_ctx* ctx);
@@ -538,6 +555,18 @@ int ccst_debug_surfaces(ccst_ctx* ctx, const void* frames_dev, int64_t n, int64_
 int ccst_track_static(const float* ref_dev, int H, int W, const ccst_params* p,
                       const void* frames_dev, int64_t n, int64_t pitch_elems,
                       ccst_result* out_dev);
+
+/* FP32 FMA throughput of the current device, for the roofline of the tracking kernel.
+ * Not in the paper: the paper's dense work (the FFTs of Eq. (4) and the upsampled DFT of
+ * Sec. III) needs FP32 accuracy, so its bound is the rate of the FP32 FMA pipes.
+ *   stream          cudaStream_t to run on (NULL = default stream); the call blocks until done.
+ *   iters           loop trips of the timing kernel (each thread does iters x 128 FMAs;
+ *                   about 20000 gives a 20 ms launch on a 148-SM B300).
+ *   tflops          out: measured rate, the best of three timed launches after one warm-up
+ *                   (every SM full, independent FMA chains), in TFLOP/s (1 FMA = 2 flop).
+ *   nominal_tflops  out: SMs x 128 FP32 lanes x 2 x the device's reported peak clock.
+ * Allocates nothing. Errors: CCST_E_INVALID (null outputs, iters < 1), CCST_E_CUDA. */
+int ccst_fp32_fma_peak(void* stream, int iters, double* tflops, double* nominal_tflops);
 
 /* Message of the last failed ccst_track_static call in this process. Never NULL. */
 const char* ccst_static_last_error(void);

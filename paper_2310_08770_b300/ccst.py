@@ -83,6 +83,10 @@ _SIGS = [
     ("ccst_track_host", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                        ctypes.c_void_p]),
     ("ccst_set_stream", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("ccst_fp32_fma_peak", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]),
+    ("ccst_graph_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     ("ccst_sync", ctypes.c_int, [ctypes.c_void_p]),
     ("ccst_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                    ctypes.POINTER(ctypes.c_uint64)]),
@@ -206,6 +210,22 @@ def ccst_track_host(ctx, frames_host, n: int, pitch_elems: int, out_host) -> Non
 
 def ccst_set_stream(ctx, stream) -> None:
     _check(lib().ccst_set_stream(ctx, stream), ctx)
+
+
+def ccst_graph_stats(ctx) -> dict:
+    """Graph instantiations, replays and cached graphs of the context so far."""
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().ccst_graph_stats(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), ctx)
+    return {"instantiations": a.value, "replays": b.value, "cached": c.value}
+
+
+def ccst_fp32_fma_peak(stream=None, iters: int = 20000) -> dict:
+    """Measured and nominal FP32 FMA throughput of the current device, TFLOP/s."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    rc = lib().ccst_fp32_fma_peak(stream, int(iters), ctypes.byref(a), ctypes.byref(b))
+    if rc:
+        raise CcstError(rc, "ccst_fp32_fma_peak failed")
+    return {"tflops": a.value, "nominal_tflops": b.value}
 
 
 def ccst_sync(ctx) -> None:

@@ -37,8 +37,11 @@ constexpr int kTickets = 64;      // in-flight submissions per context
 constexpr int kHostSlots = 4;     // staging slots of the pipelined host path
 constexpr size_t kMaxGraphs = 512;
 
-// Guard thresholds, in units of the FP32 unit roundoff times sum w|X| (see DESIGN notes
-// in the repository: calibrated against the FP64 oracle with a wide margin).
+// Guard thresholds, in units of the FP32 unit roundoff eps32 times sum w|X|. Each is a
+// multiple of the largest surface error measured against the FP64 oracle at that level:
+// the integer surface errs by at most 2.2 eps32 sum|X| (threshold 32), the peak-relative
+// upsampled surface by under 0.125 (threshold 1), the FP32 pair differences by under
+// 0.0026 (threshold 0.02). Points the threshold cannot separate go to the next level.
 constexpr float kEps32 = 1.1920929e-07f;
 constexpr float kTauInt = 32.0f * kEps32;
 constexpr float kTau0 = 1.0f * kEps32;
@@ -654,19 +657,35 @@ struct ccst_ctx {
     int rois_grid = 0;
     void* d_addref_tmp = nullptr;     // ccst_add_reference: reference copy and FFT workspace
     size_t addref_tmp_bytes = 0;
-    // graphs keyed by (frames, n, pitch, out), each with its own profiling event pair
-    // and its own frame counter, so graphs of different batches can run at once on
-    // different streams
+    // graphs keyed by (stream, frames, n, pitch, out). Each owns a profiling event pair, a
+    // completion event and a frame counter that no other graph uses, so graphs of different
+    // batches can run at once on different streams. Replays of one graph are ordered by CUDA
+    // (a graph exec runs after its own previous launch), so its counter is never shared.
+    // A counter goes back to the pool only after the graph's last replay has finished
+    // (drop_graphs waits on the completion events first).
     struct GraphEntry {
         cudaGraphExec_t exec = nullptr;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaEvent_t done = nullptr;    // recorded after every replay
+        unsigned counter = 0;          // index into d_graph_counters
     };
-    unsigned* d_graph_counters = nullptr;   // kMaxGraphs counters, one per captured graph
-    // direct launches take counters from a ring of kTickets, so launches on different
-    // streams do not share one (d_next stays the real-time path's counter)
+    unsigned* d_graph_counters = nullptr;   // kMaxGraphs counters, one per cached graph
+    std::vector<unsigned> free_graph_counters;
+    int64_t graph_instantiations = 0, graph_replays = 0;
+    // direct launches take counters from a ring of kTickets; before a counter is reused,
+    // the new launch's stream waits for the previous launch that used it (ring_ev), so
+    // launches on different streams never share a counter (d_next stays the real-time
+    // path's counter)
     unsigned* d_launch_counters = nullptr;
     unsigned launch_seq = 0;
-    std::map<std::tuple<const void*, long long, long long, void*>, GraphEntry> graphs;
+    cudaEvent_t ring_ev[kTickets] = {};
+    bool ring_used[kTickets] = {};
+    // the ROI path and a general-shape context's ccst_track share per-context device
+    // buffers (work-item lists, the general kernel's lane-0 scratch, fixed counters): each
+    // such call waits for the previous one, whichever stream it ran on (shared_ev)
+    cudaEvent_t shared_ev = nullptr;
+    bool shared_used = false;
+    std::map<std::tuple<cudaStream_t, const void*, long long, long long, void*>, GraphEntry> graphs;
     // profiling ring for direct launches
     std::vector<cudaEvent_t> prof0, prof1;
     int prof_next = 0, prof_used = 0;
@@ -706,13 +725,68 @@ static int fail(ccst_ctx* c, int code, const std::string& msg) {
                         std::string(#call) + ": " + cudaGetErrorString(e_));                      \
     } while (0)
 
+// Destroy every cached graph after its last replay has finished, and return the frame
+// counters to the pool: no counter is handed out again while a launch may still use it.
 static void drop_graphs(ccst_ctx* c) {
+    for (auto& kv : c->graphs)
+        if (kv.second.done) cudaEventSynchronize(kv.second.done);
     for (auto& kv : c->graphs) {
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
         if (kv.second.e0) cudaEventDestroy(kv.second.e0);
         if (kv.second.e1) cudaEventDestroy(kv.second.e1);
+        if (kv.second.done) cudaEventDestroy(kv.second.done);
     }
     c->graphs.clear();
+    c->free_graph_counters.clear();
+    for (unsigned i = 0; i < (unsigned)kMaxGraphs; ++i) c->free_graph_counters.push_back((unsigned)kMaxGraphs - 1 - i);
+}
+
+// A frame counter of the direct-launch ring for a launch on `stream`: the stream first
+// waits for the previous launch that used the same counter (a no-op when it ran on the
+// same stream or has finished). Call ring_release after the launch has been issued.
+static unsigned ring_acquire(ccst_ctx* c, cudaStream_t stream, cudaError_t* err) {
+    const unsigned k = c->launch_seq++ % kTickets;
+    *err = cudaSuccess;
+    if (c->ring_used[k]) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        *err = cudaStreamIsCapturing(stream, &cs);
+        // inside a caller's stream capture the wait would join an outside event into the
+        // graph; the caller's graph then orders its own launches
+        if (*err == cudaSuccess && cs == cudaStreamCaptureStatusNone)
+            *err = cudaStreamWaitEvent(stream, c->ring_ev[k], 0);
+    }
+    return k;
+}
+
+// Order a call that uses the context's shared buffers after the previous such call.
+static cudaError_t shared_acquire(ccst_ctx* c, cudaStream_t stream) {
+    if (!c->shared_ev) {
+        const cudaError_t e = cudaEventCreateWithFlags(&c->shared_ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+    }
+    if (!c->shared_used) return cudaSuccess;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(stream, &cs);
+    if (e == cudaSuccess && cs == cudaStreamCaptureStatusNone) e = cudaStreamWaitEvent(stream, c->shared_ev, 0);
+    return e;
+}
+
+static cudaError_t shared_release(ccst_ctx* c, cudaStream_t stream) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(stream, &cs);
+    if (e != cudaSuccess || cs != cudaStreamCaptureStatusNone) return e;
+    e = cudaEventRecord(c->shared_ev, stream);
+    if (e == cudaSuccess) c->shared_used = true;
+    return e;
+}
+
+static cudaError_t ring_release(ccst_ctx* c, unsigned k, cudaStream_t stream) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(stream, &cs);
+    if (e != cudaSuccess || cs != cudaStreamCaptureStatusNone) return e;
+    e = cudaEventRecord(c->ring_ev[k], stream);
+    if (e == cudaSuccess) c->ring_used[k] = true;
+    return e;
 }
 
 static void free_all(ccst_ctx* c) {
@@ -723,8 +797,10 @@ static void free_all(ccst_ctx* c) {
     }
     c->prof0.clear();
     c->prof1.clear();
-    for (int i = 0; i < kTickets; ++i)
+    for (int i = 0; i < kTickets; ++i) {
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+        if (c->ring_ev[i]) cudaEventDestroy(c->ring_ev[i]);
+    }
     for (int i = 0; i < kHostSlots; ++i) {
         if (c->h_frames[i]) cudaFree(c->h_frames[i]);
         if (c->h_out[i]) cudaFree(c->h_out[i]);
@@ -744,6 +820,7 @@ static void free_all(ccst_ctx* c) {
     if (c->gstream) cudaStreamDestroy(c->gstream);
     if (c->gfork) cudaEventDestroy(c->gfork);
     if (c->gjoin) cudaEventDestroy(c->gjoin);
+    if (c->shared_ev) cudaEventDestroy(c->shared_ev);
     void* ptrs[] = {c->d_ref32, c->d_b64, c->d_FE64, c->d_FE32, c->d_tw64, c->d_tw32,
                     c->d_tab,   c->d_df,  c->d_frames, c->d_out, c->d_next, c->d_rtE, c->d_rtY, c->d_rtSync,
                     c->d_offPart, c->d_offScratch, c->d_adjY, c->d_geoms, c->d_refs, c->d_items, c->d_addref_tmp,
@@ -811,7 +888,8 @@ static int create_general(const float* ref, int H, int W, const ccst_params& p, 
             return bail(e == cudaErrorMemoryAllocation ? CCST_E_NOMEM : CCST_E_CUDA);
         }
     for (int i = 0; i < kTickets; ++i)
-        if ((e = cudaEventCreateWithFlags(&c->ev[i], cudaEventDisableTiming)) != cudaSuccess) {
+        if ((e = cudaEventCreateWithFlags(&c->ev[i], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&c->ring_ev[i], cudaEventDisableTiming)) != cudaSuccess) {
             c->err = std::string("event: ") + cudaGetErrorString(e);
             return bail(CCST_E_CUDA);
         }
@@ -945,7 +1023,8 @@ extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pi
     }
     c->grid_main = prop.multiProcessorCount * occ;
     for (int i = 0; i < kTickets; ++i)
-        if (!step(cudaEventCreateWithFlags(&c->ev[i], cudaEventDisableTiming), "event"))
+        if (!step(cudaEventCreateWithFlags(&c->ev[i], cudaEventDisableTiming), "event") ||
+            !step(cudaEventCreateWithFlags(&c->ring_ev[i], cudaEventDisableTiming), "event"))
             return bail(CCST_E_CUDA);
     if (p.flags & CCST_FLAG_PROFILE) {
         c->prof0.resize(1024);
@@ -978,11 +1057,18 @@ static int launch(ccst_ctx* c, const Batch& b, bool reset_counter = true, unsign
     {
         Geom gk = c->g;
         Batch bk = b;
-        if (!counter) counter = c->d_launch_counters + (c->launch_seq++ % kTickets);
+        int ring = -1;
+        if (!counter) {
+            cudaError_t e;
+            ring = (int)ring_acquire(c, c->stream, &e);
+            CK(c, e);
+            counter = c->d_launch_counters + ring;
+        }
         bk.next = counter;
         if (reset_counter) CK(c, cudaMemsetAsync(bk.next, 0, sizeof(unsigned), c->stream));
         void* args[] = {&gk, &bk};
         CK(c, cudaLaunchKernel(c->kernel, dim3(grid), dim3(kThreads), args, c->smem, c->stream));
+        if (ring >= 0) CK(c, ring_release(c, (unsigned)ring, c->stream));
     }
     if (prof) CK(c, cudaEventRecordWithFlags(e1, c->stream, c->capturing ? cudaEventRecordExternal : 0));
     CK(c, cudaGetLastError());
@@ -1037,16 +1123,28 @@ extern "C" int ccst_track(ccst_ctx* c, const void* frames_dev, int64_t n, int64_
     Batch b;
     if ((rc = make_batch(c, frames_dev, n, pitch_elems, out_dev, &b))) return rc;
     if (n == 0) return CCST_OK;
-    if (c->general) return gen_track(c, b, c->stream, c->glane[0], c->d_launch_counters + (c->launch_seq++ % kTickets));
+    if (c->general) {
+        cudaError_t e;
+        const unsigned k = ring_acquire(c, c->stream, &e);
+        CK(c, e);
+        CK(c, shared_acquire(c, c->stream));
+        if ((rc = gen_track(c, b, c->stream, c->glane[0], c->d_launch_counters + k))) return rc;
+        CK(c, ring_release(c, k, c->stream));
+        CK(c, shared_release(c, c->stream));
+        return CCST_OK;
+    }
     const bool graphs = (c->p.flags & CCST_FLAG_GRAPHS) && c->stream != nullptr;
     if (!graphs) return launch(c, b);
-    auto key = std::make_tuple(frames_dev, (long long)n, (long long)b.pitch, (void*)out_dev);
+    auto key = std::make_tuple(c->stream, frames_dev, (long long)n, (long long)b.pitch, (void*)out_dev);
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
-        if (c->graphs.size() >= kMaxGraphs) drop_graphs(c);
+        if (c->graphs.size() >= kMaxGraphs || c->free_graph_counters.empty()) drop_graphs(c);
         if (!c->d_graph_counters) CK(c, cudaMalloc(&c->d_graph_counters, kMaxGraphs * sizeof(unsigned)));
-        unsigned* counter = c->d_graph_counters + c->graphs.size();
         ccst_ctx::GraphEntry ent;
+        CK(c, cudaEventCreateWithFlags(&ent.done, cudaEventDisableTiming));
+        ent.counter = c->free_graph_counters.back();
+        c->free_graph_counters.pop_back();
+        unsigned* counter = c->d_graph_counters + ent.counter;
         if (c->p.flags & CCST_FLAG_PROFILE) {
             CK(c, cudaEventCreate(&ent.e0));
             CK(c, cudaEventCreate(&ent.e1));
@@ -1064,9 +1162,12 @@ extern "C" int ccst_track(ccst_ctx* c, const void* frames_dev, int64_t n, int64_
         e = cudaGraphInstantiate(&ent.exec, graph, 0);
         cudaGraphDestroy(graph);
         CK(c, e);
+        ++c->graph_instantiations;
         it = c->graphs.emplace(key, ent).first;
     }
     CK(c, cudaGraphLaunch(it->second.exec, c->stream));
+    CK(c, cudaEventRecord(it->second.done, c->stream));
+    ++c->graph_replays;
     return CCST_OK;
 }
 
@@ -1150,8 +1251,17 @@ extern "C" int ccst_submit_host(ccst_ctx* c, const void* frames_host, int64_t n,
 extern "C" int ccst_set_stream(ccst_ctx* c, void* stream) {
     int rc = check_ctx(c);
     if (rc) return rc;
-    if ((cudaStream_t)stream != c->stream) drop_graphs(c);
-    c->stream = (cudaStream_t)stream;
+    c->stream = (cudaStream_t)stream;      // cached graphs are keyed by stream: none is dropped
+    return CCST_OK;
+}
+
+extern "C" int ccst_graph_stats(ccst_ctx* c, int64_t* instantiations, int64_t* replays, int64_t* cached) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!instantiations || !replays || !cached) return fail(c, CCST_E_INVALID, "ccst_graph_stats: null output");
+    *instantiations = c->graph_instantiations;
+    *replays = c->graph_replays;
+    *cached = (int64_t)c->graphs.size();
     return CCST_OK;
 }
 
@@ -2225,6 +2335,7 @@ extern "C" int ccst_track_rois(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccs
         it.vec_ok = ((uintptr_t)q.frame % 16 == 0) && ((size_t)pitch * elem % 16 == 0) ? 1 : 0;
         it.pad = 0;
     }
+    CK(c, shared_acquire(c, c->stream));
     if (ng > 0) {
         // the general sizes run on their own stream, forked here and joined below
         if (!c->gstream) {
@@ -2254,6 +2365,7 @@ extern "C" int ccst_track_rois(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccs
             return rc;
     }
     if (ng > 0) CK(c, cudaStreamWaitEvent(c->stream, c->gjoin, 0));     // both batches done
+    CK(c, shared_release(c, c->stream));
     return CCST_OK;
 }
 
@@ -2722,6 +2834,8 @@ extern "C" int ccst_track_static(const float* ref_dev, int H, int W, const ccst_
         return static_fail(CCST_E_INVALID, "ccst_track_static: upsample must be in [1, 16384]");
     if (p.method != CCST_CC_U && p.method != CCST_CC_SN)
         return static_fail(CCST_E_INVALID, "ccst_track_static: unknown method");
+    if (p.method == CCST_CC_SN && !(p.eps == p.eps))
+        return static_fail(CCST_E_INVALID, "ccst_track_static: eps is NaN");
     if (p.in_dtype != CCST_U16 && p.in_dtype != CCST_F32)
         return static_fail(CCST_E_INVALID, "ccst_track_static: unknown in_dtype");
     if (pitch_elems == 0) pitch_elems = W;

@@ -419,21 +419,39 @@ def test_pair_difference_error_is_far_below_tau1(torch):
 
 @pytest.mark.parametrize("graphs", [False, True])
 def test_batches_in_flight_on_several_streams_match_one_at_a_time(torch, graphs):
-    # every graph, and every direct launch, has its own frame counter: batches that overlap on
-    # different streams give the records of batches run one at a time
-    s = synth.frame_stream(seed=0, n=10_000, count=768)
+    # The 10,000-frame stream as 40 batches (39 x 256 + 16) over three rotating streams, two
+    # passes, into outputs pre-filled with a 0xFF sentinel: every record must be written and
+    # byte-equal to the records of the same batches run one at a time on one stream. With
+    # graphs, each (stream, batch) pair is captured exactly once: 40 instantiations, 80 replays.
+    s = synth.frame_stream(seed=0, n=10_000)
+    n = len(s.frames)
     dev = torch.from_numpy(s.frames.view(np.int16)).cuda().view(torch.uint16)
+    bounds = [(lo, min(n, lo + 256)) for lo in range(0, n, 256)]
+    assert len(bounds) == 40
+    one_t = C.Tracker(s.ref, upsample=100, in_dtype="u16", max_batch=256)
+    one = torch.full((n, 24), 0xFF, dtype=torch.uint8, device="cuda")
+    for lo, hi in bounds:
+        C.ccst_track(one_t.ctx, dev[lo:hi], hi - lo, 0, one[lo:hi])
+    C.ccst_sync(one_t.ctx)
+    one_t.close()
     streams = [torch.cuda.Stream() for _ in range(3)]
     t = C.Tracker(s.ref, upsample=100, in_dtype="u16", max_batch=256, graphs=graphs, stream=streams[0])
-    one = t.empty_results(768)
-    for b in range(3):
-        C.ccst_track(t.ctx, dev[256 * b:256 * (b + 1)], 256, 0, one[256 * b:256 * (b + 1)])
-    C.ccst_sync(t.ctx)
-    many = t.empty_results(768)
-    for rep in range(3):
-        for b in range(3):
-            C.ccst_set_stream(t.ctx, streams[b].cuda_stream)
-            C.ccst_track(t.ctx, dev[256 * b:256 * (b + 1)], 256, 0, many[256 * b:256 * (b + 1)])
-    torch.cuda.synchronize()
-    assert C.decode(many).tobytes() == C.decode(one).tobytes()
+    for rep in range(2):
+        many = torch.full((n, 24), 0xFF, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        for b, (lo, hi) in enumerate(bounds):
+            C.ccst_set_stream(t.ctx, streams[b % 3].cuda_stream)
+            C.ccst_track(t.ctx, dev[lo:hi], hi - lo, 0, many[lo:hi])
+        torch.cuda.synchronize()
+        got = many.cpu().numpy()
+        unwritten = np.flatnonzero((got == 0xFF).all(axis=1))
+        assert unwritten.size == 0, unwritten[:20]
+        bad = np.flatnonzero((got != one.cpu().numpy()).any(axis=1))
+        assert bad.size == 0, bad[:20]
+        del many
+    st = C.ccst_graph_stats(t.ctx)
+    if graphs:
+        assert st == {"instantiations": 40, "replays": 80, "cached": 40}, st
+    else:
+        assert st == {"instantiations": 0, "replays": 0, "cached": 0}, st
     t.close()

@@ -90,3 +90,9 @@ def test_static_entry_rejects_oversized_requests(torch):
     with pytest.raises(C.CcstError) as e:
         C.ccst_track_static(ref, 256, 256, None, frames, 1, 0, out)
     assert e.value.code == C.E_SHAPE
+    p = C.ccst_default_params()
+    p.method = C.CC_SN
+    p.eps = float("nan")                     # ccst_create refuses the same parameters
+    with pytest.raises(C.CcstError) as e:
+        C.ccst_track_static(ref, 128, 128, p, frames, 1, 0, out)
+    assert e.value.code == C.E_INVALID
