@@ -5,11 +5,14 @@ Workload (frame stream): 10,000 uint16 128x128 frames of a Gaussian spot
 (sigma 2.5 px, peak 2000 photons, background 20, Poisson noise) on a reflected
 2-D Brownian trajectory (step 0.3 px), tracked against one noise-free reference
 with u = 100, CC-U, in 256-frame batches (the last batch has 16 frames), one
-CUDA-graph launch per batch. One step = one batch. The stream (328 MB) is larger
-than L2 and is staged in HBM before timing; consecutive steps read different
-slices of it.
+CUDA-graph launch per batch. One step = one pass over the whole stream: its 40
+batches (39 x 256 + 16), batch b on CUDA stream b mod 3. The stream (328 MB) is
+larger than L2 and is staged in HBM before timing; each step reads all of it once.
 
-Prints one JSON line (see the repository's design notes for every key).
+Prints one JSON line: the contract keys (metric, value, unit, n_gpus, steps, warmup,
+ms_per_step, config, roofline, cpu_baseline, e2e, clocks, gpu_launches), the headline's
+latency percentiles and oracle parity, and one object per extra leg (plain per-frame
+launch, latency under offered load, real-time, offline, uneven ROIs, serving, adjoint).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
 from __future__ import annotations
@@ -48,7 +51,9 @@ def grid_size(u):
 
 
 def flop_per_frame(h=H, w=W, u=U):
-    """Algorithmic FP32 flops of one frame in the folded formulation the kernel computes."""
+    """Algorithmic FP32 flops of one frame in the folded formulation the kernel computes:
+    the contraction exploits the Hermitian symmetry of the real-input spectrum in both
+    stages (ky folded into P/Q planes, +-t and +-tx pairs from one product)."""
     m = grid_size(u)
     h0 = m // 2
     wc = w // 2 + 1
@@ -58,6 +63,25 @@ def flop_per_frame(h=H, w=W, u=U):
     stage_b = m * m * wc * 2                             # one FMA per (grid point, kx)
     g_row = (h0 + 1) * wc * 4
     return fft + product + stage_a + stage_b + g_row
+
+
+def scope_flop_per_frame(h=H, w=W, u=U):
+    """Algorithmic flops of one frame as the scope table counts them (real input and
+    output, Hermitian half in kx only): the two FFTs, the product and the integer-peak
+    phase (6 flop per half-spectrum bin each), stage A as a complex contraction over all
+    H rows (8 flop per (grid row, ky, kx)) and stage B over the half spectrum (4 flop per
+    (grid point, kx)). 17.1 MFLOP at 128 x 128, u = 100."""
+    m = grid_size(u)
+    wc = w // 2 + 1
+    fft = 2 * 2.5 * h * w * math.log2(h * w)
+    return fft + 12 * h * wc + 8 * m * h * wc + 4 * m * m * wc
+
+
+def scope_contraction_flop(h=H, w=W, u=U):
+    """The upsampled-DFT contraction's share of scope_flop_per_frame (stages A and B)."""
+    m = grid_size(u)
+    wc = w // 2 + 1
+    return 8 * m * h * wc + 4 * m * m * wc
 
 
 def kernel_source_hash():
@@ -617,6 +641,44 @@ def plain_leg(C, torch, s, frames_dev, stream):
 
 
 # ---------------------------------------------------------------- our arm
+TIE_MARGIN = 1e-12               # oracle top-2 margin (relative) below which a frame is a genuine tie
+
+
+def batch_bounds(n_frames, batch=BATCH):
+    """The stream's batches: 39 x 256 frames and a last batch of 16 at 10,000 frames."""
+    return [(lo, min(n_frames, lo + batch)) for lo in range(0, n_frames, batch)]
+
+
+def headline_config(world):
+    """config of the headline line; the reference arm prints the same dictionary."""
+    return {"workload": WORKLOAD, "global_batch": BATCH * world, "frames_per_rank": N_FRAMES,
+            "frames_per_step": N_FRAMES * world, "batches_per_step": len(batch_bounds(N_FRAMES)),
+            "upsample": U, "streams": 3, "parallelism": f"replicas x{world} (independent streams)",
+            "l2": "inputs larger than L2 (the 328 MB stream per rank is read once per step)"}
+
+
+def parity_with_ties(gpu, orc, u=U):
+    """Frame-by-frame comparison with the oracle: integer peaks identical and |d| within 1e-3
+    px, except where the oracle's own top-2 margin shows a genuine tie (< TIE_MARGIN relative),
+    where a one-bin difference is allowed and counted. Lists every mismatch and tie."""
+    mism, ties = [], []
+    for i, (a, o) in enumerate(zip(gpu, orc)):
+        int_same = (int(a["ipy"]), int(a["ipx"])) == (o["ipy"], o["ipx"])
+        close = abs(float(a["dx"]) - o["dx32"]) <= 1e-3 and abs(float(a["dy"]) - o["dy32"]) <= 1e-3
+        if int_same and close:
+            continue
+        one_bin = (abs(float(a["dx"]) - o["dx32"]) <= 1.0 / u + 1e-6 and abs(float(a["dy"]) - o["dy32"]) <= 1.0 / u + 1e-6)
+        item = {"frame": i, "gpu": [float(a["dx"]), float(a["dy"]), int(a["ipy"]), int(a["ipx"])],
+                "oracle": [o["dx32"], o["dy32"], o["ipy"], o["ipx"]],
+                "int_margin": o["int_margin"], "sub_margin": o["sub_margin"]}
+        tie = ((not int_same and o["int_margin"] < TIE_MARGIN) or
+               (int_same and one_bin and o["sub_margin"] < TIE_MARGIN))
+        (ties if tie else mism).append(item)
+    return {"frames": len(orc), "mismatches": len(mism), "genuine_ties": len(ties), "tolerance_px": 1e-3,
+            "tie_rule": f"one bin allowed where the oracle's top-2 margin < {TIE_MARGIN} of sum|X|/HW",
+            "mismatch_list": mism[:20], "tie_list": ties[:20]}
+
+
 def run_ours(args):
     import torch
     from paper_2310_08770_b300 import ccst as C
@@ -630,29 +692,37 @@ def run_ours(args):
     n_frames = args.frames
     s = synth.frame_stream(seed=shard_seed(rank), n=N_FRAMES, count=n_frames)
     frames_dev = torch.from_numpy(s.frames.view(np.int16)).cuda().view(torch.uint16)
-    nb = (n_frames + BATCH - 1) // BATCH
+    bounds = batch_bounds(n_frames)
+    nb = len(bounds)
     outs = torch.empty((n_frames, 24), dtype=torch.uint8, device="cuda")
-    # consecutive batches alternate over `streams` CUDA streams, so the next batch's CTAs start
-    # on the SMs the previous batch's last frames leave idle (each graph has its own counter)
+    # batch b runs on stream b % streams: the next batch's CTAs start on the SMs the previous
+    # batch's last frames leave idle; each cached graph (one per stream and batch) owns its
+    # frame counter
     streams = [torch.cuda.Stream() for _ in range(args.streams)]
     stream = streams[0]
     t = C.Tracker(s.ref, upsample=U, method="ccu", in_dtype="u16", max_batch=BATCH, stream=stream, graphs=True)
+    lat_passes = min(args.steps, 50)                # per-batch latency events for the first passes
 
-    def step(i):
-        b = i % nb
-        lo, hi = b * BATCH, min(n_frames, (b + 1) * BATCH)
-        C.ccst_set_stream(t.ctx, streams[i % len(streams)].cuda_stream)
-        C.ccst_track(t.ctx, frames_dev[lo:hi], hi - lo, 0, outs[lo:hi])
-        return hi - lo
+    def one_pass(ev=None):
+        for b, (lo, hi) in enumerate(bounds):
+            si = streams[b % len(streams)]
+            if ev is not None:
+                ev[b][0].record(si)
+            C.ccst_set_stream(t.ctx, si.cuda_stream)
+            C.ccst_track(t.ctx, frames_dev[lo:hi], hi - lo, 0, outs[lo:hi])
+            if ev is not None:
+                ev[b][1].record(si)
 
+    fma = C.ccst_fp32_fma_peak(stream.cuda_stream)
     with torch.cuda.stream(stream):
-        for i in range(max(args.warmup, nb)):          # warm-up also captures every batch's graph
-            step(i)
+        for _ in range(args.warmup):                # the first pass captures every batch's graph
+            one_pass()
         torch.cuda.synchronize()
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        outs.fill_(0xFF)                            # sentinel: every record must be rewritten
+        stats0 = C.ccst_graph_stats(t.ctx)
+        lat_ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in bounds]
+                  for _ in range(lat_passes)]
         t_begin, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        sizes = []
         clocks = ClockSampler(local)
         clocks.start()
         if world > 1:
@@ -662,10 +732,7 @@ def run_ours(args):
         for st in streams[1:]:
             st.wait_event(t_begin)
         for i in range(args.steps):
-            si = streams[i % len(streams)]
-            starts[i].record(si)
-            sizes.append(step(i))
-            ends[i].record(si)
+            one_pass(lat_ev[i] if i < lat_passes else None)
         for st in streams[1:]:
             e = torch.cuda.Event()
             e.record(st)
@@ -675,23 +742,32 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
         clk = clocks.stop()
-    lat_ms = np.array([starts[i].elapsed_time(ends[i]) for i in range(args.steps)])
+    stats1 = C.ccst_graph_stats(t.ctx)
+    lat_us = np.array([[a.elapsed_time(b) * 1e3 for a, b in row] for row in lat_ev])
+    lat_w = np.array([[hi - lo for lo, hi in bounds]] * lat_passes, dtype=float)
     total_ms = t_begin.elapsed_time(t_end)
     total_ms_max = max_over_ranks(total_ms, world, device="cuda")
-    frames_all = sum(sizes) * world
-    value = frames_all / (total_ms_max / 1e3)
-
-    # roofline of the dominant kernel (FP32 ALU bound). The timed region holds only its
-    # launches (and their counter memsets); with batches in flight on several streams their
-    # event spans overlap, so a launch's average duration is the region's time per launch
-    fpf = flop_per_frame()
-    achieved = fpf * sum(sizes) / (total_ms / 1e3) / 1e12
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    frames_step = n_frames
+    value = frames_step * args.steps * world / (total_ms_max / 1e3)
+    raw = outs.cpu().numpy()
+    unwritten = int(np.sum((raw == 0xFF).all(axis=1)))
+    assert unwritten == 0, f"{unwritten} records not written in the timed region"
     res_all = C.decode(outs)
     flags = res_all["flags"]
 
+    # roofline of the dominant kernel (FP32 ALU bound, the FMA rate measured above). The timed
+    # region holds only its launches (40 graph replays per step); with three batches in flight
+    # their spans overlap, so a launch's average duration is the region's time per launch
+    launches = args.steps * nb
+    ms_per_launch = total_ms / launches
+    fpf_s, fpf_f, fpf_c = scope_flop_per_frame(), flop_per_frame(), scope_contraction_flop()
+    rate = frames_step * args.steps / (total_ms / 1e3)
+    peak = fma["tflops"]
+    peaks = load_peaks()
+    tensor_peak = peaks.get("bf16_tflops")
+
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
-    e2e_steps = 0 if args.no_e2e else min(args.steps, 2 * nb)
+    e2e_steps = 0 if args.no_e2e else args.steps
     pinned_t = torch.from_numpy(s.frames.view(np.int16)).pin_memory()
     pinned = pinned_t.numpy().view(np.uint16)
     # pipelined: up to DEPTH batches in flight, each with its own host result area; a
@@ -700,64 +776,83 @@ def run_ours(args):
     host_outs = [torch.empty((BATCH * 24,), dtype=torch.uint8).pin_memory() for _ in range(DEPTH + 1)]
     host_views = [h.numpy().view(C.RESULT_DTYPE) for h in host_outs]
 
-    def e2e_run(steps):
-        pending, done_frames = [], 0
-        for i in range(steps):
-            b = i % nb
-            lo, hi = b * BATCH, min(n_frames, (b + 1) * BATCH)
-            pending.append(C.ccst_submit_host(t.ctx, pinned[lo:hi], hi - lo, 0, host_views[i % (DEPTH + 1)]))
-            done_frames += hi - lo
-            if len(pending) >= DEPTH:
-                while not C.ccst_poll(t.ctx, pending.pop(0), 100000):
-                    pass
+    def e2e_run(passes):
+        pending, done_frames, i = [], 0, 0
+        for _ in range(passes):
+            for lo, hi in bounds:
+                pending.append(C.ccst_submit_host(t.ctx, pinned[lo:hi], hi - lo, 0, host_views[i % (DEPTH + 1)]))
+                done_frames += hi - lo
+                i += 1
+                if len(pending) >= DEPTH:
+                    while not C.ccst_poll(t.ctx, pending.pop(0), 100000):
+                        pass
         for tk in pending:
             while not C.ccst_poll(t.ctx, tk, 100000):
                 pass
-        return done_frames
+        return done_frames, i
+    C.ccst_set_stream(t.ctx, stream.cuda_stream)
     if e2e_steps:
-        e2e_run(3)
+        e2e_run(1)
     t0 = time.perf_counter()
-    e2e_frames = e2e_run(e2e_steps)
+    e2e_frames, e2e_batches = e2e_run(e2e_steps)
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, device="cuda")
     # the results of the last batch, read back through the pipelined path, match the device path
     if e2e_steps:
-        b_last = (e2e_steps - 1) % nb
-        lo, hi = b_last * BATCH, min(n_frames, (b_last + 1) * BATCH)
-        got = host_views[(e2e_steps - 1) % (DEPTH + 1)][:hi - lo]
+        lo, hi = bounds[-1]
+        got = host_views[(e2e_batches - 1) % (DEPTH + 1)][:hi - lo]
         ref = res_all[lo:hi]
-        assert np.array_equal(got["ipx"], ref["ipx"]) and np.array_equal(got["dx"], ref["dx"]), "e2e results differ"
+        assert got.tobytes() == ref.tobytes(), "e2e results differ"
     e2e = {"value": e2e_frames * world / e2e_s if e2e_frames else None, "unit": "frames/s",
-           "h2d_bytes_per_step": BATCH * H * W * 2, "d2h_bytes_per_step": BATCH * 24,
-           "api": f"ccst_submit_host + ccst_poll (pinned host frames in, host results out; {DEPTH} batches in "
-                  "flight over 4 staging slots and 2 streams, so copies overlap tracking)"}
+           "h2d_bytes_per_step": n_frames * H * W * 2, "d2h_bytes_per_step": n_frames * 24,
+           "api": f"ccst_submit_host + ccst_poll, one step = the {nb} batches of the stream (pinned host frames "
+                  f"in, host results out; {DEPTH} batches in flight over 4 staging slots and 2 streams, so copies "
+                  "overlap tracking)"}
 
     line = {
         "metric": "frames/s and p50/p99 per-frame latency (us) at 128x128, <=1e-3 px vs FP64 oracle",
         "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "p50_us": weighted_percentile(lat_ms * 1e3, sizes, 50), "p99_us": weighted_percentile(lat_ms * 1e3, sizes, 99),
-        "config": {"workload": WORKLOAD,
-                   "global_batch": BATCH * world, "frames_per_rank": n_frames, "upsample": U,
-                   "streams": len(streams),
-                   "parallelism": f"replicas x{world} (independent streams)",
-                   "l2": "inputs larger than L2 (328 MB stream per rank, each step reads a new 8.4 MB slice)"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(),
-                     "kernel": "track_kernel", "flop_per_frame": fpf,
-                     "ms_per_launch": total_ms / args.steps,
-                     "achieved_basis": f"flop/frame x frames / timed region; {len(streams)} batches in flight "
-                                       "on alternating streams, so launch spans overlap",
-                     "peak_basis": "148 SMs x 128 FP32 FMA lanes x 2 x 2032 MHz (nominal max clock)",
-                     "ingest": {"achieved": value / world * (H * W * 2 + 24) / 1e9,
-                                "peak": load_peaks().get("hbm_gbs"), "unit": "GB/s",
-                                "frac": (value / world * (H * W * 2 + 24) / 1e9 / load_peaks()["hbm_gbs"]
-                                         if load_peaks().get("hbm_gbs") else None),
+        "p50_us": weighted_percentile(lat_us.ravel(), lat_w.ravel(), 50),
+        "p99_us": weighted_percentile(lat_us.ravel(), lat_w.ravel(), 99),
+        "latency_basis": "frame-weighted percentiles of each batch's end event - start event on its stream, "
+                         f"first {lat_passes} timed passes, three batches in flight",
+        "config": headline_config(world),
+        "roofline": {"bound": "alu", "achieved": fpf_s * rate / 1e12, "peak": peak, "unit": "TFLOP/s",
+                     "frac": fpf_s * rate / 1e12 / peak, "traffic": profiled_traffic(),
+                     "kernel": "track_kernel", "flop_per_frame": fpf_s, "frames_per_launch": frames_step / nb,
+                     "ms_per_launch": ms_per_launch, "launches_timed": launches,
+                     "achieved_basis": "scope-table flops per frame (17.1 M at 128x128, u=100: FFTs, product and "
+                                       "phase, stage A over all H rows, stage B over the half spectrum) x frames / "
+                                       "timed region (CUDA events on the launching streams)",
+                     "peak_basis": "of measured: FP32 FMA rate of this GPU (ccst_fp32_fma_peak, independent FMA "
+                                   "chains on every SM, best of 3 launches), "
+                                   f"nominal {fma['nominal_tflops']:.1f} TFLOP/s from the device attributes",
+                     "folded": {"flop_per_frame": fpf_f, "achieved": fpf_f * rate / 1e12,
+                                "frac": fpf_f * rate / 1e12 / peak,
+                                "basis": "the flops the kernel's folded formulation performs (Hermitian symmetry "
+                                         "in both contraction stages)"},
+                     "contraction_tensor_pipe": {
+                         "flop_per_frame": fpf_c, "achieved": fpf_c * rate / 1e12,
+                         "peak": tensor_peak / 3 if tensor_peak else None,
+                         "frac": fpf_c * rate / 1e12 / (tensor_peak / 3) if tensor_peak else None,
+                         "basis": "stages A and B run as fp16 hi/lo MMAs (3 products each) on the tensor pipe: "
+                                  "their scope-table flops against the measured dense bf16/fp16 rate / 3 "
+                                  "(the pool's measured bf16 GEMM rate, burst)"},
+                     "ingest": {"achieved": rate * (H * W * 2 + 24) / 1e9, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                                "frac": (rate * (H * W * 2 + 24) / 1e9 / peaks["hbm_gbs"]
+                                         if peaks.get("hbm_gbs") else None),
                                 "basis": "algorithmic HBM bytes per frame (uint16 input + 24-byte record) x "
                                          "frames/s per GPU, against the measured copy bandwidth"}},
+        "fp32_fma_peak": fma,
+        "graphs": {"instantiations": stats1["instantiations"], "distinct_batches": nb,
+                   "instantiated_in_timed_region": stats1["instantiations"] - stats0["instantiations"],
+                   "replays_timed": stats1["replays"] - stats0["replays"]},
+        "records_written": {"frames": n_frames, "unwritten_after_timed_region": unwritten,
+                            "check": "outputs filled with 0xFF before the timed region"},
         "clocks": clk,
         "e2e": e2e,
-        "gpu_launches": args.steps,                     # one tracking kernel per batch
+        "gpu_launches": launches,                       # one tracking kernel per batch
         "guard": {"frames": int(len(flags)), "int": int(np.sum((flags & C.R_INT_GUARD) != 0)),
                   "sub": int(np.sum((flags & C.R_SUB_GUARD) != 0)), "df64": int(np.sum((flags & C.R_DF64) != 0)),
                   "overflow": int(np.sum((flags & C.R_OVERFLOW) != 0))},
@@ -795,13 +890,8 @@ def run_ours(args):
         if rt_res is not None:
             rt_line["cpu_baseline"], rt_line["parity"] = realtime_cpu_baseline(s.frames, rt_res)
         orc, cb = cpu_baseline(s.frames, s.ref)
-        n = len(orc)
-        g = res_all[:n]
-        mism = sum(1 for a, o in zip(g, orc)
-                   if (int(a["ipy"]), int(a["ipx"])) != (o["ipy"], o["ipx"])
-                   or abs(float(a["dx"]) - o["dx32"]) > 1e-3 or abs(float(a["dy"]) - o["dy32"]) > 1e-3)
         line["cpu_baseline"] = cb
-        line["parity"] = {"frames": n, "mismatches": mism, "tolerance_px": 1e-3}
+        line["parity"] = parity_with_ties(res_all[:len(orc)], orc)
     t.close()
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -811,6 +901,8 @@ def run_ours(args):
 
 # ---------------------------------------------------------------- reference arm (the oracle)
 def run_reference(args):
+    """The FP64 oracle as it stands, on the host cores, on the headline's config: each step
+    tracks a bounded sample of the step's 10,000 frames (the same frames every step)."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
@@ -824,7 +916,7 @@ def run_reference(args):
     cores = os.cpu_count() or 1
     budget = 150.0
     per_step = int(max(1, budget * cores / ((args.steps + args.warmup) * max(t1, 1e-3))))
-    per_step = min(per_step, BATCH)
+    per_step = min(per_step, N_FRAMES)
     use_pool = per_step >= cores
     pool = None
     if use_pool:
@@ -832,31 +924,30 @@ def run_reference(args):
             os.environ[k] = "1"
         pool = mp.get_context("spawn").Pool(cores)
         pool.map(_oracle_chunk, [(s.frames[:1], s.ref)] * cores)
-    nb = (N_FRAMES + BATCH - 1) // BATCH
+    # the sample: frames spread evenly over the stream
+    pick = np.linspace(0, N_FRAMES - 1, per_step).astype(int)
+    fr = s.frames[pick]
 
-    def step(i):
-        b = i % nb
-        fr = s.frames[b * BATCH: b * BATCH + per_step]
+    def step():
         if pool:
             pool.map(_oracle_chunk, [(c, s.ref) for c in np.array_split(fr, cores) if len(c)])
         else:
             oracle.track_batch(fr, s.ref, u=U)
         return len(fr)
 
-    for i in range(args.warmup):
-        step(i)
-    lat = []
-    sizes = []
+    for _ in range(args.warmup):
+        step()
+    lat, sizes = [], []
     t_all = time.perf_counter()
-    for i in range(args.steps):
+    for _ in range(args.steps):
         t0 = time.perf_counter()
-        sizes.append(step(i))
+        sizes.append(step())
         lat.append(time.perf_counter() - t0)
     dt = time.perf_counter() - t_all
     if pool:
         pool.close()
     value = sum(sizes) / dt
-    sample = (f"{per_step} frame(s) of each 256-frame batch per step, FP64 numpy oracle, "
+    sample = (f"{per_step} of the 10000 frames per step (evenly spaced), FP64 numpy oracle (naive separable DFTs), "
               f"{cores if use_pool else 1} process(es)")
     print(json.dumps({
         "impl": "reference",
@@ -864,9 +955,9 @@ def run_reference(args):
         "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "p50_us": float(np.median(lat)) * 1e6, "p99_us": float(np.percentile(lat, 99)) * 1e6,
-        "config": {"workload": WORKLOAD, "global_batch": BATCH, "frames_per_step_timed": per_step,
-                   "upsample": U, "parallelism": "host cores (a bounded sample of each batch per step)"},
+        "p50_us": float(np.median(lat)) * 1e6 / max(1, per_step), "p99_us": float(np.percentile(lat, 99)) * 1e6 / max(1, per_step),
+        "latency_basis": "time per sample step / frames in it",
+        "config": headline_config(world),
         "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores if use_pool else 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -876,8 +967,8 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4000)
-    ap.add_argument("--warmup", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
