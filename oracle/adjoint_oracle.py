@@ -23,7 +23,7 @@ theta: dL/dtheta = w . d(grad_s f)/dtheta. With a and b:
 
 (w.k'/N = w_y ky'/H + w_x kx'/W), then the chain rule to pixels: CC-U dL/dI = dL/da,
 dL/dE = dL/db; CC-SN dL/dI = 2 (I + eps) dL/da, dL/dE = -dL/db / (E + eps)^2.
-The sums over k use numpy's FFT as a library step.
+The sums over k use ``cc_oracle``'s naive separable DFTs (plain matrix products).
 
 Coordinates are (y, x) throughout; records carry (dy, dx).
 Pins: ``tests/test_adjoint_oracle_pins.py``.
@@ -70,7 +70,7 @@ def continuous_peak(frame, ref, s0, method: int = co.CC_U, eps: float = 200.0, t
     Returns s (y, x), the Hessian there, the number of steps and whether it converged
     (step below tol) to an extremum of the method's kind within 1 px of s0."""
     a, b = operands(frame, ref, method, eps)
-    X = np.fft.fft2(a) * np.conj(np.fft.fft2(b))
+    X = co.dft2(a) * np.conj(co.dft2(b))
     s = np.array(s0, dtype=np.float64)
     ok, it = False, 0
     for it in range(1, max_iter + 1):
@@ -97,10 +97,10 @@ def vjp(frame, ref, s, hess, g, method: int = co.CC_U, eps: float = 200.0):
     ky, kx = _freqs(H, W)
     w = -np.linalg.solve(hess, np.asarray(g, dtype=np.float64))
     m = 2j * np.pi * (w[0] * ky + w[1] * kx) * np.exp(2j * np.pi * (ky * s[0] + kx * s[1]))
-    Za = m * np.conj(np.fft.fft2(b))
-    Zb = m * np.fft.fft2(a)
-    dLda = np.real(np.fft.fft2(Za)) / (H * W)          # sum_k Za(k) e^{-2 pi i k.r/N}
-    dLdb = np.real(np.fft.ifft2(Zb))                   # (1/HW) sum_k Zb(k) e^{+2 pi i k.r/N}
+    Za = m * np.conj(co.dft2(b))
+    Zb = m * co.dft2(a)
+    dLda = np.real(co.dft2(Za)) / (H * W)          # sum_k Za(k) e^{-2 pi i k.r/N}
+    dLdb = np.real(co.idft2(Zb))                   # (1/HW) sum_k Zb(k) e^{+2 pi i k.r/N}
     if method == co.CC_SN:
         return 2.0 * (I + eps) * dLda, -dLdb / (E + eps) ** 2
     return dLda, dLdb

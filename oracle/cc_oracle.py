@@ -11,8 +11,12 @@ What it computes, per frame, in float64, as plainly as possible:
    1/E_SN) with I' = I + eps and E_SN = E + eps, Eqs. (5)-(7).
 2. The integer cross-correlation surface c(s) = sum_r a((r+s) mod N) b(r)
    (left-hand side of Eq. (4) / Eq. (7), periodic boundaries as in Eq. (1)),
-   by direct summation, or through numpy's FFT (right-hand side of Eq. (4));
-   the pin tests check that both routes agree.
+   by direct summation, or as the right-hand side of Eq. (4) with naive
+   separable DFTs: F[a] = D_H a D_W (a row DFT then a column DFT, each a plain
+   matrix product with the N x N DFT matrix, no FFT), X = F[a] conj(F[b]), and
+   the naive inverse DFT of X. The DFT matrices' angle indices k n are reduced
+   mod N exactly in integers. The pin tests check that the two routes agree, and
+   check the DFT against numpy's FFT as an independent library.
 3. The integer peak: argmax of c for CC-U, argmin for CC-SN (the chi^2
    minimiser of Eq. (6)); ties go to the lowest row-major index; each axis is
    wrapped to (-ceil(N/2), floor(N/2)].
@@ -26,21 +30,24 @@ What it computes, per frame, in float64, as plainly as possible:
    index on ties) gives d = p + offset; ``peak`` is the surface value there, in
    the units of the direct sum (it equals c(p) at offset 0).
 
-Readings of the paper taken here (each is listed with its reason in the design
-notes of the repository): the displacement reported is the motion d of the
-frame content, frame(r) ~ ref(r - d), i.e. the shift s of the maximum of
-c(s) = sum_r I(r+s) E(r); CC-SN takes the minimum of Eq. (7) because that
-minimises Eq. (6); the grid has M = ceil(1.5 u) points with offsets
-(j - floor(M/2))/u; no windowing or mean subtraction is applied.
+Readings of the paper taken here: the displacement reported is the motion d of
+the frame content, frame(r) ~ ref(r - d), i.e. the shift s of the maximum of
+c(s) = sum_r I(r+s) E(r) (Eq. (1)'s r0 is -d); CC-SN takes the minimum of
+Eq. (7) because that minimises Eq. (6) (the text says maximum, which on a
+noise-free shifted spot lands far from the shift); the grid has M = ceil(1.5 u)
+points with offsets (j - floor(M/2))/u (the paper's u = 256 gives its 384 x 384);
+no windowing or mean subtraction is applied (the paper names none).
 
 Every function below is pinned by tests in ``tests/test_oracle_pins.py``
 against values fixed by the paper or by mathematics (exact integer shifts,
 sign flip on swapping the images, noise-free sub-pixel Gaussian spots, the
-direct-sum vs FFT identity, the Dirichlet-kernel brute force on tiny images,
+direct-sum vs naive-DFT identity, the naive DFT vs numpy's FFT, the
+Dirichlet-kernel brute force on tiny images,
 the Poisson Cramer-Rao bound).
 """
 from __future__ import annotations
 
+import functools
 import math
 
 import numpy as np
@@ -98,14 +105,44 @@ def cc_surface_direct(a, b) -> np.ndarray:
     return c
 
 
+@functools.lru_cache(maxsize=64)
+def dft_matrix(N: int, sign: int = -1) -> np.ndarray:
+    """D[k, n] = exp(sign 2 pi i k n / N), k, n = 0..N-1 (complex128, symmetric).
+
+    The angle index k n is reduced mod N exactly in integers before the trigonometric
+    call, so every entry is cos/sin of 2 pi m / N with 0 <= m < N."""
+    k = np.arange(N, dtype=np.int64)
+    m = np.mod(np.outer(k, k), N)
+    ang = (2.0 * math.pi / N) * m.astype(np.float64)
+    D = np.cos(ang) + (1j * sign) * np.sin(ang)
+    D.setflags(write=False)
+    return D
+
+
+def dft2(a) -> np.ndarray:
+    """F[a](k) = sum_n a(n) e^{-2 pi i (ky ny / H + kx nx / W)}: the naive separable DFT,
+    a row DFT (a D_W) then a column DFT (D_H (.)), each a plain matrix product."""
+    a = np.asarray(a)
+    H, W = a.shape
+    return dft_matrix(H, -1) @ (a @ dft_matrix(W, -1))
+
+
+def idft2(X) -> np.ndarray:
+    """F^-1[X](n) = (1/HW) sum_k X(k) e^{+2 pi i (ky ny / H + kx nx / W)}, naive and separable."""
+    X = np.asarray(X)
+    H, W = X.shape
+    return (dft_matrix(H, +1) @ (X @ dft_matrix(W, +1))) / (H * W)
+
+
 def product_spectrum(a, b) -> np.ndarray:
-    """X = F[a] (x) conj(F[b]): the element-wise product of Eq. (4) / Eq. (7), complex128."""
-    return np.fft.fft2(np.asarray(a, np.float64)) * np.conj(np.fft.fft2(np.asarray(b, np.float64)))
+    """X = F[a] (x) conj(F[b]): the element-wise product of Eq. (4) / Eq. (7), complex128,
+    with naive DFTs."""
+    return dft2(np.asarray(a, np.float64)) * np.conj(dft2(np.asarray(b, np.float64)))
 
 
-def cc_surface_fft(a, b) -> np.ndarray:
-    """c = F^-1[F[a] (x) conj(F[b])]: right-hand side of Eq. (4), via numpy's FFT."""
-    return np.real(np.fft.ifft2(product_spectrum(a, b)))
+def cc_surface_dft(a, b) -> np.ndarray:
+    """c = F^-1[F[a] (x) conj(F[b])]: right-hand side of Eq. (4), with naive DFTs."""
+    return np.real(idft2(product_spectrum(a, b)))
 
 
 def wrap_shift(p: int, N: int) -> int:
@@ -120,7 +157,9 @@ def extremum_index(values: np.ndarray, sense: int) -> int:
 
 
 def top2_margin(values: np.ndarray, sense: int) -> float:
-    """|best - second best| of a surface (0 if it has one element)."""
+    """best - second best of a surface in the extremum's sense (sense=+1: largest minus the
+    next largest value; sense=-1: next smallest minus smallest). Repeated values count
+    separately, so an exact tie gives 0; a one-element surface gives inf."""
     v = np.sort(np.asarray(values).ravel() * sense)
     return float(v[-1] - v[-2]) if v.size > 1 else math.inf
 
@@ -153,7 +192,7 @@ def upsampled_cc(X: np.ndarray, py: int, px: int, u: int) -> np.ndarray:
 
 
 def track_one(frame, ref, u: int = 100, method: int = CC_U, eps: float = 200.0,
-              integer_route: str = "fft") -> dict:
+              integer_route: str = "dft") -> dict:
     """Displacement of one frame against the reference (Sec. II-III), all in float64.
 
     Returns a dict with dx, dy (float64 and their float32 roundings), peak, the
@@ -166,8 +205,10 @@ def track_one(frame, ref, u: int = 100, method: int = CC_U, eps: float = 200.0,
     X = product_spectrum(a, b)
     if integer_route == "direct":
         c = cc_surface_direct(a, b)
+    elif integer_route == "dft":
+        c = np.real(idft2(X))
     else:
-        c = np.real(np.fft.ifft2(X))
+        raise ValueError("integer_route must be 'dft' or 'direct'")
     p = extremum_index(c, sense)
     py, px = wrap_shift(p // W, H), wrap_shift(p % W, W)
     cu = upsampled_cc(X, py, px, u)

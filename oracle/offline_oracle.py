@@ -32,7 +32,7 @@ def aligned_mean(frames, disp, off: float = 0.0) -> np.ndarray:
     frames = np.asarray(frames, dtype=np.float64)
     acc = np.zeros(frames.shape[1:], dtype=np.complex128)
     for f, (dy, dx) in zip(frames, np.asarray(disp, dtype=np.float64)):
-        acc += rt.shift_spectrum(np.fft.fft2(f + off), dy, dx)
+        acc += rt.shift_spectrum(co.dft2(f + off), dy, dx)
     return acc / len(frames)
 
 
@@ -43,10 +43,10 @@ def offline_track(frames, u: int = 100, passes: int = 5, method: int = co.CC_U, 
     against E_n, refs[n] the image E_n, for n = 0 .. passes."""
     frames = np.asarray(frames, dtype=np.float64)
     off = eps if method == co.CC_SN else 0.0
-    FE = np.fft.fft2(frames[0] + off)
+    FE = co.dft2(frames[0] + off)
     results, refs = [], []
     for n in range(passes + 1):
-        E = np.real(np.fft.ifft2(FE)) - off
+        E = np.real(co.idft2(FE)) - off
         recs = co.track_batch(frames, E, u, method, eps)
         results.append(recs)
         refs.append(E)

@@ -14,10 +14,12 @@ What it computes, in float64:
    F[E_i] = a0 F[I_i(r + d_i)] + b1 F[E_{i-1}], with a0 = 1 - exp(-T/tau) and
    b1 = exp(-T/tau). Frame i is tracked against E_{i-1} (``cc_oracle.track_one``) before E is
    updated with it. Frame 0 defines E_0 and is not tracked.
-   For CC-SN the paper substitutes I -> I'^2 and E -> 1/E. This oracle filters
-   E' = E + eps on the aligned I' = I + eps and forms the operand 1/E' from it (the
-   reading is recorded in the design notes). So the CC-SN reference passed to
-   ``track_one`` is E' - eps.
+   For CC-SN the paper substitutes I -> I'^2 and E -> 1/E, and never says how eps
+   enters the reference. This oracle filters E' = E + eps on the aligned I' = I + eps
+   and forms the operand 1/E' from it: averaging I'^2 instead would give an image in the
+   units of I^2, not of E, and E' = E + eps is exactly the offset reference the fixed-
+   reference CC-SN uses. So the CC-SN reference passed to ``track_one`` is E' - eps.
+   Spectra are taken with ``cc_oracle``'s naive separable DFTs.
 3. Drift removal, Eq. (10): R_0 = a0 r_0, R_n = a0 r_n + b1 R_{n-1}; output r_n - R_n.
 4. Rate-limited drift removal, Eqs. (11)-(12): dR_n = a0 r_n + (b1 - 1) R_{n-1}. A step
    longer than alpha/u is cut to length alpha/u along dR_n. R_0 follows Eq. (10)'s start,
@@ -58,13 +60,13 @@ def rt_track(frames, u: int = 100, a0: float = 0.05, b1: float | None = None, me
     if b1 is None:
         b1 = 1.0 - a0
     off = eps if method == co.CC_SN else 0.0
-    FE = np.fft.fft2(frames[0] + off)                   # F[E_0] = F[I_0] (I'_0 for CC-SN)
+    FE = co.dft2(frames[0] + off)                   # F[E_0] = F[I_0] (I'_0 for CC-SN)
     out = []
     for i in range(1, len(frames)):
-        E = np.real(np.fft.ifft2(FE)) - off
+        E = np.real(co.idft2(FE)) - off
         r = co.track_one(frames[i], E, u, method, eps)
         out.append(r)
-        FI = np.fft.fft2(frames[i] + off)
+        FI = co.dft2(frames[i] + off)
         FE = a0 * shift_spectrum(FI, r["dy"], r["dx"]) + b1 * FE
     return out
 

@@ -72,12 +72,21 @@ def gpu_run(torch, frames, ref, u, method, g=None, max_batch=256):
     return out
 
 
+def oracle_seed(f, ref64, u, method, rec):
+    """The oracle's own grid peak (dy, dx), from which its Newton iteration starts; the GPU
+    record must match it (integer peak identical, |d| within 1e-3 px)."""
+    o = oracle.track_one(f, ref64, u, method)
+    assert (int(rec["ipy"]), int(rec["ipx"])) == (o["ipy"], o["ipx"]), (rec, o)
+    assert abs(float(rec["dx"]) - o["dx32"]) <= 1e-3 and abs(float(rec["dy"]) - o["dy32"]) <= 1e-3, (rec, o)
+    return (o["dy"], o["dx"])
+
+
 def check(frames, ref, u, method, got, g=None):
     ref64 = ref.astype(np.float64)
     gE_sum = np.zeros_like(ref64)
     for i, f in enumerate(frames.astype(np.float64)):
         rec = got["rec"][i]
-        pk = ad.continuous_peak(f, ref64, (float(rec["dy"]), float(rec["dx"])), method)
+        pk = ad.continuous_peak(f, ref64, oracle_seed(f, ref64, u, method, rec), method)
         assert pk["ok"] and got["status"][i] == 0, (i, pk, got["status"][i])
         assert abs(got["peak"][i, 0] - pk["s"][1]) < 1e-9 and abs(got["peak"][i, 1] - pk["s"][0]) < 1e-9, \
             (i, got["peak"][i], pk["s"])
@@ -153,8 +162,10 @@ def test_autograd_function_matches_oracle(torch):
     t.close()
     gE_sum = np.zeros((64, 64))
     for i in range(8):
-        gdx, gdy = 0.5 + 2 * p[i, 0], -1.5 + 2 * p[i, 1]
-        pk = ad.continuous_peak(frames[i].astype(np.float64), ref.astype(np.float64), (p[i, 1], p[i, 0]))
+        o = oracle.track_one(frames[i].astype(np.float64), ref.astype(np.float64), 100)
+        pk = ad.continuous_peak(frames[i].astype(np.float64), ref.astype(np.float64), (o["dy"], o["dx"]))
+        assert abs(p[i, 0] - pk["s"][1]) < 1e-9 and abs(p[i, 1] - pk["s"][0]) < 1e-9, (p[i], pk["s"])
+        gdx, gdy = 0.5 + 2 * pk["s"][1], -1.5 + 2 * pk["s"][0]
         a, b = ad.vjp(frames[i].astype(np.float64), ref.astype(np.float64), pk["s"], pk["hess"], (gdy, gdx))
         assert np.max(np.abs(gI[i] - a)) <= 2e-6 * np.abs(a).max()
         gE_sum += b

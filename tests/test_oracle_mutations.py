@@ -19,7 +19,11 @@ def _run_pins():
     """Run a fixed selection of pins; return how many failed."""
     checks = [
         pins.test_grid_matches_paper_example,
-        lambda: pins.test_direct_sum_equals_fft_route((12, 8), CC_U),
+        lambda: pins.test_direct_sum_equals_dft_route((12, 8), CC_U),
+        lambda: pins.test_naive_dft_matches_numpy_fft((5, 7)),
+        pins.test_naive_dft_closed_forms,
+        pins.test_top2_margin_hand_built,
+        pins.test_track_one_margins_hand_built,
         lambda: pins.test_surface_is_chi_square_up_to_constants(CC_U),
         lambda: pins.test_surface_is_chi_square_up_to_constants(CC_SN),
         lambda: pins.test_integer_roll_recovered_exactly_ccu(*pins._refs()[1], 7),
@@ -46,7 +50,36 @@ def test_unmutated_oracle_passes_selection():
 
 
 def _m_conj_wrong_operand(a, b):
-    return np.conj(np.fft.fft2(np.asarray(a, float))) * np.fft.fft2(np.asarray(b, float))
+    return np.conj(co.dft2(np.asarray(a, float))) * co.dft2(np.asarray(b, float))
+
+
+def _m_dft_forward_sign(a):
+    a = np.asarray(a)
+    H, W = a.shape
+    return co.dft_matrix(H, +1) @ (a @ co.dft_matrix(W, +1))
+
+
+def _m_dft_index_not_reduced(N, sign=-1):
+    # the angle index taken as k + n instead of k n
+    k = np.arange(N, dtype=np.int64)
+    ang = (2.0 * math.pi / N) * np.add.outer(k, k).astype(np.float64)
+    return np.cos(ang) + (1j * sign) * np.sin(ang)
+
+
+def _m_margin_ignores_sense(values, sense):
+    v = np.sort(np.asarray(values).ravel())
+    return float(v[-1] - v[-2]) if v.size > 1 else math.inf
+
+
+def _m_margin_distinct_values(values, sense):
+    # exact ties merged: a tied surface would report the gap to the next distinct value
+    v = np.unique(np.asarray(values).ravel() * sense)
+    return float(v[-1] - v[-2]) if v.size > 1 else math.inf
+
+
+def _m_margin_best_minus_worst(values, sense):
+    v = np.sort(np.asarray(values).ravel() * sense)
+    return float(v[-1] - v[0]) if v.size > 1 else math.inf
 
 
 def _m_grid_floor(u):
@@ -119,6 +152,11 @@ def _m_direct_roll_sign(a, b):
 
 MUTANTS = {
     "conj_on_wrong_operand": ("product_spectrum", _m_conj_wrong_operand),
+    "dft_forward_sign": ("dft2", _m_dft_forward_sign),
+    "dft_index_not_reduced": ("dft_matrix", _m_dft_index_not_reduced),
+    "margin_ignores_sense": ("top2_margin", _m_margin_ignores_sense),
+    "margin_merges_ties": ("top2_margin", _m_margin_distinct_values),
+    "margin_best_minus_worst": ("top2_margin", _m_margin_best_minus_worst),
     "grid_floor_not_ceil": ("grid_size", _m_grid_floor),
     # (moving the Nyquist bin of an even size to +N/2 on both axes is not a mistake:
     #  the real part of the interpolant does not change, so it is not planted here)

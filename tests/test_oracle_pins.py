@@ -1,7 +1,8 @@
 """Pins of the FP64 oracle to facts fixed by the paper and by mathematics.
 
 None of these re-types the oracle's formulas: each compares it with an
-independent route (direct sum vs FFT, Dirichlet-kernel brute force), an exact
+independent route (direct sum vs naive DFT, naive DFT vs numpy's FFT,
+Dirichlet-kernel brute force), an exact
 answer (integer rolls, noise-free band-limited spots, the sign flip of Eq. (4)
 under swapping the images), a value the paper prints (the u = 256 grid), or a
 statistical bound (the Poisson Cramer-Rao limit of Sec. IV).
@@ -51,21 +52,93 @@ def test_signed_frequency_convention():
     assert np.array_equal(oracle.signed_freq(12), np.fft.fftfreq(12, 1 / 12).astype(int))
 
 
+# ---------------------------------------------------------------- the naive DFT
+@pytest.mark.parametrize("shape", [(8, 8), (5, 7), (12, 9), (48, 96), (128, 128)])
+def test_naive_dft_matches_numpy_fft(shape):
+    # an independent library (numpy's FFT) as the cross-check of the naive separable DFT
+    rng = np.random.default_rng(11)
+    a = rng.normal(size=shape)
+    X = oracle.dft2(a)
+    F = np.fft.fft2(a)
+    assert np.max(np.abs(X - F)) <= 1e-12 * np.abs(F).max()
+    Z = rng.normal(size=shape) + 1j * rng.normal(size=shape)
+    assert np.max(np.abs(oracle.idft2(Z) - np.fft.ifft2(Z))) <= 1e-12 * np.abs(Z).max()
+
+
+def test_naive_dft_closed_forms():
+    # DFT of a unit impulse at n0 is exp(-2 pi i k.n0/N); of a constant, N delta(k)
+    H, W = 6, 10
+    d = np.zeros((H, W))
+    d[2, 7] = 1.0
+    ky = np.arange(H)[:, None]
+    kx = np.arange(W)[None, :]
+    want = np.exp(-2j * np.pi * (ky * 2 / H + kx * 7 / W))
+    assert np.max(np.abs(oracle.dft2(d) - want)) <= 1e-14
+    c = oracle.dft2(np.full((H, W), 3.0))
+    assert abs(c[0, 0] - 3.0 * H * W) <= 1e-12 and np.max(np.abs(c.ravel()[1:])) <= 1e-12
+    # round trip
+    a = np.random.default_rng(1).normal(size=(H, W))
+    assert np.max(np.abs(oracle.idft2(oracle.dft2(a)) - a)) <= 1e-14
+
+
 # ---------------------------------------------------------------- Eq. (4) identity
 @pytest.mark.parametrize("shape", [(8, 8), (12, 8), (6, 10), (16, 16)])
 @pytest.mark.parametrize("method", [CC_U, CC_SN])
-def test_direct_sum_equals_fft_route(shape, method):
+def test_direct_sum_equals_dft_route(shape, method):
     rng = np.random.default_rng(7)
     I = rng.poisson(100.0, size=shape).astype(float)
     E = rng.uniform(5.0, 500.0, size=shape)
     a, b, _ = oracle.surface_operands(I, E, method, 200.0)
     cd = oracle.cc_surface_direct(a, b)
-    cf = oracle.cc_surface_fft(a, b)
+    cf = oracle.cc_surface_dft(a, b)
     scale = np.sum(np.abs(a)) * np.sum(np.abs(b))
     assert np.max(np.abs(cd - cf)) <= 1e-13 * scale
     # a shift moves the surface by the same shift (translation covariance)
     cs = oracle.cc_surface_direct(np.roll(a, (2, 3), axis=(0, 1)), b)
     assert np.allclose(cs, np.roll(cd, (2, 3), axis=(0, 1)), rtol=0, atol=1e-12 * scale)
+
+
+def test_direct_sum_on_stream_frames_128():
+    # the headline size: the O(H^2 W^2) direct sum of Eq. (4)'s left-hand side on two
+    # frames of the 128 x 128 stream agrees with the naive-DFT route, and both integer
+    # routes give the same record
+    s = synth.frame_stream(seed=0, n=10_000, count=120)
+    ref = s.ref.astype(float)
+    for i in (0, 119):
+        f = s.frames[i].astype(float)
+        a, b, _ = oracle.surface_operands(f, ref)
+        cd = oracle.cc_surface_direct(a, b)
+        cf = oracle.cc_surface_dft(a, b)
+        assert np.max(np.abs(cd - cf)) <= 1e-13 * np.sum(np.abs(a)) * np.sum(np.abs(b))
+        r1 = oracle.track_one(f, ref, u=100, integer_route="direct")
+        r2 = oracle.track_one(f, ref, u=100)
+        assert (r1["ipy"], r1["ipx"], r1["jy"], r1["jx"]) == (r2["ipy"], r2["ipx"], r2["jy"], r2["jx"])
+
+
+# ---------------------------------------------------------------- top-2 margin
+def test_top2_margin_hand_built():
+    v = np.array([[5.0, 3.0], [7.0, 6.75]])
+    assert oracle.top2_margin(v, +1) == 0.25            # 7 - 6.75
+    assert oracle.top2_margin(v, -1) == 2.0             # 5 - 3 (minimum sense)
+    assert oracle.top2_margin(np.array([4.0, 9.0, 9.0]), +1) == 0.0     # an exact tie
+    assert oracle.top2_margin(np.array([4.0, 4.0, 9.0]), -1) == 0.0
+    assert oracle.top2_margin(np.array([2.5]), +1) == math.inf
+
+
+def test_track_one_margins_hand_built():
+    # with E a unit impulse at the origin the integer surface is the frame itself
+    # (c(s) = sum_r I(r+s) delta(r) = I(s)), so its top-2 gap is known: 0.5. track_one
+    # reports it divided by sum|X| / HW with X = F[I] (F[delta] = 1)
+    H, W = 8, 8
+    I = np.full((H, W), 2.0)
+    I[1, 2] = 10.0
+    I[5, 6] = 9.5
+    E = np.zeros((H, W))
+    E[0, 0] = 1.0
+    r = oracle.track_one(I, E, u=4)
+    scale = np.sum(np.abs(np.fft.fft2(I))) / (H * W)
+    assert (r["ipy"], r["ipx"]) == (1, 2)
+    assert abs(r["int_margin"] - 0.5 / scale) <= 1e-12 * (0.5 / scale)
 
 
 @pytest.mark.parametrize("method", [CC_U, CC_SN])
@@ -230,7 +303,7 @@ def test_upsampled_grid_equals_dirichlet_brute_force(shape, u, method):
     E = rng.uniform(10.0, 100.0, size=shape)
     a, b, sense = oracle.surface_operands(I, E, method, 200.0)
     X = oracle.product_spectrum(a, b)
-    c = oracle.cc_surface_fft(a, b)
+    c = oracle.cc_surface_direct(a, b)
     idx = oracle.extremum_index(c, sense)
     py, px = oracle.wrap_shift(idx // W, H), oracle.wrap_shift(idx % W, W)
     cu = oracle.upsampled_cc(X, py, px, u)
