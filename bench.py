@@ -483,6 +483,119 @@ def adjoint_cpu_baseline(C, torch, stream, p, sd):
              "min_ratio": float(ratio.min())})
 
 
+REFINE_CAL = 512                 # template refinement leg: calibration frames (known shifts)
+REFINE_TEST = 512                # held-out frames
+REFINE_STEPS = 30
+REFINE_STEP_REL = 0.01
+REFINE_ORACLE = (16, 3)          # oracle parity sample: frames, steps
+
+
+def refine_workload(seed=0, n_cal=REFINE_CAL, n_test=REFINE_TEST, H=64, W=64, sigma=3.0, amp=1000.0, bg=10.0):
+    """64 x 64 FP32 spot frames (sigma 3, peak 1000, bg 10, Poisson): calibration frame 0 at
+    the centre (it is also the noisy starting template E_0 = I_0), the other calibration and
+    all held-out frames at shifts uniform in [-2, 2]^2 px."""
+    from paper_2310_08770_b300 import synth
+    rng = np.random.default_rng(seed)
+    d = rng.uniform(-2.0, 2.0, size=(n_cal + n_test, 2))
+    d[0] = 0.0
+    fr = np.array([rng.poisson(synth.gaussian_spot(H, W, H / 2 + p[1], W / 2 + p[0], sigma, amp, bg))
+                   for p in d]).astype(np.float32)
+    truth = synth.gaussian_spot(H, W, H / 2, W / 2, sigma, amp, bg).astype(np.float32)
+    return fr[:n_cal], d[:n_cal], fr[n_cal:], d[n_cal:], truth
+
+
+def refine_leg(C, torch, stream):
+    """Reference refinement by the adjoint (ccst_refine_reference) against the paper's Eq. (8)
+    offline mean, judged by the displacement error on held-out frames."""
+    fc, dc, ft, dt, truth = refine_workload()
+    fc_d, ft_d = torch.from_numpy(fc).cuda(), torch.from_numpy(ft).cuda()
+    dc_d = torch.from_numpy(dc).cuda()
+    n_cal, n_test = len(fc), len(ft)
+    ev = lambda: torch.cuda.Event(enable_timing=True)          # noqa: E731
+
+    def test_error(t):
+        rec = t.empty_results(n_test)
+        peak = torch.empty((n_test, 2), dtype=torch.float64, device="cuda")
+        status = torch.empty((n_test,), dtype=torch.int32, device="cuda")
+        C.ccst_track(t.ctx, ft_d, n_test, 0, rec)
+        C.ccst_peak_continuous(t.ctx, ft_d, n_test, 0, rec, peak, status)
+        C.ccst_sync(t.ctx)
+        r = C.decode(rec)
+        grid = np.stack([r["dx"], r["dy"]], 1).astype(np.float64)
+        pk = peak.cpu().numpy()
+        return {"rms_px": float(np.sqrt(np.mean(np.sum((grid - dt) ** 2, 1)))),
+                "rms_continuous_px": float(np.sqrt(np.mean(np.sum((pk - dt) ** 2, 1)))),
+                "bias_px": [float(x) for x in np.mean(grid - dt, 0)]}
+
+    def tracker(ref):
+        return C.Tracker(ref, upsample=U, method="ccu", in_dtype="f32", max_batch=n_cal, stream=stream)
+
+    out = {"workload": f"64x64 FP32 spot frames (sigma 3, peak 1000, bg 10, Poisson), {n_cal} calibration frames "
+                       f"(frame 0 at the centre, the rest shifted U(-2,2)^2 px, shifts known) and {n_test} held-out "
+                       f"frames; u={U}, CC-U; noisy start E_0 = calibration frame 0; {REFINE_STEPS} steps, first "
+                       f"step {REFINE_STEP_REL} |E|",
+           "loss": "mean over calibration frames of |s* - d|^2 (continuous peak), px^2",
+           "metric": "rms displacement error on the held-out frames (grid records and continuous peaks)"}
+    with torch.cuda.stream(stream):
+        t = tracker(truth)
+        out["noise_free_template"] = test_error(t)
+        t.close()
+        t = tracker(fc[0])
+        out["noisy_start"] = test_error(t)
+        hist = torch.empty((REFINE_STEPS + 1, 2), dtype=torch.float64, device="cuda")
+        C.ccst_refine_reference(t.ctx, fc_d, n_cal, 0, dc_d, 1, REFINE_STEP_REL, hist)     # warm-up
+        t.close()
+        t = tracker(fc[0])
+        a, b = ev(), ev()
+        a.record(stream)
+        C.ccst_refine_reference(t.ctx, fc_d, n_cal, 0, dc_d, REFINE_STEPS, REFINE_STEP_REL, hist)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        h = hist.cpu().numpy()
+        out["adjoint_from_noisy_start"] = test_error(t)
+        out["adjoint_from_noisy_start"].update({"loss_first": float(h[0, 0]), "loss_last_accepted": float(
+            min(h[:, 0])), "rejected_steps": int(np.sum(np.diff(h[:, 1]) < 0)), "ms_total": ms,
+            "ms_per_step": ms / (REFINE_STEPS + 1)})
+        t.close()
+        t = tracker(fc[0])
+        C.ccst_offline_track(t.ctx, fc_d, n_cal, 0, 5, t.empty_results(n_cal))          # Eq. (8), 5 passes
+        out["eq8_offline_mean"] = test_error(t)
+        C.ccst_refine_reference(t.ctx, fc_d, n_cal, 0, dc_d, REFINE_STEPS, REFINE_STEP_REL, hist)
+        h = hist.cpu().numpy()
+        out["adjoint_from_eq8"] = test_error(t)
+        out["adjoint_from_eq8"].update({"loss_first": float(h[0, 0]), "loss_last_accepted": float(min(h[:, 0])),
+                                        "rejected_steps": int(np.sum(np.diff(h[:, 1]) < 0))})
+        t.close()
+    return out
+
+
+def refine_cpu_baseline(C, torch, stream):
+    """The FP64 refinement oracle on a small sample: its rate and parity of the GPU's loss
+    history and template with it."""
+    from oracle import refine_oracle
+    n, steps = REFINE_ORACLE
+    fc, dc, _, _, _ = refine_workload()
+    fc, dc = fc[:n], dc[:n]
+    t = C.Tracker(fc[0], upsample=U, method="ccu", in_dtype="f32", max_batch=n, stream=stream)
+    hist = torch.empty((steps + 1, 2), dtype=torch.float64, device="cuda")
+    E = torch.empty((64, 64), dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        C.ccst_refine_reference(t.ctx, torch.from_numpy(fc).cuda(), n, 0, torch.from_numpy(dc).cuda(), steps,
+                                REFINE_STEP_REL, hist, E)
+        torch.cuda.synchronize()
+    t.close()
+    t0 = time.perf_counter()
+    E_o, h_o = refine_oracle.refine(fc.astype(np.float64), fc[0].astype(np.float64), dc, steps, REFINE_STEP_REL, U)
+    dt = time.perf_counter() - t0
+    h = hist.cpu().numpy()
+    return ({"value": n * (steps + 1) / dt, "unit": "frame-evaluations/s", "cores": 1, "kind": "oracle",
+             "sample": f"first {n} calibration frames, {steps} steps, FP64 refinement oracle, one process"},
+            {"frames": n, "steps": steps, "same_steps": bool(np.array_equal(h[:, 1], h_o[:, 1])),
+             "max_rel_loss": float(np.max(np.abs(h[:, 0] - h_o[:, 0]) / np.abs(h_o[:, 0]))),
+             "max_template_diff_rel": float(np.max(np.abs(E.cpu().numpy() - E_o)) / np.abs(E_o).max())})
+
+
 ROIS_N = 4096                    # uneven-ROI leg
 ROIS_SIDES = (32, 48, 64, 96, 128)   # 48 and 96 run on the general-size (double-float) path
 ROIS_POW2_SIDES = (32, 64, 128)      # the power-of-two kernel alone, for context
@@ -879,12 +992,14 @@ def run_ours(args):
     adj_extra = None
     if world == 1 and not args.no_adjoint:
         line["adjoint"], adj_extra = adjoint_leg(C, torch, stream)
+        line["refine"] = refine_leg(C, torch, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         if rois_extra is not None:
             line["rois"]["cpu_baseline"], line["rois"]["parity"] = rois_cpu_baseline(*rois_extra)
         if adj_extra is not None:
             (line["adjoint"]["cpu_baseline"], line["adjoint"]["parity"],
              line["adjoint"]["cramer_rao"]) = adjoint_cpu_baseline(C, torch, stream, *adj_extra)
+            line["refine"]["cpu_baseline"], line["refine"]["parity"] = refine_cpu_baseline(C, torch, stream)
         if "offline" in line:
             line["offline"]["cpu_baseline"], line["offline"]["parity"] = offline_cpu_baseline(C, torch, s, stream)
         if rt_res is not None:

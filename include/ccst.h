@@ -483,6 +483,49 @@ int ccst_peak_continuous(ccst_ctx* ctx, const void* frames_dev, int64_t n, int64
 int ccst_backward(ccst_ctx* ctx, const void* frames_dev, int64_t n, int64_t pitch_elems,
                   const ccst_result* rec_dev, const float* g_dxdy_dev, float* g_frames_dev, float* g_ref_dev);
 
+/* Set the context's reference from an FP64 image: image_dev is device memory, H x W
+ * doubles, row-major with pitch W, holding E (the template itself, not the CC-SN offset
+ * E + eps: the context adds eps for CC-SN). All resident copies of the reference spectrum
+ * and operand are recomputed from it in the FP64 pipeline of the reference updates
+ * (Sec. III; the same pipeline as ccst_set_reference_frame, with FP64 input). This is
+ * how a caller moves the reference after a gradient step of its own (for example a
+ * torch optimiser on dL/dE from ccst_backward). Power-of-two contexts only.
+ * Stream-ordered. Errors: CCST_E_INVALID (null image), CCST_E_UNSUPPORTED (general
+ * shape, no cooperative launch), CCST_E_NOMEM, CCST_E_CUDA. */
+int ccst_set_reference_image(ccst_ctx* ctx, const double* image_dev);
+
+/* Refinement of the reference template by the adjoint of the displacement. It is not in
+ * the paper, whose own reference refinements are the offline mean of Eq. (8) and the
+ * real-time filter of Eq. (9). Here the template E is fitted to calibration frames whose
+ * displacements d_i are known, by gradient descent on
+ *   L(E) = (1/n) sum_i |s*_i(E) - d_i|^2
+ * over the frames whose continuous peak s* (ccst_peak_continuous) has status 0.
+ * dL/dE comes from ccst_backward with dL/ds*_i = 2 (s*_i - d_i) / n.
+ * Starting from the context's current reference, each evaluation k = 0 .. steps does this:
+ *   1. tracks every frame (ccst_track), then finds s* and L(E_k), then dL/dE;
+ *   2. if L(E_k) exceeds the loss of the last accepted template, rejects E_k: it goes
+ *      back to that template and its gradient, and halves the step h;
+ *      otherwise it accepts E_k;
+ *   3. unless k = steps, takes the step E <- E - h |E|_2 / |dL/dE|_2 dL/dE from the
+ *      accepted template and sets the reference from it (ccst_set_reference_image).
+ * At the end the context's reference is the last accepted template. Arguments:
+ *   frames_dev    device memory, n frames (in_dtype) of H rows pitch_elems apart (0 = W).
+ *   target_dev    device memory, n x 2 doubles, the known (dx, dy) of each frame.
+ *   steps         gradient steps (>= 0); steps + 1 evaluations.
+ *   step_rel      the first step h, relative to |E| (> 0); 0.01 suits 64 x 64 spots.
+ *   hist_dev      device memory, 2 (steps + 1) doubles: for evaluation k, L(E_k) and the
+ *                 step h that produced E_k.
+ *   ref_out_dev   device memory for the final template, H x W doubles, or NULL.
+ * The first call allocates a workspace for n frames (records, peaks, gradients and four
+ * H x W images); a larger n later reallocates it after a stream synchronisation.
+ * Everything runs on the context's stream, with no host synchronisation.
+ * Power-of-two contexts only.
+ * Errors: CCST_E_INVALID (n < 1, steps < 0, step_rel not finite and positive, null
+ * pointers, pitch < W), CCST_E_UNSUPPORTED (general shape), CCST_E_NOMEM, CCST_E_CUDA. */
+int ccst_refine_reference(ccst_ctx* ctx, const void* frames_dev, int64_t n, int64_t pitch_elems,
+                          const double* target_dev, int steps, double step_rel, double* hist_dev,
+                          double* ref_out_dev);
+
 /* Free everything the context owns. NULL is a no-op. Synchronises its stream first. */
 void ccst_destroy(ccst_ctx* ctx);
 

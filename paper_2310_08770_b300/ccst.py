@@ -97,6 +97,10 @@ _SIGS = [
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("ccst_backward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("ccst_set_reference_image", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("ccst_refine_reference", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                             ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                                             ctypes.c_void_p]),
     ("ccst_destroy", None, [ctypes.c_void_p]),
     ("ccst_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("ccst_grid_size", ctypes.c_int, [ctypes.c_void_p]),
@@ -384,6 +388,16 @@ def ccst_peak_continuous(ctx, frames_dev, n, pitch_elems, rec_dev, peak_dev, sta
 def ccst_backward(ctx, frames_dev, n, pitch_elems, rec_dev, g_dxdy_dev, g_frames_dev, g_ref_dev) -> None:
     _check(lib().ccst_backward(ctx, _ptr(frames_dev), int(n), int(pitch_elems), _ptr(rec_dev), _ptr(g_dxdy_dev),
                                _ptr(g_frames_dev), _ptr(g_ref_dev)), ctx)
+
+
+def ccst_set_reference_image(ctx, image_dev) -> None:
+    _check(lib().ccst_set_reference_image(ctx, _ptr(image_dev)), ctx)
+
+
+def ccst_refine_reference(ctx, frames_dev, n, pitch_elems, target_dev, steps, step_rel, hist_dev,
+                          ref_out_dev=None) -> None:
+    _check(lib().ccst_refine_reference(ctx, _ptr(frames_dev), int(n), int(pitch_elems), _ptr(target_dev),
+                                       int(steps), float(step_rel), _ptr(hist_dev), _ptr(ref_out_dev)), ctx)
 
 
 def ccst_destroy(ctx) -> None:

@@ -250,6 +250,7 @@ struct RtArgs {
     int nparts;
     const unsigned* count;      // ... over *count frames
     unsigned* next;             // frame counter of the tracking kernel, zeroed here (or null)
+    int frame_f64;              // kRtStart: `frame` is an FP64 image (pitch in doubles), not in_dtype
 };
 
 constexpr int kRtStart = 0, kRtUpdate = 1, kRtMean = 2;
@@ -330,9 +331,10 @@ __device__ void rt_row_pair_fwd(const Geom& g, const RtArgs& a, int r, dfc* z, c
     const int W = g.W, Wc = g.Wc;
     const df off = df_from_double(a.off);
     for (int x = threadIdx.x; x < W; x += blockDim.x) {
-        const df v0 = df_add(df_make(pixel_f32(a.frame, g.in_dtype, (long long)(2 * r) * a.pitch + x)), off);
-        const df v1 = df_add(df_make(pixel_f32(a.frame, g.in_dtype, (long long)(2 * r + 1) * a.pitch + x)), off);
-        z[brev(x, g.logW)] = dfc{v0, v1};
+        const long long i0 = (long long)(2 * r) * a.pitch + x, i1 = i0 + a.pitch;
+        const df p0 = a.frame_f64 ? df_from_double(((const double*)a.frame)[i0]) : df_make(pixel_f32(a.frame, g.in_dtype, i0));
+        const df p1 = a.frame_f64 ? df_from_double(((const double*)a.frame)[i1]) : df_make(pixel_f32(a.frame, g.in_dtype, i1));
+        z[brev(x, g.logW)] = dfc{df_add(p0, off), df_add(p1, off)};
     }
     __syncthreads();
     fft_r2_passes(z, g.logW, 1, W, 1, tw, g.logNtw, false);
@@ -610,6 +612,19 @@ struct ccst_ctx {
     int off_parts = 0;                // partial sums written by the last accumulation
     int off_max_parts = 0;
     double2* d_adjY = nullptr;        // adjoint: [H][Wc] column-inverse of the summed dL/db spectra
+    // reference refinement by the adjoint (ccst_refine_reference): workspace for `cap` frames
+    struct RefineWs {
+        int64_t cap = 0;
+        Result* rec = nullptr;        // [cap] records of the calibration frames
+        double* peak = nullptr;       // [cap][2] continuous peaks (dx, dy)
+        int32_t* status = nullptr;    // [cap]
+        float* g = nullptr;           // [cap][2] dL/ds*
+        double* E = nullptr;          // [H][W] the template being refined
+        double* Eprev = nullptr;      // [H][W] the last accepted template
+        float* gE = nullptr;          // [H][W] dL/dE at E
+        float* gEprev = nullptr;      // [H][W] dL/dE at Eprev
+        double* scal = nullptr;       // [0] loss at E, [1] step, [2] loss at Eprev, [3] Eprev valid
+    } rf;
     double rt_a0 = 0.0, rt_b1 = 1.0;
     bool rt_on = false;               // ccst_rt_begin has run
     // uneven-ROI batches: size classes (plan 0 = this context's size) and references
@@ -828,6 +843,10 @@ static void free_all(ccst_ctx* c) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& l : c->glane) lane_free(l);
+    void* rfp[] = {c->rf.rec, c->rf.peak, c->rf.status, c->rf.g, c->rf.E, c->rf.Eprev, c->rf.gE, c->rf.gEprev,
+                   c->rf.scal};
+    for (void* p : rfp)
+        if (p) cudaFree(p);
 }
 
 static int gen_track(ccst_ctx* c, const Batch& b, cudaStream_t stream, GenLane& lane, unsigned* counter);
@@ -1474,10 +1493,11 @@ extern "C" int ccst_debug_timeout(ccst_ctx* c, const void* frames_dev, int64_t n
 // ------------------------------------------------------- real-time reference (Sec. III B)
 // One reference update (rt_update) on the context's stream; rec null when starting.
 static int rt_launch(ccst_ctx* c, int mode, const void* frame, long long pitch, ccst_result* rec,
-                     unsigned extra = 0) {
+                     unsigned extra = 0, int frame_f64 = 0) {
     const Geom& g = c->g;
     RtArgs a;
     a.frame = frame;
+    a.frame_f64 = frame_f64;
     a.pitch = pitch;
     a.off = g.method == CCST_CC_SN ? (double)g.eps : 0.0;
     a.mode = mode;
@@ -1541,6 +1561,168 @@ extern "C" int ccst_set_reference_frame(ccst_ctx* c, const void* frame_dev, int6
     CK(c, cudaMemsetAsync(c->d_rtSync, 0, 4 * sizeof(unsigned), c->stream));
     c->rt_seq = 0;
     return rt_launch(c, kRtStart, frame_dev, pitch_elems, nullptr);
+}
+
+extern "C" int ccst_set_reference_image(ccst_ctx* c, const double* image_dev) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if ((rc = not_general(c, "ccst_set_reference_image"))) return rc;
+    if (!image_dev) return fail(c, CCST_E_INVALID, "ccst_set_reference_image: null image");
+    if ((rc = rt_prepare(c))) return rc;
+    CK(c, cudaMemsetAsync(c->d_rtSync, 0, 4 * sizeof(unsigned), c->stream));
+    c->rt_seq = 0;
+    return rt_launch(c, kRtStart, image_dev, c->g.W, nullptr, 0, 1);
+}
+
+// ------------------------------------------- reference refinement by the adjoint
+// The template E is refined by gradient steps on the mean squared error of the continuous
+// peaks of calibration frames with known displacements d_i:
+//   L(E) = (1/n) sum_{i: status 0} |s*_i(E) - d_i|^2,   dL/ds*_i = 2 (s*_i - d_i) / n,
+// dL/dE from the adjoint (ccst_backward). A step is E <- E - h |E| / |dL/dE| dL/dE (2-norms
+// over the pixels). A step whose loss exceeds the last accepted one is undone and h halved.
+
+// Block-wide sum of one double per thread in a fixed order (a shuffle tree per warp, then
+// the warps' sums in warp order); the result is returned to every thread.
+__device__ double refine_block_sum(double v, double* red) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = l < nw ? red[l] : 0.0;
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (l == 0) red[32] = v;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+// E from the reference operand b: CC-U E = b, CC-SN E = 1/b - eps.
+__global__ void refine_init(Geom g, const double* b64, double* E, double* scal, double step) {
+    const int n = g.H * g.W;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        E[i] = g.method == 0 ? b64[i] : 1.0 / b64[i] - (double)g.eps;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        scal[0] = 0.0;
+        scal[1] = step;
+        scal[2] = 0.0;
+        scal[3] = 0.0;
+    }
+}
+
+// Loss at the current template and the upstream gradient of every frame.
+__global__ void __launch_bounds__(256) refine_seed(const double* peak, const int32_t* status, const double* target,
+                                                   long long n, float* g, double* scal) {
+    __shared__ double red[33];
+    double acc = 0.0;
+    const double inv = 1.0 / (double)n;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        float gx = 0.f, gy = 0.f;
+        if (status[i] == 0) {
+            const double ex = peak[2 * i] - target[2 * i], ey = peak[2 * i + 1] - target[2 * i + 1];
+            acc += ex * ex + ey * ey;
+            gx = (float)(2.0 * ex * inv);
+            gy = (float)(2.0 * ey * inv);
+        }
+        g[2 * i] = gx;
+        g[2 * i + 1] = gy;
+    }
+    acc = refine_block_sum(acc, red);
+    if (threadIdx.x == 0) scal[0] = acc * inv;
+}
+
+// Accept the evaluated template (or undo the step and halve it), record the loss and the
+// step that produced it, and take the next step unless this is the last evaluation.
+__global__ void __launch_bounds__(1024) refine_step(int nel, double* E, double* Eprev, const float* gE, float* gEprev,
+                                                    double* scal, double* hist, int k, int last) {
+    __shared__ double red[33];
+    __shared__ int revert;
+    __shared__ double coef;
+    if (threadIdx.x == 0) {
+        const double L = scal[0];
+        hist[2 * k] = L;
+        hist[2 * k + 1] = scal[1];
+        revert = scal[3] != 0.0 && L > scal[2];
+        if (revert) scal[1] *= 0.5;
+        else scal[2] = L;
+        scal[3] = 1.0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nel; i += blockDim.x) {
+        if (revert) E[i] = Eprev[i];
+        else { Eprev[i] = E[i]; gEprev[i] = gE[i]; }
+    }
+    if (last) return;
+    double se = 0.0, sg = 0.0;
+    for (int i = threadIdx.x; i < nel; i += blockDim.x) {
+        const double gv = (double)gEprev[i];
+        se += E[i] * E[i];
+        sg += gv * gv;
+    }
+    se = refine_block_sum(se, red);
+    sg = refine_block_sum(sg, red);
+    if (threadIdx.x == 0) coef = sg > 0.0 ? scal[1] * sqrt(se) / sqrt(sg) : 0.0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nel; i += blockDim.x) E[i] -= coef * (double)gEprev[i];
+}
+
+extern "C" int ccst_refine_reference(ccst_ctx* c, const void* frames_dev, int64_t n, int64_t pitch_elems,
+                                     const double* target_dev, int steps, double step_rel, double* hist_dev,
+                                     double* ref_out_dev) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if ((rc = not_general(c, "ccst_refine_reference"))) return rc;
+    if (n < 1 || steps < 0 || !(step_rel > 0.0) || !std::isfinite(step_rel))
+        return fail(c, CCST_E_INVALID, "ccst_refine_reference: need n >= 1, steps >= 0, finite step_rel > 0");
+    if (!target_dev || !hist_dev) return fail(c, CCST_E_INVALID, "ccst_refine_reference: null target or hist");
+    if ((rc = check_frame(c, frames_dev, &pitch_elems, "ccst_refine_reference"))) return rc;
+    const Geom& g = c->g;
+    const int nel = g.H * g.W;
+    auto& w = c->rf;
+    if (!w.E) {
+        CK(c, cudaMalloc(&w.E, nel * sizeof(double)));
+        CK(c, cudaMalloc(&w.Eprev, nel * sizeof(double)));
+        CK(c, cudaMalloc(&w.gE, nel * sizeof(float)));
+        CK(c, cudaMalloc(&w.gEprev, nel * sizeof(float)));
+        CK(c, cudaMalloc(&w.scal, 4 * sizeof(double)));
+    }
+    if (w.cap < n) {
+        CK(c, cudaStreamSynchronize(c->stream));          // the old buffers may still be in use
+        void* old[] = {w.rec, w.peak, w.status, w.g};
+        for (void* p : old)
+            if (p) cudaFree(p);
+        w.rec = nullptr; w.peak = nullptr; w.status = nullptr; w.g = nullptr;
+        w.cap = 0;
+        CK(c, cudaMalloc(&w.rec, (size_t)n * sizeof(Result)));
+        CK(c, cudaMalloc(&w.peak, (size_t)n * 2 * sizeof(double)));
+        CK(c, cudaMalloc(&w.status, (size_t)n * sizeof(int32_t)));
+        CK(c, cudaMalloc(&w.g, (size_t)n * 2 * sizeof(float)));
+        w.cap = n;
+    }
+    const size_t elem = c->p.in_dtype == CCST_U16 ? 2 : 4;
+    refine_init<<<32, 256, 0, c->stream>>>(g, c->d_b64, w.E, w.scal, step_rel);
+    CK(c, cudaGetLastError());
+    for (int k = 0; k <= steps; ++k) {
+        for (int64_t s = 0; s < n; s += c->p.max_batch) {          // records against the current E
+            const int64_t m = n - s < c->p.max_batch ? n - s : c->p.max_batch;
+            Batch b;
+            const char* f = (const char*)frames_dev + (size_t)s * g.H * pitch_elems * elem;
+            if ((rc = make_batch(c, f, m, pitch_elems, (ccst_result*)(w.rec + s), &b))) return rc;
+            if ((rc = launch(c, b))) return rc;
+        }
+        if ((rc = ccst_peak_continuous(c, frames_dev, n, pitch_elems, (const ccst_result*)w.rec, w.peak, w.status)))
+            return rc;
+        refine_seed<<<1, 256, 0, c->stream>>>(w.peak, w.status, target_dev, (long long)n, w.g, w.scal);
+        CK(c, cudaGetLastError());
+        if ((rc = ccst_backward(c, frames_dev, n, pitch_elems, (const ccst_result*)w.rec, w.g, nullptr, w.gE)))
+            return rc;
+        refine_step<<<1, 1024, 0, c->stream>>>(nel, w.E, w.Eprev, w.gE, w.gEprev, w.scal, hist_dev, k, k == steps);
+        CK(c, cudaGetLastError());
+        if ((rc = ccst_set_reference_image(c, w.E))) return rc;
+    }
+    if (ref_out_dev) CK(c, cudaMemcpyAsync(ref_out_dev, w.E, nel * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    return CCST_OK;
 }
 
 extern "C" int ccst_rt_begin(ccst_ctx* c, const void* frame0_dev, int64_t pitch_elems, double a0, double b1) {
