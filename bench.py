@@ -723,6 +723,48 @@ def serving_leg(C, torch, sides=SERVE_SIDES, seconds=SERVE_SECONDS, slots=4096, 
             "latency": "host clock, submit call to the worker seeing the batch's completion event"}
 
 
+LOAD_RATES_HZ = (5e3, 15e3, 30e3, 100e3, 300e3)
+LOAD_SECONDS = 1.0
+LOAD_POOL = 4096
+LOAD_BUDGET = LOAD_POOL * H * W * 2          # admission arena: 4096 frames of 128 x 128 uint16
+
+
+def load_latency_leg(C, torch, s):
+    """Latency under offered load: one 128 x 128 uint16 camera (frames of the stream) with
+    Poisson arrivals at each rate, through the server twice: served (continuous batching, up
+    to 1024 frames per launch, 4 batches in flight) and plain (one launch per frame, each
+    after the previous one finished: max_batch 1, 1 in flight). Same admission budget, same
+    host-clock latency (submit to the worker seeing the result), same load generator."""
+    pool = np.ascontiguousarray(s.frames[:LOAD_POOL])
+    t = C.Tracker(s.ref, upsample=U, method="ccu", in_dtype="u16")
+    forms = {"served": (1024, 4), "plain": (1, 1)}
+    rows = []
+    try:
+        for rate in LOAD_RATES_HZ:
+            row = {"offered_hz": rate}
+            for name, (mb, depth) in forms.items():
+                srv = C.ccst_server_create_ex(t.ctx, mb, depth, LOAD_BUDGET)
+                try:
+                    C.ccst_server_loadgen(srv, [0], [min(rate, 20e3)], [pool], 0.05, seed=98)     # warm-up
+                    st = C.ccst_server_loadgen(srv, [0], [rate], [pool], LOAD_SECONDS, seed=1)
+                finally:
+                    C.ccst_server_destroy(srv)
+                row[name] = {"frames_per_s": st["completed"] / LOAD_SECONDS,
+                             "refused_fraction": st["rejected"] / max(1, st["submitted"] + st["rejected"]),
+                             "p50_us": st["p50_us"], "p99_us": st["p99_us"], "mean_batch": st["mean_batch"]}
+            rows.append(row)
+    finally:
+        t.close()
+    wins = [r["offered_hz"] for r in rows
+            if r["served"]["p99_us"] < r["plain"]["p99_us"] and r["served"]["frames_per_s"] >= r["plain"]["frames_per_s"]]
+    return {"workload": f"one 128x128 uint16 camera (frames of the stream, pool of {LOAD_POOL}), Poisson arrivals "
+                        f"for {LOAD_SECONDS} s per rate, u={U}, CC-U; admission budget {LOAD_BUDGET >> 20} MiB",
+            "forms": {"served": "continuous batching: up to 1024 frames per launch, 4 batches in flight",
+                      "plain": "one launch per frame, each after the previous finished (max_batch 1, 1 in flight)"},
+            "latency": "host clock, submit call to the worker seeing the frame's completion event",
+            "rates": rows, "served_beats_plain_on_p99_and_rate_at_hz": wins}
+
+
 PLAIN_FRAMES = 1024
 
 
@@ -973,6 +1015,8 @@ def run_ours(args):
     rt_line = rt_res = None
     if world == 1:
         line["plain_per_frame_launch"] = plain_leg(C, torch, s, frames_dev, stream)
+    if world == 1 and not args.no_serving:
+        line["latency_under_load"] = load_latency_leg(C, torch, s)
     if world == 1 and not args.no_realtime:         # the extra legs are single-GPU measurements
         rt_line, rt_res = realtime_leg(C, torch, s, stream, args.rt_frames)
         line["realtime"] = rt_line

@@ -292,21 +292,27 @@ int ccst_autotune(ccst_ctx* ctx, int reps, const ccst_roi* rois, int64_t n_rois,
                   int max_out, int* n_out);
 
 /* ---- Serving: continuous batching of single frames from several cameras.
+ * Not in the paper, which tracks one camera; frames are independent under a fixed
+ * reference (Sec. III), so frames of several cameras can share a launch.
  *
  * A server runs a worker thread over a context. Each camera is a reference of the
- * context (id 0 or from ccst_add_reference): its frames have that reference's size. A
- * submitted frame is copied into one of `slots` frame slots reserved at creation (pinned
- * host memory mapped into the device's address space: the kernel reads each frame in
- * place, with no per-frame copy); a submit without a free slot is refused with
- * CCST_E_BUSY (admission by reserved memory).
+ * context (id 0 or from ccst_add_reference): its frames have that reference's size.
+ * Admission is by memory: a submitted frame is copied into an arena of budget_bytes
+ * (pinned host memory mapped into the device's address space, so the kernels read each
+ * frame in place with no per-frame copy), taking its own size rounded up to 256 bytes.
+ * A submit that does not fit in what admitted frames leave free is refused with
+ * CCST_E_BUSY. So small cameras are not charged the largest camera's size. The device
+ * memory of the in-flight batches (records, work items, general-size scratch) is
+ * allocated at creation, so the budget bounds what admitted frames add.
  * The worker takes everything pending (up to max_batch frames, any cameras and sizes) as
  * one batch on its own stream: the power-of-two ROI kernel for cameras of 16, 32, 64 or
  * 128 px, then the general-size kernel for the others (each ring entry has its own
- * scratch for it). Up to 4 batches are in flight, so frames
- * that arrive while others run are admitted as slots free up and their work overlaps on
- * the device. Each result equals that of the frame tracked alone (the batch changes only
- * which CTA runs it). While a server exists its context must not be used by other calls
- * (nor references added). */
+ * scratch for it). Up to max_in_flight (at most 4) batches are in flight. Frames that
+ * arrive while others run are admitted as memory frees up, and their work overlaps on
+ * the device. With max_batch = 1 and max_in_flight = 1 the server is the plain form:
+ * one launch per frame, each after the previous one has finished. Each result equals
+ * that of the frame tracked alone (the batch changes only which CTA runs it). While a
+ * server exists its context must not be used by other calls (nor references added). */
 typedef struct ccst_server ccst_server;
 
 typedef struct ccst_server_stats {
@@ -315,11 +321,27 @@ typedef struct ccst_server_stats {
     double   mean_batch;                       /* frames per launch                          */
     double   p50_us, p99_us, max_us;           /* submit -> result available (host clock)   */
     int64_t  in_flight;                        /* admitted, not yet completed               */
+    int64_t  bytes_in_flight;                  /* arena bytes held by admitted frames now    */
+    int64_t  max_bytes_in_flight;              /* most held since the last reset             */
+    int64_t  budget_bytes;                     /* the arena's size                           */
 } ccst_server_stats;
 
+typedef struct ccst_server_config {
+    int32_t max_batch;       /* frames per launch, >= 1                                       */
+    int32_t max_in_flight;   /* batches in flight at once, 1 .. 4                            */
+    int64_t budget_bytes;    /* admission arena, >= 256 (rounded up to a multiple of 256)    */
+    uint32_t flags;          /* 0                                                             */
+    int32_t reserved;
+} ccst_server_config;
+
 /* Start a server over ctx (ctx keeps ownership of its references and must outlive it).
- * The frame slots are sized for the largest reference present at creation; a camera
- * added later must not be larger (its submits return CCST_E_INVALID).
+ * A camera whose frame is larger than the budget is refused at submit (CCST_E_INVALID).
+ * Errors: CCST_E_INVALID (bad configuration, no reference usable by ROI batches),
+ * CCST_E_NOMEM, CCST_E_CUDA. */
+int ccst_server_create_ex(ccst_ctx* ctx, const ccst_server_config* cfg, ccst_server** out);
+
+/* The same with a budget of `slots` frames of the largest reference present now, at most
+ * min(max_batch, slots) frames per launch, and 4 batches in flight.
  * Errors: CCST_E_INVALID (slots or max_batch < 1, no reference usable by ROI batches),
  * CCST_E_NOMEM, CCST_E_CUDA. */
 int ccst_server_create(ccst_ctx* ctx, int slots, int max_batch, ccst_server** out);
@@ -327,7 +349,7 @@ int ccst_server_create(ccst_ctx* ctx, int slots, int max_batch, ccst_server** ou
 /* Submit one frame of camera ref_id from host memory (rows pitch_elems apart, 0 = W; copied
  * before the call returns). With ticket non-NULL the result is kept for ccst_server_poll;
  * with NULL it is only counted in the statistics. Thread-safe.
- * Errors: CCST_E_INVALID, CCST_E_BUSY (no free slot: retry later), CCST_E_CUDA. */
+ * Errors: CCST_E_INVALID, CCST_E_BUSY (the budget is full: retry later), CCST_E_CUDA. */
 int ccst_server_submit(ccst_server* srv, int ref_id, const void* frame_host, int64_t pitch_elems,
                        uint64_t* ticket);
 

@@ -45,7 +45,14 @@ class ccst_roi(ctypes.Structure):
 class ccst_server_stats_t(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
                 ("batches", ctypes.c_uint64), ("mean_batch", ctypes.c_double), ("p50_us", ctypes.c_double),
-                ("p99_us", ctypes.c_double), ("max_us", ctypes.c_double), ("in_flight", ctypes.c_int64)]
+                ("p99_us", ctypes.c_double), ("max_us", ctypes.c_double), ("in_flight", ctypes.c_int64),
+                ("bytes_in_flight", ctypes.c_int64), ("max_bytes_in_flight", ctypes.c_int64),
+                ("budget_bytes", ctypes.c_int64)]
+
+
+class ccst_server_config(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_int32), ("max_in_flight", ctypes.c_int32), ("budget_bytes", ctypes.c_int64),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
 
 
 class ccst_tune_result(ctypes.Structure):
@@ -114,6 +121,8 @@ _SIGS = [
     ("ccst_track_rois", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ccst_roi), ctypes.c_int64, ctypes.c_void_p]),
     ("ccst_server_create", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_void_p)]),
+    ("ccst_server_create_ex", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ccst_server_config),
+                                             ctypes.POINTER(ctypes.c_void_p)]),
     ("ccst_server_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                                           ctypes.POINTER(ctypes.c_uint64)]),
     ("ccst_server_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p,
@@ -288,9 +297,16 @@ def ccst_server_create(ctx, slots: int, max_batch: int):
     return out.value
 
 
+def ccst_server_create_ex(ctx, max_batch: int, max_in_flight: int, budget_bytes: int):
+    cfg = ccst_server_config(int(max_batch), int(max_in_flight), int(budget_bytes), 0, 0)
+    out = ctypes.c_void_p()
+    _check(lib().ccst_server_create_ex(ctx, ctypes.byref(cfg), ctypes.byref(out)), ctx)
+    return out.value
+
+
 def ccst_server_submit(srv, ref_id: int, frame_host, pitch_elems: int = 0, keep: bool = True):
     """Submit one host frame (numpy); returns the ticket (keep) or None. Raises CcstError
-    (E_BUSY when no slot is free)."""
+    (E_BUSY when the admission budget is full)."""
     t = ctypes.c_uint64()
     rc = lib().ccst_server_submit(srv, int(ref_id), _ptr(frame_host), int(pitch_elems),
                                   ctypes.byref(t) if keep else None)

@@ -2561,11 +2561,18 @@ extern "C" int ccst_track_rois(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccs
 // (admission control).
 struct ccst_server {
     static constexpr int kRing = 4;
+    static constexpr size_t kAlign = 256;
     struct Req {
-        int ref = 0, slot = 0;
+        int ref = 0;
+        uint64_t vstart = 0;           // the frame's bytes in the arena: virtual offset (see reserve)
         uint64_t ticket = 0;
         bool keep = false;
         std::chrono::steady_clock::time_point t0;
+    };
+    // one reservation of the arena, in reservation order
+    struct Span {
+        uint64_t vstart = 0, vend = 0;
+        bool released = false;
     };
     struct InFlight {
         cudaStream_t st = nullptr;
@@ -2580,22 +2587,56 @@ struct ccst_server {
         bool busy = false;
     };
     ccst_ctx* c = nullptr;
-    int slots = 0, max_batch = 0;
-    size_t slot_bytes = 0, elem = 0;
-    char* h_frames = nullptr;          // pinned, mapped: slot i at h_frames + i * slot_bytes
+    int max_batch = 0, depth = kRing;
+    size_t elem = 0;
+    // Admission arena: `cap` bytes of pinned host memory mapped into the device's address
+    // space (the kernels read each frame in place). A frame takes its own size rounded to
+    // 256 bytes, reserved at the head of a ring in virtual offsets (physical = virtual mod
+    // cap; a frame never straddles the end: the rest of the ring is skipped). Reservations
+    // free in completion order, but the tail only moves past the oldest live one.
+    uint64_t cap = 0, head = 0, tail = 0, max_used = 0;
+    std::deque<Span> spans;
+    char* h_frames = nullptr;
     char* d_frames = nullptr;          // the same memory as the device addresses it
     unsigned* d_counters = nullptr;    // two item counters per ring entry (power-of-two, general)
     InFlight ring[kRing];
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Req> pending;
-    std::vector<int> free_slots;
+    std::atomic<int> npending{0};
     std::unordered_map<uint64_t, std::pair<bool, Result>> results;
     uint64_t next_ticket = 1, submitted = 0, completed = 0, rejected = 0, batches = 0, batched = 0;
     std::vector<float> lat_us;
     int error = 0;
     bool stop = false;
     std::thread worker;
+
+    // Reserve `bytes` (a multiple of kAlign) at the head; false when the budget is full.
+    // Call with mu held.
+    bool reserve(uint64_t bytes, uint64_t* vstart) {
+        uint64_t v = head;
+        const uint64_t off = v % cap;
+        if (off + bytes > cap) v += cap - off;            // skip the end of the ring
+        if (v + bytes - tail > cap) return false;
+        spans.push_back(Span{v, v + bytes, false});
+        head = v + bytes;
+        max_used = std::max(max_used, head - tail);
+        *vstart = v;
+        return true;
+    }
+    // Release the reservation starting at vstart (mu held).
+    void release(uint64_t vstart) {
+        for (auto& sp : spans)
+            if (sp.vstart == vstart) {
+                sp.released = true;
+                break;
+            }
+        while (!spans.empty() && spans.front().released) {
+            tail = spans.front().vend;
+            spans.pop_front();
+        }
+        if (spans.empty()) tail = head;
+    }
 };
 
 // The frame shape of reference `ref`, for either kernel.
@@ -2636,7 +2677,7 @@ static bool server_retire(ccst_server* s, ccst_server::InFlight& b, bool block) 
             const auto& r = b.reqs[i];
             s->lat_us.push_back(std::chrono::duration<float, std::micro>(t1 - r.t0).count());
             if (r.keep) s->results[r.ticket] = {true, b.h_out[i]};
-            s->free_slots.push_back(r.slot);
+            s->release(r.vstart);
             ++s->completed;
         }
     }
@@ -2669,8 +2710,15 @@ static void server_loop(ccst_server* s) {
                 const size_t m = std::min(s->pending.size(), (size_t)s->max_batch);
                 take.assign(s->pending.begin(), s->pending.begin() + m);
                 s->pending.erase(s->pending.begin(), s->pending.begin() + m);
+                s->npending -= (int)m;
             } else if (!any_busy && s->pending.empty()) {
-                s->cv_work.wait_for(lk, std::chrono::milliseconds(10));
+                // idle: poll for a new frame for up to 200 us (a thread wake-up costs tens of
+                // microseconds of latency), then sleep until one is submitted
+                lk.unlock();
+                const auto spin_end = std::chrono::steady_clock::now() + std::chrono::microseconds(200);
+                while (s->npending.load() == 0 && std::chrono::steady_clock::now() < spin_end) std::this_thread::yield();
+                lk.lock();
+                if (s->pending.empty() && !s->stop) s->cv_work.wait_for(lk, std::chrono::milliseconds(10));
                 continue;
             }
         }
@@ -2686,7 +2734,7 @@ static void server_loop(ccst_server* s) {
             const auto& re = c->refs[r.ref];
             int H = 0, W = 0;
             ref_shape(c, r.ref, &H, &W);
-            const char* frame = s->d_frames + (size_t)r.slot * s->slot_bytes;
+            const char* frame = s->d_frames + (size_t)(r.vstart % s->cap);
             if (re.cls >= 0) b.h_items[np++] = RoiItem{frame, (long long)W, i, re.cls, r.ref, 1, 0};
             else b.h_gitems[ng++] = GenItem{frame, (long long)W, i, re.gcls, r.ref};
         }
@@ -2714,7 +2762,7 @@ static void server_loop(ccst_server* s) {
             ++s->batches;
             s->batched += (uint64_t)m;
         }
-        next = (next + 1) % ccst_server::kRing;
+        next = (next + 1) % s->depth;
     }
 }
 
@@ -2734,10 +2782,20 @@ static void server_free(ccst_server* s) {
     if (s->d_counters) cudaFree(s->d_counters);
 }
 
-extern "C" int ccst_server_create(ccst_ctx* c, int slots, int max_batch, ccst_server** out) {
+// Bytes a frame of reference `ref` takes in the admission arena.
+static uint64_t frame_bytes(const ccst_server* s, int ref) {
+    int H = 0, W = 0;
+    ref_shape(s->c, ref, &H, &W);
+    const uint64_t b = (uint64_t)H * W * s->elem;
+    return (b + ccst_server::kAlign - 1) / ccst_server::kAlign * ccst_server::kAlign;
+}
+
+extern "C" int ccst_server_create_ex(ccst_ctx* c, const ccst_server_config* cfg, ccst_server** out) {
     int rc = check_ctx(c);
     if (rc) return rc;
-    if (!out || slots < 1 || max_batch < 1) return fail(c, CCST_E_INVALID, "ccst_server_create: bad arguments");
+    if (!out || !cfg || cfg->max_batch < 1 || cfg->max_in_flight < 1 || cfg->max_in_flight > ccst_server::kRing ||
+        cfg->budget_bytes < (int64_t)ccst_server::kAlign)
+        return fail(c, CCST_E_INVALID, "ccst_server_create_ex: bad configuration");
     *out = nullptr;
     rois_init(c);
     if ((rc = rois_upload(c))) return rc;
@@ -2745,16 +2803,13 @@ extern "C" int ccst_server_create(ccst_ctx* c, int slots, int max_batch, ccst_se
     ccst_server* s = new (std::nothrow) ccst_server();
     if (!s) return fail(c, CCST_E_NOMEM, "ccst_server_create: host allocation failed");
     s->c = c;
-    s->slots = slots;
-    s->max_batch = std::min(max_batch, slots);
+    s->max_batch = cfg->max_batch;
+    s->depth = cfg->max_in_flight;
     s->elem = c->p.in_dtype == CCST_U16 ? 2 : 4;
-    for (int i = 0; i < (int)c->refs.size(); ++i)
-        if (ref_usable(c, i)) {
-            int H = 0, W = 0;
-            ref_shape(c, i, &H, &W);
-            s->slot_bytes = std::max(s->slot_bytes, ((size_t)H * W * s->elem + 255) & ~(size_t)255);
-        }
-    if (s->slot_bytes == 0) {
+    s->cap = ((uint64_t)cfg->budget_bytes + ccst_server::kAlign - 1) / ccst_server::kAlign * ccst_server::kAlign;
+    bool any = false;
+    for (int i = 0; i < (int)c->refs.size(); ++i) any |= ref_usable(c, i);
+    if (!any) {
         delete s;
         return fail(c, CCST_E_INVALID, "ccst_server_create: no reference usable by ROI batches");
     }
@@ -2765,11 +2820,11 @@ extern "C" int ccst_server_create(ccst_ctx* c, int slots, int max_batch, ccst_se
                     std::string("ccst_server_create: ") + cudaGetErrorString(e));
     };
     cudaError_t e;
-    if ((e = cudaHostAlloc(&s->h_frames, (size_t)slots * s->slot_bytes, cudaHostAllocMapped)) != cudaSuccess)
-        return bad(e);
+    if ((e = cudaHostAlloc(&s->h_frames, (size_t)s->cap, cudaHostAllocMapped)) != cudaSuccess) return bad(e);
     if ((e = cudaHostGetDevicePointer((void**)&s->d_frames, s->h_frames, 0)) != cudaSuccess) return bad(e);
     if ((e = cudaMalloc(&s->d_counters, 2 * ccst_server::kRing * sizeof(unsigned))) != cudaSuccess) return bad(e);
-    for (auto& b : s->ring) {
+    for (int k = 0; k < s->depth; ++k) {
+        auto& b = s->ring[k];
         if ((e = cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking)) != cudaSuccess) return bad(e);
         if ((e = cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming)) != cudaSuccess) return bad(e);
         if ((e = cudaMalloc(&b.d_out, (size_t)s->max_batch * sizeof(Result))) != cudaSuccess) return bad(e);
@@ -2781,10 +2836,31 @@ extern "C" int ccst_server_create(ccst_ctx* c, int slots, int max_batch, ccst_se
         if ((e = cudaHostAlloc(&b.h_gitems, (size_t)s->max_batch * sizeof(GenItem), cudaHostAllocDefault)) != cudaSuccess)
             return bad(e);
     }
-    for (int i = slots - 1; i >= 0; --i) s->free_slots.push_back(i);
     s->worker = std::thread(server_loop, s);
     *out = s;
     return CCST_OK;
+}
+
+extern "C" int ccst_server_create(ccst_ctx* c, int slots, int max_batch, ccst_server** out) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!out || slots < 1 || max_batch < 1) return fail(c, CCST_E_INVALID, "ccst_server_create: bad arguments");
+    rois_init(c);
+    // the budget of `slots` frames of the largest reference present now
+    uint64_t largest = 0;
+    const size_t elem = c->p.in_dtype == CCST_U16 ? 2 : 4;
+    for (int i = 0; i < (int)c->refs.size(); ++i)
+        if (ref_usable(c, i)) {
+            int H = 0, W = 0;
+            ref_shape(c, i, &H, &W);
+            largest = std::max(largest, ((uint64_t)H * W * elem + 255) / 256 * 256);
+        }
+    if (largest == 0) return fail(c, CCST_E_INVALID, "ccst_server_create: no reference usable by ROI batches");
+    ccst_server_config cfg{};
+    cfg.max_batch = std::min(max_batch, slots);
+    cfg.max_in_flight = ccst_server::kRing;
+    cfg.budget_bytes = (int64_t)(largest * (uint64_t)slots);
+    return ccst_server_create_ex(c, &cfg, out);
 }
 
 extern "C" int ccst_server_submit(ccst_server* s, int ref_id, const void* frame_host, int64_t pitch_elems,
@@ -2794,21 +2870,20 @@ extern "C" int ccst_server_submit(ccst_server* s, int ref_id, const void* frame_
     if (!ref_usable(c, ref_id)) return CCST_E_INVALID;
     int H = 0, W = 0;
     ref_shape(c, ref_id, &H, &W);
-    if ((size_t)H * W * s->elem > s->slot_bytes) return CCST_E_INVALID;    // added after the server
+    const uint64_t bytes = frame_bytes(s, ref_id);
+    if (bytes > s->cap) return CCST_E_INVALID;                 // can never be admitted
     if (pitch_elems == 0) pitch_elems = W;
     if (pitch_elems < W) return CCST_E_INVALID;
     ccst_server::Req r;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->error) return s->error;
-        if (s->free_slots.empty()) {
+        if (!s->reserve(bytes, &r.vstart)) {
             ++s->rejected;
             return CCST_E_BUSY;
         }
-        r.slot = s->free_slots.back();
-        s->free_slots.pop_back();
     }
-    char* dst = s->h_frames + (size_t)r.slot * s->slot_bytes;
+    char* dst = s->h_frames + (size_t)(r.vstart % s->cap);
     const size_t row = (size_t)W * s->elem;
     for (int y = 0; y < H; ++y) std::memcpy(dst + y * row, (const char*)frame_host + (size_t)y * pitch_elems * s->elem, row);
     r.ref = ref_id;
@@ -2822,6 +2897,7 @@ extern "C" int ccst_server_submit(ccst_server* s, int ref_id, const void* frame_
             *ticket = r.ticket;
         }
         s->pending.push_back(r);
+        ++s->npending;
         ++s->submitted;
     }
     s->cv_work.notify_one();
@@ -2861,9 +2937,13 @@ extern "C" int ccst_server_read_stats(ccst_server* s, int reset, ccst_server_sta
     out->p99_us = pct(0.99);
     out->max_us = v.empty() ? 0.0 : (double)v.back();
     out->in_flight = (int64_t)(s->submitted - s->completed);
+    out->bytes_in_flight = (int64_t)(s->head - s->tail);
+    out->max_bytes_in_flight = (int64_t)s->max_used;
+    out->budget_bytes = (int64_t)s->cap;
     if (reset) {
         s->lat_us.clear();
         s->submitted = s->completed = s->rejected = s->batches = s->batched = 0;
+        s->max_used = s->head - s->tail;
     }
     return s->error;
 }

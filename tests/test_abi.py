@@ -85,8 +85,11 @@ def test_new_record_layouts_match_the_header():
     assert ctypes.sizeof(C.ccst_roi) == 32
     assert (C.ccst_roi.frame.offset, C.ccst_roi.H.offset, C.ccst_roi.W.offset, C.ccst_roi.pitch_elems.offset,
             C.ccst_roi.ref_id.offset) == (0, 8, 12, 16, 24)
-    # ccst_server_stats: 4 x uint64, 4 x double, int64
-    assert ctypes.sizeof(C.ccst_server_stats_t) == 72 and C.ccst_server_stats_t.in_flight.offset == 64
+    # ccst_server_stats: 4 x uint64, 4 x double, 4 x int64
+    assert ctypes.sizeof(C.ccst_server_stats_t) == 96 and C.ccst_server_stats_t.in_flight.offset == 64
+    assert C.ccst_server_stats_t.budget_bytes.offset == 88
+    # ccst_server_config: 2 x int32, int64, uint32, int32
+    assert ctypes.sizeof(C.ccst_server_config) == 24 and C.ccst_server_config.budget_bytes.offset == 8
     # ccst_tune_result: 6 x int32, double
     assert ctypes.sizeof(C.ccst_tune_result) == 32 and C.ccst_tune_result.us_per_frame.offset == 24
 
@@ -108,6 +111,13 @@ def test_null_handles_are_rejected_without_gpu(lib):
     assert lib.ccst_track_rois(n, n, 1, n) == C.E_INVALID
     out = ctypes.c_void_p()
     assert lib.ccst_server_create(n, 4, 4, ctypes.byref(out)) == C.E_INVALID
+    cfg = C.ccst_server_config(16, 2, 1 << 20, 0, 0)
+    assert lib.ccst_server_create_ex(n, ctypes.byref(cfg), ctypes.byref(out)) == C.E_INVALID
+    assert lib.ccst_set_reference_image(n, n) == C.E_INVALID
+    assert lib.ccst_refine_reference(n, n, 4, 0, n, 2, 0.01, n, n) == C.E_INVALID
+    i64 = ctypes.c_int64()
+    assert lib.ccst_graph_stats(n, ctypes.byref(i64), ctypes.byref(i64), ctypes.byref(i64)) == C.E_INVALID
+    assert lib.ccst_fp32_fma_peak(n, 100, n, n) == C.E_INVALID
     assert lib.ccst_server_submit(n, 0, n, 0, n) == C.E_INVALID
     done = ctypes.c_int()
     assert lib.ccst_server_poll(n, 1, 0, n, ctypes.byref(done)) == C.E_INVALID

@@ -180,3 +180,68 @@ def test_general_size_cameras_equal_the_roi_path(torch):
     finally:
         C.ccst_server_destroy(srv)
         t.close()
+
+
+def test_admission_by_bytes_charges_each_frame_its_own_size(torch):
+    # a budget of one 128 x 128 uint16 frame (32 KiB): a 128 px frame alone fills it, while up
+    # to 16 frames of a 32 px camera (2 KiB each) fit at once; nothing larger than the budget
+    # is ever admissible
+    cams = cameras(seed=11, sides=(128, 32), n=8)
+    t = C.Tracker(cams[0][0], upsample=100, in_dtype="u16")
+    ids = [0, C.ccst_add_reference(t.ctx, cams[1][0], 32, 32)]
+    srv = C.ccst_server_create_ex(t.ctx, 64, 2, 128 * 128 * 2)
+    try:
+        admitted, refused = 0, 0
+        for i in range(3000):
+            k = 1 if i % 10 else 0
+            try:
+                C.ccst_server_submit(srv, ids[k], cams[k][1][i % 8], keep=False)
+                admitted += 1
+            except C.CcstError as e:
+                assert e.code == C.E_BUSY
+                refused += 1
+        for _ in range(200000):
+            st = C.ccst_server_read_stats(srv)
+            if st["in_flight"] == 0:
+                break
+        assert st["completed"] == admitted and st["rejected"] == refused and refused > 0
+        assert st["budget_bytes"] == 32768 and 2048 < st["max_bytes_in_flight"] <= 32768
+        assert st["bytes_in_flight"] == 0
+    finally:
+        C.ccst_server_destroy(srv)
+    small = C.ccst_server_create_ex(t.ctx, 8, 1, 16 * 1024)      # below one 128 px frame
+    try:
+        with pytest.raises(C.CcstError) as e:
+            C.ccst_server_submit(small, 0, cams[0][1][0])
+        assert e.value.code == C.E_INVALID
+        tk = C.ccst_server_submit(small, ids[1], cams[1][1][0])
+        assert C.ccst_server_poll(small, tk, 5_000_000) is not None
+    finally:
+        C.ccst_server_destroy(small)
+    for bad in [(0, 1, 1 << 20), (4, 0, 1 << 20), (4, 5, 1 << 20), (4, 1, 100)]:
+        with pytest.raises(C.CcstError):
+            C.ccst_server_create_ex(t.ctx, *bad)
+    t.close()
+
+
+def test_plain_configuration_launches_one_frame_at_a_time(torch):
+    cams = cameras(seed=12, sides=(64, 128), n=10)
+    t = C.Tracker(cams[0][0], upsample=100, in_dtype="u16")
+    ids = [0, C.ccst_add_reference(t.ctx, cams[1][0], 128, 128)]
+    batched = C.ccst_server_create_ex(t.ctx, 256, 4, 8 << 20)
+    plain = C.ccst_server_create_ex(t.ctx, 1, 1, 8 << 20)
+    try:
+        want = {}
+        for k in range(2):
+            for i in range(10):
+                want[(k, i)] = C.ccst_server_poll(batched, C.ccst_server_submit(batched, ids[k], cams[k][1][i]),
+                                                  5_000_000).tobytes()
+        tickets = [((k, i), C.ccst_server_submit(plain, ids[k], cams[k][1][i])) for i in range(10) for k in range(2)]
+        for key, tk in tickets:
+            assert C.ccst_server_poll(plain, tk, 5_000_000).tobytes() == want[key]
+        st = C.ccst_server_read_stats(plain)
+        assert st["completed"] == 20 and st["batches"] == 20 and st["mean_batch"] == 1.0
+    finally:
+        C.ccst_server_destroy(batched)
+        C.ccst_server_destroy(plain)
+        t.close()
