@@ -605,59 +605,90 @@ ROIS_ORACLE = 48
 
 def rois_leg(C, torch, stream, n_rois=ROIS_N, sides=ROIS_SIDES, plain=True):
     """Uneven batch: FP32 ROIs of mixed sizes, each against its own reference, in one
-    ccst_track_rois call (the power-of-two kernel and the general-size kernel run side by
-    side), against the same ROIs as one call each. Timed with the default general-size
-    schedule, then after ccst_autotune (the reported value)."""
+    ccst_track_rois call (the power-of-two kernel and the general-size kernel side by side),
+    after ccst_autotune, replayed as one captured CUDA graph (the reported value). Beside it:
+    the same call launched directly, the same ROIs as one batched call per size class (the
+    per-size form), and (context) one call per ROI."""
     import ctypes
     from paper_2310_08770_b300 import synth
     r = synth.uneven_rois(seed=0, n=n_rois, sides=sides)
     n = len(r.frames)
-    t = C.Tracker(r.refs[0], upsample=U, method="ccu", in_dtype="f32", stream=stream)
-    t0 = time.perf_counter()
-    ids = [0] + [C.ccst_add_reference(t.ctx, ref, ref.shape[0], ref.shape[1]) for ref in r.refs[1:]]
-    setup_s = time.perf_counter() - t0
     frames = [torch.from_numpy(f).cuda() for f in r.frames]
-    rois = C.make_rois(frames, ids)
-    out = t.empty_results(n)
     ev = lambda: torch.cuda.Event(enable_timing=True)          # noqa: E731
-    def batched():
+    needs_tune = any(x not in (16, 32, 64, 128) for x in sides)
+
+    def make(graphs):
+        t = C.Tracker(r.refs[0], upsample=U, method="ccu", in_dtype="f32", stream=stream, graphs=graphs)
+        t0 = time.perf_counter()
+        ids = [0] + [C.ccst_add_reference(t.ctx, ref, ref.shape[0], ref.shape[1]) for ref in r.refs[1:]]
+        return t, C.make_rois(frames, ids), time.perf_counter() - t0
+
+    def timed(fn, reps=ROIS_REPS):
         for _ in range(3):
-            C.ccst_track_rois(t.ctx, rois, n, out)
+            fn()
         torch.cuda.synchronize()
         a, b = ev(), ev()
         a.record(stream)
-        for _ in range(ROIS_REPS):
-            C.ccst_track_rois(t.ctx, rois, n, out)
+        for _ in range(reps):
+            fn()
         b.record(stream)
         torch.cuda.synchronize()
-        return a.elapsed_time(b) / ROIS_REPS
+        return a.elapsed_time(b) / reps
 
     with torch.cuda.stream(stream):
-        default_ms = batched()
+        # direct launches
+        t, rois, setup_s = make(False)
+        out = t.empty_results(n)
+        default_ms = timed(lambda: C.ccst_track_rois(t.ctx, rois, n, out))
         t0 = time.perf_counter()
-        tuned = C.ccst_autotune(t.ctx, 3, rois, n) if any(s not in (16, 32, 64, 128) for s in sides) else []
+        tuned = C.ccst_autotune(t.ctx, 3, rois, n) if needs_tune else []
         tune_s = time.perf_counter() - t0
-        batched_ms = batched() if tuned else default_ms
+        direct_ms = timed(lambda: C.ccst_track_rois(t.ctx, rois, n, out)) if tuned else default_ms
         res = C.decode(out)
+        # per-size form: one batched call per size class, one after another
+        groups = {}
+        for i, f in enumerate(r.frames):
+            groups.setdefault(f.shape[0], []).append(i)
+        per = [(C.make_rois([frames[i] for i in idx], [rois[i].ref_id for i in idx]), len(idx),
+                t.empty_results(len(idx)), idx) for _, idx in sorted(groups.items())]
+        per_size_ms = timed(lambda: [C.ccst_track_rois(t.ctx, rr, m, oo) for rr, m, oo, _ in per])
+        per_same = all(C.decode(oo).tobytes() == res[idx].tobytes() for _, _, oo, idx in per)
         plain_ms = None
         if plain:
             a, b = ev(), ev()
             a.record(stream)
-            for i in range(n):                                  # the plain form: one call per ROI
+            for i in range(n):                                  # one call per ROI
                 C.ccst_track_rois(t.ctx, ctypes.byref(rois[i]), 1, out[i:i + 1])
             b.record(stream)
             torch.cuda.synchronize()
             plain_ms = a.elapsed_time(b)
-    same = bool(C.decode(out).tobytes() == res.tobytes())
-    t.close()
+        same = bool(C.decode(out).tobytes() == res.tobytes())
+        t.close()
+        # the same work list captured as one graph and replayed (the product path)
+        tg, rois_g, _ = make(True)
+        if needs_tune:
+            C.ccst_autotune(tg.ctx, 3, rois_g, n)
+        out_g = tg.empty_results(n)
+        graph_ms = timed(lambda: C.ccst_track_rois(tg.ctx, rois_g, n, out_g))
+        gstats = C.ccst_graph_stats(tg.ctx)
+        graph_same = bool(C.decode(out_g).tobytes() == res.tobytes())
+        tg.close()
     flop = sum(flop_per_frame(f.shape[0], f.shape[1], U) for f in r.frames)
-    achieved = flop / (batched_ms / 1e3) / 1e12
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
-    sizes = {s: int(sum(1 for f in r.frames if f.shape[0] == s)) for s in sides}
+    fma = C.ccst_fp32_fma_peak(stream.cuda_stream)
+    peak = fma["tflops"]
+    achieved = flop / (graph_ms / 1e3) / 1e12
+    sizes = {s_: int(sum(1 for f in r.frames if f.shape[0] == s_)) for s_ in sides}
     line = {"workload": f"{n} FP32 square ROIs, sides uniform over {list(sides)} ({sizes}), per-ROI noise-free "
                         "reference (sigma U(1.5,4), peak U(200,5000), bg U(5,50)), Poisson frames shifted U(-3,3)^2 px, "
                         f"u={U}, CC-U",
-            "value": n / (batched_ms / 1e3), "unit": "ROIs/s", "ms_per_batch": batched_ms,
+            "value": n / (graph_ms / 1e3), "unit": "ROIs/s", "ms_per_batch": graph_ms,
+            "form": "one ccst_track_rois work list captured as one CUDA graph (both kernels) and replayed",
+            "graphs": gstats, "records_equal_to_direct": graph_same,
+            "direct_launch": {"value": n / (direct_ms / 1e3), "ms": direct_ms},
+            "per_size_batched": {"value": n / (per_size_ms / 1e3), "ms": per_size_ms, "calls": len(per),
+                                 "records_equal": bool(per_same),
+                                 "form": "one batched ccst_track_rois call per side, one after another"},
+            "speedup_vs_per_size_batched": per_size_ms / graph_ms,
             "reference_setup_s": setup_s,
             "autotune": {"ms_per_batch_default_schedule": default_ms, "seconds": tune_s,
                          "plans": [{k: x[k] for k in ("H", "W", "H1", "W1", "threads", "us_per_frame")}
@@ -665,11 +696,12 @@ def rois_leg(C, torch, stream, n_rois=ROIS_N, sides=ROIS_SIDES, plain=True):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "kernel": "track_rois_kernel + track_generic_kernel", "flop_total": flop,
                          "flop_basis": "the folded formulation's algorithmic flops for every ROI (the general-size "
-                                       "path does more work than that: two-level DFTs in double-float and the FP32 grid with double-float candidates)",
-                         "peak_basis": "148 SMs x 128 FP32 FMA lanes x 2 x 2032 MHz (nominal max clock)"}}
+                                       "path does more work than that: two-level DFTs in double-float and the FP32 "
+                                       "grid with double-float candidates)",
+                         "peak_basis": "of measured: FP32 FMA rate of this GPU (ccst_fp32_fma_peak)"}}
     if plain:
         line.update({"plain_per_roi_call": {"value": n / (plain_ms / 1e3), "unit": "ROIs/s", "ms": plain_ms},
-                     "speedup_vs_plain": plain_ms / batched_ms, "records_equal_to_plain": same})
+                     "speedup_vs_plain": plain_ms / graph_ms, "records_equal_to_plain": same})
     return line, (r, res)
 
 

@@ -257,6 +257,14 @@ int ccst_add_reference(ccst_ctx* ctx, const float* ref, int H, int W, int* ref_i
  * identical to those of ccst_track on a context made for that ROI's reference. ROIs of
  * general sizes run as a second persistent launch, on an internal stream, concurrently
  * with the first; the call's work is complete when the context's stream reaches it.
+ * With CCST_FLAG_GRAPHS (and a non-default stream), both launches are captured once as
+ * one CUDA graph per (stream, out_dev, work list), with the work items uploaded to memory
+ * the graph owns, and replayed by later calls with the same list (compared byte by byte).
+ * A graph's frame counters and items are its own. The general-size scratch is one area
+ * per stream, and graphs on one stream run in order. Adding a reference or running
+ * ccst_autotune drops the captured graphs, after their last replays have finished.
+ * At most 64 are kept; beyond that the cache is emptied and starts again.
+ * Without the flag every call uploads its items and launches directly.
  * Stream-ordered and asynchronous.
  * Errors: CCST_E_INVALID (null pointers, n < 0, unknown ref_id, pitch < W), CCST_E_SHAPE (a
  * ROI whose size differs from its reference's), CCST_E_NOMEM, CCST_E_CUDA. */

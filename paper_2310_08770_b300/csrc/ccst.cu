@@ -667,6 +667,21 @@ struct ccst_ctx {
     RoiItem* d_items = nullptr;
     size_t items_cap = 0;
     std::vector<RoiItem> h_items;
+    // ROI batches captured as CUDA graphs (CCST_FLAG_GRAPHS): one per (stream, out, work
+    // list), each with its own uploaded work items and frame counters; the general-size
+    // kernel's scratch is one lane per stream (graphs on one stream run in order). Dropped
+    // (after their last replay) whenever plans, references or schedules change.
+    struct RoiGraph {
+        std::vector<ccst_roi> rois;   // the work list it was captured for
+        cudaGraphExec_t exec = nullptr;
+        cudaEvent_t done = nullptr;
+        RoiItem* d_items = nullptr;
+        GenItem* d_gitems = nullptr;
+        unsigned* counters = nullptr; // [0] power-of-two kernel, [1] general-size kernel
+    };
+    std::map<std::tuple<cudaStream_t, void*, int64_t, uint64_t>, RoiGraph> roi_graphs;
+    std::map<cudaStream_t, GenLane> roi_lanes;
+    int64_t roi_graph_instantiations = 0, roi_graph_replays = 0;
     bool rois_dirty = true;
     size_t rois_smem = 0;
     int rois_grid = 0;
@@ -756,6 +771,22 @@ static void drop_graphs(ccst_ctx* c) {
     for (unsigned i = 0; i < (unsigned)kMaxGraphs; ++i) c->free_graph_counters.push_back((unsigned)kMaxGraphs - 1 - i);
 }
 
+static void free_roi_graph(ccst_ctx::RoiGraph& e) {
+    if (e.done) cudaEventSynchronize(e.done);
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+    if (e.done) cudaEventDestroy(e.done);
+    if (e.d_items) cudaFree(e.d_items);
+    if (e.d_gitems) cudaFree(e.d_gitems);
+    if (e.counters) cudaFree(e.counters);
+    e = ccst_ctx::RoiGraph{};
+}
+
+// Destroy every captured ROI graph after its last replay has finished.
+static void drop_roi_graphs(ccst_ctx* c) {
+    for (auto& kv : c->roi_graphs) free_roi_graph(kv.second);
+    c->roi_graphs.clear();
+}
+
 // A frame counter of the direct-launch ring for a launch on `stream`: the stream first
 // waits for the previous launch that used the same counter (a no-op when it ran on the
 // same stream or has finished). Call ring_release after the launch has been issued.
@@ -806,6 +837,9 @@ static cudaError_t ring_release(ccst_ctx* c, unsigned k, cudaStream_t stream) {
 
 static void free_all(ccst_ctx* c) {
     drop_graphs(c);
+    drop_roi_graphs(c);
+    for (auto& kv : c->roi_lanes) lane_free(kv.second);
+    c->roi_lanes.clear();
     for (size_t i = 0; i < c->prof0.size(); ++i) {
         cudaEventDestroy(c->prof0[i]);
         cudaEventDestroy(c->prof1[i]);
@@ -1278,9 +1312,9 @@ extern "C" int ccst_graph_stats(ccst_ctx* c, int64_t* instantiations, int64_t* r
     int rc = check_ctx(c);
     if (rc) return rc;
     if (!instantiations || !replays || !cached) return fail(c, CCST_E_INVALID, "ccst_graph_stats: null output");
-    *instantiations = c->graph_instantiations;
-    *replays = c->graph_replays;
-    *cached = (int64_t)c->graphs.size();
+    *instantiations = c->graph_instantiations + c->roi_graph_instantiations;
+    *replays = c->graph_replays + c->roi_graph_replays;
+    *cached = (int64_t)(c->graphs.size() + c->roi_graphs.size());
     return CCST_OK;
 }
 
@@ -2215,6 +2249,29 @@ static int gen_prepare(ccst_ctx* c) {
     return CCST_OK;
 }
 
+// The general-size kernel over gb.n frames on `stream` (gb.items already on the device, or
+// null for a uniform batch), with per-CTA scratch of `stride` elements: counter reset, launch.
+static int gen_kernel_launch(ccst_ctx* c, GenBatch gb, dfc* scratch, long long stride, cudaStream_t stream,
+                             unsigned* counter) {
+    const int grid = (int)(gb.n < c->gen_grid ? gb.n : c->gen_grid);
+    CK(c, cudaMemsetAsync(counter, 0, sizeof(unsigned), stream));
+    gb.plans = c->d_gplans;
+    gb.refs = c->d_grefs;
+    gb.next = counter;
+    gb.scratch = scratch;
+    gb.scratch_stride = stride;
+    void* args[] = {&gb};
+    CK(c, cudaLaunchKernel(track_generic_kernel_ptr(), dim3(grid), dim3(c->gen_threads), args, 0, stream));
+    return CCST_OK;
+}
+
+// Per-CTA scratch stride of the general-size kernel over every plan of the context.
+static long long gen_stride(ccst_ctx* c) {
+    long long stride = 0;
+    for (auto& g : c->gplans) stride = std::max(stride, gen_scratch_stride(g.p.H, g.p.W, g.p.M));
+    return stride;
+}
+
 // Launch the general-size kernel on `stream` over gb.n frames: the work list `items_host`
 // (copied to the lane at once; the caller orders it) or, if null, the uniform batch that
 // gb describes. gb.out is set by the caller; the rest is filled in here.
@@ -2223,8 +2280,7 @@ static int gen_launch(ccst_ctx* c, GenLane& lane, GenBatch gb, const GenItem* it
     if (gb.n == 0) return CCST_OK;
     int rc = gen_prepare(c);
     if (rc) return rc;
-    long long stride = 0;
-    for (auto& g : c->gplans) stride = std::max(stride, gen_scratch_stride(g.p.H, g.p.W, g.p.M));
+    const long long stride = gen_stride(c);
     const int grid = (int)(gb.n < c->gen_grid ? gb.n : c->gen_grid);
     if (lane.scratch_elems < (size_t)grid * stride) {
         if (lane.scratch) cudaFree(lane.scratch);
@@ -2245,15 +2301,7 @@ static int gen_launch(ccst_ctx* c, GenLane& lane, GenBatch gb, const GenItem* it
         CK(c, cudaMemcpyAsync(lane.d_items, items_host, (size_t)gb.n * sizeof(GenItem), cudaMemcpyHostToDevice, stream));
         gb.items = lane.d_items;
     }
-    CK(c, cudaMemsetAsync(counter, 0, sizeof(unsigned), stream));
-    gb.plans = c->d_gplans;
-    gb.refs = c->d_grefs;
-    gb.next = counter;
-    gb.scratch = lane.scratch;
-    gb.scratch_stride = stride;
-    void* args[] = {&gb};
-    CK(c, cudaLaunchKernel(track_generic_kernel_ptr(), dim3(grid), dim3(c->gen_threads), args, 0, stream));
-    return CCST_OK;
+    return gen_kernel_launch(c, gb, lane.scratch, stride, stream, counter);
 }
 
 // Largest frames first (the longest work starts first; equal shapes stay together).
@@ -2303,6 +2351,7 @@ extern "C" int ccst_autotune(ccst_ctx* c, int reps, const ccst_roi* rois, int64_
     if (n_out) *n_out = 0;
     const int np = (int)c->gplans.size();
     if (np == 0) return CCST_OK;
+    drop_roi_graphs(c);           // schedules change below: captured launches would go stale
     std::vector<int> ref_of(np, -1);
     for (int i = 0; i < (int)c->refs.size(); ++i)
         if (c->refs[i].gcls >= 0 && ref_of[c->refs[i].gcls] < 0) ref_of[c->refs[i].gcls] = i;
@@ -2334,6 +2383,7 @@ extern "C" int ccst_autotune(ccst_ctx* c, int reps, const ccst_roi* rois, int64_
         for (int p = 0; p < np; ++p) set_split(p, saved[p].first, saved[p].second);
         c->gen_threads = saved_threads;
         c->gen_grid = 0;
+        c->gen_dirty = true;
         return code;
     };
     // the best of `reps` timed launches (after one untimed), in ms
@@ -2406,6 +2456,7 @@ extern "C" int ccst_autotune(ccst_ctx* c, int reps, const ccst_roi* rois, int64_
         for (int ti = 0; ti < 2; ++ti) {
             c->gen_threads = threads[ti];
             c->gen_grid = 0;
+            c->gen_dirty = true;      // a graph-captured ROI batch must be captured again
             double best = 1e300;
             for (int r = -1; r < reps; ++r) {
                 if (cudaEventRecord(e0, c->stream) != cudaSuccess) return bail(fail(c, CCST_E_CUDA, "ccst_autotune: event"));
@@ -2461,14 +2512,15 @@ static int not_general(ccst_ctx* c, const char* who) {
 // Sort items largest first (the longest work starts first; size classes stay contiguous),
 // copy them to items_dev (n slots) and launch the ROI kernel on `stream` with `counter`.
 // The host items must stay valid until the copy has been issued (it is staged at once).
-static int rois_launch(ccst_ctx* c, RoiItem* items, int64_t n, Result* out, cudaStream_t stream, RoiItem* items_dev,
-                       unsigned* counter) {
+static void rois_sort(ccst_ctx* c, RoiItem* items, int64_t n) {
     std::stable_sort(items, items + n, [&](const RoiItem& a, const RoiItem& b) {
         return c->plans[a.cls].g.H > c->plans[b.cls].g.H;
     });
-    int rc = rois_upload(c);
-    if (rc) return rc;
-    CK(c, cudaMemcpyAsync(items_dev, items, (size_t)n * sizeof(RoiItem), cudaMemcpyHostToDevice, stream));
+}
+
+// The ROI kernel over n items already on the device: counter reset, launch.
+static int rois_kernel_launch(ccst_ctx* c, const RoiItem* items_dev, int64_t n, Result* out, cudaStream_t stream,
+                              unsigned* counter) {
     CK(c, cudaMemsetAsync(counter, 0, sizeof(unsigned), stream));
     RoiBatch rb;
     rb.items = items_dev;
@@ -2480,6 +2532,128 @@ static int rois_launch(ccst_ctx* c, RoiItem* items, int64_t n, Result* out, cuda
     const int grid = (int)(n < c->rois_grid ? n : c->rois_grid);
     void* args[] = {&rb};
     CK(c, cudaLaunchKernel(track_rois_kernel_ptr(), dim3(grid), dim3(kThreads), args, c->rois_smem, stream));
+    return CCST_OK;
+}
+
+static int rois_launch(ccst_ctx* c, RoiItem* items, int64_t n, Result* out, cudaStream_t stream, RoiItem* items_dev,
+                       unsigned* counter) {
+    rois_sort(c, items, n);
+    int rc = rois_upload(c);
+    if (rc) return rc;
+    CK(c, cudaMemcpyAsync(items_dev, items, (size_t)n * sizeof(RoiItem), cudaMemcpyHostToDevice, stream));
+    return rois_kernel_launch(c, items_dev, n, out, stream, counter);
+}
+
+constexpr size_t kMaxRoiGraphs = 64;
+
+static uint64_t fnv1a(const void* p, size_t bytes) {
+    const unsigned char* b = (const unsigned char*)p;
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < bytes; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    return h;
+}
+
+// ccst_track_rois as a replay of a graph captured once per (stream, out, work list): the
+// general-size kernel forked onto the context's second stream and the power-of-two kernel,
+// joined. The work items (sorted as the direct path sorts them) are uploaded at capture.
+// c->h_items[0, np) and c->h_gitems[0, ng) hold the validated items.
+static int rois_graph_track(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccst_result* out_dev, int64_t np,
+                            int64_t ng) {
+    // captured pointers and launch shapes would go stale; the general-size state matters
+    // only once the context has general-size plans
+    if (c->rois_dirty || (c->gen_dirty && !c->gplans.empty())) drop_roi_graphs(c);
+    int rc = rois_upload(c);
+    if (rc) return rc;
+    if (!c->gplans.empty() && (rc = gen_prepare(c))) return rc;
+    const auto key = std::make_tuple(c->stream, (void*)out_dev, n, fnv1a(rois, (size_t)n * sizeof(ccst_roi)));
+    auto it = c->roi_graphs.find(key);
+    if (it != c->roi_graphs.end() &&
+        std::memcmp(it->second.rois.data(), rois, (size_t)n * sizeof(ccst_roi)) != 0) {   // hash collision
+        free_roi_graph(it->second);
+        c->roi_graphs.erase(it);
+        it = c->roi_graphs.end();
+    }
+    if (it == c->roi_graphs.end()) {
+        if (c->roi_graphs.size() >= kMaxRoiGraphs) drop_roi_graphs(c);
+        if (ng > 0 && !c->gstream) {
+            CK(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+            CK(c, cudaEventCreateWithFlags(&c->gfork, cudaEventDisableTiming));
+            CK(c, cudaEventCreateWithFlags(&c->gjoin, cudaEventDisableTiming));
+        }
+        GenLane* lane = nullptr;
+        const long long stride = ng > 0 ? gen_stride(c) : 0;
+        if (ng > 0) {
+            lane = &c->roi_lanes[c->stream];
+            const size_t need = (size_t)c->gen_grid * (size_t)stride;
+            if (lane->scratch_elems < need) {
+                drop_roi_graphs(c);                               // graphs on this stream use the lane
+                if (lane->scratch) cudaFree(lane->scratch);
+                lane->scratch = nullptr;
+                lane->scratch_elems = 0;
+                CK(c, cudaMalloc(&lane->scratch, need * sizeof(dfc)));
+                lane->scratch_elems = need;
+            }
+        }
+        ccst_ctx::RoiGraph e;
+        e.rois.assign(rois, rois + n);
+        auto bail = [&](int code) { free_roi_graph(e); return code; };
+        cudaError_t err;
+        if ((err = cudaEventCreateWithFlags(&e.done, cudaEventDisableTiming)) != cudaSuccess ||
+            (err = cudaMalloc(&e.counters, 2 * sizeof(unsigned))) != cudaSuccess)
+            return bail(fail(c, CCST_E_CUDA, std::string("ccst_track_rois: ") + cudaGetErrorString(err)));
+        if (np > 0) {
+            rois_sort(c, c->h_items.data(), np);
+            if ((err = cudaMalloc(&e.d_items, (size_t)np * sizeof(RoiItem))) != cudaSuccess ||
+                (err = cudaMemcpy(e.d_items, c->h_items.data(), (size_t)np * sizeof(RoiItem), cudaMemcpyHostToDevice)) !=
+                    cudaSuccess)
+                return bail(fail(c, err == cudaErrorMemoryAllocation ? CCST_E_NOMEM : CCST_E_CUDA,
+                                 std::string("ccst_track_rois: ") + cudaGetErrorString(err)));
+        }
+        if (ng > 0) {
+            gen_sort(c, c->h_gitems.data(), ng);
+            if ((err = cudaMalloc(&e.d_gitems, (size_t)ng * sizeof(GenItem))) != cudaSuccess ||
+                (err = cudaMemcpy(e.d_gitems, c->h_gitems.data(), (size_t)ng * sizeof(GenItem),
+                                  cudaMemcpyHostToDevice)) != cudaSuccess)
+                return bail(fail(c, err == cudaErrorMemoryAllocation ? CCST_E_NOMEM : CCST_E_CUDA,
+                                 std::string("ccst_track_rois: ") + cudaGetErrorString(err)));
+        }
+        cudaGraph_t graph = nullptr;
+        if ((err = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return bail(fail(c, CCST_E_CUDA, std::string("ccst_track_rois: capture: ") + cudaGetErrorString(err)));
+        int lrc = CCST_OK;
+        if (ng > 0) {
+            GenBatch gb{};
+            gb.n = ng;
+            gb.out = (Result*)out_dev;
+            gb.items = e.d_gitems;
+            if (cudaEventRecord(c->gfork, c->stream) != cudaSuccess ||
+                cudaStreamWaitEvent(c->gstream, c->gfork, 0) != cudaSuccess)
+                lrc = fail(c, CCST_E_CUDA, "ccst_track_rois: fork during capture");
+            if (!lrc) lrc = gen_kernel_launch(c, gb, lane->scratch, stride, c->gstream, e.counters + 1);
+            if (!lrc && cudaEventRecord(c->gjoin, c->gstream) != cudaSuccess)
+                lrc = fail(c, CCST_E_CUDA, "ccst_track_rois: join during capture");
+        }
+        if (!lrc && np > 0) lrc = rois_kernel_launch(c, e.d_items, np, (Result*)out_dev, c->stream, e.counters);
+        if (!lrc && ng > 0 && cudaStreamWaitEvent(c->stream, c->gjoin, 0) != cudaSuccess)
+            lrc = fail(c, CCST_E_CUDA, "ccst_track_rois: join during capture");
+        err = cudaStreamEndCapture(c->stream, &graph);
+        if (lrc) {
+            if (graph) cudaGraphDestroy(graph);
+            c->dead = true;                                       // a broken capture leaves the stream unusable
+            return bail(lrc);
+        }
+        if (err != cudaSuccess) return bail(fail(c, CCST_E_CUDA, std::string("ccst_track_rois: capture: ") +
+                                                                     cudaGetErrorString(err)));
+        err = cudaGraphInstantiate(&e.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (err != cudaSuccess)
+            return bail(fail(c, CCST_E_CUDA, std::string("ccst_track_rois: instantiate: ") + cudaGetErrorString(err)));
+        ++c->roi_graph_instantiations;
+        it = c->roi_graphs.emplace(key, std::move(e)).first;
+    }
+    CK(c, cudaGraphLaunch(it->second.exec, c->stream));
+    CK(c, cudaEventRecord(it->second.done, c->stream));
+    ++c->roi_graph_replays;
     return CCST_OK;
 }
 
@@ -2517,6 +2691,7 @@ extern "C" int ccst_track_rois(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccs
         it.vec_ok = ((uintptr_t)q.frame % 16 == 0) && ((size_t)pitch * elem % 16 == 0) ? 1 : 0;
         it.pad = 0;
     }
+    if ((c->p.flags & CCST_FLAG_GRAPHS) && c->stream != nullptr) return rois_graph_track(c, rois, n, out_dev, np, ng);
     CK(c, shared_acquire(c, c->stream));
     if (ng > 0) {
         // the general sizes run on their own stream, forked here and joined below

@@ -107,3 +107,70 @@ def test_general_size_errors(torch):
         C.ccst_track_rois(t.ctx, C.make_rois([f96], [r48]), 1, out)          # size differs
     assert e.value.code == C.E_SHAPE
     t.close()
+
+
+def test_graph_captured_batches_replay_the_direct_records(torch):
+    # with CCST_FLAG_GRAPHS a work list is captured once per stream (both kernels in one
+    # graph) and replayed; records are byte-identical to the direct path's, every record is
+    # written on every replay, and a new reference drops the captured graphs
+    items = uneven([48, 32, 96, 64, 24, 128, 48, 16, 96, 32], seed=21, u16=True)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    ref0 = synth.gaussian_spot(32, 32, 16, 16, 2.0, 500.0, 10.0).astype(np.float32)
+    direct = C.Tracker(ref0, upsample=60, in_dtype="u16")
+    ids = [C.ccst_add_reference(direct.ctx, r, *r.shape) for r, _ in items]
+    frames = [dev(torch, f) for _, f in items]
+    want = direct.empty_results(len(items))
+    C.ccst_track_rois(direct.ctx, C.make_rois(frames, ids), len(items), want)
+    C.ccst_sync(direct.ctx)
+    want = C.decode(want).tobytes()
+    direct.close()
+    t = C.Tracker(ref0, upsample=60, in_dtype="u16", graphs=True, stream=streams[0])
+    gids = [C.ccst_add_reference(t.ctx, r, *r.shape) for r, _ in items]
+    rois = C.make_rois(frames, gids)
+    for rep in range(3):
+        for st in streams:
+            C.ccst_set_stream(t.ctx, st.cuda_stream)
+            out = torch.full((len(items), 24), 0xFF, dtype=torch.uint8, device="cuda")
+            torch.cuda.synchronize()
+            C.ccst_track_rois(t.ctx, rois, len(items), out)
+            torch.cuda.synchronize()
+            assert C.decode(out).tobytes() == want, (rep, st)
+            if rep == 0:
+                keep = out          # the graph captured for this out buffer
+            del out
+    # the same list on the same stream and output buffer replays its graph
+    out = torch.empty((len(items), 24), dtype=torch.uint8, device="cuda")
+    C.ccst_set_stream(t.ctx, streams[1].cuda_stream)
+    C.ccst_track_rois(t.ctx, rois, len(items), out)
+    g = C.ccst_graph_stats(t.ctx)
+    for _ in range(3):
+        C.ccst_track_rois(t.ctx, rois, len(items), out)
+    torch.cuda.synchronize()
+    g2 = C.ccst_graph_stats(t.ctx)
+    assert g2["instantiations"] == g["instantiations"] and g2["replays"] == g["replays"] + 3
+    assert 1 <= g["cached"] <= 7
+    assert C.decode(out).tobytes() == want
+    C.ccst_add_reference(t.ctx, items[0][0], 48, 48)          # drops the captured graphs
+    C.ccst_track_rois(t.ctx, rois, len(items), out)
+    torch.cuda.synchronize()
+    g3 = C.ccst_graph_stats(t.ctx)
+    assert g3["cached"] == 1 and g3["instantiations"] == g2["instantiations"] + 1
+    assert C.decode(out).tobytes() == want
+    del keep
+    t.close()
+
+
+def test_power_of_two_work_list_is_captured_once(torch):
+    # a list with no general-size ROI on a context without general plans: one capture, then
+    # replays only
+    items = uneven([32, 64, 16, 128, 32, 64], seed=23)
+    t = C.Tracker(synth.gaussian_spot(32, 32, 16, 16, 2.0, 500.0, 10.0).astype(np.float32), upsample=50,
+                  in_dtype="f32", graphs=True, stream=torch.cuda.Stream())
+    ids = [C.ccst_add_reference(t.ctx, r, *r.shape) for r, _ in items]
+    rois = C.make_rois([dev(torch, f) for _, f in items], ids)
+    out = t.empty_results(len(items))
+    for _ in range(5):
+        C.ccst_track_rois(t.ctx, rois, len(items), out)
+    C.ccst_sync(t.ctx)
+    assert C.ccst_graph_stats(t.ctx) == {"instantiations": 1, "replays": 5, "cached": 1}
+    t.close()
