@@ -36,6 +36,10 @@ namespace {
 constexpr int kTickets = 64;      // in-flight submissions per context
 constexpr int kHostSlots = 4;     // staging slots of the pipelined host path
 constexpr size_t kMaxGraphs = 512;
+// static shared memory beside the dynamic plan: the tensor-core state of the 128 x 128
+// kernels (TcShared), and in the ROI kernel also its Geom and work-item index
+constexpr int kTcStaticSmem = 64;
+constexpr int kRoisStaticSmem = (int)sizeof(Geom) + 128;
 
 // Guard thresholds, in units of the FP32 unit roundoff eps32 times sum w|X|. Each is a
 // multiple of the largest surface error measured against the FP64 oracle at that level:
@@ -64,9 +68,13 @@ __global__ void init_tables(Geom g, float* cm1, float* sA, float* wc, float* ws,
     const long long Dy = (long long)g.u * g.H, Dx = (long long)g.u * g.W;
     const int nA = g.Hh * g.T1p, nB = g.Wc * g.T1p;
     const int Hq = g.Hh / 2, SAq = g.SA / 2, T1 = g.T1p, T8 = g.T1p8;
-    const int nAh = 2 * g.TAB * Hq, nBh = 2 * T1 * SAq, nBn = 2 * T8;
+    // the tensor-core tables: uint2 fp16 pairs (warp-level form), or with g.tc single fp16
+    // values of four 128-byte-swizzled K-major matrices each (stage A: [cos - 1, sin] x
+    // [hi, lo], RA rows t - 1, K = m - 1; stage B: [w cos, w sin] x [hi, lo], T1p8 rows tx,
+    // K = kx)
+    const int nAh = g.tc ? 4 * g.RA * 64 : 2 * g.TAB * Hq, nBh = g.tc ? 4 * T8 * 64 : 2 * T1 * SAq, nBn = 2 * T8;
     const float s13 = 8192.f;                                // 2^13: table scale of the fp16 pairs
-    float* bn = (float*)(tbh + nBh);
+    float* bn = g.tc ? (float*)((unsigned char*)tbh + (size_t)4 * T8 * 128) : (float*)(tbh + nBh);
     // w cos, w sin and w (cos - 1) of 2 pi kx' t/(uW), kx' the signed frequency (W/2 -> -W/2)
     auto wcs = [&](int kx, int t, float* a, float* b, float* c) {
         const int kxs = (kx < g.W / 2) ? kx : kx - g.W;
@@ -101,6 +109,24 @@ __global__ void init_tables(Geom g, float* cm1, float* sA, float* wc, float* ws,
             const int k = i - nA;
             const int kx = k / g.T1p, t = k % g.T1p;
             wcs(kx, t, &wc[k], &ws[k], &gc[k]);
+        } else if (g.tc && i < nA + nB + nAh) {
+            const int k = i - nA - nB;
+            const int mat = k / (g.RA * 64), rem = k - mat * g.RA * 64, ta = rem / 64, kk = rem - ta * 64;
+            float c1, s1;
+            cm1_s(kk + 1, ta + 1, &c1, &s1);
+            const float v = s13 * (mat < 2 ? c1 : s1);
+            const __half hi = __float2half_rn(v);
+            const __half out = (mat & 1) ? __float2half_rn(v - __half2float(hi)) : hi;
+            *(__half*)((unsigned char*)tah + (size_t)mat * g.RA * 128 + sw128_off(ta, kk)) = out;
+        } else if (g.tc && i < nA + nB + nAh + nBh) {
+            const int k = i - nA - nB - nAh;
+            const int mat = k / (T8 * 64), rem = k - mat * T8 * 64, tx = rem / 64, kx = rem - tx * 64;
+            float a, b, d;
+            wcs(kx, tx, &a, &b, &d);
+            const float v = s13 * (mat < 2 ? a : b);
+            const __half hi = __float2half_rn(v);
+            const __half out = (mat & 1) ? __float2half_rn(v - __half2float(hi)) : hi;
+            *(__half*)((unsigned char*)tbh + (size_t)mat * T8 * 128 + sw128_off(tx, kx)) = out;
         } else if (i < nA + nB + nAh) {
             // stage-A pairs: [cm1 | s][t - 1][pair p of m = 2p+1, 2p+2], pairs swizzled by row
             const int k = i - nA - nB;
@@ -203,6 +229,8 @@ bool plan_geometry(int H, int W, const ccst_params& p, size_t smem_limit, Geom* 
     g.sense = p.method == CCST_CC_U ? 1.f : -1.f;
     g.tau_int = kTauInt; g.tau0 = kTau0; g.tau1 = kTau1;
     g.guard = (p.flags & CCST_FLAG_TIE_GUARD) ? 1 : 0;
+    // the 128 x 128 kernels hold the tensor-core state in static shared memory
+    if (H == 128 && W == 128) smem_limit -= kTcStaticSmem;
     const int h15 = ((g.h0 + 14) / 15) * 15;
     for (int smem_tables = 1; smem_tables >= 0; --smem_tables) {
         for (int tc = h15; tc >= 15; tc -= 15) {
@@ -210,6 +238,17 @@ bool plan_geometry(int H, int W, const ccst_params& p, size_t smem_limit, Geom* 
             g.nchunk = (g.h0 + tc - 1) / tc;
             g.TAB = g.nchunk * tc;
             g.tables_smem = smem_tables;
+            g.tc = 0;
+            // the 5th-generation tensor-core contraction: 128 x 128 frames (K = 64 in both
+            // stages), one chunk, tables in shared memory, every operand and accumulator
+            // within 128 rows / lanes
+            if (H == 128 && W == 128 && smem_tables && g.nchunk == 1 && tc <= 128 && g.T1p8 <= 128) {
+                Geom t = g;
+                t.tc = 1;
+                t.RA = (t.TAB + 7) & ~7;
+                t.NB = (t.TC + 15) & ~15;
+                if (t.RA <= 128 && t.NB <= 128 && smem_plan(t).total <= smem_limit) { *out = t; return true; }
+            }
             if (smem_plan(g).total <= smem_limit) { *out = g; return true; }
         }
     }
@@ -1064,7 +1103,8 @@ extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pi
     d_work = nullptr;
     c->kernel = track_kernel_for(H, W);
     // the attribute is per function: set it to the device limit so contexts of any size coexist
-    if (!step(cudaFuncSetAttribute(c->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit),
+    if (!step(cudaFuncSetAttribute(c->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)limit - ((H == 128 && W == 128) ? kTcStaticSmem : 0)),
               "smem attribute"))
         return bail(CCST_E_CUDA);
     int occ = 0;
@@ -1943,7 +1983,9 @@ static int rois_plan(ccst_ctx* c, int H, int W, int* cls) {
     CK(c, cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     ccst_ctx::SizePlan sp;
     Geom& g = sp.g;
-    if (!plan_geometry(H, W, c->p, (size_t)limit, &g)) return fail(c, CCST_E_SHAPE, "ccst_add_reference: frame too large");
+    // the ROI kernel keeps its Geom, work-item index and tensor-core state in static shared memory
+    if (!plan_geometry(H, W, c->p, (size_t)(limit - kRoisStaticSmem), &g))
+        return fail(c, CCST_E_SHAPE, "ccst_add_reference: frame too large");
     const long long Dy = (long long)g.u * H, Dx = (long long)g.u * W;
     g.By = 1; while ((long long)g.By * g.By < Dy) ++g.By;
     g.Bx = 1; while ((long long)g.Bx * g.Bx < Dx) ++g.Bx;
@@ -2090,7 +2132,7 @@ static int rois_upload(ccst_ctx* c) {
     int limit = 0, occ = 0, sms = 0;
     CK(c, cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-    CK(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, limit - (int)sizeof(Geom) - 64));
+    CK(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, limit - kRoisStaticSmem));
     CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kThreads, smem));
     if (occ < 1) return fail(c, CCST_E_SHAPE, "ccst_track_rois: the ROI kernel does not fit on an SM");
     c->rois_smem = smem;
@@ -3244,7 +3286,8 @@ int static_setup(int dev, StaticDevice* out) {
         for (int h = 8; h <= 128; h *= 2)
             for (int w = 8; w <= 128; w *= 2) {
                 if ((e = cudaFuncSetAttribute(track_kernel_for(h, w), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)d.smem_limit)) != cudaSuccess) {
+                                              (int)d.smem_limit - ((h == 128 && w == 128) ? kTcStaticSmem : 0))) !=
+                    cudaSuccess) {
                     snprintf(g_static_err, sizeof(g_static_err), "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
                     return CCST_E_CUDA;
                 }

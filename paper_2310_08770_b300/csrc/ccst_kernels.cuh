@@ -44,6 +44,7 @@
 
 #include "ccst_device.cuh"
 #include "ccst_fft.cuh"
+#include "ccst_tc.cuh"
 #include <cuda_fp16.h>
 
 namespace ccst {
@@ -68,6 +69,8 @@ struct Geom {
     float eps, sense;                   // sense = +1 (CC-U maximum) or -1 (CC-SN minimum)
     float tau_int, tau0, tau1;          // guard thresholds, relative to sum w|X|
     int guard;                          // tie guard on/off
+    int tc;                             // the contraction runs on tcgen05 (H = W = 128, one chunk, tables in smem)
+    int RA, NB;                         // tc: rows of a stage-A table matrix (TAB rounded to 8), stage-B N (TC to 16)
     // resident device data (owned by the context)
     const float2* FE32;                 // H x Wc   F[b]
     const double2* FE64;                // H x Wc   F[b] in FP64
@@ -326,14 +329,66 @@ struct SmemPlan {
     size_t a, xn, r1, b, zc, ta, tb, uv, uvn, r2, misc, total;
 };
 
-// sizes (bytes) of the two tensor-core table blocks
-__host__ __device__ inline size_t ta_bytes(const Geom& g) { return sizeof(uint2) * 2 * (size_t)g.TAB * (g.Hh / 2); }
+// sizes (bytes) of the two tensor-core table blocks. With g.tc: stage A's four matrices
+// (2^13 (cos - 1) and 2^13 sin, fp16 hi and lo each; rows t - 1, K = m - 1) and stage B's four
+// (2^13 w cos and 2^13 w sin, hi and lo; rows tx, K = kx), 128-byte-swizzled K-major, then
+// the kx = W/2 column in FP32.
+__host__ __device__ inline size_t ta_bytes(const Geom& g) {
+    if (g.tc) return (size_t)4 * g.RA * 128;
+    return sizeof(uint2) * 2 * (size_t)g.TAB * (g.Hh / 2);
+}
 __host__ __device__ inline size_t tb_bytes(const Geom& g) {
+    if (g.tc) return (size_t)4 * g.T1p8 * 128 + sizeof(float) * 2 * (size_t)g.T1p8;
     return sizeof(uint2) * 2 * (size_t)g.T1p * (g.SA / 2) + sizeof(float) * 2 * (size_t)g.T1p8;
 }
 __host__ __device__ inline size_t table_bytes(const Geom& g) { return ta_bytes(g) + tb_bytes(g); }
 
+// The tcgen05 plan (g.tc). R1 starts on a 1024-byte boundary (the dynamic base is padded at
+// run time; the total counts 1024 for it). R1 holds the spectrum, then the P/Q planes as eight
+// matrices [Pr, Pi, Qr, Qi] x [hi, lo] of SA rows (kx) by 64 K values (m - 1). R2 in the
+// contraction phase: TB (the stage-B tables, read as 128-row A operands: rows past T1p8 fall
+// in what follows), then one block that holds TA (stage A's A operands, also read as 128
+// rows) and, once stage A has finished, CB: stage B's B operands, eight matrices
+// [C0, C1, E0, E1] x [hi, lo] of NB rows (t) by 64 K values (kx). Then the scratch area UV
+// (R, partial sums, guard scratch) and UVN (the x-Nyquist combinations in FP32).
+__host__ __device__ inline SmemPlan smem_plan_tc(const Geom& g) {
+    SmemPlan p;
+    const size_t pq = (size_t)8 * g.SA * 128, spec = sizeof(float2) * (size_t)g.H * g.SA;
+    p.a = align_up(pq > spec ? pq : spec, 16);
+    p.xn = align_up(sizeof(float2) * (size_t)g.H, 16);
+    p.r1 = align_up(p.a + p.xn, 1024);
+    p.b = align_up(sizeof(float2) * (size_t)g.H * g.SA, 16);
+    p.zc = align_up(sizeof(float2) * (size_t)(g.H / 2) * g.SZ, 16);
+    const size_t fft = p.b + p.zc;
+    p.tb = align_up(tb_bytes(g), 1024);
+    const size_t ta_read = (size_t)4 * g.RA * 128 + (size_t)(128 - g.RA) * 128;   // last matrix read as 128 rows
+    const size_t cb = (size_t)8 * g.NB * 128;
+    p.ta = align_up(ta_read > cb ? ta_read : cb, 1024);
+    // the epilogue stages float2 [2][TC][T1p8] over TB and this block
+    const size_t stg = sizeof(float2) * 2 * (size_t)g.TC * g.T1p8;
+    if (p.tb + p.ta < stg) p.ta = align_up(stg - p.tb, 1024);
+    size_t rscr = sizeof(float2) * ((size_t)g.Wcp + 8 * (size_t)(g.SA + 1)) + sizeof(float) * 2 * kGParts * (size_t)g.T1p;
+    const size_t gscr = sizeof(float2) * (size_t)(4 * g.Wc + 23 * g.H + 17);
+    const size_t dscr = sizeof(double2) * (size_t)(2 * g.H + 2 * g.Wc);
+    if (rscr < gscr) rscr = gscr;
+    if (rscr < dscr) rscr = dscr;
+    p.uv = align_up(rscr, 16);
+    p.uvn = align_up(sizeof(float4) * (size_t)g.TC, 16);
+    const size_t k6 = p.tb + p.ta + p.uv + p.uvn;
+    p.r2 = fft > k6 ? fft : k6;
+    const size_t chunk = (size_t)g.W > (size_t)(g.H + g.Wc) ? (size_t)g.W : (size_t)(g.H + g.Wc);
+    const size_t dfl = sizeof(dfc) * ((size_t)g.H * g.Wcp + (size_t)(g.Ntw / 2) + g.W + g.H + chunk);
+    if (p.r1 + p.r2 < dfl) p.r2 = align_up(dfl - p.r1, 16);
+    p.misc = sizeof(double) * 32 + 16 + sizeof(float2) * (size_t)(g.Wc + g.Hh + 1) +
+             sizeof(float2) * (size_t)(g.Ntw / 2 + g.H + g.W) + sizeof(float2) * (size_t)g.SA +
+             sizeof(float) * 2 * (size_t)g.T1p + sizeof(float) * 64 + sizeof(int) * 64 +
+             (sizeof(int) + sizeof(float)) * kMaxCand + sizeof(int) * 16 + 64;
+    p.total = align_up(1024 + p.r1 + p.r2 + p.misc, 16);
+    return p;
+}
+
 __host__ __device__ inline SmemPlan smem_plan(const Geom& g) {
+    if (g.tc) return smem_plan_tc(g);
     SmemPlan p;
     p.a = align_up(sizeof(float2) * (size_t)g.H * g.SA, 16);
     p.xn = align_up(sizeof(float2) * (size_t)g.H, 16);
@@ -376,6 +431,7 @@ __host__ __device__ inline SmemPlan smem_plan(const Geom& g) {
 static __device__ inline Smem carve(const Geom& g, unsigned char* base) {
     const SmemPlan p = smem_plan(g);
     Smem s;
+    if (g.tc) base += (1024u - (smem_addr(base) & 1023u)) & 1023u;     // R1 on a 1024-byte boundary
     s.r1 = base;
     s.A = (float2*)base;
     s.XN = (float2*)(base + p.a);
@@ -383,11 +439,18 @@ static __device__ inline Smem carve(const Geom& g, unsigned char* base) {
     s.B = (float2*)r2;
     s.ZC = (float2*)(r2 + p.b);
     s.PQ = (uint2*)base;
-    s.TA = (uint2*)r2;
-    s.TB = (uint2*)(r2 + p.ta);
-    s.UV = (float4*)(r2 + p.ta + p.tb);
-    s.UVN = (float4*)(r2 + p.ta + p.tb + p.uv);
-    s.CB = (uint2*)s.UV;
+    if (g.tc) {
+        s.TB = (uint2*)r2;
+        s.TA = (uint2*)(r2 + p.tb);
+        s.UV = (float4*)(r2 + p.tb + p.ta);
+        s.UVN = (float4*)(r2 + p.tb + p.ta + p.uv);
+    } else {
+        s.TA = (uint2*)r2;
+        s.TB = (uint2*)(r2 + p.ta);
+        s.UV = (float4*)(r2 + p.ta + p.tb);
+        s.UVN = (float4*)(r2 + p.ta + p.tb + p.uv);
+    }
+    s.CB = g.tc ? s.TA : (uint2*)s.UV;      // tc: stage B's operands replace the stage-A tables
     s.CBN = (float*)s.UVN;
     s.r12_bytes = p.r1 + p.r2;
     unsigned char* m = r2 + p.r2;
@@ -826,7 +889,27 @@ static __device__ void build_pq_and_g(const Geom& g, const Smem& S, int py, int 
         }
     }
     __syncthreads();
-    if (mine) {
+    if (mine && g.tc) {
+        // eight matrices [Pr hi, Pi hi, Pr lo, Pi lo, Qr hi, Qi hi, Qr lo, Qi lo] (so that Pr and
+        // Pi, and Qr and Qi, form one 2 SA-row operand): row c, K = m - 1; the pair (m1, m2) is
+        // two adjacent K values, one 32-bit store per matrix
+        unsigned char* pqb = (unsigned char*)S.PQ;
+        const size_t ms = (size_t)SA * 128;
+#pragma unroll
+        for (int j = 0; j < kMaxPairs; ++j) {
+            const int p = part + 8 * j;
+            if (p >= Hq) break;
+            const uint32_t off = sw128_off(c, 2 * p);
+            const uint2 v[4] = {split_pair(pq[j][0].x, pq[j][2].x), split_pair(pq[j][0].y, pq[j][2].y),
+                                split_pair(pq[j][1].x, pq[j][3].x), split_pair(pq[j][1].y, pq[j][3].y)};
+#pragma unroll
+            for (int pl = 0; pl < 4; ++pl) {
+                const int mi = (pl >> 1) * 4 + (pl & 1);
+                *(unsigned*)(pqb + mi * ms + off) = v[pl].x;
+                *(unsigned*)(pqb + (mi + 2) * ms + off) = v[pl].y;
+            }
+        }
+    } else if (mine) {
         const int sw = pswz(c, Hq);
 #pragma unroll
         for (int j = 0; j < kMaxPairs; ++j) {
@@ -912,7 +995,19 @@ __device__ __forceinline__ void stage_a_nyquist(const Geom& g, const Smem& S, in
             const int ta = t0 - 1 + lt, sw = pswz(ta, Hq);
             for (int p = Hq - 1 - part; p >= 0; p -= 4) {
                 const int m1 = 2 * p + 1, m2 = 2 * p + 2;
-                const float2 cm = unsplit_pair(Tc[ta * Hq + (p ^ sw)]), sn = unsplit_pair(Ts[ta * Hq + (p ^ sw)]);
+                float2 cm, sn;
+                if (g.tc) {
+                    // matrices [cos - 1, sin] x [hi, lo] of RA rows; row ta, K = m - 1
+                    const size_t ms = (size_t)g.RA * 128;
+                    const unsigned char* b = (const unsigned char*)TA + sw128_off(ta, 2 * p);
+                    const __half2 ch = *(const __half2*)b, cl = *(const __half2*)(b + ms);
+                    const __half2 shv = *(const __half2*)(b + 2 * ms), slv = *(const __half2*)(b + 3 * ms);
+                    cm = make_float2(__low2float(ch) + __low2float(cl), __high2float(ch) + __high2float(cl));
+                    sn = make_float2(__low2float(shv) + __low2float(slv), __high2float(shv) + __high2float(slv));
+                } else {
+                    cm = unsplit_pair(Tc[ta * Hq + (p ^ sw)]);
+                    sn = unsplit_pair(Ts[ta * Hq + (p ^ sw)]);
+                }
                 const float2 p1 = S.XN[posH(g, m1)], p2 = S.XN[posH(g, m2)], q1 = S.XN[posH(g, H - m1)];
                 const float2 q2 = (m2 == Hh) ? make_float2(-p2.x, -p2.y) : S.XN[posH(g, H - m2)];
                 acc.x = fmaf(cm.x * un, p1.x, fmaf(cm.y * un, p2.x, acc.x));
@@ -1216,10 +1311,242 @@ __device__ __forceinline__ void stage_b_simt(const Geom& g, const Smem& S, int t
     }
 }
 
+// The upsampled surface on the 5th-generation tensor cores (g.tc: H = W = 128, one chunk,
+// tables in shared memory). One thread issues every MMA; the accumulators live in Tensor
+// Memory, and the other threads never hold them in registers.
+//   Stage A: D_a[t][kx] = sum_m T[t][m] P_a[kx][m] for a = (Cm1 Pr, Cm1 Pi, S Qr, S Qi), four
+//   M = 128 (t rows; rows past TC are discarded), N = 64 (kx), K = 64 (m) accumulators in
+//   columns 64 a, each as lo*hi + hi*lo + hi*hi of the fp16 pairs.
+//   Its rows are read back one t row per lane, combined (C0, C1, E0, E1) and written as
+//   stage B's fp16 pair operands over the stage-A tables.
+//   Stage B: D_b[tx][t] = sum_kx Wtab[tx][kx] CE_b[t][kx] for b = (wc C0, ws E0, wc C1, ws E1),
+//   four M = 128 (tx lanes), N = NB (t) accumulators in columns NB b; the epilogue feeds
+//   the same Emitter as the warp-level form. The x-Nyquist column and the t = 0 row are FP32,
+//   as in the other forms.
+// A batch of MMAs that does not complete within the bounded wait marks the CTA failed
+// (TcShared::failed): no further MMA is issued and the caller stops the CTA.
+template <bool kCollect>
+__device__ void upsampled_pass_tc(const Geom& g, const Smem& S, TopK<kTopK>& top, float thr, float* dbg) {
+    TcShared* ts = tc_shared();
+    const uint32_t tmem = ts->tmem, bar = smem_addr(&ts->bar);
+    const float dsc = ldexpf(1.f, -13 - S.misc[3]);
+    const float un = ldexpf(1.f, -13);
+    const Emitter<kCollect> emit{g, S, top, thr, dbg};
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, sp = warp & 3, grp = warp >> 2;
+    const int SA = g.SA, TC = g.TC, NB = g.NB, RA = g.RA, T8 = g.T1p8;
+    const uint32_t pq = smem_addr(S.PQ), ta = smem_addr(S.TA), tb = smem_addr(S.TB);
+    unsigned char* cb = (unsigned char*)S.CB;
+    const uint32_t lanes = (uint32_t)(32 * sp) << 16;          // this warp's Tensor Memory lanes
+    constexpr int kWait = 1 << 22;
+    // the P/Q planes were written by ordinary stores: make them visible to the tensor cores
+    tc_fence_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const bool live = ts->failed == 0;
+    // the MMAs are issued by the last thread, idle in the x-Nyquist step (4 TC items) and in
+    // the t = 0 row (h0 + 1 items) that run beside them; issue takes about as long as the MMAs
+    const bool issuer = threadIdx.x == blockDim.x - 1;
+    if (issuer && live) {
+        // two N = 2 SA MMAs: U = Cm1 [Pr; Pi] (columns 0 .. 127), V = S [Qr; Qi] (128 .. 255)
+        const uint32_t id = tc_idesc(128, 2 * SA);
+        for (int a = 0; a < 2; ++a) {
+            const uint32_t am = ta + (uint32_t)(2 * a * RA * 128), al = am + (uint32_t)(RA * 128);
+            const uint32_t bm = pq + (uint32_t)(4 * a * SA * 128), bl = bm + (uint32_t)(2 * SA * 128);
+            const uint32_t d = tmem + (uint32_t)(2 * SA * a);
+            for (int st = 0; st < 4; ++st) {
+                const uint32_t ko = 32u * st;
+                tc_mma(d, tc_desc(al + ko), tc_desc(bm + ko), id, st > 0 ? 1u : 0u);
+                tc_mma(d, tc_desc(am + ko), tc_desc(bl + ko), id, 1u);
+                tc_mma(d, tc_desc(am + ko), tc_desc(bm + ko), id, 1u);
+            }
+        }
+        tc_commit(bar);
+    }
+    stage_a_nyquist(g, S, 1, S.TA);                            // FP32, beside the MMAs
+    bool ok = live && tc_bar_wait(bar, ts->batches & 1u, kWait);
+    tc_fence_after();
+    if (__syncthreads_or(live && !ok)) {
+        if (threadIdx.x == 0) ts->failed = 1;
+    }
+    const bool liveA = live && __syncthreads_and(ok);          // (also: the table reads are done)
+    if (threadIdx.x == 0 && live) ts->batches++;
+    // stage A read back: lane = t row lt, this warp's 16 kx of each accumulator
+    {
+        const int lt = 32 * sp + lane;
+        float ur[16], ui[16], vr[16], vi[16];
+        tc_ld16(tmem + lanes + 0 * 64 + 16 * grp, ur);
+        tc_ld16(tmem + lanes + 1 * 64 + 16 * grp, ui);
+        tc_ld16(tmem + lanes + 2 * 64 + 16 * grp, vr);
+        tc_ld16(tmem + lanes + 3 * 64 + 16 * grp, vi);
+        tc_ld_wait();
+        if (lt < NB && liveA) {
+            const size_t ms = (size_t)NB * 128;
+            const bool row = lt < TC;
+#pragma unroll
+            for (int j = 0; j < 16; j += 2) {
+                const uint32_t off = sw128_off(lt, 16 * grp + j);
+                float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+                if (row) {
+                    a = combos(ur[j] * un, ui[j] * un, vr[j] * un, vi[j] * un);
+                    b = combos(ur[j + 1] * un, ui[j + 1] * un, vr[j + 1] * un, vi[j + 1] * un);
+                }
+                const uint2 v[4] = {split_pair(a.x, b.x), split_pair(a.y, b.y), split_pair(a.z, b.z), split_pair(a.w, b.w)};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    // [C0 hi, C1 hi, C0 lo, C1 lo, E0 hi, E1 hi, E0 lo, E1 lo]
+                    const int mi = (c >> 1) * 4 + (c & 1);
+                    *(unsigned*)(cb + mi * ms + off) = v[c].x;
+                    *(unsigned*)(cb + (mi + 2) * ms + off) = v[c].y;
+                }
+            }
+        }
+    }
+    tc_fence_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (issuer && liveA) {
+        // two N = 2 NB MMAs: wc [C0; C1] (columns 0 .. 2 NB - 1: A0, A1) and ws [E0; E1]
+        // (2 NB .. 4 NB - 1: B0, B1)
+        const uint32_t id = tc_idesc(128, 2 * NB);
+        const uint32_t cbs = smem_addr(cb);
+        for (int b = 0; b < 2; ++b) {
+            const uint32_t am = tb + (uint32_t)(2 * b * T8 * 128), al = am + (uint32_t)(T8 * 128);
+            const uint32_t bm = cbs + (uint32_t)(4 * b * NB * 128), bl = bm + (uint32_t)(2 * NB * 128);
+            const uint32_t d = tmem + (uint32_t)(2 * NB * b);
+            for (int st = 0; st < 4; ++st) {
+                const uint32_t ko = 32u * st;
+                tc_mma(d, tc_desc(al + ko), tc_desc(bm + ko), id, st > 0 ? 1u : 0u);
+                tc_mma(d, tc_desc(am + ko), tc_desc(bl + ko), id, 1u);
+                tc_mma(d, tc_desc(am + ko), tc_desc(bm + ko), id, 1u);
+            }
+        }
+        tc_commit(bar);
+    }
+    // the t = 0 row: S = 0, the surface is g(tx)
+    float vmax = -INFINITY;                                     // this thread's largest surface value
+    for (int x = threadIdx.x; x <= g.h0; x += blockDim.x) {
+        if (x <= g.pmax) { emit(S.gP[x], 0, x); vmax = fmaxf(vmax, g.sense * S.gP[x]); }
+        if (x >= 1) { emit(S.gM[x], 0, -x); vmax = fmaxf(vmax, g.sense * S.gM[x]); }
+    }
+    ok = liveA && tc_bar_wait(bar, ts->batches & 1u, kWait);
+    tc_fence_after();
+    if (__syncthreads_or(liveA && !ok)) {
+        if (threadIdx.x == 0) ts->failed = 1;
+    }
+    const bool liveB = liveA && __syncthreads_and(ok);
+    if (threadIdx.x == 0 && liveA) ts->batches++;
+    // epilogue, in two steps. The warps that own the accumulator lanes (tx rows; only the
+    // tx <= h0 of them matter, so one SMSP's warps would idle) move the final stage-B values
+    // (A, B) of each (sign, t, tx), with the x-Nyquist terms, into the dead table area as
+    // float2 [sg][lt][tx]; then every warp feeds the Emitter from there.
+    float2* stg = (float2*)S.TB;                                // TB + TA/CB are dead now
+    {
+        const int x = 32 * sp + lane;
+        const bool xok = liveB && x <= g.h0;
+        const float* WCN = (const float*)((const unsigned char*)S.TB + (size_t)4 * T8 * 128);
+        const float* WSN = WCN + T8;
+        const float wcn = xok ? WCN[x] : 0.f, wsn = xok ? WSN[x] : 0.f;
+        __syncthreads();                                        // the weights are read before stg overwrites them
+        const int q = NB >> 2;
+        for (int c = grp * q; c < grp * q + q; c += 4) {
+            float a0[4], a1[4], b0[4], b1[4];
+            tc_ld4(tmem + lanes + c, a0);
+            tc_ld4(tmem + lanes + NB + c, a1);
+            tc_ld4(tmem + lanes + 2 * NB + c, b0);
+            tc_ld4(tmem + lanes + 3 * NB + c, b1);
+            tc_ld_wait();
+            if (!xok) continue;
+            const float gpx = S.gP[x], gmx = S.gM[x];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int lt = c + i, t = 1 + lt;
+                if (lt >= TC) continue;
+                const float2 v0 = make_float2(fmaf(wcn, S.CBN[lt], a0[i] * dsc), fmaf(wsn, S.CBN[2 * TC + lt], b0[i] * dsc));
+                const float2 v1 = make_float2(fmaf(wcn, S.CBN[TC + lt], a1[i] * dsc), fmaf(wsn, S.CBN[3 * TC + lt], b1[i] * dsc));
+                stg[(size_t)lt * T8 + x] = v0;
+                stg[(size_t)(TC + lt) * T8 + x] = v1;
+                if (t <= g.h0) {                                // the grid points of rows +-t
+                    if (t <= g.pmax && x <= g.pmax) vmax = fmaxf(vmax, g.sense * (v0.x - v0.y + gpx));
+                    if (t <= g.pmax && x >= 1) vmax = fmaxf(vmax, g.sense * (v0.x + v0.y + gmx));
+                    if (x <= g.pmax) vmax = fmaxf(vmax, g.sense * (v1.x - v1.y + gpx));
+                    if (x >= 1) vmax = fmaxf(vmax, g.sense * (v1.x + v1.y + gmx));
+                }
+            }
+        }
+    }
+    // the surface's maximum: only points within the near-tie band of it can matter, so the
+    // top-K pass pushes no point below it minus the band (thr = the (0, 0) value minus the
+    // band; 1% slack keeps the raised threshold below the one the guard applies later)
+    for (int o = 16; o; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    if (lane == 0) S.rv[warp] = vmax;
+    __syncthreads();
+    if (!kCollect && !dbg) {
+        float m = -INFINITY;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, S.rv[w]);
+        const float band = g.sense * S.gP[0] - thr;
+        const float raised = m - 1.01f * band;
+        if (raised > thr) thr = raised;
+    }
+    __syncthreads();
+    if (liveB) {
+        // one staged row (sign, t) per warp at a time, tx = lane + 32 k: the row's loads are
+        // issued together before its points are emitted
+        const int nt = TC < g.h0 ? TC : g.h0, nwarp = blockDim.x >> 5;
+        // this lane's columns: g(+-tx) and whether +tx / -tx are grid points, hoisted out
+        // of the row loop; the surface values are sense * (A -+ B + g(+-tx))
+        float gp[4], gm[4];
+        bool okp[4], okm[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int x = lane + 32 * k;
+            const bool in = x <= g.h0;
+            gp[k] = in ? S.gP[x] : 0.f;
+            gm[k] = in ? S.gM[x] : 0.f;
+            okp[k] = in && x <= g.pmax;
+            okm[k] = in && x >= 1;
+        }
+        const float sense = g.sense;
+        for (int r = warp; r < 2 * nt; r += nwarp) {
+            const int sg = r >= nt ? 1 : 0, lt = r - sg * nt, t = 1 + lt, ts = sg ? -t : t;
+            const bool rowok = sg || t <= g.pmax;
+            const float2* row = stg + (size_t)(sg * TC + lt) * T8;
+            float2 v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int x = lane + 32 * k;
+                v[k] = x <= g.h0 ? row[x] : make_float2(0.f, 0.f);
+            }
+            if (dbg) {                                          // debug surfaces: the generic path
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (lane + 32 * k <= g.h0) emit.quad(sg, t, lane + 32 * k, v[k].x, v[k].y);
+                continue;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float vp = sense * (v[k].x - v[k].y + gp[k]), vm = sense * (v[k].x + v[k].y + gm[k]);
+                if (rowok && okp[k] && vp >= thr) emit.keep(vp, ts, lane + 32 * k);
+                if (rowok && okm[k] && vm >= thr) emit.keep(vm, ts, -(lane + 32 * k));
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+}
+
 // Full upsampled surface pass (all chunks): top-K, or candidate collection.
 template <int H, int W, bool kCollect>
 __device__ __forceinline__ void upsampled_pass(const Geom& g, const Smem& S, TopK<kTopK>& top, float thr,
                                                float* dbg) {
+    if constexpr (H == 128 && W == 128) {
+        if (g.tc) {
+            upsampled_pass_tc<kCollect>(g, S, top, thr, dbg);
+            return;
+        }
+    }
     const uint2* TA = g.tables_smem ? S.TA : g.tAh;
     const uint2* TB = g.tables_smem ? S.TB : g.tBh;
     const float dsc = ldexpf(1.f, -13 - S.misc[3]);
@@ -1257,7 +1584,20 @@ static __device__ int collect_near(const Geom& g, const Smem& S, float thr) {
 // X'(ky, kx) for any row and column, from the P/Q layout.
 // P(m, kx) and Q(m, kx), m = 1 .. Hh, of a regular column from the fp16 planes (unscaled
 // by inv = 2^-kexp)
+// (tc layout) plane pl (Pr, Pi, Qr, Qi) at row kx, K index k: hi + lo
+__device__ __forceinline__ float pq_tc(const Geom& g, const Smem& S, int pl, int kx, int k) {
+    const size_t ms = (size_t)g.SA * 128;
+    const unsigned char* b = (const unsigned char*)S.PQ + (size_t)((pl >> 1) * 4 + (pl & 1)) * ms + sw128_off(kx, k);
+    return __half2float(*(const __half*)b) + __half2float(*(const __half*)(b + 2 * ms));
+}
+
 __device__ __forceinline__ void pq_at(const Geom& g, const Smem& S, int m, int kx, float inv, float2* P, float2* Q) {
+    if (g.tc) {
+        const int k = m - 1;
+        *P = make_float2(pq_tc(g, S, 0, kx, k) * inv, pq_tc(g, S, 1, kx, k) * inv);
+        *Q = make_float2(pq_tc(g, S, 2, kx, k) * inv, pq_tc(g, S, 3, kx, k) * inv);
+        return;
+    }
     const int SA = g.SA, Hq = g.Hh / 2, k = m - 1, q = (k >> 1) ^ pswz(kx, Hq);
     const float2 pr = unsplit_pair(S.PQ[(0 * SA + kx) * Hq + q]), pi = unsplit_pair(S.PQ[(1 * SA + kx) * Hq + q]);
     const float2 qr = unsplit_pair(S.PQ[(2 * SA + kx) * Hq + q]), qi = unsplit_pair(S.PQ[(3 * SA + kx) * Hq + q]);
@@ -1326,6 +1666,13 @@ struct XRow {
     }
     __device__ __forceinline__ float2 at(const Geom& g, const Smem& S, int kx) const {
         if (mode == 0) return S.X0[kx];
+        if (g.tc) {
+            const int k = 2 * p + h;
+            const float pr = pq_tc(g, S, 0, kx, k), pi = pq_tc(g, S, 1, kx, k);
+            if (mode == 1) return make_float2(sa * pr, sa * pi);
+            const float qr = pq_tc(g, S, 2, kx, k), qi = pq_tc(g, S, 3, kx, k);
+            return make_float2(fmaf(sa, pr, sb * qr), fmaf(sa, pi, sb * qi));
+        }
         const int SA = g.SA, Hq = g.Hh / 2, q = p ^ pswz(kx, Hq);
         auto half = [&](uint2 v) {
             const float2 hh = unpack_f16x2(v.x), ll = unpack_f16x2(v.y);
@@ -1728,6 +2075,24 @@ __device__ __forceinline__ void track_setup(const Geom& g, const Smem& S) {
     build_pass_twiddles<W>(S.t4w, S.tw, g.logNtw);
 }
 
+// A tensor-core batch of this CTA never completed (upsampled_pass_tc): the frame's record
+// says so (CCST_R_TIMEOUT) and the CTA must stop. CTA-uniform (read after a barrier).
+template <int H, int W>
+__device__ __forceinline__ bool tc_failed(const Geom& g, const Batch& b, long long f, unsigned flags) {
+    if constexpr (H == 128 && W == 128) {
+        if (g.tc && tc_shared()->failed) {
+            if (threadIdx.x == 0) {
+                Result r{};
+                r.flags = flags | 0x20u;
+                b.out[f] = r;
+            }
+            __syncthreads();
+            return true;
+        }
+    }
+    return false;
+}
+
 // a1-a7 for one frame (rows b.pitch elements apart) against the reference of g; the record
 // goes to b.out[f], and f indexes the optional debug outputs of b. Returns false when the
 // stage tables never arrived (the record says so; the CTA must stop).
@@ -1780,6 +2145,7 @@ __device__ __forceinline__ bool track_frame(const Geom& g, const Batch& b, const
     // no point below the (0, 0) point's value minus the near-tie band can matter
     const float lb = g.sense * S.gP[0] - g.tau0 * scale;
     upsampled_pass<H, W, false>(g, S, top, lb, dbg);
+    if (tc_failed<H, W>(g, b, f, flags)) return false;
     float vw = top.v[0];
     int jw = top.j[0];
     block_argmax(vw, jw, S.rv, S.rj);
@@ -1817,6 +2183,7 @@ __device__ __forceinline__ bool track_frame(const Geom& g, const Batch& b, const
             } else {
                 // a thread holds more near-ties than it kept: collect them all with a second pass
                 nc = collect_near<H, W>(g, S, thr);
+                if (tc_failed<H, W>(g, b, f, flags)) return false;
                 if (nc > kMaxCand) {
                     flags |= 0x08u;
                     nc = 1;
@@ -1861,6 +2228,9 @@ __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
     track_setup<H, W>(g, S);
     tables_bar_init(S);
     unsigned bar_parity = 0;
+    if constexpr (H == 128 && W == 128) {
+        if (g.tc) tc_setup();                       // Tensor Memory for the contraction
+    }
     __syncthreads();
     const size_t elem = g.in_dtype == 0 ? 2 : 4;
     // next frame: from the shared counter (every thread has read the current index at the
@@ -1874,7 +2244,10 @@ __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
     };
     for (long long f = fetch(-1); f < b.n; f = fetch(f)) {
         const char* frame = (const char*)b.frames + (size_t)f * g.H * b.pitch * elem;
-        if (!track_frame<H, W>(g, b, S, f, frame, bar_parity)) return;
+        if (!track_frame<H, W>(g, b, S, f, frame, bar_parity)) break;
+    }
+    if constexpr (H == 128 && W == 128) {
+        if (g.tc) tc_teardown();                    // every exit path releases the columns
     }
 }
 

@@ -24,6 +24,9 @@ __global__ void __launch_bounds__(kThreads, 1) track_rois_kernel(RoiBatch rb) {
     int cur = -1;                      // size class of the current set-up
     unsigned parity = 0;
     Smem S{};
+    // Tensor Memory for the 128 x 128 class's tensor-core contraction; one CTA per SM (the
+    // register file is full), so the allocation never waits on another CTA
+    tc_setup();
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_item = (long long)atomicAdd(rb.next, 1u);
@@ -68,8 +71,9 @@ __global__ void __launch_bounds__(kThreads, 1) track_rois_kernel(RoiBatch rb) {
             case 64: ok = track_frame<64, 64>(sg, b, S, it.out_index, frame, parity); break;
             default: ok = track_frame<128, 128>(sg, b, S, it.out_index, frame, parity); break;
         }
-        if (!ok) return;
+        if (!ok) break;
     }
+    tc_teardown();
 }
 
 const void* track_rois_kernel_ptr() { return (const void*)track_rois_kernel; }
