@@ -43,7 +43,8 @@ FP32_LANES_PER_SM = 128          # FFMA lanes per SM (4 SMSPs x 32)
 MAX_SM_MHZ = 2032.0
 PROFILE_FILE = os.path.join(ROOT, "profiles", "track_kernel_128x128_u100.txt")
 KERNEL_SOURCES = ["paper_2310_08770_b300/csrc/ccst_kernels.cuh", "paper_2310_08770_b300/csrc/ccst_device.cuh",
-                  "paper_2310_08770_b300/csrc/ccst_dfloat.cuh", "paper_2310_08770_b300/csrc/ccst_fft.cuh"]
+                  "paper_2310_08770_b300/csrc/ccst_dfloat.cuh", "paper_2310_08770_b300/csrc/ccst_fft.cuh",
+                  "paper_2310_08770_b300/csrc/ccst_tc.cuh"]
 
 
 def grid_size(u):
