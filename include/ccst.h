@@ -85,8 +85,14 @@ extern "C" {
 #define CCST_R_NONFINITE   0x10u /* the surface held no finite value (non-finite input) */
 #define CCST_R_TIMEOUT     0x20u /* a bounded wait inside the kernel gave up (the staged stage tables never
                                     arrived); this frame and the rest of its CTA's frames are not tracked */
-#define CCST_R_GENERIC     0x80u /* tracked by the general-size path (ccst_track_rois, sides other than
-                                    16, 32, 64, 128): direct DFTs in double-float, no near-tie levels */
+#define CCST_R_GENERIC     0x80u /* tracked by the double-float general-size kernel (ccst_track_rois,
+                                    sides other than 16, 32, 64, 128): direct DFTs in double-float,
+                                    no near-tie levels */
+#define CCST_R_FP32_GENERAL 0x100u /* tracked by the FP32 general-size kernel (square sides 48, 96,
+                                    192 and 256, u <= 256): mixed-radix (2, 3) FFTs and the
+                                    upsampled contraction in FP32, with the integer and sub-pixel
+                                    guard levels; a frame they cannot certify is tracked again by
+                                    the double-float kernel and its record carries CCST_R_GENERIC */
 #define CCST_R_RT_STALE    0x40u /* real-time mode: the reference update after this frame did not complete
                                     (a bounded wait gave up, now or earlier); the reference stays stale
                                     until the next ccst_rt_begin */

@@ -14,9 +14,9 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libccst.so")
-SOURCES = ["ccst.cu", "ccst_rois.cu", "ccst_generic.cu", "ccst_peak.cu"] + [f"ccst_track_h{h}.cu" for h in (8, 16, 32, 64, 128)]
+SOURCES = ["ccst.cu", "ccst_rois.cu", "ccst_generic.cu", "ccst_mixed.cu", "ccst_peak.cu"] + [f"ccst_track_h{h}.cu" for h in (8, 16, 32, 64, 128)]
 DEPS = SOURCES + ["ccst_kernels.cuh", "ccst_device.cuh", "ccst_dfloat.cuh", "ccst_fft.cuh", "ccst_adjoint.cuh",
-        "ccst_generic.cuh"]
+        "ccst_generic.cuh", "ccst_mixed.cuh", "ccst_mixfft.cuh", "ccst_tc.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -28,6 +28,7 @@ R_NONFINITE = 0x10
 R_TIMEOUT = 0x20
 R_RT_STALE = 0x40
 R_GENERIC = 0x80
+R_FP32_GENERAL = 0x100
 
 OK, E_INVALID, E_SHAPE, E_UNSUPPORTED, E_NOMEM, E_CUDA, E_TIMEOUT, E_BUSY = 0, -1, -2, -3, -4, -5, -6, -7
 _CODES = {0: "OK", -1: "E_INVALID", -2: "E_SHAPE", -3: "E_UNSUPPORTED", -4: "E_NOMEM",

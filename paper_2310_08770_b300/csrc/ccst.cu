@@ -25,6 +25,7 @@
 #include "ccst_kernels.cuh"
 #include "ccst_adjoint.cuh"
 #include "ccst_generic.cuh"
+#include "ccst_mixed.cuh"
 
 using namespace ccst;
 
@@ -50,6 +51,19 @@ constexpr float kEps32 = 1.1920929e-07f;
 constexpr float kTauInt = 32.0f * kEps32;
 constexpr float kTau0 = 1.0f * kEps32;
 constexpr float kTau1 = 0.02f * kEps32;
+// The same three levels for the FP32 general-size kernel (ccst_mixed.cu), whose frames
+// fall back to the double-float kernel when a level cannot decide. Largest errors measured
+// against the FP64 oracle (sides 48 to 256, u = 100, in eps32 sum w|X|): integer surface
+// 4.1, peak-relative surface 0.056 (CC-U) and 0.0083 (CC-SN), pair differences 0.0014
+// (CC-U) and 0.0003 (CC-SN). Each threshold keeps at least an 8x margin; a level-1 winner
+// must lead by 2 tau1 (two differences, each within tau1). CC-SN gets its own because its
+// sum w|X| is dominated by the DC term, which the peak-relative sums never see.
+constexpr float kMixTauInt = 32.0f * kEps32;
+constexpr float kMixTau0 = 1.0f * kEps32;
+constexpr float kMixTau1 = 0.02f * kEps32;
+constexpr float kMixTau0Sn = 0.125f * kEps32;
+constexpr float kMixTau1Sn = 0.005f * kEps32;
+constexpr int kMixCounters = 8;     // per lane: [0] fallback count, [1 + s] item counter of FP32 segment s
 
 std::mutex g_create_err_mu;
 std::string g_create_err = "no error";
@@ -608,11 +622,16 @@ struct GenLane {
     size_t scratch_elems = 0;
     GenItem* d_items = nullptr;
     size_t items_cap = 0;
+    GenItem* d_fb = nullptr;        // the FP32 kernel's fallback list
+    size_t fb_cap = 0;
+    unsigned* d_mixc = nullptr;     // kMixCounters counters of the FP32 kernel's launches
 };
 
 static void lane_free(GenLane& l) {
     if (l.scratch) cudaFree(l.scratch);
     if (l.d_items) cudaFree(l.d_items);
+    if (l.d_fb) cudaFree(l.d_fb);
+    if (l.d_mixc) cudaFree(l.d_mixc);
     l = GenLane{};
 }
 
@@ -683,6 +702,9 @@ struct ccst_ctx {
     struct GenPlanH {
         GenPlan p;
         std::vector<void*> mem;
+        MixPlan mp{};                 // the FP32 general-size kernel's plan, if `mix`
+        bool mix = false;
+        int mix_grid = 0;             // resident CTAs of that kernel (whole clusters)
     };
     std::vector<SizePlan> plans;
     std::vector<RefEntry> refs;
@@ -922,7 +944,8 @@ static void free_all(ccst_ctx* c) {
         if (p) cudaFree(p);
 }
 
-static int gen_track(ccst_ctx* c, const Batch& b, cudaStream_t stream, GenLane& lane, unsigned* counter);
+static int gen_track(ccst_ctx* c, const Batch& b, cudaStream_t stream, GenLane& lane, unsigned* counter,
+                     const MixDbg* dbg = nullptr);
 static int gen_ref_spectrum(ccst_ctx* c, int H, int W, const void* src, int frame_kind, long long pitch, dfc* Fb);
 static int add_generic_reference(ccst_ctx* c, const float* ref, int H, int W, int* ref_id);
 static int not_general(ccst_ctx* c, const char* who);
@@ -1483,9 +1506,23 @@ extern "C" int ccst_debug_surfaces(ccst_ctx* c, const void* frames_dev, int64_t 
                                    ccst_result* out_dev, float* int_surf_dev, float* sub_surf_dev) {
     int rc = check_ctx(c);
     if (rc) return rc;
-    if ((rc = not_general(c, "ccst_debug_surfaces"))) return rc;
+    if (c->general && !c->gplans[c->refs[0].gcls].mix) return not_general(c, "ccst_debug_surfaces");
     Batch b;
     if ((rc = make_batch(c, frames_dev, n, pitch_elems, out_dev, &b))) return rc;
+    if (c->general) {
+        // the FP32 general-size kernel's surfaces; frames it cannot certify still get their
+        // records from the double-float kernel
+        if (n == 0) return CCST_OK;
+        cudaError_t e;
+        const unsigned k = ring_acquire(c, c->stream, &e);
+        CK(c, e);
+        CK(c, shared_acquire(c, c->stream));
+        const MixDbg dbg{int_surf_dev, sub_surf_dev, nullptr, nullptr};
+        if ((rc = gen_track(c, b, c->stream, c->glane[0], c->d_launch_counters + k, &dbg))) return rc;
+        CK(c, ring_release(c, k, c->stream));
+        CK(c, shared_release(c, c->stream));
+        return CCST_OK;
+    }
     b.dbg_int = int_surf_dev;
     b.dbg_sub = sub_surf_dev;
     return launch(c, b);
@@ -1531,10 +1568,24 @@ extern "C" int ccst_debug_pairs(ccst_ctx* c, const void* frames_dev, int64_t n, 
                                 const int32_t* pairs_dev, float* d32_dev, double* d64_dev) {
     int rc = check_ctx(c);
     if (rc) return rc;
-    if ((rc = not_general(c, "ccst_debug_pairs"))) return rc;
+    if (c->general && !c->gplans[c->refs[0].gcls].mix) return not_general(c, "ccst_debug_pairs");
     if (!pairs_dev || !d32_dev || !d64_dev) return fail(c, CCST_E_INVALID, "null pair buffers");
     Batch b;
     if ((rc = make_batch(c, frames_dev, n, pitch_elems, (ccst_result*)c->d_out, &b))) return rc;
+    if (c->general) {
+        // the FP32 general-size kernel's pair-difference level; it has no FP64 variant (NaN)
+        if (n == 0) return CCST_OK;
+        CK(c, cudaMemsetAsync(d64_dev, 0xFF, (size_t)n * sizeof(double), c->stream));
+        cudaError_t e;
+        const unsigned k = ring_acquire(c, c->stream, &e);
+        CK(c, e);
+        CK(c, shared_acquire(c, c->stream));
+        const MixDbg dbg{nullptr, nullptr, pairs_dev, d32_dev};
+        if ((rc = gen_track(c, b, c->stream, c->glane[0], c->d_launch_counters + k, &dbg))) return rc;
+        CK(c, ring_release(c, k, c->stream));
+        CK(c, shared_release(c, c->stream));
+        return CCST_OK;
+    }
     b.dbg_pairs = pairs_dev;
     b.dbg_d32 = d32_dev;
     b.dbg_d64 = d64_dev;
@@ -2193,6 +2244,48 @@ static int gen_plan(ccst_ctx* c, int H, int W, int* gcls) {
         cudaFree(tab);
         return fail(c, CCST_E_CUDA, std::string("gen_init_tables: ") + cudaGetErrorString(e));
     }
+    if (!pl.exhaustive && H == W && mix_side_ok(H)) {
+        // the FP32 kernel for this side, with this kernel as its fallback
+        int optin = 0;
+        CK(c, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+        void* mm = nullptr;
+        const bool sn = c->p.method == CCST_CC_SN;
+        const int mrc = mix_plan_create(H, W, u, c->p.method, c->p.in_dtype, c->p.eps, kMixTauInt,
+                                        sn ? kMixTau0Sn : kMixTau0, sn ? kMixTau1Sn : kMixTau1, optin, &gp.mp, &mm);
+        if (mrc > 0) {
+            for (void* q : gp.mem) cudaFree(q);
+            return fail(c, CCST_E_CUDA, std::string("FP32 general-size plan: ") + cudaGetErrorString((cudaError_t)mrc));
+        }
+        if (mrc == 0) {
+            gp.mem.push_back(mm);
+            const void* k = mix_kernel_ptr(H, W);
+            const int cl = gp.mp.CL;
+            cudaError_t ea = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, gp.mp.smem);
+            int sms = 0, resident = 0;
+            if (ea == cudaSuccess) ea = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+            if (ea == cudaSuccess && cl == 1) {
+                int occ = 0;
+                ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 512, gp.mp.smem);
+                resident = occ * sms;
+            } else if (ea == cudaSuccess) {
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3((unsigned)(cl * sms));
+                cfg.blockDim = dim3(512);
+                cfg.dynamicSmemBytes = (size_t)gp.mp.smem;
+                int ncl = 0;
+                ea = cudaOccupancyMaxActiveClusters(&ncl, k, &cfg);
+                resident = ncl * cl;
+            }
+            if (ea != cudaSuccess) {
+                for (void* q : gp.mem) cudaFree(q);
+                return fail(c, CCST_E_CUDA, std::string("FP32 general-size kernel: ") + cudaGetErrorString(ea));
+            }
+            if (resident >= cl) {
+                gp.mix = true;
+                gp.mix_grid = resident;
+            }
+        }
+    }
     c->gplans.push_back(gp);
     *gcls = (int)c->gplans.size() - 1;
     c->rois_dirty = true;
@@ -2291,16 +2384,108 @@ static int gen_prepare(ccst_ctx* c) {
     return CCST_OK;
 }
 
-// The general-size kernel over gb.n frames on `stream` (gb.items already on the device, or
-// null for a uniform batch), with per-CTA scratch of `stride` elements: counter reset, launch.
-static int gen_kernel_launch(ccst_ctx* c, GenBatch gb, dfc* scratch, long long stride, cudaStream_t stream,
-                             unsigned* counter) {
-    const int grid = (int)(gb.n < c->gen_grid ? gb.n : c->gen_grid);
+// The FP32 kernel's device state of a lane for batches of up to n items: its counters and
+// a fallback list of n items. *grew: a buffer was (re)allocated (graphs that captured the
+// old ones must go).
+static int mix_reserve(ccst_ctx* c, GenLane& lane, long long n, bool* grew) {
+    *grew = false;
+    if (!lane.d_mixc) {
+        CK(c, cudaMalloc(&lane.d_mixc, kMixCounters * sizeof(unsigned)));
+        *grew = true;
+    }
+    if (lane.fb_cap < (size_t)n) {
+        if (lane.d_fb) cudaFree(lane.d_fb);
+        lane.d_fb = nullptr;
+        lane.fb_cap = 0;
+        CK(c, cudaMalloc(&lane.d_fb, (size_t)n * sizeof(GenItem)));
+        lane.fb_cap = (size_t)n;
+        *grew = true;
+    }
+    return CCST_OK;
+}
+
+static bool any_mix_plan(ccst_ctx* c) {
+    for (auto& g : c->gplans)
+        if (g.mix) return true;
+    return false;
+}
+
+// The general-size launches over gb.n frames on `stream` (gb.items already on the device,
+// ordered by gen_sort, with `items_host` its host copy; or null for a uniform batch).
+// Items whose plan has the FP32 kernel come last, equal plans together: each such run is
+// one FP32 launch, and the frames it cannot certify join a fallback list. Then the double-
+// float kernel, with per-CTA scratch of `stride` elements, takes the other items and the
+// fallback list. dbg: the FP32 kernel's diagnostic outputs (uniform batches).
+static int gen_kernel_launch(ccst_ctx* c, GenBatch gb, GenLane& lane, long long stride, cudaStream_t stream,
+                             unsigned* counter, const GenItem* items_host, const MixDbg* dbg = nullptr) {
+    struct Seg { long long first, n; int plan; };
+    Seg segs[kMixCounters - 1];
+    int ns = 0;
+    long long ndirect = gb.n;
+    if (!gb.items) {
+        if (c->gplans[gb.plan].mix) {
+            segs[ns++] = Seg{0, gb.n, gb.plan};
+            ndirect = 0;
+        }
+    } else if (items_host) {
+        long long i = 0;
+        while (i < gb.n && !c->gplans[items_host[i].plan].mix) ++i;
+        ndirect = i;
+        while (i < gb.n && ns < kMixCounters - 1) {
+            long long j = i;
+            while (j < gb.n && items_host[j].plan == items_host[i].plan) ++j;
+            segs[ns++] = Seg{i, j - i, items_host[i].plan};
+            i = j;
+        }
+        if (i < gb.n) return fail(c, CCST_E_INVALID, "general-size batch: too many FP32 plans in one batch");
+    }
+    const long long ntot = gb.n;
+    gb.fb_items = nullptr;
+    gb.fb_count = nullptr;
+    if (ns > 0) {
+        if (!lane.d_mixc || lane.fb_cap < (size_t)(ntot - ndirect))
+            return fail(c, CCST_E_INVALID, "general-size batch: FP32 lane state not reserved");
+        CK(c, cudaMemsetAsync(lane.d_mixc, 0, (size_t)(1 + ns) * sizeof(unsigned), stream));
+        for (int k = 0; k < ns; ++k) {
+            const ccst_ctx::GenPlanH& gp = c->gplans[segs[k].plan];
+            MixArgs ma{};
+            ma.items = gb.items;
+            ma.first = segs[k].first;
+            ma.n = segs[k].n;
+            ma.frames = gb.frames;
+            ma.frame_bytes = gb.frame_bytes;
+            ma.pitch = gb.pitch;
+            ma.plan = gb.plan;
+            ma.ref = gb.ref;
+            ma.p = gp.mp;
+            ma.refs = c->d_grefs;
+            ma.out = gb.out;
+            ma.next = lane.d_mixc + 1 + k;
+            ma.fb = lane.d_fb;
+            ma.fb_count = lane.d_mixc;
+            if (dbg) {
+                ma.dbg_int = dbg->dbg_int;
+                ma.dbg_sub = dbg->dbg_sub;
+                ma.dbg_pairs = dbg->pairs;
+                ma.dbg_d32 = dbg->d32;
+            }
+            const int cl = gp.mp.CL;
+            const long long want = segs[k].n * cl;
+            const int grid = (int)(want < gp.mix_grid ? want : gp.mix_grid) / cl * cl;
+            void* margs[] = {&ma};
+            CK(c, cudaLaunchKernel(mix_kernel_ptr(gp.mp.H, gp.mp.W), dim3(grid), dim3(512), margs,
+                                   (size_t)gp.mp.smem, stream));
+        }
+        gb.fb_items = lane.d_fb;
+        gb.fb_count = lane.d_mixc;
+    }
+    const int grid = (int)(ntot < c->gen_grid ? ntot : c->gen_grid);
+    gb.n = ndirect;
     CK(c, cudaMemsetAsync(counter, 0, sizeof(unsigned), stream));
     gb.plans = c->d_gplans;
     gb.refs = c->d_grefs;
     gb.next = counter;
-    gb.scratch = scratch;
+    gb.scratch = lane.scratch;
     gb.scratch_stride = stride;
     void* args[] = {&gb};
     CK(c, cudaLaunchKernel(track_generic_kernel_ptr(), dim3(grid), dim3(c->gen_threads), args, 0, stream));
@@ -2318,7 +2503,7 @@ static long long gen_stride(ccst_ctx* c) {
 // (copied to the lane at once; the caller orders it) or, if null, the uniform batch that
 // gb describes. gb.out is set by the caller; the rest is filled in here.
 static int gen_launch(ccst_ctx* c, GenLane& lane, GenBatch gb, const GenItem* items_host, cudaStream_t stream,
-                      unsigned* counter) {
+                      unsigned* counter, const MixDbg* dbg = nullptr) {
     if (gb.n == 0) return CCST_OK;
     int rc = gen_prepare(c);
     if (rc) return rc;
@@ -2343,19 +2528,27 @@ static int gen_launch(ccst_ctx* c, GenLane& lane, GenBatch gb, const GenItem* it
         CK(c, cudaMemcpyAsync(lane.d_items, items_host, (size_t)gb.n * sizeof(GenItem), cudaMemcpyHostToDevice, stream));
         gb.items = lane.d_items;
     }
-    return gen_kernel_launch(c, gb, lane.scratch, stride, stream, counter);
+    if (any_mix_plan(c)) {
+        bool grew = false;
+        if ((rc = mix_reserve(c, lane, gb.n, &grew))) return rc;
+    }
+    return gen_kernel_launch(c, gb, lane, stride, stream, counter, items_host, dbg);
 }
 
-// Largest frames first (the longest work starts first; equal shapes stay together).
+// Items of plans without the FP32 kernel first, then those with it; within each part the
+// largest frames first (the longest work starts first; equal plans stay together).
 static void gen_sort(ccst_ctx* c, GenItem* items, int64_t n) {
     std::stable_sort(items, items + n, [&](const GenItem& a, const GenItem& b) {
-        const GenPlan &pa = c->gplans[a.plan].p, &pb = c->gplans[b.plan].p;
-        return pa.H * pa.W > pb.H * pb.W;
+        const auto &ga = c->gplans[a.plan], &gb = c->gplans[b.plan];
+        if (ga.mix != gb.mix) return !ga.mix;
+        if (ga.p.H * ga.p.W != gb.p.H * gb.p.W) return ga.p.H * ga.p.W > gb.p.H * gb.p.W;
+        return a.plan < b.plan;
     });
 }
 
 // A batch of a general-shape context: frame i at frames + i * H * pitch elements.
-static int gen_track(ccst_ctx* c, const Batch& b, cudaStream_t stream, GenLane& lane, unsigned* counter) {
+static int gen_track(ccst_ctx* c, const Batch& b, cudaStream_t stream, GenLane& lane, unsigned* counter,
+                     const MixDbg* dbg) {
     const size_t elem = c->p.in_dtype == CCST_U16 ? 2 : 4;
     GenBatch gb{};
     gb.n = b.n;
@@ -2365,7 +2558,7 @@ static int gen_track(ccst_ctx* c, const Batch& b, cudaStream_t stream, GenLane& 
     gb.pitch = b.pitch;
     gb.plan = c->refs[0].gcls;
     gb.ref = 0;
-    return gen_launch(c, lane, gb, nullptr, stream, counter);
+    return gen_launch(c, lane, gb, nullptr, stream, counter, dbg);
 }
 
 // Two-level splits worth timing for an N-point DFT: the default (largest divisor not above
@@ -2635,6 +2828,11 @@ static int rois_graph_track(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccst_r
                 CK(c, cudaMalloc(&lane->scratch, need * sizeof(dfc)));
                 lane->scratch_elems = need;
             }
+            if (any_mix_plan(c) && (!lane->d_mixc || lane->fb_cap < (size_t)ng)) {
+                drop_roi_graphs(c);
+                bool grew = false;
+                if ((rc = mix_reserve(c, *lane, ng, &grew))) return rc;
+            }
         }
         ccst_ctx::RoiGraph e;
         e.rois.assign(rois, rois + n);
@@ -2671,7 +2869,7 @@ static int rois_graph_track(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccst_r
             if (cudaEventRecord(c->gfork, c->stream) != cudaSuccess ||
                 cudaStreamWaitEvent(c->gstream, c->gfork, 0) != cudaSuccess)
                 lrc = fail(c, CCST_E_CUDA, "ccst_track_rois: fork during capture");
-            if (!lrc) lrc = gen_kernel_launch(c, gb, lane->scratch, stride, c->gstream, e.counters + 1);
+            if (!lrc) lrc = gen_kernel_launch(c, gb, *lane, stride, c->gstream, e.counters + 1, c->h_gitems.data());
             if (!lrc && cudaEventRecord(c->gjoin, c->gstream) != cudaSuccess)
                 lrc = fail(c, CCST_E_CUDA, "ccst_track_rois: join during capture");
         }

@@ -141,9 +141,12 @@ __global__ void __launch_bounds__(512) track_generic_kernel(GenBatch gb) {
         if (threadIdx.x == 0) s_item = (long long)atomicAdd(gb.next, 1u);
         __syncthreads();
         const long long item = s_item;
-        if (item >= gb.n) break;
+        const long long nfb = gb.fb_count ? (long long)*gb.fb_count : 0;
+        if (item >= gb.n + nfb) break;
         GenItem it;
-        if (gb.items) {
+        if (item >= gb.n) {
+            it = gb.fb_items[item - gb.n];
+        } else if (gb.items) {
             it = gb.items[item];
         } else {
             it.frame = (const char*)gb.frames + item * gb.frame_bytes;

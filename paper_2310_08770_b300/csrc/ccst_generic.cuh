@@ -62,6 +62,10 @@ struct GenBatch {
     long long frame_bytes;
     long long pitch;
     int plan, ref;
+    // frames the FP32 general-size kernel (ccst_mixed.cu) could not certify: items n ..
+    // n + *fb_count - 1 of this launch are fb_items[0 ..] (null: none)
+    const GenItem* fb_items;
+    const unsigned* fb_count;
 };
 
 // Kernel addresses (ccst_generic.cu).

@@ -167,7 +167,7 @@ def test_general_size_cameras_equal_the_roi_path(torch):
                               len(frames), out)
             C.ccst_sync(t.ctx)
             for i, r in enumerate(C.decode(out)):
-                assert bool(r["flags"] & C.R_GENERIC) == (frames.shape[-1] != 64)
+                assert bool(r["flags"] & (C.R_GENERIC | C.R_FP32_GENERAL)) == (frames.shape[-1] != 64)
                 want[(k, i)] = r.tobytes()
         tickets = [((k, i), submit_wait(srv, ids[k], cams[k][1][i])) for i in range(8) for k in range(len(cams))]
         for key, tk in tickets:
