@@ -51,18 +51,22 @@ constexpr float kEps32 = 1.1920929e-07f;
 constexpr float kTauInt = 32.0f * kEps32;
 constexpr float kTau0 = 1.0f * kEps32;
 constexpr float kTau1 = 0.02f * kEps32;
-// The same three levels for the FP32 general-size kernel (ccst_mixed.cu), whose frames
-// fall back to the double-float kernel when a level cannot decide. Largest errors measured
-// against the FP64 oracle (sides 48 to 256, u = 100, in eps32 sum w|X|): integer surface
-// 4.1, peak-relative surface 0.056 (CC-U) and 0.0083 (CC-SN), pair differences 0.0014
-// (CC-U) and 0.0003 (CC-SN). Each threshold keeps at least an 8x margin; a level-1 winner
-// must lead by 2 tau1 (two differences, each within tau1). CC-SN gets its own because its
-// sum w|X| is dominated by the DC term, which the peak-relative sums never see.
+// The same three levels for the FP32 general-size kernel (ccst_mixed.cu), which re-decides
+// what they leave open from a double-float spectrum and otherwise falls back to the double-
+// float kernel. Largest errors measured against the FP64 oracle (u = 100, in eps32 sum w|X|):
+//   integer surface                 4.1 (all sides, both methods)
+//   peak-relative surface, CC-U     0.056 (sides 48 to 256)
+//   the same, CC-SN                 0.0083 at 48, 0.0068 at 96, 0.0030 at 192, 0.0013 at 256
+//   pair differences                0.0014 (CC-U), 0.0003 (CC-SN)
+// Each threshold keeps an 8x margin or more; a level-1 winner must lead by 2 tau1 (two
+// differences, each within tau1). CC-SN gets its own because its sum w|X| is dominated by
+// the DC term, which the peak-relative sums never see; and the larger its side, the more
+// that term dominates, so its tau0 falls with the side.
 constexpr float kMixTauInt = 32.0f * kEps32;
 constexpr float kMixTau0 = 1.0f * kEps32;
 constexpr float kMixTau1 = 0.02f * kEps32;
-constexpr float kMixTau0Sn = 0.125f * kEps32;
 constexpr float kMixTau1Sn = 0.005f * kEps32;
+static float mix_tau0_sn(int N) { return (N <= 96 ? 0.125f : N <= 192 ? 0.06f : 0.03f) * kEps32; }
 constexpr int kMixCounters = 8;     // per lane: [0] fallback count, [1 + s] item counter of FP32 segment s
 
 std::mutex g_create_err_mu;
@@ -2251,13 +2255,15 @@ static int gen_plan(ccst_ctx* c, int H, int W, int* gcls) {
         void* mm = nullptr;
         const bool sn = c->p.method == CCST_CC_SN;
         const int mrc = mix_plan_create(H, W, u, c->p.method, c->p.in_dtype, c->p.eps, kMixTauInt,
-                                        sn ? kMixTau0Sn : kMixTau0, sn ? kMixTau1Sn : kMixTau1, optin, &gp.mp, &mm);
+                                        sn ? mix_tau0_sn(H) : kMixTau0, sn ? kMixTau1Sn : kMixTau1, optin, &gp.mp, &mm);
         if (mrc > 0) {
             for (void* q : gp.mem) cudaFree(q);
             return fail(c, CCST_E_CUDA, std::string("FP32 general-size plan: ") + cudaGetErrorString((cudaError_t)mrc));
         }
         if (mrc == 0) {
             gp.mem.push_back(mm);
+            gp.mp.uHd = pl.uH;                         // the double-float level's phase tables
+            gp.mp.uWd = pl.uW;
             const void* k = mix_kernel_ptr(H, W);
             const int cl = gp.mp.CL;
             cudaError_t ea = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, gp.mp.smem);
@@ -2265,12 +2271,12 @@ static int gen_plan(ccst_ctx* c, int H, int W, int* gcls) {
             if (ea == cudaSuccess) ea = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
             if (ea == cudaSuccess && cl == 1) {
                 int occ = 0;
-                ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 512, gp.mp.smem);
+                ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, gp.mp.NT, gp.mp.smem);
                 resident = occ * sms;
             } else if (ea == cudaSuccess) {
                 cudaLaunchConfig_t cfg = {};
                 cfg.gridDim = dim3((unsigned)(cl * sms));
-                cfg.blockDim = dim3(512);
+                cfg.blockDim = dim3((unsigned)gp.mp.NT);
                 cfg.dynamicSmemBytes = (size_t)gp.mp.smem;
                 int ncl = 0;
                 ea = cudaOccupancyMaxActiveClusters(&ncl, k, &cfg);
@@ -2473,7 +2479,7 @@ static int gen_kernel_launch(ccst_ctx* c, GenBatch gb, GenLane& lane, long long 
             const long long want = segs[k].n * cl;
             const int grid = (int)(want < gp.mix_grid ? want : gp.mix_grid) / cl * cl;
             void* margs[] = {&ma};
-            CK(c, cudaLaunchKernel(mix_kernel_ptr(gp.mp.H, gp.mp.W), dim3(grid), dim3(512), margs,
+            CK(c, cudaLaunchKernel(mix_kernel_ptr(gp.mp.H, gp.mp.W), dim3(grid), dim3((unsigned)gp.mp.NT), margs,
                                    (size_t)gp.mp.smem, stream));
         }
         gb.fb_items = lane.d_fb;

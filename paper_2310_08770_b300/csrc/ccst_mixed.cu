@@ -43,7 +43,9 @@ namespace cg = cooperative_groups;
 namespace ccst {
 namespace mix {
 
-constexpr int kNT = 512;          // threads per CTA
+// threads per CTA: 512, and 384 for the 256-pixel kernel (whose 16-point register DFTs
+// want more than the 128 registers a 512-thread CTA leaves each thread)
+__host__ __device__ constexpr int mix_threads(int H) { return H >= 256 ? 384 : 512; }
 constexpr int kTM = 8;            // t rows per contraction task
 
 template <int CL>
@@ -164,8 +166,172 @@ struct Geo {
     static_assert(N2h > 1 && N2r > 1, "two-pass lengths only");
 };
 
+    // Level 2: the candidates S.gj[0, nc) re-evaluated from a double-float product
+    // spectrum (about 48 significant bits) computed here: the forward transforms of the
+    // rows and the band's columns in double-float into [0, off_small) (the FP32 band and
+    // the work area are no longer needed), then per candidate the double-float kernel's
+    // own sums, cu(j) = sum_kx g Re[e^{2 pi i kx' qx/(uW)} sum_ky X(ky, kx) e^{2 pi i ky' qy/(uH)}],
+    // qy = py u + ty, qx = px u + tx (the y-Nyquist row through its real part in the
+    // folded columns). Returns the winner's slot in S.gj and its raw value, or -1 when the
+    // two best are within 2^-36 sum g|X| (a tie in all but name: the fallback decides it
+    // exactly as the double-float kernel does everywhere).
 template <int H, int W, int CL>
-__global__ void __launch_bounds__(kNT, 1) __cluster_dims__(CL, 1, 1) mix_track_kernel(const MixArgs a) {
+__device__ __forceinline__ int mix_level2(const MixArgs& a, const MixSh& S, unsigned char* mix_smem, const GenItem& it,
+                                          const dfc* Fb, int nc, int py, int px, float scale, double* vbest) {
+    using Gm = Geo<H, W, CL>;
+    constexpr int L = Gm::L, Wc = Gm::Wc, RH = Gm::RH, KB = Gm::KB;
+    constexpr int N1h = Gm::N1h, N2h = Gm::N2h, N1r = Gm::N1r, N2r = Gm::N2r, RSG = Gm::RSG;
+    constexpr int NP = L / 2 + 1;
+    constexpr int kNT = mix_threads(H);
+    const MixPlan& P = a.p;
+    const int rank = Clu<CL>::rank(), tid = threadIdx.x;
+    const int b0 = rank * KB, nb = min(KB, Wc - b0), row0 = rank * RH;
+    const int M = P.M, h0 = P.h0;
+    const float sense = P.sense;
+    const int elem = P.in_dtype == 0 ? 2 : 4;
+    const char* frame = (const char*)it.frame;
+        dfc* Xd = reinterpret_cast<dfc*>(mix_smem);
+        dfc* Sd = reinterpret_cast<dfc*>(mix_smem + P.off_l2s);
+        df* cs = reinterpret_cast<df*>(mix_smem + P.off_l2c);
+        const int G2 = P.G2;
+        Clu<CL>::sync();
+        for (int g0 = 0; g0 < RH; g0 += G2) {
+            const char* rbase = frame + (size_t)(row0 + g0) * it.pitch * elem;
+            for (int i = tid; i < G2 * L; i += kNT) {
+                const int s2 = i / L, n = i - s2 * L;
+                const long long o = (long long)s2 * it.pitch + 2 * n;
+                float i0, i1;
+                if (elem == 2) {
+                    i0 = (float)__ldg((const unsigned short*)rbase + o);
+                    i1 = (float)__ldg((const unsigned short*)rbase + o + 1);
+                } else {
+                    i0 = __ldg((const float*)rbase + o);
+                    i1 = __ldg((const float*)rbase + o + 1);
+                }
+                df d0 = df_make(i0), d1 = df_make(i1);
+                if (P.method != 0) {                      // (I + eps)^2, exactly formed
+                    float sh, sl;
+                    two_sum(i0, P.eps, sh, sl);
+                    d0 = df_mul(df{sh, sl}, df{sh, sl});
+                    two_sum(i1, P.eps, sh, sl);
+                    d1 = df_mul(df{sh, sl}, df{sh, sl});
+                }
+                Sd[s2 * RSG + mix_phys<L>(n)] = dfc{d0, d1};
+            }
+            __syncthreads();
+            fwd_pass_s<N1r, N2r, false, kNT>(
+                G2, P.t4r_d, [&](int s2, int n2, int n1) { return Sd[s2 * RSG + mix_phys<L>(N2r * n1 + n2)]; },
+                [&](int s2, int n2, int k1, dfc v) { Sd[s2 * RSG + mix_phys<L>(N2r * k1 + n2)] = v; });
+            __syncthreads();
+            fwd_pass_c<N1r, N2r, false, kNT>(
+                G2, [&](int s2, int k1, int n2) { return Sd[s2 * RSG + mix_phys<L>(N2r * k1 + n2)]; },
+                [&](int s2, int k1, int k2, dfc v) { Sd[s2 * RSG + mix_phys<L>(N2r * k1 + k2)] = v; });
+            __syncthreads();
+            for (int task = tid; task < G2 * NP; task += kNT) {
+                const int s2 = task / NP, k = task - s2 * NP, y = row0 + g0 + s2;
+                const dfc* zr = Sd + s2 * RSG;
+                const dfc zk = zr[mix_phys<L>(mix_pos<L>(k))];
+                auto put = [&](int kx, dfc v) {
+                    const int r = kx / KB;
+                    Clu<CL>::at(Xd, r)[y * KB + (kx - r * KB)] = v;
+                };
+                const df zero{0.f, 0.f};
+                if (k == 0) {
+                    put(0, dfc{df_add_abs(zk.re, zk.im), zero});
+                    put(L, dfc{df_add_abs(zk.re, df_neg(zk.im)), zero});
+                } else {
+                    const dfc zm = zr[mix_phys<L>(mix_pos<L>(L - k))];
+                    const dfc fe = {df_scale(df_add_abs(zk.re, zm.re), 0.5f), df_scale(df_add_abs(zk.im, df_neg(zm.im)), 0.5f)};
+                    const dfc fo = {df_scale(df_add_abs(zk.im, zm.im), 0.5f), df_scale(df_add_abs(zm.re, df_neg(zk.re)), 0.5f)};
+                    const dfc rt = *reinterpret_cast<const dfc*>(P.rtw_d + k);
+                    const dfc t = cmul(rt, fo);
+                    put(k, cadd(fe, t));
+                    if (2 * k != L) put(L - k, cconj(csub(fe, t)));
+                }
+            }
+            __syncthreads();
+        }
+        Clu<CL>::sync();
+        fwd_pass_s<N1h, N2h, true, kNT>(
+            nb, P.t4h_d, [&](int c, int n2, int n1) { return Xd[(N2h * n1 + n2) * KB + c]; },
+            [&](int c, int n2, int k1, dfc v) { Xd[(N2h * k1 + n2) * KB + c] = v; });
+        __syncthreads();
+        fwd_pass_c<N1h, N2h, true, kNT>(
+            nb, [&](int c, int k1, int n2) { return Xd[(N2h * k1 + n2) * KB + c]; },
+            [&](int c, int k1, int k2, dfc v) {
+                const int ky = k1 + N1h * k2, kx = b0 + c;
+                const float4 f = __ldg(reinterpret_cast<const float4*>(Fb + (size_t)ky * Wc + kx));
+                Xd[(N2h * k1 + k2) * KB + c] = cmul(v, dfc{df{f.x, f.y}, df{-f.z, -f.w}});
+            });
+        __syncthreads();
+        // per (candidate, column): the double-float kernel's column sum and x-phase
+        const long long DH = (long long)P.u * H, DW = (long long)P.u * W;
+        for (int e = tid; e < nc * nb; e += kNT) {
+            const int k = e / nb, c = e - k * nb, kx = b0 + c, j = S.gj[k];
+            const bool folded = kx != 0 && kx != L;
+            const long long qy = (long long)py * P.u + j / M - h0, qx = (long long)px * P.u + j % M - h0;
+            dfc acc = {df{0.f, 0.f}, df{0.f, 0.f}};
+            for (int ky = 0; ky < H; ++ky) {
+                const long long ks = 2 * ky >= H ? ky - H : ky;
+                long long m = (ks * qy) % DH;
+                if (m < 0) m += DH;
+                const float4 ev = __ldg(reinterpret_cast<const float4*>(P.uHd + m));
+                dfc ey = {df{ev.x, ev.y}, df{ev.z, ev.w}};
+                if (2 * ky == H && folded) ey.im = df{0.f, 0.f};
+                acc = cadd(acc, cmul(Xd[mix_pos<H>(ky) * KB + c], ey));
+            }
+            long long mx = ((long long)(kx == L ? -L : kx) * qx) % DW;
+            if (mx < 0) mx += DW;
+            const float4 xv = __ldg(reinterpret_cast<const float4*>(P.uWd + mx));
+            df re = df_add_abs(df_mul(acc.re, df{xv.x, xv.y}), df_neg(df_mul(acc.im, df{xv.z, xv.w})));
+            if (folded) re = df_scale(re, 2.f);
+            cs[e] = re;
+        }
+        __syncthreads();
+        {
+            const int lane = tid & 31, wid = tid >> 5;
+            for (int k = wid; k < nc; k += kNT / 32) {
+                if (lane == 0) {
+                    df sum{0.f, 0.f};
+                    for (int c = 0; c < nb; ++c) sum = df_add_abs(sum, cs[k * nb + c]);
+                    S.cv[k] = sum.hi;
+                    S.cd[k] = sum.lo;
+                }
+            }
+        }
+        Clu<CL>::sync();
+        int kb = -1;
+        double bv = -INFINITY, second = -INFINITY;
+        for (int k = 0; k < nc; ++k) {
+            df tot{0.f, 0.f};
+            for (int r = 0; r < CL; ++r)
+                tot = df_add_abs(tot, df{Clu<CL>::at(S.cv, r)[k], Clu<CL>::at(S.cd, r)[k]});
+            const double v = (double)sense * df_to_double(tot);
+            if (kb < 0 || v > bv || (v == bv && S.gj[k] < S.gj[kb])) {
+                second = bv;
+                bv = v;
+                kb = k;
+            } else if (v > second) {
+                second = v;
+            }
+        }
+        Clu<CL>::sync();                                   // the partial sums are read
+        *vbest = (double)sense * bv;
+        return (bv - second > 0x1p-36 * (double)scale) ? kb : -1;
+    }
+
+// The 256-pixel kernel calls it out of line: its 16-point double-float DFTs do not fit
+// beside the main loop's registers. The smaller sides inline it, which spills nothing.
+template <int H, int W, int CL>
+__device__ __noinline__ int mix_level2_call(const MixArgs& a, const MixSh& S, unsigned char* mix_smem,
+                                            const GenItem& it, const dfc* Fb, int nc, int py, int px, float scale,
+                                            double* vbest) {
+    return mix_level2<H, W, CL>(a, S, mix_smem, it, Fb, nc, py, px, scale, vbest);
+}
+
+template <int H, int W, int CL>
+__global__ void __launch_bounds__(mix_threads(H), 1) __cluster_dims__(CL, 1, 1) mix_track_kernel(const MixArgs a) {
+    constexpr int kNT = mix_threads(H);
     using Gm = Geo<H, W, CL>;
     constexpr int L = Gm::L, Wc = Gm::Wc, Hh = Gm::Hh, RH = Gm::RH, KB = Gm::KB;
     constexpr int N1h = Gm::N1h, N2h = Gm::N2h, N1r = Gm::N1r, N2r = Gm::N2r, RSG = Gm::RSG;
@@ -520,19 +686,7 @@ __global__ void __launch_bounds__(kNT, 1) __cluster_dims__(CL, 1, 1) mix_track_k
             }
             __syncthreads();
         };
-        if (a.dbg_pairs) {
-            // diagnostic: v(jb) - v(ja) for the given pair, by level 1; no record
-            if (tid == 0) {
-                S.gj[0] = a.dbg_pairs[2 * idx];
-                S.gj[1] = a.dbg_pairs[2 * idx + 1];
-            }
-            __syncthreads();
-            pair_diffs(2, S.gj[0]);
-            if (rank == 0 && tid == 0) a.dbg_d32[idx] = S.cv[1];
-            continue;
-        }
-
-        // ---- a6: the contraction, chunk by chunk of t
+        // ---- a6: the contraction, chunk by chunk of t (skipped by the pair diagnostic)
         TopK<kTopK> top;
         top.init();
         const float lb = -P.tau0 * scale;                     // D(0, 0) = 0 is a candidate
@@ -558,7 +712,7 @@ __global__ void __launch_bounds__(kNT, 1) __cluster_dims__(CL, 1, 1) mix_track_k
         }
         const int TC = P.TC, TAp = P.TAp, TXp = P.TXp;
         const int ntx = (TX + 1) / 2;
-        for (int t0 = 1; t0 <= h0; t0 += TC) {
+        for (int t0 = 1; t0 <= (a.dbg_pairs ? 0 : h0); t0 += TC) {
             const int tcn = min(TC, h0 - t0 + 1), ntg = (tcn + kTM - 1) / kTM;
             // stage A: (C0, E0, C1, E1)(t, kx) for the band
             for (int task = tid; task < ntg * nb; task += kNT) {
@@ -651,9 +805,14 @@ __global__ void __launch_bounds__(kNT, 1) __cluster_dims__(CL, 1, 1) mix_track_k
             }
         }
 
-        // ---- a7: level 0 -- the best point and its near-ties within tau0
+        // ---- a7: level 0 -- the best point and its near-ties within tau0 (the pair
+        // diagnostic instead takes its pair as the candidates, ja first, and stops after level 1)
         float vw = top.v[0];
         int jw = top.j[0];
+        if (a.dbg_pairs) {
+            vw = 0.f;
+            jw = a.dbg_pairs[2 * idx];
+        }
         block_argmax(vw, jw, S.rv, S.rj);
         if constexpr (CL > 1) {
             if (tid == 0) { S.xf[2] = vw; S.xi[2] = jw; }
@@ -677,6 +836,10 @@ __global__ void __launch_bounds__(kNT, 1) __cluster_dims__(CL, 1, 1) mix_track_k
 #pragma unroll
         for (int k = 0; k < kTopK; ++k) nc += __syncthreads_count(top.v[k] >= thr);
         int full = __syncthreads_or(top.v[kTopK - 1] >= thr);
+        if (a.dbg_pairs) {
+            nc = 2;
+            full = 0;
+        }
         if constexpr (CL > 1) {
             if (tid == 0) { S.xi[3] = nc; S.xi[4] = full; }
             Clu<CL>::sync();
@@ -689,6 +852,7 @@ __global__ void __launch_bounds__(kNT, 1) __cluster_dims__(CL, 1, 1) mix_track_k
         }
         unsigned flags = kRMixed;
         float dwin = 0.f;
+        double raw_peak = NAN;                               // HW cu(winner) from level 2, if it ran
         if (nc > 1) {
             if (full || nc > kMaxCand) {
                 to_fallback();
@@ -698,12 +862,20 @@ __global__ void __launch_bounds__(kNT, 1) __cluster_dims__(CL, 1, 1) mix_track_k
             flags |= 0x02u;
             if (tid == 0) S.misc[1] = 0;
             __syncthreads();
-#pragma unroll
-            for (int k = 0; k < kTopK; ++k)
-                if (top.v[k] >= thr) {
-                    const int slot = atomicAdd(&S.misc[1], 1);
-                    S.cj[slot] = top.j[k];
+            if (a.dbg_pairs) {
+                if (tid == 0 && rank == 0) {
+                    S.cj[0] = a.dbg_pairs[2 * idx];
+                    S.cj[1] = a.dbg_pairs[2 * idx + 1];
+                    S.misc[1] = 2;
                 }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kTopK; ++k)
+                    if (top.v[k] >= thr) {
+                        const int slot = atomicAdd(&S.misc[1], 1);
+                        S.cj[slot] = top.j[k];
+                    }
+            }
             if constexpr (CL > 1) {
                 Clu<CL>::sync();
                 if (tid == 0) {
@@ -720,6 +892,10 @@ __global__ void __launch_bounds__(kNT, 1) __cluster_dims__(CL, 1, 1) mix_track_k
             }
             __syncthreads();
             pair_diffs(nc, jw);
+            if (a.dbg_pairs) {
+                if (rank == 0 && tid == 0) a.dbg_d32[idx] = S.cv[1];
+                continue;
+            }
             // the winner must beat every other candidate by more than 2 tau1 sum g|X|
             int kb = -1;
             for (int k = 0; k < nc; ++k) {
@@ -730,20 +906,30 @@ __global__ void __launch_bounds__(kNT, 1) __cluster_dims__(CL, 1, 1) mix_track_k
             const float need = 2.f * P.tau1 * scale;
             for (int k = 0; k < nc; ++k)
                 if (k != kb && !(sense * (S.cv[kb] - S.cv[k]) > need)) ok = false;
-            if (!ok) {
-                to_fallback();
-                continue;
+            if (ok) {
+                // d of j1 itself is exactly zero (its factors vanish), so S.cv[kb] is v(winner) - v(j1)
+                jw = S.gj[kb];
+                dwin = S.cv[kb];
+            } else {
+                double v2 = 0.0;
+                int k2;
+                if constexpr (H >= 256) k2 = mix_level2_call<H, W, CL>(a, S, mix_smem, it, Fb, nc, py, px, scale, &v2);
+                else k2 = mix_level2<H, W, CL>(a, S, mix_smem, it, Fb, nc, py, px, scale, &v2);
+                if (k2 < 0) {
+                    to_fallback();
+                    continue;
+                }
+                jw = S.gj[k2];
+                flags |= 0x04u;
+                raw_peak = v2;
             }
-            // d of j1 itself is exactly zero (its factors vanish), so S.cv[kb] is v(winner) - v(j1)
-            jw = S.gj[kb];
-            dwin = S.cv[kb];
         }
         if (rank == 0 && tid == 0) {
             const int jy = jw / M, jx = jw % M;
             Result r;
             r.dy = (float)(((double)py * P.u + (jy - h0)) / P.u);
             r.dx = (float)(((double)px * P.u + (jx - h0)) / P.u);
-            r.peak = (c0 + sense * vw + dwin) / (float)(H * W);
+            r.peak = raw_peak == raw_peak ? (float)(raw_peak / ((double)H * W)) : (c0 + sense * vw + dwin) / (float)(H * W);
             r.ipy = py;
             r.ipx = px;
             r.flags = flags;
@@ -830,6 +1016,7 @@ int mix_plan_create(int H, int W, int u, int method, int in_dtype, float eps, fl
     p.Wc = p.L + 1;
     p.Hh = H / 2;
     p.CL = mix_cluster(H);
+    p.NT = mix::mix_threads(H);
     p.KB = (p.Wc + p.CL - 1) / p.CL;
     p.u = u;
     p.M = (3 * u + 1) / 2;
@@ -848,6 +1035,9 @@ int mix_plan_create(int H, int W, int u, int method, int in_dtype, float eps, fl
     p.RSG = p.L + n1r;
     p.G = staged_rows(H / p.CL, p.RSG);
     if (p.G < 1) return -1;
+    p.G2 = 1;                                   // double-float staging: up to 8 rows per group
+    for (int d = 1; d <= 8; ++d)
+        if ((H / p.CL) % d == 0) p.G2 = d;
     // stage A reads 8 t entries per task from t' = t0 - 1 + 8 tg: one spare group of padding
     p.TAp = (p.h0 + mix::kTM - 1) / mix::kTM * mix::kTM + mix::kTM;
     p.TXp = 2 * ((p.TX + 1) / 2);
@@ -855,6 +1045,13 @@ int mix_plan_create(int H, int W, int u, int method, int in_dtype, float eps, fl
     const size_t band = mix::mal(sizeof(float2) * (size_t)H * p.KB);
     const size_t ysg = band + mix::mal(sizeof(float2) * (size_t)p.G * p.RSG);
     const size_t lvl1 = mix::mal(sizeof(float2) * p.Hh) + sizeof(float2) * ((size_t)kMaxCand * p.Hh + (size_t)kMaxCand * p.KB + p.KB);
+    // the double-float level from offset 0: band, staging, per-(candidate, column) sums
+    const size_t l2s = mix::mal(sizeof(dfc) * (size_t)H * p.KB);
+    const size_t l2c = l2s + mix::mal(sizeof(dfc) * (size_t)p.G2 * p.RSG);
+    const size_t lvl2 = l2c + sizeof(df) * (size_t)kMaxCand * p.KB;
+    p.off_l2s = (int)l2s;
+    p.off_l2c = (int)l2c;
+    const size_t lvl2w = lvl2 > band ? lvl2 - band : 0;
     p.off_w = (int)band;
     p.TC = 1;
     p.off_small = 0;
@@ -868,11 +1065,11 @@ int mix_plan_create(int H, int W, int u, int method, int in_dtype, float eps, fl
     // 8 t entries then stay 16-byte aligned)
     int tc = p.h0;
     while (tc > 8) {
-        const size_t work = std::max(std::max(ysg, lvl1), contraction(tc));
+        const size_t work = std::max(std::max(std::max(ysg, lvl1), lvl2w), contraction(tc));
         if (band + work + small <= limit) break;
         tc = (tc - 1) / 8 * 8;
     }
-    const size_t work = std::max(std::max(ysg, lvl1), contraction(tc));
+    const size_t work = std::max(std::max(std::max(ysg, lvl1), lvl2w), contraction(tc));
     if (band + work + small > limit) return -1;
     p.TC = tc;
     p.off_small = (int)(band + mix::mal(work));
@@ -884,6 +1081,26 @@ int mix_plan_create(int H, int W, int u, int method, int in_dtype, float eps, fl
     pass_twiddles_n(H, t4h);
     pass_twiddles_n(p.L, t4r);
     if ((int)t4h.size() != H || (int)t4r.size() != p.L) return -1;
+    // the same twiddles as double-floats (hi = the FP32 rounding, lo = the rest)
+    auto to_df = [](double x) { const float h = (float)x; return df{h, (float)(x - (double)h)}; };
+    std::vector<dfc> t4h_d, t4r_d, rtw_d;
+    auto pass_twiddles_d = [&](int N, std::vector<dfc>& t) {
+        const int n2c = N == 256 ? 16 : N == 192 ? 12 : N == 128 ? 8 : N == 96 ? 8 : N == 48 ? 4 : 3;
+        const int n1c = N / n2c;
+        for (int k1 = 0; k1 < n1c; ++k1)
+            for (int n2 = 0; n2 < n2c; ++n2) {
+                double c, sn;
+                cexp2pi(-(long long)n2 * k1, N, &c, &sn);
+                t.push_back(dfc{to_df(c), to_df(sn)});
+            }
+    };
+    pass_twiddles_d(H, t4h_d);
+    pass_twiddles_d(p.L, t4r_d);
+    for (int k = 0; k <= p.L / 2; ++k) {
+        double c, sn;
+        cexp2pi(-k, W, &c, &sn);
+        rtw_d.push_back(dfc{to_df(c), to_df(sn)});
+    }
     for (int k = 0; k <= p.L / 2; ++k) {
         double c, s;
         cexp2pi(-k, W, &c, &s);
@@ -923,7 +1140,8 @@ int mix_plan_create(int H, int W, int u, int method, int in_dtype, float eps, fl
         }
     }
     const size_t n2 = t4h.size() + t4r.size() + rtw.size() + phH.size() + phW.size() + tA.size() + tB.size();
-    const size_t bytes = n2 * sizeof(float2) + tG.size() * sizeof(float) + 256;
+    const size_t bytes = n2 * sizeof(float2) + tG.size() * sizeof(float) +
+                         (t4h_d.size() + t4r_d.size() + rtw_d.size()) * sizeof(dfc) + 512;
     char* d = nullptr;
     cudaError_t e = cudaMalloc(&d, bytes);
     if (e != cudaSuccess) return (int)e;
@@ -944,6 +1162,9 @@ int mix_plan_create(int H, int W, int u, int method, int in_dtype, float eps, fl
     p.tA = (const float2*)put(tA.data(), tA.size() * sizeof(float2));
     p.tB = (const float2*)put(tB.data(), tB.size() * sizeof(float2));
     p.tG = (const float*)put(tG.data(), tG.size() * sizeof(float));
+    p.t4h_d = (const dfc*)put(t4h_d.data(), t4h_d.size() * sizeof(dfc));
+    p.t4r_d = (const dfc*)put(t4r_d.data(), t4r_d.size() * sizeof(dfc));
+    p.rtw_d = (const dfc*)put(rtw_d.data(), rtw_d.size() * sizeof(dfc));
     e = cudaMemcpy(d, h.data(), bytes, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(d);

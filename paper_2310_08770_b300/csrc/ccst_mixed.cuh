@@ -17,6 +17,7 @@ constexpr unsigned kRMixed = 0x100u;   // record flag: tracked by the general-si
 struct MixPlan {
     int H, W, L, Wc, Hh;        // L = W/2, Wc = W/2 + 1, Hh = H/2
     int CL, KB;                 // CTAs per frame, spectrum columns per CTA (the last may have fewer)
+    int NT;                     // threads per CTA
     int u, M, h0, pmax, TX;     // grid offsets t in [-h0, pmax]; TX = h0 + 1 (tx = 0..h0)
     int method, in_dtype;
     float eps, sense;
@@ -33,6 +34,15 @@ struct MixPlan {
     const float2* tA;           // [Hh][TAp]: (cos(2 pi m t/(uH)) - 1, sin(2 pi m t/(uH))), m = i + 1, t = t' + 1
     const float2* tB;           // [Wc][TXp]: (g cos(2 pi kx' tx/(uW)), g sin(.)), g = fold weight
     const float* tG;            // [Wc][TXp]: g (cos(2 pi kx' tx/(uW)) - 1)
+    // the double-float level: twiddles as double-floats, the phase tables e^{+2 pi i m/(uH)}
+    // (m < uH) and e^{+2 pi i m/(uW)} (m < uW) of the double-float kernel's plan, staged rows
+    // per group, and its shared-memory carve (spectrum band at 0, staging, candidate sums)
+    const dfc* t4h_d;
+    const dfc* t4r_d;
+    const dfc* rtw_d;
+    const dfc* uHd;
+    const dfc* uWd;
+    int G2, off_l2s, off_l2c;
 };
 
 struct MixArgs {

@@ -86,7 +86,8 @@ __device__ __forceinline__ void dft3(float2& a, float2& b, float2& c) {
     c = csub(t, r);
 }
 
-// In-register DFT of R points, natural order in and out. 6 = 3 x 2 and 12 = 3 x 4 use the
+// In-register DFT of R points, natural order in and out (FP32; the double-float overload
+// follows). 6 = 3 x 2 and 12 = 3 x 4 use the
 // four-step split R = R1 R2 (R1-point DFTs over v[R2 n1 + n2], twiddles W_R^{n2 k1},
 // R2-point DFTs, X[k1 + R1 k2] read from slot R2 k1 + k2); the powers of two are the
 // radix-2/4 register DFTs of ccst_fft.cuh.
@@ -120,18 +121,73 @@ __device__ __forceinline__ void mdft(float2 (&v)[R]) {
     }
 }
 
+// ------------------------------------------------------------------ double-float
+// The same register DFTs over double-float complex values (the last guard level): the
+// radix-2/4 butterflies of ccst_fft.cuh and a 3-point DFT, all constants as double-floats.
+template <bool INV>
+__device__ __forceinline__ dfc mul_w12_df(dfc x, int idx) {
+    constexpr double kS3 = 0.86602540378443864676;      // sqrt(3)/2
+    idx %= 12;
+    if (idx >= 6) { x = {df_neg(x.re), df_neg(x.im)}; idx -= 6; }
+    if (idx == 0) return x;
+    if (idx == 3) return INV ? dfc{df_neg(x.im), x.re} : dfc{x.im, df_neg(x.re)};
+    const double c = idx == 1 ? kS3 : idx == 2 ? 0.5 : idx == 4 ? -0.5 : -kS3;
+    const double sn = idx == 1 ? 0.5 : idx == 2 ? kS3 : idx == 4 ? kS3 : 0.5;
+    return cmul(x, dfc{df_const(c), df_const(INV ? sn : -sn)});
+}
+template <bool INV>
+__device__ __forceinline__ void dft3_df(dfc& a, dfc& b, dfc& c) {
+    const df k3 = df_const(0.86602540378443864676);
+    const dfc s = cadd(b, c), d = csub(b, c);
+    const dfc t = csub(a, dfc{df_scale(s.re, 0.5f), df_scale(s.im, 0.5f)});
+    const dfc sd = {df_mul(k3, d.re), df_mul(k3, d.im)};
+    const dfc r = INV ? dfc{df_neg(sd.im), sd.re} : dfc{sd.im, df_neg(sd.re)};   // -+ i s3 d
+    a = cadd(a, s);
+    b = cadd(t, r);
+    c = csub(t, r);
+}
+template <int R, bool INV>
+__device__ __forceinline__ void mdft(dfc (&v)[R]) {
+    if constexpr (R == 1) {
+    } else if constexpr (R == 3) {
+        dft3_df<INV>(v[0], v[1], v[2]);
+    } else if constexpr (R == 6 || R == 12) {
+        constexpr int R1 = 3, R2 = R / 3;
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) dft3_df<INV>(v[n2], v[R2 + n2], v[2 * R2 + n2]);
+#pragma unroll
+        for (int k1 = 1; k1 < R1; ++k1)
+#pragma unroll
+            for (int n2 = 1; n2 < R2; ++n2) v[R2 * k1 + n2] = mul_w12_df<INV>(v[R2 * k1 + n2], n2 * k1 * (12 / R));
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) {
+            if constexpr (R2 == 2) dft2_df<INV>(v[R2 * k1], v[R2 * k1 + 1]);
+            else dft4_df<INV>(v[R2 * k1], v[R2 * k1 + 1], v[R2 * k1 + 2], v[R2 * k1 + 3]);
+        }
+        dfc t[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) t[i] = v[i];
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1)
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) v[k1 + R1 * k2] = t[R2 * k1 + k2];
+    } else {
+        dft_reg_df<R, INV>(v);
+    }
+}
+
 // Forward pass S over nseq sequences. kSeqFast: consecutive tasks take consecutive
 // sequences (column data); otherwise consecutive n2 of one sequence (row data).
 // t4: W_N^{n2 k1} laid out [k1][n2]; ld(s, n2, n1) -> sample N2 n1 + n2; st(s, n2, k1, v)
 // stores the result for slot N2 k1 + n2.
-template <int N1, int N2, bool kSeqFast, int NT, class LD, class ST>
-__device__ __forceinline__ void fwd_pass_s(int nseq, const float2* t4, LD ld, ST st) {
+template <int N1, int N2, bool kSeqFast, int NT, class T, class LD, class ST>
+__device__ __forceinline__ void fwd_pass_s(int nseq, const T* t4, LD ld, ST st) {
     const int ntask = nseq * N2;
     for (int task = threadIdx.x; task < ntask; task += NT) {
         int s, n2;
         if (kSeqFast) { n2 = task / nseq; s = task - n2 * nseq; }
         else { s = task / N2; n2 = task - s * N2; }
-        float2 v[N1];
+        T v[N1];
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) v[n1] = ld(s, n2, n1);
         mdft<N1, false>(v);
@@ -152,7 +208,7 @@ __device__ __forceinline__ void fwd_pass_c(int nseq, LD ld, ST st) {
         int s, k1;
         if (kSeqFast) { k1 = task / nseq; s = task - k1 * nseq; }
         else { s = task / N1; k1 = task - s * N1; }
-        float2 w[N2];
+        decltype(ld(0, 0, 0)) w[N2];
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) w[n2] = ld(s, k1, n2);
         mdft<N2, false>(w);
