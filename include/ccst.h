@@ -78,7 +78,8 @@ extern "C" {
                                      out. The records are the same; this is for verification. */
 
 /* ccst_result.flags (per frame) */
-#define CCST_R_INT_GUARD   0x01u /* integer peak re-decided by FP64 direct sums */
+#define CCST_R_INT_GUARD   0x01u /* integer peak re-decided in higher precision (FP64 direct sums; the
+                                    FP32 general-size kernel: its double-float spectrum) */
 #define CCST_R_SUB_GUARD   0x02u /* sub-pixel peak re-decided by exact FP32 grid differences */
 #define CCST_R_DF64        0x04u /* sub-pixel peak decided from a double-float (~48-bit) product spectrum */
 #define CCST_R_OVERFLOW    0x08u /* too many near-tied points to certify: the FP32 choice is reported */

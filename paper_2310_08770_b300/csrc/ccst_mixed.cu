@@ -174,10 +174,12 @@ struct Geo {
     // qy = py u + ty, qx = px u + tx (the y-Nyquist row through its real part in the
     // folded columns). Returns the winner's slot in S.gj and its raw value, or -1 when the
     // two best are within 2^-36 sum g|X| (a tie in all but name: the fallback decides it
-    // exactly as the double-float kernel does everywhere).
+    // exactly as the double-float kernel does everywhere). With `integer` the candidates are
+    // integer shifts (flat indices y W + x) and the values those of the integer surface.
 template <int H, int W, int CL>
 __device__ __forceinline__ int mix_level2(const MixArgs& a, const MixSh& S, unsigned char* mix_smem, const GenItem& it,
-                                          const dfc* Fb, int nc, int py, int px, float scale, double* vbest) {
+                                          const dfc* Fb, int nc, int py, int px, float scale, double* vbest,
+                                          bool integer) {
     using Gm = Geo<H, W, CL>;
     constexpr int L = Gm::L, Wc = Gm::Wc, RH = Gm::RH, KB = Gm::KB;
     constexpr int N1h = Gm::N1h, N2h = Gm::N2h, N1r = Gm::N1r, N2r = Gm::N2r, RSG = Gm::RSG;
@@ -269,7 +271,15 @@ __device__ __forceinline__ int mix_level2(const MixArgs& a, const MixSh& S, unsi
         for (int e = tid; e < nc * nb; e += kNT) {
             const int k = e / nb, c = e - k * nb, kx = b0 + c, j = S.gj[k];
             const bool folded = kx != 0 && kx != L;
-            const long long qy = (long long)py * P.u + j / M - h0, qx = (long long)px * P.u + j % M - h0;
+            long long qy, qx;
+            if (integer) {                        // j = y W + x: the shift (y, x), wrapped, t = 0
+                const int y = j / W, x = j - (j / W) * W;
+                qy = (long long)(y > H / 2 ? y - H : y) * P.u;
+                qx = (long long)(x > W / 2 ? x - W : x) * P.u;
+            } else {
+                qy = (long long)py * P.u + j / M - h0;
+                qx = (long long)px * P.u + j % M - h0;
+            }
             dfc acc = {df{0.f, 0.f}, df{0.f, 0.f}};
             for (int ky = 0; ky < H; ++ky) {
                 const long long ks = 2 * ky >= H ? ky - H : ky;
@@ -325,8 +335,8 @@ __device__ __forceinline__ int mix_level2(const MixArgs& a, const MixSh& S, unsi
 template <int H, int W, int CL>
 __device__ __noinline__ int mix_level2_call(const MixArgs& a, const MixSh& S, unsigned char* mix_smem,
                                             const GenItem& it, const dfc* Fb, int nc, int py, int px, float scale,
-                                            double* vbest) {
-    return mix_level2<H, W, CL>(a, S, mix_smem, it, Fb, nc, py, px, scale, vbest);
+                                            double* vbest, bool integer) {
+    return mix_level2<H, W, CL>(a, S, mix_smem, it, Fb, nc, py, px, scale, vbest, integer);
 }
 
 template <int H, int W, int CL>
@@ -392,7 +402,10 @@ __global__ void __launch_bounds__(mix_threads(H), 1) __cluster_dims__(CL, 1, 1) 
             Clu<CL>::at(S.X, r)[y * KB + (kx - r * KB)] = v;
         };
 
-        // ---- a1-a2: rows -> half spectra in the owners' bands
+        // ---- a1-a3: the product spectrum X in the bands (sabs: this thread's part of sum g|X|)
+        float sabs = 0.f;
+        auto forward = [&]() {
+        // a1-a2: rows -> half spectra in the owners' bands
         for (int g0 = 0; g0 < RH; g0 += G) {
             const char* rbase = frame + (size_t)(row0 + g0) * it.pitch * elem;
             if (vec && elem == 2) {
@@ -460,12 +473,12 @@ __global__ void __launch_bounds__(mix_threads(H), 1) __cluster_dims__(CL, 1, 1) 
         }
         Clu<CL>::sync();
 
-        // ---- a3: column FFTs over the band, product with conj F[b]
+        // a3: column FFTs over the band, product with conj F[b]
         fwd_pass_s<N1h, N2h, true, kNT>(
             nb, S.t4h, [&](int c, int n2, int n1) { return S.X[(N2h * n1 + n2) * KB + c]; },
             [&](int c, int n2, int k1, float2 v) { S.X[(N2h * k1 + n2) * KB + c] = v; });
         __syncthreads();
-        float sabs = 0.f;
+        sabs = 0.f;
         fwd_pass_c<N1h, N2h, true, kNT>(
             nb, [&](int c, int k1, int n2) { return S.X[(N2h * k1 + n2) * KB + c]; },
             [&](int c, int k1, int k2, float2 v) {
@@ -476,6 +489,8 @@ __global__ void __launch_bounds__(mix_threads(H), 1) __cluster_dims__(CL, 1, 1) 
                 sabs += (kx == 0 || kx == L ? 1.f : 2.f) * (fabsf(x.x) + fabsf(x.y));
             });
         __syncthreads();
+        };
+        forward();
 
         // ---- a4: inverse columns (X -> Y), then inverse rows scanned for the extremum
         inv_pass_c<N1h, N2h, true, kNT>(
@@ -486,8 +501,8 @@ __global__ void __launch_bounds__(mix_threads(H), 1) __cluster_dims__(CL, 1, 1) 
             nb, [&](int c, int n2, int k1) { return S.Y[(N2h * k1 + n2) * KB + c]; },
             [&](int c, int n2, int n1, float2 v) { S.Y[(N2h * n1 + n2) * KB + c] = v; });
         Clu<CL>::sync();
-        Best2 t2;
-        t2.init();
+        // the CTA's rows of HW c(y, x), each value handed to visit(value, flat index)
+        auto inverse_rows = [&](auto&& visit) {
         for (int g0 = 0; g0 < RH; g0 += G) {
             for (int task = tid; task < G * NP; task += kNT) {
                 const int s = task / NP, k = task - s * NP, y = row0 + g0 + s;
@@ -521,12 +536,18 @@ __global__ void __launch_bounds__(mix_threads(H), 1) __cluster_dims__(CL, 1, 1) 
                 G, [&](int s, int n2, int k1) { return S.SG[s * RSG + mix_phys<L>(N2r * k1 + n2)]; },
                 [&](int s, int n2, int n1, float2 v) {
                     const int y = row0 + g0 + s, x = 2 * (n2 + N2r * n1), fe = y * W + x;
-                    if (dbg_int) { dbg_int[fe] = v.x; dbg_int[fe + 1] = v.y; }
-                    t2.push(sense * v.x, fe);
-                    t2.push(sense * v.y, fe + 1);
+                    visit(v.x, fe);
+                    visit(v.y, fe + 1);
                 });
             __syncthreads();
         }
+        };
+        Best2 t2;
+        t2.init();
+        inverse_rows([&](float v, int fe) {
+            if (dbg_int) dbg_int[fe] = v;
+            t2.push(sense * v, fe);
+        });
         // a5: the integer extremum and the spectral scale over the cluster
         float v1 = t2.v1;
         int best = t2.j1;
@@ -560,11 +581,59 @@ __global__ void __launch_bounds__(mix_threads(H), 1) __cluster_dims__(CL, 1, 1) 
                 a.fb[s] = it;
             }
         };
-        if (!(v1 > -INFINITY) || !(scale < INFINITY) || (near > 0 && !dbg_sub)) {
+        if (!(v1 > -INFINITY) || !(scale < INFINITY)) {
             to_fallback();
             continue;
         }
-        const float c0 = sense * v1;                         // HW c(p)
+        float c0 = sense * v1;                               // HW c(p)
+        unsigned iflags = 0;
+        if (near > 0 && !dbg_sub) {
+            // integer near-ties: every shift within tau_int of the best, evaluated from the
+            // double-float spectrum (the interpolant at a whole-pixel offset is the integer
+            // surface), then the FP32 spectrum again for the sub-pixel stage
+            if (tid == 0) S.misc[2] = 0;
+            __syncthreads();
+            const float thr_i = v1 - tau_i;
+            inverse_rows([&](float v, int fe) {
+                if (sense * v >= thr_i) {
+                    const int slot = atomicAdd(&S.misc[2], 1);
+                    if (slot < kMaxCand) S.cj[slot] = fe;
+                }
+            });
+            int ni = S.misc[2];
+            if constexpr (CL > 1) {
+                Clu<CL>::sync();
+                ni = 0;
+                for (int r = 0; r < CL; ++r) ni += Clu<CL>::at(S.misc, r)[2];
+                if (tid == 0 && ni <= kMaxCand) {
+                    int n = 0;
+                    for (int r = 0; r < CL; ++r) {
+                        const int cnt = Clu<CL>::at(S.misc, r)[2];
+                        const int* cj = Clu<CL>::at(S.cj, r);
+                        for (int k = 0; k < cnt; ++k) S.gj[n++] = cj[k];
+                    }
+                }
+            } else {
+                for (int k = tid; k < ni && ni <= kMaxCand; k += kNT) S.gj[k] = S.cj[k];
+            }
+            __syncthreads();
+            if (ni > kMaxCand || ni < 1) {
+                to_fallback();
+                continue;
+            }
+            double vi = 0.0;
+            int ki;
+            if constexpr (H >= 256) ki = mix_level2_call<H, W, CL>(a, S, mix_smem, it, Fb, ni, 0, 0, scale, &vi, true);
+            else ki = mix_level2<H, W, CL>(a, S, mix_smem, it, Fb, ni, 0, 0, scale, &vi, true);
+            if (ki < 0) {
+                to_fallback();
+                continue;
+            }
+            best = S.gj[ki];
+            c0 = (float)vi;
+            iflags = 0x01u;
+            forward();
+        }
         const int iy = best / W, ix = best - (best / W) * W;
         const int py = iy > H / 2 ? iy - H : iy, px = ix > W / 2 ? ix - W : ix;
         const int pyy = iy, pxx = ix;
@@ -850,7 +919,7 @@ __global__ void __launch_bounds__(mix_threads(H), 1) __cluster_dims__(CL, 1, 1) 
                 full |= Clu<CL>::at(S.xi, r)[4];
             }
         }
-        unsigned flags = kRMixed;
+        unsigned flags = kRMixed | iflags;
         float dwin = 0.f;
         double raw_peak = NAN;                               // HW cu(winner) from level 2, if it ran
         if (nc > 1) {
@@ -913,8 +982,8 @@ __global__ void __launch_bounds__(mix_threads(H), 1) __cluster_dims__(CL, 1, 1) 
             } else {
                 double v2 = 0.0;
                 int k2;
-                if constexpr (H >= 256) k2 = mix_level2_call<H, W, CL>(a, S, mix_smem, it, Fb, nc, py, px, scale, &v2);
-                else k2 = mix_level2<H, W, CL>(a, S, mix_smem, it, Fb, nc, py, px, scale, &v2);
+                if constexpr (H >= 256) k2 = mix_level2_call<H, W, CL>(a, S, mix_smem, it, Fb, nc, py, px, scale, &v2, false);
+                else k2 = mix_level2<H, W, CL>(a, S, mix_smem, it, Fb, nc, py, px, scale, &v2, false);
                 if (k2 < 0) {
                     to_fallback();
                     continue;

@@ -259,3 +259,19 @@ def test_rois_of_every_fp32_side_graph_and_direct(torch):
     for (ref, f), g, N in zip(items, res, sides):
         if N in (48, 96, 192, 256):
             check(ref, f[None], g[None], 100, oracle.CC_U)
+
+
+@pytest.mark.parametrize("N", [48, 96, 192, 256])
+def test_integer_near_ties_are_decided_in_double_float(torch, N):
+    # noise-free spots shifted by 1/2 + d px along x: the integer shifts 0 and 1 nearly tie
+    # (d = 1e-4 .. 1e-6 px, far inside the FP32 threshold), and the kernel re-decides them
+    # from its double-float spectrum (CCST_R_INT_GUARD); an exact half-pixel shift of a
+    # symmetric spot ties exactly and goes to the double-float kernel
+    ref = synth.gaussian_spot(N, N, N / 2, N / 2, 2.5, 2000.0, 10.0).astype(np.float32)
+    ds = [1e-4, -1e-4, 3e-5, 1e-5, -3e-6, 1e-6]
+    frames = np.array([synth.gaussian_spot(N, N, N / 2 + 0.3, N / 2 + 0.5 + d, 2.5, 2000.0, 10.0) for d in ds],
+                      np.float32)
+    res = track(torch, ref, frames, 100)
+    guarded = int(np.sum((res["flags"] & C.R_INT_GUARD) != 0))
+    assert guarded >= 3, res["flags"]
+    check(ref, frames, res, 100, oracle.CC_U)
