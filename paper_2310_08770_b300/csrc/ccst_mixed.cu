@@ -43,9 +43,12 @@ namespace cg = cooperative_groups;
 namespace ccst {
 namespace mix {
 
-// threads per CTA: 512, and 384 for the 256-pixel kernel (whose 16-point register DFTs
-// want more than the 128 registers a 512-thread CTA leaves each thread)
-__host__ __device__ constexpr int mix_threads(int H) { return H >= 256 ? 384 : 512; }
+// Threads per CTA and CTAs per SM. A small frame is latency-bound (each phase is a few
+// hundred tasks between barriers), so 48 and 96 run 4 and 2 smaller CTAs per SM; 192 takes
+// a whole SM per CTA, and 256 takes 384 threads, whose 16-point register DFTs want more
+// than the 128 registers a 512-thread CTA leaves each thread.
+__host__ __device__ constexpr int mix_threads(int H) { return H <= 48 ? 128 : H <= 96 ? 256 : H >= 256 ? 384 : 512; }
+__host__ __device__ constexpr int mix_min_ctas(int H) { return H <= 48 ? 4 : H <= 96 ? 2 : 1; }
 constexpr int kTM = 8;            // t rows per contraction task
 
 template <int CL>
@@ -340,7 +343,8 @@ __device__ __noinline__ int mix_level2_call(const MixArgs& a, const MixSh& S, un
 }
 
 template <int H, int W, int CL>
-__global__ void __launch_bounds__(mix_threads(H), 1) __cluster_dims__(CL, 1, 1) mix_track_kernel(const MixArgs a) {
+__global__ void __launch_bounds__(mix_threads(H), mix_min_ctas(H)) __cluster_dims__(CL, 1, 1)
+    mix_track_kernel(const MixArgs a) {
     constexpr int kNT = mix_threads(H);
     using Gm = Geo<H, W, CL>;
     constexpr int L = Gm::L, Wc = Gm::Wc, Hh = Gm::Hh, RH = Gm::RH, KB = Gm::KB;
