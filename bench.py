@@ -598,7 +598,7 @@ def refine_cpu_baseline(C, torch, stream):
 
 
 ROIS_N = 4096                    # uneven-ROI leg
-ROIS_SIDES = (32, 48, 64, 96, 128)   # 48 and 96 run on the general-size (double-float) path
+ROIS_SIDES = (32, 48, 64, 96, 128)   # 48 and 96 run on the FP32 general-size kernel
 ROIS_POW2_SIDES = (32, 64, 128)      # the power-of-two kernel alone, for context
 ROIS_REPS = 10
 ROIS_ORACLE = 48
@@ -606,7 +606,7 @@ ROIS_ORACLE = 48
 
 def rois_leg(C, torch, stream, n_rois=ROIS_N, sides=ROIS_SIDES, plain=True):
     """Uneven batch: FP32 ROIs of mixed sizes, each against its own reference, in one
-    ccst_track_rois call (the power-of-two kernel and the general-size kernel side by side),
+    ccst_track_rois call (the power-of-two kernel and the general-size kernels side by side),
     after ccst_autotune, replayed as one captured CUDA graph (the reported value). Beside it:
     the same call launched directly, the same ROIs as one batched call per size class (the
     per-size form), and (context) one call per ROI."""
@@ -695,10 +695,10 @@ def rois_leg(C, torch, stream, n_rois=ROIS_N, sides=ROIS_SIDES, plain=True):
                          "plans": [{k: x[k] for k in ("H", "W", "H1", "W1", "threads", "us_per_frame")}
                                    for x in tuned]},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "kernel": "track_rois_kernel + track_generic_kernel", "flop_total": flop,
-                         "flop_basis": "the folded formulation's algorithmic flops for every ROI (the general-size "
-                                       "path does more work than that: two-level DFTs in double-float and the FP32 "
-                                       "grid with double-float candidates)",
+                         "kernel": "track_rois_kernel + mix_track_kernel (+ track_generic_kernel on its fallback "
+                                   "list)", "flop_total": flop,
+                         "flop_basis": "the folded formulation's algorithmic flops for every ROI (both FP32 kernels "
+                                       "perform that formulation; the guard levels come on top)",
                          "peak_basis": "of measured: FP32 FMA rate of this GPU (ccst_fp32_fma_peak)"}}
     if plain:
         line.update({"plain_per_roi_call": {"value": n / (plain_ms / 1e3), "unit": "ROIs/s", "ms": plain_ms},
@@ -1058,14 +1058,16 @@ def run_ours(args):
     if world == 1 and not args.no_serving:
         line["serving"] = serving_leg(C, torch, note=" (power-of-two stand-ins for 64, 96, 128, 192, 256, 64, "
                                                      "128, 256)")
-        # the workload's own sides: 96, 192 and 256 run on the double-float general-size kernel
+        # the workload's own sides: 96, 192 and 256 run on the FP32 general-size kernel
         line["serving"]["true_sides"] = serving_leg(C, torch, SERVE_TRUE_SIDES, SERVE_TRUE_SECONDS, 2048,
-                                                    " (96, 192, 256 on the general-size kernel)")
+                                                    " (96, 192, 256 on the FP32 general-size kernel)")
     rois_extra = None
     if world == 1 and not args.no_rois:
-        line["rois"], rois_extra = rois_leg(C, torch, stream, args.rois_n)
-        line["rois"]["power_of_two_sides_only"] = rois_leg(C, torch, stream, args.rois_n, ROIS_POW2_SIDES,
-                                                           plain=False)[0]
+        sides = tuple(int(x) for x in args.rois_sides.split(",")) if args.rois_sides else ROIS_SIDES
+        line["rois"], rois_extra = rois_leg(C, torch, stream, args.rois_n, sides, plain=sides == ROIS_SIDES)
+        if sides == ROIS_SIDES:
+            line["rois"]["power_of_two_sides_only"] = rois_leg(C, torch, stream, args.rois_n, ROIS_POW2_SIDES,
+                                                               plain=False)[0]
     adj_extra = None
     if world == 1 and not args.no_adjoint:
         line["adjoint"], adj_extra = adjoint_leg(C, torch, stream)
@@ -1170,6 +1172,8 @@ def main():
     ap.add_argument("--no-rois", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--rois-n", type=int, default=ROIS_N)
+    ap.add_argument("--rois-sides", default="", help="comma-separated ROI sides of the uneven-ROI leg "
+                    "(default: the survey's mix); e.g. 96 to profile one kernel")
     ap.add_argument("--streams", type=int, default=3)
     ap.add_argument("--rt-frames", type=int, default=RT_FRAMES)
     ap.add_argument("--frames", type=int, default=N_FRAMES,
