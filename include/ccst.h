@@ -65,17 +65,19 @@ extern "C" {
 
 /* ccst_params.flags */
 /* TIE_GUARD, GRAPHS and PROFILE concern power-of-two contexts; a general-shape context
- * (see ccst_create) needs no near-tie levels, launches directly, and has no profiling. */
+ * (see ccst_create) runs its own guard levels always, launches directly, and has no
+ * profiling. */
 #define CCST_FLAG_TIE_GUARD 0x1u  /* resolve near-ties of the FP32 surfaces in higher precision (default on) */
 #define CCST_FLAG_GRAPHS    0x2u  /* ccst_track replays one captured CUDA graph per (stream, frames, n,
                                       pitch, out); each graph owns its frame counter, so graphs of
                                       different batches may run at once on different streams
                                       (ccst_set_stream) */
 #define CCST_FLAG_PROFILE   0x4u  /* record CUDA events around each launch of the tracking kernel */
-#define CCST_FLAG_EXHAUSTIVE 0x8u /* general-size kernel (ccst_create): evaluate the whole upsampled
-                                     grid in double-float, instead of FP32 with a rounding bound and
-                                     double-float re-evaluation of the points the bound cannot rule
-                                     out. The records are the same; this is for verification. */
+#define CCST_FLAG_EXHAUSTIVE 0x8u /* general-shape contexts (ccst_create): every frame on the
+                                     double-float kernel, evaluating the whole upsampled grid in
+                                     double-float (no FP32 general-size kernel, no FP32 grid with
+                                     a rounding bound). Decisions are the same; this is for
+                                     verification. */
 
 /* ccst_result.flags (per frame) */
 #define CCST_R_INT_GUARD   0x01u /* integer peak re-decided in higher precision (FP64 direct sums; the
@@ -146,15 +148,23 @@ int ccst_default_params(ccst_params* p);
  *         - Powers of two up to 128 (8, 16, 32, 64, 128 per axis) make a power-of-two
  *           context: FP32 FFTs, the upsampled contraction on tensor cores, the near-tie
  *           levels, and every entry point below.
- *         - Every other shape (48 x 48, 96 x 96, 256 x 128, 256 x 256, 100 x 60, ...)
- *           makes a general-shape context. Its batches run on the general-size kernel:
- *           direct DFTs over the Hermitian half and the full-grid upsampled sum, in
- *           double-float (about 2^-46 per term, so no near-tie levels are needed).
- *           Records carry CCST_R_GENERIC. ccst_track, ccst_track_host, ccst_submit,
- *           ccst_submit_host, ccst_poll, ccst_set_reference_frame, ccst_add_reference,
- *           ccst_track_rois and the server work on it. The real-time and offline
- *           reference, the continuous peak, the adjoint, profiling and the debug entry
- *           points return CCST_E_UNSUPPORTED.
+ *         - Every other shape makes a general-shape context.
+ *           48 x 48, 96 x 96, 192 x 192 and 256 x 256 (u <= 256) run on the FP32
+ *           general-size kernel: mixed-radix (2, 3) FFTs and the upsampled contraction
+ *           in FP32 in shared memory (one to four CTAs per frame), with the integer,
+ *           sub-pixel, pair-difference and double-float guard levels; records carry
+ *           CCST_R_FP32_GENERAL. A frame those levels cannot certify (a tie within
+ *           2^-36 sum|X|) is tracked again by the double-float kernel.
+ *           Every other shape (256 x 128, 100 x 60, ...), and those frames, run on the
+ *           double-float kernel: direct DFTs over the Hermitian half and the full-grid
+ *           upsampled sum, in double-float (about 2^-46 per term, so no near-tie levels
+ *           are needed); records carry CCST_R_GENERIC.
+ *           ccst_track, ccst_track_host, ccst_submit, ccst_submit_host, ccst_poll,
+ *           ccst_set_reference_frame, ccst_add_reference, ccst_track_rois and the server
+ *           work on a general-shape context; so do ccst_debug_surfaces and
+ *           ccst_debug_pairs when it has the FP32 general-size kernel. The real-time and
+ *           offline reference, the continuous peak, the adjoint and profiling return
+ *           CCST_E_UNSUPPORTED.
  *   p     parameters; NULL means the defaults.
  *   out   receives the context.
  *
@@ -241,10 +251,9 @@ int ccst_poll(ccst_ctx* ctx, uint64_t ticket, int timeout_us, int* done);
  *   ref      H*W float32, row-major, host or device memory; copied.
  *   H, W     square, 8 to 256 pixels a side; others return CCST_E_SHAPE.
  *            16, 32, 64 and 128 run on the power-of-two ROI kernel (FP32 surfaces with the
- *            near-tie levels, as ccst_track). Every other side (8, 48, 96, 192, 256, odd
- *            sides, ...) runs on the general-size kernel of general-shape contexts (see
- *            ccst_create): about ten times slower per pixel than the power-of-two
- *            kernel, but general; its records carry CCST_R_GENERIC.
+ *            near-tie levels, as ccst_track). 48, 96, 192 and 256 run on the FP32
+ *            general-size kernel and every other side (8, 24, odd sides, ...) on the
+ *            double-float kernel, as in general-shape contexts (see ccst_create).
  * The first reference of a new size also creates that size's plan (geometry, FFT
  * twiddles, upsampling tables) with the context's parameters (u, method, eps); for the
  * general path u * N must not exceed 2^22. Each power-of-two reference keeps its spectra
@@ -262,8 +271,10 @@ int ccst_add_reference(ccst_ctx* ctx, const float* ref, int H, int W, int* ref_i
  * Work items run largest ROI first; each CTA takes the next item from a counter and
  * re-plans its shared memory when the size changes. The records of power-of-two ROIs are
  * identical to those of ccst_track on a context made for that ROI's reference. ROIs of
- * general sizes run as a second persistent launch, on an internal stream, concurrently
- * with the first; the call's work is complete when the context's stream reaches it.
+ * general sizes run on an internal stream, concurrently with the first launch: one
+ * persistent launch of the FP32 general-size kernel per side it takes (48, 96, 192, 256),
+ * then one of the double-float kernel over the other general sides and the frames the
+ * FP32 kernel handed on; the call's work is complete when the context's stream reaches it.
  * With CCST_FLAG_GRAPHS (and a non-default stream), both launches are captured once as
  * one CUDA graph per (stream, out_dev, work list), with the work items uploaded to memory
  * the graph owns, and replayed by later calls with the same list (compared byte by byte).
@@ -286,8 +297,9 @@ typedef struct ccst_tune_result {
     double   us_per_frame;  /* the chosen splits' time per frame (512 threads, two grid waves) */
 } ccst_tune_result;
 
-/* Autotune the general-size kernel (NEXT-2: the size-dependent choices of the uneven-ROI
- * path). For every general-size plan of the context (shapes added by ccst_create or
+/* Autotune the double-float general-size kernel (NEXT-2: the size-dependent choices of the
+ * uneven-ROI path; the FP32 general-size kernel has one compiled schedule per side and
+ * nothing to tune). For every general-size plan of the context (shapes added by ccst_create or
  * ccst_add_reference outside the power-of-two kernel) it times, on synthetic frames of the
  * plan's shape and one of its references, each two-level split of the row and column DFTs
  * (the default: the largest divisor of N not above sqrt(N); its cofactor; the next divisor
@@ -321,8 +333,8 @@ int ccst_autotune(ccst_ctx* ctx, int reps, const ccst_roi* rois, int64_t n_rois,
  * allocated at creation, so the budget bounds what admitted frames add.
  * The worker takes everything pending (up to max_batch frames, any cameras and sizes) as
  * one batch on its own stream: the power-of-two ROI kernel for cameras of 16, 32, 64 or
- * 128 px, then the general-size kernel for the others (each ring entry has its own
- * scratch for it). Up to max_in_flight (at most 4) batches are in flight. Frames that
+ * 128 px, then the general-size kernels for the others (each ring entry has its own
+ * lane for them). Up to max_in_flight (at most 4) batches are in flight. Frames that
  * arrive while others run are admitted as memory frees up, and their work overlaps on
  * the device. With max_batch = 1 and max_in_flight = 1 the server is the plain form:
  * one launch per frame, each after the previous one has finished. Each result equals
@@ -588,8 +600,10 @@ int ccst_grid_size(ccst_ctx* ctx);
  *                 (unnormalised), s in 0..H-1 x 0..W-1 (Eq. (4)/(7));
  *   sub_surf_dev  n x M x M floats: the FP32 upsampled surface relative to the
  *                 integer peak, H*W*(cu(j) - cu(centre)), row = y offset (Sec. III).
- * Both buffers are caller-owned device memory.
- * Errors: as ccst_track. */
+ * Both buffers are caller-owned device memory. On a general-shape context with the FP32
+ * general-size kernel (see ccst_create) the surfaces are that kernel's; a frame it sends
+ * to the double-float kernel may leave them unwritten, and still gets its record.
+ * Errors: as ccst_track; CCST_E_UNSUPPORTED on other general-shape contexts. */
 int ccst_debug_surfaces(ccst_ctx* ctx, const void* frames_dev, int64_t n, int64_t pitch_elems,
                         ccst_result* out_dev, float* int_surf_dev, float* sub_surf_dev);
 
@@ -656,9 +670,11 @@ const char* ccst_static_last_error(void);
  * unnormalised and relative to the frame's integer peak, for the flat grid
  * indices ja = pairs_dev[2f] and jb = pairs_dev[2f+1], two ways:
  *   d32_dev[f]  by the FP32 pair-difference guard;
- *   d64_dev[f]  accumulated in FP64 from the same FP32 product spectrum.
+ *   d64_dev[f]  accumulated in FP64 from the same FP32 product spectrum (NaN on a
+ *               general-shape context, whose FP32 general-size kernel has no such sum).
  * No tracking results are written. All buffers are caller-owned device memory.
- * Errors: as ccst_track, plus CCST_E_INVALID for NULL buffers. */
+ * Errors: as ccst_track, plus CCST_E_INVALID for NULL buffers; CCST_E_UNSUPPORTED on
+ * general-shape contexts without the FP32 general-size kernel. */
 int ccst_debug_pairs(ccst_ctx* ctx, const void* frames_dev, int64_t n, int64_t pitch_elems,
                      const int32_t* pairs_dev, float* d32_dev, double* d64_dev);
 
