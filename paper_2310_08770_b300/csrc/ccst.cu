@@ -645,6 +645,7 @@ struct ccst_ctx {
     cudaStream_t stream = nullptr;
     int device = 0;
     int grid_main = 1;
+    int threads = kThreads;            // CTA size of track_kernel<H, W> (track_threads)
     size_t smem = 0;
     const void* kernel = nullptr;      // track_kernel<H, W>
     bool dead = false;
@@ -742,14 +743,16 @@ struct ccst_ctx {
         cudaEvent_t done = nullptr;
         RoiItem* d_items = nullptr;
         GenItem* d_gitems = nullptr;
-        unsigned* counters = nullptr; // [0] power-of-two kernel, [1] general-size kernel
+        unsigned* counters = nullptr; // [0], [1] power-of-two kernels (128 px; up to 64 px), [2] general-size
     };
     std::map<std::tuple<cudaStream_t, void*, int64_t, uint64_t>, RoiGraph> roi_graphs;
     std::map<cudaStream_t, GenLane> roi_lanes;
     int64_t roi_graph_instantiations = 0, roi_graph_replays = 0;
     bool rois_dirty = true;
-    size_t rois_smem = 0;
+    size_t rois_smem = 0;             // ROI kernel for the 128 x 128 class
     int rois_grid = 0;
+    size_t rois_smem_small = 0;       // ROI kernel for the classes up to 64 x 64
+    int rois_grid_small = 0;
     void* d_addref_tmp = nullptr;     // ccst_add_reference: reference copy and FFT workspace
     size_t addref_tmp_bytes = 0;
     // graphs keyed by (stream, frames, n, pitch, out). Each owns a profiling event pair, a
@@ -1129,13 +1132,14 @@ extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pi
     cudaFree(d_work);
     d_work = nullptr;
     c->kernel = track_kernel_for(H, W);
+    c->threads = track_threads(H, W);
     // the attribute is per function: set it to the device limit so contexts of any size coexist
     if (!step(cudaFuncSetAttribute(c->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)limit - ((H == 128 && W == 128) ? kTcStaticSmem : 0)),
               "smem attribute"))
         return bail(CCST_E_CUDA);
     int occ = 0;
-    if (!step(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->kernel, kThreads, c->smem), "occupancy"))
+    if (!step(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->kernel, c->threads, c->smem), "occupancy"))
         return bail(CCST_E_CUDA);
     if (occ < 1) {
         fail(nullptr, CCST_E_SHAPE, "ccst_create: tracking kernel does not fit on an SM");
@@ -1187,7 +1191,7 @@ static int launch(ccst_ctx* c, const Batch& b, bool reset_counter = true, unsign
         bk.next = counter;
         if (reset_counter) CK(c, cudaMemsetAsync(bk.next, 0, sizeof(unsigned), c->stream));
         void* args[] = {&gk, &bk};
-        CK(c, cudaLaunchKernel(c->kernel, dim3(grid), dim3(kThreads), args, c->smem, c->stream));
+        CK(c, cudaLaunchKernel(c->kernel, dim3(grid), dim3(c->threads), args, c->smem, c->stream));
         if (ring >= 0) CK(c, ring_release(c, (unsigned)ring, c->stream));
     }
     if (prof) CK(c, cudaEventRecordWithFlags(e1, c->stream, c->capturing ? cudaEventRecordExternal : 0));
@@ -1204,7 +1208,7 @@ static int launch_on(ccst_ctx* c, const Batch& b, cudaStream_t stream, unsigned*
     bk.next = counter;
     CK(c, cudaMemsetAsync(counter, 0, sizeof(unsigned), stream));
     void* args[] = {&gk, &bk};
-    CK(c, cudaLaunchKernel(c->kernel, dim3(grid), dim3(kThreads), args, c->smem, stream));
+    CK(c, cudaLaunchKernel(c->kernel, dim3(grid), dim3(c->threads), args, c->smem, stream));
     CK(c, cudaGetLastError());
     return CCST_OK;
 }
@@ -1597,7 +1601,7 @@ extern "C" int ccst_debug_pairs(ccst_ctx* c, const void* frames_dev, int64_t n, 
     const int grid = (int)(n < c->grid_main ? n : c->grid_main);
     Geom gk = c->g;
     void* args[] = {&gk, &b};
-    CK(c, cudaLaunchKernel(c->kernel, dim3(grid), dim3(kThreads), args, c->smem, c->stream));
+    CK(c, cudaLaunchKernel(c->kernel, dim3(grid), dim3(c->threads), args, c->smem, c->stream));
     return CCST_OK;
 }
 
@@ -1615,7 +1619,7 @@ extern "C" int ccst_debug_timeout(ccst_ctx* c, const void* frames_dev, int64_t n
     const int grid = (int)(n < c->grid_main ? n : c->grid_main);
     Geom gk = c->g;
     void* args[] = {&gk, &b};
-    CK(c, cudaLaunchKernel(c->kernel, dim3(grid), dim3(kThreads), args, c->smem, c->stream));
+    CK(c, cudaLaunchKernel(c->kernel, dim3(grid), dim3(c->threads), args, c->smem, c->stream));
     return CCST_OK;
 }
 
@@ -2174,24 +2178,30 @@ static int rois_upload(ccst_ctx* c) {
         c->refs_cap = 2 * c->refs.size();
     }
     std::vector<Geom> gs;
-    size_t smem = 0;
+    size_t smem = 0, smem_small = 0;
     for (auto& pl : c->plans) {
         gs.push_back(pl.g);
-        if (rois_size_ok(pl.g.H, pl.g.W)) smem = std::max(smem, smem_plan(pl.g).total);
+        if (!rois_size_ok(pl.g.H, pl.g.W)) continue;
+        if (pl.g.H <= 64) smem_small = std::max(smem_small, smem_plan(pl.g).total);
+        else smem = std::max(smem, smem_plan(pl.g).total);
     }
     std::vector<RefSpectra> rs;
     for (auto& re : c->refs) rs.push_back(re.r);
     CK(c, cudaMemcpy(c->d_geoms, gs.data(), gs.size() * sizeof(Geom), cudaMemcpyHostToDevice));
     CK(c, cudaMemcpy(c->d_refs, rs.data(), rs.size() * sizeof(RefSpectra), cudaMemcpyHostToDevice));
-    const void* k = track_rois_kernel_ptr();
     int limit = 0, occ = 0, sms = 0;
     CK(c, cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-    CK(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, limit - kRoisStaticSmem));
-    CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kThreads, smem));
-    if (occ < 1) return fail(c, CCST_E_SHAPE, "ccst_track_rois: the ROI kernel does not fit on an SM");
+    for (int small = 0; small < 2; ++small) {
+        const void* k = track_rois_kernel_ptr(small != 0);
+        CK(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, limit - kRoisStaticSmem));
+        CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, small ? track_threads(64, 64) : kThreads,
+                                                             small ? smem_small : smem));
+        if (occ < 1) return fail(c, CCST_E_SHAPE, "ccst_track_rois: the ROI kernel does not fit on an SM");
+        (small ? c->rois_grid_small : c->rois_grid) = occ * sms;
+    }
     c->rois_smem = smem;
-    c->rois_grid = occ * sms;
+    c->rois_smem_small = smem_small;
     c->rois_dirty = false;
     return CCST_OK;
 }
@@ -2759,20 +2769,36 @@ static void rois_sort(ccst_ctx* c, RoiItem* items, int64_t n) {
     });
 }
 
-// The ROI kernel over n items already on the device: counter reset, launch.
-static int rois_kernel_launch(ccst_ctx* c, const RoiItem* items_dev, int64_t n, Result* out, cudaStream_t stream,
-                              unsigned* counter) {
-    CK(c, cudaMemsetAsync(counter, 0, sizeof(unsigned), stream));
-    RoiBatch rb;
-    rb.items = items_dev;
-    rb.n = n;
-    rb.geoms = c->d_geoms;
-    rb.refs = c->d_refs;
-    rb.out = out;
-    rb.next = counter;
-    const int grid = (int)(n < c->rois_grid ? n : c->rois_grid);
-    void* args[] = {&rb};
-    CK(c, cudaLaunchKernel(track_rois_kernel_ptr(), dim3(grid), dim3(kThreads), args, c->rois_smem, stream));
+// Leading items of a sorted list (largest first) that take the 512-thread ROI kernel.
+static int64_t rois_big_items(ccst_ctx* c, const RoiItem* items, int64_t n) {
+    int64_t k = 0;
+    while (k < n && c->plans[items[k].cls].g.H > 64) ++k;
+    return k;
+}
+
+// The ROI kernels over n items already on the device, the first nbig of them 128 x 128
+// (ordered by rois_sort): counter reset, then the 512-thread kernel over those and the
+// small-class kernel over the rest, each with its own counter (counter[0], counter[1]).
+static int rois_kernel_launch(ccst_ctx* c, const RoiItem* items_dev, int64_t n, int64_t nbig, Result* out,
+                              cudaStream_t stream, unsigned* counter) {
+    CK(c, cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned), stream));
+    for (int small = 0; small < 2; ++small) {
+        const int64_t m = small ? n - nbig : nbig;
+        if (m == 0) continue;
+        RoiBatch rb;
+        rb.items = items_dev + (small ? nbig : 0);
+        rb.n = m;
+        rb.geoms = c->d_geoms;
+        rb.refs = c->d_refs;
+        rb.out = out;
+        rb.next = counter + small;
+        const int cap = small ? c->rois_grid_small : c->rois_grid;
+        const int grid = (int)(m < cap ? m : cap);
+        void* args[] = {&rb};
+        CK(c, cudaLaunchKernel(track_rois_kernel_ptr(small != 0), dim3(grid),
+                               dim3(small ? track_threads(64, 64) : kThreads), args,
+                               small ? c->rois_smem_small : c->rois_smem, stream));
+    }
     return CCST_OK;
 }
 
@@ -2782,7 +2808,7 @@ static int rois_launch(ccst_ctx* c, RoiItem* items, int64_t n, Result* out, cuda
     int rc = rois_upload(c);
     if (rc) return rc;
     CK(c, cudaMemcpyAsync(items_dev, items, (size_t)n * sizeof(RoiItem), cudaMemcpyHostToDevice, stream));
-    return rois_kernel_launch(c, items_dev, n, out, stream, counter);
+    return rois_kernel_launch(c, items_dev, n, rois_big_items(c, items, n), out, stream, counter);
 }
 
 constexpr size_t kMaxRoiGraphs = 64;
@@ -2845,7 +2871,7 @@ static int rois_graph_track(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccst_r
         auto bail = [&](int code) { free_roi_graph(e); return code; };
         cudaError_t err;
         if ((err = cudaEventCreateWithFlags(&e.done, cudaEventDisableTiming)) != cudaSuccess ||
-            (err = cudaMalloc(&e.counters, 2 * sizeof(unsigned))) != cudaSuccess)
+            (err = cudaMalloc(&e.counters, 3 * sizeof(unsigned))) != cudaSuccess)
             return bail(fail(c, CCST_E_CUDA, std::string("ccst_track_rois: ") + cudaGetErrorString(err)));
         if (np > 0) {
             rois_sort(c, c->h_items.data(), np);
@@ -2875,11 +2901,13 @@ static int rois_graph_track(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccst_r
             if (cudaEventRecord(c->gfork, c->stream) != cudaSuccess ||
                 cudaStreamWaitEvent(c->gstream, c->gfork, 0) != cudaSuccess)
                 lrc = fail(c, CCST_E_CUDA, "ccst_track_rois: fork during capture");
-            if (!lrc) lrc = gen_kernel_launch(c, gb, *lane, stride, c->gstream, e.counters + 1, c->h_gitems.data());
+            if (!lrc) lrc = gen_kernel_launch(c, gb, *lane, stride, c->gstream, e.counters + 2, c->h_gitems.data());
             if (!lrc && cudaEventRecord(c->gjoin, c->gstream) != cudaSuccess)
                 lrc = fail(c, CCST_E_CUDA, "ccst_track_rois: join during capture");
         }
-        if (!lrc && np > 0) lrc = rois_kernel_launch(c, e.d_items, np, (Result*)out_dev, c->stream, e.counters);
+        if (!lrc && np > 0)
+            lrc = rois_kernel_launch(c, e.d_items, np, rois_big_items(c, c->h_items.data(), np), (Result*)out_dev,
+                                     c->stream, e.counters);
         if (!lrc && ng > 0 && cudaStreamWaitEvent(c->stream, c->gjoin, 0) != cudaSuccess)
             lrc = fail(c, CCST_E_CUDA, "ccst_track_rois: join during capture");
         err = cudaStreamEndCapture(c->stream, &graph);
@@ -3019,7 +3047,7 @@ struct ccst_server {
     std::deque<Span> spans;
     char* h_frames = nullptr;
     char* d_frames = nullptr;          // the same memory as the device addresses it
-    unsigned* d_counters = nullptr;    // two item counters per ring entry (power-of-two, general)
+    unsigned* d_counters = nullptr;    // three item counters per ring entry (power-of-two: two kernels; general)
     InFlight ring[kRing];
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -3161,13 +3189,13 @@ static void server_loop(ccst_server* s) {
         }
         // each kernel writes record i of the batch to d_out[i]; out_index survives the sorts
         bool ok = true;
-        if (np > 0) ok = rois_launch(c, b.h_items, np, b.d_out, b.st, b.d_items, s->d_counters + 2 * next) == CCST_OK;
+        if (np > 0) ok = rois_launch(c, b.h_items, np, b.d_out, b.st, b.d_items, s->d_counters + 3 * next) == CCST_OK;
         if (ok && ng > 0) {
             gen_sort(c, b.h_gitems, ng);
             GenBatch gb{};
             gb.n = ng;
             gb.out = b.d_out;
-            ok = gen_launch(c, b.lane, gb, b.h_gitems, b.st, s->d_counters + 2 * next + 1) == CCST_OK;
+            ok = gen_launch(c, b.lane, gb, b.h_gitems, b.st, s->d_counters + 3 * next + 2) == CCST_OK;
         }
         ok = ok && cudaMemcpyAsync(b.h_out, b.d_out, (size_t)m * sizeof(Result), cudaMemcpyDeviceToHost, b.st) ==
                        cudaSuccess;
@@ -3243,7 +3271,7 @@ extern "C" int ccst_server_create_ex(ccst_ctx* c, const ccst_server_config* cfg,
     cudaError_t e;
     if ((e = cudaHostAlloc(&s->h_frames, (size_t)s->cap, cudaHostAllocMapped)) != cudaSuccess) return bad(e);
     if ((e = cudaHostGetDevicePointer((void**)&s->d_frames, s->h_frames, 0)) != cudaSuccess) return bad(e);
-    if ((e = cudaMalloc(&s->d_counters, 2 * ccst_server::kRing * sizeof(unsigned))) != cudaSuccess) return bad(e);
+    if ((e = cudaMalloc(&s->d_counters, 3 * ccst_server::kRing * sizeof(unsigned))) != cudaSuccess) return bad(e);
     for (int k = 0; k < s->depth; ++k) {
         auto& b = s->ring[k];
         if ((e = cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking)) != cudaSuccess) return bad(e);
@@ -3589,11 +3617,11 @@ extern "C" int ccst_track_static(const float* ref_dev, int H, int W, const ccst_
         b.vec_ok = ((uintptr_t)frames_dev % 16 == 0) && ((size_t)pitch_elems * el % 16 == 0) ? 1 : 0;
         const void* kern = track_kernel_for(H, W);
         int occ = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, track_threads(H, W), smem);
         const long long cap = (long long)sd.sms * (occ > 0 ? occ : 1);
         const int grid = (int)(n < cap ? n : cap);
         void* args[] = {&g, &b};
-        if ((e = cudaLaunchKernel(kern, dim3(grid), dim3(kThreads), args, smem, stream)) != cudaSuccess)
+        if ((e = cudaLaunchKernel(kern, dim3(grid), dim3(track_threads(H, W)), args, smem, stream)) != cudaSuccess)
             return static_fail(CCST_E_CUDA, "ccst_track_static launch: ", cudaGetErrorString(e));
     }
     if ((e = cudaGetLastError()) != cudaSuccess)

@@ -2222,8 +2222,15 @@ __device__ __forceinline__ bool track_frame(const Geom& g, const Batch& b, const
     return true;
 }
 
+// CTA size and CTAs per SM of track_kernel<H, W>: frames up to 64 x 64 are latency-bound
+// with one 512-thread CTA per SM (a few hundred tasks per phase between barriers), so they
+// run two 256-thread CTAs per SM. The P/Q build takes one task per thread for 4 W tasks,
+// which 256 threads cover up to W = 64.
+__host__ __device__ constexpr int track_threads(int H, int W) { return (H <= 64 && W <= 64) ? 256 : kThreads; }
+__host__ __device__ constexpr int track_min_ctas(int H, int W) { return (H <= 64 && W <= 64) ? 2 : 1; }
+
 template <int H, int W>
-__global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
+__global__ void __launch_bounds__(track_threads(H, W), track_min_ctas(H, W)) track_kernel(Geom g, Batch b) {
     const Smem S = carve(g, ccst_smem);
     track_setup<H, W>(g, S);
     tables_bar_init(S);
@@ -2251,8 +2258,10 @@ __global__ void __launch_bounds__(kThreads, 1) track_kernel(Geom g, Batch b) {
     }
 }
 
-// Address of the uneven-ROI kernel (ccst_rois.cu).
-const void* track_rois_kernel_ptr();
+// Address of the uneven-ROI kernel (ccst_rois.cu): `small` is the instantiation for the
+// size classes up to 64 x 64 (track_threads(64, 64) threads, two CTAs per SM); the other
+// takes every class (the host gives it the 128 x 128 items).
+const void* track_rois_kernel_ptr(bool small);
 
 // Address of track_kernel<H, W> (defined in the per-height translation units).
 const void* track_kernel_h8(int W);

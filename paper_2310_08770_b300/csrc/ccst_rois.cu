@@ -18,7 +18,11 @@ __device__ __forceinline__ void bar_inval(const Smem& S) {
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) track_rois_kernel(RoiBatch rb) {
+// kSmall: the instantiation for classes up to 64 x 64, with the CTA shape of
+// track_kernel<64, 64> (so that its records equal ccst_track's at those sizes).
+template <bool kSmall>
+__global__ void __launch_bounds__(kSmall ? track_threads(64, 64) : kThreads, kSmall ? track_min_ctas(64, 64) : 1)
+    track_rois_kernel(RoiBatch rb) {
     __shared__ Geom sg;
     __shared__ long long s_item;
     int cur = -1;                      // size class of the current set-up
@@ -26,7 +30,7 @@ __global__ void __launch_bounds__(kThreads, 1) track_rois_kernel(RoiBatch rb) {
     Smem S{};
     // Tensor Memory for the 128 x 128 class's tensor-core contraction; one CTA per SM (the
     // register file is full), so the allocation never waits on another CTA
-    tc_setup();
+    if constexpr (!kSmall) tc_setup();
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_item = (long long)atomicAdd(rb.next, 1u);
@@ -43,7 +47,9 @@ __global__ void __launch_bounds__(kThreads, 1) track_rois_kernel(RoiBatch rb) {
                 case 16: track_setup<16, 16>(sg, S); break;
                 case 32: track_setup<32, 32>(sg, S); break;
                 case 64: track_setup<64, 64>(sg, S); break;
-                default: track_setup<128, 128>(sg, S); break;
+                default:
+                    if constexpr (!kSmall) track_setup<128, 128>(sg, S);
+                    break;
             }
             tables_bar_init(S);
             parity = 0;
@@ -69,13 +75,18 @@ __global__ void __launch_bounds__(kThreads, 1) track_rois_kernel(RoiBatch rb) {
             case 16: ok = track_frame<16, 16>(sg, b, S, it.out_index, frame, parity); break;
             case 32: ok = track_frame<32, 32>(sg, b, S, it.out_index, frame, parity); break;
             case 64: ok = track_frame<64, 64>(sg, b, S, it.out_index, frame, parity); break;
-            default: ok = track_frame<128, 128>(sg, b, S, it.out_index, frame, parity); break;
+            default:
+                if constexpr (!kSmall) ok = track_frame<128, 128>(sg, b, S, it.out_index, frame, parity);
+                else ok = false;              // never given to this instantiation
+                break;
         }
         if (!ok) break;
     }
-    tc_teardown();
+    if constexpr (!kSmall) tc_teardown();
 }
 
-const void* track_rois_kernel_ptr() { return (const void*)track_rois_kernel; }
+const void* track_rois_kernel_ptr(bool small) {
+    return small ? (const void*)track_rois_kernel<true> : (const void*)track_rois_kernel<false>;
+}
 
 }  // namespace ccst
