@@ -299,7 +299,9 @@ typedef struct ccst_tune_result {
 
 /* Autotune the double-float general-size kernel (NEXT-2: the size-dependent choices of the
  * uneven-ROI path; the FP32 general-size kernel has one compiled schedule per side and
- * nothing to tune). For every general-size plan of the context (shapes added by ccst_create or
+ * nothing to tune, and is bypassed while this call times, so that every plan's frames
+ * exercise the double-float kernel, which also takes the FP32 kernel's fallback frames).
+ * For every general-size plan of the context (shapes added by ccst_create or
  * ccst_add_reference outside the power-of-two kernel) it times, on synthetic frames of the
  * plan's shape and one of its references, each two-level split of the row and column DFTs
  * (the default: the largest divisor of N not above sqrt(N); its cofactor; the next divisor

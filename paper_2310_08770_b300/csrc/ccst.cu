@@ -726,6 +726,7 @@ struct ccst_ctx {
     int gen_grid = 0;
     int gen_threads = 512;            // CTA size of the general-size kernel (ccst_autotune may lower it)
     bool gen_dirty = true;            // plans or references changed since the last upload
+    bool mix_off = false;             // ccst_autotune: the FP32 general-size kernel is bypassed
     bool general = false;             // every frame of this context takes the general-size kernel
     Geom* d_geoms = nullptr;
     RefSpectra* d_refs = nullptr;
@@ -2420,9 +2421,13 @@ static int mix_reserve(ccst_ctx* c, GenLane& lane, long long n, bool* grew) {
     return CCST_OK;
 }
 
+// Plan p runs on the FP32 general-size kernel (not while ccst_autotune times the
+// double-float kernel).
+static bool plan_mix(ccst_ctx* c, int p) { return c->gplans[p].mix && !c->mix_off; }
+
 static bool any_mix_plan(ccst_ctx* c) {
-    for (auto& g : c->gplans)
-        if (g.mix) return true;
+    for (int p = 0; p < (int)c->gplans.size(); ++p)
+        if (plan_mix(c, p)) return true;
     return false;
 }
 
@@ -2439,13 +2444,13 @@ static int gen_kernel_launch(ccst_ctx* c, GenBatch gb, GenLane& lane, long long 
     int ns = 0;
     long long ndirect = gb.n;
     if (!gb.items) {
-        if (c->gplans[gb.plan].mix) {
+        if (plan_mix(c, gb.plan)) {
             segs[ns++] = Seg{0, gb.n, gb.plan};
             ndirect = 0;
         }
     } else if (items_host) {
         long long i = 0;
-        while (i < gb.n && !c->gplans[items_host[i].plan].mix) ++i;
+        while (i < gb.n && !plan_mix(c, items_host[i].plan)) ++i;
         ndirect = i;
         while (i < gb.n && ns < kMixCounters - 1) {
             long long j = i;
@@ -2556,7 +2561,8 @@ static int gen_launch(ccst_ctx* c, GenLane& lane, GenBatch gb, const GenItem* it
 static void gen_sort(ccst_ctx* c, GenItem* items, int64_t n) {
     std::stable_sort(items, items + n, [&](const GenItem& a, const GenItem& b) {
         const auto &ga = c->gplans[a.plan], &gb = c->gplans[b.plan];
-        if (ga.mix != gb.mix) return !ga.mix;
+        const bool ma = plan_mix(c, a.plan), mb = plan_mix(c, b.plan);
+        if (ma != mb) return !ma;
         if (ga.p.H * ga.p.W != gb.p.H * gb.p.W) return ga.p.H * ga.p.W > gb.p.H * gb.p.W;
         return a.plan < b.plan;
     });
@@ -2603,6 +2609,7 @@ extern "C" int ccst_autotune(ccst_ctx* c, int reps, const ccst_roi* rois, int64_
     const int np = (int)c->gplans.size();
     if (np == 0) return CCST_OK;
     drop_roi_graphs(c);           // schedules change below: captured launches would go stale
+    c->mix_off = true;            // time the double-float kernel itself, on every plan
     std::vector<int> ref_of(np, -1);
     for (int i = 0; i < (int)c->refs.size(); ++i)
         if (c->refs[i].gcls >= 0 && ref_of[c->refs[i].gcls] < 0) ref_of[c->refs[i].gcls] = i;
@@ -2631,6 +2638,7 @@ extern "C" int ccst_autotune(ccst_ctx* c, int reps, const ccst_roi* rois, int64_
     };
     auto bail = [&](int code) {
         cleanup();
+        c->mix_off = false;
         for (int p = 0; p < np; ++p) set_split(p, saved[p].first, saved[p].second);
         c->gen_threads = saved_threads;
         c->gen_grid = 0;
@@ -2741,6 +2749,7 @@ extern "C" int ccst_autotune(ccst_ctx* c, int reps, const ccst_roi* rois, int64_
         ++timed;
     }
     cleanup();
+    c->mix_off = false;
     c->gen_threads = tms[1] < tms[0] ? 256 : 512;
     c->gen_grid = 0;
     c->gen_dirty = true;
