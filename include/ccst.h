@@ -91,8 +91,8 @@ extern "C" {
 #define CCST_R_GENERIC     0x80u /* tracked by the double-float general-size kernel (ccst_track_rois,
                                     sides other than 16, 32, 64, 128): direct DFTs in double-float,
                                     no near-tie levels */
-#define CCST_R_FP32_GENERAL 0x100u /* tracked by the FP32 general-size kernel (square sides 48, 96,
-                                    192 and 256, u <= 256): mixed-radix (2, 3) FFTs and the
+#define CCST_R_FP32_GENERAL 0x100u /* tracked by the FP32 general-size kernel (48, 96, 192 and 256
+                                    square, 256 x 128 either way, u <= 256): mixed-radix (2, 3) FFTs and the
                                     upsampled contraction in FP32, with the integer and sub-pixel
                                     guard levels; a frame they cannot certify is tracked again by
                                     the double-float kernel and its record carries CCST_R_GENERIC */
@@ -149,13 +149,14 @@ int ccst_default_params(ccst_params* p);
  *           context: FP32 FFTs, the upsampled contraction on tensor cores, the near-tie
  *           levels, and every entry point below.
  *         - Every other shape makes a general-shape context.
- *           48 x 48, 96 x 96, 192 x 192 and 256 x 256 (u <= 256) run on the FP32
+ *           48 x 48, 96 x 96, 192 x 192, 256 x 256, and 256 x 128 either way round
+ *           (u <= 256) run on the FP32
  *           general-size kernel: mixed-radix (2, 3) FFTs and the upsampled contraction
  *           in FP32 in shared memory (one to four CTAs per frame), with the integer,
  *           sub-pixel, pair-difference and double-float guard levels; records carry
  *           CCST_R_FP32_GENERAL. A frame those levels cannot certify (a tie within
  *           2^-36 sum|X|) is tracked again by the double-float kernel.
- *           Every other shape (256 x 128, 100 x 60, ...), and those frames, run on the
+ *           Every other shape (192 x 64, 100 x 60, ...), and those frames, run on the
  *           double-float kernel: direct DFTs over the Hermitian half and the full-grid
  *           upsampled sum, in double-float (about 2^-46 per term, so no near-tie levels
  *           are needed); records carry CCST_R_GENERIC.

@@ -2259,7 +2259,7 @@ static int gen_plan(ccst_ctx* c, int H, int W, int* gcls) {
         cudaFree(tab);
         return fail(c, CCST_E_CUDA, std::string("gen_init_tables: ") + cudaGetErrorString(e));
     }
-    if (!pl.exhaustive && H == W && mix_side_ok(H)) {
+    if (!pl.exhaustive && mix_shape_ok(H, W)) {
         // the FP32 kernel for this side, with this kernel as its fallback
         int optin = 0;
         CK(c, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));

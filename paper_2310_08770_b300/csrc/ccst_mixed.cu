@@ -47,8 +47,10 @@ namespace mix {
 // hundred tasks between barriers), so 48 and 96 run 4 and 2 smaller CTAs per SM; 192 takes
 // a whole SM per CTA, and 256 takes 384 threads, whose 16-point register DFTs want more
 // than the 128 registers a 512-thread CTA leaves each thread.
-__host__ __device__ constexpr int mix_threads(int H) { return H <= 48 ? 128 : H <= 96 ? 256 : H >= 256 ? 384 : 512; }
-__host__ __device__ constexpr int mix_min_ctas(int H) { return H <= 48 ? 4 : H <= 96 ? 2 : 1; }
+__host__ __device__ constexpr int mix_threads(int H, int W) {
+    return H * W <= 48 * 48 ? 128 : H * W <= 96 * 96 ? 256 : (H >= 256 || W >= 256) ? 384 : 512;
+}
+__host__ __device__ constexpr int mix_min_ctas(int H, int W) { return H * W <= 48 * 48 ? 4 : H * W <= 96 * 96 ? 2 : 1; }
 constexpr int kTM = 8;            // t rows per contraction task
 
 template <int CL>
@@ -187,7 +189,7 @@ __device__ __forceinline__ int mix_level2(const MixArgs& a, const MixSh& S, unsi
     constexpr int L = Gm::L, Wc = Gm::Wc, RH = Gm::RH, KB = Gm::KB;
     constexpr int N1h = Gm::N1h, N2h = Gm::N2h, N1r = Gm::N1r, N2r = Gm::N2r, RSG = Gm::RSG;
     constexpr int NP = L / 2 + 1;
-    constexpr int kNT = mix_threads(H);
+    constexpr int kNT = mix_threads(H, W);
     const MixPlan& P = a.p;
     const int rank = Clu<CL>::rank(), tid = threadIdx.x;
     const int b0 = rank * KB, nb = min(KB, Wc - b0), row0 = rank * RH;
@@ -343,9 +345,9 @@ __device__ __noinline__ int mix_level2_call(const MixArgs& a, const MixSh& S, un
 }
 
 template <int H, int W, int CL>
-__global__ void __launch_bounds__(mix_threads(H), mix_min_ctas(H)) __cluster_dims__(CL, 1, 1)
+__global__ void __launch_bounds__(mix_threads(H, W), mix_min_ctas(H, W)) __cluster_dims__(CL, 1, 1)
     mix_track_kernel(const MixArgs a) {
-    constexpr int kNT = mix_threads(H);
+    constexpr int kNT = mix_threads(H, W);
     using Gm = Geo<H, W, CL>;
     constexpr int L = Gm::L, Wc = Gm::Wc, Hh = Gm::Hh, RH = Gm::RH, KB = Gm::KB;
     constexpr int N1h = Gm::N1h, N2h = Gm::N2h, N1r = Gm::N1r, N2r = Gm::N2r, RSG = Gm::RSG;
@@ -1011,22 +1013,21 @@ __global__ void __launch_bounds__(mix_threads(H), mix_min_ctas(H)) __cluster_dim
     }
 }
 
-template <int N>
+template <int H, int W>
 const void* kernel_for() {
-    return (const void*)mix_track_kernel<N, N, (N <= 96 ? 1 : (N == 192 ? 2 : 4))>;
+    return (const void*)mix_track_kernel<H, W, mix_cluster(H, W)>;
 }
 
 }  // namespace mix
 
 const void* mix_kernel_ptr(int H, int W) {
-    if (H != W) return nullptr;
-    switch (H) {
-        case 48: return mix::kernel_for<48>();
-        case 96: return mix::kernel_for<96>();
-        case 192: return mix::kernel_for<192>();
-        case 256: return mix::kernel_for<256>();
-        default: return nullptr;
-    }
+    if (H == 48 && W == 48) return mix::kernel_for<48, 48>();
+    if (H == 96 && W == 96) return mix::kernel_for<96, 96>();
+    if (H == 192 && W == 192) return mix::kernel_for<192, 192>();
+    if (H == 256 && W == 256) return mix::kernel_for<256, 256>();
+    if (H == 256 && W == 128) return mix::kernel_for<256, 128>();
+    if (H == 128 && W == 256) return mix::kernel_for<128, 256>();
+    return nullptr;
 }
 
 // ------------------------------------------------------------------ host: the plan
@@ -1047,26 +1048,27 @@ double cosm1_2pi(long long n, long long D) {
     const double h = std::sin(kPi * (double)n / (double)D);
     return -2.0 * h * h;
 }
-template <int N>
-void pass_twiddles(std::vector<float2>& t) {
-    constexpr int N1 = mix::MSplit<N>::N1, N2 = mix::MSplit<N>::N2;
-    for (int k1 = 0; k1 < N1; ++k1)
-        for (int n2 = 0; n2 < N2; ++n2) {
-            double c, s;
-            cexp2pi(-(long long)n2 * k1, N, &c, &s);
-            t.push_back(make_float2((float)c, (float)s));
-        }
-}
-void pass_twiddles_n(int N, std::vector<float2>& t) {
+// the kernel's four-step split of length N (mix::MSplit), false if it has none
+bool msplit(int N, int* n1, int* n2) {
     switch (N) {
-        case 24: pass_twiddles<24>(t); break;
-        case 48: pass_twiddles<48>(t); break;
-        case 96: pass_twiddles<96>(t); break;
-        case 128: pass_twiddles<128>(t); break;
-        case 192: pass_twiddles<192>(t); break;
-        case 256: pass_twiddles<256>(t); break;
-        default: break;
+#define CCST_SPLIT(n) case n: *n1 = mix::MSplit<n>::N1; *n2 = mix::MSplit<n>::N2; return true;
+        CCST_SPLIT(24) CCST_SPLIT(48) CCST_SPLIT(64) CCST_SPLIT(96) CCST_SPLIT(128) CCST_SPLIT(192) CCST_SPLIT(256)
+#undef CCST_SPLIT
+        default: return false;
     }
+}
+// W_N^{n2 k1} laid out [k1][n2] for the split of N, through `put(c, s)`
+template <class PUT>
+bool pass_twiddles_n(int N, PUT put) {
+    int n1 = 0, n2 = 0;
+    if (!msplit(N, &n1, &n2)) return false;
+    for (int k1 = 0; k1 < n1; ++k1)
+        for (int j = 0; j < n2; ++j) {
+            double c, s;
+            cexp2pi(-(long long)j * k1, N, &c, &s);
+            put(c, s);
+        }
+    return true;
 }
 // staged rows per group: the largest divisor of the CTA's row count up to 64 whose staging
 // buffer stays within 36 KB
@@ -1081,15 +1083,15 @@ int staged_rows(int RH, int rsg) {
 int mix_plan_create(int H, int W, int u, int method, int in_dtype, float eps, float tau_int, float tau0, float tau1,
                     int smem_optin, MixPlan* out, void** mem) {
     *mem = nullptr;
-    if (H != W || !mix_side_ok(H) || u < 1 || u > 256) return -1;
+    if (!mix_shape_ok(H, W) || u < 1 || u > 256) return -1;
     MixPlan p{};
     p.H = H;
     p.W = W;
     p.L = W / 2;
     p.Wc = p.L + 1;
     p.Hh = H / 2;
-    p.CL = mix_cluster(H);
-    p.NT = mix::mix_threads(H);
+    p.CL = mix_cluster(H, W);
+    p.NT = mix::mix_threads(H, W);
     p.KB = (p.Wc + p.CL - 1) / p.CL;
     p.u = u;
     p.M = (3 * u + 1) / 2;
@@ -1104,8 +1106,10 @@ int mix_plan_create(int H, int W, int u, int method, int in_dtype, float eps, fl
     p.tau0 = tau0;
     p.tau1 = tau1;
     p.RSX = p.KB;
-    const int n2r = p.L == 24 ? 3 : (p.L == 48 ? 4 : 8), n1r = p.L / n2r;
-    p.RSG = p.L + n1r;
+    int n1r = 0, n2r = 0;
+    if (!msplit(p.L, &n1r, &n2r) || !msplit(H, &n1r, &n2r)) return -1;
+    msplit(p.L, &n1r, &n2r);
+    p.RSG = n2r > 1 ? p.L + n1r : p.L;          // mix_padded_len of the half-row length
     p.G = staged_rows(H / p.CL, p.RSG);
     if (p.G < 1) return -1;
     p.G2 = 1;                                   // double-float staging: up to 8 rows per group
@@ -1151,24 +1155,18 @@ int mix_plan_create(int H, int W, int u, int method, int in_dtype, float eps, fl
     // tables, in one device block
     std::vector<float2> t4h, t4r, rtw, phH, phW, tA((size_t)p.Hh * p.TAp), tB((size_t)p.Wc * p.TXp);
     std::vector<float> tG((size_t)p.Wc * p.TXp);
-    pass_twiddles_n(H, t4h);
-    pass_twiddles_n(p.L, t4r);
-    if ((int)t4h.size() != H || (int)t4r.size() != p.L) return -1;
-    // the same twiddles as double-floats (hi = the FP32 rounding, lo = the rest)
+    // inter-pass twiddles in FP32 and as double-floats (hi = the FP32 rounding, lo = the rest)
     auto to_df = [](double x) { const float h = (float)x; return df{h, (float)(x - (double)h)}; };
     std::vector<dfc> t4h_d, t4r_d, rtw_d;
-    auto pass_twiddles_d = [&](int N, std::vector<dfc>& t) {
-        const int n2c = N == 256 ? 16 : N == 192 ? 12 : N == 128 ? 8 : N == 96 ? 8 : N == 48 ? 4 : 3;
-        const int n1c = N / n2c;
-        for (int k1 = 0; k1 < n1c; ++k1)
-            for (int n2 = 0; n2 < n2c; ++n2) {
-                double c, sn;
-                cexp2pi(-(long long)n2 * k1, N, &c, &sn);
-                t.push_back(dfc{to_df(c), to_df(sn)});
-            }
-    };
-    pass_twiddles_d(H, t4h_d);
-    pass_twiddles_d(p.L, t4r_d);
+    pass_twiddles_n(H, [&](double c, double sn) {
+        t4h.push_back(make_float2((float)c, (float)sn));
+        t4h_d.push_back(dfc{to_df(c), to_df(sn)});
+    });
+    pass_twiddles_n(p.L, [&](double c, double sn) {
+        t4r.push_back(make_float2((float)c, (float)sn));
+        t4r_d.push_back(dfc{to_df(c), to_df(sn)});
+    });
+    if ((int)t4h.size() != H || (int)t4r.size() != p.L) return -1;
     for (int k = 0; k <= p.L / 2; ++k) {
         double c, sn;
         cexp2pi(-k, W, &c, &sn);

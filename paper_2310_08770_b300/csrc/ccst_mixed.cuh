@@ -71,9 +71,13 @@ struct MixDbg {
     float* d32;
 };
 
-// Side lengths with an FP32 kernel, and their cluster sizes.
-inline bool mix_side_ok(int N) { return N == 48 || N == 96 || N == 192 || N == 256; }
-inline int mix_cluster(int N) { return N <= 96 ? 1 : (N == 192 ? 2 : 4); }
+// Shapes with an FP32 kernel (H x W: the squares 48, 96, 192, 256 and the paper's Table I
+// shape 256 x 128 both ways), and their CTAs per frame.
+inline bool mix_shape_ok(int H, int W) {
+    return (H == W && (H == 48 || H == 96 || H == 192 || H == 256)) || (H == 256 && W == 128) ||
+           (H == 128 && W == 256);
+}
+__host__ __device__ constexpr int mix_cluster(int H, int W) { return H * W <= 96 * 96 ? 1 : H * W <= 192 * 192 ? 2 : 4; }
 
 // Kernel address for an H x W plan (null if none), and the plan's tables and layout: fills
 // every field of *p from (H, W, u, method, in_dtype, eps) and uploads the tables into one

@@ -175,7 +175,7 @@ def test_shapes_outside_the_range_are_refused(torch):
 
 
 @pytest.mark.parametrize("H,W,u,method", [(72, 72, 100, oracle.CC_U), (48, 80, 64, oracle.CC_SN),
-                                          (30, 30, 100, oracle.CC_U), (256, 128, 50, oracle.CC_U),
+                                          (30, 30, 100, oracle.CC_U), (192, 128, 50, oracle.CC_U),
                                           (12, 8, 3, oracle.CC_SN),
                                           # grids above 256 points a side: pass 2 recomputes the
                                           # FP32 values, and the row bitmap spans many words

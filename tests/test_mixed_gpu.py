@@ -275,3 +275,18 @@ def test_integer_near_ties_are_decided_in_double_float(torch, N):
     guarded = int(np.sum((res["flags"] & C.R_INT_GUARD) != 0))
     assert guarded >= 3, res["flags"]
     check(ref, frames, res, 100, oracle.CC_U)
+
+
+@pytest.mark.parametrize("H,W", [(256, 128), (128, 256)])
+@pytest.mark.parametrize("method", [oracle.CC_U, oracle.CC_SN])
+def test_table_one_shape_both_ways(torch, H, W, method):
+    # the paper's Table I frame shape, 256 x 128, and its transpose: clusters of two CTAs
+    rng = np.random.default_rng(150 + H + method)
+    ref = synth.gaussian_spot(H, W, H / 2, W / 2, 3.0, 1500.0, 15.0).astype(np.float32)
+    d = rng.uniform(-3, 3, size=(8, 2))
+    frames = np.array([rng.poisson(synth.gaussian_spot(H, W, H / 2 + p[0], W / 2 + p[1], 3.0, 1500.0, 15.0))
+                       for p in d]).astype(np.uint16)
+    res = track(torch, ref, frames, 100, method)
+    check(ref, frames, res, 100, method)
+    if method == oracle.CC_U:
+        assert np.sum((res["flags"] & C.R_FP32_GENERAL) != 0) >= 7, res["flags"]
