@@ -706,6 +706,60 @@ def rois_leg(C, torch, stream, n_rois=ROIS_N, sides=ROIS_SIDES, plain=True):
     return line, (r, res)
 
 
+# The paper's Table I (CC-SN images/s, CUDA on an RTX 3080): context for the same shapes and
+# upsampling factors on this GPU, not a target (other hardware, unstated workload).
+TABLE1_CUDA = {(256, 128): {128: 1636, 256: 811}, (256, 256): {128: 981, 256: 432}}
+TABLE1_FRAMES = 2048
+TABLE1_ORACLE = 4
+
+
+def table1_leg(C, torch, stream):
+    """CC-SN on noise-free-reference / Poisson spot frames of the paper's Table I shapes
+    (256 x 128 and 256 x 256, uint16) at u = 128 and 256: batched images/s through ccst_track
+    (the FP32 general-size kernel), with the first frames checked against the FP64 oracle."""
+    import oracle
+    from paper_2310_08770_b300 import synth
+    out = []
+    rng = np.random.default_rng(11)
+    for (h, w), paper in TABLE1_CUDA.items():
+        ref = synth.gaussian_spot(h, w, h / 2, w / 2, 3.0, 2000.0, 20.0).astype(np.float32)
+        d = rng.uniform(-3, 3, size=(64, 2))
+        pool = np.array([rng.poisson(synth.gaussian_spot(h, w, h / 2 + p[0], w / 2 + p[1], 3.0, 2000.0, 20.0))
+                         for p in d]).astype(np.uint16)
+        frames = np.concatenate([pool] * (TABLE1_FRAMES // len(pool)))
+        dev = torch.from_numpy(frames.view(np.int16)).cuda().view(torch.uint16)
+        for u in sorted(paper):
+            with torch.cuda.stream(stream):
+                t = C.Tracker(ref, upsample=u, method="ccsn", in_dtype="u16", max_batch=len(frames), stream=stream)
+                o = t.empty_results(len(frames))
+                for _ in range(2):
+                    C.ccst_track(t.ctx, dev, len(frames), 0, o)
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(3):
+                    C.ccst_track(t.ctx, dev, len(frames), 0, o)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(b) / 3
+                res = C.decode(o)
+                t.close()
+            bad = 0
+            for i in range(TABLE1_ORACLE):
+                q = oracle.track_one(frames[i].astype(np.float64), ref.astype(np.float64), u, oracle.CC_SN)
+                if (int(res["ipy"][i]), int(res["ipx"][i])) != (q["ipy"], q["ipx"]) or \
+                        abs(float(res["dx"][i]) - q["dx32"]) > 1e-3 or abs(float(res["dy"][i]) - q["dy32"]) > 1e-3:
+                    bad += 1
+            out.append({"shape": f"{h}x{w}", "u": u, "images_per_s": len(frames) / (ms / 1e3),
+                        "fp32_records": int(np.sum((res["flags"] & C.R_FP32_GENERAL) != 0)),
+                        "frames": len(frames), "oracle_checked": TABLE1_ORACLE, "oracle_mismatches": bad,
+                        "paper_cuda_images_per_s": paper[u]})
+    return {"workload": "the paper's Table I shapes, CC-SN, uint16 Poisson spot frames (sigma 3, peak 2000, bg 20, "
+                        f"shifts U(-3,3)^2) against a noise-free reference, batches of {TABLE1_FRAMES} frames",
+            "context": "paper_cuda_images_per_s: Table I, CUDA on an RTX 3080 (another GPU, workload unstated); "
+                       "not a target", "runs": out}
+
+
 def rois_cpu_baseline(r, res):
     """The FP64 oracle on the first ROIS_ORACLE ROIs: its rate and parity with the batch."""
     import oracle
@@ -1062,6 +1116,8 @@ def run_ours(args):
         line["serving"]["true_sides"] = serving_leg(C, torch, SERVE_TRUE_SIDES, SERVE_TRUE_SECONDS, 2048,
                                                     " (96, 192, 256 on the FP32 general-size kernel)")
     rois_extra = None
+    if world == 1 and not args.no_table1:
+        line["table1"] = table1_leg(C, torch, stream)
     if world == 1 and not args.no_rois:
         sides = tuple(int(x) for x in args.rois_sides.split(",")) if args.rois_sides else ROIS_SIDES
         line["rois"], rois_extra = rois_leg(C, torch, stream, args.rois_n, sides, plain=sides == ROIS_SIDES)
@@ -1171,6 +1227,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-rois", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-table1", action="store_true")
     ap.add_argument("--rois-n", type=int, default=ROIS_N)
     ap.add_argument("--rois-sides", default="", help="comma-separated ROI sides of the uneven-ROI leg "
                     "(default: the survey's mix); e.g. 96 to profile one kernel")
