@@ -1132,7 +1132,7 @@ extern "C" int ccst_create(const float* ref, int H, int W, const ccst_params* pi
         return bail_work(CCST_E_CUDA);
     cudaFree(d_work);
     d_work = nullptr;
-    c->kernel = track_kernel_for(H, W);
+    c->kernel = (H == 128 && W == 128 && g.tc) ? track_kernel_128_tc() : track_kernel_for(H, W);
     c->threads = track_threads(H, W);
     // the attribute is per function: set it to the device limit so contexts of any size coexist
     if (!step(cudaFuncSetAttribute(c->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

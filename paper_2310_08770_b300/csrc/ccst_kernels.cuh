@@ -1538,43 +1538,49 @@ __device__ void upsampled_pass_tc(const Geom& g, const Smem& S, TopK<kTopK>& top
 }
 
 // Full upsampled surface pass (all chunks): top-K, or candidate collection.
-template <int H, int W, bool kCollect>
+// kTcOnly: the 128 x 128 instantiation for plans that use tcgen05 (g.tc), compiled without
+// the warp-MMA stages (a smaller kernel: its first stall was instruction fetch).
+template <int H, int W, bool kCollect, bool kTcOnly = false>
 __device__ __forceinline__ void upsampled_pass(const Geom& g, const Smem& S, TopK<kTopK>& top, float thr,
                                                float* dbg) {
-    if constexpr (H == 128 && W == 128) {
-        if (g.tc) {
-            upsampled_pass_tc<kCollect>(g, S, top, thr, dbg);
-            return;
-        }
-    }
-    const uint2* TA = g.tables_smem ? S.TA : g.tAh;
-    const uint2* TB = g.tables_smem ? S.TB : g.tBh;
-    const float dsc = ldexpf(1.f, -13 - S.misc[3]);
-    const Emitter<kCollect> emit{g, S, top, thr, dbg};
-    for (int c = 0; c < g.nchunk; ++c) {
-        const int t0 = 1 + c * g.TC;
-        stage_a<H, W>(g, S, t0, TA);
-        if (W % 32 == 0 && g.tables_smem) stage_b_mma<W, kCollect>(g, S, t0, TB, dsc, emit);
-        else stage_b_simt<kCollect>(g, S, t0, TB, dsc, emit);
-        // the t = 0 row: S = 0, the surface is g(tx)
-        if (t0 == 1) {
-            for (int x = threadIdx.x; x <= g.h0; x += blockDim.x) {
-                if (x <= g.pmax) emit(S.gP[x], 0, x);
-                if (x >= 1) emit(S.gM[x], 0, -x);
+    if constexpr (kTcOnly) {
+        upsampled_pass_tc<kCollect>(g, S, top, thr, dbg);
+    } else {
+        if constexpr (H == 128 && W == 128 && !kTcOnly) {
+            if (g.tc) {
+                upsampled_pass_tc<kCollect>(g, S, top, thr, dbg);
+                return;
             }
         }
-        __syncthreads();
+        const uint2* TA = g.tables_smem ? S.TA : g.tAh;
+        const uint2* TB = g.tables_smem ? S.TB : g.tBh;
+        const float dsc = ldexpf(1.f, -13 - S.misc[3]);
+        const Emitter<kCollect> emit{g, S, top, thr, dbg};
+        for (int c = 0; c < g.nchunk; ++c) {
+            const int t0 = 1 + c * g.TC;
+            stage_a<H, W>(g, S, t0, TA);
+            if (W % 32 == 0 && g.tables_smem) stage_b_mma<W, kCollect>(g, S, t0, TB, dsc, emit);
+            else stage_b_simt<kCollect>(g, S, t0, TB, dsc, emit);
+            // the t = 0 row: S = 0, the surface is g(tx)
+            if (t0 == 1) {
+                for (int x = threadIdx.x; x <= g.h0; x += blockDim.x) {
+                    if (x <= g.pmax) emit(S.gP[x], 0, x);
+                    if (x >= 1) emit(S.gM[x], 0, -x);
+                }
+            }
+            __syncthreads();
+        }
     }
 }
 
 // Second surface pass that lists every point with v >= thr (S.cj/S.cv, count returned).
-template <int H, int W>
+template <int H, int W, bool kTcOnly = false>
 static __device__ int collect_near(const Geom& g, const Smem& S, float thr) {
     TopK<kTopK> unused;
     unused.init();
     if (threadIdx.x == 0) S.misc[1] = 0;
     __syncthreads();
-    upsampled_pass<H, W, true>(g, S, unused, thr, nullptr);
+    upsampled_pass<H, W, true, kTcOnly>(g, S, unused, thr, nullptr);
     const int nc = S.misc[1];
     __syncthreads();
     return nc;
@@ -2096,7 +2102,7 @@ __device__ __forceinline__ bool tc_failed(const Geom& g, const Batch& b, long lo
 // a1-a7 for one frame (rows b.pitch elements apart) against the reference of g; the record
 // goes to b.out[f], and f indexes the optional debug outputs of b. Returns false when the
 // stage tables never arrived (the record says so; the CTA must stop).
-template <int H, int W>
+template <int H, int W, bool kTcOnly = false>
 __device__ __forceinline__ bool track_frame(const Geom& g, const Batch& b, const Smem& S, long long f,
                                             const char* frame, unsigned& bar_parity) {
     unsigned flags = 0;
@@ -2144,7 +2150,7 @@ __device__ __forceinline__ bool track_frame(const Geom& g, const Batch& b, const
     float* dbg = b.dbg_sub ? b.dbg_sub + (size_t)f * g.M * g.M : nullptr;
     // no point below the (0, 0) point's value minus the near-tie band can matter
     const float lb = g.sense * S.gP[0] - g.tau0 * scale;
-    upsampled_pass<H, W, false>(g, S, top, lb, dbg);
+    upsampled_pass<H, W, false, kTcOnly>(g, S, top, lb, dbg);
     if (tc_failed<H, W>(g, b, f, flags)) return false;
     float vw = top.v[0];
     int jw = top.j[0];
@@ -2182,7 +2188,7 @@ __device__ __forceinline__ bool track_frame(const Geom& g, const Batch& b, const
                 __syncthreads();
             } else {
                 // a thread holds more near-ties than it kept: collect them all with a second pass
-                nc = collect_near<H, W>(g, S, thr);
+                nc = collect_near<H, W, kTcOnly>(g, S, thr);
                 if (tc_failed<H, W>(g, b, f, flags)) return false;
                 if (nc > kMaxCand) {
                     flags |= 0x08u;
@@ -2229,7 +2235,7 @@ __device__ __forceinline__ bool track_frame(const Geom& g, const Batch& b, const
 __host__ __device__ constexpr int track_threads(int H, int W) { return (H <= 64 && W <= 64) ? 256 : kThreads; }
 __host__ __device__ constexpr int track_min_ctas(int H, int W) { return (H <= 64 && W <= 64) ? 2 : 1; }
 
-template <int H, int W>
+template <int H, int W, bool kTcOnly = false>
 __global__ void __launch_bounds__(track_threads(H, W), track_min_ctas(H, W)) track_kernel(Geom g, Batch b) {
     const Smem S = carve(g, ccst_smem);
     track_setup<H, W>(g, S);
@@ -2251,7 +2257,7 @@ __global__ void __launch_bounds__(track_threads(H, W), track_min_ctas(H, W)) tra
     };
     for (long long f = fetch(-1); f < b.n; f = fetch(f)) {
         const char* frame = (const char*)b.frames + (size_t)f * g.H * b.pitch * elem;
-        if (!track_frame<H, W>(g, b, S, f, frame, bar_parity)) break;
+        if (!track_frame<H, W, kTcOnly>(g, b, S, f, frame, bar_parity)) break;
     }
     if constexpr (H == 128 && W == 128) {
         if (g.tc) tc_teardown();                    // every exit path releases the columns
@@ -2269,6 +2275,7 @@ const void* track_kernel_h16(int W);
 const void* track_kernel_h32(int W);
 const void* track_kernel_h64(int W);
 const void* track_kernel_h128(int W);
+const void* track_kernel_128_tc();      // track_kernel<128, 128, true>
 inline const void* track_kernel_for(int H, int W) {
     switch (H) {
         case 8: return track_kernel_h8(W);

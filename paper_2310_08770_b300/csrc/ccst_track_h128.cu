@@ -8,6 +8,7 @@ template __global__ void track_kernel<128, 16>(Geom, Batch);
 template __global__ void track_kernel<128, 32>(Geom, Batch);
 template __global__ void track_kernel<128, 64>(Geom, Batch);
 template __global__ void track_kernel<128, 128>(Geom, Batch);
+template __global__ void track_kernel<128, 128, true>(Geom, Batch);
 
 const void* track_kernel_h128(int W) {
     switch (W) {
@@ -19,5 +20,7 @@ const void* track_kernel_h128(int W) {
         default: return nullptr;
     }
 }
+
+const void* track_kernel_128_tc() { return (const void*)track_kernel<128, 128, true>; }
 
 }  // namespace ccst
