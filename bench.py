@@ -44,7 +44,7 @@ MAX_SM_MHZ = 2032.0
 PROFILE_FILE = os.path.join(ROOT, "profiles", "track_kernel_128x128_u100.txt")
 KERNEL_SOURCES = ["paper_2310_08770_b300/csrc/ccst_kernels.cuh", "paper_2310_08770_b300/csrc/ccst_device.cuh",
                   "paper_2310_08770_b300/csrc/ccst_dfloat.cuh", "paper_2310_08770_b300/csrc/ccst_fft.cuh",
-                  "paper_2310_08770_b300/csrc/ccst_tc.cuh"]
+                  "paper_2310_08770_b300/csrc/ccst_tc.cuh", "paper_2310_08770_b300/csrc/ccst_track_h128.cu"]
 
 
 def grid_size(u):
