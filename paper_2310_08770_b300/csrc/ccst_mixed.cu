@@ -85,7 +85,7 @@ struct MixSh {
     float2 *t4h, *t4r, *rtw, *phH, *phW, *R;
     float *gP, *gM, *gpart;
     int *pslot, *qslot;
-    float *rv, *rs, *xf, *cv, *cd, *gv;
+    float *rv, *rs, *xf, *cv, *cd;
     int *rj, *xi, *misc, *cj, *gj;
 };
 
@@ -98,7 +98,7 @@ __host__ __device__ inline size_t mix_small_bytes(const MixPlan& p) {
          mal(sizeof(float2) * p.H) + mal(sizeof(float2) * p.W) + mal(sizeof(float2) * p.KB);
     s += 4 * mal(sizeof(float) * p.TX);
     s += 2 * mal(sizeof(int) * p.Hh);
-    s += 3 * mal(sizeof(float) * 32) + mal(sizeof(float) * 32) + 3 * mal(sizeof(float) * kMaxCand);
+    s += 3 * mal(sizeof(float) * 32) + 2 * mal(sizeof(float) * kMaxCand);
     s += mal(sizeof(int) * 32) + mal(sizeof(int) * 32) + mal(sizeof(int) * 16) + 2 * mal(sizeof(int) * kMaxCand);
     return s;
 }
@@ -132,10 +132,8 @@ __host__ __device__ inline MixSh mix_carve(const MixPlan& p, unsigned char* base
     s.rv = (float*)take(sizeof(float) * 32);
     s.rs = (float*)take(sizeof(float) * 32);
     s.xf = (float*)take(sizeof(float) * 32);
-    s.gv = (float*)take(sizeof(float) * 32);
     s.cv = (float*)take(sizeof(float) * kMaxCand);
     s.cd = (float*)take(sizeof(float) * kMaxCand);
-    (void)take(sizeof(float) * kMaxCand);
     s.rj = (int*)take(sizeof(int) * 32);
     s.xi = (int*)take(sizeof(int) * 32);
     s.misc = (int*)take(sizeof(int) * 16);
