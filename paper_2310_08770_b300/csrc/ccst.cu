@@ -629,6 +629,11 @@ struct GenLane {
     GenItem* d_fb = nullptr;        // the FP32 kernel's fallback list
     size_t fb_cap = 0;
     unsigned* d_mixc = nullptr;     // kMixCounters counters of the FP32 kernel's launches
+    // auxiliary streams on which the FP32 launches of further sides run beside the first,
+    // forked from and joined back to the launching stream
+    cudaStream_t aux[kMixCounters - 2] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[kMixCounters - 2] = {};
 };
 
 static void lane_free(GenLane& l) {
@@ -636,6 +641,11 @@ static void lane_free(GenLane& l) {
     if (l.d_items) cudaFree(l.d_items);
     if (l.d_fb) cudaFree(l.d_fb);
     if (l.d_mixc) cudaFree(l.d_mixc);
+    for (auto& st : l.aux)
+        if (st) cudaStreamDestroy(st);
+    for (auto& ev : l.ev_join)
+        if (ev) cudaEventDestroy(ev);
+    if (l.ev_fork) cudaEventDestroy(l.ev_fork);
     l = GenLane{};
 }
 
@@ -754,6 +764,10 @@ struct ccst_ctx {
     int rois_grid = 0;
     size_t rois_smem_small = 0;       // ROI kernel for the classes up to 64 x 64
     int rois_grid_small = 0;
+    // the small-class ROI kernel runs beside the 128 x 128 one on this stream, forked from
+    // and joined back to the context's stream (direct and graph-captured ROI batches)
+    cudaStream_t rs_aux = nullptr;
+    cudaEvent_t rs_fork = nullptr, rs_join = nullptr;
     void* d_addref_tmp = nullptr;     // ccst_add_reference: reference copy and FFT workspace
     size_t addref_tmp_bytes = 0;
     // graphs keyed by (stream, frames, n, pitch, out). Each owns a profiling event pair, a
@@ -936,6 +950,9 @@ static void free_all(ccst_ctx* c) {
     c->refs.clear();
     c->gplans.clear();
     if (c->gstream) cudaStreamDestroy(c->gstream);
+    if (c->rs_aux) cudaStreamDestroy(c->rs_aux);
+    if (c->rs_fork) cudaEventDestroy(c->rs_fork);
+    if (c->rs_join) cudaEventDestroy(c->rs_join);
     if (c->gfork) cudaEventDestroy(c->gfork);
     if (c->gjoin) cudaEventDestroy(c->gjoin);
     if (c->shared_ev) cudaEventDestroy(c->shared_ev);
@@ -2193,6 +2210,11 @@ static int rois_upload(ccst_ctx* c) {
     int limit = 0, occ = 0, sms = 0;
     CK(c, cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    if (!c->rs_aux) {
+        CK(c, cudaStreamCreateWithFlags(&c->rs_aux, cudaStreamNonBlocking));
+        CK(c, cudaEventCreateWithFlags(&c->rs_fork, cudaEventDisableTiming));
+        CK(c, cudaEventCreateWithFlags(&c->rs_join, cudaEventDisableTiming));
+    }
     for (int small = 0; small < 2; ++small) {
         const void* k = track_rois_kernel_ptr(small != 0);
         CK(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, limit - kRoisStaticSmem));
@@ -2410,6 +2432,13 @@ static int mix_reserve(ccst_ctx* c, GenLane& lane, long long n, bool* grew) {
         CK(c, cudaMalloc(&lane.d_mixc, kMixCounters * sizeof(unsigned)));
         *grew = true;
     }
+    if (!lane.ev_fork) {
+        CK(c, cudaEventCreateWithFlags(&lane.ev_fork, cudaEventDisableTiming));
+        for (int k = 0; k < kMixCounters - 2; ++k) {
+            CK(c, cudaStreamCreateWithFlags(&lane.aux[k], cudaStreamNonBlocking));
+            CK(c, cudaEventCreateWithFlags(&lane.ev_join[k], cudaEventDisableTiming));
+        }
+    }
     if (lane.fb_cap < (size_t)n) {
         if (lane.d_fb) cudaFree(lane.d_fb);
         lane.d_fb = nullptr;
@@ -2440,7 +2469,7 @@ static bool any_mix_plan(ccst_ctx* c) {
 static int gen_kernel_launch(ccst_ctx* c, GenBatch gb, GenLane& lane, long long stride, cudaStream_t stream,
                              unsigned* counter, const GenItem* items_host, const MixDbg* dbg = nullptr) {
     struct Seg { long long first, n; int plan; };
-    Seg segs[kMixCounters - 1];
+    Seg segs[kMixCounters - 2];
     int ns = 0;
     long long ndirect = gb.n;
     if (!gb.items) {
@@ -2452,7 +2481,7 @@ static int gen_kernel_launch(ccst_ctx* c, GenBatch gb, GenLane& lane, long long 
         long long i = 0;
         while (i < gb.n && !plan_mix(c, items_host[i].plan)) ++i;
         ndirect = i;
-        while (i < gb.n && ns < kMixCounters - 1) {
+        while (i < gb.n && ns < kMixCounters - 2) {
             long long j = i;
             while (j < gb.n && items_host[j].plan == items_host[i].plan) ++j;
             segs[ns++] = Seg{i, j - i, items_host[i].plan};
@@ -2464,9 +2493,22 @@ static int gen_kernel_launch(ccst_ctx* c, GenBatch gb, GenLane& lane, long long 
     gb.fb_items = nullptr;
     gb.fb_count = nullptr;
     if (ns > 0) {
-        if (!lane.d_mixc || lane.fb_cap < (size_t)(ntot - ndirect))
+        if (!lane.d_mixc || !lane.ev_fork || lane.fb_cap < (size_t)(ntot - ndirect))
             return fail(c, CCST_E_INVALID, "general-size batch: FP32 lane state not reserved");
         CK(c, cudaMemsetAsync(lane.d_mixc, 0, (size_t)(1 + ns) * sizeof(unsigned), stream));
+        // the first side on `stream`, the others beside it on the lane's auxiliary streams,
+        // when some side leaves SMs free (fewer items than resident CTAs, as in a served
+        // batch); sides that each fill the GPU run one after the other
+        bool fan = false;
+        for (int k = 0; k < ns; ++k) {
+            const ccst_ctx::GenPlanH& gp = c->gplans[segs[k].plan];
+            if (segs[k].n * gp.mp.CL < gp.mix_grid) fan = true;
+        }
+        fan = fan && ns > 1;
+        if (fan) {
+            CK(c, cudaEventRecord(lane.ev_fork, stream));
+            for (int k = 1; k < ns; ++k) CK(c, cudaStreamWaitEvent(lane.aux[k - 1], lane.ev_fork, 0));
+        }
         for (int k = 0; k < ns; ++k) {
             const ccst_ctx::GenPlanH& gp = c->gplans[segs[k].plan];
             MixArgs ma{};
@@ -2495,7 +2537,12 @@ static int gen_kernel_launch(ccst_ctx* c, GenBatch gb, GenLane& lane, long long 
             const int grid = (int)(want < gp.mix_grid ? want : gp.mix_grid) / cl * cl;
             void* margs[] = {&ma};
             CK(c, cudaLaunchKernel(mix_kernel_ptr(gp.mp.H, gp.mp.W), dim3(grid), dim3((unsigned)gp.mp.NT), margs,
-                                   (size_t)gp.mp.smem, stream));
+                                   (size_t)gp.mp.smem, (k == 0 || !fan) ? stream : lane.aux[k - 1]));
+        }
+        // the fallback launch reads the count every side may have added to
+        for (int k = 1; k < ns && fan; ++k) {
+            CK(c, cudaEventRecord(lane.ev_join[k - 1], lane.aux[k - 1]));
+            CK(c, cudaStreamWaitEvent(stream, lane.ev_join[k - 1], 0));
         }
         gb.fb_items = lane.d_fb;
         gb.fb_count = lane.d_mixc;
@@ -2785,12 +2832,27 @@ static int64_t rois_big_items(ccst_ctx* c, const RoiItem* items, int64_t n) {
     return k;
 }
 
+// Auxiliary stream and fork/join events for the small-class ROI kernel of one launch site.
+struct RoiFork {
+    cudaStream_t aux;
+    cudaEvent_t fork, join;
+};
+
 // The ROI kernels over n items already on the device, the first nbig of them 128 x 128
 // (ordered by rois_sort): counter reset, then the 512-thread kernel over those and the
 // small-class kernel over the rest, each with its own counter (counter[0], counter[1]).
+// When both have items and one of them has fewer than its resident CTAs (a launch that
+// leaves SMs free, as in a served batch), the small-class kernel runs on f.aux beside the
+// other. Two launches that each fill the GPU run one after the other: side by side they
+// pack worse (a 128 x 128 CTA needs a whole SM).
 static int rois_kernel_launch(ccst_ctx* c, const RoiItem* items_dev, int64_t n, int64_t nbig, Result* out,
-                              cudaStream_t stream, unsigned* counter) {
+                              cudaStream_t stream, unsigned* counter, const RoiFork& f) {
     CK(c, cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned), stream));
+    const bool both = nbig > 0 && n > nbig && (nbig < c->rois_grid || n - nbig < c->rois_grid_small);
+    if (both) {
+        CK(c, cudaEventRecord(f.fork, stream));
+        CK(c, cudaStreamWaitEvent(f.aux, f.fork, 0));
+    }
     for (int small = 0; small < 2; ++small) {
         const int64_t m = small ? n - nbig : nbig;
         if (m == 0) continue;
@@ -2806,18 +2868,22 @@ static int rois_kernel_launch(ccst_ctx* c, const RoiItem* items_dev, int64_t n, 
         void* args[] = {&rb};
         CK(c, cudaLaunchKernel(track_rois_kernel_ptr(small != 0), dim3(grid),
                                dim3(small ? track_threads(64, 64) : kThreads), args,
-                               small ? c->rois_smem_small : c->rois_smem, stream));
+                               small ? c->rois_smem_small : c->rois_smem, (small && both) ? f.aux : stream));
+    }
+    if (both) {
+        CK(c, cudaEventRecord(f.join, f.aux));
+        CK(c, cudaStreamWaitEvent(stream, f.join, 0));
     }
     return CCST_OK;
 }
 
 static int rois_launch(ccst_ctx* c, RoiItem* items, int64_t n, Result* out, cudaStream_t stream, RoiItem* items_dev,
-                       unsigned* counter) {
+                       unsigned* counter, const RoiFork& f) {
     rois_sort(c, items, n);
     int rc = rois_upload(c);
     if (rc) return rc;
     CK(c, cudaMemcpyAsync(items_dev, items, (size_t)n * sizeof(RoiItem), cudaMemcpyHostToDevice, stream));
-    return rois_kernel_launch(c, items_dev, n, rois_big_items(c, items, n), out, stream, counter);
+    return rois_kernel_launch(c, items_dev, n, rois_big_items(c, items, n), out, stream, counter, f);
 }
 
 constexpr size_t kMaxRoiGraphs = 64;
@@ -2916,7 +2982,7 @@ static int rois_graph_track(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccst_r
         }
         if (!lrc && np > 0)
             lrc = rois_kernel_launch(c, e.d_items, np, rois_big_items(c, c->h_items.data(), np), (Result*)out_dev,
-                                     c->stream, e.counters);
+                                     c->stream, e.counters, RoiFork{c->rs_aux, c->rs_fork, c->rs_join});
         if (!lrc && ng > 0 && cudaStreamWaitEvent(c->stream, c->gjoin, 0) != cudaSuccess)
             lrc = fail(c, CCST_E_CUDA, "ccst_track_rois: join during capture");
         err = cudaStreamEndCapture(c->stream, &graph);
@@ -3001,7 +3067,9 @@ extern "C" int ccst_track_rois(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccs
             CK(c, cudaMalloc(&c->d_items, (size_t)n * sizeof(RoiItem)));
             c->items_cap = (size_t)n;
         }
-        if ((rc = rois_launch(c, c->h_items.data(), n, (Result*)out_dev, c->stream, c->d_items, c->d_next + 16)))
+        if ((rc = rois_upload(c))) return rc;       // also makes the fork stream and events
+        if ((rc = rois_launch(c, c->h_items.data(), n, (Result*)out_dev, c->stream, c->d_items, c->d_next + 16,
+                              RoiFork{c->rs_aux, c->rs_fork, c->rs_join})))
             return rc;
     }
     if (ng > 0) CK(c, cudaStreamWaitEvent(c->stream, c->gjoin, 0));     // both batches done
@@ -3035,6 +3103,13 @@ struct ccst_server {
     struct InFlight {
         cudaStream_t st = nullptr;
         cudaEvent_t ev = nullptr;
+        // the general-size part of a batch runs on st_gen beside the power-of-two part,
+        // forked from and joined back to st
+        cudaStream_t st_gen = nullptr;
+        cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+        // the small-class ROI kernel beside the 128 x 128 one
+        cudaStream_t st_small = nullptr;
+        cudaEvent_t ev_sfork = nullptr, ev_sjoin = nullptr;
         Result* d_out = nullptr;
         Result* h_out = nullptr;
         RoiItem* d_items = nullptr;
@@ -3198,13 +3273,25 @@ static void server_loop(ccst_server* s) {
         }
         // each kernel writes record i of the batch to d_out[i]; out_index survives the sorts
         bool ok = true;
-        if (np > 0) ok = rois_launch(c, b.h_items, np, b.d_out, b.st, b.d_items, s->d_counters + 3 * next) == CCST_OK;
+        const bool both = np > 0 && ng > 0;
+        if (both) {
+            ok = cudaEventRecord(b.ev_fork, b.st) == cudaSuccess &&
+                 cudaStreamWaitEvent(b.st_gen, b.ev_fork, 0) == cudaSuccess;
+        }
+        if (ok && np > 0)
+            ok = rois_launch(c, b.h_items, np, b.d_out, b.st, b.d_items, s->d_counters + 3 * next,
+                             RoiFork{b.st_small, b.ev_sfork, b.ev_sjoin}) == CCST_OK;
         if (ok && ng > 0) {
             gen_sort(c, b.h_gitems, ng);
             GenBatch gb{};
             gb.n = ng;
             gb.out = b.d_out;
-            ok = gen_launch(c, b.lane, gb, b.h_gitems, b.st, s->d_counters + 3 * next + 2) == CCST_OK;
+            ok = gen_launch(c, b.lane, gb, b.h_gitems, both ? b.st_gen : b.st, s->d_counters + 3 * next + 2) ==
+                 CCST_OK;
+        }
+        if (ok && both) {
+            ok = cudaEventRecord(b.ev_join, b.st_gen) == cudaSuccess &&
+                 cudaStreamWaitEvent(b.st, b.ev_join, 0) == cudaSuccess;
         }
         ok = ok && cudaMemcpyAsync(b.h_out, b.d_out, (size_t)m * sizeof(Result), cudaMemcpyDeviceToHost, b.st) ==
                        cudaSuccess;
@@ -3227,8 +3314,16 @@ static void server_loop(ccst_server* s) {
 static void server_free(ccst_server* s) {
     for (auto& b : s->ring) {
         if (b.st) cudaStreamSynchronize(b.st);
+        if (b.st_gen) cudaStreamSynchronize(b.st_gen);
+        if (b.st_small) cudaStreamSynchronize(b.st_small);
+        if (b.st_small) cudaStreamDestroy(b.st_small);
+        if (b.ev_sfork) cudaEventDestroy(b.ev_sfork);
+        if (b.ev_sjoin) cudaEventDestroy(b.ev_sjoin);
         if (b.ev) cudaEventDestroy(b.ev);
+        if (b.ev_fork) cudaEventDestroy(b.ev_fork);
+        if (b.ev_join) cudaEventDestroy(b.ev_join);
         if (b.st) cudaStreamDestroy(b.st);
+        if (b.st_gen) cudaStreamDestroy(b.st_gen);
         if (b.d_out) cudaFree(b.d_out);
         if (b.h_out) cudaFreeHost(b.h_out);
         if (b.d_items) cudaFree(b.d_items);
@@ -3285,6 +3380,12 @@ extern "C" int ccst_server_create_ex(ccst_ctx* c, const ccst_server_config* cfg,
         auto& b = s->ring[k];
         if ((e = cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking)) != cudaSuccess) return bad(e);
         if ((e = cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming)) != cudaSuccess) return bad(e);
+        if ((e = cudaStreamCreateWithFlags(&b.st_gen, cudaStreamNonBlocking)) != cudaSuccess) return bad(e);
+        if ((e = cudaEventCreateWithFlags(&b.ev_fork, cudaEventDisableTiming)) != cudaSuccess) return bad(e);
+        if ((e = cudaEventCreateWithFlags(&b.ev_join, cudaEventDisableTiming)) != cudaSuccess) return bad(e);
+        if ((e = cudaStreamCreateWithFlags(&b.st_small, cudaStreamNonBlocking)) != cudaSuccess) return bad(e);
+        if ((e = cudaEventCreateWithFlags(&b.ev_sfork, cudaEventDisableTiming)) != cudaSuccess) return bad(e);
+        if ((e = cudaEventCreateWithFlags(&b.ev_sjoin, cudaEventDisableTiming)) != cudaSuccess) return bad(e);
         if ((e = cudaMalloc(&b.d_out, (size_t)s->max_batch * sizeof(Result))) != cudaSuccess) return bad(e);
         if ((e = cudaHostAlloc(&b.h_out, (size_t)s->max_batch * sizeof(Result), cudaHostAllocDefault)) != cudaSuccess)
             return bad(e);
