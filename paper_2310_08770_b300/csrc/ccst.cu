@@ -629,11 +629,6 @@ struct GenLane {
     GenItem* d_fb = nullptr;        // the FP32 kernel's fallback list
     size_t fb_cap = 0;
     unsigned* d_mixc = nullptr;     // kMixCounters counters of the FP32 kernel's launches
-    // auxiliary streams on which the FP32 launches of further sides run beside the first,
-    // forked from and joined back to the launching stream
-    cudaStream_t aux[kMixCounters - 2] = {};
-    cudaEvent_t ev_fork = nullptr;
-    cudaEvent_t ev_join[kMixCounters - 2] = {};
 };
 
 static void lane_free(GenLane& l) {
@@ -641,12 +636,30 @@ static void lane_free(GenLane& l) {
     if (l.d_items) cudaFree(l.d_items);
     if (l.d_fb) cudaFree(l.d_fb);
     if (l.d_mixc) cudaFree(l.d_mixc);
-    for (auto& st : l.aux)
-        if (st) cudaStreamDestroy(st);
-    for (auto& ev : l.ev_join)
-        if (ev) cudaEventDestroy(ev);
-    if (l.ev_fork) cudaEventDestroy(l.ev_fork);
     l = GenLane{};
+}
+
+// A second stream with its fork and join events, made on first use: the general-size part
+// of an uneven-ROI batch runs on it beside the power-of-two part.
+struct SideStream {
+    cudaStream_t st = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+static cudaError_t side_make(SideStream& s) {
+    cudaError_t e = cudaSuccess;
+    if (!s.st && (e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if (!s.fork && (e = cudaEventCreateWithFlags(&s.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+    if (!s.join && (e = cudaEventCreateWithFlags(&s.join, cudaEventDisableTiming)) != cudaSuccess) return e;
+    return e;
+}
+
+static void side_free(SideStream& s) {
+    if (s.st) cudaStreamSynchronize(s.st);
+    if (s.st) cudaStreamDestroy(s.st);
+    if (s.fork) cudaEventDestroy(s.fork);
+    if (s.join) cudaEventDestroy(s.join);
+    s = SideStream{};
 }
 
 struct ccst_ctx {
@@ -731,8 +744,6 @@ struct ccst_ctx {
     // lane 0: ccst_track and ccst_track_rois (ordered through the context's stream);
     // lanes 1 and 2: the two streams of the pipelined host path
     GenLane glane[3];
-    cudaStream_t gstream = nullptr;   // ROI batches run their general sizes here, beside the main kernel
-    cudaEvent_t gfork = nullptr, gjoin = nullptr;
     int gen_grid = 0;
     int gen_threads = 512;            // CTA size of the general-size kernel (ccst_autotune may lower it)
     bool gen_dirty = true;            // plans or references changed since the last upload
@@ -759,15 +770,14 @@ struct ccst_ctx {
     std::map<std::tuple<cudaStream_t, void*, int64_t, uint64_t>, RoiGraph> roi_graphs;
     std::map<cudaStream_t, GenLane> roi_lanes;
     int64_t roi_graph_instantiations = 0, roi_graph_replays = 0;
+    SideStream rside;                 // ROI batches' general-size part (direct and captured)
     bool rois_dirty = true;
     size_t rois_smem = 0;             // ROI kernel for the 128 x 128 class
     int rois_grid = 0;
+    int rois_big_cls = 1;             // its instantiation: 2 if the class's plan uses tcgen05, else 1
+    Geom rois_g128{};                 // the class's geometry, a parameter of that kernel
     size_t rois_smem_small = 0;       // ROI kernel for the classes up to 64 x 64
     int rois_grid_small = 0;
-    // the small-class ROI kernel runs beside the 128 x 128 one on this stream, forked from
-    // and joined back to the context's stream (direct and graph-captured ROI batches)
-    cudaStream_t rs_aux = nullptr;
-    cudaEvent_t rs_fork = nullptr, rs_join = nullptr;
     void* d_addref_tmp = nullptr;     // ccst_add_reference: reference copy and FFT workspace
     size_t addref_tmp_bytes = 0;
     // graphs keyed by (stream, frames, n, pitch, out). Each owns a profiling event pair, a
@@ -923,6 +933,7 @@ static void free_all(ccst_ctx* c) {
     drop_roi_graphs(c);
     for (auto& kv : c->roi_lanes) lane_free(kv.second);
     c->roi_lanes.clear();
+    side_free(c->rside);
     for (size_t i = 0; i < c->prof0.size(); ++i) {
         cudaEventDestroy(c->prof0[i]);
         cudaEventDestroy(c->prof1[i]);
@@ -949,12 +960,6 @@ static void free_all(ccst_ctx* c) {
     c->plans.clear();
     c->refs.clear();
     c->gplans.clear();
-    if (c->gstream) cudaStreamDestroy(c->gstream);
-    if (c->rs_aux) cudaStreamDestroy(c->rs_aux);
-    if (c->rs_fork) cudaEventDestroy(c->rs_fork);
-    if (c->rs_join) cudaEventDestroy(c->rs_join);
-    if (c->gfork) cudaEventDestroy(c->gfork);
-    if (c->gjoin) cudaEventDestroy(c->gjoin);
     if (c->shared_ev) cudaEventDestroy(c->shared_ev);
     void* ptrs[] = {c->d_ref32, c->d_b64, c->d_FE64, c->d_FE32, c->d_tw64, c->d_tw32,
                     c->d_tab,   c->d_df,  c->d_frames, c->d_out, c->d_next, c->d_rtE, c->d_rtY, c->d_rtSync,
@@ -2197,11 +2202,17 @@ static int rois_upload(ccst_ctx* c) {
     }
     std::vector<Geom> gs;
     size_t smem = 0, smem_small = 0;
+    int big_cls = 1;
     for (auto& pl : c->plans) {
         gs.push_back(pl.g);
         if (!rois_size_ok(pl.g.H, pl.g.W)) continue;
-        if (pl.g.H <= 64) smem_small = std::max(smem_small, smem_plan(pl.g).total);
-        else smem = std::max(smem, smem_plan(pl.g).total);
+        if (pl.g.H <= 64) {
+            smem_small = std::max(smem_small, smem_plan(pl.g).total);
+        } else {
+            smem = std::max(smem, smem_plan(pl.g).total);
+            big_cls = pl.g.tc ? 2 : 1;                  // one 128 x 128 class per context
+            c->rois_g128 = pl.g;
+        }
     }
     std::vector<RefSpectra> rs;
     for (auto& re : c->refs) rs.push_back(re.r);
@@ -2210,13 +2221,8 @@ static int rois_upload(ccst_ctx* c) {
     int limit = 0, occ = 0, sms = 0;
     CK(c, cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-    if (!c->rs_aux) {
-        CK(c, cudaStreamCreateWithFlags(&c->rs_aux, cudaStreamNonBlocking));
-        CK(c, cudaEventCreateWithFlags(&c->rs_fork, cudaEventDisableTiming));
-        CK(c, cudaEventCreateWithFlags(&c->rs_join, cudaEventDisableTiming));
-    }
     for (int small = 0; small < 2; ++small) {
-        const void* k = track_rois_kernel_ptr(small != 0);
+        const void* k = track_rois_kernel_ptr(small ? 0 : big_cls);
         CK(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, limit - kRoisStaticSmem));
         CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, small ? track_threads(64, 64) : kThreads,
                                                              small ? smem_small : smem));
@@ -2224,6 +2230,7 @@ static int rois_upload(ccst_ctx* c) {
         (small ? c->rois_grid_small : c->rois_grid) = occ * sms;
     }
     c->rois_smem = smem;
+    c->rois_big_cls = big_cls;
     c->rois_smem_small = smem_small;
     c->rois_dirty = false;
     return CCST_OK;
@@ -2432,13 +2439,6 @@ static int mix_reserve(ccst_ctx* c, GenLane& lane, long long n, bool* grew) {
         CK(c, cudaMalloc(&lane.d_mixc, kMixCounters * sizeof(unsigned)));
         *grew = true;
     }
-    if (!lane.ev_fork) {
-        CK(c, cudaEventCreateWithFlags(&lane.ev_fork, cudaEventDisableTiming));
-        for (int k = 0; k < kMixCounters - 2; ++k) {
-            CK(c, cudaStreamCreateWithFlags(&lane.aux[k], cudaStreamNonBlocking));
-            CK(c, cudaEventCreateWithFlags(&lane.ev_join[k], cudaEventDisableTiming));
-        }
-    }
     if (lane.fb_cap < (size_t)n) {
         if (lane.d_fb) cudaFree(lane.d_fb);
         lane.d_fb = nullptr;
@@ -2460,96 +2460,119 @@ static bool any_mix_plan(ccst_ctx* c) {
     return false;
 }
 
-// The general-size launches over gb.n frames on `stream` (gb.items already on the device,
-// ordered by gen_sort, with `items_host` its host copy; or null for a uniform batch).
-// Items whose plan has the FP32 kernel come last, equal plans together: each such run is
-// one FP32 launch, and the frames it cannot certify join a fallback list. Then the double-
-// float kernel, with per-CTA scratch of `stride` elements, takes the other items and the
-// fallback list. dbg: the FP32 kernel's diagnostic outputs (uniform batches).
-static int gen_kernel_launch(ccst_ctx* c, GenBatch gb, GenLane& lane, long long stride, cudaStream_t stream,
-                             unsigned* counter, const GenItem* items_host, const MixDbg* dbg = nullptr) {
-    struct Seg { long long first, n; int plan; };
-    Seg segs[kMixCounters - 2];
+// A kernel launch on `stream`; with `chained`, by programmatic dependent launch behind the
+// kernel launched just before it on that stream: it may start once every CTA of that kernel
+// has taken its last item (pdl_trigger), and it calls pdl_wait before it exits.
+static cudaError_t launch_kernel(const void* k, int grid, int block, void** args, size_t smem, cudaStream_t stream,
+                                 bool chained) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = chained ? at : nullptr;
+    cfg.numAttrs = chained ? 1 : 0;
+    return cudaLaunchKernelExC(&cfg, k, args);
+}
+
+// The general-size part of a batch (gb.items already on the device, ordered by gen_sort,
+// with `items_host` its host copy; or null for a uniform batch): items whose plan has the
+// FP32 kernel come last, equal plans together, and each such run is one FP32 launch (a
+// segment); the frames it cannot certify join a fallback list. The double-float kernel then
+// takes the other items (the first `ndirect`) and the fallback list.
+struct MixSeg { long long first, n; int plan; };
+struct GenSplit {
+    MixSeg segs[kMixCounters - 2];
     int ns = 0;
-    long long ndirect = gb.n;
+    long long ndirect = 0;
+};
+
+static int gen_split_items(ccst_ctx* c, const GenBatch& gb, const GenItem* items_host, const GenLane& lane,
+                           GenSplit* sp) {
+    sp->ns = 0;
+    sp->ndirect = gb.n;
     if (!gb.items) {
         if (plan_mix(c, gb.plan)) {
-            segs[ns++] = Seg{0, gb.n, gb.plan};
-            ndirect = 0;
+            sp->segs[sp->ns++] = MixSeg{0, gb.n, gb.plan};
+            sp->ndirect = 0;
         }
     } else if (items_host) {
         long long i = 0;
         while (i < gb.n && !plan_mix(c, items_host[i].plan)) ++i;
-        ndirect = i;
-        while (i < gb.n && ns < kMixCounters - 2) {
+        sp->ndirect = i;
+        while (i < gb.n && sp->ns < kMixCounters - 2) {
             long long j = i;
             while (j < gb.n && items_host[j].plan == items_host[i].plan) ++j;
-            segs[ns++] = Seg{i, j - i, items_host[i].plan};
+            sp->segs[sp->ns++] = MixSeg{i, j - i, items_host[i].plan};
             i = j;
         }
         if (i < gb.n) return fail(c, CCST_E_INVALID, "general-size batch: too many FP32 plans in one batch");
     }
-    const long long ntot = gb.n;
-    gb.fb_items = nullptr;
-    gb.fb_count = nullptr;
-    if (ns > 0) {
-        if (!lane.d_mixc || !lane.ev_fork || lane.fb_cap < (size_t)(ntot - ndirect))
-            return fail(c, CCST_E_INVALID, "general-size batch: FP32 lane state not reserved");
-        CK(c, cudaMemsetAsync(lane.d_mixc, 0, (size_t)(1 + ns) * sizeof(unsigned), stream));
-        // the first side on `stream`, the others beside it on the lane's auxiliary streams,
-        // when some side leaves SMs free (fewer items than resident CTAs, as in a served
-        // batch); sides that each fill the GPU run one after the other
-        bool fan = false;
-        for (int k = 0; k < ns; ++k) {
-            const ccst_ctx::GenPlanH& gp = c->gplans[segs[k].plan];
-            if (segs[k].n * gp.mp.CL < gp.mix_grid) fan = true;
-        }
-        fan = fan && ns > 1;
-        if (fan) {
-            CK(c, cudaEventRecord(lane.ev_fork, stream));
-            for (int k = 1; k < ns; ++k) CK(c, cudaStreamWaitEvent(lane.aux[k - 1], lane.ev_fork, 0));
-        }
-        for (int k = 0; k < ns; ++k) {
-            const ccst_ctx::GenPlanH& gp = c->gplans[segs[k].plan];
-            MixArgs ma{};
-            ma.items = gb.items;
-            ma.first = segs[k].first;
-            ma.n = segs[k].n;
-            ma.frames = gb.frames;
-            ma.frame_bytes = gb.frame_bytes;
-            ma.pitch = gb.pitch;
-            ma.plan = gb.plan;
-            ma.ref = gb.ref;
-            ma.p = gp.mp;
-            ma.refs = c->d_grefs;
-            ma.out = gb.out;
-            ma.next = lane.d_mixc + 1 + k;
-            ma.fb = lane.d_fb;
-            ma.fb_count = lane.d_mixc;
-            if (dbg) {
-                ma.dbg_int = dbg->dbg_int;
-                ma.dbg_sub = dbg->dbg_sub;
-                ma.dbg_pairs = dbg->pairs;
-                ma.dbg_d32 = dbg->d32;
-            }
-            const int cl = gp.mp.CL;
-            const long long want = segs[k].n * cl;
-            const int grid = (int)(want < gp.mix_grid ? want : gp.mix_grid) / cl * cl;
-            void* margs[] = {&ma};
-            CK(c, cudaLaunchKernel(mix_kernel_ptr(gp.mp.H, gp.mp.W), dim3(grid), dim3((unsigned)gp.mp.NT), margs,
-                                   (size_t)gp.mp.smem, (k == 0 || !fan) ? stream : lane.aux[k - 1]));
-        }
-        // the fallback launch reads the count every side may have added to
-        for (int k = 1; k < ns && fan; ++k) {
-            CK(c, cudaEventRecord(lane.ev_join[k - 1], lane.aux[k - 1]));
-            CK(c, cudaStreamWaitEvent(stream, lane.ev_join[k - 1], 0));
-        }
-        gb.fb_items = lane.d_fb;
-        gb.fb_count = lane.d_mixc;
-    }
-    const int grid = (int)(ntot < c->gen_grid ? ntot : c->gen_grid);
-    gb.n = ndirect;
+    if (sp->ns > 0 && (!lane.d_mixc || lane.fb_cap < (size_t)(gb.n - sp->ndirect)))
+        return fail(c, CCST_E_INVALID, "general-size batch: FP32 lane state not reserved");
+    return CCST_OK;
+}
+
+// Zero the general-size part's counters: the FP32 launches' (with the fallback count) and
+// the double-float kernel's.
+static int gen_zero(ccst_ctx* c, const GenSplit& sp, const GenLane& lane, unsigned* counter, cudaStream_t stream) {
+    if (sp.ns > 0) CK(c, cudaMemsetAsync(lane.d_mixc, 0, (size_t)(1 + sp.ns) * sizeof(unsigned), stream));
     CK(c, cudaMemsetAsync(counter, 0, sizeof(unsigned), stream));
+    return CCST_OK;
+}
+
+// The FP32 launches, one per segment, each chained behind the kernel before it (*chained:
+// a chained kernel was the last launch on `stream`). dbg: diagnostic outputs (uniform
+// batches).
+static int gen_mix_launch(ccst_ctx* c, const GenBatch& gb, const GenSplit& sp, const GenLane& lane,
+                          cudaStream_t stream, bool* chained, const MixDbg* dbg = nullptr) {
+    for (int k = 0; k < sp.ns; ++k) {
+        const ccst_ctx::GenPlanH& gp = c->gplans[sp.segs[k].plan];
+        MixArgs ma{};
+        ma.items = gb.items;
+        ma.first = sp.segs[k].first;
+        ma.n = sp.segs[k].n;
+        ma.frames = gb.frames;
+        ma.frame_bytes = gb.frame_bytes;
+        ma.pitch = gb.pitch;
+        ma.plan = gb.plan;
+        ma.ref = gb.ref;
+        ma.p = gp.mp;
+        ma.refs = c->d_grefs;
+        ma.out = gb.out;
+        ma.next = lane.d_mixc + 1 + k;
+        ma.fb = lane.d_fb;
+        ma.fb_count = lane.d_mixc;
+        if (dbg) {
+            ma.dbg_int = dbg->dbg_int;
+            ma.dbg_sub = dbg->dbg_sub;
+            ma.dbg_pairs = dbg->pairs;
+            ma.dbg_d32 = dbg->d32;
+        }
+        const int cl = gp.mp.CL;
+        const long long want = sp.segs[k].n * cl;
+        const int grid = (int)(want < gp.mix_grid ? want : gp.mix_grid) / cl * cl;
+        void* margs[] = {&ma};
+        CK(c, launch_kernel(mix_kernel_ptr(gp.mp.H, gp.mp.W), grid, gp.mp.NT, margs, (size_t)gp.mp.smem, stream,
+                            *chained));
+        *chained = true;
+    }
+    return CCST_OK;
+}
+
+// The double-float kernel over the first sp.ndirect items and the fallback list, with
+// per-CTA scratch of `stride` elements: a plain launch, so it starts once everything before
+// it on `stream` has completed (the fallback list is whole).
+static int gen_direct_launch(ccst_ctx* c, GenBatch gb, const GenSplit& sp, const GenLane& lane, long long stride,
+                             unsigned* counter, cudaStream_t stream) {
+    const long long ntot = gb.n;
+    gb.fb_items = sp.ns > 0 ? lane.d_fb : nullptr;
+    gb.fb_count = sp.ns > 0 ? lane.d_mixc : nullptr;
+    const int grid = (int)(ntot < c->gen_grid ? ntot : c->gen_grid);
+    gb.n = sp.ndirect;
     gb.plans = c->d_gplans;
     gb.refs = c->d_grefs;
     gb.next = counter;
@@ -2560,6 +2583,19 @@ static int gen_kernel_launch(ccst_ctx* c, GenBatch gb, GenLane& lane, long long 
     return CCST_OK;
 }
 
+// The whole general-size part on `stream`: counters, the FP32 launches chained one behind
+// the other, then the double-float kernel.
+static int gen_kernel_launch(ccst_ctx* c, const GenBatch& gb, GenLane& lane, long long stride, cudaStream_t stream,
+                             unsigned* counter, const GenItem* items_host, const MixDbg* dbg = nullptr) {
+    GenSplit sp;
+    int rc = gen_split_items(c, gb, items_host, lane, &sp);
+    if (!rc) rc = gen_zero(c, sp, lane, counter, stream);
+    bool chained = false;
+    if (!rc) rc = gen_mix_launch(c, gb, sp, lane, stream, &chained, dbg);
+    if (!rc) rc = gen_direct_launch(c, gb, sp, lane, stride, counter, stream);
+    return rc;
+}
+
 // Per-CTA scratch stride of the general-size kernel over every plan of the context.
 static long long gen_stride(ccst_ctx* c) {
     long long stride = 0;
@@ -2567,39 +2603,52 @@ static long long gen_stride(ccst_ctx* c) {
     return stride;
 }
 
-// Launch the general-size kernel on `stream` over gb.n frames: the work list `items_host`
+// Device state of a general-size batch of gb->n frames on `lane`: the double-float kernel's
+// scratch, the work list `items_host` (copied to the lane on `stream`; the caller orders it;
+// gb->items is set to the copy) and the FP32 kernel's counters and fallback list.
+// *stride: the scratch stride of each CTA.
+static int gen_stage(ccst_ctx* c, GenLane& lane, GenBatch* gb, const GenItem* items_host, cudaStream_t stream,
+                     long long* stride) {
+    int rc = gen_prepare(c);
+    if (rc) return rc;
+    *stride = gen_stride(c);
+    const int grid = (int)(gb->n < c->gen_grid ? gb->n : c->gen_grid);
+    if (lane.scratch_elems < (size_t)grid * *stride) {
+        if (lane.scratch) cudaFree(lane.scratch);
+        lane.scratch = nullptr;
+        lane.scratch_elems = 0;
+        CK(c, cudaMalloc(&lane.scratch, (size_t)grid * *stride * sizeof(dfc)));
+        lane.scratch_elems = (size_t)grid * *stride;
+    }
+    gb->items = nullptr;
+    if (items_host) {
+        if (lane.items_cap < (size_t)gb->n) {
+            if (lane.d_items) cudaFree(lane.d_items);
+            lane.d_items = nullptr;
+            lane.items_cap = 0;
+            CK(c, cudaMalloc(&lane.d_items, (size_t)gb->n * sizeof(GenItem)));
+            lane.items_cap = (size_t)gb->n;
+        }
+        CK(c, cudaMemcpyAsync(lane.d_items, items_host, (size_t)gb->n * sizeof(GenItem), cudaMemcpyHostToDevice,
+                              stream));
+        gb->items = lane.d_items;
+    }
+    if (any_mix_plan(c)) {
+        bool grew = false;
+        if ((rc = mix_reserve(c, lane, gb->n, &grew))) return rc;
+    }
+    return CCST_OK;
+}
+
+// Launch the general-size kernels on `stream` over gb.n frames: the work list `items_host`
 // (copied to the lane at once; the caller orders it) or, if null, the uniform batch that
 // gb describes. gb.out is set by the caller; the rest is filled in here.
 static int gen_launch(ccst_ctx* c, GenLane& lane, GenBatch gb, const GenItem* items_host, cudaStream_t stream,
                       unsigned* counter, const MixDbg* dbg = nullptr) {
     if (gb.n == 0) return CCST_OK;
-    int rc = gen_prepare(c);
+    long long stride = 0;
+    int rc = gen_stage(c, lane, &gb, items_host, stream, &stride);
     if (rc) return rc;
-    const long long stride = gen_stride(c);
-    const int grid = (int)(gb.n < c->gen_grid ? gb.n : c->gen_grid);
-    if (lane.scratch_elems < (size_t)grid * stride) {
-        if (lane.scratch) cudaFree(lane.scratch);
-        lane.scratch = nullptr;
-        lane.scratch_elems = 0;
-        CK(c, cudaMalloc(&lane.scratch, (size_t)grid * stride * sizeof(dfc)));
-        lane.scratch_elems = (size_t)grid * stride;
-    }
-    gb.items = nullptr;
-    if (items_host) {
-        if (lane.items_cap < (size_t)gb.n) {
-            if (lane.d_items) cudaFree(lane.d_items);
-            lane.d_items = nullptr;
-            lane.items_cap = 0;
-            CK(c, cudaMalloc(&lane.d_items, (size_t)gb.n * sizeof(GenItem)));
-            lane.items_cap = (size_t)gb.n;
-        }
-        CK(c, cudaMemcpyAsync(lane.d_items, items_host, (size_t)gb.n * sizeof(GenItem), cudaMemcpyHostToDevice, stream));
-        gb.items = lane.d_items;
-    }
-    if (any_mix_plan(c)) {
-        bool grew = false;
-        if ((rc = mix_reserve(c, lane, gb.n, &grew))) return rc;
-    }
     return gen_kernel_launch(c, gb, lane, stride, stream, counter, items_host, dbg);
 }
 
@@ -2816,9 +2865,7 @@ static int not_general(ccst_ctx* c, const char* who) {
     return CCST_OK;
 }
 
-// Sort items largest first (the longest work starts first; size classes stay contiguous),
-// copy them to items_dev (n slots) and launch the ROI kernel on `stream` with `counter`.
-// The host items must stay valid until the copy has been issued (it is staged at once).
+// Sort items largest first (the longest work starts first; size classes stay contiguous).
 static void rois_sort(ccst_ctx* c, RoiItem* items, int64_t n) {
     std::stable_sort(items, items + n, [&](const RoiItem& a, const RoiItem& b) {
         return c->plans[a.cls].g.H > c->plans[b.cls].g.H;
@@ -2832,27 +2879,12 @@ static int64_t rois_big_items(ccst_ctx* c, const RoiItem* items, int64_t n) {
     return k;
 }
 
-// Auxiliary stream and fork/join events for the small-class ROI kernel of one launch site.
-struct RoiFork {
-    cudaStream_t aux;
-    cudaEvent_t fork, join;
-};
-
-// The ROI kernels over n items already on the device, the first nbig of them 128 x 128
-// (ordered by rois_sort): counter reset, then the 512-thread kernel over those and the
-// small-class kernel over the rest, each with its own counter (counter[0], counter[1]).
-// When both have items and one of them has fewer than its resident CTAs (a launch that
-// leaves SMs free, as in a served batch), the small-class kernel runs on f.aux beside the
-// other. Two launches that each fill the GPU run one after the other: side by side they
-// pack worse (a 128 x 128 CTA needs a whole SM).
+// The power-of-two ROI kernels over n items already on the device, the first nbig of them
+// 128 x 128 (ordered by rois_sort): the 512-thread kernel over those, then the small-class
+// kernel over the rest, each chained behind the kernel launched before it (*chained) and
+// with its own counter (counter[0], counter[1], zeroed by the caller).
 static int rois_kernel_launch(ccst_ctx* c, const RoiItem* items_dev, int64_t n, int64_t nbig, Result* out,
-                              cudaStream_t stream, unsigned* counter, const RoiFork& f) {
-    CK(c, cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned), stream));
-    const bool both = nbig > 0 && n > nbig && (nbig < c->rois_grid || n - nbig < c->rois_grid_small);
-    if (both) {
-        CK(c, cudaEventRecord(f.fork, stream));
-        CK(c, cudaStreamWaitEvent(f.aux, f.fork, 0));
-    }
+                              cudaStream_t stream, unsigned* counter, bool* chained) {
     for (int small = 0; small < 2; ++small) {
         const int64_t m = small ? n - nbig : nbig;
         if (m == 0) continue;
@@ -2865,25 +2897,81 @@ static int rois_kernel_launch(ccst_ctx* c, const RoiItem* items_dev, int64_t n, 
         rb.next = counter + small;
         const int cap = small ? c->rois_grid_small : c->rois_grid;
         const int grid = (int)(m < cap ? m : cap);
-        void* args[] = {&rb};
-        CK(c, cudaLaunchKernel(track_rois_kernel_ptr(small != 0), dim3(grid),
-                               dim3(small ? track_threads(64, 64) : kThreads), args,
-                               small ? c->rois_smem_small : c->rois_smem, (small && both) ? f.aux : stream));
-    }
-    if (both) {
-        CK(c, cudaEventRecord(f.join, f.aux));
-        CK(c, cudaStreamWaitEvent(stream, f.join, 0));
+        void* args[] = {&rb, &c->rois_g128};
+        CK(c, launch_kernel(track_rois_kernel_ptr(small ? 0 : c->rois_big_cls), grid,
+                            small ? track_threads(64, 64) : kThreads, args, small ? c->rois_smem_small : c->rois_smem,
+                            stream, *chained));
+        *chained = true;
     }
     return CCST_OK;
 }
 
-static int rois_launch(ccst_ctx* c, RoiItem* items, int64_t n, Result* out, cudaStream_t stream, RoiItem* items_dev,
-                       unsigned* counter, const RoiFork& f) {
+// One uneven-ROI batch on `stream`, its work lists already on the device and sorted:
+//   - every counter zeroed;
+//   - the FP32 general-size launches (largest side first) on side.st, forked from `stream`;
+//   - the 128 x 128 ROI kernel, then the small-class ROI kernel, on `stream`;
+//   - joined, the double-float kernel over the general items without an FP32 plan and the
+//     fallback list, once everything before it has completed.
+// On each stream a kernel is chained behind the one before it (programmatic dependent
+// launch): it may start once every CTA of that one has taken its last item, so a tail
+// overlaps the next kernel's start and a batch too small to fill the GPU runs side by side.
+// The general-size launches are issued first: their items are the longest (about 100 us per
+// CTA, against 45 us for the power-of-two kernels), and starting them first, with the 128 x
+// 128 kernel taking SMs as they drain, packed the survey's uneven mix about 8% tighter in a
+// captured graph than the other way round or one chain of all four kernels.
+struct RoiPart {
+    const RoiItem* items_dev;   // n items, largest first
+    const RoiItem* items;       // their host copy
+    int64_t n;
+    unsigned* counter;          // 2 counters
+};
+struct GenPart {
+    GenBatch gb;                // gb.items on the device (gen_sort order), gb.n items, gb.out
+    const GenItem* items;       // their host copy
+    GenLane* lane;
+    long long stride;           // double-float scratch per CTA
+    unsigned* counter;
+};
+static int rois_chain_launch(ccst_ctx* c, const RoiPart& rp, const GenPart& gp, Result* out, cudaStream_t stream,
+                             SideStream& side) {
+    GenSplit sp;
+    int rc;
+    if (gp.gb.n > 0) {
+        if ((rc = gen_split_items(c, gp.gb, gp.items, *gp.lane, &sp))) return rc;
+        if ((rc = gen_zero(c, sp, *gp.lane, gp.counter, stream))) return rc;
+    }
+    if (rp.n > 0) CK(c, cudaMemsetAsync(rp.counter, 0, 2 * sizeof(unsigned), stream));
+    const bool fork = sp.ns > 0 && rp.n > 0;
+    cudaStream_t gs = stream;
+    if (fork) {
+        CK(c, side_make(side));
+        CK(c, cudaEventRecord(side.fork, stream));
+        CK(c, cudaStreamWaitEvent(side.st, side.fork, 0));
+        gs = side.st;
+    }
+    bool chained = false;
+    if (sp.ns > 0 && (rc = gen_mix_launch(c, gp.gb, sp, *gp.lane, gs, &chained))) return rc;
+    if (fork) chained = false;
+    if (rp.n > 0 && (rc = rois_kernel_launch(c, rp.items_dev, rp.n, rois_big_items(c, rp.items, rp.n), out, stream,
+                                             rp.counter, &chained)))
+        return rc;
+    if (fork) {
+        CK(c, cudaEventRecord(side.join, side.st));
+        CK(c, cudaStreamWaitEvent(stream, side.join, 0));
+    }
+    if (gp.gb.n > 0) return gen_direct_launch(c, gp.gb, sp, *gp.lane, gp.stride, gp.counter, stream);
+    return CCST_OK;
+}
+
+// Sort the power-of-two items, upload the plans and references, copy the items to
+// items_dev (n slots) on `stream`. The host items must stay valid until the copy has run
+// (pageable memory is staged at once).
+static int rois_stage(ccst_ctx* c, RoiItem* items, int64_t n, cudaStream_t stream, RoiItem* items_dev) {
     rois_sort(c, items, n);
     int rc = rois_upload(c);
     if (rc) return rc;
     CK(c, cudaMemcpyAsync(items_dev, items, (size_t)n * sizeof(RoiItem), cudaMemcpyHostToDevice, stream));
-    return rois_kernel_launch(c, items_dev, n, rois_big_items(c, items, n), out, stream, counter, f);
+    return CCST_OK;
 }
 
 constexpr size_t kMaxRoiGraphs = 64;
@@ -2896,8 +2984,8 @@ static uint64_t fnv1a(const void* p, size_t bytes) {
 }
 
 // ccst_track_rois as a replay of a graph captured once per (stream, out, work list): the
-// general-size kernel forked onto the context's second stream and the power-of-two kernel,
-// joined. The work items (sorted as the direct path sorts them) are uploaded at capture.
+// batch's chain of launches (rois_chain_launch). The work items (sorted as the direct path
+// sorts them) are uploaded at capture.
 // c->h_items[0, np) and c->h_gitems[0, ng) hold the validated items.
 static int rois_graph_track(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccst_result* out_dev, int64_t np,
                             int64_t ng) {
@@ -2917,11 +3005,6 @@ static int rois_graph_track(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccst_r
     }
     if (it == c->roi_graphs.end()) {
         if (c->roi_graphs.size() >= kMaxRoiGraphs) drop_roi_graphs(c);
-        if (ng > 0 && !c->gstream) {
-            CK(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
-            CK(c, cudaEventCreateWithFlags(&c->gfork, cudaEventDisableTiming));
-            CK(c, cudaEventCreateWithFlags(&c->gjoin, cudaEventDisableTiming));
-        }
         GenLane* lane = nullptr;
         const long long stride = ng > 0 ? gen_stride(c) : 0;
         if (ng > 0) {
@@ -2964,27 +3047,21 @@ static int rois_graph_track(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccst_r
                 return bail(fail(c, err == cudaErrorMemoryAllocation ? CCST_E_NOMEM : CCST_E_CUDA,
                                  std::string("ccst_track_rois: ") + cudaGetErrorString(err)));
         }
+        if ((err = side_make(c->rside)) != cudaSuccess)               // not made during capture
+            return bail(fail(c, CCST_E_CUDA, std::string("ccst_track_rois: ") + cudaGetErrorString(err)));
         cudaGraph_t graph = nullptr;
         if ((err = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
             return bail(fail(c, CCST_E_CUDA, std::string("ccst_track_rois: capture: ") + cudaGetErrorString(err)));
-        int lrc = CCST_OK;
-        if (ng > 0) {
-            GenBatch gb{};
-            gb.n = ng;
-            gb.out = (Result*)out_dev;
-            gb.items = e.d_gitems;
-            if (cudaEventRecord(c->gfork, c->stream) != cudaSuccess ||
-                cudaStreamWaitEvent(c->gstream, c->gfork, 0) != cudaSuccess)
-                lrc = fail(c, CCST_E_CUDA, "ccst_track_rois: fork during capture");
-            if (!lrc) lrc = gen_kernel_launch(c, gb, *lane, stride, c->gstream, e.counters + 2, c->h_gitems.data());
-            if (!lrc && cudaEventRecord(c->gjoin, c->gstream) != cudaSuccess)
-                lrc = fail(c, CCST_E_CUDA, "ccst_track_rois: join during capture");
-        }
-        if (!lrc && np > 0)
-            lrc = rois_kernel_launch(c, e.d_items, np, rois_big_items(c, c->h_items.data(), np), (Result*)out_dev,
-                                     c->stream, e.counters, RoiFork{c->rs_aux, c->rs_fork, c->rs_join});
-        if (!lrc && ng > 0 && cudaStreamWaitEvent(c->stream, c->gjoin, 0) != cudaSuccess)
-            lrc = fail(c, CCST_E_CUDA, "ccst_track_rois: join during capture");
+        GenPart gpart{};
+        gpart.gb.n = ng;
+        gpart.gb.out = (Result*)out_dev;
+        gpart.gb.items = e.d_gitems;
+        gpart.items = c->h_gitems.data();
+        gpart.lane = lane;
+        gpart.stride = stride;
+        gpart.counter = e.counters + 2;
+        const int lrc = rois_chain_launch(c, RoiPart{e.d_items, c->h_items.data(), np, e.counters}, gpart,
+                                          (Result*)out_dev, c->stream, c->rside);
         err = cudaStreamEndCapture(c->stream, &graph);
         if (lrc) {
             if (graph) cudaGraphDestroy(graph);
@@ -3042,37 +3119,29 @@ extern "C" int ccst_track_rois(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccs
     }
     if ((c->p.flags & CCST_FLAG_GRAPHS) && c->stream != nullptr) return rois_graph_track(c, rois, n, out_dev, np, ng);
     CK(c, shared_acquire(c, c->stream));
+    GenPart gpart{};
     if (ng > 0) {
-        // the general sizes run on their own stream, forked here and joined below
-        if (!c->gstream) {
-            CK(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
-            CK(c, cudaEventCreateWithFlags(&c->gfork, cudaEventDisableTiming));
-            CK(c, cudaEventCreateWithFlags(&c->gjoin, cudaEventDisableTiming));
-        }
         gen_sort(c, c->h_gitems.data(), ng);
-        CK(c, cudaEventRecord(c->gfork, c->stream));
-        CK(c, cudaStreamWaitEvent(c->gstream, c->gfork, 0));
-        GenBatch gb{};
-        gb.n = ng;
-        gb.out = (Result*)out_dev;
-        if ((rc = gen_launch(c, c->glane[0], gb, c->h_gitems.data(), c->gstream, c->d_next + 24))) return rc;
-        CK(c, cudaEventRecord(c->gjoin, c->gstream));
+        gpart.gb.n = ng;
+        gpart.gb.out = (Result*)out_dev;
+        if ((rc = gen_stage(c, c->glane[0], &gpart.gb, c->h_gitems.data(), c->stream, &gpart.stride))) return rc;
+        gpart.items = c->h_gitems.data();
+        gpart.lane = &c->glane[0];
+        gpart.counter = c->d_next + 24;
     }
     if (np > 0) {
-        n = np;
-        if (c->items_cap < (size_t)n) {
+        if (c->items_cap < (size_t)np) {
             if (c->d_items) cudaFree(c->d_items);
             c->d_items = nullptr;
             c->items_cap = 0;
-            CK(c, cudaMalloc(&c->d_items, (size_t)n * sizeof(RoiItem)));
-            c->items_cap = (size_t)n;
+            CK(c, cudaMalloc(&c->d_items, (size_t)np * sizeof(RoiItem)));
+            c->items_cap = (size_t)np;
         }
-        if ((rc = rois_upload(c))) return rc;       // also makes the fork stream and events
-        if ((rc = rois_launch(c, c->h_items.data(), n, (Result*)out_dev, c->stream, c->d_items, c->d_next + 16,
-                              RoiFork{c->rs_aux, c->rs_fork, c->rs_join})))
-            return rc;
+        if ((rc = rois_stage(c, c->h_items.data(), np, c->stream, c->d_items))) return rc;
     }
-    if (ng > 0) CK(c, cudaStreamWaitEvent(c->stream, c->gjoin, 0));     // both batches done
+    if ((rc = rois_chain_launch(c, RoiPart{c->d_items, c->h_items.data(), np, c->d_next + 16}, gpart,
+                                (Result*)out_dev, c->stream, c->rside)))
+        return rc;
     CK(c, shared_release(c, c->stream));
     return CCST_OK;
 }
@@ -3103,13 +3172,7 @@ struct ccst_server {
     struct InFlight {
         cudaStream_t st = nullptr;
         cudaEvent_t ev = nullptr;
-        // the general-size part of a batch runs on st_gen beside the power-of-two part,
-        // forked from and joined back to st
-        cudaStream_t st_gen = nullptr;
-        cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-        // the small-class ROI kernel beside the 128 x 128 one
-        cudaStream_t st_small = nullptr;
-        cudaEvent_t ev_sfork = nullptr, ev_sjoin = nullptr;
+        SideStream side;               // the batch's general-size part, beside st
         Result* d_out = nullptr;
         Result* h_out = nullptr;
         RoiItem* d_items = nullptr;
@@ -3273,26 +3336,19 @@ static void server_loop(ccst_server* s) {
         }
         // each kernel writes record i of the batch to d_out[i]; out_index survives the sorts
         bool ok = true;
-        const bool both = np > 0 && ng > 0;
-        if (both) {
-            ok = cudaEventRecord(b.ev_fork, b.st) == cudaSuccess &&
-                 cudaStreamWaitEvent(b.st_gen, b.ev_fork, 0) == cudaSuccess;
-        }
-        if (ok && np > 0)
-            ok = rois_launch(c, b.h_items, np, b.d_out, b.st, b.d_items, s->d_counters + 3 * next,
-                             RoiFork{b.st_small, b.ev_sfork, b.ev_sjoin}) == CCST_OK;
-        if (ok && ng > 0) {
+        GenPart gpart{};
+        if (ng > 0) {
             gen_sort(c, b.h_gitems, ng);
-            GenBatch gb{};
-            gb.n = ng;
-            gb.out = b.d_out;
-            ok = gen_launch(c, b.lane, gb, b.h_gitems, both ? b.st_gen : b.st, s->d_counters + 3 * next + 2) ==
-                 CCST_OK;
+            gpart.gb.n = ng;
+            gpart.gb.out = b.d_out;
+            ok = gen_stage(c, b.lane, &gpart.gb, b.h_gitems, b.st, &gpart.stride) == CCST_OK;
+            gpart.items = b.h_gitems;
+            gpart.lane = &b.lane;
+            gpart.counter = s->d_counters + 3 * next + 2;
         }
-        if (ok && both) {
-            ok = cudaEventRecord(b.ev_join, b.st_gen) == cudaSuccess &&
-                 cudaStreamWaitEvent(b.st, b.ev_join, 0) == cudaSuccess;
-        }
+        if (ok && np > 0) ok = rois_stage(c, b.h_items, np, b.st, b.d_items) == CCST_OK;
+        ok = ok && rois_chain_launch(c, RoiPart{b.d_items, b.h_items, np, s->d_counters + 3 * next}, gpart, b.d_out,
+                                     b.st, b.side) == CCST_OK;
         ok = ok && cudaMemcpyAsync(b.h_out, b.d_out, (size_t)m * sizeof(Result), cudaMemcpyDeviceToHost, b.st) ==
                        cudaSuccess;
         ok = ok && cudaEventRecord(b.ev, b.st) == cudaSuccess;
@@ -3314,16 +3370,9 @@ static void server_loop(ccst_server* s) {
 static void server_free(ccst_server* s) {
     for (auto& b : s->ring) {
         if (b.st) cudaStreamSynchronize(b.st);
-        if (b.st_gen) cudaStreamSynchronize(b.st_gen);
-        if (b.st_small) cudaStreamSynchronize(b.st_small);
-        if (b.st_small) cudaStreamDestroy(b.st_small);
-        if (b.ev_sfork) cudaEventDestroy(b.ev_sfork);
-        if (b.ev_sjoin) cudaEventDestroy(b.ev_sjoin);
+        side_free(b.side);
         if (b.ev) cudaEventDestroy(b.ev);
-        if (b.ev_fork) cudaEventDestroy(b.ev_fork);
-        if (b.ev_join) cudaEventDestroy(b.ev_join);
         if (b.st) cudaStreamDestroy(b.st);
-        if (b.st_gen) cudaStreamDestroy(b.st_gen);
         if (b.d_out) cudaFree(b.d_out);
         if (b.h_out) cudaFreeHost(b.h_out);
         if (b.d_items) cudaFree(b.d_items);
@@ -3380,12 +3429,6 @@ extern "C" int ccst_server_create_ex(ccst_ctx* c, const ccst_server_config* cfg,
         auto& b = s->ring[k];
         if ((e = cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking)) != cudaSuccess) return bad(e);
         if ((e = cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming)) != cudaSuccess) return bad(e);
-        if ((e = cudaStreamCreateWithFlags(&b.st_gen, cudaStreamNonBlocking)) != cudaSuccess) return bad(e);
-        if ((e = cudaEventCreateWithFlags(&b.ev_fork, cudaEventDisableTiming)) != cudaSuccess) return bad(e);
-        if ((e = cudaEventCreateWithFlags(&b.ev_join, cudaEventDisableTiming)) != cudaSuccess) return bad(e);
-        if ((e = cudaStreamCreateWithFlags(&b.st_small, cudaStreamNonBlocking)) != cudaSuccess) return bad(e);
-        if ((e = cudaEventCreateWithFlags(&b.ev_sfork, cudaEventDisableTiming)) != cudaSuccess) return bad(e);
-        if ((e = cudaEventCreateWithFlags(&b.ev_sjoin, cudaEventDisableTiming)) != cudaSuccess) return bad(e);
         if ((e = cudaMalloc(&b.d_out, (size_t)s->max_batch * sizeof(Result))) != cudaSuccess) return bad(e);
         if ((e = cudaHostAlloc(&b.h_out, (size_t)s->max_batch * sizeof(Result), cudaHostAllocDefault)) != cudaSuccess)
             return bad(e);

@@ -45,6 +45,27 @@ template <> __device__ __forceinline__ double2 cmake<double2>(double x, double y
 
 __device__ __forceinline__ int brev(int x, int logN) { return (int)(__brev((unsigned)x) >> (32 - logN)); }
 
+// Hint that [p, p + bytes) is read soon: bulk prefetches into L2 (cp.async.bulk.prefetch,
+// sm_90 and later) over the 16-byte-aligned part of the range, in pieces of at most 32 KB.
+// One thread issues them; nothing waits on them, and no byte outside the range is touched.
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+    const uintptr_t a = ((uintptr_t)p + 15) & ~(uintptr_t)15, e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+    for (uintptr_t q = a; q < e; q += 32768) {
+        const unsigned n = (unsigned)(e - q < 32768 ? e - q : 32768);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(q), "r"(n) : "memory");
+    }
+}
+
+// Programmatic dependent launch (sm_90 and later), for persistent kernels chained on one
+// stream. pdl_trigger: the next kernel on the stream, if it was launched with programmatic
+// stream serialization, may start once every CTA of this grid has called it or exited (a
+// no-op without such a kernel). pdl_wait: returns once the grid this one was let in early
+// behind has completed and its writes are visible (at once if there is none). A chained
+// kernel calls pdl_wait before it exits, so that its completion implies that of every
+// kernel before it in the chain.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
 // ------------------------------------------------------------------ radix-2 FFT
 // In-place radix-2 decimation-in-time passes over `nseq` independent sequences of
 // length N = 2^logN. Element i of sequence s sits at buf[s*seq_stride + i*elem_stride].

@@ -312,6 +312,9 @@ struct Smem {
     int* cj;               // candidate list
     float* cv;             // candidate values
     int* misc;             // small broadcast ints
+    // the frame's reference spectra, when they are not the geometry's own (an uneven-ROI
+    // item's, in shared memory), else null
+    const RefSpectra* ref;
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -469,6 +472,7 @@ static __device__ inline Smem carve(const Geom& g, unsigned char* base) {
     s.cj = (int*)m; m += sizeof(int) * kMaxCand;
     s.cv = (float*)m; m += sizeof(float) * kMaxCand;
     s.misc = (int*)m;
+    s.ref = nullptr;
     return s;
 }
 
@@ -569,13 +573,14 @@ static __device__ void fft_correlate_t(const Geom& g, const Smem& S, const void*
         [&](int s, int n2, int k1, float2 v) { A[(N2h * k1 + n2) * SA + s] = v; });
     __syncthreads();
     // column pass 2 + a3: product with conj(F[b]) (slot 0 is unpacked afterwards)
+    const float2* FE32 = S.ref ? S.ref->FE32 : g.FE32;
     float sabs = 0.f;
     fft_pass2<N1h, N2h, false, true>(
         SA, [&](int s, int k1, int n2) { return A[(N2h * k1 + n2) * SA + s]; },
         [&](int s, int k1, int k2, float2 v) {
             if (s != 0) {
                 const int ky = k1 + N1h * k2;
-                const float2 x = cmul(v, cconj(__ldg(&g.FE32[ky * (W / 2 + 1) + s])));
+                const float2 x = cmul(v, cconj(__ldg(&FE32[ky * (W / 2 + 1) + s])));
                 sabs += 2.f * (fabsf(x.x) + fabsf(x.y));
                 v = x;
             }
@@ -589,8 +594,8 @@ static __device__ void fft_correlate_t(const Geom& g, const Smem& S, const void*
         const float2 f0 = make_float2(0.5f * (zp.x + zm.x), 0.5f * (zp.y + zm.y));
         const float2 d = csub(zp, zm);
         const float2 fn = make_float2(0.5f * d.y, -0.5f * d.x);
-        const float2 x0 = cmul(f0, cconj(__ldg(&g.FE32[ky * (W / 2 + 1)])));
-        const float2 xn = cmul(fn, cconj(__ldg(&g.FE32[ky * (W / 2 + 1) + W / 2])));
+        const float2 x0 = cmul(f0, cconj(__ldg(&FE32[ky * (W / 2 + 1)])));
+        const float2 xn = cmul(fn, cconj(__ldg(&FE32[ky * (W / 2 + 1) + W / 2])));
         sabs += fabsf(x0.x) + fabsf(x0.y) + fabsf(xn.x) + fabsf(xn.y);
         XN[q] = xn;
         B[q] = x0;                       // staged: other threads still read slot 0
@@ -669,6 +674,7 @@ __device__ __forceinline__ float int_surface(const Geom& g, const Smem& S, int f
 // FP64 direct sum c(s) = sum_r a((r + s) mod N) b(r) (left-hand side of Eq. (4)/(7)).
 static __device__ double direct_sum_f64(const Geom& g, const Smem& S, const void* frame, long long pitch,
                                  int sy, int sx) {
+    const double* b64 = S.ref ? S.ref->b64 : g.b64;
     double acc = 0.0;
     for (int idx = threadIdx.x; idx < g.H * g.W; idx += blockDim.x) {
         const int y = idx >> g.logW, x = idx & (g.W - 1);
@@ -676,7 +682,7 @@ static __device__ double direct_sum_f64(const Geom& g, const Smem& S, const void
         double I;
         if (g.in_dtype == 0) I = load_pixel((const unsigned short*)frame, (long long)yy * pitch + xx);
         else I = load_pixel((const float*)frame, (long long)yy * pitch + xx);
-        acc = fma(operand_f64(I, g), __ldg(&g.b64[idx]), acc);
+        acc = fma(operand_f64(I, g), __ldg(&b64[idx]), acc);
     }
     return block_sum(acc, S.rd);
 }
@@ -2002,7 +2008,8 @@ static __device__ int df_reevaluate(const Geom& g, const Smem& S, const void* fr
         __syncthreads();
     }
     // columns, with the product X = F[a] conj F[b] fused into the last pass
-    auto product = [&](int ky, int kx, dfc v) { return cmul(v, cconj(g.FEdf[ky * Wc + kx])); };
+    const dfc* FEdf = S.ref ? S.ref->FEdf : g.FEdf;
+    auto product = [&](int ky, int kx, dfc v) { return cmul(v, cconj(FEdf[ky * Wc + kx])); };
     fft_pass1_df<N1h, N2h, true>(
         Wc, t4h, [&](int s, int n2, int n1) { return Xd[(N2h * n1 + n2) * Wcp + s]; },
         [&](int s, int n2, int k1, dfc v) {
@@ -2264,10 +2271,10 @@ __global__ void __launch_bounds__(track_threads(H, W), track_min_ctas(H, W)) tra
     }
 }
 
-// Address of the uneven-ROI kernel (ccst_rois.cu): `small` is the instantiation for the
-// size classes up to 64 x 64 (track_threads(64, 64) threads, two CTAs per SM); the other
-// takes every class (the host gives it the 128 x 128 items).
-const void* track_rois_kernel_ptr(bool small);
+// Address of an uneven-ROI kernel (ccst_rois.cu): cls 0 is the instantiation for the size
+// classes up to 64 x 64 (track_threads(64, 64) threads, two CTAs per SM); 1 takes the
+// 128 x 128 class with either contraction form, 2 the 128 x 128 class of a tcgen05 plan.
+const void* track_rois_kernel_ptr(int cls);
 
 // Address of track_kernel<H, W> (defined in the per-height translation units).
 const void* track_kernel_h8(int W);

@@ -379,6 +379,7 @@ __global__ void __launch_bounds__(mix_threads(H, W), mix_min_ctas(H, W)) __clust
         }
         Clu<CL>::sync();
         const long long idx = S.misc[0];
+        if (idx >= a.n - (long long)(gridDim.x / CL)) pdl_trigger();      // the last wave
         if (idx >= a.n) break;
         GenItem it;
         if (a.items) {
@@ -391,6 +392,9 @@ __global__ void __launch_bounds__(mix_threads(H, W), mix_min_ctas(H, W)) __clust
             it.ref = a.ref;
         }
         const dfc* Fb = a.refs[it.ref];
+        // a per-ROI reference is cold in L2 and the product step reads it after the row
+        // FFTs: each CTA of the cluster prefetches its share of the rows
+        if (tid == 0) prefetch_l2(Fb + (size_t)row0 * Wc, (size_t)RH * Wc * sizeof(dfc));
         const int elem = P.in_dtype == 0 ? 2 : 4;
         const char* frame = (const char*)it.frame;
         const bool vec = ((uintptr_t)frame % 16 == 0) && ((it.pitch * elem) % 16 == 0) && ((W * elem) % 16 == 0);
@@ -1009,6 +1013,7 @@ __global__ void __launch_bounds__(mix_threads(H, W), mix_min_ctas(H, W)) __clust
             a.out[it.out_index] = r;
         }
     }
+    pdl_wait();
 }
 
 template <int H, int W>
