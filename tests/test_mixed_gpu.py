@@ -261,6 +261,39 @@ def test_rois_of_every_fp32_side_graph_and_direct(torch):
             check(ref, f[None], g[None], 100, oracle.CC_U)
 
 
+def test_fallbacks_of_both_chained_fp32_launches_reach_the_double_float_kernel(torch):
+    # flat ROIs (every shift ties) at 96 and 48 px, whose FP32 launches run one behind the
+    # other on the second stream, beside power-of-two ROIs on the first: the double-float
+    # kernel, launched after the join, must find the fallbacks of both launches. Every ROI's
+    # record equals the one its own context gives for that frame alone (direct and graph-
+    # replayed calls alike).
+    rng = np.random.default_rng(150)
+    sides = [96, 128, 48, 32, 96, 48, 64, 128, 96, 48]
+    flat = {4, 5}
+    items = []
+    for i, N in enumerate(sides):
+        ref, fr = spots(N, 1, seed=int(rng.integers(1 << 30)))
+        items.append((ref, np.full((N, N), 7, np.uint16) if i in flat else fr[0]))
+    alone = [track(torch, ref, f[None], 100)[0] for ref, f in items]
+    for i in flat:
+        assert alone[i]["flags"] & C.R_GENERIC and not alone[i]["flags"] & C.R_FP32_GENERAL, (i, alone[i])
+    frames = [dev(torch, f) for _, f in items]
+    ref0 = synth.gaussian_spot(32, 32, 16, 16, 2.0, 500.0, 10.0).astype(np.float32)
+    for graphs in (False, True):
+        st = torch.cuda.Stream() if graphs else None
+        t = C.Tracker(ref0, upsample=100, in_dtype="u16", graphs=graphs, stream=st)
+        ids = [C.ccst_add_reference(t.ctx, r, *r.shape) for r, _ in items]
+        rois = C.make_rois(frames, ids)
+        for _ in range(2 if graphs else 1):
+            out = t.empty_results(len(items))
+            C.ccst_track_rois(t.ctx, rois, len(items), out)
+            C.ccst_sync(t.ctx)
+            res = C.decode(out)
+            for i in range(len(items)):
+                assert res[i].tobytes() == alone[i].tobytes(), (graphs, i, sides[i], res[i], alone[i])
+        t.close()
+
+
 @pytest.mark.parametrize("N", [48, 96, 192, 256])
 def test_integer_near_ties_are_decided_in_double_float(torch, N):
     # noise-free spots shifted by 1/2 + d px along x: the integer shifts 0 and 1 nearly tie
