@@ -266,17 +266,20 @@ int ccst_poll(ccst_ctx* ctx, uint64_t ticket, int timeout_us, int* done);
 int ccst_add_reference(ccst_ctx* ctx, const float* ref, int H, int W, int* ref_id);
 
 /* Track an uneven batch: n ROIs of mixed sizes, each against its own reference (Secs. II-III
- * per ROI, as ccst_track), in ONE persistent launch.
+ * per ROI, as ccst_track), in one call of persistent launches.
  *   rois      host memory, n descriptors (read during the call).
  *   out_dev   device memory, n records; record i belongs to rois[i].
- * Work items run largest ROI first; each CTA takes the next item from a counter and
- * re-plans its shared memory when the size changes. The records of power-of-two ROIs are
- * identical to those of ccst_track on a context made for that ROI's reference. ROIs of
- * general sizes run on an internal stream, concurrently with the first launch: one
- * persistent launch of the FP32 general-size kernel per side it takes (48, 96, 192, 256),
- * then one of the double-float kernel over the other general sides and the frames the
- * FP32 kernel handed on; the call's work is complete when the context's stream reaches it.
- * With CCST_FLAG_GRAPHS (and a non-default stream), both launches are captured once as
+ * Work items run largest ROI first; each CTA takes the next item from a counter. The
+ * power-of-two ROIs run on the context's stream in two launches (the 128 x 128 ROIs; the
+ * 16, 32 and 64 px ROIs, whose CTAs re-plan their shared memory when the size changes).
+ * Their records are identical to those of ccst_track on a context made for that ROI's
+ * reference. ROIs of general sizes run on an internal stream beside them: one persistent
+ * launch of the FP32 general-size kernel per side it takes (48, 96, 192, 256). On each
+ * stream a launch may start in the last wave of the one before it (programmatic dependent
+ * launch). After both, one launch of the double-float kernel takes the other general sides
+ * and the frames the FP32 kernel handed on; the call's work is complete when the context's
+ * stream reaches it.
+ * With CCST_FLAG_GRAPHS (and a non-default stream), the launches are captured once as
  * one CUDA graph per (stream, out_dev, work list), with the work items uploaded to memory
  * the graph owns, and replayed by later calls with the same list (compared byte by byte).
  * A graph's frame counters and items are its own. The general-size scratch is one area
@@ -335,9 +338,10 @@ int ccst_autotune(ccst_ctx* ctx, int reps, const ccst_roi* rois, int64_t n_rois,
  * memory of the in-flight batches (records, work items, general-size scratch) is
  * allocated at creation, so the budget bounds what admitted frames add.
  * The worker takes everything pending (up to max_batch frames, any cameras and sizes) as
- * one batch on its own stream: the power-of-two ROI kernel for cameras of 16, 32, 64 or
- * 128 px, then the general-size kernels for the others (each ring entry has its own
- * lane for them). Up to max_in_flight (at most 4) batches are in flight. Frames that
+ * one batch on its own stream, launched as ccst_track_rois launches a batch: the
+ * power-of-two ROI kernels for cameras of 16, 32, 64 or 128 px and, beside them, the
+ * general-size kernels for the others (each ring entry has its own lane and second
+ * stream for them). Up to max_in_flight (at most 4) batches are in flight. Frames that
  * arrive while others run are admitted as memory frees up, and their work overlaps on
  * the device. With max_batch = 1 and max_in_flight = 1 the server is the plain form:
  * one launch per frame, each after the previous one has finished. Each result equals
