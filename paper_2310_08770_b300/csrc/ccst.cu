@@ -2603,39 +2603,49 @@ static long long gen_stride(ccst_ctx* c) {
     return stride;
 }
 
-// Device state of a general-size batch of gb->n frames on `lane`: the double-float kernel's
-// scratch, the work list `items_host` (copied to the lane on `stream`; the caller orders it;
-// gb->items is set to the copy) and the FP32 kernel's counters and fallback list.
-// *stride: the scratch stride of each CTA.
-static int gen_stage(ccst_ctx* c, GenLane& lane, GenBatch* gb, const GenItem* items_host, cudaStream_t stream,
-                     long long* stride) {
+// A lane's device buffers for general-size batches of up to n frames: the double-float
+// kernel's scratch, the work-list copy and the FP32 kernel's counters and fallback list.
+// Grows them (a reallocation synchronises the device) and never shrinks them.
+static int lane_reserve(ccst_ctx* c, GenLane& lane, long long n) {
+    if (n <= 0) return CCST_OK;
     int rc = gen_prepare(c);
     if (rc) return rc;
-    *stride = gen_stride(c);
-    const int grid = (int)(gb->n < c->gen_grid ? gb->n : c->gen_grid);
-    if (lane.scratch_elems < (size_t)grid * *stride) {
+    const long long stride = gen_stride(c);
+    const int grid = (int)(n < c->gen_grid ? n : c->gen_grid);
+    if (lane.scratch_elems < (size_t)grid * stride) {
         if (lane.scratch) cudaFree(lane.scratch);
         lane.scratch = nullptr;
         lane.scratch_elems = 0;
-        CK(c, cudaMalloc(&lane.scratch, (size_t)grid * *stride * sizeof(dfc)));
-        lane.scratch_elems = (size_t)grid * *stride;
+        CK(c, cudaMalloc(&lane.scratch, (size_t)grid * stride * sizeof(dfc)));
+        lane.scratch_elems = (size_t)grid * stride;
     }
-    gb->items = nullptr;
-    if (items_host) {
-        if (lane.items_cap < (size_t)gb->n) {
-            if (lane.d_items) cudaFree(lane.d_items);
-            lane.d_items = nullptr;
-            lane.items_cap = 0;
-            CK(c, cudaMalloc(&lane.d_items, (size_t)gb->n * sizeof(GenItem)));
-            lane.items_cap = (size_t)gb->n;
-        }
-        CK(c, cudaMemcpyAsync(lane.d_items, items_host, (size_t)gb->n * sizeof(GenItem), cudaMemcpyHostToDevice,
-                              stream));
-        gb->items = lane.d_items;
+    if (lane.items_cap < (size_t)n) {
+        if (lane.d_items) cudaFree(lane.d_items);
+        lane.d_items = nullptr;
+        lane.items_cap = 0;
+        CK(c, cudaMalloc(&lane.d_items, (size_t)n * sizeof(GenItem)));
+        lane.items_cap = (size_t)n;
     }
     if (any_mix_plan(c)) {
         bool grew = false;
-        if ((rc = mix_reserve(c, lane, gb->n, &grew))) return rc;
+        if ((rc = mix_reserve(c, lane, n, &grew))) return rc;
+    }
+    return CCST_OK;
+}
+
+// Device state of a general-size batch of gb->n frames on `lane` (lane_reserve), and the
+// work list `items_host` copied to the lane on `stream` (the caller orders it; gb->items is
+// set to the copy, or null for a uniform batch). *stride: the scratch stride of each CTA.
+static int gen_stage(ccst_ctx* c, GenLane& lane, GenBatch* gb, const GenItem* items_host, cudaStream_t stream,
+                     long long* stride) {
+    int rc = lane_reserve(c, lane, gb->n);
+    if (rc) return rc;
+    *stride = gen_stride(c);
+    gb->items = nullptr;
+    if (items_host) {
+        CK(c, cudaMemcpyAsync(lane.d_items, items_host, (size_t)gb->n * sizeof(GenItem), cudaMemcpyHostToDevice,
+                              stream));
+        gb->items = lane.d_items;
     }
     return CCST_OK;
 }
@@ -2908,10 +2918,13 @@ static int rois_kernel_launch(ccst_ctx* c, const RoiItem* items_dev, int64_t n, 
 
 // One uneven-ROI batch on `stream`, its work lists already on the device and sorted:
 //   - every counter zeroed;
-//   - the FP32 general-size launches (largest side first) on side.st, forked from `stream`;
-//   - the 128 x 128 ROI kernel, then the small-class ROI kernel, on `stream`;
-//   - joined, the double-float kernel over the general items without an FP32 plan and the
-//     fallback list, once everything before it has completed.
+//   - on side.st, forked from `stream`: the FP32 general-size launches (largest side
+//     first), then the double-float kernel over the general items without an FP32 plan
+//     and the fallback list, a plain launch that starts once the FP32 launches have
+//     completed;
+//   - on `stream`: the 128 x 128 ROI kernel, then the small-class ROI kernel;
+//   - joined.
+// (Without power-of-two items, or without general ones, everything runs on `stream`.)
 // On each stream a kernel is chained behind the one before it (programmatic dependent
 // launch): it may start once every CTA of that one has taken its last item, so a tail
 // overlaps the next kernel's start and a batch too small to fill the GPU runs side by side.
@@ -2941,7 +2954,7 @@ static int rois_chain_launch(ccst_ctx* c, const RoiPart& rp, const GenPart& gp, 
         if ((rc = gen_zero(c, sp, *gp.lane, gp.counter, stream))) return rc;
     }
     if (rp.n > 0) CK(c, cudaMemsetAsync(rp.counter, 0, 2 * sizeof(unsigned), stream));
-    const bool fork = sp.ns > 0 && rp.n > 0;
+    const bool fork = gp.gb.n > 0 && rp.n > 0;
     cudaStream_t gs = stream;
     if (fork) {
         CK(c, side_make(side));
@@ -2955,11 +2968,11 @@ static int rois_chain_launch(ccst_ctx* c, const RoiPart& rp, const GenPart& gp, 
     if (rp.n > 0 && (rc = rois_kernel_launch(c, rp.items_dev, rp.n, rois_big_items(c, rp.items, rp.n), out, stream,
                                              rp.counter, &chained)))
         return rc;
+    if (gp.gb.n > 0 && (rc = gen_direct_launch(c, gp.gb, sp, *gp.lane, gp.stride, gp.counter, gs))) return rc;
     if (fork) {
         CK(c, cudaEventRecord(side.join, side.st));
         CK(c, cudaStreamWaitEvent(stream, side.join, 0));
     }
-    if (gp.gb.n > 0) return gen_direct_launch(c, gp.gb, sp, *gp.lane, gp.stride, gp.counter, stream);
     return CCST_OK;
 }
 
@@ -3429,6 +3442,7 @@ extern "C" int ccst_server_create_ex(ccst_ctx* c, const ccst_server_config* cfg,
         auto& b = s->ring[k];
         if ((e = cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking)) != cudaSuccess) return bad(e);
         if ((e = cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming)) != cudaSuccess) return bad(e);
+        if ((e = side_make(b.side)) != cudaSuccess) return bad(e);     // not made while serving
         if ((e = cudaMalloc(&b.d_out, (size_t)s->max_batch * sizeof(Result))) != cudaSuccess) return bad(e);
         if ((e = cudaHostAlloc(&b.h_out, (size_t)s->max_batch * sizeof(Result), cudaHostAllocDefault)) != cudaSuccess)
             return bad(e);
@@ -3437,6 +3451,13 @@ extern "C" int ccst_server_create_ex(ccst_ctx* c, const ccst_server_config* cfg,
             return bad(e);
         if ((e = cudaHostAlloc(&b.h_gitems, (size_t)s->max_batch * sizeof(GenItem), cudaHostAllocDefault)) != cudaSuccess)
             return bad(e);
+        // the general-size lane for a whole batch: growing it while serving would
+        // reallocate, and so synchronise the device under every batch in flight
+        if (!c->gplans.empty() && (rc = lane_reserve(c, b.lane, s->max_batch)) != CCST_OK) {
+            server_free(s);
+            delete s;
+            return rc;
+        }
     }
     s->worker = std::thread(server_loop, s);
     *out = s;
