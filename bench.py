@@ -952,13 +952,20 @@ def run_ours(args):
     t = C.Tracker(s.ref, upsample=U, method="ccu", in_dtype="u16", max_batch=BATCH, stream=stream, graphs=True)
     lat_passes = min(args.steps, 50)                # per-batch latency events for the first passes
 
+    # each batch's stream handle and device addresses, computed once: the host loop that
+    # issues a step's 40 launches then costs a few microseconds per batch, below the
+    # device's time per batch (the loop is otherwise the bound on a slow host)
+    lib = C.lib()
+    fbase, obase = frames_dev.data_ptr(), outs.data_ptr()
+    issue = [(streams[b % len(streams)], streams[b % len(streams)].cuda_stream, fbase + lo * H * W * 2, hi - lo,
+              obase + lo * 24) for b, (lo, hi) in enumerate(bounds)]
+
     def one_pass(ev=None):
-        for b, (lo, hi) in enumerate(bounds):
-            si = streams[b % len(streams)]
+        for b, (si, sh, fp, m, op) in enumerate(issue):
             if ev is not None:
                 ev[b][0].record(si)
-            C.ccst_set_stream(t.ctx, si.cuda_stream)
-            C.ccst_track(t.ctx, frames_dev[lo:hi], hi - lo, 0, outs[lo:hi])
+            if lib.ccst_set_stream(t.ctx, sh) or lib.ccst_track(t.ctx, fp, m, 0, op):
+                raise C.CcstError(-1, lib.ccst_last_error(t.ctx).decode())
             if ev is not None:
                 ev[b][1].record(si)
 
@@ -980,8 +987,10 @@ def run_ours(args):
         t_begin.record(stream)
         for st in streams[1:]:
             st.wait_event(t_begin)
+        h0 = time.perf_counter()
         for i in range(args.steps):
             one_pass(lat_ev[i] if i < lat_passes else None)
+        host_issue_s = time.perf_counter() - h0
         for st in streams[1:]:
             e = torch.cuda.Event()
             e.record(st)
@@ -1102,6 +1111,9 @@ def run_ours(args):
         "clocks": clk,
         "e2e": e2e,
         "gpu_launches": launches,                       # one tracking kernel per batch
+        "host_issue": {"ms_per_step": host_issue_s * 1e3 / args.steps, "gpu_ms_per_step": total_ms / args.steps,
+                       "basis": "wall time of the host loop that issues a step's launches (and its latency "
+                                "events), against the device time of a step: near equal means host-bound"},
         "guard": {"frames": int(len(flags)), "int": int(np.sum((flags & C.R_INT_GUARD) != 0)),
                   "sub": int(np.sum((flags & C.R_SUB_GUARD) != 0)), "df64": int(np.sum((flags & C.R_DF64) != 0)),
                   "overflow": int(np.sum((flags & C.R_OVERFLOW) != 0))},
