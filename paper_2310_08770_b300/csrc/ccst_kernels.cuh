@@ -1514,27 +1514,37 @@ __device__ void upsampled_pass_tc(const Geom& g, const Smem& S, TopK<kTopK>& top
             okm[k] = in && x >= 1;
         }
         const float sense = g.sense;
-        for (int r = warp; r < 2 * nt; r += nwarp) {
-            const int sg = r >= nt ? 1 : 0, lt = r - sg * nt, t = 1 + lt, ts = sg ? -t : t;
-            const bool rowok = sg || t <= g.pmax;
-            const float2* row = stg + (size_t)(sg * TC + lt) * T8;
-            float2 v[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int x = lane + 32 * k;
-                v[k] = x <= g.h0 ? row[x] : make_float2(0.f, 0.f);
-            }
-            if (dbg) {                                          // debug surfaces: the generic path
-#pragma unroll
+        if (dbg) {                                              // debug surfaces: the generic path
+            for (int r = warp; r < 2 * nt; r += nwarp) {
+                const int sg = r >= nt ? 1 : 0, lt = r - sg * nt, t = 1 + lt;
+                const float2* row = stg + (size_t)(sg * TC + lt) * T8;
                 for (int k = 0; k < 4; ++k)
-                    if (lane + 32 * k <= g.h0) emit.quad(sg, t, lane + 32 * k, v[k].x, v[k].y);
-                continue;
+                    if (lane + 32 * k <= g.h0) emit.quad(sg, t, lane + 32 * k, row[lane + 32 * k].x, row[lane + 32 * k].y);
             }
+        } else {
+            // the hot loop only loads a row and compares its points with the threshold; the
+            // rare points at or above it (about one a frame) are kept in one block after it
+            for (int r = warp; r < 2 * nt; r += nwarp) {
+                const int sg = r >= nt ? 1 : 0, lt = r - sg * nt;
+                const bool rowok = sg || 1 + lt <= g.pmax;
+                const float2* row = stg + (size_t)(sg * TC + lt) * T8;
+                float vp[4], vm[4];
+                bool hit = false;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float vp = sense * (v[k].x - v[k].y + gp[k]), vm = sense * (v[k].x + v[k].y + gm[k]);
-                if (rowok && okp[k] && vp >= thr) emit.keep(vp, ts, lane + 32 * k);
-                if (rowok && okm[k] && vm >= thr) emit.keep(vm, ts, -(lane + 32 * k));
+                for (int k = 0; k < 4; ++k) {
+                    const float2 v = lane + 32 * k <= g.h0 ? row[lane + 32 * k] : make_float2(0.f, 0.f);
+                    vp[k] = sense * (v.x - v.y + gp[k]);
+                    vm[k] = sense * (v.x + v.y + gm[k]);
+                    hit |= (rowok && okp[k] && vp[k] >= thr) || (rowok && okm[k] && vm[k] >= thr);
+                }
+                if (__builtin_expect(hit, 0)) {
+                    const int ts = sg ? -(1 + lt) : 1 + lt;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (rowok && okp[k] && vp[k] >= thr) emit.keep(vp[k], ts, lane + 32 * k);
+                        if (rowok && okm[k] && vm[k] >= thr) emit.keep(vm[k], ts, -(lane + 32 * k));
+                    }
+                }
             }
         }
     }
