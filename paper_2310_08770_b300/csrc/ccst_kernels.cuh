@@ -2179,16 +2179,25 @@ __device__ __forceinline__ bool track_frame(const Geom& g, const Batch& b, const
         jw = 0;
     } else if (g.guard) {
         const float thr = vw - g.tau0 * scale;
-        // each thread kept its best kTopK points; count those within tau0 of the maximum
-        int nc = 0;
+        // each thread kept its best kTopK points; count those within tau0 of the maximum,
+        // and whether some thread kept kTopK of them (it may have dropped more): one warp
+        // reduction each, then one barrier (S.rj[32 ..], apart from block_argmax's entries)
         unsigned mine = 0;
 #pragma unroll
-        for (int k = 0; k < kTopK; ++k) {
-            const bool q = top.v[k] >= thr;
-            mine |= (q ? 1u : 0u) << k;
-            nc += __syncthreads_count(q);
+        for (int k = 0; k < kTopK; ++k) mine |= (top.v[k] >= thr ? 1u : 0u) << k;
+        {
+            const int cw = (int)__reduce_add_sync(0xffffffffu, (unsigned)__popc(mine));
+            const bool fw = __any_sync(0xffffffffu, top.v[kTopK - 1] >= thr);
+            if ((threadIdx.x & 31) == 0) S.rj[32 + (threadIdx.x >> 5)] = cw | (fw ? 1 << 16 : 0);
         }
-        const bool full = __syncthreads_or(top.v[kTopK - 1] >= thr);
+        __syncthreads();
+        int nc = 0;
+        bool full = false;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            const int e = S.rj[32 + w];
+            nc += e & 0xffff;
+            full |= (e >> 16) != 0;
+        }
         if (nc > 1) {
             flags |= 0x02u;
             if (!full && nc <= kMaxCand) {
