@@ -1163,11 +1163,21 @@ struct Emitter {
     const Geom& g;
     const Smem& S;
     TopK<kTopK>& top;
-    float thr;
-    float* dbg;
     // thr: candidate-list threshold (kCollect), else a lower bound below which no point can
     // be the maximum or within the near-tie band of it (the (0, 0) point's value minus that
-    // band): most points stop at this one comparison.
+    // band): most points stop at this one comparison. In top-K mode each thread raises it
+    // as it keeps points: no point below the thread's best so far minus the band can be
+    // within the band of the maximum. The raise uses twice the band, so that its rounding
+    // (an ulp of values of a few percent of sum w|X|, against a band of eps32 sum w|X|)
+    // keeps it below the threshold the guard applies later.
+    mutable float thr;
+    float* dbg;
+    float band;
+    __device__ __forceinline__ Emitter(const Geom& g_, const Smem& S_, TopK<kTopK>& top_, float thr_, float* dbg_)
+        : g(g_), S(S_), top(top_), thr(thr_), dbg(dbg_), band(2.f * (g_.sense * S_.gP[0] - thr_)) {}
+    __device__ __forceinline__ void raise(float v) const {
+        if (!kCollect && !dbg) thr = fmaxf(thr, v - band);
+    }
     __device__ __forceinline__ void operator()(float raw, int ty, int tx) const {
         const float v = g.sense * raw;
         if (!kCollect && dbg) dbg[grid_index(g, ty, tx)] = raw;
@@ -1178,6 +1188,7 @@ struct Emitter {
             if (k < kMaxCand) { S.cj[k] = j; S.cv[k] = v; }
         } else {
             top.push(v, j);
+            raise(v);
         }
     }
     // the two points (+-tx) of row t of the sign `sg` (0: +t, 1: -t) from (A, B)
@@ -1201,6 +1212,7 @@ struct Emitter {
             if (k < kMaxCand) { S.cj[k] = j; S.cv[k] = v; }
         } else {
             top.push(v, j);
+            raise(v);
         }
     }
 };
@@ -1484,7 +1496,8 @@ __device__ void upsampled_pass_tc(const Geom& g, const Smem& S, TopK<kTopK>& top
     }
     // the surface's maximum: only points within the near-tie band of it can matter, so the
     // top-K pass pushes no point below it minus the band (thr = the (0, 0) value minus the
-    // band; 1% slack keeps the raised threshold below the one the guard applies later)
+    // band; taking twice the band keeps the raised threshold, rounding included, below the
+    // one the guard applies later)
     for (int o = 16; o; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
     if (lane == 0) S.rv[warp] = vmax;
     __syncthreads();
@@ -1492,7 +1505,7 @@ __device__ void upsampled_pass_tc(const Geom& g, const Smem& S, TopK<kTopK>& top
         float m = -INFINITY;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, S.rv[w]);
         const float band = g.sense * S.gP[0] - thr;
-        const float raised = m - 1.01f * band;
+        const float raised = m - 2.f * band;
         if (raised > thr) thr = raised;
     }
     __syncthreads();

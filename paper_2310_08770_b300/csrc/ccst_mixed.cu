@@ -766,12 +766,20 @@ __global__ void __launch_bounds__(mix_threads(H, W), mix_min_ctas(H, W)) __clust
         // ---- a6: the contraction, chunk by chunk of t (skipped by the pair diagnostic)
         TopK<kTopK> top;
         top.init();
-        const float lb = -P.tau0 * scale;                     // D(0, 0) = 0 is a candidate
+        // D(0, 0) = 0 is a candidate, so no point below -tau0 sum w|X| can matter. Each thread
+        // raises that bound as it keeps points: no point below its best so far minus the
+        // band can be within the band of the maximum. Twice the band keeps the raised bound,
+        // rounding included, below the level-0 threshold applied later.
+        const float lb = -P.tau0 * scale;
+        float lb_run = lb;
         auto emit = [&](float D, int ty, int tx) {
             const int j = (ty + h0) * M + (tx + h0);
             if (dbg_sub) dbg_sub[j] = D;
             const float v = sense * D;
-            if (v >= lb) top.push(v, j);
+            if (v >= lb_run) {
+                top.push(v, j);
+                if (!dbg_sub) lb_run = fmaxf(lb_run, v + 2.f * lb);
+            }
         };
         auto epilogue = [&](int t, int tx, float4 s) {
             if (t <= pmax) {
