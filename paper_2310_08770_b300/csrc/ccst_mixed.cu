@@ -78,6 +78,7 @@ struct MixSh {
     float2* SG;      // [G][RSG]: staged rows
     float4* CE;      // [TCp][KB]: stage-A output (C0, E0, C1, E1)
     float4* PS;      // [TC][TX]: stage-B partial sums (CL > 1)
+    float2* TBs;     // [Wc][TXp]: the stage-B table (p.tbs; CL = 1), at PS's place
     float2* gy;      // level 1: [Hh] E(m, ry)
     float2* fy;      // level 1: [kMaxCand][Hh] E(m, ty) - E(m, ry)
     float2* acol;    // level 1: [kMaxCand][KB]
@@ -112,6 +113,7 @@ __host__ __device__ inline MixSh mix_carve(const MixPlan& p, unsigned char* base
     s.CE = (float4*)w;
     const int TCp = (p.TC + kTM - 1) / kTM * kTM;
     s.PS = (float4*)(w + mal(sizeof(float4) * (size_t)TCp * p.KB));
+    s.TBs = (float2*)s.PS;
     s.gy = (float2*)w;
     s.fy = s.gy + mal(sizeof(float2) * p.Hh) / sizeof(float2);
     s.acol = s.fy + (size_t)kMaxCand * p.Hh;
@@ -797,6 +799,14 @@ __global__ void __launch_bounds__(mix_threads(H, W), mix_min_ctas(H, W)) __clust
         }
         const int TC = P.TC, TAp = P.TAp, TXp = P.TXp;
         const int ntx = (TX + 1) / 2;
+        if (P.tbs) {
+            // the stage-B table into shared memory (one CTA: the band is every column); the
+            // barrier after stage A orders these stores before stage B reads them
+            const float4* src = reinterpret_cast<const float4*>(P.tB);
+            float4* dst = reinterpret_cast<float4*>(S.TBs);
+            const int n4 = Wc * TXp / 2;
+            for (int i = tid; i < n4; i += kNT) dst[i] = __ldg(src + i);
+        }
         for (int t0 = 1; t0 <= (a.dbg_pairs ? 0 : h0); t0 += TC) {
             const int tcn = min(TC, h0 - t0 + 1), ntg = (tcn + kTM - 1) / kTM;
             // stage A: (C0, E0, C1, E1)(t, kx) for the band
@@ -830,7 +840,9 @@ __global__ void __launch_bounds__(mix_threads(H, W), mix_min_ctas(H, W)) __clust
                     S.CE[(tg * kTM + r) * KB + c] = make_float4(ur[r] - vi[r], ui[r] + vr[r], ur[r] + vi[r], ui[r] - vr[r]);
             }
             __syncthreads();
-            // stage B: per (t, tx) the four sums over the band
+            // stage B: per (t, tx) the four sums over the band, the table entries from
+            // `ldtb` (shared memory with p.tbs, else global memory)
+            auto stage_b = [&](auto ldtb) {
             for (int task = tid; task < ntg * ntx; task += kNT) {
                 const int tg = task / ntx, q = task - tg * ntx;
                 const int txa = q, txb = q + ntx;
@@ -841,9 +853,8 @@ __global__ void __launch_bounds__(mix_threads(H, W), mix_min_ctas(H, W)) __clust
                     for (int h = 0; h < 2; ++h)
 #pragma unroll
                         for (int e = 0; e < 4; ++e) acc[r][h][e] = 0.f;
-                const float2* tb = P.tB + (size_t)b0 * TXp;
                 for (int c = 0; c < nb; ++c) {
-                    const float2 ba = ldg2(tb + (size_t)c * TXp + txa), bb = ldg2(tb + (size_t)c * TXp + txb);
+                    const float2 ba = ldtb((size_t)c * TXp + txa), bb = ldtb((size_t)c * TXp + txb);
 #pragma unroll
                     for (int r = 0; r < kTM; ++r) {
                         const float4 ce = S.CE[(tg * kTM + r) * KB + c];
@@ -870,6 +881,14 @@ __global__ void __launch_bounds__(mix_threads(H, W), mix_min_ctas(H, W)) __clust
                         }
                     }
                 }
+            }
+            };
+            if (P.tbs) {
+                const float2* tbs = S.TBs;
+                stage_b([&](size_t i) { return tbs[i]; });
+            } else {
+                const float2* tb = P.tB + (size_t)b0 * TXp;
+                stage_b([&](size_t i) { return ldg2(tb + i); });
             }
             if constexpr (CL > 1) {
                 Clu<CL>::sync();
@@ -1160,6 +1179,21 @@ int mix_plan_create(int H, int W, int u, int method, int in_dtype, float eps, fl
     const size_t work = std::max(std::max(std::max(ysg, lvl1), lvl2w), contraction(tc));
     if (band + work + small > limit) return -1;
     p.TC = tc;
+    // one-CTA sides from 96 px: a smaller chunk (a multiple of 8 rows, at least 32) beside a
+    // copy of the stage-B table, if both fit in the same work area (the same shared memory,
+    // so the same CTAs per SM); stage B then reads the table from shared memory instead of
+    // through L1. At 48 px the second chunk cost more than the copy saved (6.89 -> 6.54 M
+    // ROIs/s); at 96 px it gained (2.94 -> 2.97 M)
+    p.tbs = 0;
+    if (p.CL == 1 && H >= 96) {
+        const size_t tb = mix::mal(sizeof(float2) * (size_t)p.Wc * p.TXp);
+        for (int tc2 = tc / 8 * 8; tc2 >= 32; tc2 -= 8)
+            if (contraction(tc2) + tb <= work) {
+                p.TC = tc2;
+                p.tbs = 1;
+                break;
+            }
+    }
     p.off_small = (int)(band + mix::mal(work));
     p.smem = (int)(p.off_small + small);
 

@@ -25,6 +25,9 @@ struct MixPlan {
     int RSX, RSG, G;            // row strides (float2) of the band and staging buffers; staged rows
     int TC;                     // t rows per contraction chunk
     int TAp, TXp;               // row lengths of the stage-A (t) and stage-B (tx) tables
+    int tbs;                    // one-CTA sides: the stage-B table is copied into shared memory
+                                //   each frame, beside a t chunk small enough that the work
+                                //   area keeps its size
     int off_w, off_small, smem; // shared-memory carve: band, work area, small arrays (bytes)
     const float2* t4h;          // H: W_H^{n2 k1} [k1][n2] (column FFT)
     const float2* t4r;          // L: W_L^{n2 k1} [k1][n2] (half-length row FFT)
