@@ -1,6 +1,7 @@
 // ccst_adjoint.cuh -- the continuous peak of the cross-correlation interpolant and its
-// vector-Jacobian product (the adjoint of the displacement). Newton's sums and the VJP
-// spectra are FP64; the 2-D transforms run in double-float on the FP32 pipes.
+// vector-Jacobian product (the adjoint of the displacement). The 2-D transforms and
+// Newton's row sums run in double-float on the FP32 pipes (B300's FP64 rate is about 1/64
+// of its FP32 rate); the moments built from the row sums and the VJP spectra are FP64.
 //
 // The tracker's estimate is the extremum of the interpolant of Sec. III on the 1/u grid,
 // a piecewise-constant function of the pixels. The differentiable quantity is the
@@ -101,7 +102,6 @@ __global__ void __launch_bounds__(512) adj_kernel(Geom g, AdjArgs a) {
     dfc* BxF = (dfc*)(red + 6 * 16 + 16);      // [Wc] Bx as double-floats
     df* kapd = (df*)(BxF + Wc);                // [Wc] 2 pi kx' / W
     df* kap2d = kapd + Wc;                     // [Wc] -(2 pi kx' / W)^2
-    __shared__ int sdf;                        // Newton's sums in double-float (1) or FP64 (0)
     __shared__ double st[8];                   // sy, sx, hyy, hxy, hxx, step, f
     __shared__ int sflag;
     const double eps = (double)g.eps, inv_hw = 1.0 / ((double)H * W);
@@ -166,7 +166,6 @@ __global__ void __launch_bounds__(512) adj_kernel(Geom g, AdjArgs a) {
             st[0] = ((double)q.ipy * g.u + rint((double)q.dy * g.u - (double)q.ipy * g.u)) / g.u;
             st[1] = ((double)q.ipx * g.u + rint((double)q.dx * g.u - (double)q.ipx * g.u)) / g.u;
             sflag = 0;
-            sdf = 1;
         }
         __syncthreads();
         const double sy0 = st[0], sx0 = st[1];
@@ -189,63 +188,32 @@ __global__ void __launch_bounds__(512) adj_kernel(Geom g, AdjArgs a) {
             }
             __syncthreads();
             if (done) break;                                    // Ay, Bx now at s*
-            // row sums R0 = sum c X B, R1 = sum c X (i kx) B, R2 = sum c X (-kx^2) B: in double-float
-            // while the steps are large, in FP64 for the last ones
-            if (sdf) {
-                const int row = t / tpr, j = t - row * tpr;
-                if (row < H) {
-                    const dfc z0 = dfc{df{0.f, 0.f}, df{0.f, 0.f}};
-                    dfc r0 = z0, r1 = z0, r2 = z0, m0 = z0, m1 = z0, m2 = z0;
-                    const bool nyq_row = 2 * row == H;
-                    for (int kx = j; kx < Wc; kx += tpr) {
-                        const dfc xb = cmul(buf[kx * CS + row], BxF[kx]);
-                        const df kap = kapd[kx], kap2 = kap2d[kx];
-                        const dfc x1 = dfc{df_neg(df_mul(kap, xb.im)), df_mul(kap, xb.re)};
-                        const dfc x2 = dfc{df_mul(kap2, xb.re), df_mul(kap2, xb.im)};
-                        if (nyq_row && kx != 0 && 2 * kx != W) {
-                            m0 = cadd(m0, xb); m1 = cadd(m1, x1); m2 = cadd(m2, x2);
-                        } else {
-                            r0 = cadd(r0, xb); r1 = cadd(r1, x1); r2 = cadd(r2, x2);
-                        }
-                    }
-                    for (int o = tpr >> 1; o > 0; o >>= 1) {
-                        r0 = cadd(r0, shfl_xor_dfc(r0, o)); r1 = cadd(r1, shfl_xor_dfc(r1, o));
-                        r2 = cadd(r2, shfl_xor_dfc(r2, o)); m0 = cadd(m0, shfl_xor_dfc(m0, o));
-                        m1 = cadd(m1, shfl_xor_dfc(m1, o)); m2 = cadd(m2, shfl_xor_dfc(m2, o));
-                    }
-                    if (j == 0) {
-                        R[3 * row] = dfc_double(r0); R[3 * row + 1] = dfc_double(r1); R[3 * row + 2] = dfc_double(r2);
-                        if (nyq_row) { R[3 * H] = dfc_double(m0); R[3 * H + 1] = dfc_double(m1); R[3 * H + 2] = dfc_double(m2); }
+            // row sums R0 = sum c X B, R1 = sum c X (i kx) B, R2 = sum c X (-kx^2) B, in
+            // double-float (about 2^-46 a term; s* settles to about 1e-13 px)
+            const int row = t / tpr, j = t - row * tpr;
+            if (row < H) {
+                const dfc z0 = dfc{df{0.f, 0.f}, df{0.f, 0.f}};
+                dfc r0 = z0, r1 = z0, r2 = z0, m0 = z0, m1 = z0, m2 = z0;
+                const bool nyq_row = 2 * row == H;
+                for (int kx = j; kx < Wc; kx += tpr) {
+                    const dfc xb = cmul(buf[kx * CS + row], BxF[kx]);
+                    const df kap = kapd[kx], kap2 = kap2d[kx];
+                    const dfc x1 = dfc{df_neg(df_mul(kap, xb.im)), df_mul(kap, xb.re)};
+                    const dfc x2 = dfc{df_mul(kap2, xb.re), df_mul(kap2, xb.im)};
+                    if (nyq_row && kx != 0 && 2 * kx != W) {
+                        m0 = cadd(m0, xb); m1 = cadd(m1, x1); m2 = cadd(m2, x2);
+                    } else {
+                        r0 = cadd(r0, xb); r1 = cadd(r1, x1); r2 = cadd(r2, x2);
                     }
                 }
-            } else {
-                const int row = t / tpr, j = t - row * tpr;
-                if (row < H) {
-                    double2 r0 = {0, 0}, r1 = {0, 0}, r2 = {0, 0}, m0 = {0, 0}, m1 = {0, 0}, m2 = {0, 0};
-                    const bool nyq_row = 2 * row == H;
-                    for (int kx = j; kx < Wc; kx += tpr) {
-                        const double kap = 2.0 * CUDART_PI * adj_freq(kx, W) / W;
-                        const double2 xb = cmul(dfc_double(buf[kx * CS + row]), Bx[kx]);
-                        const double2 x1 = adj_i_times(kap, xb);
-                        const double2 x2 = make_double2(-kap * kap * xb.x, -kap * kap * xb.y);
-                        if (nyq_row && kx != 0 && 2 * kx != W) {
-                            m0.x += xb.x; m0.y += xb.y; m1.x += x1.x; m1.y += x1.y; m2.x += x2.x; m2.y += x2.y;
-                        } else {
-                            r0.x += xb.x; r0.y += xb.y; r1.x += x1.x; r1.y += x1.y; r2.x += x2.x; r2.y += x2.y;
-                        }
-                    }
-                    for (int o = tpr >> 1; o > 0; o >>= 1) {
-                        r0.x += __shfl_xor_sync(0xffffffffu, r0.x, o); r0.y += __shfl_xor_sync(0xffffffffu, r0.y, o);
-                        r1.x += __shfl_xor_sync(0xffffffffu, r1.x, o); r1.y += __shfl_xor_sync(0xffffffffu, r1.y, o);
-                        r2.x += __shfl_xor_sync(0xffffffffu, r2.x, o); r2.y += __shfl_xor_sync(0xffffffffu, r2.y, o);
-                        m0.x += __shfl_xor_sync(0xffffffffu, m0.x, o); m0.y += __shfl_xor_sync(0xffffffffu, m0.y, o);
-                        m1.x += __shfl_xor_sync(0xffffffffu, m1.x, o); m1.y += __shfl_xor_sync(0xffffffffu, m1.y, o);
-                        m2.x += __shfl_xor_sync(0xffffffffu, m2.x, o); m2.y += __shfl_xor_sync(0xffffffffu, m2.y, o);
-                    }
-                    if (j == 0) {
-                        R[3 * row] = r0; R[3 * row + 1] = r1; R[3 * row + 2] = r2;
-                        if (nyq_row) { R[3 * H] = m0; R[3 * H + 1] = m1; R[3 * H + 2] = m2; }
-                    }
+                for (int o = tpr >> 1; o > 0; o >>= 1) {
+                    r0 = cadd(r0, shfl_xor_dfc(r0, o)); r1 = cadd(r1, shfl_xor_dfc(r1, o));
+                    r2 = cadd(r2, shfl_xor_dfc(r2, o)); m0 = cadd(m0, shfl_xor_dfc(m0, o));
+                    m1 = cadd(m1, shfl_xor_dfc(m1, o)); m2 = cadd(m2, shfl_xor_dfc(m2, o));
+                }
+                if (j == 0) {
+                    R[3 * row] = dfc_double(r0); R[3 * row + 1] = dfc_double(r1); R[3 * row + 2] = dfc_double(r2);
+                    if (nyq_row) { R[3 * H] = dfc_double(m0); R[3 * H + 1] = dfc_double(m1); R[3 * H + 2] = dfc_double(m2); }
                 }
             }
             __syncthreads();
@@ -277,10 +245,7 @@ __global__ void __launch_bounds__(512) adj_kernel(Geom g, AdjArgs a) {
                 st[2] = hyy; st[3] = hxy; st[4] = hxx;
                 ++iters;
                 const double step = fmax(fabs(dy), fabs(dx));
-                if (sdf) {
-                    if (!(step >= 1e-9)) sdf = 0;                           // finish in FP64
-                    if (iters >= kAdjIters) sflag = 2;
-                } else if (!(step >= 1e-13)) {
+                if (!(step >= 1e-11)) {
                     sflag = 1;                                             // settled (or NaN: stop)
                 } else if (iters >= kAdjIters) {
                     sflag = 2;

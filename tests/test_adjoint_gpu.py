@@ -1,9 +1,9 @@
 """Continuous peak and its adjoint (ccst_peak_continuous / ccst_backward) through the C ABI,
 against the FP64 oracle (``oracle.adjoint_oracle``).
 
-Bar: s* within 1e-9 px of the oracle (both are FP64 Newton solutions of the same equation;
-the sums differ in order only), and the gradients, returned as float32, within 2e-6 of the
-largest oracle value of the same image.
+Bar: s* within 1e-9 px of the oracle (both are Newton solutions of the same equation: the
+oracle's sums in FP64, the kernel's row sums in double-float, about 2^-46 a term), and the
+gradients, returned as float32, within 2e-6 of the largest oracle value of the same image.
 """
 import numpy as np
 import pytest
