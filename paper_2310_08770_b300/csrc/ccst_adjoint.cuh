@@ -1,7 +1,8 @@
 // ccst_adjoint.cuh -- the continuous peak of the cross-correlation interpolant and its
-// vector-Jacobian product (the adjoint of the displacement). The 2-D transforms and
-// Newton's row sums run in double-float on the FP32 pipes (B300's FP64 rate is about 1/64
-// of its FP32 rate); the moments built from the row sums and the VJP spectra are FP64.
+// vector-Jacobian product (the adjoint of the displacement). The 2-D transforms, Newton's
+// row sums, the product spectrum and the VJP spectra run in double-float on the FP32 pipes
+// (B300's FP64 rate is about 1/64 of its FP32 rate); the phases, Newton's moments and the
+// partial-sum accumulation are FP64.
 //
 // The tracker's estimate is the extremum of the interpolant of Sec. III on the 1/u grid,
 // a piecewise-constant function of the pixels. The differentiable quantity is the
@@ -80,13 +81,15 @@ __device__ void adj_block_sum6(double v[6], double* red) {
 
 // Shared memory of adj_kernel, in double2: the transform buffer (then X as double-floats),
 // Ay[H], Bx[Wc], the row sums R[H][3] (+3 for the y-Nyquist row's middle columns), 6
-// doubles per warp, and the double-float column phases and factors BxF, kap, -kap^2 [Wc].
+// doubles per warp, the double-float column phases and factors BxF, kap, -kap^2 [Wc], and
+// the double-float row phases and factors AyF, kapy [H].
 __host__ __device__ inline int adj_nbuf(int H, int W) {
     const int a = (H / 2) * W, b = (W / 2 + 1) * (H + 1);
     return a > b ? a : b;
 }
 __host__ __device__ inline size_t adj_smem_bytes(int H, int W) {
-    return (size_t)(adj_nbuf(H, W) + H + (W / 2 + 1) + 3 * H + 3 + 3 * 16 + 8 + 2 * (W / 2 + 1) + 2) * sizeof(double2);
+    return (size_t)(adj_nbuf(H, W) + H + (W / 2 + 1) + 3 * H + 3 + 3 * 16 + 8 + 2 * (W / 2 + 1) + 2 + 2 * H) *
+           sizeof(double2);
 }
 
 // One CTA per frame f = blockIdx.x, blockIdx.x + gridDim.x, ... (blockDim.x = 512).
@@ -102,10 +105,12 @@ __global__ void __launch_bounds__(512) adj_kernel(Geom g, AdjArgs a) {
     dfc* BxF = (dfc*)(red + 6 * 16 + 16);      // [Wc] Bx as double-floats
     df* kapd = (df*)(BxF + Wc);                // [Wc] 2 pi kx' / W
     df* kap2d = kapd + Wc;                     // [Wc] -(2 pi kx' / W)^2
+    dfc* AyF = (dfc*)(kap2d + Wc);             // [H] Ay as double-floats
+    df* kapyd = (df*)(AyF + H);                // [H] 2 pi ky' / H
     __shared__ double st[8];                   // sy, sx, hyy, hxy, hxx, step, f
     __shared__ int sflag;
     const double eps = (double)g.eps, inv_hw = 1.0 / ((double)H * W);
-    const double2* Fb = g.FE64;
+    const dfc* FbD = g.FEdf;                   // F[b] as double-floats (H x Wc)
     double2* S = a.scratch + (size_t)blockIdx.x * HWc;
     dfc* Sd = (dfc*)S;                         // S as double-float scratch between the passes
     double2* P = a.part ? a.part + (size_t)blockIdx.x * HWc : nullptr;
@@ -145,22 +150,22 @@ __global__ void __launch_bounds__(512) adj_kernel(Geom g, AdjArgs a) {
         }
         __syncthreads();
         fft_r2_passes(buf, g.logH, Wc, CS, 1, g.twdf, g.logNtw, false);
-        // S keeps F[a] in FP64 (row-major); the buffer takes X = F[a] conj F[b] (FP64 product,
-        // kept as a double-float) with the fold weight c; each thread rewrites the slot it read
+        // Sd keeps F[a] (row-major); the buffer takes X = F[a] conj F[b] with the fold weight
+        // (1 at kx = 0 and W/2, 2 elsewhere: exact), all in double-float; each thread
+        // rewrites the slot it read
         for (int i = t; i < HWc; i += blockDim.x) {
             const int ky = i / Wc, kx = i - ky * Wc;
             const dfc fd = buf[kx * CS + ky];
-            const double2 fa = make_double2(df_to_double(fd.re), df_to_double(fd.im));
-            S[i] = fa;
-            const double c = (kx == 0 || 2 * kx == W) ? 1.0 : 2.0;
-            const double2 x = cmul(fa, cconj(Fb[i]));
-            buf[kx * CS + ky] = dfc{df_from_double(c * x.x), df_from_double(c * x.y)};
+            Sd[i] = fd;
+            const dfc x = cmul(fd, cconj(FbD[i]));
+            buf[kx * CS + ky] = (kx == 0 || 2 * kx == W) ? x : dfc{df_scale(x.re, 2.f), df_scale(x.im, 2.f)};
         }
         for (int k = t; k < Wc; k += blockDim.x) {
             const double kap = 2.0 * CUDART_PI * adj_freq(k, W) / W;
             kapd[k] = df_from_double(kap);
             kap2d[k] = df_from_double(-kap * kap);
         }
+        for (int k = t; k < H; k += blockDim.x) kapyd[k] = df_from_double(2.0 * CUDART_PI * adj_freq(k, H) / H);
         if (t == 0) {
             const Result q = a.rec[f];
             st[0] = ((double)q.ipy * g.u + rint((double)q.dy * g.u - (double)q.ipy * g.u)) / g.u;
@@ -179,6 +184,7 @@ __global__ void __launch_bounds__(512) adj_kernel(Geom g, AdjArgs a) {
                 double sn, cs;
                 sincospi(2.0 * adj_freq(k, H) * sy / H, &sn, &cs);
                 Ay[k] = make_double2(cs, sn);
+                AyF[k] = dfc{df_from_double(cs), df_from_double(sn)};
             }
             for (int k = t; k < Wc; k += blockDim.x) {
                 double sn, cs;
@@ -275,19 +281,32 @@ __global__ void __launch_bounds__(512) adj_kernel(Geom g, AdjArgs a) {
             wx = -(hyy * gx - hxy * gy) / det;
         }
         // dL/db spectra, symmetrised, into this CTA's partial sum
+        // (in double-float: the phases AyF, BxF, the frequencies kapy, kap, F[a] and F[b])
+        const df wyd = df_from_double(wy), wxd = df_from_double(wx);
+        // k' and the pair's k' (negated, except on a Nyquist index), each weighted by w, and
+        // the phase at k and at the pair
+        auto wdot = [&](int ky, int kx, df* kw, df* kwp, dfc* ph, dfc* pph) {
+            const bool ny = 2 * ky == H, nx = 2 * kx == W;
+            const df my = kapyd[ky], mx = kapd[kx];
+            *kw = df_add(df_mul(wyd, my), df_mul(wxd, mx));
+            *kwp = df_add(df_mul(wyd, ny ? my : df_neg(my)), df_mul(wxd, (nx || kx == 0) ? mx : df_neg(mx)));
+            const dfc ay = AyF[ky], bx = BxF[kx];
+            *ph = cmul(ay, bx);
+            *pph = cmul(ny ? ay : cconj(ay), nx ? bx : cconj(bx));
+        };
         if (P) {
             for (int i = t; i < HWc; i += blockDim.x) {
                 const int ky = i / Wc, kx = i - ky * Wc;
-                const double my = 2.0 * CUDART_PI * adj_freq(ky, H) / H, mx = 2.0 * CUDART_PI * adj_freq(kx, W) / W;
-                const bool ny = 2 * ky == H, nx = 2 * kx == W;
-                const double2 fa = S[i], ph = cmul(Ay[ky], Bx[kx]);
-                // pair's signed frequencies and phase: negated, except on a Nyquist index
-                const double pmy = ny ? my : -my, pmx = (nx || kx == 0) ? mx : -mx;
-                const double2 pph = cmul(ny ? Ay[ky] : cconj(Ay[ky]), nx ? Bx[kx] : cconj(Bx[kx]));
-                const double2 z = adj_i_times(wy * my + wx * mx, cmul(ph, fa));
-                const double2 zp = adj_i_times(wy * pmy + wx * pmx, cmul(pph, cconj(fa)));
+                df kw, kwp;
+                dfc ph, pph;
+                wdot(ky, kx, &kw, &kwp, &ph, &pph);
+                const dfc fa = Sd[i];
+                const dfc q = cmul(ph, fa), qp = cmul(pph, cconj(fa));
+                // z = i kw q, zp = i kwp qp; the partial sum takes (z + conj-free pair) / 2
+                const df sx = df_add(df_neg(df_mul(kw, q.im)), df_neg(df_mul(kwp, qp.im)));   // z.x + zp.x
+                const df sy = df_add(df_mul(kw, q.re), df_neg(df_mul(kwp, qp.re)));          // z.y - zp.y
                 const double2 p = P[i];
-                P[i] = make_double2(p.x + 0.5 * (z.x + zp.x), p.y + 0.5 * (z.y - zp.y));
+                P[i] = make_double2(p.x + 0.5 * df_to_double(sx), p.y + 0.5 * df_to_double(sy));
             }
         }
         // dL/da: V(k) = conj of (2 pi i w.k') conj F[b](k) e^{2 pi i k'.s}, symmetrised, then
@@ -295,16 +314,16 @@ __global__ void __launch_bounds__(512) adj_kernel(Geom g, AdjArgs a) {
         if (a.g_frames) {
             for (int i = t; i < HWc; i += blockDim.x) {
                 const int ky = i / Wc, kx = i - ky * Wc;
-                const double my = 2.0 * CUDART_PI * adj_freq(ky, H) / H, mx = 2.0 * CUDART_PI * adj_freq(kx, W) / W;
-                const bool ny = 2 * ky == H, nx = 2 * kx == W;
-                const double2 fb = Fb[i], ph = cmul(Ay[ky], Bx[kx]);
-                const double pmy = ny ? my : -my, pmx = (nx || kx == 0) ? mx : -mx;
-                const double2 pph = cmul(ny ? Ay[ky] : cconj(Ay[ky]), nx ? Bx[kx] : cconj(Bx[kx]));
-                const double2 z = adj_i_times(wy * my + wx * mx, cmul(ph, cconj(fb)));     // Z(k)
-                const double2 zp = adj_i_times(wy * pmy + wx * pmx, cmul(pph, fb));         // Z(pair)
-                // V = conj Z; V_h = (V(k) + conj V(pair)) / 2 = (conj Z(k) + Z(pair)) / 2
-                const double2 vh = make_double2(0.5 * (z.x + zp.x), 0.5 * (-z.y + zp.y));
-                buf[kx * CS + brev(ky, g.logH)] = dfc{df_from_double(vh.x), df_from_double(vh.y)};
+                df kw, kwp;
+                dfc ph, pph;
+                wdot(ky, kx, &kw, &kwp, &ph, &pph);
+                const dfc fb = FbD[i];
+                const dfc q = cmul(ph, cconj(fb)), qp = cmul(pph, fb);
+                // Z(k) = i kw q, Z(pair) = i kwp qp; V = conj Z; V_h = (V(k) + conj V(pair)) / 2
+                // = (conj Z(k) + Z(pair)) / 2
+                const df vx = df_add(df_neg(df_mul(kw, q.im)), df_neg(df_mul(kwp, qp.im)));   // Z.x + Zp.x
+                const df vy = df_add(df_neg(df_mul(kw, q.re)), df_mul(kwp, qp.re));          // -Z.y + Zp.y
+                buf[kx * CS + brev(ky, g.logH)] = dfc{df_scale(vx, 0.5f), df_scale(vy, 0.5f)};
             }
             __syncthreads();
             fft_r2_passes(buf, g.logH, Wc, CS, 1, g.twdf, g.logNtw, true);
