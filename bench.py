@@ -430,10 +430,14 @@ def adjoint_leg(C, torch, stream):
                         "shifted uniformly in [-2, 2] px, u=100, CC-U; dL/dd = 1",
             "value": n / ((times["forward"] + times["backward"]) / 1e3), "unit": "pairs/s (forward + backward)",
             "forward_ms": times["forward"], "backward_ms": times["backward"], "status_nonzero": bad,
-            "roofline": {"bound": "fp64", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "roofline": {"bound": "latency", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS, "flop_per_pair": flop,
                          "kernel": "adj_kernel (+ track_kernel in forward)",
-                         "peak_basis": "nominal B300 FP64 1.25 TFLOP/s (not measured)"}}, (p, sd)
+                         "peak_basis": "nominal B300 FP64 1.25 TFLOP/s (not measured): the rate FP64-precision "
+                                       "flops would have on the FP64 pipe; the kernel runs most of them as "
+                                       "double-float on the FP32 pipes, so frac can exceed 1",
+                         "bound_basis": "ncu: the FP64 pipe 36% busy, the first stall the barriers between the "
+                                        "kernel's phases (profiles/adj_kernel_64x64_1024pairs.txt)"}}, (p, sd)
 
 
 def adjoint_cpu_baseline(C, torch, stream, p, sd):
