@@ -1062,7 +1062,6 @@ __device__ __forceinline__ void stage_a_mma(const Geom& g, const Smem& S, int t0
     constexpr unsigned PL = (unsigned)SA * Hq * 8u;              // one P/Q plane, bytes
     const int TC = g.TC;
     const uint2* Tc = TA;
-    const uint2* Ts = TA + (size_t)g.TAB * Hq;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int gq = lane >> 2, tq = lane & 3;
     const int ntt = (TC + 15) >> 4, nnt = SA >> 3;
@@ -1141,8 +1140,13 @@ __device__ __forceinline__ void stage_a_simt(const Geom& g, const Smem& S, int t
 
 template <int H, int W>
 __device__ __forceinline__ void stage_a(const Geom& g, const Smem& S, int t0, const uint2* TA) {
-    if (H % 32 == 0 && g.tables_smem) stage_a_mma<H, W>(g, S, t0, TA);
-    else stage_a_simt(g, S, t0, TA);
+    // the warp-MMA form takes kx tiles of 8 columns: W >= 16 (W = 8 has W/2 = 4 columns)
+    if constexpr (H % 32 == 0 && W >= 16) {
+        if (g.tables_smem) stage_a_mma<H, W>(g, S, t0, TA);
+        else stage_a_simt(g, S, t0, TA);
+    } else {
+        stage_a_simt(g, S, t0, TA);
+    }
     stage_a_nyquist(g, S, t0, TA);
     __syncthreads();
 }
@@ -1228,7 +1232,6 @@ __device__ __forceinline__ void stage_b_mma(const Geom& g, const Smem& S, int t0
     constexpr unsigned R8 = 8u * SAq * 8u;                       // 8 operand rows, bytes
     const int T1 = g.T1p, T8 = g.T1p8, TC = g.TC;
     const uint2* WC = TB;
-    const uint2* WS = TB + (size_t)T1 * SAq;
     const float* WCN = (const float*)(TB + 2 * (size_t)T1 * SAq);
     const float* WSN = WCN + T8;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -1242,8 +1245,7 @@ __device__ __forceinline__ void stage_b_mma(const Geom& g, const Smem& S, int t0
         const int nt0 = 2 * (rem - sg * nng);
         if (t0 + 16 * tt > g.h0) continue;                       // warp-uniform
         const bool two = nt0 + 1 < nnt;                          // warp-uniform
-        const uint2* Ca = S.CB + (size_t)sg * TC * SAq;          // C0 / C1
-        const uint2* Eb = S.CB + (size_t)(2 + sg) * TC * SAq;    // E0 / E1
+        const uint2* Ca = S.CB + (size_t)sg * TC * SAq;          // C0 / C1 (E0 / E1 at deb bytes on)
         // rows 16 tt + gq (+ 8) of the combinations and tx rows 8 nt0 + gq (+ 8) of the tables;
         // rows past the chunk / the tables read the following rows of the shared area (in
         // bounds) and only feed discarded outputs
@@ -1588,8 +1590,12 @@ __device__ __forceinline__ void upsampled_pass(const Geom& g, const Smem& S, Top
         for (int c = 0; c < g.nchunk; ++c) {
             const int t0 = 1 + c * g.TC;
             stage_a<H, W>(g, S, t0, TA);
-            if (W % 32 == 0 && g.tables_smem) stage_b_mma<W, kCollect>(g, S, t0, TB, dsc, emit);
-            else stage_b_simt<kCollect>(g, S, t0, TB, dsc, emit);
+            if constexpr (W % 32 == 0) {
+                if (g.tables_smem) stage_b_mma<W, kCollect>(g, S, t0, TB, dsc, emit);
+                else stage_b_simt<kCollect>(g, S, t0, TB, dsc, emit);
+            } else {
+                stage_b_simt<kCollect>(g, S, t0, TB, dsc, emit);
+            }
             // the t = 0 row: S = 0, the surface is g(tx)
             if (t0 == 1) {
                 for (int x = threadIdx.x; x <= g.h0; x += blockDim.x) {

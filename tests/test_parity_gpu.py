@@ -179,7 +179,8 @@ def test_frame_stream_full_size_sampled(torch):
 # them from global memory
 @pytest.mark.parametrize("H,W,u", [(8, 8, 7), (16, 16, 1), (16, 32, 2), (32, 32, 37), (64, 32, 100),
                                    (32, 128, 100), (128, 64, 50), (64, 64, 256), (128, 128, 11),
-                                   (128, 128, 120), (128, 128, 200)])
+                                   (128, 128, 120), (128, 128, 200), (32, 8, 50), (64, 8, 100),
+                                   (128, 8, 100)])
 @pytest.mark.parametrize("method", [oracle.CC_U, oracle.CC_SN])
 def test_shapes_and_upsampling(torch, H, W, u, method):
     rng = np.random.default_rng(H * 1000 + W + u)
