@@ -196,6 +196,23 @@ def test_shapes_and_upsampling(torch, H, W, u, method):
     compare(res, orc, f"{H}x{W} u={u} m={method}")
 
 
+# every shape the power-of-two kernel accepts (H, W in {8, ..., 128}): each one is its own
+# instantiation, with its own choice of stage forms
+@pytest.mark.parametrize("H", [8, 16, 32, 64, 128])
+@pytest.mark.parametrize("W", [8, 16, 32, 64, 128])
+@pytest.mark.parametrize("method", [oracle.CC_U, oracle.CC_SN])
+def test_every_power_of_two_shape(torch, H, W, method):
+    rng = np.random.default_rng(7 * H + W)
+    sigma = max(1.2, min(H, W) / 16)
+    ref = synth.gaussian_spot(H, W, H / 2, W / 2, sigma, 800.0, 12.0)
+    d = rng.uniform(-min(H, W) / 6, min(H, W) / 6, size=(6, 2))
+    frames = np.array([rng.poisson(synth.gaussian_spot(H, W, H / 2 + p[1], W / 2 + p[0], sigma, 800.0, 12.0))
+                       for p in d], np.float32)
+    res = run_gpu(torch, ref, frames, u=40, method=method)
+    orc = oracle.track_batch(frames, ref, u=40, method=method)
+    compare(res, orc, f"{H}x{W} m={method}")
+
+
 def test_ccsn_stream_batch(torch):
     s = synth.frame_stream(seed=3, n=128, H=64, W=64, sigma=3.0, amplitude=1000.0, background=10.0, step=0.5,
                            bound=10.0)
