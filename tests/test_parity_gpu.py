@@ -213,6 +213,26 @@ def test_every_power_of_two_shape(torch, H, W, method):
     compare(res, orc, f"{H}x{W} m={method}")
 
 
+# the upsampling factor across the plan's switch points (the tcgen05 contraction at 128^2,
+# the chunked stages, the stage tables in shared or in global memory, odd and even grids)
+U_SWEEP = [1, 2, 3, 4, 5, 8, 13, 16, 33, 64, 101, 127, 150, 181, 255, 301, 512]
+
+
+@pytest.mark.parametrize("N", [64, 128])
+@pytest.mark.parametrize("u", U_SWEEP)
+def test_upsampling_factor_sweep(torch, N, u):
+    rng = np.random.default_rng(N + 13 * u)
+    ref = synth.gaussian_spot(N, N, N / 2, N / 2, 2.5, 1000.0, 10.0)
+    d = rng.uniform(-3, 3, size=(6, 2))
+    frames = np.array([rng.poisson(synth.gaussian_spot(N, N, N / 2 + p[1], N / 2 + p[0], 2.5, 1000.0, 10.0))
+                       for p in d], np.float32)
+    methods = (oracle.CC_U, oracle.CC_SN) if N == 128 and u in (1, 64, 101, 255, 512) else (oracle.CC_U,)
+    for method in methods:
+        res = run_gpu(torch, ref, frames, u=u, method=method)
+        orc = oracle.track_batch(frames, ref, u=u, method=method)
+        compare(res, orc, f"{N}x{N} u={u} m={method}")
+
+
 def test_ccsn_stream_batch(torch):
     s = synth.frame_stream(seed=3, n=128, H=64, W=64, sigma=3.0, amplitude=1000.0, background=10.0, step=0.5,
                            bound=10.0)
