@@ -294,6 +294,16 @@ def test_fallbacks_of_both_chained_fp32_launches_reach_the_double_float_kernel(t
         t.close()
 
 
+@pytest.mark.parametrize("N", [48, 96])
+@pytest.mark.parametrize("u", [2, 5, 16, 45, 64, 101, 181])
+def test_upsampling_factor_sweep(torch, N, u):
+    # the plan's chunking (one chunk, or 40-row chunks beside the shared-memory stage-B
+    # table at 96 px from h0 >= 32) across u
+    ref, frames = spots(N, 6, seed=160 + N + u)
+    res = track(torch, ref, frames, u)
+    check(ref, frames, res, u, oracle.CC_U)
+
+
 @pytest.mark.parametrize("N", [48, 96, 192, 256])
 def test_integer_near_ties_are_decided_in_double_float(torch, N):
     # noise-free spots shifted by 1/2 + d px along x: the integer shifts 0 and 1 nearly tie
