@@ -88,6 +88,15 @@ def test_rt_track_matches_oracle_ccu(torch, H, W, u, a0, n, step, u16):
     compare(rt_gpu(torch, frames, u, a0), orc)
 
 
+# extreme aspect ratios: the update's cooperative grid is max(H/2, W/2 + 1) CTAs, and the
+# narrow shapes take the plain-FP32 contraction stages
+@pytest.mark.parametrize("H,W", [(8, 8), (128, 8), (8, 128), (128, 32), (16, 64)])
+def test_rt_track_shapes(torch, H, W):
+    frames, _ = spot_stream(10, H, W, 0.3, seed=3 * H + W, sigma=1.5)
+    orc = rt.rt_track(frames.astype(np.float64), u=50, a0=0.3, method=oracle.CC_U)
+    compare(rt_gpu(torch, frames, 50, 0.3), orc)
+
+
 @pytest.mark.parametrize("H,W,u,a0,n", [(64, 64, 100, 0.2, 16), (32, 32, 50, 0.5, 12)])
 def test_rt_track_matches_oracle_ccsn(torch, H, W, u, a0, n):
     frames, _ = spot_stream(n, H, W, 0.4, seed=7 * H + u)
