@@ -103,6 +103,18 @@ def test_offline_passes_match_oracle_ccu(torch, H, W, u, n, passes, u16):
         compare(res[p], ores[p])
 
 
+# extreme aspect ratios (the accumulation's grid follows the frame shape; the narrow shapes
+# take the plain-FP32 contraction stages)
+@pytest.mark.parametrize("H,W", [(8, 8), (128, 8), (8, 128), (128, 32)])
+def test_offline_shapes(torch, H, W):
+    frames = spot_frames(24, H, W, seed=5 * H + W, u16=True)
+    res, refs = stepwise(torch, frames, 50, 2)
+    ores, orefs = off.offline_track(frames.astype(np.float64), u=50, passes=2)
+    check_refs(refs, orefs, oracle.CC_U)
+    for p in range(3):
+        compare(res[p], ores[p])
+
+
 @pytest.mark.parametrize("H,W,u,n,passes", [(64, 64, 100, 32, 2), (32, 32, 50, 200, 3)])
 def test_offline_passes_match_oracle_ccsn(torch, H, W, u, n, passes):
     frames = spot_frames(n, H, W, seed=3 * n + u)
