@@ -213,6 +213,22 @@ def test_every_power_of_two_shape(torch, H, W, method):
     compare(res, orc, f"{H}x{W} m={method}")
 
 
+# uint16 input, aligned (16-byte vector loads) and with a row pitch of W + 3 (scalar loads),
+# on the narrow and the square shapes: the same records either way, and the oracle's
+@pytest.mark.parametrize("H,W", [(8, 8), (128, 8), (8, 128), (64, 64), (128, 128)])
+def test_uint16_ingest_aligned_and_pitched(torch, H, W):
+    rng = np.random.default_rng(11 * H + W)
+    sigma = max(1.2, min(H, W) / 16)
+    ref = synth.gaussian_spot(H, W, H / 2, W / 2, sigma, 800.0, 12.0)
+    d = rng.uniform(-min(H, W) / 6, min(H, W) / 6, size=(6, 2))
+    frames = np.array([rng.poisson(synth.gaussian_spot(H, W, H / 2 + p[1], W / 2 + p[0], sigma, 800.0, 12.0))
+                       for p in d]).astype(np.uint16)
+    a = run_gpu(torch, ref, frames, u=50)
+    b = run_gpu(torch, ref, frames, u=50, pitch_pad=3)
+    assert a.tobytes() == b.tobytes()
+    compare(a, oracle.track_batch(frames.astype(np.float64), ref, u=50), f"{H}x{W} u16")
+
+
 # the upsampling factor across the plan's switch points (the tcgen05 contraction at 128^2,
 # the chunked stages, the stage tables in shared or in global memory, odd and even grids)
 U_SWEEP = [1, 2, 3, 4, 5, 8, 13, 16, 33, 64, 101, 127, 150, 181, 255, 301, 512]
