@@ -95,6 +95,18 @@ def test_rois_equal_per_reference_contexts_and_the_oracle(torch, method):
     assert not bad, bad
 
 
+@pytest.mark.parametrize("u", [7, 120, 200])
+def test_rois_upsampling_factors(torch, u):
+    # the 128 px class across its plans: tcgen05 at u = 7 (one chunk), the warp-MMA stages
+    # in chunks at u = 120, the stage tables read from global memory at u = 200 (the
+    # 128 x 128 ROI kernel with both contraction forms); every record equals its own
+    # context's
+    items = uneven(12, [16, 64, 128], seed=20 + u)
+    res = run_rois(torch, items, u)
+    for i, ((ref, frame), g) in enumerate(zip(items, res)):
+        assert g.tobytes() == single(torch, ref, frame, u).tobytes(), (u, i)
+
+
 def test_rois_u16_padded_rows_and_many_items(torch):
     items = uneven(300, [32, 64], seed=5, u16=True)
     res = run_rois(torch, items, 50, pad=8, u16=True)
