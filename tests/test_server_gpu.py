@@ -182,6 +182,34 @@ def test_general_size_cameras_equal_the_roi_path(torch):
         t.close()
 
 
+def test_double_float_cameras_beside_fp32_and_power_of_two_ones(torch):
+    # a 40 px camera (no FP32 plan: the double-float kernel, on the batch's second stream
+    # after the FP32 launches), 96 px (FP32 general-size) and 64 / 128 px (power-of-two) in
+    # the same batches: every result equals the ROI path's for that frame
+    cams = cameras(seed=13, sides=(64, 40, 96, 128), n=6)
+    t, ids, srv = make_server(cams)
+    try:
+        want = {}
+        for k, (_, frames) in enumerate(cams):
+            d = torch.from_numpy(frames.view(np.int16)).cuda().view(torch.uint16)
+            out = t.empty_results(len(frames))
+            C.ccst_track_rois(t.ctx, C.make_rois([d[i] for i in range(len(frames))], [ids[k]] * len(frames)),
+                              len(frames), out)
+            C.ccst_sync(t.ctx)
+            for i, r in enumerate(C.decode(out)):
+                if frames.shape[-1] == 40:
+                    assert r["flags"] & C.R_GENERIC and not r["flags"] & C.R_FP32_GENERAL
+                want[(k, i)] = r.tobytes()
+        tickets = [((k, i), submit_wait(srv, ids[k], cams[k][1][i])) for i in range(6) for k in range(len(cams))]
+        for key, tk in tickets:
+            assert C.ccst_server_poll(srv, tk, 20_000_000).tobytes() == want[key], key
+        st = C.ccst_server_read_stats(srv)
+        assert st["completed"] == st["submitted"] and st["in_flight"] == 0
+    finally:
+        C.ccst_server_destroy(srv)
+        t.close()
+
+
 def test_admission_by_bytes_charges_each_frame_its_own_size(torch):
     # a budget of one 128 x 128 uint16 frame (32 KiB): a 128 px frame alone fills it, while up
     # to 16 frames of a 32 px camera (2 KiB each) fit at once; nothing larger than the budget
