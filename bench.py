@@ -689,7 +689,7 @@ def rois_leg(C, torch, stream, n_rois=ROIS_N, sides=ROIS_SIDES, plain=True):
                         "reference (sigma U(1.5,4), peak U(200,5000), bg U(5,50)), Poisson frames shifted U(-3,3)^2 px, "
                         f"u={U}, CC-U",
             "value": n / (graph_ms / 1e3), "unit": "ROIs/s", "ms_per_batch": graph_ms,
-            "form": "one ccst_track_rois work list captured as one CUDA graph (both kernels) and replayed",
+            "form": "one ccst_track_rois work list captured as one CUDA graph (all its kernels) and replayed",
             "graphs": gstats, "records_equal_to_direct": graph_same,
             "direct_launch": {"value": n / (direct_ms / 1e3), "ms": direct_ms},
             "per_size_batched": {"value": n / (per_size_ms / 1e3), "ms": per_size_ms, "calls": len(per),

@@ -270,9 +270,8 @@ int ccst_add_reference(ccst_ctx* ctx, const float* ref, int H, int W, int* ref_i
  *   rois      host memory, n descriptors (read during the call).
  *   out_dev   device memory, n records; record i belongs to rois[i].
  * Work items run largest ROI first; each CTA takes the next item from a counter. The
- * power-of-two ROIs run on the context's stream in two launches (the 128 x 128 ROIs; the
- * 16, 32 and 64 px ROIs, whose CTAs re-plan their shared memory when the size changes).
- * Their records are identical to those of ccst_track on a context made for that ROI's
+ * power-of-two ROIs run on the context's stream, one launch per side present (128, 64,
+ * 32, 16 px), each compiled for its own side. Their records are identical to those of ccst_track on a context made for that ROI's
  * reference. ROIs of general sizes run on an internal stream beside them: one persistent
  * launch of the FP32 general-size kernel per side it takes (48, 96, 192, 256). On each
  * stream a launch may start in the last wave of the one before it (programmatic dependent
@@ -311,8 +310,8 @@ typedef struct ccst_tune_result {
  * (the default: the largest divisor of N not above sqrt(N); its cofactor; the next divisor
  * below) as the best of `reps` launches of two grid waves after a warm-up, and keeps the
  * fastest. Then it times both CTA sizes (512 and 256 threads, one per launch) and keeps the
- * faster: on the caller's ROI batch `rois` (n_rois > 0; run through ccst_track_rois, both
- * kernels, as the caller will run it), else on a work list of every plan's frames, largest
+ * faster: on the caller's ROI batch `rois` (n_rois > 0; run through ccst_track_rois, all
+ * its kernels, as the caller will run it), else on a work list of every plan's frames, largest
  * first. Later launches of the context (ccst_track, ccst_track_rois, the server) use them.
  *   rois     host, n_rois descriptors as for ccst_track_rois, or NULL with n_rois = 0. The splits change only the rounding order of the double-float DFTs: records
  * keep the parity bar and stay the same alone and in a batch. Power-of-two shapes have

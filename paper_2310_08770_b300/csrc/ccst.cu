@@ -639,6 +639,19 @@ static void lane_free(GenLane& l) {
     l = GenLane{};
 }
 
+// The uneven-ROI kernel of one power-of-two side (ccst_rois.cu): its address (null until a
+// plan of that side exists), the side's geometry (a parameter of the kernel), its dynamic
+// shared memory and its grid (CTAs per SM x SMs).
+struct RoiKernel {
+    const void* fn = nullptr;
+    Geom g{};
+    size_t smem = 0;
+    int grid = 0;
+};
+static int roi_side_slot(int side) { return side == 16 ? 0 : side == 32 ? 1 : side == 64 ? 2 : 3; }
+// Item counters of an uneven-ROI batch's power-of-two part: one per side's launch.
+constexpr int kRoiCounters = 4;
+
 // A second stream with its fork and join events, made on first use: the general-size part
 // of an uneven-ROI batch runs on it beside the power-of-two part.
 struct SideStream {
@@ -749,9 +762,8 @@ struct ccst_ctx {
     bool gen_dirty = true;            // plans or references changed since the last upload
     bool mix_off = false;             // ccst_autotune: the FP32 general-size kernel is bypassed
     bool general = false;             // every frame of this context takes the general-size kernel
-    Geom* d_geoms = nullptr;
     RefSpectra* d_refs = nullptr;
-    size_t geoms_cap = 0, refs_cap = 0;
+    size_t refs_cap = 0;
     RoiItem* d_items = nullptr;
     size_t items_cap = 0;
     std::vector<RoiItem> h_items;
@@ -772,12 +784,7 @@ struct ccst_ctx {
     int64_t roi_graph_instantiations = 0, roi_graph_replays = 0;
     SideStream rside;                 // ROI batches' general-size part (direct and captured)
     bool rois_dirty = true;
-    size_t rois_smem = 0;             // ROI kernel for the 128 x 128 class
-    int rois_grid = 0;
-    int rois_big_cls = 1;             // its instantiation: 2 if the class's plan uses tcgen05, else 1
-    Geom rois_g128{};                 // the class's geometry, a parameter of that kernel
-    size_t rois_smem_small = 0;       // ROI kernel for the classes up to 64 x 64
-    int rois_grid_small = 0;
+    RoiKernel rois_k[4];              // the ROI kernel of each side 16, 32, 64, 128 (roi_side_slot)
     void* d_addref_tmp = nullptr;     // ccst_add_reference: reference copy and FFT workspace
     size_t addref_tmp_bytes = 0;
     // graphs keyed by (stream, frames, n, pitch, out). Each owns a profiling event pair, a
@@ -963,7 +970,7 @@ static void free_all(ccst_ctx* c) {
     if (c->shared_ev) cudaEventDestroy(c->shared_ev);
     void* ptrs[] = {c->d_ref32, c->d_b64, c->d_FE64, c->d_FE32, c->d_tw64, c->d_tw32,
                     c->d_tab,   c->d_df,  c->d_frames, c->d_out, c->d_next, c->d_rtE, c->d_rtY, c->d_rtSync,
-                    c->d_offPart, c->d_offScratch, c->d_adjY, c->d_geoms, c->d_refs, c->d_items, c->d_addref_tmp,
+                    c->d_offPart, c->d_offScratch, c->d_adjY, c->d_refs, c->d_items, c->d_addref_tmp,
                     c->d_graph_counters, c->d_launch_counters, c->d_gplans, c->d_grefs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -2183,16 +2190,9 @@ extern "C" int ccst_add_reference(ccst_ctx* c, const float* ref, int H, int W, i
     return CCST_OK;
 }
 
-// Device copies of the plans and references, the kernel's shared-memory size and grid.
+// Device copies of the references; each side's ROI kernel, shared-memory size and grid.
 static int rois_upload(ccst_ctx* c) {
     if (!c->rois_dirty) return CCST_OK;
-    if (c->geoms_cap < c->plans.size()) {
-        if (c->d_geoms) cudaFree(c->d_geoms);
-        c->d_geoms = nullptr;
-        c->geoms_cap = 0;
-        CK(c, cudaMalloc(&c->d_geoms, 2 * c->plans.size() * sizeof(Geom)));
-        c->geoms_cap = 2 * c->plans.size();
-    }
     if (c->refs_cap < c->refs.size()) {
         if (c->d_refs) cudaFree(c->d_refs);
         c->d_refs = nullptr;
@@ -2200,38 +2200,24 @@ static int rois_upload(ccst_ctx* c) {
         CK(c, cudaMalloc(&c->d_refs, 2 * c->refs.size() * sizeof(RefSpectra)));
         c->refs_cap = 2 * c->refs.size();
     }
-    std::vector<Geom> gs;
-    size_t smem = 0, smem_small = 0;
-    int big_cls = 1;
-    for (auto& pl : c->plans) {
-        gs.push_back(pl.g);
-        if (!rois_size_ok(pl.g.H, pl.g.W)) continue;
-        if (pl.g.H <= 64) {
-            smem_small = std::max(smem_small, smem_plan(pl.g).total);
-        } else {
-            smem = std::max(smem, smem_plan(pl.g).total);
-            big_cls = pl.g.tc ? 2 : 1;                  // one 128 x 128 class per context
-            c->rois_g128 = pl.g;
-        }
-    }
     std::vector<RefSpectra> rs;
     for (auto& re : c->refs) rs.push_back(re.r);
-    CK(c, cudaMemcpy(c->d_geoms, gs.data(), gs.size() * sizeof(Geom), cudaMemcpyHostToDevice));
     CK(c, cudaMemcpy(c->d_refs, rs.data(), rs.size() * sizeof(RefSpectra), cudaMemcpyHostToDevice));
     int limit = 0, occ = 0, sms = 0;
     CK(c, cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-    for (int small = 0; small < 2; ++small) {
-        const void* k = track_rois_kernel_ptr(small ? 0 : big_cls);
-        CK(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, limit - kRoisStaticSmem));
-        CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, small ? track_threads(64, 64) : kThreads,
-                                                             small ? smem_small : smem));
+    for (auto& pl : c->plans) {
+        if (!rois_size_ok(pl.g.H, pl.g.W)) continue;
+        RoiKernel& rk = c->rois_k[roi_side_slot(pl.g.H)];
+        rk.fn = track_rois_kernel_ptr(pl.g.H, pl.g.tc != 0);
+        rk.g = pl.g;
+        rk.smem = smem_plan(pl.g).total;
+        const int threads = track_threads(pl.g.H, pl.g.W);
+        CK(c, cudaFuncSetAttribute(rk.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, limit - kRoisStaticSmem));
+        CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rk.fn, threads, rk.smem));
         if (occ < 1) return fail(c, CCST_E_SHAPE, "ccst_track_rois: the ROI kernel does not fit on an SM");
-        (small ? c->rois_grid_small : c->rois_grid) = occ * sms;
+        rk.grid = occ * sms;
     }
-    c->rois_smem = smem;
-    c->rois_big_cls = big_cls;
-    c->rois_smem_small = smem_small;
     c->rois_dirty = false;
     return CCST_OK;
 }
@@ -2882,36 +2868,29 @@ static void rois_sort(ccst_ctx* c, RoiItem* items, int64_t n) {
     });
 }
 
-// Leading items of a sorted list (largest first) that take the 512-thread ROI kernel.
-static int64_t rois_big_items(ccst_ctx* c, const RoiItem* items, int64_t n) {
-    int64_t k = 0;
-    while (k < n && c->plans[items[k].cls].g.H > 64) ++k;
-    return k;
-}
-
-// The power-of-two ROI kernels over n items already on the device, the first nbig of them
-// 128 x 128 (ordered by rois_sort): the 512-thread kernel over those, then the small-class
-// kernel over the rest, each chained behind the kernel launched before it (*chained) and
-// with its own counter (counter[0], counter[1], zeroed by the caller).
-static int rois_kernel_launch(ccst_ctx* c, const RoiItem* items_dev, int64_t n, int64_t nbig, Result* out,
+// The power-of-two ROI kernels over n items already on the device (items: their host copy),
+// ordered by rois_sort: one launch per side over that side's run of items, largest side
+// first, each chained behind the kernel launched before it (*chained) and with its own
+// counter (counter[0 .. kRoiCounters), zeroed by the caller).
+static int rois_kernel_launch(ccst_ctx* c, const RoiItem* items_dev, const RoiItem* items, int64_t n, Result* out,
                               cudaStream_t stream, unsigned* counter, bool* chained) {
-    for (int small = 0; small < 2; ++small) {
-        const int64_t m = small ? n - nbig : nbig;
-        if (m == 0) continue;
+    int k = 0;
+    for (int64_t s = 0; s < n; ++k) {
+        const int side = c->plans[items[s].cls].g.H;
+        int64_t e = s + 1;
+        while (e < n && c->plans[items[e].cls].g.H == side) ++e;
+        RoiKernel& rk = c->rois_k[roi_side_slot(side)];
         RoiBatch rb;
-        rb.items = items_dev + (small ? nbig : 0);
-        rb.n = m;
-        rb.geoms = c->d_geoms;
+        rb.items = items_dev + s;
+        rb.n = e - s;
         rb.refs = c->d_refs;
         rb.out = out;
-        rb.next = counter + small;
-        const int cap = small ? c->rois_grid_small : c->rois_grid;
-        const int grid = (int)(m < cap ? m : cap);
-        void* args[] = {&rb, &c->rois_g128};
-        CK(c, launch_kernel(track_rois_kernel_ptr(small ? 0 : c->rois_big_cls), grid,
-                            small ? track_threads(64, 64) : kThreads, args, small ? c->rois_smem_small : c->rois_smem,
-                            stream, *chained));
+        rb.next = counter + k;
+        const int grid = (int)(rb.n < rk.grid ? rb.n : rk.grid);
+        void* args[] = {&rb, &rk.g};
+        CK(c, launch_kernel(rk.fn, grid, track_threads(side, side), args, rk.smem, stream, *chained));
         *chained = true;
+        s = e;
     }
     return CCST_OK;
 }
@@ -2922,7 +2901,7 @@ static int rois_kernel_launch(ccst_ctx* c, const RoiItem* items_dev, int64_t n, 
 //     first), then the double-float kernel over the general items without an FP32 plan
 //     and the fallback list, a plain launch that starts once the FP32 launches have
 //     completed;
-//   - on `stream`: the 128 x 128 ROI kernel, then the small-class ROI kernel;
+//   - on `stream`: the ROI kernel of each side present, 128 down to 16;
 //   - joined.
 // (Without power-of-two items, or without general ones, everything runs on `stream`.)
 // On each stream a kernel is chained behind the one before it (programmatic dependent
@@ -2936,7 +2915,7 @@ struct RoiPart {
     const RoiItem* items_dev;   // n items, largest first
     const RoiItem* items;       // their host copy
     int64_t n;
-    unsigned* counter;          // 2 counters
+    unsigned* counter;          // kRoiCounters counters
 };
 struct GenPart {
     GenBatch gb;                // gb.items on the device (gen_sort order), gb.n items, gb.out
@@ -2953,7 +2932,7 @@ static int rois_chain_launch(ccst_ctx* c, const RoiPart& rp, const GenPart& gp, 
         if ((rc = gen_split_items(c, gp.gb, gp.items, *gp.lane, &sp))) return rc;
         if ((rc = gen_zero(c, sp, *gp.lane, gp.counter, stream))) return rc;
     }
-    if (rp.n > 0) CK(c, cudaMemsetAsync(rp.counter, 0, 2 * sizeof(unsigned), stream));
+    if (rp.n > 0) CK(c, cudaMemsetAsync(rp.counter, 0, kRoiCounters * sizeof(unsigned), stream));
     const bool fork = gp.gb.n > 0 && rp.n > 0;
     cudaStream_t gs = stream;
     if (fork) {
@@ -2965,8 +2944,7 @@ static int rois_chain_launch(ccst_ctx* c, const RoiPart& rp, const GenPart& gp, 
     bool chained = false;
     if (sp.ns > 0 && (rc = gen_mix_launch(c, gp.gb, sp, *gp.lane, gs, &chained))) return rc;
     if (fork) chained = false;
-    if (rp.n > 0 && (rc = rois_kernel_launch(c, rp.items_dev, rp.n, rois_big_items(c, rp.items, rp.n), out, stream,
-                                             rp.counter, &chained)))
+    if (rp.n > 0 && (rc = rois_kernel_launch(c, rp.items_dev, rp.items, rp.n, out, stream, rp.counter, &chained)))
         return rc;
     if (gp.gb.n > 0 && (rc = gen_direct_launch(c, gp.gb, sp, *gp.lane, gp.stride, gp.counter, gs))) return rc;
     if (fork) {
@@ -3042,7 +3020,7 @@ static int rois_graph_track(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccst_r
         auto bail = [&](int code) { free_roi_graph(e); return code; };
         cudaError_t err;
         if ((err = cudaEventCreateWithFlags(&e.done, cudaEventDisableTiming)) != cudaSuccess ||
-            (err = cudaMalloc(&e.counters, 3 * sizeof(unsigned))) != cudaSuccess)
+            (err = cudaMalloc(&e.counters, (kRoiCounters + 1) * sizeof(unsigned))) != cudaSuccess)
             return bail(fail(c, CCST_E_CUDA, std::string("ccst_track_rois: ") + cudaGetErrorString(err)));
         if (np > 0) {
             rois_sort(c, c->h_items.data(), np);
@@ -3072,7 +3050,7 @@ static int rois_graph_track(ccst_ctx* c, const ccst_roi* rois, int64_t n, ccst_r
         gpart.items = c->h_gitems.data();
         gpart.lane = lane;
         gpart.stride = stride;
-        gpart.counter = e.counters + 2;
+        gpart.counter = e.counters + kRoiCounters;
         const int lrc = rois_chain_launch(c, RoiPart{e.d_items, c->h_items.data(), np, e.counters}, gpart,
                                           (Result*)out_dev, c->stream, c->rside);
         err = cudaStreamEndCapture(c->stream, &graph);
@@ -3207,7 +3185,7 @@ struct ccst_server {
     std::deque<Span> spans;
     char* h_frames = nullptr;
     char* d_frames = nullptr;          // the same memory as the device addresses it
-    unsigned* d_counters = nullptr;    // three item counters per ring entry (power-of-two: two kernels; general)
+    unsigned* d_counters = nullptr;    // kRoiCounters + 1 item counters per ring entry (power-of-two sides; general)
     InFlight ring[kRing];
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -3357,10 +3335,10 @@ static void server_loop(ccst_server* s) {
             ok = gen_stage(c, b.lane, &gpart.gb, b.h_gitems, b.st, &gpart.stride) == CCST_OK;
             gpart.items = b.h_gitems;
             gpart.lane = &b.lane;
-            gpart.counter = s->d_counters + 3 * next + 2;
+            gpart.counter = s->d_counters + (kRoiCounters + 1) * next + kRoiCounters;
         }
         if (ok && np > 0) ok = rois_stage(c, b.h_items, np, b.st, b.d_items) == CCST_OK;
-        ok = ok && rois_chain_launch(c, RoiPart{b.d_items, b.h_items, np, s->d_counters + 3 * next}, gpart, b.d_out,
+        ok = ok && rois_chain_launch(c, RoiPart{b.d_items, b.h_items, np, s->d_counters + (kRoiCounters + 1) * next}, gpart, b.d_out,
                                      b.st, b.side) == CCST_OK;
         ok = ok && cudaMemcpyAsync(b.h_out, b.d_out, (size_t)m * sizeof(Result), cudaMemcpyDeviceToHost, b.st) ==
                        cudaSuccess;
@@ -3437,7 +3415,7 @@ extern "C" int ccst_server_create_ex(ccst_ctx* c, const ccst_server_config* cfg,
     cudaError_t e;
     if ((e = cudaHostAlloc(&s->h_frames, (size_t)s->cap, cudaHostAllocMapped)) != cudaSuccess) return bad(e);
     if ((e = cudaHostGetDevicePointer((void**)&s->d_frames, s->h_frames, 0)) != cudaSuccess) return bad(e);
-    if ((e = cudaMalloc(&s->d_counters, 3 * ccst_server::kRing * sizeof(unsigned))) != cudaSuccess) return bad(e);
+    if ((e = cudaMalloc(&s->d_counters, (kRoiCounters + 1) * ccst_server::kRing * sizeof(unsigned))) != cudaSuccess) return bad(e);
     for (int k = 0; k < s->depth; ++k) {
         auto& b = s->ring[k];
         if ((e = cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking)) != cudaSuccess) return bad(e);

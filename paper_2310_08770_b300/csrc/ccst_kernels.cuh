@@ -107,16 +107,15 @@ struct RoiItem {
     const void* frame;      // the ROI's pixels (in_dtype), rows `pitch` elements apart
     long long pitch;
     long long out_index;    // record slot
-    int cls;                // size class: index into RoiBatch::geoms
+    int cls;                // size class: the plan of the ROI's side
     int ref;                // reference: index into RoiBatch::refs
     int vec_ok;             // 16-byte vector loads allowed
     int pad;
 };
 
 struct RoiBatch {
-    const RoiItem* items;   // largest size first
+    const RoiItem* items;   // items of one side
     long long n;
-    const struct Geom* geoms;
     const RefSpectra* refs;
     Result* out;
     unsigned* next;         // item counter, zeroed before the launch
@@ -2309,10 +2308,10 @@ __global__ void __launch_bounds__(track_threads(H, W), track_min_ctas(H, W)) tra
     }
 }
 
-// Address of an uneven-ROI kernel (ccst_rois.cu): cls 0 is the instantiation for the size
-// classes up to 64 x 64 (track_threads(64, 64) threads, two CTAs per SM); 1 takes the
-// 128 x 128 class with either contraction form, 2 the 128 x 128 class of a tcgen05 plan.
-const void* track_rois_kernel_ptr(int cls);
+// Address of the uneven-ROI kernel for one side (ccst_rois.cu: 16, 32, 64 or 128; null for
+// another), with track_threads(side, side) threads; at 128, tc_only picks the instantiation
+// for a tcgen05 plan (compiled without the warp-MMA stages).
+const void* track_rois_kernel_ptr(int side, bool tc_only);
 
 // Address of track_kernel<H, W> (defined in the per-height translation units).
 const void* track_kernel_h8(int W);

@@ -111,7 +111,7 @@ def test_general_size_errors(torch):
 
 
 def test_graph_captured_batches_replay_the_direct_records(torch):
-    # with CCST_FLAG_GRAPHS a work list is captured once per stream (both kernels in one
+    # with CCST_FLAG_GRAPHS a work list is captured once per stream (all its kernels in one
     # graph) and replayed; records are byte-identical to the direct path's, every record is
     # written on every replay, and a new reference drops the captured graphs
     items = uneven([48, 32, 96, 64, 24, 128, 48, 16, 96, 32], seed=21, u16=True)
