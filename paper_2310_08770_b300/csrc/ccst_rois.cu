@@ -9,15 +9,22 @@
 
 namespace ccst {
 
-// kN: the side of every item of the launch, with the CTA shape of track_kernel<kN, kN> (so
+// CTAs per SM of a side's ROI kernel: track_kernel's count at 64 and 128 px. The 32 and
+// 16 px bodies need far less shared memory, and with the registers capped at 80 and 64 a
+// thread (a few hundred bytes of spills) three and four CTAs fit on an SM. Small frames are
+// latency-bound and take the extra warps: 16 px ROIs alone 5.63 -> 6.66 M ROIs/s; 32 px
+// alone unchanged, but the uneven mix, where its CTAs fill SMs beside the other sides'
+// kernels, 4.72 -> 4.79 M. The arithmetic is unchanged, so the records are too.
+constexpr int rois_min_ctas(int n) { return n == 32 ? 3 : n == 16 ? 4 : track_min_ctas(n, n); }
+
+// kN: the side of every item of the launch, with the CTA size of track_kernel<kN, kN> (so
 // that its records equal ccst_track's at that size); kTcOnly: the 128 x 128 class whose
 // plan contracts on tcgen05 (g.tc), compiled without the warp-MMA stages. Each
 // instantiation holds one side's body and reads that side's geometry g from the parameter
 // space as track_kernel reads its own: a kernel that carried several sides' bodies, with
 // the geometry in shared memory, lost time to instruction fetch.
 template <int kN, bool kTcOnly>
-__global__ void __launch_bounds__(track_threads(kN, kN), track_min_ctas(kN, kN))
-    track_rois_kernel(RoiBatch rb, Geom g) {
+__global__ void __launch_bounds__(track_threads(kN, kN), rois_min_ctas(kN)) track_rois_kernel(RoiBatch rb, Geom g) {
     __shared__ long long s_item;
     __shared__ RefSpectra s_ref;       // the current item's reference
     auto next_item = [&](RoiItem* it) {
