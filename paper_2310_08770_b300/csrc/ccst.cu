@@ -2880,6 +2880,8 @@ static int rois_kernel_launch(ccst_ctx* c, const RoiItem* items_dev, const RoiIt
         int64_t e = s + 1;
         while (e < n && c->plans[items[e].cls].g.H == side) ++e;
         RoiKernel& rk = c->rois_k[roi_side_slot(side)];
+        if (!rk.fn || k >= kRoiCounters)
+            return fail(c, CCST_E_SHAPE, "ccst_track_rois: no ROI kernel for a side of the work list");
         RoiBatch rb;
         rb.items = items_dev + s;
         rb.n = e - s;
